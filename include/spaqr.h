@@ -1,0 +1,209 @@
+/*
+ * spaqr.h -- C ABI of the GB300 spaQR library: a hierarchical sparse QR
+ * preconditioner for sparse least squares  min ||A x - b||_2,  A in R^{M x N},
+ * M >= N, rank(A) = N  (problem statement, Section 1 of Gnanasekaran & Darve,
+ * "Hierarchical Orthogonal Factorization: Sparse Least Squares problems").
+ *
+ * The factorization (Algorithm 1, Section 2.7) produces Q^T A W^{-1} ~= I with
+ * W a product of sparse upper-triangular and orthogonal factors; the solve is
+ * CGLS preconditioned on the right by W (Section 4).
+ *
+ * Conventions for every entry point:
+ *  - Return value: SPAQR_OK (0) or one of the SPAQR_ERR_* codes below; the
+ *    message of the last failure on the calling thread is spaqr_last_error().
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the current device.  The library never takes ownership
+ *    of caller memory; it copies what it keeps.
+ *  - All device work is issued on the stream given in the options (NULL =
+ *    legacy default stream) and every entry point returns with that stream
+ *    synchronised unless stated otherwise.
+ *  - Matrices are column-major; "ld" is the leading dimension in elements.
+ *  - There is no CPU fallback: without a CUDA device the compute entry points
+ *    fail with SPAQR_ERR_NO_DEVICE.  spaqr_analyze and the analysis queries
+ *    are host-only.
+ */
+#ifndef SPAQR_H
+#define SPAQR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPAQR_OK 0
+#define SPAQR_ERR_INVALID_ARG 1
+#define SPAQR_ERR_RANK_DEFICIENT 2 /* a diagonal block lost full column rank (Section 1: rank(A) = N) */
+#define SPAQR_ERR_CAPACITY 3       /* a planned size bound was exceeded */
+#define SPAQR_ERR_NOT_CONVERGED 4  /* CGLS hit maxit; x and info are still written */
+#define SPAQR_ERR_TIMEOUT 5        /* a bounded device wait gave up */
+#define SPAQR_ERR_CUDA 6
+#define SPAQR_ERR_OOM 7
+#define SPAQR_ERR_NO_DEVICE 8
+
+#define SPAQR_PREC_FP64 0  /* every step in FP64 */
+#define SPAQR_PREC_MIXED 1 /* factor in FP32, CGLS in FP64 */
+
+#define SPAQR_MODE_SPAQR 0  /* scaling + two-step sparsification (Algorithm 1) */
+#define SPAQR_MODE_DIRECT 1 /* no compression: multifrontal QR ("Direct", Section 4) */
+
+/* Sparse A in CSR form (host pointers).  Column indices in [0, n) and
+ * ascending within a row; no explicit zeros are required to be absent. */
+typedef struct {
+  int64_t m, n, nnz;
+  const int64_t* rowptr; /* m + 1 entries */
+  const int32_t* colidx; /* nnz entries */
+  const double* vals;    /* nnz entries */
+} spaqr_csr;
+
+/* Geometric ordering of a structured grid (Section 4.1, "regular geometric
+ * partitioning"): column j is the vertex (i, j', k) with j = i + nx*(j' + ny*k).
+ * depth = number of levels L of the nested-dissection tree (leaves at level L). */
+typedef struct {
+  int nx, ny, nz;
+  int depth;
+} spaqr_grid_ordering;
+
+typedef struct {
+  double eps;      /* rank tolerance of the sparsification RRQRs (Section 4: |R_ii| >= eps |R_11|) */
+  int skip;        /* scaling/sparsification start at stage L - skip (default 2, Section 4.2) */
+  int precision;   /* SPAQR_PREC_FP64 or SPAQR_PREC_MIXED */
+  int mode;        /* SPAQR_MODE_SPAQR or SPAQR_MODE_DIRECT */
+  double tol;      /* CGLS stop: ||A^T (A x - b)|| / ||A^T b|| < tol (default 1e-10) */
+  int maxit;       /* CGLS iteration cap (default 500) */
+  int use_graphs;  /* capture the per-iteration apply + SpMV sequence in a CUDA graph */
+  int verbose;     /* print per-stage statistics to stderr */
+  void* stream;    /* cudaStream_t for all device work (NULL = default stream) */
+} spaqr_options;
+
+/* Fill *opt with the defaults: eps 1e-4, skip 2, FP64, spaqr mode, tol 1e-10,
+ * maxit 500, graphs on, quiet, default stream. */
+void spaqr_default_options(spaqr_options* opt);
+
+/* ---------------------------------------------------------------- analysis
+ * Symbolic phase (host only): geometric nested dissection of the grid, the
+ * interfaces of every separator at every stage (modified nested dissection,
+ * Section 2.2, Fig. 2-3) and the clustering hierarchy used by the merges
+ * (Section 2.6).  Depends only on the grid and the depth, never on values. */
+typedef struct spaqr_analysis spaqr_analysis;
+
+/* Errors: INVALID_ARG for non-positive sizes or depth outside [1, 30]. */
+int spaqr_analyze(const spaqr_grid_ordering* ord, spaqr_analysis** out);
+void spaqr_analysis_destroy(spaqr_analysis* an);
+
+/* Number of clusters alive at stage k (1 <= k <= depth) and the total number
+ * of their vertices.  Host only. */
+int spaqr_analysis_stage_size(const spaqr_analysis* an, int k, int64_t* nclusters, int64_t* nverts);
+
+/* Copy the clusters of stage k in canonical order (node id, interface key):
+ * node[c] = nested-dissection node (heap numbering, root 0), level[c] = its
+ * level, vptr[c]..vptr[c+1] index verts[] = the cluster's vertex ids in
+ * ascending order.  Arrays are caller-owned host memory sized by
+ * spaqr_analysis_stage_size (vptr has nclusters + 1 entries). */
+int spaqr_analysis_stage_clusters(const spaqr_analysis* an, int k, int32_t* node, int32_t* level,
+                                  int64_t* vptr, int32_t* verts);
+
+/* ---------------------------------------------------------------- factor
+ * spaqr_factor: Algorithm 1 on A D (D = column scaling to unit 2-norms,
+ * Section 2.7) with the given analysis.  Level by level, leaves to root:
+ * block Householder QR of every separator front and reassignment of its extra
+ * rows (Section 2.3), scaling of the remaining interfaces (2.4), sparsification
+ * step 1 (2.5.1) and step 2 (2.5.2), merge (2.6).  A is read from host memory.
+ * The handle owns every device allocation.  The analysis must outlive nothing:
+ * the handle keeps what it needs.
+ * Errors: INVALID_ARG (shape mismatch, n != grid size, m < n), RANK_DEFICIENT,
+ * OOM, CUDA, NO_DEVICE. */
+typedef struct spaqr_handle spaqr_handle;
+int spaqr_factor(const spaqr_csr* A, const spaqr_analysis* an, const spaqr_options* opt, spaqr_handle** out);
+
+typedef struct {
+  int iters;         /* CGLS iterations taken */
+  double rel_resid;  /* final ||A^T (A x - b)|| / ||A^T b|| */
+  int converged;     /* rel_resid < tol */
+  double seconds;    /* wall time of the solve */
+} spaqr_solve_info;
+
+/* spaqr_solve: right-preconditioned CGLS (Section 4) on min ||A D W^{-1} y - b||,
+ * x = D W^{-1} y.  b has m entries, x has n; both host pointers when
+ * on_device == 0 (copied in / out inside the call) or device pointers when
+ * on_device != 0.  Returns NOT_CONVERGED (x and info written) at maxit. */
+int spaqr_solve(spaqr_handle* h, const double* b, double* x, int on_device, spaqr_solve_info* info);
+
+/* z <- W^{-1} z (transpose = 0) or z <- W^{-T} z (transpose = 1) for a device
+ * vector z of n entries in column (slot) order (Section 2.7: W is stored as a
+ * sequence of sparse triangular and orthogonal factors). */
+int spaqr_apply_Winv(spaqr_handle* h, double* z, int transpose);
+
+/* y <- A D x (forward = 1, x: n, y: m) or y <- (A D)^T x (forward = 0, x: m,
+ * y: n); device pointers.  The scaled operator the preconditioner is built for. */
+int spaqr_apply_A(spaqr_handle* h, const double* x, double* y, int forward);
+
+typedef struct {
+  double t_analyze;  /* seconds in spaqr_analyze (copied from the analysis) */
+  double t_factor;   /* seconds in spaqr_factor */
+  double t_solve;    /* seconds in the last spaqr_solve */
+  int iters;         /* iterations of the last solve */
+  int64_t nnz_W;     /* stored entries of W (Section 3 memory measure) */
+  int64_t n_ops;     /* number of stored W operations */
+  int64_t n_fronts;  /* eliminated separator fronts */
+  int64_t max_front_rows, max_front_cols;
+  int64_t top_cols, top_rows; /* size of the root front (Section 4.3 top separator) */
+  double flops_front;  /* algorithmic flops of the front QRs (Golub-Van Loan counts) */
+  double flops_sparsify;
+  double t_phase[6];   /* eliminate, reassign, scale, step1, step2, merge (device + host) */
+  int64_t launches;    /* kernels launched by the factorization */
+  int64_t syncs;       /* device-to-host waits during the factorization */
+  /* device time (CUDA events on the library stream) summed per kernel family:
+   * [0] block copies, [1] front QR (eliminate + scale), [2] column-pivoted QR,
+   * [3] other factor kernels (argmax, trsm, reflector apply),
+   * [4] W^{-1}/W^{-T} apply in the last solve, [5] SpMV + vector kernels in
+   * the last solve.  Seconds. */
+  double t_kernel[6];
+  int64_t n_kernel[6]; /* launches counted in each family */
+  double bytes_apply;  /* algorithmic bytes of one W^{-1} plus one W^{-T} apply */
+} spaqr_stats;
+
+int spaqr_get_stats(const spaqr_handle* h, spaqr_stats* st);
+
+/* ------------------------------------------------------------ W inspection
+ * The stored operations in factorization order (for tests and diagnostics).
+ * kind: 0 = R_s (elimination, Section 2.3), 1 = R_p (scaling, 2.4),
+ * 2 = Q_p (step-2 reflectors, 2.5.2).  For op i: stage, c (slots of s or p),
+ * w (R_s: columns of R_sn; Q_p: number of reflectors k). */
+int spaqr_num_ops(const spaqr_handle* h, int64_t* count);
+int spaqr_op_info(const spaqr_handle* h, int64_t i, int* kind, int* stage, int* c, int* w);
+/* Copy op i to host memory: slots (c ints), nslots (w ints, R_s only),
+ * R (c x c column-major; R_s/R_p) or V (c x w reflectors, Q_p), Rn (c x w,
+ * R_s only), taus (w, Q_p only).  Unused outputs may be NULL. */
+int spaqr_op_copy(const spaqr_handle* h, int64_t i, int32_t* slots, int32_t* nslots, double* R, double* Rn,
+                  double* taus);
+
+const char* spaqr_last_error(void);
+void spaqr_destroy(spaqr_handle* h);
+
+/* ----------------------------------------------------- batched dense kernels
+ * The dense building blocks of the factorization, exposed for testing.  Each
+ * takes `count` problems described by host arrays; A[i] are device pointers
+ * to column-major matrices; stream as in spaqr_options.
+ *
+ * spaqr_dense_front_qr: Householder QR (Section 2.3) of the first c[i]
+ * columns of the m[i] x n[i] matrix A[i], every reflector applied to the
+ * remaining columns; afterwards rows 0..c-1 hold R (diag >= 0, zeros below
+ * the diagonal in the first c columns) and rows c.. the transformed rows.
+ * Requires c[i] <= m[i]. */
+int spaqr_dense_front_qr(int count, double* const* A, const int* m, const int* n, const int* c, const int* ld,
+                         void* stream);
+
+/* spaqr_dense_qrcp: column-pivoted Householder QR stopped at the rank
+ * k = max r with |R_ii| >= eps |R_11| and R_ii != 0 (Section 4).  On return
+ * rank[i] (host) = k; A[i] rows 0..k-1 hold the first k rows of Q^T A[i] in the
+ * ORIGINAL column order; columns 0..k-1 of V[i] (device, m[i] x min(m,n),
+ * ld = m[i]) hold the reflectors (unit diagonal) and taus[i] (device) their
+ * scalars, so that Q = H_1 ... H_k. */
+int spaqr_dense_qrcp(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
+                     double* const* V, double* const* taus, int* rank, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPAQR_H */

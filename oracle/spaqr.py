@@ -264,17 +264,18 @@ class OracleSpaQR:
             raise RankDeficient(f"cluster {s}: zero pivot")
         self.stats.fronts.append((k, m, F.shape[1], cs))
         rest = cols[1:]
-        self.ops.append(
-            Op(
-                "Rs",
-                k,
-                self.slots[s].copy(),
-                R=np.triu(F[:cs, :cs]).copy(),
-                Rn=F[:cs, cs:].copy(),
-                nslots=np.concatenate([self.slots[c] for c in rest]) if rest else np.zeros(0, np.int64),
-                color=col,
+        if cs > 0:  # a cluster whose slots were all dropped stores no factor
+            self.ops.append(
+                Op(
+                    "Rs",
+                    k,
+                    self.slots[s].copy(),
+                    R=np.triu(F[:cs, :cs]).copy(),
+                    Rn=F[:cs, cs:].copy(),
+                    nslots=np.concatenate([self.slots[c] for c in rest]) if rest else np.zeros(0, np.int64),
+                    color=col,
+                )
             )
-        )
         roffs = offs[1:] - offs[1]
         for g in fg:
             del self.groups[g.gid]

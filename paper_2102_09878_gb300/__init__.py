@@ -1,0 +1,236 @@
+"""GB300-native spaQR: hierarchical sparse QR preconditioning for sparse least squares.
+
+Python face of the C ABI (include/spaqr.h).  Every floating-point step of the
+factorization and of the solve runs in the CUDA library; PyTorch only supplies
+device memory and streams.  See ``capi`` for the raw binding.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import capi
+from .capi import SpaqrError
+
+__all__ = ["Analysis", "SpaQR", "SpaqrError", "dense_front_qr", "dense_qrcp", "capi"]
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(int(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream))
+
+
+class Analysis:
+    """Symbolic analysis of an nx*ny*nz grid to nested-dissection depth L (host only)."""
+
+    def __init__(self, dims, depth: int):
+        lib = capi.load()
+        nx, ny, nz = (tuple(dims) + (1, 1))[:3]
+        self.dims = (int(nx), int(ny), int(nz))
+        self.depth = int(depth)
+        ordg = capi.GridOrdering(self.dims[0], self.dims[1], self.dims[2], self.depth)
+        h = C.c_void_p()
+        capi.check(lib.spaqr_analyze(C.byref(ordg), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stage_clusters(self, k: int):
+        """(node, level, vptr, verts) of the clusters alive at stage k."""
+        lib = capi.load()
+        nc, nv = C.c_int64(), C.c_int64()
+        capi.check(lib.spaqr_analysis_stage_size(self._h, k, C.byref(nc), C.byref(nv)))
+        node = np.zeros(nc.value, np.int32)
+        level = np.zeros(nc.value, np.int32)
+        vptr = np.zeros(nc.value + 1, np.int64)
+        verts = np.zeros(nv.value, np.int32)
+        capi.check(
+            lib.spaqr_analysis_stage_clusters(
+                self._h, k, capi.ptr(node), capi.ptr(level), capi.ptr(vptr), capi.ptr(verts)
+            )
+        )
+        return node, level, vptr, verts
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                capi.load().spaqr_analysis_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+class SpaQR:
+    """spaQR factorization of A (CSR arrays on the host) and its CGLS solve.
+
+    ``A`` is any object with m, n, rowptr (int64), colidx (int32), vals (float64).
+    """
+
+    def __init__(self, A, analysis: Analysis, eps: float = 1e-4, skip: int = 2, precision: str = "fp64",
+                 mode: str = "spaqr", tol: float = 1e-10, maxit: int = 500, use_graphs: bool = True,
+                 verbose: bool = False, stream=None):
+        lib = capi.load()
+        self.m, self.n = int(A.m), int(A.n)
+        self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+        self._colidx = np.ascontiguousarray(A.colidx, dtype=np.int32)
+        self._vals = np.ascontiguousarray(A.vals, dtype=np.float64)
+        csr = capi.Csr(self.m, self.n, int(self._rowptr[-1]), capi.ptr(self._rowptr), capi.ptr(self._colidx),
+                       capi.ptr(self._vals))
+        o = capi.default_options()
+        o.eps = float(eps)
+        o.skip = int(skip)
+        o.precision = capi.PREC[precision]
+        o.mode = capi.MODE[mode]
+        o.tol = float(tol)
+        o.maxit = int(maxit)
+        o.use_graphs = 1 if use_graphs else 0
+        o.verbose = 1 if verbose else 0
+        o.stream = _stream_ptr(stream)
+        self.precision = precision
+        self.options = o
+        h = C.c_void_p()
+        capi.check(lib.spaqr_factor(C.byref(csr), analysis.handle, C.byref(o), C.byref(h)))
+        self._h = h
+        self._analysis = analysis
+
+    # ------------------------------------------------------------- solve
+    def solve(self, b, check_convergence: bool = True):
+        """x = argmin ||A x - b||.  numpy in -> numpy out (host copies inside the
+        call); a CUDA float64 tensor in -> a CUDA tensor out (device pointers)."""
+        lib = capi.load()
+        info = capi.SolveInfo()
+        if hasattr(b, "is_cuda") and b.is_cuda:
+            import torch
+
+            x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+            bb = b.contiguous()
+            rc = lib.spaqr_solve(self._h, capi.ptr(bb), capi.ptr(x), 1, C.byref(info))
+        else:
+            bb = np.ascontiguousarray(b, dtype=np.float64)
+            x = np.zeros(self.n)
+            rc = lib.spaqr_solve(self._h, capi.ptr(bb), capi.ptr(x), 0, C.byref(info))
+        if rc != capi.SPAQR_OK and (check_convergence or rc != 4):
+            capi.check(rc)
+        self.last_info = dict(iters=info.iters, rel=info.rel_resid, converged=bool(info.converged),
+                              seconds=info.seconds)
+        return x
+
+    def apply_Winv(self, z, transpose: bool = False):
+        """In place z <- W^{-1} z (or W^{-T} z) for a CUDA float64 tensor of length n."""
+        assert z.is_cuda and z.dtype.is_floating_point and z.element_size() == 8 and z.is_contiguous()
+        capi.check(capi.load().spaqr_apply_Winv(self._h, capi.ptr(z), 1 if transpose else 0))
+        return z
+
+    def apply_A(self, x, forward: bool = True):
+        """A D x (forward) or (A D)^T x on CUDA float64 tensors."""
+        import torch
+
+        y = torch.empty(self.m if forward else self.n, dtype=torch.float64, device=x.device)
+        capi.check(capi.load().spaqr_apply_A(self._h, capi.ptr(x.contiguous()), capi.ptr(y), 1 if forward else 0))
+        return y
+
+    def stats(self) -> dict:
+        st = capi.Stats()
+        capi.check(capi.load().spaqr_get_stats(self._h, C.byref(st)))
+        out = {f: getattr(st, f) for f, _ in capi.Stats._fields_ if f not in ("t_phase", "t_kernel", "n_kernel")}
+        out["t_phase"] = dict(zip(["eliminate", "reassign", "scale", "step1", "step2", "merge"], list(st.t_phase)))
+        fam = ["copy", "front_qr", "qrcp", "other", "apply", "spmv"]
+        out["t_kernel"] = dict(zip(fam, list(st.t_kernel)))
+        out["n_kernel"] = dict(zip(fam, list(st.n_kernel)))
+        return out
+
+    def ops(self):
+        """The stored factors of W in factorization order (host copies)."""
+        lib = capi.load()
+        cnt = C.c_int64()
+        capi.check(lib.spaqr_num_ops(self._h, C.byref(cnt)))
+        out = []
+        for i in range(cnt.value):
+            kind, stage, c, w = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+            capi.check(lib.spaqr_op_info(self._h, i, C.byref(kind), C.byref(stage), C.byref(c), C.byref(w)))
+            c_, w_ = c.value, w.value
+            slots = np.zeros(c_, np.int32)
+            if kind.value == 0:
+                nslots = np.zeros(w_, np.int32)
+                R = np.zeros(c_ * c_)
+                Rn = np.zeros(c_ * w_)
+                capi.check(lib.spaqr_op_copy(self._h, i, capi.ptr(slots), capi.ptr(nslots), capi.ptr(R),
+                                             capi.ptr(Rn), None))
+                out.append(dict(kind="Rs", stage=stage.value, slots=slots, nslots=nslots,
+                                R=R.reshape(c_, c_, order="F"), Rn=Rn.reshape(c_, w_, order="F")))
+            elif kind.value == 1:
+                R = np.zeros(c_ * c_)
+                capi.check(lib.spaqr_op_copy(self._h, i, capi.ptr(slots), None, capi.ptr(R), None, None))
+                out.append(dict(kind="Rp", stage=stage.value, slots=slots, R=R.reshape(c_, c_, order="F")))
+            else:
+                V = np.zeros(c_ * w_)
+                taus = np.zeros(w_)
+                capi.check(lib.spaqr_op_copy(self._h, i, capi.ptr(slots), None, capi.ptr(V), None, capi.ptr(taus)))
+                out.append(dict(kind="Qp", stage=stage.value, slots=slots, V=V.reshape(c_, w_, order="F"),
+                                taus=taus))
+        return out
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                capi.load().spaqr_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------- dense kernels
+def _colmajor_cuda(A):
+    import torch
+
+    A = np.asarray(A, dtype=np.float64)
+    return torch.from_numpy(np.ascontiguousarray(A.T)).cuda()  # (n, m) row-major = m x n column-major
+
+
+def _from_colmajor(t, m, n):
+    return t.cpu().numpy().reshape(n, m).T.copy()
+
+
+def dense_front_qr(mats, cs, stream=None):
+    """Batched front QR (Section 2.3) of numpy matrices; returns the results."""
+    lib = capi.load()
+    ts = [_colmajor_cuda(A) for A in mats]
+    ptrs = (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+    m = np.array([A.shape[0] for A in mats], np.int32)
+    n = np.array([A.shape[1] for A in mats], np.int32)
+    c = np.array(cs, np.int32)
+    ld = np.maximum(m, 1).astype(np.int32)
+    capi.check(lib.spaqr_dense_front_qr(len(ts), ptrs, capi.ptr(m), capi.ptr(n), capi.ptr(c), capi.ptr(ld),
+                                        _stream_ptr(stream)))
+    return [_from_colmajor(t, A.shape[0], A.shape[1]) for t, A in zip(ts, mats)]
+
+
+def dense_qrcp(mats, eps: float, stream=None):
+    """Batched rank-revealing QR; returns (ranks, leading rows of Q^T A, V, taus)."""
+    import torch
+
+    lib = capi.load()
+    ts = [_colmajor_cuda(A) for A in mats]
+    Vs = [torch.zeros(max(min(A.shape), 1) * max(A.shape[0], 1), dtype=torch.float64, device="cuda") for A in mats]
+    Ts = [torch.zeros(max(min(A.shape), 1), dtype=torch.float64, device="cuda") for A in mats]
+    ptrs = (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+    vp = (C.c_void_p * len(ts))(*[t.data_ptr() for t in Vs])
+    tp = (C.c_void_p * len(ts))(*[t.data_ptr() for t in Ts])
+    m = np.array([A.shape[0] for A in mats], np.int32)
+    n = np.array([A.shape[1] for A in mats], np.int32)
+    ld = np.maximum(m, 1).astype(np.int32)
+    rank = np.zeros(len(ts), np.int32)
+    capi.check(lib.spaqr_dense_qrcp(len(ts), ptrs, capi.ptr(m), capi.ptr(n), capi.ptr(ld), float(eps), vp, tp,
+                                    capi.ptr(rank), _stream_ptr(stream)))
+    rows, Vout, Tout = [], [], []
+    for i, A in enumerate(mats):
+        k = int(rank[i])
+        out = _from_colmajor(ts[i], A.shape[0], A.shape[1])
+        rows.append(out[:k] if k < A.shape[0] else A.copy())
+        Vout.append(Vs[i].cpu().numpy()[: A.shape[0] * k].reshape(k, A.shape[0]).T.copy())
+        Tout.append(Ts[i].cpu().numpy()[:k].copy())
+    return rank, rows, Vout, Tout

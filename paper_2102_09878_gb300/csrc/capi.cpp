@@ -1,0 +1,432 @@
+// C ABI of the library (declared in include/spaqr.h).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+struct spaqr_analysis {
+  std::unique_ptr<spaqr::Analysis> an;
+};
+struct spaqr_handle {
+  std::unique_ptr<spaqr::Handle> h;
+};
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const spaqr::Error& e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(SPAQR_ERR_OOM, "host allocation failed");
+  } catch (const std::invalid_argument& e) {
+    return fail(SPAQR_ERR_INVALID_ARG, e.what());
+  } catch (const std::exception& e) {
+    return fail(SPAQR_ERR_CUDA, e.what());
+  }
+}
+
+int need_device() {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return fail(SPAQR_ERR_NO_DEVICE, "no CUDA device");
+  }
+  return SPAQR_OK;
+}
+
+double secs_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+}  // namespace
+
+namespace spaqr {
+void Handle::wait_caller() {
+  if (!ev) SPAQR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  SPAQR_CUDA(cudaEventRecord(ev, user_st));
+  SPAQR_CUDA(cudaStreamWaitEvent(st, ev, 0));
+}
+
+Handle::~Handle() {
+  free_apply_plan(*this);
+  if (ev) cudaEventDestroy(ev);
+  cudaFree(d_rowptr);
+  cudaFree(d_colidx);
+  cudaFree(d_vals);
+  cudaFree(d_trowptr);
+  cudaFree(d_tcolidx);
+  cudaFree(d_tvals);
+  cudaFree(d_D);
+  cudaFree(d_work);
+  if (own_stream && st) cudaStreamDestroy(st);
+}
+}  // namespace spaqr
+
+extern "C" {
+
+void spaqr_default_options(spaqr_options* o) {
+  if (!o) return;
+  o->eps = 1e-4;
+  o->skip = 2;
+  o->precision = SPAQR_PREC_FP64;
+  o->mode = SPAQR_MODE_SPAQR;
+  o->tol = 1e-10;
+  o->maxit = 500;
+  o->use_graphs = 1;
+  o->verbose = 0;
+  o->stream = nullptr;
+}
+
+const char* spaqr_last_error(void) { return g_last_error.c_str(); }
+
+int spaqr_analyze(const spaqr_grid_ordering* ord, spaqr_analysis** out) {
+  if (!ord || !out) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    auto* a = new spaqr_analysis();
+    a->an.reset(spaqr::build_analysis(ord->nx, ord->ny, ord->nz, ord->depth));
+    *out = a;
+    return SPAQR_OK;
+  });
+}
+
+void spaqr_analysis_destroy(spaqr_analysis* an) { delete an; }
+
+int spaqr_analysis_stage_size(const spaqr_analysis* an, int k, int64_t* nclusters, int64_t* nverts) {
+  if (!an || !nclusters || !nverts) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  if (k < 1 || k > an->an->depth) return fail(SPAQR_ERR_INVALID_ARG, "stage out of range");
+  const auto& st = an->an->stages[(size_t)k];
+  *nclusters = (int64_t)st.node.size();
+  *nverts = (int64_t)st.verts.size();
+  return SPAQR_OK;
+}
+
+int spaqr_analysis_stage_clusters(const spaqr_analysis* an, int k, int32_t* node, int32_t* level, int64_t* vptr,
+                                  int32_t* verts) {
+  if (!an || !node || !level || !vptr || !verts) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  if (k < 1 || k > an->an->depth) return fail(SPAQR_ERR_INVALID_ARG, "stage out of range");
+  const auto& st = an->an->stages[(size_t)k];
+  std::copy(st.node.begin(), st.node.end(), node);
+  std::copy(st.level.begin(), st.level.end(), level);
+  std::copy(st.vptr.begin(), st.vptr.end(), vptr);
+  std::copy(st.verts.begin(), st.verts.end(), verts);
+  return SPAQR_OK;
+}
+
+int spaqr_factor(const spaqr_csr* A, const spaqr_analysis* an, const spaqr_options* opt, spaqr_handle** out) {
+  if (!A || !an || !out) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  if (int rc = need_device()) return rc;
+  return guarded([&] {
+    auto t0 = std::chrono::steady_clock::now();
+    const spaqr::Analysis& a = *an->an;
+    if (A->n != a.n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A has n != nx*ny*nz columns");
+    if (A->m < A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A must have m >= n");
+    if (!A->rowptr || !A->colidx || !A->vals) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "null CSR array");
+    if (A->rowptr[0] != 0 || A->rowptr[A->m] != A->nnz) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "bad rowptr");
+    for (int64_t r = 0; r < A->m; ++r)
+      if (A->rowptr[r + 1] < A->rowptr[r]) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "rowptr not monotone");
+    for (int64_t e = 0; e < A->nnz; ++e)
+      if (A->colidx[e] < 0 || A->colidx[e] >= A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "column index out of range");
+    auto hd = std::make_unique<spaqr::Handle>();
+    spaqr::Handle& h = *hd;
+    if (opt)
+      h.opt = *opt;
+    else
+      spaqr_default_options(&h.opt);
+    if (h.opt.skip < 0) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "skip must be >= 0");
+    if (!(h.opt.eps >= 0.0)) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "eps must be >= 0");
+    // all library work runs on a non-blocking stream of its own unless the
+    // caller gives one (the legacy default stream cannot be graph-captured)
+    h.user_st = static_cast<cudaStream_t>(h.opt.stream);
+    if (h.user_st) {
+      h.st = h.user_st;
+    } else {
+      SPAQR_CUDA(cudaStreamCreateWithFlags(&h.st, cudaStreamNonBlocking));
+      h.own_stream = true;
+    }
+    h.precision = h.opt.precision;
+    h.m = A->m;
+    h.n = A->n;
+    h.nnz = A->nnz;
+    h.depth = a.depth;
+    h.t_analyze = a.seconds;
+    spaqr::run_factor(h, *A, a);
+    // scaled operator A~ = A D and its transpose on the device (FP64)
+    std::vector<double> v((size_t)A->nnz);
+    for (int64_t e = 0; e < A->nnz; ++e) v[(size_t)e] = A->vals[e] * h.D[(size_t)A->colidx[e]];
+    std::vector<int64_t> trp((size_t)A->n + 1, 0);
+    for (int64_t e = 0; e < A->nnz; ++e) trp[(size_t)A->colidx[e] + 1]++;
+    for (int64_t j = 0; j < A->n; ++j) trp[(size_t)j + 1] += trp[(size_t)j];
+    std::vector<int32_t> tci((size_t)A->nnz);
+    std::vector<double> tv((size_t)A->nnz);
+    {
+      std::vector<int64_t> pos(trp.begin(), trp.end() - 1);
+      for (int64_t r = 0; r < A->m; ++r)
+        for (int64_t e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e) {
+          const int64_t q = pos[(size_t)A->colidx[e]]++;
+          tci[(size_t)q] = (int32_t)r;
+          tv[(size_t)q] = v[(size_t)e];
+        }
+    }
+    SPAQR_CUDA(cudaMalloc(&h.d_rowptr, (size_t)(A->m + 1) * sizeof(int64_t)));
+    SPAQR_CUDA(cudaMalloc(&h.d_colidx, (size_t)A->nnz * sizeof(int32_t)));
+    SPAQR_CUDA(cudaMalloc(&h.d_vals, (size_t)A->nnz * sizeof(double)));
+    SPAQR_CUDA(cudaMalloc(&h.d_trowptr, (size_t)(A->n + 1) * sizeof(int64_t)));
+    SPAQR_CUDA(cudaMalloc(&h.d_tcolidx, (size_t)A->nnz * sizeof(int32_t)));
+    SPAQR_CUDA(cudaMalloc(&h.d_tvals, (size_t)A->nnz * sizeof(double)));
+    SPAQR_CUDA(cudaMalloc(&h.d_D, (size_t)A->n * sizeof(double)));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_rowptr, A->rowptr, (size_t)(A->m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_colidx, A->colidx, (size_t)A->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, h.st));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_vals, v.data(), (size_t)A->nnz * sizeof(double), cudaMemcpyHostToDevice, h.st));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_trowptr, trp.data(), trp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_tcolidx, tci.data(), tci.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h.st));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_tvals, tv.data(), tv.size() * sizeof(double), cudaMemcpyHostToDevice, h.st));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_D, h.D.data(), h.D.size() * sizeof(double), cudaMemcpyHostToDevice, h.st));
+    spaqr::build_apply_plan(h);
+    SPAQR_CUDA(cudaStreamSynchronize(h.st));
+    int64_t nnzW = 0;
+    for (auto& op : h.ops) {
+      const int64_t c = op.c;
+      if (op.kind == 0)
+        nnzW += c * (c + 1) / 2 + c * op.w;
+      else if (op.kind == 1)
+        nnzW += c * (c + 1) / 2;
+      else
+        nnzW += c * op.k;
+    }
+    h.stats.nnz_W = nnzW;
+    h.stats.n_ops = (int64_t)h.ops.size();
+    h.stats.t_analyze = h.t_analyze;
+    h.stats.t_factor = secs_since(t0);
+    auto* out_h = new spaqr_handle();
+    out_h->h = std::move(hd);
+    *out = out_h;
+    return SPAQR_OK;
+  });
+}
+
+void spaqr_destroy(spaqr_handle* h) { delete h; }
+
+int spaqr_solve(spaqr_handle* hh, const double* b, double* x, int on_device, spaqr_solve_info* info) {
+  if (!hh || !b || !x) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    spaqr::Handle& h = *hh->h;
+    const double* bd = b;
+    double* xd = x;
+    double* tmp = nullptr;
+    if (on_device) h.wait_caller();
+    if (!on_device) {
+      SPAQR_CUDA(cudaMalloc(&tmp, (size_t)(h.m + h.n) * sizeof(double)));
+      SPAQR_CUDA(cudaMemcpyAsync(tmp, b, (size_t)h.m * sizeof(double), cudaMemcpyHostToDevice, h.st));
+      bd = tmp;
+      xd = tmp + h.m;
+    }
+    spaqr_solve_info inf{};
+    spaqr::cgls(h, bd, xd, &inf);
+    if (!on_device) {
+      SPAQR_CUDA(cudaMemcpyAsync(x, xd, (size_t)h.n * sizeof(double), cudaMemcpyDeviceToHost, h.st));
+      SPAQR_CUDA(cudaStreamSynchronize(h.st));
+      cudaFree(tmp);
+    }
+    if (info) *info = inf;
+    return inf.converged ? SPAQR_OK : fail(SPAQR_ERR_NOT_CONVERGED, "CGLS reached maxit");
+  });
+}
+
+int spaqr_apply_Winv(spaqr_handle* hh, double* z, int transpose) {
+  if (!hh || !z) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    hh->h->wait_caller();
+    spaqr::apply_Winv(*hh->h, z, transpose ? 1 : 0);
+    SPAQR_CUDA(cudaStreamSynchronize(hh->h->st));
+    return SPAQR_OK;
+  });
+}
+
+int spaqr_apply_A(spaqr_handle* hh, const double* x, double* y, int forward) {
+  if (!hh || !x || !y) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    hh->h->wait_caller();
+    spaqr::apply_A(*hh->h, x, y, forward ? 1 : 0);
+    SPAQR_CUDA(cudaStreamSynchronize(hh->h->st));
+    return SPAQR_OK;
+  });
+}
+
+int spaqr_get_stats(const spaqr_handle* hh, spaqr_stats* st) {
+  if (!hh || !st) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  *st = hh->h->stats;
+  return SPAQR_OK;
+}
+
+int spaqr_num_ops(const spaqr_handle* hh, int64_t* count) {
+  if (!hh || !count) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  *count = (int64_t)hh->h->ops.size();
+  return SPAQR_OK;
+}
+
+int spaqr_op_info(const spaqr_handle* hh, int64_t i, int* kind, int* stage, int* c, int* w) {
+  if (!hh) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  const auto& ops = hh->h->ops;
+  if (i < 0 || i >= (int64_t)ops.size()) return fail(SPAQR_ERR_INVALID_ARG, "op index out of range");
+  const auto& op = ops[(size_t)i];
+  if (kind) *kind = op.kind;
+  if (stage) *stage = op.stage;
+  if (c) *c = op.c;
+  if (w) *w = op.kind == 2 ? op.k : op.w;
+  return SPAQR_OK;
+}
+
+int spaqr_op_copy(const spaqr_handle* hh, int64_t i, int32_t* slots, int32_t* nslots, double* R, double* Rn,
+                  double* taus) {
+  if (!hh) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    const spaqr::Handle& h = *hh->h;
+    if (i < 0 || i >= (int64_t)h.ops.size()) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "op index out of range");
+    const auto& op = h.ops[(size_t)i];
+    const bool f32 = h.precision == SPAQR_PREC_MIXED;
+    const size_t es = f32 ? 4 : 8;
+    auto fetch = [&](const void* src, size_t count, double* dst) {
+      if (!dst || count == 0) return;
+      std::vector<char> buf(count * es);
+      SPAQR_CUDA(cudaMemcpy(buf.data(), src, count * es, cudaMemcpyDeviceToHost));
+      for (size_t t = 0; t < count; ++t)
+        dst[t] = f32 ? (double)reinterpret_cast<float*>(buf.data())[t] : reinterpret_cast<double*>(buf.data())[t];
+    };
+    if (slots) std::copy(op.slots.begin(), op.slots.end(), slots);
+    if (nslots && op.kind == 0) std::copy(op.nslots.begin(), op.nslots.end(), nslots);
+    const size_t c = (size_t)op.c;
+    if (op.kind == 0) {
+      fetch(op.R, c * c, R);
+      if (Rn && op.w) fetch(static_cast<const char*>(op.R) + c * c * es, c * (size_t)op.w, Rn);
+    } else if (op.kind == 1) {
+      fetch(op.R, c * c, R);
+    } else {
+      fetch(op.V, c * (size_t)op.k, R);
+      fetch(op.tau, (size_t)op.k, taus);
+    }
+    return SPAQR_OK;
+  });
+}
+
+int spaqr_dense_front_qr(int count, double* const* A, const int* m, const int* n, const int* c, const int* ld,
+                         void* stream) {
+  if (count < 0 || (count > 0 && (!A || !m || !n || !c || !ld))) return fail(SPAQR_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = need_device()) return rc;
+  return guarded([&] {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int lim = spaqr::max_smem_optin();
+    std::vector<spaqr::FrontDesc<double>> small, big;
+    int need = 0, maxc = 0, maxtiles = 0;
+    for (int i = 0; i < count; ++i) {
+      if (c[i] < 0 || c[i] > m[i] || n[i] < c[i] || ld[i] < std::max(1, m[i]))
+        throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "front " + std::to_string(i) + ": bad shape");
+      spaqr::FrontDesc<double> f{A[i], m[i], n[i], c[i], ld[i]};
+      if (c[i] == 0 || m[i] == 0) continue;
+      const int b = spaqr::front_smem_bytes(m[i], n[i], c[i], 8);
+      if ((int64_t)m[i] * n[i] * 8 + 64 > lim) {
+        big.push_back(f);
+        maxc = std::max(maxc, c[i]);
+      } else {
+        small.push_back(f);
+        need = std::max(need, b);
+      }
+    }
+    spaqr::FrontDesc<double>* d = nullptr;
+    const size_t tot = small.size() + big.size();
+    double* Tbuf = nullptr;
+    SPAQR_CUDA(cudaMalloc(&d, std::max<size_t>(tot, 1) * sizeof(spaqr::FrontDesc<double>)));
+    if (!small.empty()) {
+      SPAQR_CUDA(cudaMemcpyAsync(d, small.data(), small.size() * sizeof(small[0]), cudaMemcpyHostToDevice, st));
+      SPAQR_CUDA(spaqr::launch_front_qr_smem<double>(d, (int)small.size(), need, st));
+    }
+    if (!big.empty()) {
+      auto* db = d + small.size();
+      SPAQR_CUDA(cudaMemcpyAsync(db, big.data(), big.size() * sizeof(big[0]), cudaMemcpyHostToDevice, st));
+      SPAQR_CUDA(cudaMalloc(&Tbuf, big.size() * 32 * 32 * sizeof(double)));
+      for (int j0 = 0; j0 < maxc; j0 += 32) {
+        maxtiles = 0;
+        for (auto& f : big) {
+          const int steps = std::min(f.c, f.m);
+          if (j0 >= steps) continue;
+          const int b = std::min(32, steps - j0);
+          maxtiles = std::max(maxtiles, (f.n - (j0 + b) + 31) / 32);
+        }
+        SPAQR_CUDA(spaqr::launch_front_panel<double>(db, (int)big.size(), j0, 32, Tbuf, st));
+        SPAQR_CUDA(spaqr::launch_front_trailing<double>(db, (int)big.size(), j0, 32, Tbuf, maxtiles, st));
+      }
+      SPAQR_CUDA(spaqr::launch_front_finish<double>(db, (int)big.size(), maxc, st));
+    }
+    SPAQR_CUDA(cudaStreamSynchronize(st));
+    cudaFree(d);
+    cudaFree(Tbuf);
+    return SPAQR_OK;
+  });
+}
+
+int spaqr_dense_qrcp(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
+                     double* const* V, double* const* taus, int* rank, void* stream) {
+  if (count < 0 || (count > 0 && (!A || !m || !n || !ld || !rank))) return fail(SPAQR_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = need_device()) return rc;
+  return guarded([&] {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int lim = spaqr::max_smem_optin();
+    std::vector<spaqr::QrcpDesc<double>> small, large;
+    std::vector<int> si, li;
+    std::vector<double*> work;
+    int need_s = 0, need_l = 0;
+    int* d_rank = nullptr;
+    SPAQR_CUDA(cudaMalloc(&d_rank, std::max(count, 1) * sizeof(int)));
+    for (int i = 0; i < count; ++i) {
+      if (m[i] < 0 || n[i] < 0 || ld[i] < std::max(1, m[i])) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "bad shape");
+      spaqr::QrcpDesc<double> q{A[i], nullptr, A[i], V ? V[i] : nullptr, taus ? taus[i] : nullptr, d_rank + i,
+                                m[i], n[i], ld[i], ld[i]};
+      const int whole = spaqr::qrcp_smem_bytes(m[i], n[i], 8, true);
+      if (whole <= lim) {
+        small.push_back(q);
+        need_s = std::max(need_s, whole);
+      } else {
+        const int part = spaqr::qrcp_smem_bytes(m[i], n[i], 8, false);
+        if (part > lim) throw spaqr::Error(SPAQR_ERR_CAPACITY, "too many columns");
+        double* w = nullptr;
+        SPAQR_CUDA(cudaMalloc(&w, (size_t)m[i] * n[i] * sizeof(double)));
+        work.push_back(w);
+        q.work = w;
+        large.push_back(q);
+        need_l = std::max(need_l, part);
+      }
+    }
+    spaqr::QrcpDesc<double>* d = nullptr;
+    SPAQR_CUDA(cudaMalloc(&d, std::max<size_t>(small.size() + large.size(), 1) * sizeof(spaqr::QrcpDesc<double>)));
+    if (!small.empty()) {
+      SPAQR_CUDA(cudaMemcpyAsync(d, small.data(), small.size() * sizeof(small[0]), cudaMemcpyHostToDevice, st));
+      SPAQR_CUDA(spaqr::launch_qrcp<double>(d, (int)small.size(), eps, need_s, st));
+    }
+    if (!large.empty()) {
+      auto* dl = d + small.size();
+      SPAQR_CUDA(cudaMemcpyAsync(dl, large.data(), large.size() * sizeof(large[0]), cudaMemcpyHostToDevice, st));
+      SPAQR_CUDA(spaqr::launch_qrcp<double>(dl, (int)large.size(), eps, -need_l, st));
+    }
+    SPAQR_CUDA(cudaMemcpyAsync(rank, d_rank, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SPAQR_CUDA(cudaStreamSynchronize(st));
+    cudaFree(d);
+    cudaFree(d_rank);
+    for (double* w : work) cudaFree(w);
+    return SPAQR_OK;
+  });
+}
+
+}  // extern "C"

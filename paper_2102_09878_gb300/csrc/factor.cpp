@@ -1,0 +1,1446 @@
+// Host driver of the spaQR factorization (Algorithm 1, Section 2.7) on one GPU.
+//
+// The evolving matrix is a set of row groups: rows that share an owner cluster
+// and a column support; a group keeps one dense column-major block over its
+// support clusters (in ascending cluster id).  The host plans every phase from
+// the symbolic structure, the device does every floating-point step:
+//
+//   stage k = L..1:
+//     eliminate   rounds of independent level-k separators; per round one
+//                 batched front QR (Section 2.3), the max-norm destinations of
+//                 the extra rows (Section 2.2 rule), one device->host wait
+//     scale       batched QR of every remaining A_pp, X <- X R_pp^{-1} on every
+//                 block column (Section 2.4)
+//     step 1      batched column-pivoted QR of every p2 block (Section 2.5.1)
+//     step 2      colour by colour: M_p = [A_np^T A_p1n], column-pivoted QR,
+//                 reflectors applied to block column p and block row p1
+//                 (Section 2.5.2); one wait for the ranks
+//     merge       relayout of the groups onto the merged clusters (Section 2.6)
+//
+// Readings of the paper (identical to the ones the CPU oracle implements):
+//   column scaling to unit norms, max-norm row rule on A D with ties to the
+//   deeper then lower-id cluster; front rows = own groups (by creation
+//   number) then the other owners' groups touching s (by owner, number);
+//   rows at positions >= r_s return to their owners, positions c_s..r_s-1 are
+//   reassigned; same-level separators run in rounds of a greedy maximal set of
+//   separators with disjoint fronts; step 2 by a greedy colouring of
+//   "q in support(p1 of p)"; scaling and sparsification at stages k <= L - skip.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <numeric>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace spaqr {
+
+// ------------------------------------------------------------- DevicePool
+DevicePool::~DevicePool() {
+  for (auto& c : chunks_) cudaFree(c.base);
+}
+
+int DevicePool::find(void* p) const {
+  auto it = std::lower_bound(live_.begin(), live_.end(), std::make_pair(p, -1),
+                             [](const std::pair<void*, int>& a, const std::pair<void*, int>& b) {
+                               return a.first < b.first;
+                             });
+  if (it == live_.end() || it->first != p) return -1;
+  return (int)(it - live_.begin());
+}
+
+void* DevicePool::alloc(size_t bytes) {
+  if (bytes == 0) bytes = 1;
+  int cls = 0;
+  while ((size_t(256) << cls) < bytes) ++cls;
+  const size_t sz = size_t(256) << cls;
+  if ((int)free_.size() <= cls) free_.resize((size_t)cls + 1);
+  void* p = nullptr;
+  if (!free_[(size_t)cls].empty()) {
+    p = free_[(size_t)cls].back();
+    free_[(size_t)cls].pop_back();
+  } else {
+    Chunk* ch = chunks_.empty() ? nullptr : &chunks_.back();
+    if (!ch || ch->used + sz > ch->size) {
+      // keep the tail of the old chunk usable by smaller classes
+      if (ch) {
+        while (ch->size - ch->used >= 256) {
+          int c2 = 0;
+          while ((size_t(256) << (c2 + 1)) <= ch->size - ch->used) ++c2;
+          const size_t s2 = size_t(256) << c2;
+          if ((int)free_.size() <= c2) free_.resize((size_t)c2 + 1);
+          void* q = ch->base + ch->used;
+          free_[(size_t)c2].push_back(q);
+          ch->used += s2;
+        }
+      }
+      const size_t csz = std::max(chunk_, sz);
+      char* base = nullptr;
+      SPAQR_CUDA(cudaMalloc(&base, csz));
+      chunks_.push_back(Chunk{base, csz, 0});
+      reserved_ += csz;
+      ch = &chunks_.back();
+    }
+    p = ch->base + ch->used;
+    ch->used += sz;
+  }
+  auto it = std::lower_bound(live_.begin(), live_.end(), std::make_pair(p, -1),
+                             [](const std::pair<void*, int>& a, const std::pair<void*, int>& b) {
+                               return a.first < b.first;
+                             });
+  live_.insert(it, std::make_pair(p, cls));
+  in_use_ += sz;
+  peak_ = std::max(peak_, in_use_);
+  return p;
+}
+
+bool DevicePool::contains(const void* p, size_t bytes) const {
+  if (live_.empty()) return false;
+  auto it = std::upper_bound(live_.begin(), live_.end(), std::make_pair(const_cast<void*>(p), 1 << 30),
+                             [](const std::pair<void*, int>& a, const std::pair<void*, int>& b) {
+                               return a.first < b.first;
+                             });
+  if (it == live_.begin()) return false;
+  --it;
+  const char* base = static_cast<const char*>(it->first);
+  const char* q = static_cast<const char*>(p);
+  const size_t sz = size_t(256) << it->second;
+  return q >= base && q + bytes <= base + sz;
+}
+
+void DevicePool::release(void* p) {
+  if (!p) return;
+  const int i = find(p);
+  if (i < 0) return;
+  const int cls = live_[(size_t)i].second;
+  live_.erase(live_.begin() + i);
+  free_[(size_t)cls].push_back(p);
+  in_use_ -= size_t(256) << cls;
+}
+
+// --------------------------------------------------------------- Uploader
+void Uploader::free_block(Block& b) {
+  if (b.host) cudaFreeHost(b.host);
+  if (b.dev) cudaFree(b.dev);
+  b = Block();
+}
+
+Uploader::~Uploader() {
+  for (auto& b : retired_) free_block(b);
+  free_block(cur_);
+}
+
+void Uploader::init(cudaStream_t st, size_t bytes) {
+  st_ = st;
+  if (cur_.cap < bytes) {
+    free_block(cur_);
+    cur_.cap = bytes;
+    SPAQR_CUDA(cudaMallocHost(&cur_.host, cur_.cap));
+    SPAQR_CUDA(cudaMalloc(&cur_.dev, cur_.cap));
+  }
+  off_ = 0;
+}
+
+void Uploader::reset() {
+  // called after a stream synchronisation: nothing handed out is in use
+  for (auto& b : retired_) free_block(b);
+  retired_.clear();
+  off_ = 0;
+}
+
+void* Uploader::take(size_t bytes, const void* src) {
+  const size_t need = (bytes + 255) & ~size_t(255);
+  if (off_ + need > cur_.cap) {
+    retired_.push_back(cur_);
+    cur_ = Block();
+    cur_.cap = std::max(need, 2 * retired_.back().cap);
+    SPAQR_CUDA(cudaMallocHost(&cur_.host, cur_.cap));
+    SPAQR_CUDA(cudaMalloc(&cur_.dev, cur_.cap));
+    off_ = 0;
+  }
+  char* d = cur_.dev + off_;
+  if (src && bytes) {
+    char* h = cur_.host + off_;
+    std::memcpy(h, src, bytes);
+    SPAQR_CUDA(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st_));
+  }
+  off_ += need;
+  return d;
+}
+
+void* Uploader::put_bytes(const void* src, size_t bytes) { return take(bytes, src); }
+void* Uploader::scratch(size_t bytes) { return take(bytes, nullptr); }
+
+// ------------------------------------------------------------- EventTimer
+EventTimer::~EventTimer() {
+  for (auto e : free_) cudaEventDestroy(e);
+  for (auto& p : pending_) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+}
+
+cudaEvent_t EventTimer::get() {
+  if (!free_.empty()) {
+    cudaEvent_t e = free_.back();
+    free_.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  SPAQR_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+void EventTimer::begin(cudaStream_t st, int family) {
+  open_.a = get();
+  open_.fam = family;
+  SPAQR_CUDA(cudaEventRecord(open_.a, st));
+}
+
+void EventTimer::end(cudaStream_t st) {
+  open_.b = get();
+  SPAQR_CUDA(cudaEventRecord(open_.b, st));
+  pending_.push_back(open_);
+  open_ = Pair{nullptr, nullptr, -1};
+}
+
+void EventTimer::drain(double* totals, int64_t* counts) {
+  for (auto& p : pending_) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      totals[p.fam] += ms * 1e-3;
+      counts[p.fam] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    free_.push_back(p.a);
+    free_.push_back(p.b);
+  }
+  pending_.clear();
+}
+
+namespace {
+
+double now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <typename T>
+class Factorizer {
+ public:
+  Factorizer(Handle& h, const Analysis& an) : h_(h), an_(an), st_(h.st) {}
+  void run(const spaqr_csr& A);
+
+ private:
+  struct Group {
+    int owner = -1;
+    int rows = 0, ld = 0, width = 0;
+    std::vector<int> sup, off;
+    T* ptr = nullptr;
+    int buf = -1;
+    bool alive = false;
+  };
+  struct Buf {
+    void* p;
+    int refs;
+  };
+
+  Handle& h_;
+  const Analysis& an_;
+  cudaStream_t st_;
+  DevicePool pool_;
+  Uploader up_;
+  EventTimer tm_;
+  int L_ = 0, k_ = 0;
+  const StageClusters* sc_ = nullptr;
+  std::vector<int> ccols_;
+  std::vector<std::vector<int32_t>> slots_;
+  std::vector<char> calive_;
+  std::vector<Group> G_;
+  std::vector<Buf> bufs_;
+  std::vector<int> p1_of_, p2_of_;
+  std::vector<int> own_head_;  // scratch
+  int smem_max_ = 0;
+  int64_t launches_ = 0;
+
+  // ----------------------------------------------------------- helpers
+  int level(int c) const { return sc_->level[(size_t)c]; }
+  void check(cudaError_t e, const char* what) {
+    ++launches_;
+    if (e != cudaSuccess) throw Error(SPAQR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+  void sync() {
+    SPAQR_CUDA(cudaStreamSynchronize(st_));
+    ++up_.syncs;
+    up_.reset();
+    tm_.drain(h_.stats.t_kernel, h_.stats.n_kernel);
+  }
+  int new_group(int owner, int rows, std::vector<int> sup) {
+    Group g;
+    g.owner = owner;
+    g.rows = rows;
+    g.ld = std::max(rows, 1);
+    g.sup = std::move(sup);
+    g.off.resize(g.sup.size());
+    int w = 0;
+    for (size_t t = 0; t < g.sup.size(); ++t) {
+      g.off[t] = w;
+      w += ccols_[(size_t)g.sup[t]];
+    }
+    g.width = w;
+    g.alive = true;
+    G_.push_back(std::move(g));
+    return (int)G_.size() - 1;
+  }
+  // one buffer for a list of new groups (zero-initialised when zero = true)
+  void assign_buffer(const std::vector<int>& ids, bool zero) {
+    size_t total = 0;
+    for (int id : ids) total += (size_t)G_[(size_t)id].ld * G_[(size_t)id].width;
+    if (total == 0) {
+      for (int id : ids) G_[(size_t)id].ptr = nullptr;
+      return;
+    }
+    T* base = static_cast<T*>(pool_.alloc(total * sizeof(T)));
+    if (zero) SPAQR_CUDA(cudaMemsetAsync(base, 0, total * sizeof(T), st_));
+    bufs_.push_back(Buf{base, 0});
+    const int b = (int)bufs_.size() - 1;
+    size_t o = 0;
+    for (int id : ids) {
+      Group& g = G_[(size_t)id];
+      const size_t sz = (size_t)g.ld * g.width;
+      g.ptr = sz ? base + o : nullptr;
+      g.buf = sz ? b : -1;
+      if (sz) bufs_[(size_t)b].refs++;
+      o += sz;
+    }
+    if (bufs_[(size_t)b].refs == 0) {
+      pool_.release(base);
+      bufs_[(size_t)b].p = nullptr;
+    }
+  }
+  void drop_data(Group& g) {
+    if (g.buf >= 0) {
+      Buf& b = bufs_[(size_t)g.buf];
+      if (--b.refs == 0) {
+        pool_.release(b.p);
+        b.p = nullptr;
+      }
+    }
+    g.buf = -1;
+    g.ptr = nullptr;
+  }
+  void kill(int id) {
+    Group& g = G_[(size_t)id];
+    drop_data(g);
+    g.alive = false;
+    std::vector<int>().swap(g.sup);
+    std::vector<int>().swap(g.off);
+  }
+  int col_off(const Group& g, int c) const {
+    auto it = std::lower_bound(g.sup.begin(), g.sup.end(), c);
+    if (it == g.sup.end() || *it != c) return -1;
+    return g.off[(size_t)(it - g.sup.begin())];
+  }
+  T* wstore(size_t elems) { return static_cast<T*>(h_.wpool.alloc(std::max<size_t>(elems, 1) * sizeof(T))); }
+
+  // ---- optional host-side bounds checks of every descriptor (SPAQR_CHECK=1)
+  bool checking_ = false;
+  void in_bounds(const void* p, int64_t rows, int64_t cols, int64_t ld, int64_t esz, const char* what) const {
+    if (rows <= 0 || cols <= 0) return;
+    if (!p) throw Error(SPAQR_ERR_CAPACITY, std::string("check: null pointer in ") + what);
+    if (ld < rows) throw Error(SPAQR_ERR_CAPACITY, std::string("check: ld < rows in ") + what);
+    const size_t bytes = (size_t)((rows - 1) + (cols - 1) * ld + 1) * (size_t)esz;
+    if (!pool_.contains(p, bytes) && !h_.wpool.contains(p, bytes))
+      throw Error(SPAQR_ERR_CAPACITY, std::string("check: out-of-bounds ") + what + " rows " + std::to_string(rows) +
+                                          " cols " + std::to_string(cols) + " ld " + std::to_string(ld) + " at stage " +
+                                          std::to_string(k_));
+  }
+  void check_copies(const std::vector<CopyDesc<T>>& v, const std::vector<std::vector<int>>* rowsets = nullptr) const {
+    (void)rowsets;
+    for (auto& d : v) {
+      if (d.src) in_bounds(d.src, d.rowidx ? 1 : d.rows, d.cols, d.rowidx ? std::max(d.sld, 1) : d.sld, sizeof(T), "copy src");
+      if (d.transpose)
+        in_bounds(d.dst, d.cols, d.rows, d.dld, sizeof(T), "copy dst (transposed)");
+      else
+        in_bounds(d.dst, d.rows, d.cols, d.dld, sizeof(T), "copy dst");
+    }
+  }
+
+  // batched front QR of fronts (ptr,m,n,c,ld) in device memory
+  void front_qr(std::vector<FrontDesc<T>>& fr);
+  // batched QRCP
+  void qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_bufs);
+  void copies(const std::vector<CopyDesc<T>>& cps);
+
+  void init_stage(const spaqr_csr& A);
+  void eliminate();
+  void eliminate_round(const std::vector<std::pair<int, std::vector<int>>>& batch, int round);
+  void scale();
+  void step1();
+  void step2();
+  void merge();
+  bool sparsify_here() const {
+    return h_.opt.mode == SPAQR_MODE_SPAQR && k_ <= L_ - h_.opt.skip && k_ >= 2;
+  }
+  void index_groups(std::vector<std::vector<int>>& own, std::vector<std::vector<int>>& touch);
+};
+
+template <typename T>
+void Factorizer<T>::copies(const std::vector<CopyDesc<T>>& cps) {
+  if (cps.empty()) return;
+  std::vector<int> start(cps.size() + 1, 0);
+  int64_t tot = 0;
+  for (size_t i = 0; i < cps.size(); ++i) {
+    start[i] = (int)tot;
+    tot += copy_chunks((int64_t)cps[i].rows * cps[i].cols);
+    if (tot > INT32_MAX / 2) throw Error(SPAQR_ERR_CAPACITY, "block copies larger than one launch covers");
+  }
+  start[cps.size()] = (int)tot;
+  if (checking_) check_copies(cps);
+  auto* d = up_.put(cps);
+  int* ds = up_.put(start);
+  tm_.begin(st_, 0);
+  check(launch_copy<T>(d, ds, (int)cps.size(), (int)tot, st_), "copy");
+  tm_.end(st_);
+}
+
+template <typename T>
+void Factorizer<T>::front_qr(std::vector<FrontDesc<T>>& fr) {
+  if (fr.empty()) return;
+  struct Scope {
+    EventTimer& t;
+    cudaStream_t s;
+    Scope(EventTimer& t_, cudaStream_t s_) : t(t_), s(s_) {}
+    ~Scope() { t.end(s); }
+  };
+  // bucket by shared-memory need
+  const int lim = smem_max_;
+  const int classes[4] = {24 << 10, 48 << 10, 100 << 10, lim};
+  std::vector<FrontDesc<T>> b[4];
+  std::vector<FrontDesc<T>> big;
+  for (auto& f : fr) {
+    if (f.c == 0 || f.m == 0 || f.n == 0) continue;
+    if (checking_) in_bounds(f.ptr, f.m, f.n, f.ld, sizeof(T), "front");
+    const int need = front_smem_bytes(f.m, f.n, f.c, (int)sizeof(T));
+    if ((int64_t)f.m * f.n * (int64_t)sizeof(T) + 64 > lim) {
+      big.push_back(f);
+      continue;
+    }
+    for (int q = 0; q < 4; ++q)
+      if (need <= classes[q]) {
+        b[q].push_back(f);
+        break;
+      }
+  }
+  std::vector<FrontDesc<T>*> dq(4, nullptr);
+  for (int q = 0; q < 4; ++q)
+    if (!b[q].empty()) dq[(size_t)q] = up_.put(b[q]);
+  FrontDesc<T>* dbig = big.empty() ? nullptr : up_.put(big);
+  T* Tbuf = big.empty() ? nullptr : static_cast<T*>(up_.scratch(big.size() * 32 * 32 * sizeof(T)));
+  tm_.begin(st_, 1);
+  Scope scope(tm_, st_);
+  for (int q = 0; q < 4; ++q) {
+    if (b[q].empty()) continue;
+    int need = 0;
+    for (auto& f : b[q]) need = std::max(need, front_smem_bytes(f.m, f.n, f.c, (int)sizeof(T)));
+    auto* d = dq[(size_t)q];
+    check(launch_front_qr_smem<T>(d, (int)b[q].size(), need, st_), "front_qr_smem");
+  }
+  if (!big.empty()) {
+    const int nb = 32;
+    int maxc = 0, maxtiles = 0;
+    for (auto& f : big) {
+      maxc = std::max(maxc, std::min(f.c, f.m));
+    }
+    auto* d = dbig;
+    for (int j0 = 0; j0 < maxc; j0 += nb) {
+      maxtiles = 0;
+      for (auto& f : big) {
+        const int steps = std::min(f.c, f.m);
+        if (j0 >= steps) continue;
+        const int b = std::min(nb, steps - j0);
+        maxtiles = std::max(maxtiles, (f.n - (j0 + b) + 31) / 32);
+      }
+      check(launch_front_panel<T>(d, (int)big.size(), j0, nb, Tbuf, st_), "front_panel");
+      check(launch_front_trailing<T>(d, (int)big.size(), j0, nb, Tbuf, maxtiles, st_), "front_trailing");
+    }
+    check(launch_front_finish<T>(d, (int)big.size(), maxc, st_), "front_finish");
+  }
+}
+
+template <typename T>
+void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_bufs) {
+  if (qs.empty()) return;
+  std::vector<QrcpDesc<T>> small, large;
+  int need_s = 0, need_l = 0;
+  for (auto& q : qs) {
+    if (checking_) {
+      in_bounds(q.src, q.m, q.n, q.ld, sizeof(T), "qrcp src");
+      if (q.out) in_bounds(q.out, q.m, q.n, q.ldo, sizeof(T), "qrcp out");
+      if (q.V) in_bounds(q.V, q.m, std::min(q.m, q.n), q.m, sizeof(T), "qrcp V");
+      if (q.tau) in_bounds(q.tau, 1, std::min(q.m, q.n), 1, sizeof(T), "qrcp tau");
+    }
+    const int whole = qrcp_smem_bytes(q.m, q.n, (int)sizeof(T), true);
+    if (whole <= smem_max_) {
+      small.push_back(q);
+      need_s = std::max(need_s, whole);
+    } else {
+      const int part = qrcp_smem_bytes(q.m, q.n, (int)sizeof(T), false);
+      if (part > smem_max_)
+        throw Error(SPAQR_ERR_CAPACITY, "column-pivoted QR with too many columns for shared memory");
+      T* w = static_cast<T*>(pool_.alloc((size_t)q.m * q.n * sizeof(T)));
+      work_bufs.push_back(w);
+      q.work = w;
+      large.push_back(q);
+      need_l = std::max(need_l, part);
+    }
+  }
+  const double eps = h_.opt.mode == SPAQR_MODE_SPAQR ? h_.opt.eps : 0.0;
+  auto* ds = small.empty() ? nullptr : up_.put(small);
+  auto* dl = large.empty() ? nullptr : up_.put(large);
+  tm_.begin(st_, 2);
+  if (!small.empty()) check(launch_qrcp<T>(ds, (int)small.size(), eps, need_s, st_), "qrcp_smem");
+  if (!large.empty()) check(launch_qrcp<T>(dl, (int)large.size(), eps, -need_l, st_), "qrcp_global");
+  tm_.end(st_);
+}
+
+template <typename T>
+void Factorizer<T>::index_groups(std::vector<std::vector<int>>& own, std::vector<std::vector<int>>& touch) {
+  const size_t nc = ccols_.size();
+  own.assign(nc, {});
+  touch.assign(nc, {});
+  for (size_t id = 0; id < G_.size(); ++id) {
+    const Group& g = G_[id];
+    if (!g.alive) continue;
+    own[(size_t)g.owner].push_back((int)id);
+    for (int c : g.sup)
+      if (c != g.owner) touch[(size_t)c].push_back((int)id);
+  }
+}
+
+// ------------------------------------------------------------ init (a0)
+template <typename T>
+void Factorizer<T>::init_stage(const spaqr_csr& A) {
+  const StageClusters& st = an_.stages[(size_t)L_];
+  sc_ = &st;
+  const size_t nc = st.node.size();
+  ccols_.assign(nc, 0);
+  slots_.assign(nc, {});
+  calive_.assign(nc, 1);
+  std::vector<int32_t> cl_of((size_t)h_.n, -1), pos_of((size_t)h_.n, 0);
+  for (size_t c = 0; c < nc; ++c) {
+    const int64_t b = st.vptr[c], e = st.vptr[c + 1];
+    ccols_[c] = (int)(e - b);
+    slots_[c].assign(st.verts.begin() + b, st.verts.begin() + e);
+    for (int64_t t = b; t < e; ++t) {
+      cl_of[(size_t)st.verts[(size_t)t]] = (int)c;
+      pos_of[(size_t)st.verts[(size_t)t]] = (int)(t - b);
+    }
+  }
+  // column scaling (R1)
+  std::vector<double> nrm((size_t)h_.n, 0.0);
+  for (int64_t e = 0; e < A.nnz; ++e) nrm[(size_t)A.colidx[e]] += A.vals[e] * A.vals[e];
+  h_.D.resize((size_t)h_.n);
+  for (int64_t j = 0; j < h_.n; ++j) {
+    if (!(nrm[(size_t)j] > 0.0)) throw Error(SPAQR_ERR_RANK_DEFICIENT, "zero column " + std::to_string(j));
+    h_.D[(size_t)j] = 1.0 / std::sqrt(nrm[(size_t)j]);
+  }
+  // row owners by the max-norm rule on A D (R2), grouped by (owner, support)
+  const int64_t M = A.m;
+  std::vector<int32_t> owner((size_t)M);
+  std::vector<int64_t> sptr((size_t)M + 1, 0);
+  std::vector<int32_t> sups;
+  sups.reserve((size_t)A.nnz);
+  std::vector<int> tmp;
+  std::vector<double> sc;
+  for (int64_t r = 0; r < M; ++r) {
+    tmp.clear();
+    for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) tmp.push_back(cl_of[(size_t)A.colidx[e]]);
+    std::sort(tmp.begin(), tmp.end());
+    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+    if (tmp.empty()) throw Error(SPAQR_ERR_INVALID_ARG, "empty row " + std::to_string(r));
+    sc.assign(tmp.size(), 0.0);
+    for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
+      const int32_t j = A.colidx[e];
+      const double v = A.vals[e] * h_.D[(size_t)j];
+      const size_t t = (size_t)(std::lower_bound(tmp.begin(), tmp.end(), cl_of[(size_t)j]) - tmp.begin());
+      sc[t] += v * v;
+    }
+    int best = 0;
+    for (size_t t = 1; t < tmp.size(); ++t) {
+      const int a = tmp[t], b = tmp[(size_t)best];
+      if (sc[t] > sc[(size_t)best] ||
+          (sc[t] == sc[(size_t)best] && (level(a) > level(b) || (level(a) == level(b) && a < b))))
+        best = (int)t;
+    }
+    owner[(size_t)r] = tmp[(size_t)best];
+    sups.insert(sups.end(), tmp.begin(), tmp.end());
+    sptr[(size_t)r + 1] = (int64_t)sups.size();
+  }
+  // counting sort by owner, then (support, row) inside an owner
+  std::vector<int64_t> cnt(nc + 1, 0);
+  for (int64_t r = 0; r < M; ++r) cnt[(size_t)owner[(size_t)r] + 1]++;
+  for (size_t c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
+  std::vector<int64_t> order((size_t)M);
+  {
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+    for (int64_t r = 0; r < M; ++r) order[(size_t)pos[(size_t)owner[(size_t)r]]++] = r;
+  }
+  auto sup_less = [&](int64_t a, int64_t b) {
+    const int32_t *pa = &sups[(size_t)sptr[(size_t)a]], *pb = &sups[(size_t)sptr[(size_t)b]];
+    const int64_t la = sptr[(size_t)a + 1] - sptr[(size_t)a], lb = sptr[(size_t)b + 1] - sptr[(size_t)b];
+    if (std::lexicographical_compare(pa, pa + la, pb, pb + lb)) return true;
+    if (std::lexicographical_compare(pb, pb + lb, pa, pa + la)) return false;
+    return a < b;
+  };
+  for (size_t c = 0; c < nc; ++c) std::sort(order.begin() + cnt[c], order.begin() + cnt[c + 1], sup_less);
+  // groups
+  std::vector<int> ids;
+  std::vector<int32_t> grp_of_row((size_t)M), rowpos((size_t)M);
+  int64_t i = 0;
+  while (i < M) {
+    int64_t j = i + 1;
+    const int64_t r0 = order[(size_t)i];
+    auto same = [&](int64_t a, int64_t b) {
+      if (owner[(size_t)a] != owner[(size_t)b]) return false;
+      const int64_t la = sptr[(size_t)a + 1] - sptr[(size_t)a], lb = sptr[(size_t)b + 1] - sptr[(size_t)b];
+      return la == lb && std::equal(&sups[(size_t)sptr[(size_t)a]], &sups[(size_t)sptr[(size_t)a]] + la,
+                                    &sups[(size_t)sptr[(size_t)b]]);
+    };
+    while (j < M && same(order[(size_t)j], r0)) ++j;
+    std::vector<int> sup(&sups[(size_t)sptr[(size_t)r0]], &sups[(size_t)sptr[(size_t)r0 + 1]]);
+    const int id = new_group(owner[(size_t)r0], (int)(j - i), sup);
+    ids.push_back(id);
+    for (int64_t t = i; t < j; ++t) {
+      grp_of_row[(size_t)order[(size_t)t]] = id;
+      rowpos[(size_t)order[(size_t)t]] = (int32_t)(t - i);
+    }
+    i = j;
+  }
+  assign_buffer(ids, true);
+  // scatter the scaled values into the group blocks
+  T* base = G_[(size_t)ids.front()].ptr;  // all initial groups share one buffer, in id order
+  std::vector<int64_t> dest((size_t)A.nnz);
+  std::vector<T> vals((size_t)A.nnz);
+  for (int64_t r = 0; r < M; ++r) {
+    const Group& g = G_[(size_t)grp_of_row[(size_t)r]];
+    const int64_t gbase = g.ptr - base;
+    for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
+      const int32_t jcol = A.colidx[e];
+      const int co = col_off(g, cl_of[(size_t)jcol]) + pos_of[(size_t)jcol];
+      dest[(size_t)e] = gbase + rowpos[(size_t)r] + (int64_t)co * g.ld;
+      vals[(size_t)e] = (T)(A.vals[e] * h_.D[(size_t)jcol]);
+    }
+  }
+  int64_t* d_dest = static_cast<int64_t*>(pool_.alloc(dest.size() * sizeof(int64_t)));
+  T* d_vals = static_cast<T*>(pool_.alloc(vals.size() * sizeof(T)));
+  SPAQR_CUDA(cudaMemcpyAsync(d_dest, dest.data(), dest.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st_));
+  SPAQR_CUDA(cudaMemcpyAsync(d_vals, vals.data(), vals.size() * sizeof(T), cudaMemcpyHostToDevice, st_));
+  check(launch_scatter_values<T>(base, d_dest, d_vals, A.nnz, st_), "scatter_values");
+  sync();
+  pool_.release(d_dest);
+  pool_.release(d_vals);
+}
+
+// ------------------------------------------------------------ eliminate
+template <typename T>
+void Factorizer<T>::eliminate() {
+  std::vector<int> todo;
+  for (size_t c = 0; c < ccols_.size(); ++c)
+    if (calive_[c] && level((int)c) == k_) todo.push_back((int)c);
+  std::vector<std::vector<int>> own, touch;
+  std::vector<int64_t> stamp(G_.size() + 1, -1);
+  int round = 0;
+  while (!todo.empty()) {
+    index_groups(own, touch);
+    if (stamp.size() < G_.size()) stamp.resize(G_.size(), -1);
+    std::vector<std::pair<int, std::vector<int>>> batch;
+    std::vector<int> rest;
+    for (int s : todo) {
+      std::vector<int> fg = own[(size_t)s];
+      std::vector<int> oth = touch[(size_t)s];
+      std::sort(oth.begin(), oth.end(), [&](int a, int b) {
+        const int oa = G_[(size_t)a].owner, ob = G_[(size_t)b].owner;
+        return oa != ob ? oa < ob : a < b;
+      });
+      fg.insert(fg.end(), oth.begin(), oth.end());
+      bool clash = false;
+      for (int g : fg)
+        if (stamp[(size_t)g] == round) {
+          clash = true;
+          break;
+        }
+      if (clash) {
+        rest.push_back(s);
+        continue;
+      }
+      for (int g : fg) stamp[(size_t)g] = round;
+      batch.emplace_back(s, std::move(fg));
+    }
+    eliminate_round(batch, round);
+    todo.swap(rest);
+    ++round;
+  }
+}
+
+template <typename T>
+void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector<int>>>& batch, int round) {
+  struct FrontInfo {
+    int s, m, n, c, rs;
+    std::vector<int> cols, coff;  // clusters (s first), column offsets (size cols+1)
+    size_t foff;                  // offset in the workspace (elements)
+    int nextra;
+    size_t dest_off;
+  };
+  std::vector<FrontInfo> fi(batch.size());
+  size_t ws = 0, ndest = 0;
+  std::vector<CopyDesc<T>> gat;
+  for (size_t b = 0; b < batch.size(); ++b) {
+    const int s = batch[b].first;
+    const auto& fg = batch[b].second;
+    FrontInfo& f = fi[b];
+    f.s = s;
+    f.c = ccols_[(size_t)s];
+    f.rs = 0;
+    f.m = 0;
+    std::vector<int> u;
+    for (int g : fg) {
+      const Group& gg = G_[(size_t)g];
+      if (gg.owner == s) f.rs += gg.rows;
+      f.m += gg.rows;
+      u.insert(u.end(), gg.sup.begin(), gg.sup.end());
+    }
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
+    f.cols.push_back(s);
+    for (int c : u)
+      if (c != s) f.cols.push_back(c);
+    f.coff.assign(f.cols.size() + 1, 0);
+    for (size_t t = 0; t < f.cols.size(); ++t) f.coff[t + 1] = f.coff[t] + ccols_[(size_t)f.cols[t]];
+    f.n = f.coff.back();
+    if (f.rs < f.c)
+      throw Error(SPAQR_ERR_RANK_DEFICIENT,
+                  "cluster " + std::to_string(s) + " at stage " + std::to_string(k_) + ": " + std::to_string(f.rs) +
+                      " rows < " + std::to_string(f.c) + " columns");
+    f.foff = ws;
+    ws += (size_t)f.m * f.n;
+    f.nextra = (f.cols.size() > 1 && f.rs > f.c) ? f.rs - f.c : 0;
+    f.dest_off = ndest;
+    ndest += (size_t)f.nextra;
+  }
+  T* W = static_cast<T*>(pool_.alloc(std::max<size_t>(ws, 1) * sizeof(T)));
+  SPAQR_CUDA(cudaMemsetAsync(W, 0, std::max<size_t>(ws, 1) * sizeof(T), st_));
+  std::vector<FrontDesc<T>> fr;
+  for (size_t b = 0; b < batch.size(); ++b) {
+    FrontInfo& f = fi[b];
+    T* F = W + f.foff;
+    int row = 0;
+    for (int g : batch[b].second) {
+      const Group& gg = G_[(size_t)g];
+      for (size_t t = 0; t < gg.sup.size(); ++t) {
+        const int c = gg.sup[t];
+        const size_t ci = (size_t)(std::find(f.cols.begin(), f.cols.end(), c) - f.cols.begin());
+        if (gg.rows == 0 || ccols_[(size_t)c] == 0) continue;
+        gat.push_back(CopyDesc<T>{gg.ptr + (size_t)gg.off[t] * gg.ld, F + row + (size_t)f.coff[ci] * f.m, nullptr,
+                                  gg.ld, f.m, gg.rows, ccols_[(size_t)c], 0, 0});
+      }
+      row += gg.rows;
+    }
+    fr.push_back(FrontDesc<T>{F, f.m, f.n, f.c, f.m});
+  }
+  copies(gat);
+  front_qr(fr);
+  // extra-row destinations (max-norm rule over the remaining front clusters)
+  std::vector<ArgmaxDesc<T>> am;
+  std::vector<int> pack;  // per front: coff (ncl + 1), lvl (ncl), cid (ncl)
+  std::vector<size_t> pack_off;
+  int* d_dest = ndest ? static_cast<int*>(up_.scratch(ndest * sizeof(int))) : nullptr;
+  int max_extra = 0;
+  for (auto& f : fi) {
+    if (!f.nextra) continue;
+    const int ncl = (int)f.cols.size() - 1;
+    pack_off.push_back(pack.size());
+    for (int t = 0; t <= ncl; ++t) pack.push_back(f.coff[(size_t)t + 1]);
+    for (int t = 0; t < ncl; ++t) pack.push_back(level(f.cols[(size_t)t + 1]));
+    for (int t = 0; t < ncl; ++t) pack.push_back(f.cols[(size_t)t + 1]);
+  }
+  if (!pack_off.empty()) {
+    int* dp0 = up_.put(pack);
+    size_t q = 0;
+    for (auto& f : fi) {
+      if (!f.nextra) continue;
+      const int ncl = (int)f.cols.size() - 1;
+      int* dp = dp0 + pack_off[q++];
+      am.push_back(ArgmaxDesc<T>{W + f.foff, f.m, f.c, f.rs, ncl, dp, dp + ncl + 1, dp + 2 * ncl + 1,
+                                 d_dest + f.dest_off});
+      max_extra = std::max(max_extra, f.nextra);
+    }
+    if (checking_)
+      for (auto& a : am) in_bounds(a.F, a.r1, 1, a.ld, sizeof(T), "argmax rows");
+    auto* d = up_.put(am);
+    tm_.begin(st_, 3);
+    check(launch_argmax<T>(d, (int)am.size(), max_extra, st_), "argmax");
+    tm_.end(st_);
+  }
+  // R_s = [R_ss R_sn] into the W store
+  std::vector<CopyDesc<T>> rc;
+  for (auto& f : fi) {
+    WOp op;
+    op.kind = 0;
+    op.stage = k_;
+    op.round = round;
+    op.c = f.c;
+    op.w = f.n - f.c;
+    op.slots = slots_[(size_t)f.s];
+    for (size_t t = 1; t < f.cols.size(); ++t)
+      op.nslots.insert(op.nslots.end(), slots_[(size_t)f.cols[t]].begin(), slots_[(size_t)f.cols[t]].end());
+    if (f.c > 0) {
+      T* R = wstore((size_t)f.c * f.n);
+      op.R = R;
+      rc.push_back(CopyDesc<T>{W + f.foff, R, nullptr, f.m, f.c, f.c, f.n, 0, 0});
+    }
+    h_.stats.n_fronts++;
+    h_.stats.max_front_rows = std::max<int64_t>(h_.stats.max_front_rows, f.m);
+    h_.stats.max_front_cols = std::max<int64_t>(h_.stats.max_front_cols, f.n);
+    if (k_ == 1) {
+      h_.stats.top_rows = f.m;
+      h_.stats.top_cols = f.c;
+    }
+    const double m = f.m, c = f.c, t = f.n - f.c;
+    h_.stats.flops_front += 2.0 * c * c * (m - c / 3.0) + (4.0 * m * c - 2.0 * c * c) * t;
+    if (f.c > 0) h_.ops.push_back(std::move(op));
+  }
+  copies(rc);
+  std::vector<int> dest(ndest);
+  if (ndest) {
+    SPAQR_CUDA(cudaMemcpyAsync(dest.data(), d_dest, ndest * sizeof(int), cudaMemcpyDeviceToHost, st_));
+  }
+  sync();
+  // new groups: returned rows per owner, then extra rows per destination
+  std::vector<int> ids;
+  struct Pending {
+    int id;
+    size_t front;
+    int r0, cnt;       // contiguous rows (returned)
+    std::vector<int> rows;  // explicit rows (extra)
+  };
+  std::vector<Pending> pend;
+  for (size_t b = 0; b < batch.size(); ++b) {
+    FrontInfo& f = fi[b];
+    std::vector<int> rest(f.cols.begin() + 1, f.cols.end());
+    int pos = f.rs;
+    const auto& fg = batch[b].second;
+    size_t q = 0;
+    while (q < fg.size() && G_[(size_t)fg[q]].owner == f.s) ++q;
+    while (q < fg.size()) {
+      const int o = G_[(size_t)fg[q]].owner;
+      int cnt = 0;
+      while (q < fg.size() && G_[(size_t)fg[q]].owner == o) cnt += G_[(size_t)fg[q++]].rows;
+      if (!rest.empty()) {
+        const int id = new_group(o, cnt, rest);
+        ids.push_back(id);
+        pend.push_back(Pending{id, b, pos, cnt, {}});
+      }
+      pos += cnt;
+    }
+    if (f.nextra) {
+      std::vector<std::vector<int>> by((size_t)rest.size());
+      for (int i = 0; i < f.nextra; ++i) {
+        const int t = dest[f.dest_off + (size_t)i];
+        if (t < 0 || t >= (int)rest.size())
+          throw Error(SPAQR_ERR_RANK_DEFICIENT, "non-finite values in a front at stage " + std::to_string(k_));
+        by[(size_t)t].push_back(f.c + i);
+      }
+      for (size_t t = 0; t < rest.size(); ++t) {
+        if (by[t].empty()) continue;
+        const int id = new_group(rest[t], (int)by[t].size(), rest);
+        ids.push_back(id);
+        pend.push_back(Pending{id, b, 0, (int)by[t].size(), by[t]});
+      }
+    }
+    for (int g : fg) kill(g);
+    calive_[(size_t)f.s] = 0;
+  }
+  assign_buffer(ids, false);
+  std::vector<CopyDesc<T>> sc;
+  std::vector<int32_t> rowlist;
+  std::vector<size_t> row_off(pend.size(), 0);
+  for (size_t i = 0; i < pend.size(); ++i) {
+    row_off[i] = rowlist.size();
+    rowlist.insert(rowlist.end(), pend[i].rows.begin(), pend[i].rows.end());
+  }
+  int32_t* d_rows = rowlist.empty() ? nullptr : up_.put(rowlist);
+  for (size_t i = 0; i < pend.size(); ++i) {
+    const Pending& p = pend[i];
+    const Group& g = G_[(size_t)p.id];
+    const FrontInfo& f = fi[p.front];
+    if (g.rows == 0 || g.width == 0) continue;
+    const T* src = W + f.foff + (size_t)f.c * f.m;
+    if (p.rows.empty())
+      sc.push_back(CopyDesc<T>{src + p.r0, g.ptr, nullptr, f.m, g.ld, g.rows, g.width, 0, 0});
+    else
+      sc.push_back(CopyDesc<T>{src, g.ptr, d_rows + row_off[i], f.m, g.ld, g.rows, g.width, 0, 0});
+  }
+  copies(sc);
+  pool_.release(W);
+}
+
+// ---------------------------------------------------------------- scale
+template <typename T>
+void Factorizer<T>::scale() {
+  std::vector<std::vector<int>> own, touch;
+  index_groups(own, touch);
+  p1_of_.assign(ccols_.size(), -1);
+  p2_of_.assign(ccols_.size(), -1);
+  struct SInfo {
+    int p, rp, c, n;
+    std::vector<int> cols, coff;
+    size_t foff;
+    T* R;
+  };
+  std::vector<SInfo> si;
+  size_t ws = 0;
+  for (size_t p = 0; p < ccols_.size(); ++p) {
+    if (!calive_[p] || ccols_[p] == 0) continue;
+    SInfo s;
+    s.p = (int)p;
+    s.c = ccols_[p];
+    s.rp = 0;
+    std::vector<int> u;
+    for (int g : own[p]) {
+      s.rp += G_[(size_t)g].rows;
+      u.insert(u.end(), G_[(size_t)g].sup.begin(), G_[(size_t)g].sup.end());
+    }
+    if (s.rp < s.c)
+      throw Error(SPAQR_ERR_RANK_DEFICIENT, "interface " + std::to_string(p) + " at stage " + std::to_string(k_) +
+                                                ": " + std::to_string(s.rp) + " rows < " + std::to_string(s.c) +
+                                                " columns");
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
+    s.cols.push_back((int)p);
+    for (int c : u)
+      if (c != (int)p) s.cols.push_back(c);
+    s.coff.assign(s.cols.size() + 1, 0);
+    for (size_t t = 0; t < s.cols.size(); ++t) s.coff[t + 1] = s.coff[t] + ccols_[(size_t)s.cols[t]];
+    s.n = s.coff.back();
+    s.foff = ws;
+    ws += (size_t)s.rp * s.n;
+    si.push_back(std::move(s));
+  }
+  if (si.empty()) return;
+  T* W = static_cast<T*>(pool_.alloc(std::max<size_t>(ws, 1) * sizeof(T)));
+  SPAQR_CUDA(cudaMemsetAsync(W, 0, std::max<size_t>(ws, 1) * sizeof(T), st_));
+  std::vector<CopyDesc<T>> gat;
+  std::vector<FrontDesc<T>> fr;
+  for (auto& s : si) {
+    T* F = W + s.foff;
+    int row = 0;
+    for (int g : own[(size_t)s.p]) {
+      const Group& gg = G_[(size_t)g];
+      for (size_t t = 0; t < gg.sup.size(); ++t) {
+        const int c = gg.sup[t];
+        const size_t ci = (size_t)(std::find(s.cols.begin(), s.cols.end(), c) - s.cols.begin());
+        if (gg.rows == 0 || ccols_[(size_t)c] == 0) continue;
+        gat.push_back(CopyDesc<T>{gg.ptr + (size_t)gg.off[t] * gg.ld, F + row + (size_t)s.coff[ci] * s.rp, nullptr,
+                                  gg.ld, s.rp, gg.rows, ccols_[(size_t)c], 0, 0});
+      }
+      row += gg.rows;
+    }
+    fr.push_back(FrontDesc<T>{F, s.rp, s.n, s.c, s.rp});
+    const double m = s.rp, c = s.c, t = s.n - s.c;
+    h_.stats.flops_front += 2.0 * c * c * (m - c / 3.0) + (4.0 * m * c - 2.0 * c * c) * t;
+  }
+  copies(gat);
+  front_qr(fr);
+  // R_pp into the W store; new groups p1 (identity on p) and p2
+  std::vector<CopyDesc<T>> rc, idn, cp;
+  std::vector<int> ids;
+  for (auto& s : si) {
+    WOp op;
+    op.kind = 1;
+    op.stage = k_;
+    op.c = s.c;
+    op.slots = slots_[(size_t)s.p];
+    s.R = wstore((size_t)s.c * s.c);
+    op.R = s.R;
+    rc.push_back(CopyDesc<T>{W + s.foff, s.R, nullptr, s.rp, s.c, s.c, s.c, 0, 0});
+    h_.ops.push_back(std::move(op));
+    for (int g : own[(size_t)s.p]) kill(g);
+    std::vector<int> sup1(s.cols.begin(), s.cols.end());
+    std::sort(sup1.begin(), sup1.end());
+    const int id1 = new_group(s.p, s.c, sup1);
+    p1_of_[(size_t)s.p] = id1;
+    ids.push_back(id1);
+    std::vector<int> rest(s.cols.begin() + 1, s.cols.end());
+    if (s.rp > s.c && !rest.empty()) {
+      std::sort(rest.begin(), rest.end());
+      const int id2 = new_group(s.p, s.rp - s.c, rest);
+      p2_of_[(size_t)s.p] = id2;
+      ids.push_back(id2);
+    }
+  }
+  assign_buffer(ids, false);
+  for (auto& s : si) {
+    const T* F = W + s.foff;
+    const Group& g1 = G_[(size_t)p1_of_[(size_t)s.p]];
+    for (size_t t = 0; t < s.cols.size(); ++t) {
+      const int c = s.cols[t];
+      const int wc = ccols_[(size_t)c];
+      if (wc == 0) continue;
+      T* dst1 = g1.ptr + (size_t)col_off(g1, c) * g1.ld;
+      if (t == 0)
+        idn.push_back(CopyDesc<T>{nullptr, dst1, nullptr, 0, g1.ld, s.c, s.c, 0, 0});
+      else
+        cp.push_back(CopyDesc<T>{F + (size_t)s.coff[t] * s.rp, dst1, nullptr, s.rp, g1.ld, s.c, wc, 0, 0});
+      if (t > 0 && p2_of_[(size_t)s.p] >= 0) {
+        const Group& g2 = G_[(size_t)p2_of_[(size_t)s.p]];
+        cp.push_back(CopyDesc<T>{F + s.c + (size_t)s.coff[t] * s.rp, g2.ptr + (size_t)col_off(g2, c) * g2.ld,
+                                 nullptr, s.rp, g2.ld, g2.rows, wc, 0, 0});
+      }
+    }
+  }
+  copies(rc);
+  copies(cp);
+  if (!idn.empty()) {
+    auto* d = up_.put(idn);
+    check(launch_identity<T>(d, (int)idn.size(), st_), "identity");
+  }
+  pool_.release(W);
+  // X <- X R_pp^{-1} on every block column p of the other owners' rows
+  std::vector<T*> Rof(ccols_.size(), nullptr);
+  for (auto& s : si) Rof[(size_t)s.p] = s.R;
+  std::vector<TrsmDesc<T>> tr;
+  int maxr = 0;
+  for (size_t id = 0; id < G_.size(); ++id) {
+    const Group& g = G_[id];
+    if (!g.alive || g.rows == 0) continue;
+    for (size_t t = 0; t < g.sup.size(); ++t) {
+      const int c = g.sup[t];
+      if (c == g.owner || !Rof[(size_t)c]) continue;
+      tr.push_back(TrsmDesc<T>{g.ptr + (size_t)g.off[t] * g.ld, Rof[(size_t)c], g.ld, g.rows, ccols_[(size_t)c],
+                               ccols_[(size_t)c]});
+      maxr = std::max(maxr, g.rows);
+    }
+  }
+  if (checking_)
+    for (auto& t : tr) {
+      in_bounds(t.ptr, t.rows, t.c, t.ld, sizeof(T), "trsm X");
+      in_bounds(t.R, t.c, t.c, t.rld, sizeof(T), "trsm R");
+    }
+  if (!tr.empty()) {
+    auto* d = up_.put(tr);
+    tm_.begin(st_, 3);
+    check(launch_trsm<T>(d, (int)tr.size(), maxr, st_), "trsm");
+    tm_.end(st_);
+  }
+}
+
+// ---------------------------------------------------------------- step 1
+template <typename T>
+void Factorizer<T>::step1() {
+  std::vector<QrcpDesc<T>> qs;
+  std::vector<int> who;
+  for (size_t p = 0; p < ccols_.size(); ++p) {
+    const int id = p2_of_.empty() ? -1 : p2_of_[p];
+    if (id < 0) continue;
+    Group& g = G_[(size_t)id];
+    if (g.rows == 0 || g.width == 0) continue;
+    who.push_back(id);
+  }
+  if (who.empty()) return;
+  int* d_rank = static_cast<int*>(up_.scratch(who.size() * sizeof(int)));
+  for (size_t i = 0; i < who.size(); ++i) {
+    Group& g = G_[(size_t)who[i]];
+    qs.push_back(QrcpDesc<T>{g.ptr, nullptr, g.ptr, nullptr, nullptr, d_rank + i, g.rows, g.width, g.ld, g.ld});
+  }
+  std::vector<T*> work;
+  qrcp(qs, work);
+  std::vector<int> rank(who.size());
+  SPAQR_CUDA(cudaMemcpyAsync(rank.data(), d_rank, who.size() * sizeof(int), cudaMemcpyDeviceToHost, st_));
+  sync();
+  for (T* w : work) pool_.release(w);
+  for (size_t i = 0; i < who.size(); ++i) {
+    Group& g = G_[(size_t)who[i]];
+    const double m = g.rows, n = g.width, k = rank[i];
+    h_.stats.flops_sparsify += 4.0 * m * n * k - 2.0 * k * k * (m + n) + 4.0 * k * k * k / 3.0;
+    if (rank[i] < g.rows) {
+      g.rows = rank[i];
+      if (g.rows == 0) {
+        kill(who[i]);
+        p2_of_[(size_t)g.owner] = -1;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- step 2
+template <typename T>
+void Factorizer<T>::step2() {
+  std::vector<int> ps;
+  for (size_t p = 0; p < ccols_.size(); ++p)
+    if (!p1_of_.empty() && p1_of_[p] >= 0) ps.push_back((int)p);
+  if (ps.empty()) return;
+  // greedy colouring of q ~ p  <=>  q in support(p1 of p) or p in support(p1 of q)
+  const size_t nc = ccols_.size();
+  std::vector<std::vector<int>> adj(nc);
+  for (int p : ps) {
+    for (int q : G_[(size_t)p1_of_[(size_t)p]].sup)
+      if (q != p && p1_of_[(size_t)q] >= 0) {
+        adj[(size_t)p].push_back(q);
+        adj[(size_t)q].push_back(p);
+      }
+  }
+  std::vector<int> colour(nc, -1);
+  int ncol = 0;
+  for (int p : ps) {
+    std::vector<char> used((size_t)ncol + 1, 0);
+    for (int q : adj[(size_t)p])
+      if (colour[(size_t)q] >= 0) used[(size_t)colour[(size_t)q]] = 1;
+    int c = 0;
+    while (c < ncol && used[(size_t)c]) ++c;
+    colour[(size_t)p] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  std::vector<std::vector<int>> own, touch;
+  index_groups(own, touch);
+  struct P2 {
+    int p;
+    size_t op;
+    int ncm;
+  };
+  std::vector<P2> recs;
+  std::vector<T*> work_all;
+  for (int col = 0; col < ncol; ++col) {
+    std::vector<CopyDesc<T>> cps;
+    std::vector<QrcpDesc<T>> qs;
+    std::vector<ReflDesc<T>> rf;
+    std::vector<size_t> opidx;
+    size_t ws = 0;
+    struct MInfo {
+      int p, cp, rn, cn;
+      std::vector<int> nb, ncols;
+      size_t moff;
+    };
+    std::vector<MInfo> mi;
+    for (int p : ps) {
+      if (colour[(size_t)p] != col) continue;
+      MInfo x;
+      x.p = p;
+      x.cp = ccols_[(size_t)p];
+      x.nb = touch[(size_t)p];
+      x.nb.erase(std::remove_if(x.nb.begin(), x.nb.end(), [&](int g) { return !G_[(size_t)g].alive; }), x.nb.end());
+      std::sort(x.nb.begin(), x.nb.end(), [&](int a, int b) {
+        const int oa = G_[(size_t)a].owner, ob = G_[(size_t)b].owner;
+        return oa != ob ? oa < ob : a < b;
+      });
+      x.rn = 0;
+      for (int g : x.nb) x.rn += G_[(size_t)g].rows;
+      const Group& g1 = G_[(size_t)p1_of_[(size_t)p]];
+      x.cn = 0;
+      for (int c : g1.sup)
+        if (c != p) {
+          x.ncols.push_back(c);
+          x.cn += ccols_[(size_t)c];
+        }
+      x.moff = ws;
+      ws += (size_t)x.cp * (x.rn + x.cn);
+      mi.push_back(std::move(x));
+    }
+    T* M = static_cast<T*>(pool_.alloc(std::max<size_t>(ws, 1) * sizeof(T)));
+    for (auto& x : mi) {
+      T* Mp = M + x.moff;
+      int colm = 0;
+      for (int g : x.nb) {
+        const Group& gg = G_[(size_t)g];
+        if (gg.rows)
+          cps.push_back(CopyDesc<T>{gg.ptr + (size_t)col_off(gg, x.p) * gg.ld, Mp + (size_t)colm * x.cp, nullptr,
+                                    gg.ld, x.cp, gg.rows, x.cp, 1, 0});
+        colm += gg.rows;
+      }
+      const Group& g1 = G_[(size_t)p1_of_[(size_t)x.p]];
+      for (int c : x.ncols) {
+        if (ccols_[(size_t)c])
+          cps.push_back(CopyDesc<T>{g1.ptr + (size_t)col_off(g1, c) * g1.ld, Mp + (size_t)colm * x.cp, nullptr, g1.ld,
+                                    x.cp, x.cp, ccols_[(size_t)c], 0, 0});
+        colm += ccols_[(size_t)c];
+      }
+      const int ncm = x.rn + x.cn;
+      const int kmax = std::min(x.cp, ncm);
+      WOp op;
+      op.kind = 2;
+      op.stage = k_;
+      op.round = col;
+      op.c = x.cp;
+      op.w = kmax;
+      op.slots = slots_[(size_t)x.p];
+      T* V = wstore((size_t)x.cp * std::max(kmax, 1));
+      T* tau = wstore((size_t)std::max(kmax, 1));
+      op.V = V;
+      op.tau = tau;
+      op.kdev = static_cast<int*>(h_.wpool.alloc(sizeof(int)));
+      qs.push_back(QrcpDesc<T>{Mp, nullptr, nullptr, V, tau, op.kdev, x.cp, ncm, x.cp, x.cp});
+      for (int g : x.nb) {
+        const Group& gg = G_[(size_t)g];
+        if (gg.rows)
+          rf.push_back(ReflDesc<T>{gg.ptr + (size_t)col_off(gg, x.p) * gg.ld, V, tau, op.kdev, gg.ld, x.cp, gg.rows, 0});
+      }
+      for (int c : x.ncols)
+        if (ccols_[(size_t)c])
+          rf.push_back(ReflDesc<T>{g1.ptr + (size_t)col_off(g1, c) * g1.ld, V, tau, op.kdev, g1.ld, x.cp,
+                                   ccols_[(size_t)c], 1});
+      recs.push_back(P2{x.p, h_.ops.size(), ncm});
+      h_.ops.push_back(std::move(op));
+    }
+    copies(cps);
+    qrcp(qs, work_all);
+    if (checking_)
+      for (auto& r : rf) {
+        if (r.mode == 0)
+          in_bounds(r.ptr, r.nvec, r.len, r.ld, sizeof(T), "refl rows");
+        else
+          in_bounds(r.ptr, r.len, r.nvec, r.ld, sizeof(T), "refl cols");
+      }
+    if (!rf.empty()) {
+      int mv = 0;
+      for (auto& r : rf) mv = std::max(mv, r.nvec);
+      auto* d = up_.put(rf);
+      tm_.begin(st_, 3);
+      check(launch_refl<T>(d, (int)rf.size(), mv, st_), "refl");
+      tm_.end(st_);
+    }
+    pool_.release(M);
+  }
+  // ranks back; keep the ops that drop something
+  std::vector<int> ks(recs.size());
+  for (size_t i = 0; i < recs.size(); ++i)
+    SPAQR_CUDA(cudaMemcpyAsync(&ks[i], h_.ops[recs[i].op].kdev, sizeof(int), cudaMemcpyDeviceToHost, st_));
+  sync();
+  for (T* w : work_all) pool_.release(w);
+  std::vector<char> drop(h_.ops.size(), 0);
+  for (size_t i = 0; i < recs.size(); ++i) {
+    WOp& op = h_.ops[recs[i].op];
+    const int k = ks[i], p = recs[i].p;
+    op.k = k;
+    {
+      // column-pivoted QR to rank k of the c_p x ncm block, then the two-sided application
+      const double m = op.c, n = recs[i].ncm, kk = k;
+      h_.stats.flops_sparsify += 4.0 * m * n * kk - 2.0 * kk * kk * (m + n) + 4.0 * kk * kk * kk / 3.0;
+      h_.stats.flops_sparsify += 4.0 * kk * m * n;
+    }
+    if (k >= op.c) {
+      drop[recs[i].op] = 1;
+      continue;
+    }
+    ccols_[(size_t)p] = k;
+    slots_[(size_t)p].resize((size_t)k);
+    Group& g1 = G_[(size_t)p1_of_[(size_t)p]];
+    g1.rows = k;
+    if (k == 0) {
+      kill(p1_of_[(size_t)p]);
+      p1_of_[(size_t)p] = -1;
+    }
+  }
+  // remove identity ops (k == c) -- their device blocks stay in the W pool
+  std::vector<WOp> kept;
+  kept.reserve(h_.ops.size());
+  for (size_t i = 0; i < h_.ops.size(); ++i)
+    if (!drop[i]) kept.push_back(std::move(h_.ops[i]));
+  h_.ops.swap(kept);
+  (void)own;
+}
+
+// ---------------------------------------------------------------- merge
+template <typename T>
+void Factorizer<T>::merge() {
+  const StageClusters& nxt = an_.stages[(size_t)k_ - 1];
+  const size_t nnew = nxt.node.size();
+  std::vector<int> nccols(nnew, 0);
+  std::vector<std::vector<int32_t>> nslots(nnew);
+  std::vector<int> choff(ccols_.size(), 0), nchild(nnew, 0);
+  for (size_t c = 0; c < ccols_.size(); ++c) {
+    if (!calive_[c]) continue;
+    const int P = sc_->parent[c];
+    if (P < 0) throw Error(SPAQR_ERR_CUDA, "internal: live cluster without parent");
+    choff[c] = nccols[(size_t)P];
+    nccols[(size_t)P] += ccols_[c];
+    nchild[(size_t)P]++;
+    nslots[(size_t)P].insert(nslots[(size_t)P].end(), slots_[c].begin(), slots_[c].end());
+  }
+  // groups whose column layout changes get a new block
+  std::vector<int> moved;
+  std::vector<Group> newg;
+  std::vector<CopyDesc<T>> cps;
+  std::vector<int> ids;
+  const auto old_ccols = ccols_;
+  for (size_t id = 0; id < G_.size(); ++id) {
+    Group& g = G_[id];
+    if (!g.alive) continue;
+    std::vector<int> nsup;
+    for (int c : g.sup) nsup.push_back(sc_->parent[(size_t)c]);
+    std::sort(nsup.begin(), nsup.end());
+    nsup.erase(std::unique(nsup.begin(), nsup.end()), nsup.end());
+    bool same = nsup.size() == g.sup.size();
+    for (size_t t = 0; same && t < g.sup.size(); ++t) {
+      const int c = g.sup[t], P = sc_->parent[(size_t)c];
+      if (nchild[(size_t)P] != 1) same = false;
+      // columns dropped by step 2 (block width larger than the cluster now)
+      const int wold = (t + 1 < g.sup.size() ? g.off[t + 1] : g.width) - g.off[t];
+      if (wold != ccols_[(size_t)c]) same = false;
+    }
+    g.owner = sc_->parent[(size_t)g.owner];
+    if (same) {
+      for (auto& c : g.sup) c = sc_->parent[(size_t)c];
+      continue;
+    }
+    moved.push_back((int)id);
+  }
+  // new blocks for moved groups (one buffer, zero-filled)
+  std::vector<int> tmpids;
+  std::vector<std::vector<int>> oldsup(moved.size()), oldoff(moved.size());
+  std::vector<T*> oldptr(moved.size());
+  std::vector<int> oldld(moved.size()), oldbuf(moved.size());
+  for (size_t i = 0; i < moved.size(); ++i) {
+    Group& g = G_[(size_t)moved[i]];
+    oldsup[i] = g.sup;
+    oldoff[i] = g.off;
+    oldptr[i] = g.ptr;
+    oldld[i] = g.ld;
+    oldbuf[i] = g.buf;
+    std::vector<int> nsup;
+    for (int c : g.sup) nsup.push_back(sc_->parent[(size_t)c]);
+    std::sort(nsup.begin(), nsup.end());
+    nsup.erase(std::unique(nsup.begin(), nsup.end()), nsup.end());
+    g.sup = nsup;
+    g.off.assign(nsup.size(), 0);
+    int w = 0;
+    for (size_t t = 0; t < nsup.size(); ++t) {
+      g.off[t] = w;
+      w += nccols[(size_t)nsup[t]];
+    }
+    g.width = w;
+    g.ld = std::max(g.rows, 1);
+    g.buf = -1;
+    g.ptr = nullptr;
+  }
+  {
+    size_t total = 0;
+    for (int id : moved) total += (size_t)G_[(size_t)id].ld * G_[(size_t)id].width;
+    if (total) {
+      T* base = static_cast<T*>(pool_.alloc(total * sizeof(T)));
+      SPAQR_CUDA(cudaMemsetAsync(base, 0, total * sizeof(T), st_));
+      bufs_.push_back(Buf{base, 0});
+      const int b = (int)bufs_.size() - 1;
+      size_t o = 0;
+      for (int id : moved) {
+        Group& g = G_[(size_t)id];
+        const size_t sz = (size_t)g.ld * g.width;
+        if (sz) {
+          g.ptr = base + o;
+          g.buf = b;
+          bufs_[(size_t)b].refs++;
+        }
+        o += sz;
+      }
+      if (bufs_[(size_t)b].refs == 0) pool_.release(base);
+    }
+  }
+  for (size_t i = 0; i < moved.size(); ++i) {
+    Group& g = G_[(size_t)moved[i]];
+    for (size_t t = 0; t < oldsup[i].size(); ++t) {
+      const int c = oldsup[i][t];
+      const int P = sc_->parent[(size_t)c];
+      const int wc = ccols_[(size_t)c];
+      if (wc == 0 || g.rows == 0) continue;
+      const int dcol = col_off(g, P) + choff[(size_t)c];
+      cps.push_back(CopyDesc<T>{oldptr[i] + (size_t)oldoff[i][t] * oldld[i], g.ptr + (size_t)dcol * g.ld, nullptr,
+                                oldld[i], g.ld, g.rows, wc, 0, 0});
+    }
+  }
+  copies(cps);
+  for (size_t i = 0; i < moved.size(); ++i) {
+    if (oldbuf[i] >= 0) {
+      Buf& b = bufs_[(size_t)oldbuf[i]];
+      if (--b.refs == 0) {
+        pool_.release(b.p);
+        b.p = nullptr;
+      }
+    }
+  }
+  // adopt the stage k-1 clusters
+  sc_ = &nxt;
+  ccols_.swap(nccols);
+  slots_.swap(nslots);
+  calive_.assign(nnew, 1);
+  p1_of_.clear();
+  p2_of_.clear();
+  (void)old_ccols;
+  (void)tmpids;
+  (void)newg;
+  (void)ids;
+}
+
+template <typename T>
+void Factorizer<T>::run(const spaqr_csr& A) {
+  L_ = an_.depth;
+  smem_max_ = max_smem_optin();
+  {
+    const char* e = std::getenv("SPAQR_CHECK");
+    checking_ = e && e[0] == '1';
+  }
+  up_.init(st_, size_t(32) << 20);
+  double t0 = now();
+  init_stage(A);
+  double tp[6] = {0, 0, 0, 0, 0, 0};
+  for (k_ = L_; k_ >= 1; --k_) {
+    double a = now();
+    eliminate();
+    double b = now();
+    tp[0] += b - a;
+    if (sparsify_here()) {
+      scale();
+      double c = now();
+      tp[2] += c - b;
+      step1();
+      double d = now();
+      tp[3] += d - c;
+      step2();
+      double e = now();
+      tp[4] += e - d;
+      b = e;
+    }
+    if (k_ > 1) {
+      merge();
+      double f = now();
+      tp[5] += f - b;
+    }
+    if (h_.opt.verbose) {
+      size_t live = 0;
+      for (auto& g : G_) live += g.alive;
+      std::fprintf(stderr, "[spaqr] stage %d done: live groups %zu, pool %.1f MB (peak %.1f)\n", k_, live,
+                   pool_.in_use() / 1e6, pool_.peak() / 1e6);
+    }
+  }
+  sync();
+  for (auto& g : G_)
+    if (g.alive) throw Error(SPAQR_ERR_CUDA, "internal: rows left after the root");
+  for (int i = 0; i < 6; ++i) h_.stats.t_phase[i] = tp[i];
+  h_.stats.launches = launches_;
+  h_.stats.syncs = up_.syncs;
+  (void)t0;
+}
+
+}  // namespace
+
+void run_factor(Handle& h, const spaqr_csr& A, const Analysis& an) {
+  if (h.precision == SPAQR_PREC_MIXED) {
+    Factorizer<float> f(h, an);
+    f.run(A);
+  } else {
+    Factorizer<double> f(h, an);
+    f.run(A);
+  }
+}
+
+}  // namespace spaqr

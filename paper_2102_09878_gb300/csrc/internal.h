@@ -1,0 +1,170 @@
+// Internal types shared by the factorization, the solve and the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/spaqr.h"
+#include "symbolic.h"
+
+namespace spaqr {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& msg) : std::runtime_error(msg), code(c) {}
+};
+
+#define SPAQR_CUDA(x)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (x);                                                                          \
+    if (e_ != cudaSuccess)                                                                         \
+      throw ::spaqr::Error(e_ == cudaErrorMemoryAllocation ? SPAQR_ERR_OOM : SPAQR_ERR_CUDA,       \
+                           std::string(#x) + ": " + cudaGetErrorString(e_) + " at " + __FILE__ + ":" + \
+                               std::to_string(__LINE__));                                          \
+  } while (0)
+
+// Size-class sub-allocator over large cudaMalloc chunks.  All work of one
+// handle runs on one stream, so a block released on the host after its last
+// use was enqueued may be handed out again at once (stream order protects it).
+class DevicePool {
+ public:
+  explicit DevicePool(size_t chunk_bytes = size_t(256) << 20) : chunk_(chunk_bytes) {}
+  ~DevicePool();
+  DevicePool(const DevicePool&) = delete;
+  DevicePool& operator=(const DevicePool&) = delete;
+  void* alloc(size_t bytes);
+  void release(void* p);
+  // true when [p, p + bytes) lies inside one live block (host-side bounds check)
+  bool contains(const void* p, size_t bytes) const;
+  size_t in_use() const { return in_use_; }
+  size_t peak() const { return peak_; }
+  size_t reserved() const { return reserved_; }
+
+ private:
+  struct Chunk {
+    char* base;
+    size_t size, used;
+  };
+  size_t chunk_;
+  std::vector<Chunk> chunks_;
+  std::vector<std::vector<void*>> free_;  // by size class
+  std::vector<std::pair<void*, int>> live_;  // sorted by pointer: block -> class
+  size_t in_use_ = 0, peak_ = 0, reserved_ = 0;
+  int find(void* p) const;
+};
+
+// Pinned staging + device arena for small descriptor arrays.  put() copies a
+// host array into pinned memory and enqueues the H2D copy; the device pointer
+// stays valid until reset(), which the owner calls right after a stream
+// synchronisation.  When a block fills up a larger one is started; retired
+// blocks are released at the next reset(), so no pointer handed out since the
+// last reset is ever reused early.
+class Uploader {
+ public:
+  Uploader() = default;
+  ~Uploader();
+  void init(cudaStream_t st, size_t bytes);
+  template <typename X>
+  X* put(const std::vector<X>& v) {
+    return static_cast<X*>(put_bytes(v.data(), v.size() * sizeof(X)));
+  }
+  void* put_bytes(const void* src, size_t bytes);
+  void* scratch(size_t bytes);  // device-only space, same lifetime
+  void reset();
+  int64_t syncs = 0;
+
+ private:
+  struct Block {
+    char* host = nullptr;
+    char* dev = nullptr;
+    size_t cap = 0;
+  };
+  cudaStream_t st_ = nullptr;
+  Block cur_;
+  std::vector<Block> retired_;
+  size_t off_ = 0;
+  void* take(size_t bytes, const void* src);
+  static void free_block(Block& b);
+};
+
+// Device-time accounting by kernel family with CUDA events on one stream.
+// begin()/end() bracket the launches of a family; drain() (after a stream
+// synchronisation) adds the elapsed times into the totals.
+class EventTimer {
+ public:
+  ~EventTimer();
+  void begin(cudaStream_t st, int family);
+  void end(cudaStream_t st);
+  void drain(double* totals, int64_t* counts);
+
+ private:
+  struct Pair {
+    cudaEvent_t a, b;
+    int fam;
+  };
+  std::vector<cudaEvent_t> free_;
+  std::vector<Pair> pending_;
+  Pair open_{nullptr, nullptr, -1};
+  cudaEvent_t get();
+};
+
+// One stored factor of W (Section 2.7): kind 0 = R_s = [R_ss R_sn], kind 1 =
+// R_pp, kind 2 = Q_pp as k Householder reflectors.
+struct WOp {
+  int kind = 0, stage = 0, round = 0;
+  int c = 0, w = 0;                 // slots of s/p; R_sn columns or reflector capacity
+  int k = 0;                        // Q_p: number of reflectors (known after the sync)
+  std::vector<int32_t> slots, nslots;
+  void* R = nullptr;                // c x (c + w) (kind 0), c x c (kind 1); ld = c
+  void* V = nullptr;                // c x w, ld c (kind 2)
+  void* tau = nullptr;              // w (kind 2)
+  int* kdev = nullptr;              // device rank (kind 2)
+};
+
+struct Handle {
+  spaqr_options opt{};
+  cudaStream_t st = nullptr;       // stream of all library work
+  cudaStream_t user_st = nullptr;  // caller's stream (NULL = legacy default stream)
+  bool own_stream = false;
+  cudaEvent_t ev = nullptr;
+  // make st wait for the work the caller enqueued on its stream so far
+  void wait_caller();
+  int precision = SPAQR_PREC_FP64;
+  int64_t m = 0, n = 0, nnz = 0;
+  double t_analyze = 0.0;
+  // scaled operator A~ = A D (FP64, device) and its transpose, CSR
+  int64_t* d_rowptr = nullptr;
+  int32_t* d_colidx = nullptr;
+  double* d_vals = nullptr;
+  int64_t* d_trowptr = nullptr;
+  int32_t* d_tcolidx = nullptr;
+  double* d_tvals = nullptr;
+  double* d_D = nullptr;  // column scaling
+  std::vector<double> D;
+  // W store
+  DevicePool wpool{size_t(64) << 20};
+  std::vector<WOp> ops;
+  int depth = 0;
+  // device-side apply plan (built after the factorization)
+  struct ApplyPlan* plan = nullptr;
+  spaqr_stats stats{};
+  // solve workspace
+  double* d_work = nullptr;
+  size_t work_elems = 0;
+  ~Handle();
+};
+
+// Factorization entry (factor.cpp): fills h.ops, h.stats, device CSR.
+void run_factor(Handle& h, const spaqr_csr& A, const Analysis& an);
+// Apply / solve (solve.cu)
+void build_apply_plan(Handle& h);
+void free_apply_plan(Handle& h);
+void apply_Winv(Handle& h, double* z, int transpose);
+void apply_A(Handle& h, const double* x, double* y, int forward);
+void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info);
+
+}  // namespace spaqr

@@ -1,0 +1,473 @@
+// Apply of the stored factor W and the W-preconditioned CGLS (Section 4).
+//
+// W = W_1 ... W_L with W_l = (prod Q_p^T)(prod R_p)(prod R_s) for the
+// operations of stage l (Section 2.7).  W^{-1} z replays the operations in
+// reverse factorization order, W^{-T} z in factorization order.  Operations
+// of one elimination round, of one scaling phase and of one step-2 phase act
+// on disjoint slots and run as one batched launch each ("segment").  Every
+// vector is FP64; the stored factor is FP64 or FP32 (mixed precision).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "internal.h"
+
+namespace spaqr {
+
+namespace {
+constexpr int kT = 256;
+constexpr int kW = kT / 32;
+
+template <typename TW>
+struct ApplyOp {
+  const TW* R;  // kind 0: c x (c + w) = [R_ss R_sn]; kind 1: c x c
+  const TW* V;
+  const TW* tau;
+  const int* kdev;
+  const int32_t* slots;
+  const int32_t* nslots;
+  int c, w;
+};
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Back substitution R y = rhs (R upper, ld c) on a shared vector y of length c.
+template <typename TW>
+__device__ void upper_solve(const TW* R, int c, double* y) {
+  for (int j = c - 1; j >= 0; --j) {
+    __syncthreads();
+    const double yj = y[j] / (double)R[j + (int64_t)j * c];
+    __syncthreads();
+    if (threadIdx.x == 0) y[j] = yj;
+    for (int i = threadIdx.x; i < j; i += kT) y[i] -= (double)R[i + (int64_t)j * c] * yj;
+  }
+  __syncthreads();
+}
+
+// Forward substitution R^T y = rhs.
+template <typename TW>
+__device__ void lower_t_solve(const TW* R, int c, double* y) {
+  for (int i = 0; i < c; ++i) {
+    __syncthreads();
+    const double yi = y[i] / (double)R[i + (int64_t)i * c];
+    __syncthreads();
+    if (threadIdx.x == 0) y[i] = yi;
+    // y_j -= R_ij y_i for j > i (row i of R, stride c)
+    for (int j = i + 1 + threadIdx.x; j < c; j += kT) y[j] -= (double)R[i + (int64_t)j * c] * yi;
+  }
+  __syncthreads();
+}
+
+// W^{-1}: z_s <- R_ss^{-1} (z_s - R_sn z_n)  (kind 0) or z_p <- R_pp^{-1} z_p (kind 1)
+template <typename TW>
+__global__ void __launch_bounds__(kT) r_inv_kernel(const ApplyOp<TW>* ops, double* z) {
+  const ApplyOp<TW> op = ops[blockIdx.x];
+  extern __shared__ double sh[];
+  double* y = sh;          // c
+  double* part = sh + op.c;  // kW * c partials
+  const int c = op.c, w = op.w;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < kW * c; i += kT) part[i] = 0.0;
+  __syncthreads();
+  if (w > 0) {
+    const TW* Rn = op.R + (int64_t)c * c;
+    for (int i0 = 0; i0 < c; i0 += 32) {
+      const int i = i0 + lane;
+      double acc = 0.0;
+      for (int j = warp; j < w; j += kW) {
+        const double zj = z[op.nslots[j]];
+        if (i < c) acc += (double)Rn[i + (int64_t)j * c] * zj;
+      }
+      if (i < c) part[warp * c + i] = acc;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < c; i += kT) {
+    double s = z[op.slots[i]];
+    for (int q = 0; q < kW; ++q) s -= part[q * c + i];
+    y[i] = s;
+  }
+  upper_solve(op.R, c, y);
+  for (int i = threadIdx.x; i < c; i += kT) z[op.slots[i]] = y[i];
+}
+
+// W^{-T}: y = R_ss^{-T} z_s, z_s <- y, z_n -= R_sn^T y (kind 0); z_p <- R_pp^{-T} z_p (kind 1)
+template <typename TW>
+__global__ void __launch_bounds__(kT) r_invT_kernel(const ApplyOp<TW>* ops, double* z) {
+  const ApplyOp<TW> op = ops[blockIdx.x];
+  extern __shared__ double sh[];
+  double* y = sh;
+  const int c = op.c, w = op.w;
+  for (int i = threadIdx.x; i < c; i += kT) y[i] = z[op.slots[i]];
+  lower_t_solve(op.R, c, y);
+  for (int i = threadIdx.x; i < c; i += kT) z[op.slots[i]] = y[i];
+  if (w > 0) {
+    const TW* Rn = op.R + (int64_t)c * c;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < w; j += kW) {
+      const TW* col = Rn + (int64_t)j * c;
+      double s = 0.0;
+      for (int i = lane; i < c; i += 32) s += (double)col[i] * y[i];
+      s = wsum(s);
+      if (lane == 0) atomicAdd(&z[op.nslots[j]], -s);
+    }
+  }
+}
+
+// z_p <- Q z_p (inverse = 0: apply H_k first ... H_1 last; used by W^{-1})
+// z_p <- Q^T z_p (apply H_1 first; used by W^{-T})
+template <typename TW>
+__global__ void __launch_bounds__(kT) q_kernel(const ApplyOp<TW>* ops, double* z, int transpose) {
+  const ApplyOp<TW> op = ops[blockIdx.x];
+  extern __shared__ double sh[];
+  double* y = sh;
+  __shared__ double red[kW];
+  const int c = op.c;
+  const int k = *op.kdev;
+  for (int i = threadIdx.x; i < c; i += kT) y[i] = z[op.slots[i]];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = 0; t < k; ++t) {
+    const int i = transpose ? t : k - 1 - t;
+    const TW* v = op.V + (int64_t)i * c;
+    double s = 0.0;
+    for (int l = i + threadIdx.x; l < c; l += kT) s += (l == i ? 1.0 : (double)v[l]) * y[l];
+    s = wsum(s);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    double tot = 0.0;
+    for (int q = 0; q < kW; ++q) tot += red[q];
+    tot *= (double)op.tau[i];
+    for (int l = i + threadIdx.x; l < c; l += kT) y[l] -= tot * (l == i ? 1.0 : (double)v[l]);
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < c; i += kT) z[op.slots[i]] = y[i];
+}
+
+// ----------------------------------------------------------- CGLS kernels
+// y = A x (CSR, one thread per row) with per-block partial sums of y_i^2 * wgt_i^2
+__global__ void __launch_bounds__(kT) spmv_kernel(int64_t rows, const int64_t* rp, const int32_t* ci, const double* v,
+                                                  const double* x, double* y, const double* wdiv, double* part) {
+  __shared__ double red[kW];
+  const int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x;
+  double sq = 0.0;
+  if (r < rows) {
+    double s = 0.0;
+    for (int64_t e = rp[r]; e < rp[r + 1]; ++e) s += v[e] * x[ci[e]];
+    y[r] = s;
+    const double q = wdiv ? s / wdiv[r] : s;
+    sq = q * q;
+  }
+  sq = wsum(sq);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kW; ++q) t += red[q];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kT) sumsq_kernel(int64_t n, const double* x, double* part) {
+  __shared__ double red[kW];
+  double sq = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) sq += x[i] * x[i];
+  sq = wsum(sq);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kW; ++q) t += red[q];
+    part[blockIdx.x] = t;
+  }
+}
+
+// out = sum of part[0..n) in a fixed order (one block)
+__global__ void __launch_bounds__(kT) finish_sum_kernel(int n, const double* part, double* out) {
+  __shared__ double red[kT];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += kT) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// scal[0] = gamma, scal[1] = |q|^2, scal[2] = |D^-1 u|^2, scal[3] = |s|^2, scal[4] = beta
+__global__ void __launch_bounds__(kT) update_xr_kernel(int64_t n, int64_t m, double* x, const double* t, double* r,
+                                                       const double* q, const double* scal) {
+  const double alpha = scal[0] / scal[1];
+  const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i < n) x[i] += alpha * t[i];
+  if (i < m) r[i] -= alpha * q[i];
+}
+
+__global__ void beta_kernel(double* scal) {
+  scal[4] = scal[3] / scal[0];
+  scal[0] = scal[3];
+}
+
+__global__ void __launch_bounds__(kT) update_p_kernel(int64_t n, double* p, const double* s, const double* scal) {
+  const double beta = scal[4];
+  const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i < n) p[i] = s[i] + beta * p[i];
+}
+
+__global__ void __launch_bounds__(kT) scale_kernel(int64_t n, const double* a, const double* d, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i < n) out[i] = a[i] * d[i];
+}
+
+int blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + kT - 1) / kT); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan
+struct Segment {
+  int kind;     // 0 R_s, 1 R_p, 2 Q_p
+  int count;    // ops
+  size_t first; // index in the device op array
+  int smem;     // dynamic shared memory
+};
+
+struct ApplyPlan {
+  bool fp32 = false;
+  void* d_ops = nullptr;         // ApplyOp<TW>[nops] (factorization order)
+  int32_t* d_idx = nullptr;      // slot index arrays
+  std::vector<Segment> segs;     // factorization order
+  cudaGraphExec_t graph = nullptr;
+  double* d_scal = nullptr;
+  double* d_part = nullptr;
+  int part_n = 0;
+};
+
+template <typename TW>
+static void build_plan_t(Handle& h, ApplyPlan& P) {
+  std::vector<int32_t> idx;
+  std::vector<ApplyOp<TW>> ops;
+  std::vector<size_t> soff, noff;
+  for (auto& op : h.ops) {
+    soff.push_back(idx.size());
+    idx.insert(idx.end(), op.slots.begin(), op.slots.end());
+    noff.push_back(idx.size());
+    idx.insert(idx.end(), op.nslots.begin(), op.nslots.end());
+  }
+  SPAQR_CUDA(cudaMalloc(&P.d_idx, std::max<size_t>(idx.size(), 1) * sizeof(int32_t)));
+  SPAQR_CUDA(cudaMemcpy(P.d_idx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  for (size_t i = 0; i < h.ops.size(); ++i) {
+    const WOp& op = h.ops[i];
+    ApplyOp<TW> a{};
+    a.R = static_cast<const TW*>(op.R);
+    a.V = static_cast<const TW*>(op.V);
+    a.tau = static_cast<const TW*>(op.tau);
+    a.kdev = op.kdev;
+    a.slots = P.d_idx + soff[i];
+    a.nslots = P.d_idx + noff[i];
+    a.c = op.c;
+    a.w = op.kind == 0 ? op.w : 0;
+    ops.push_back(a);
+  }
+  SPAQR_CUDA(cudaMalloc(&P.d_ops, std::max<size_t>(ops.size(), 1) * sizeof(ApplyOp<TW>)));
+  SPAQR_CUDA(cudaMemcpy(P.d_ops, ops.data(), ops.size() * sizeof(ApplyOp<TW>), cudaMemcpyHostToDevice));
+  // segments: consecutive ops with equal (kind, stage, round for R_s)
+  size_t i = 0;
+  while (i < h.ops.size()) {
+    size_t j = i + 1;
+    const WOp& a = h.ops[i];
+    int maxc = a.c;
+    while (j < h.ops.size() && h.ops[j].kind == a.kind && h.ops[j].stage == a.stage &&
+           (a.kind != 0 || h.ops[j].round == a.round)) {
+      maxc = std::max(maxc, h.ops[j].c);
+      ++j;
+    }
+    Segment s;
+    s.kind = a.kind;
+    s.count = (int)(j - i);
+    s.first = i;
+    s.smem = (int)((size_t)maxc * (kW + 1) * sizeof(double));
+    P.segs.push_back(s);
+    i = j;
+  }
+}
+
+void build_apply_plan(Handle& h) {
+  free_apply_plan(h);
+  h.plan = new ApplyPlan();
+  h.plan->fp32 = h.precision == SPAQR_PREC_MIXED;
+  if (h.plan->fp32)
+    build_plan_t<float>(h, *h.plan);
+  else
+    build_plan_t<double>(h, *h.plan);
+  int mx = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  mx -= 1024;  // margin for the kernels' static shared memory
+  for (auto& s : h.plan->segs)
+    if (s.smem > mx) throw Error(SPAQR_ERR_CAPACITY, "apply: cluster too large for shared memory");
+  cudaFuncSetAttribute(r_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(r_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(r_invT_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(r_invT_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(q_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(q_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  const int64_t big = std::max(h.m, h.n);
+  h.plan->part_n = blocks(big);
+  SPAQR_CUDA(cudaMalloc(&h.plan->d_scal, 8 * sizeof(double)));
+  SPAQR_CUDA(cudaMalloc(&h.plan->d_part, (size_t)h.plan->part_n * sizeof(double)));
+}
+
+void free_apply_plan(Handle& h) {
+  if (!h.plan) return;
+  if (h.plan->graph) cudaGraphExecDestroy(h.plan->graph);
+  cudaFree(h.plan->d_ops);
+  cudaFree(h.plan->d_idx);
+  cudaFree(h.plan->d_scal);
+  cudaFree(h.plan->d_part);
+  delete h.plan;
+  h.plan = nullptr;
+}
+
+template <typename TW>
+static void apply_t(Handle& h, double* z, int transpose) {
+  ApplyPlan& P = *h.plan;
+  const ApplyOp<TW>* ops = static_cast<const ApplyOp<TW>*>(P.d_ops);
+  const int nseg = (int)P.segs.size();
+  for (int t = 0; t < nseg; ++t) {
+    const Segment& s = P.segs[(size_t)(transpose ? t : nseg - 1 - t)];
+    const ApplyOp<TW>* o = ops + s.first;
+    if (s.kind == 2)
+      q_kernel<TW><<<s.count, kT, (size_t)s.smem, h.st>>>(o, z, transpose);
+    else if (transpose)
+      r_invT_kernel<TW><<<s.count, kT, (size_t)s.smem, h.st>>>(o, z);
+    else
+      r_inv_kernel<TW><<<s.count, kT, (size_t)s.smem, h.st>>>(o, z);
+  }
+  SPAQR_CUDA(cudaGetLastError());
+}
+
+void apply_Winv(Handle& h, double* z, int transpose) {
+  if (!h.plan) throw Error(SPAQR_ERR_INVALID_ARG, "no factorization");
+  if (h.plan->fp32)
+    apply_t<float>(h, z, transpose);
+  else
+    apply_t<double>(h, z, transpose);
+}
+
+void apply_A(Handle& h, const double* x, double* y, int forward) {
+  ApplyPlan& P = *h.plan;
+  if (forward)
+    spmv_kernel<<<blocks(h.m), kT, 0, h.st>>>(h.m, h.d_rowptr, h.d_colidx, h.d_vals, x, y, nullptr, P.d_part);
+  else
+    spmv_kernel<<<blocks(h.n), kT, 0, h.st>>>(h.n, h.d_trowptr, h.d_tcolidx, h.d_tvals, x, y, nullptr, P.d_part);
+  SPAQR_CUDA(cudaGetLastError());
+}
+
+// One CGLS iteration (everything on the stream, no host wait).
+static void cgls_body(Handle& h, double* x, double* r, double* p, double* t, double* q, double* u, double* s,
+                      const double* Dv) {
+  ApplyPlan& P = *h.plan;
+  const int64_t m = h.m, n = h.n;
+  SPAQR_CUDA(cudaMemcpyAsync(t, p, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
+  apply_Winv(h, t, 0);
+  spmv_kernel<<<blocks(m), kT, 0, h.st>>>(m, h.d_rowptr, h.d_colidx, h.d_vals, t, q, nullptr, P.d_part);
+  finish_sum_kernel<<<1, kT, 0, h.st>>>(blocks(m), P.d_part, P.d_scal + 1);
+  update_xr_kernel<<<blocks(std::max(m, n)), kT, 0, h.st>>>(n, m, x, t, r, q, P.d_scal);
+  spmv_kernel<<<blocks(n), kT, 0, h.st>>>(n, h.d_trowptr, h.d_tcolidx, h.d_tvals, r, u, Dv, P.d_part);
+  finish_sum_kernel<<<1, kT, 0, h.st>>>(blocks(n), P.d_part, P.d_scal + 2);
+  SPAQR_CUDA(cudaMemcpyAsync(s, u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
+  apply_Winv(h, s, 1);
+  sumsq_kernel<<<std::min(blocks(n), P.part_n), kT, 0, h.st>>>(n, s, P.d_part);
+  finish_sum_kernel<<<1, kT, 0, h.st>>>(std::min(blocks(n), P.part_n), P.d_part, P.d_scal + 3);
+  beta_kernel<<<1, 1, 0, h.st>>>(P.d_scal);
+  update_p_kernel<<<blocks(n), kT, 0, h.st>>>(n, p, s, P.d_scal);
+  SPAQR_CUDA(cudaGetLastError());
+}
+
+void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info) {
+  auto t0 = std::chrono::steady_clock::now();
+  ApplyPlan& P = *h.plan;
+  const int64_t m = h.m, n = h.n;
+  const size_t need = (size_t)3 * m + (size_t)5 * n;
+  if (h.work_elems < need) {
+    if (h.d_work) cudaFree(h.d_work);
+    SPAQR_CUDA(cudaMalloc(&h.d_work, need * sizeof(double)));
+    h.work_elems = need;
+    if (P.graph) {
+      cudaGraphExecDestroy(P.graph);
+      P.graph = nullptr;
+    }
+  }
+  double* r = h.d_work;
+  double* q = r + m;
+  double* xt = q + m;
+  double* p = xt + n;
+  double* t = p + n;
+  double* u = t + n;
+  double* s = u + n;
+  (void)s;
+  double* sv = s;
+  const double* Dinv_w = h.d_D;  // |D^{-1} u| = |u / D|
+  SPAQR_CUDA(cudaMemsetAsync(xt, 0, (size_t)n * sizeof(double), h.st));
+  SPAQR_CUDA(cudaMemcpyAsync(r, b_dev, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
+  spmv_kernel<<<blocks(n), kT, 0, h.st>>>(n, h.d_trowptr, h.d_tcolidx, h.d_tvals, r, u, Dinv_w, P.d_part);
+  finish_sum_kernel<<<1, kT, 0, h.st>>>(blocks(n), P.d_part, P.d_scal + 2);
+  SPAQR_CUDA(cudaMemcpyAsync(sv, u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
+  apply_Winv(h, sv, 1);
+  SPAQR_CUDA(cudaMemcpyAsync(p, sv, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
+  sumsq_kernel<<<std::min(blocks(n), P.part_n), kT, 0, h.st>>>(n, sv, P.d_part);
+  finish_sum_kernel<<<1, kT, 0, h.st>>>(std::min(blocks(n), P.part_n), P.d_part, P.d_scal + 0);
+  double res0 = 0.0;
+  SPAQR_CUDA(cudaMemcpyAsync(&res0, P.d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost, h.st));
+  SPAQR_CUDA(cudaStreamSynchronize(h.st));
+  const double norm0 = std::sqrt(res0);
+  int it = 0;
+  double rel = norm0 > 0.0 ? 1.0 : 0.0;
+  if (norm0 > 0.0) {
+    const bool graphs = h.opt.use_graphs != 0;
+    if (graphs && !P.graph) {
+      cudaGraph_t g;
+      SPAQR_CUDA(cudaStreamBeginCapture(h.st, cudaStreamCaptureModeThreadLocal));
+      cgls_body(h, xt, r, p, t, q, u, sv, Dinv_w);
+      SPAQR_CUDA(cudaStreamEndCapture(h.st, &g));
+      SPAQR_CUDA(cudaGraphInstantiate(&P.graph, g, 0));
+      cudaGraphDestroy(g);
+    }
+    for (it = 1; it <= h.opt.maxit; ++it) {
+      if (graphs)
+        SPAQR_CUDA(cudaGraphLaunch(P.graph, h.st));
+      else
+        cgls_body(h, xt, r, p, t, q, u, sv, Dinv_w);
+      double res = 0.0;
+      SPAQR_CUDA(cudaMemcpyAsync(&res, P.d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost, h.st));
+      SPAQR_CUDA(cudaStreamSynchronize(h.st));
+      rel = std::sqrt(res) / norm0;
+      if (!(rel >= h.opt.tol)) break;
+    }
+    if (it > h.opt.maxit) it = h.opt.maxit;
+  }
+  scale_kernel<<<blocks(n), kT, 0, h.st>>>(n, xt, h.d_D, x_dev);
+  SPAQR_CUDA(cudaGetLastError());
+  SPAQR_CUDA(cudaStreamSynchronize(h.st));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  h.stats.t_solve = secs;
+  h.stats.iters = it;
+  if (info) {
+    info->iters = it;
+    info->rel_resid = rel;
+    info->converged = rel < h.opt.tol;
+    info->seconds = secs;
+  }
+}
+
+}  // namespace spaqr

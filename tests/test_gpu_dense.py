@@ -1,0 +1,114 @@
+"""GPU parity of the batched dense kernels (through the C ABI) against the oracle.
+
+Front QR (Section 2.3): the oracle's textbook Householder QR of the same
+front, then its sign fix; both take the same reflector convention, so the
+whole transformed front must agree (rows below c are the rows returned to the
+owners or reassigned, so they matter too).  Column-pivoted QR (Section 2.5 /
+Section 4 rank rule): ranks and leading rows of Q^T A against the oracle.
+Batches are uneven and include empty, 1x1, wide, tall and large fronts (the
+last ones take the blocked multi-CTA path).
+"""
+import numpy as np
+import pytest
+
+from oracle import dense as dn
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+def _oracle_front(A, c):
+    F = A.copy()
+    dn.householder_qr(F, c)
+    dn.sign_fix_rows(F, c)
+    return F
+
+
+def _rel(a, b):
+    den = max(np.linalg.norm(b), 1e-300)
+    return np.linalg.norm(a - b) / den
+
+
+def test_front_qr_uneven_batch():
+    import paper_2102_09878_gb300 as sq
+
+    rng = np.random.default_rng(0)
+    shapes = [(1, 1, 1), (5, 3, 3), (40, 25, 10), (64, 64, 32), (70, 40, 20), (33, 90, 7), (200, 150, 31),
+              (128, 17, 17), (3, 9, 2), (250, 300, 64), (8, 5, 0)]
+    mats = [rng.standard_normal((m, n)) for (m, n, _) in shapes]
+    cs = [c for (_, _, c) in shapes]
+    out = sq.dense_front_qr(mats, cs)
+    for A, c, F in zip(mats, cs, out):
+        ref = _oracle_front(A, c) if c else A
+        assert _rel(F, ref) < TOL, (A.shape, c, _rel(F, ref))
+
+
+def test_front_qr_large_blocked_path():
+    import paper_2102_09878_gb300 as sq
+
+    rng = np.random.default_rng(1)
+    shapes = [(1200, 400, 70), (3000, 200, 33), (900, 900, 130), (2500, 64, 64)]
+    mats = [rng.standard_normal((m, n)) for (m, n, _) in shapes]
+    cs = [c for (_, _, c) in shapes]
+    out = sq.dense_front_qr(mats, cs)
+    for A, c, F in zip(mats, cs, out):
+        ref = _oracle_front(A, c)
+        assert _rel(F, ref) < TOL, (A.shape, c, _rel(F, ref))
+        assert np.all(np.diag(F[:c, :c]) >= 0)
+        assert np.all(np.tril(F[:, :c], -1) == 0)
+
+
+def test_front_qr_zero_column_and_rank_one():
+    import paper_2102_09878_gb300 as sq
+
+    A = np.zeros((6, 4))
+    A[:, 1] = np.arange(1, 7)
+    B = np.outer(np.arange(1.0, 9.0), np.ones(5))
+    out = sq.dense_front_qr([A, B], [2, 3])
+    for M, c, F in zip([A, B], [2, 3], out):
+        ref = _oracle_front(M, c)
+        np.testing.assert_allclose(F, ref, atol=1e-12 * max(1.0, np.abs(M).max()))
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-3, 1e-8])
+def test_qrcp_batch_matches_oracle(eps):
+    import paper_2102_09878_gb300 as sq
+
+    rng = np.random.default_rng(2)
+    mats = []
+    for (m, n, r) in [(12, 30, 12), (40, 25, 25), (20, 20, 8), (7, 100, 7), (60, 9, 9), (1, 1, 1), (30, 30, 4),
+                      (150, 400, 60)]:
+        U = rng.standard_normal((m, r))
+        Vt = rng.standard_normal((r, n))
+        s = np.logspace(0, -10, r)
+        mats.append((U * s) @ Vt)
+    mats.append(np.zeros((5, 6)))
+    ranks, rows, V, T = sq.dense_qrcp(mats, eps)
+    for i, A in enumerate(mats):
+        k, Xf, perm, Vo, To = dn.qrcp(A, eps)
+        assert ranks[i] == k, (i, ranks[i], k)
+        if k < A.shape[0]:
+            ref = np.zeros((k, A.shape[1]))
+            ref[:, perm] = Xf[:k]
+            assert _rel(rows[i], ref) < 1e-10, (i, _rel(rows[i], ref))
+        # reflectors of pivots far above the noise are well determined
+        good = np.abs(np.diag(Xf[:k, :k])) > 1e-6 * abs(Xf[0, 0]) if k else []
+        if k and good.any():
+            j = int(np.argmin(good)) if not good.all() else k
+            assert _rel(V[i][:, :j], Vo[:, :j]) < 1e-10 and _rel(T[i][:j], To[:j]) < 1e-10, i
+
+
+def test_qrcp_large_matrix_global_path():
+    import paper_2102_09878_gb300 as sq
+
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((160, 900)) * np.logspace(0, -6, 900)
+    ranks, rows, V, T = sq.dense_qrcp([A], 1e-4)
+    k, Xf, perm, Vo, To = dn.qrcp(A, 1e-4)
+    assert ranks[0] == k
+    ref = np.zeros((k, A.shape[1]))
+    ref[:, perm] = Xf[:k]
+    if k < A.shape[0]:
+        assert _rel(rows[0], ref) < 1e-10
+    assert _rel(V[0], Vo) < 1e-10
