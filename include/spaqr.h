@@ -74,10 +74,17 @@ typedef struct {
   int use_graphs;  /* capture the per-iteration apply + SpMV sequence in a CUDA graph */
   int verbose;     /* print per-stage statistics to stderr */
   void* stream;    /* cudaStream_t for all device work (NULL = default stream) */
+  int row_rule;    /* candidates of the max-norm row rule (Section 2.2): SPAQR_ROWS_TREE (default) =
+                      the touched clusters of the deepest nested-dissection node, which keeps every
+                      row on one root-to-leaf chain (disjoint subtrees stay disjoint, Section 2.5.2);
+                      SPAQR_ROWS_ANY = every touched cluster */
 } spaqr_options;
 
+#define SPAQR_ROWS_TREE 0
+#define SPAQR_ROWS_ANY 1
+
 /* Fill *opt with the defaults: eps 1e-4, skip 2, FP64, spaqr mode, tol 1e-10,
- * maxit 500, graphs on, quiet, default stream. */
+ * maxit 500, graphs on, quiet, default stream, tree row rule. */
 void spaqr_default_options(spaqr_options* opt);
 
 /* ---------------------------------------------------------------- analysis
@@ -150,7 +157,8 @@ typedef struct {
   int64_t top_cols, top_rows; /* size of the root front (Section 4.3 top separator) */
   double flops_front;  /* algorithmic flops of the front QRs (Golub-Van Loan counts) */
   double flops_sparsify;
-  double t_phase[6];   /* eliminate, reassign, scale, step1, step2, merge (device + host) */
+  double t_phase[6];   /* wall seconds: eliminate (incl. row reassignment), prep (column scaling, row
+                          owners, initial blocks), scale, step1, step2, merge */
   int64_t launches;    /* kernels launched by the factorization */
   int64_t syncs;       /* device-to-host waits during the factorization */
   /* device time (CUDA events on the library stream) summed per kernel family:

@@ -8,7 +8,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   Householder QR of a front (Section 2.3) and of A_pp in the interface
   scaling (Section 2.4).  ``sign_fix_rows`` then makes diag(R) >= 0.
 * ``qrcp``: column-pivoted Householder QR (pivot = largest remaining column
-  norm, ties to the lowest index) stopped at the numerical rank: r is the
+  norm, ties to the lowest original column index) stopped at the numerical rank: r is the
   largest prefix with |R_ii| >= eps |R_11| and R_ii != 0 (Section 4, the
   paper's use of a column-pivoted QR with that stopping rule).  Column norms
   are downdated after every step and recomputed exactly when the downdated
@@ -83,7 +83,9 @@ def qrcp(X: np.ndarray, eps: float):
     r11 = 0.0
     k = 0
     for i in range(kmax):
-        j = i + int(np.argmax(nu[i:]))
+        sub = nu[i:]
+        cand = np.flatnonzero(sub == sub.max()) + i
+        j = int(cand[np.argmin(perm[cand])])  # ties to the lowest original column index
         if j != i:
             X[:, [i, j]] = X[:, [j, i]]
             nu[[i, j]] = nu[[j, i]]

@@ -12,9 +12,13 @@ these open):
 R1  Column scaling (Section 2.7): D = diag(1 / ||A[:, j]||_2), A~ = A D.  The
     row heuristics run on A~ (Section 2.7 scales before it reorders rows).
 R2  Rows (Section 2.2): the vertex row of v is matched to column v; every
-    other row goes to argmax_c sum_{j in c} A~[r, j]^2 over the clusters it
-    touches; ties go to the deeper cluster (eliminated first), then to the
-    lower cluster id.  Initial groups: rows sorted by (owner, support, row id).
+    other row goes to argmax_c sum_{j in c} A~[r, j]^2, the candidates being
+    the clusters it touches that belong to the deepest nested-dissection node
+    among them (rows="tree", the default; rows="maxnorm" takes every touched
+    cluster); ties go to the deeper cluster, then to the lower cluster id.
+    The restriction keeps every row's support on one root-to-leaf chain of the
+    tree, which is what Section 2.5.2's statement that disjoint subtrees stay
+    disjoint requires.  Initial groups: rows sorted by (owner, support, row id).
 R3  Group order: groups are numbered in creation order; a front stacks the
     eliminated cluster's own groups (by number) and then the other owners'
     groups touching it (by owner id, then number).  Front columns: s first,
@@ -22,8 +26,8 @@ R3  Group order: groups are numbered in creation order; a front stacks the
 R4  Elimination (Section 2.3): after the Householder QR of the s columns the
     first c_s rows are R_s = [R_ss R_sn] (diag >= 0); the rows at positions
     r_s.. return to their owners (one new group per owner, in owner order);
-    positions c_s..r_s-1 are the extra rows, each sent by the max-norm rule
-    to a cluster it touches (one new group per destination).  At the root
+    positions c_s..r_s-1 are the extra rows, each sent by the R2 rule to a
+    cluster it touches (one new group per destination).  At the root
     they are dropped (all zero).
 R5  Same-level eliminations run in rounds: each round takes, in ascending
     separator id, every separator whose front shares no row group with a
@@ -102,7 +106,8 @@ def column_scaling(A: sp.csr_matrix):
 
 
 class OracleSpaQR:
-    def __init__(self, prob, depth: int, eps: float, skip: int = 2, mode: str = "spaqr"):
+    def __init__(self, prob, depth: int, eps: float, skip: int = 2, mode: str = "spaqr", rows: str = "tree"):
+        self.rows_rule = rows
         self.prob = prob
         self.L = depth
         self.eps = eps
@@ -122,6 +127,9 @@ class OracleSpaQR:
     def _argmax_cluster(self, scores):
         """R2/R4 max-norm rule with the deeper-then-lower-id tie break."""
         best = None
+        if self.rows_rule == "tree":
+            deep = max(self.level[c] for c, _ in scores)
+            scores = [(c, sc) for c, sc in scores if self.level[c] == deep]
         for cid, sc in scores:
             key = (sc, self.level[cid], -cid)
             if best is None or key > best[0]:

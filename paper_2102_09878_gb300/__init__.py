@@ -72,7 +72,7 @@ class SpaQR:
 
     def __init__(self, A, analysis: Analysis, eps: float = 1e-4, skip: int = 2, precision: str = "fp64",
                  mode: str = "spaqr", tol: float = 1e-10, maxit: int = 500, use_graphs: bool = True,
-                 verbose: bool = False, stream=None):
+                 verbose: bool = False, stream=None, rows: str = "tree"):
         lib = capi.load()
         self.m, self.n = int(A.m), int(A.n)
         self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int64)
@@ -90,6 +90,7 @@ class SpaQR:
         o.use_graphs = 1 if use_graphs else 0
         o.verbose = 1 if verbose else 0
         o.stream = _stream_ptr(stream)
+        o.row_rule = capi.ROWS[rows]
         self.precision = precision
         self.options = o
         h = C.c_void_p()
@@ -137,7 +138,7 @@ class SpaQR:
         st = capi.Stats()
         capi.check(capi.load().spaqr_get_stats(self._h, C.byref(st)))
         out = {f: getattr(st, f) for f, _ in capi.Stats._fields_ if f not in ("t_phase", "t_kernel", "n_kernel")}
-        out["t_phase"] = dict(zip(["eliminate", "reassign", "scale", "step1", "step2", "merge"], list(st.t_phase)))
+        out["t_phase"] = dict(zip(["eliminate", "prep", "scale", "step1", "step2", "merge"], list(st.t_phase)))
         fam = ["copy", "front_qr", "qrcp", "other", "apply", "spmv"]
         out["t_kernel"] = dict(zip(fam, list(st.t_kernel)))
         out["n_kernel"] = dict(zip(fam, list(st.n_kernel)))

@@ -27,6 +27,7 @@ ERRORS = {
 }
 PREC = {"fp64": 0, "mixed": 1}
 MODE = {"spaqr": 0, "direct": 1}
+ROWS = {"tree": 0, "maxnorm": 1}
 
 
 class SpaqrError(RuntimeError):
@@ -62,6 +63,7 @@ class Options(C.Structure):
         ("use_graphs", C.c_int),
         ("verbose", C.c_int),
         ("stream", C.c_void_p),
+        ("row_rule", C.c_int),
     ]
 
 

@@ -89,6 +89,7 @@ void spaqr_default_options(spaqr_options* o) {
   o->use_graphs = 1;
   o->verbose = 0;
   o->stream = nullptr;
+  o->row_rule = SPAQR_ROWS_TREE;
 }
 
 const char* spaqr_last_error(void) { return g_last_error.c_str(); }
@@ -147,6 +148,8 @@ int spaqr_factor(const spaqr_csr* A, const spaqr_analysis* an, const spaqr_optio
     else
       spaqr_default_options(&h.opt);
     if (h.opt.skip < 0) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "skip must be >= 0");
+    if (h.opt.row_rule != SPAQR_ROWS_TREE && h.opt.row_rule != SPAQR_ROWS_ANY)
+      throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "unknown row rule");
     if (!(h.opt.eps >= 0.0)) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "eps must be >= 0");
     // all library work runs on a non-blocking stream of its own unless the
     // caller gives one (the legacy default stream cannot be graph-captured)
@@ -329,50 +332,35 @@ int spaqr_dense_front_qr(int count, double* const* A, const int* m, const int* n
   return guarded([&] {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int lim = spaqr::max_smem_optin();
-    std::vector<spaqr::FrontDesc<double>> small, big;
-    int need = 0, maxc = 0, maxtiles = 0;
+    std::vector<int> ms, ns, cs;
     for (int i = 0; i < count; ++i) {
       if (c[i] < 0 || c[i] > m[i] || n[i] < c[i] || ld[i] < std::max(1, m[i]))
         throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "front " + std::to_string(i) + ": bad shape");
-      spaqr::FrontDesc<double> f{A[i], m[i], n[i], c[i], ld[i]};
-      if (c[i] == 0 || m[i] == 0) continue;
-      const int b = spaqr::front_smem_bytes(m[i], n[i], c[i], 8);
-      if ((int64_t)m[i] * n[i] * 8 + 64 > lim) {
-        big.push_back(f);
-        maxc = std::max(maxc, c[i]);
-      } else {
-        small.push_back(f);
-        need = std::max(need, b);
-      }
+      ms.push_back(m[i]);
+      ns.push_back(n[i]);
+      cs.push_back(c[i]);
     }
-    spaqr::FrontDesc<double>* d = nullptr;
-    const size_t tot = small.size() + big.size();
+    const auto groups = spaqr::plan_fronts(ms, ns, cs, 8, lim);
+    std::vector<std::vector<spaqr::FrontDesc<double>>> host(groups.size());
+    std::vector<const spaqr::FrontDesc<double>*> dev(groups.size());
+    std::vector<void*> frees;
     double* Tbuf = nullptr;
-    SPAQR_CUDA(cudaMalloc(&d, std::max<size_t>(tot, 1) * sizeof(spaqr::FrontDesc<double>)));
-    if (!small.empty()) {
-      SPAQR_CUDA(cudaMemcpyAsync(d, small.data(), small.size() * sizeof(small[0]), cudaMemcpyHostToDevice, st));
-      SPAQR_CUDA(spaqr::launch_front_qr_smem<double>(d, (int)small.size(), need, st));
-    }
-    if (!big.empty()) {
-      auto* db = d + small.size();
-      SPAQR_CUDA(cudaMemcpyAsync(db, big.data(), big.size() * sizeof(big[0]), cudaMemcpyHostToDevice, st));
-      SPAQR_CUDA(cudaMalloc(&Tbuf, big.size() * 32 * 32 * sizeof(double)));
-      for (int j0 = 0; j0 < maxc; j0 += 32) {
-        maxtiles = 0;
-        for (auto& f : big) {
-          const int steps = std::min(f.c, f.m);
-          if (j0 >= steps) continue;
-          const int b = std::min(32, steps - j0);
-          maxtiles = std::max(maxtiles, (f.n - (j0 + b) + 31) / 32);
-        }
-        SPAQR_CUDA(spaqr::launch_front_panel<double>(db, (int)big.size(), j0, 32, Tbuf, st));
-        SPAQR_CUDA(spaqr::launch_front_trailing<double>(db, (int)big.size(), j0, 32, Tbuf, maxtiles, st));
+    for (size_t g = 0; g < groups.size(); ++g) {
+      for (int i : groups[g].idx) host[g].push_back(spaqr::FrontDesc<double>{A[i], m[i], n[i], c[i], ld[i]});
+      spaqr::FrontDesc<double>* d = nullptr;
+      SPAQR_CUDA(cudaMalloc(&d, host[g].size() * sizeof(host[g][0])));
+      frees.push_back(d);
+      SPAQR_CUDA(cudaMemcpyAsync(d, host[g].data(), host[g].size() * sizeof(host[g][0]), cudaMemcpyHostToDevice, st));
+      dev[g] = d;
+      if (groups[g].kind == 2) {
+        SPAQR_CUDA(cudaMalloc(&Tbuf, host[g].size() * 32 * 32 * sizeof(double)));
+        frees.push_back(Tbuf);
       }
-      SPAQR_CUDA(spaqr::launch_front_finish<double>(db, (int)big.size(), maxc, st));
     }
+    int64_t launches = 0;
+    SPAQR_CUDA(spaqr::launch_front_groups<double>(groups, dev, host, Tbuf, st, &launches));
     SPAQR_CUDA(cudaStreamSynchronize(st));
-    cudaFree(d);
-    cudaFree(Tbuf);
+    for (void* p : frees) cudaFree(p);
     return SPAQR_OK;
   });
 }
@@ -384,41 +372,37 @@ int spaqr_dense_qrcp(int count, double* const* A, const int* m, const int* n, co
   return guarded([&] {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int lim = spaqr::max_smem_optin();
-    std::vector<spaqr::QrcpDesc<double>> small, large;
-    std::vector<int> si, li;
+    std::vector<spaqr::QrcpDesc<double>> qs;
+    std::vector<int> ms, ns;
     std::vector<double*> work;
-    int need_s = 0, need_l = 0;
     int* d_rank = nullptr;
     SPAQR_CUDA(cudaMalloc(&d_rank, std::max(count, 1) * sizeof(int)));
     for (int i = 0; i < count; ++i) {
       if (m[i] < 0 || n[i] < 0 || ld[i] < std::max(1, m[i])) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "bad shape");
-      spaqr::QrcpDesc<double> q{A[i], nullptr, A[i], V ? V[i] : nullptr, taus ? taus[i] : nullptr, d_rank + i,
-                                m[i], n[i], ld[i], ld[i]};
-      const int whole = spaqr::qrcp_smem_bytes(m[i], n[i], 8, true);
-      if (whole <= lim) {
-        small.push_back(q);
-        need_s = std::max(need_s, whole);
-      } else {
-        const int part = spaqr::qrcp_smem_bytes(m[i], n[i], 8, false);
-        if (part > lim) throw spaqr::Error(SPAQR_ERR_CAPACITY, "too many columns");
+      qs.push_back(spaqr::QrcpDesc<double>{A[i], nullptr, A[i], V ? V[i] : nullptr, taus ? taus[i] : nullptr,
+                                           d_rank + i, m[i], n[i], ld[i], ld[i]});
+      ms.push_back(m[i]);
+      ns.push_back(n[i]);
+    }
+    std::vector<spaqr::QrcpGroup> groups;
+    std::vector<char> need_work;
+    if (!spaqr::plan_qrcp(ms, ns, 8, lim, groups, need_work)) throw spaqr::Error(SPAQR_ERR_CAPACITY, "too many columns");
+    for (int i = 0; i < count; ++i)
+      if (need_work[(size_t)i]) {
         double* w = nullptr;
-        SPAQR_CUDA(cudaMalloc(&w, (size_t)m[i] * n[i] * sizeof(double)));
+        SPAQR_CUDA(cudaMalloc(&w, (size_t)std::max(1, m[i]) * std::max(1, n[i]) * sizeof(double)));
         work.push_back(w);
-        q.work = w;
-        large.push_back(q);
-        need_l = std::max(need_l, part);
+        qs[(size_t)i].work = w;
       }
-    }
     spaqr::QrcpDesc<double>* d = nullptr;
-    SPAQR_CUDA(cudaMalloc(&d, std::max<size_t>(small.size() + large.size(), 1) * sizeof(spaqr::QrcpDesc<double>)));
-    if (!small.empty()) {
-      SPAQR_CUDA(cudaMemcpyAsync(d, small.data(), small.size() * sizeof(small[0]), cudaMemcpyHostToDevice, st));
-      SPAQR_CUDA(spaqr::launch_qrcp<double>(d, (int)small.size(), eps, need_s, st));
-    }
-    if (!large.empty()) {
-      auto* dl = d + small.size();
-      SPAQR_CUDA(cudaMemcpyAsync(dl, large.data(), large.size() * sizeof(large[0]), cudaMemcpyHostToDevice, st));
-      SPAQR_CUDA(spaqr::launch_qrcp<double>(dl, (int)large.size(), eps, -need_l, st));
+    SPAQR_CUDA(cudaMalloc(&d, std::max<size_t>(qs.size(), 1) * sizeof(spaqr::QrcpDesc<double>)));
+    size_t off = 0;
+    for (auto& g : groups) {
+      std::vector<spaqr::QrcpDesc<double>> part;
+      for (int i : g.idx) part.push_back(qs[(size_t)i]);
+      SPAQR_CUDA(cudaMemcpyAsync(d + off, part.data(), part.size() * sizeof(part[0]), cudaMemcpyHostToDevice, st));
+      SPAQR_CUDA(spaqr::launch_qrcp<double>(d + off, (int)part.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st));
+      off += part.size();
     }
     SPAQR_CUDA(cudaMemcpyAsync(rank, d_rank, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st));
     SPAQR_CUDA(cudaStreamSynchronize(st));

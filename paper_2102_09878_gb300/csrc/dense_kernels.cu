@@ -10,10 +10,15 @@
 //    kept in FP64), stop at |R_ii| < eps |R_11|.
 //  * reflector application, triangular solve X R^{-1}, batched block copies
 //    and the max-norm row assignment (Section 2.2).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <climits>
 #include <cstdint>
+#include <vector>
+
+namespace cg = cooperative_groups;
 
 #include "kernels.h"
 
@@ -168,6 +173,75 @@ __global__ void __launch_bounds__(kThreads) front_qr_smem_kernel(const FrontDesc
     if (r < steps && ((negmask[r >> 5] >> (r & 31)) & 1u)) v = -v;
     d.ptr[r + (int64_t)cc * d.ld] = v;
   }
+}
+
+// ----------------------------------------------- front QR, one warp each
+// For small fronts: every warp of the CTA factors its own front in its own
+// shared-memory region (ld = m | 1, odd, so that lane-per-column accesses are
+// conflict-free).  Reflector norms by warp shuffles; trailing updates one lane
+// per column; only __syncwarp, no block barriers.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) front_qr_warp_kernel(const FrontDesc<T>* descs, int count,
+                                                                 int per_warp_elems) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.x * kWarps + warp;
+  if (f >= count) return;
+  const FrontDesc<T> d = descs[f];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* S = reinterpret_cast<T*>(smraw) + (size_t)warp * per_warp_elems;
+  const int m = d.m, n = d.n, c = d.c;
+  const int ld = m | 1;
+  for (int cc = 0; cc < n; ++cc)
+    for (int r = lane; r < m; r += 32) S[r + cc * ld] = d.ptr[r + (int64_t)cc * d.ld];
+  __syncwarp();
+  const int steps = c < m ? c : m;
+  unsigned neg = 0u;  // sign bits of R_ii, bit j of lane (j & 31) for j >> 5 == word... kept per 32-block
+  unsigned negs[4] = {0u, 0u, 0u, 0u};  // steps <= 128 for this kernel
+  for (int j = 0; j < steps; ++j) {
+    T* col = S + j * ld;
+    double sig = 0.0;
+    for (int r = j + 1 + lane; r < m; r += 32) {
+      const double v = (double)col[r];
+      sig += v * v;
+    }
+    sig = warp_sum(sig);
+    const double alpha = (double)col[j];
+    double beta, tau;
+    if (sig == 0.0) {
+      beta = alpha;
+      tau = 0.0;
+    } else {
+      const double nrm = sqrt(alpha * alpha + sig);
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      const T den = (T)(alpha - beta);
+      for (int r = j + 1 + lane; r < m; r += 32) col[r] = col[r] / den;
+    }
+    if (beta < 0.0) negs[j >> 5] |= 1u << (j & 31);
+    __syncwarp();
+    if (lane == 0) col[j] = (T)beta;
+    __syncwarp();
+    if (tau != 0.0) {
+      const T tt = (T)tau;
+      for (int cc = j + 1 + lane; cc < n; cc += 32) {
+        T* x = S + cc * ld;
+        T sacc = x[j];
+        for (int r = j + 1; r < m; ++r) sacc += col[r] * x[r];
+        const T w = tt * sacc;
+        x[j] -= w;
+        for (int r = j + 1; r < m; ++r) x[r] -= w * col[r];
+      }
+    }
+    __syncwarp();
+  }
+  (void)neg;
+  for (int cc = 0; cc < n; ++cc)
+    for (int r = lane; r < m; r += 32) {
+      T v = S[r + cc * ld];
+      if (cc < steps && r > cc) v = T(0);
+      if (r < steps && ((negs[r >> 5] >> (r & 31)) & 1u)) v = -v;
+      d.ptr[r + (int64_t)cc * d.ld] = v;
+    }
 }
 
 // ----------------------------------------------------- front QR, blocked
@@ -338,161 +412,368 @@ __global__ void __launch_bounds__(kThreads) front_finish_kernel(const FrontDesc<
 }
 
 // ------------------------------------------------------------------- QRCP
+// Column-pivoted Householder QR stopped at the rank, one thread-block cluster
+// of CS CTAs per matrix.  CTA r of the cluster owns the column slab
+// [r*nl, (r+1)*nl) (nl = ceil(n/CS)), staged in its shared memory (SMEM) or in
+// the work buffer.  Columns never move: at step i every CTA proposes its
+// not-yet-pivoted column of largest squared norm (ties to the lowest original
+// index), the cluster reads all proposals through distributed shared memory,
+// the owner of the pivot builds the reflector, and every CTA copies it from
+// the owner and applies it to its own slab.  Two cluster barriers per step.
 template <typename T, bool SMEM>
-__global__ void __launch_bounds__(kThreads) qrcp_kernel(const QrcpDesc<T>* descs, double eps) {
-  const QrcpDesc<T> d = descs[blockIdx.x];
+__global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T>* descs, double eps, int nl_max,
+                                                                int m_max) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const QrcpDesc<T> d = descs[blockIdx.x / CS];
   const int m = d.m, n = d.n;
+  const int nl = (n + CS - 1) / CS;
+  const int j0 = min(n, rank * nl), j1 = min(n, j0 + nl);
+  const int nloc = j1 - j0;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* nu = reinterpret_cast<double*>(smraw);
-  double* nuref = nu + n;
-  int* perm = reinterpret_cast<int*>(nuref + n);
-  T* taus = reinterpret_cast<T*>(smraw + (((size_t)n * 20 + 15) / 16) * 16);
-  const int kmax = m < n ? m : n;
-  T* X;
-  const int ld = m;
-  if (SMEM) {
-    X = taus + ((kmax + 1) & ~1) + 2;
-  } else {
-    X = d.work;  // m x n, ld m
-  }
-  for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += kThreads) {
-    const int r = (int)(e % m), cc = (int)(e / m);
-    X[e] = d.src[r + (int64_t)cc * d.ld];
-  }
-  __shared__ T s_tau;
+  double* nu = reinterpret_cast<double*>(smraw);   // nl_max
+  double* nuref = nu + nl_max;                      // nl_max
+  int* step_of = reinterpret_cast<int*>(nuref + nl_max);  // nl_max
+  T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 20 + 15) / 16) * 16);  // m_max + 2
+  T* taus = vbuf + ((m_max + 3) & ~1);             // min(m_max, n) + 2
+  T* X = SMEM ? taus + ((m_max + 3) & ~1) : d.work + (size_t)j0 * m;
+  __shared__ double cand_v;
+  __shared__ int cand_j;
   __shared__ double s_beta;
-  __shared__ double s_r11;
-  __shared__ int s_piv;
-  __shared__ int s_stop;
+  __shared__ T s_tau;
+  __shared__ int s_stop, s_piv;
   __shared__ double red_v[kWarps];
   __shared__ int red_i[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  for (int j = warp; j < n; j += kWarps) {
-    double s = 0.0;
-    for (int r = lane; r < m; r += 32) {
-      const double v = (double)X[r + (int64_t)j * ld];
-      s += v * v;
-    }
-    s = warp_sum(s);
-    if (lane == 0) {
-      nu[j] = s;
-      nuref[j] = s;
-      perm[j] = j;
-    }
+  for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    X[e] = d.src[r + (int64_t)(j0 + c) * d.ld];
   }
   __syncthreads();
+  for (int c = warp; c < nloc; c += kWarps) {
+    double sq = 0.0;
+    for (int r = lane; r < m; r += 32) {
+      const double v = (double)X[r + (int64_t)c * m];
+      sq += v * v;
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) {
+      nu[c] = sq;
+      nuref[c] = sq;
+      step_of[c] = -1;
+    }
+  }
+  const int kmax = m < n ? m : n;
+  double r11 = 0.0;
   int k = 0;
   for (int i = 0; i < kmax; ++i) {
-    // pivot: largest nu[j], j >= i, ties to the lowest index
+    // (1) local proposal
+    __syncthreads();
     double bv = -1.0;
-    int bi = n;
-    for (int j = i + threadIdx.x; j < n; j += kThreads) {
-      const double v = nu[j];
-      if (v > bv || (v == bv && j < bi)) {
+    int bj = INT_MAX;
+    for (int c = threadIdx.x; c < nloc; c += kThreads) {
+      if (step_of[c] >= 0) continue;
+      const double v = nu[c];
+      if (v > bv) {  // ascending c: strict > keeps the lowest index on ties
         bv = v;
-        bi = j;
+        bj = j0 + c;
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) {
+      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+      if (ov > bv || (ov == bv && oj < bj)) {
         bv = ov;
-        bi = oi;
+        bj = oj;
       }
     }
     if (lane == 0) {
       red_v[warp] = bv;
-      red_i[warp] = bi;
+      red_i[warp] = bj;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       double v = red_v[0];
-      int p = red_i[0];
+      int j = red_i[0];
       for (int w = 1; w < kWarps; ++w)
-        if (red_v[w] > v || (red_v[w] == v && red_i[w] < p)) {
+        if (red_v[w] > v || (red_v[w] == v && red_i[w] < j)) {
           v = red_v[w];
-          p = red_i[w];
+          j = red_i[w];
         }
-      s_piv = p;
+      cand_v = v;
+      cand_j = j;
+    }
+    cl.sync();  // (A) proposals visible cluster-wide
+    if (threadIdx.x == 0) {
+      double v = -1.0;
+      int j = INT_MAX;
+      for (int q = 0; q < CS; ++q) {
+        const double qv = *cl.map_shared_rank(&cand_v, q);
+        const int qj = *cl.map_shared_rank(&cand_j, q);
+        if (qv > v || (qv == v && qj < j)) {
+          v = qv;
+          j = qj;
+        }
+      }
+      s_piv = j;
     }
     __syncthreads();
     const int p = s_piv;
-    if (p != i) {
-      for (int r = threadIdx.x; r < m; r += kThreads) {
-        const T a = X[r + (int64_t)i * ld];
-        X[r + (int64_t)i * ld] = X[r + (int64_t)p * ld];
-        X[r + (int64_t)p * ld] = a;
+    const int owner = p / nl;
+    if (rank == owner) {
+      // reflector of column p, rows i..m-1 (warp 0), copied into vbuf
+      const int pl = p - j0;
+      if (threadIdx.x < 32) {
+        T* col = X + (int64_t)pl * m;
+        double sig = 0.0;
+        for (int r = i + 1 + lane; r < m; r += 32) {
+          const double v = (double)col[r];
+          sig += v * v;
+        }
+        sig = warp_sum(sig);
+        const double alpha = (double)col[i];
+        double beta, tau;
+        if (sig == 0.0) {
+          beta = alpha;
+          tau = 0.0;
+        } else {
+          const double nrm = sqrt(alpha * alpha + sig);
+          beta = alpha >= 0.0 ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+        }
+        const double ab = fabs(beta);
+        const double r11_here = (i == 0) ? ab : r11;
+        const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
+        if (!stop && sig != 0.0) {
+          const T den = (T)(alpha - beta);
+          for (int r = i + 1 + lane; r < m; r += 32) {
+            const T v = col[r] / den;
+            col[r] = v;
+            vbuf[r - i] = v;
+          }
+        } else {
+          for (int r = i + 1 + lane; r < m; r += 32) vbuf[r - i] = T(0);
+        }
+        __syncwarp();
+        if (lane == 0) {
+          vbuf[0] = T(1);
+          if (!stop) col[i] = (T)beta;
+          s_tau = (T)tau;
+          s_beta = beta;
+          s_stop = stop;
+        }
       }
+    }
+    cl.sync();  // (C) reflector ready in the owner's shared memory
+    if (rank != owner) {
+      for (int r = threadIdx.x; r < m - i; r += kThreads) vbuf[r] = *cl.map_shared_rank(vbuf + r, owner);
       if (threadIdx.x == 0) {
-        double t = nu[i];
-        nu[i] = nu[p];
-        nu[p] = t;
-        t = nuref[i];
-        nuref[i] = nuref[p];
-        nuref[p] = t;
-        const int q = perm[i];
-        perm[i] = perm[p];
-        perm[p] = q;
+        s_tau = *cl.map_shared_rank(&s_tau, owner);
+        s_beta = *cl.map_shared_rank(&s_beta, owner);
+        s_stop = *cl.map_shared_rank(&s_stop, owner);
       }
-      __syncthreads();
-    }
-    make_reflector_warp0(X, ld, m, i, &s_tau, &s_beta);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const double ab = fabs(s_beta);
-      if (i == 0) s_r11 = ab;
-      s_stop = (s_beta == 0.0 || ab < eps * s_r11) ? 1 : 0;
     }
     __syncthreads();
-    if (s_stop) break;  // column i keeps a spent reflector; only rows < k are ever read
+    if (i == 0) r11 = fabs(s_beta);
+    if (s_stop) break;
     const T tau = s_tau;
     if (threadIdx.x == 0) taus[i] = tau;
-    if (tau != T(0)) apply_reflector_cols(X, ld, m, i, tau, i + 1, n);
+    if (rank == owner && threadIdx.x == 0) step_of[p - j0] = i;
     __syncthreads();
-    for (int j = i + 1 + threadIdx.x; j < n; j += kThreads) {
-      const double x = (double)X[i + (int64_t)j * ld];
-      double v = nu[j] - x * x;
-      if (v < kRecompute * nuref[j]) {
+    if (tau != T(0)) {
+      for (int c = warp; c < nloc; c += kWarps) {
+        if (step_of[c] >= 0) continue;
+        T* col = X + (int64_t)c * m;
+        T sacc = T(0);
+        for (int r = i + 1 + lane; r < m; r += 32) sacc += vbuf[r - i] * col[r];
+        sacc = warp_sum(sacc);
+        const T w = tau * (col[i] + sacc);
+        if (lane == 0) col[i] -= w;
+        for (int r = i + 1 + lane; r < m; r += 32) col[r] -= w * vbuf[r - i];
+      }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nloc; c += kThreads) {
+      if (step_of[c] >= 0) continue;
+      const double x = (double)X[i + (int64_t)c * m];
+      double v = nu[c] - x * x;
+      if (v < kRecompute * nuref[c]) {
         v = 0.0;
         for (int r = i + 1; r < m; ++r) {
-          const double y = (double)X[r + (int64_t)j * ld];
+          const double y = (double)X[r + (int64_t)c * m];
           v += y * y;
         }
-        nuref[j] = v;
+        nuref[c] = v;
       }
-      nu[j] = v;
+      nu[c] = v;
     }
     k = i + 1;
-    __syncthreads();
   }
-  if (threadIdx.x == 0) d.rank[0] = k;
+  __syncthreads();
+  if (rank == 0 && threadIdx.x == 0) d.rank[0] = k;
   if (d.V) {
-    for (int64_t e = threadIdx.x; e < (int64_t)m * k; e += kThreads) {
-      const int r = (int)(e % m), i = (int)(e / m);
-      d.V[e] = r < i ? T(0) : (r == i ? T(1) : X[r + (int64_t)i * ld]);
+    for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
+      const int r = (int)(e % m), c = (int)(e / m);
+      const int t = step_of[c];
+      if (t < 0 || t >= k) continue;
+      d.V[r + (int64_t)t * m] = r < t ? T(0) : (r == t ? T(1) : X[r + (int64_t)c * m]);
     }
-    for (int i = threadIdx.x; i < k; i += kThreads) d.tau[i] = taus[i];
+    if (rank == 0)
+      for (int t = threadIdx.x; t < k; t += kThreads) d.tau[t] = taus[t];
   }
-  // the first k rows of Q^T A in the original column order replace rows
-  // 0..k-1 of out, and only when something is dropped (k < m)
+  // the first k rows of Q^T A in the original column order, only when k < m
   if (d.out && k < m) {
-    for (int64_t e = threadIdx.x; e < (int64_t)k * n; e += kThreads) {
-      const int i = (int)(e % k), j = (int)(e / k);
-      d.out[i + (int64_t)perm[j] * d.ldo] = j < i ? T(0) : X[i + (int64_t)j * ld];
+    for (int64_t e = threadIdx.x; e < (int64_t)k * nloc; e += kThreads) {
+      const int r = (int)(e % k), c = (int)(e / k);
+      const int t = step_of[c];
+      d.out[r + (int64_t)(j0 + c) * d.ldo] = (t >= 0 && r > t) ? T(0) : X[r + (int64_t)c * m];
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// ----------------------------------------------------- QRCP, one warp each
+// The same swap-free column-pivoted QR for small matrices: every warp owns one
+// matrix in its shared-memory region (ld = m | 1), lanes own columns for the
+// norms, the pivot search and the reflector application; no block barriers.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) qrcp_warp_kernel(const QrcpDesc<T>* descs, int count, double eps,
+                                                             int per_warp_bytes) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.x * kWarps + warp;
+  if (f >= count) return;
+  const QrcpDesc<T> d = descs[f];
+  const int m = d.m, n = d.n, ld = m | 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char* base = smraw + (size_t)warp * per_warp_bytes;
+  double* nu = reinterpret_cast<double*>(base);
+  double* nuref = nu + n;
+  int* step_of = reinterpret_cast<int*>(nuref + n);
+  T* taus = reinterpret_cast<T*>(base + (((size_t)n * 20 + 15) / 16) * 16);
+  const int kmax = m < n ? m : n;
+  T* X = taus + ((kmax + 3) & ~1);
+  for (int c = 0; c < n; ++c)
+    for (int r = lane; r < m; r += 32) X[r + c * ld] = d.src[r + (int64_t)c * d.ld];
+  __syncwarp();
+  for (int c = lane; c < n; c += 32) {
+    double sq = 0.0;
+    for (int r = 0; r < m; ++r) {
+      const double v = (double)X[r + c * ld];
+      sq += v * v;
+    }
+    nu[c] = sq;
+    nuref[c] = sq;
+    step_of[c] = -1;
+  }
+  __syncwarp();
+  double r11 = 0.0;
+  int k = 0;
+  for (int i = 0; i < kmax; ++i) {
+    double bv = -1.0;
+    int bj = INT_MAX;
+    for (int c = lane; c < n; c += 32) {
+      if (step_of[c] >= 0) continue;
+      if (nu[c] > bv) {
+        bv = nu[c];
+        bj = c;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+      if (ov > bv || (ov == bv && oj < bj)) {
+        bv = ov;
+        bj = oj;
+      }
+    }
+    const int p = bj;
+    T* col = X + p * ld;
+    double sig = 0.0;
+    for (int r = i + 1 + lane; r < m; r += 32) {
+      const double v = (double)col[r];
+      sig += v * v;
+    }
+    sig = warp_sum(sig);
+    const double alpha = (double)col[i];
+    double beta, tau;
+    if (sig == 0.0) {
+      beta = alpha;
+      tau = 0.0;
+    } else {
+      const double nrm = sqrt(alpha * alpha + sig);
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+    }
+    const double ab = fabs(beta);
+    if (i == 0) r11 = ab;
+    if (beta == 0.0 || ab < eps * r11) break;
+    if (sig != 0.0) {
+      const T den = (T)(alpha - beta);
+      for (int r = i + 1 + lane; r < m; r += 32) col[r] = col[r] / den;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      col[i] = (T)beta;
+      taus[i] = (T)tau;
+      step_of[p] = i;
+    }
+    __syncwarp();
+    const T tt = (T)tau;
+    for (int c = lane; c < n; c += 32) {
+      if (step_of[c] >= 0) continue;
+      T* x = X + c * ld;
+      if (tt != T(0)) {
+        T sacc = x[i];
+        for (int r = i + 1; r < m; ++r) sacc += col[r] * x[r];
+        const T w = tt * sacc;
+        x[i] -= w;
+        for (int r = i + 1; r < m; ++r) x[r] -= w * col[r];
+      }
+      const double xv = (double)x[i];
+      double v = nu[c] - xv * xv;
+      if (v < kRecompute * nuref[c]) {
+        v = 0.0;
+        for (int r = i + 1; r < m; ++r) {
+          const double y = (double)x[r];
+          v += y * y;
+        }
+        nuref[c] = v;
+      }
+      nu[c] = v;
+    }
+    __syncwarp();
+    k = i + 1;
+  }
+  __syncwarp();
+  if (lane == 0) d.rank[0] = k;
+  if (d.V) {
+    for (int c = 0; c < n; ++c) {
+      const int t = step_of[c];
+      if (t < 0 || t >= k) continue;
+      for (int r = lane; r < m; r += 32)
+        d.V[r + (int64_t)t * m] = r < t ? T(0) : (r == t ? T(1) : X[r + c * ld]);
+    }
+    for (int t = lane; t < k; t += 32) d.tau[t] = taus[t];
+  }
+  if (d.out && k < m) {
+    for (int c = 0; c < n; ++c) {
+      const int t = step_of[c];
+      for (int r = lane; r < k; r += 32) d.out[r + (int64_t)c * d.ldo] = (t >= 0 && r > t) ? T(0) : X[r + c * ld];
     }
   }
 }
 
 // ------------------------------------------------------ reflector applies
 template <typename T>
-__global__ void __launch_bounds__(kThreads) refl_kernel(const ReflDesc<T>* descs) {
-  const ReflDesc<T> d = descs[blockIdx.y];
+__global__ void __launch_bounds__(kThreads) refl_kernel(const ReflDesc<T>* descs, const int2* items) {
+  const int2 it = items[blockIdx.x];  // (descriptor, first vector)
+  const ReflDesc<T> d = descs[it.x];
   const int k = *d.k;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int vec = blockIdx.x * kWarps + warp;
+  const int vec = it.y + warp;
   if (vec >= d.nvec) return;
   const int len = d.len;
   if (d.mode == 0) {
@@ -526,9 +807,10 @@ __global__ void __launch_bounds__(kThreads) refl_kernel(const ReflDesc<T>* descs
 
 // ---------------------------------------------------------- X <- X R^{-1}
 template <typename T>
-__global__ void __launch_bounds__(kThreads) trsm_kernel(const TrsmDesc<T>* descs) {
-  const TrsmDesc<T> d = descs[blockIdx.y];
-  const int r = blockIdx.x * kThreads + threadIdx.x;
+__global__ void __launch_bounds__(kThreads) trsm_kernel(const TrsmDesc<T>* descs, const int2* items) {
+  const int2 it = items[blockIdx.x];  // (descriptor, first row)
+  const TrsmDesc<T> d = descs[it.x];
+  const int r = it.y + threadIdx.x;
   if (r >= d.rows) return;
   T* x = d.ptr + r;
   for (int j = 0; j < d.c; ++j) {
@@ -541,13 +823,15 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(const TrsmDesc<T>* descs
 
 // ----------------------------------------------------- max-norm row rule
 template <typename T>
-__global__ void __launch_bounds__(kThreads) argmax_kernel(const ArgmaxDesc<T>* descs) {
-  const ArgmaxDesc<T> d = descs[blockIdx.y];
-  const int r = d.r0 + blockIdx.x * kThreads + threadIdx.x;
+__global__ void __launch_bounds__(kThreads) argmax_kernel(const ArgmaxDesc<T>* descs, const int2* items) {
+  const int2 it = items[blockIdx.x];  // (descriptor, first row offset)
+  const ArgmaxDesc<T> d = descs[it.x];
+  const int r = d.r0 + it.y + threadIdx.x;
   if (r >= d.r1) return;
   double best = -1.0;
   int bl = -1, bid = 0x7fffffff, bt = -1;
   for (int t = 0; t < d.ncl; ++t) {
+    if (d.lvl[t] < 0) continue;  // not a candidate
     double s = 0.0;
     for (int c = d.coff[t]; c < d.coff[t + 1]; ++c) {
       const double v = (double)d.F[r + (int64_t)c * d.ld];
@@ -622,6 +906,19 @@ cudaError_t launch_front_qr_smem(const FrontDesc<T>* d, int count, int smem_byte
 }
 
 template <typename T>
+cudaError_t launch_front_qr_warp(const FrontDesc<T>* d, int count, int per_warp_elems, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  static bool init = false;
+  if (!init) {
+    allow_smem(front_qr_warp_kernel<T>);
+    init = true;
+  }
+  const size_t smem = (size_t)per_warp_elems * sizeof(T) * kWarps;
+  front_qr_warp_kernel<T><<<(unsigned)((count + kWarps - 1) / kWarps), kThreads, smem, st>>>(d, count, per_warp_elems);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_front_panel(const FrontDesc<T>* d, int count, int j0, int nb, T* Tbuf, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   front_panel_kernel<T><<<(unsigned)count, kThreads, 0, st>>>(d, j0, nb, Tbuf);
@@ -643,41 +940,67 @@ cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, cud
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int smem_bytes, cudaStream_t st) {
-  if (count <= 0) return cudaSuccess;
+template <typename T, bool SMEM>
+static cudaError_t launch_qrcp_cs(const QrcpDesc<T>* d, int count, double eps, int cs, int nl_max, int m_max,
+                                  int smem, cudaStream_t st) {
   static bool init = false;
   if (!init) {
-    allow_smem(qrcp_kernel<T, true>);
-    allow_smem(qrcp_kernel<T, false>);
+    allow_smem(qrcp_cluster_kernel<T, SMEM>);
+    cudaFuncSetAttribute(qrcp_cluster_kernel<T, SMEM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     init = true;
   }
-  // smem_bytes > 0: matrices in shared memory; < 0: in the work buffers with |smem_bytes| of scratch.
-  if (smem_bytes > 0)
-    qrcp_kernel<T, true><<<(unsigned)count, kThreads, (size_t)smem_bytes, st>>>(d, eps);
-  else
-    qrcp_kernel<T, false><<<(unsigned)count, kThreads, (size_t)(-smem_bytes), st>>>(d, eps);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(count * cs));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel<T, SMEM>, d, eps, nl_max, m_max);
+}
+
+template <typename T>
+cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int nl_max, int m_max, bool smem_slab,
+                        cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  if (cs == 0) {  // one warp per matrix; nl_max = per-warp bytes
+    static bool init = false;
+    if (!init) {
+      allow_smem(qrcp_warp_kernel<T>);
+      init = true;
+    }
+    qrcp_warp_kernel<T><<<(unsigned)((count + kWarps - 1) / kWarps), kThreads, (size_t)nl_max * kWarps, st>>>(
+        d, count, eps, nl_max);
+    return cudaGetLastError();
+  }
+  const int smem = qrcp_smem_bytes(m_max, nl_max, (int)sizeof(T), smem_slab);
+  if (smem_slab) return launch_qrcp_cs<T, true>(d, count, eps, cs, nl_max, m_max, smem, st);
+  return launch_qrcp_cs<T, false>(d, count, eps, cs, nl_max, m_max, smem, st);
+}
+
+template <typename T>
+cudaError_t launch_refl(const ReflDesc<T>* d, const int2* items, int nitems, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  refl_kernel<T><<<(unsigned)nitems, kThreads, 0, st>>>(d, items);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_refl(const ReflDesc<T>* d, int count, int max_vec, cudaStream_t st) {
-  if (count <= 0 || max_vec <= 0) return cudaSuccess;
-  refl_kernel<T><<<dim3((unsigned)((max_vec + kWarps - 1) / kWarps), (unsigned)count), kThreads, 0, st>>>(d);
+cudaError_t launch_trsm(const TrsmDesc<T>* d, const int2* items, int nitems, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  trsm_kernel<T><<<(unsigned)nitems, kThreads, 0, st>>>(d, items);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_trsm(const TrsmDesc<T>* d, int count, int max_rows, cudaStream_t st) {
-  if (count <= 0 || max_rows <= 0) return cudaSuccess;
-  trsm_kernel<T><<<dim3((unsigned)((max_rows + kThreads - 1) / kThreads), (unsigned)count), kThreads, 0, st>>>(d);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_argmax(const ArgmaxDesc<T>* d, int count, int max_rows, cudaStream_t st) {
-  if (count <= 0 || max_rows <= 0) return cudaSuccess;
-  argmax_kernel<T><<<dim3((unsigned)((max_rows + kThreads - 1) / kThreads), (unsigned)count), kThreads, 0, st>>>(d);
+cudaError_t launch_argmax(const ArgmaxDesc<T>* d, const int2* items, int nitems, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  argmax_kernel<T><<<(unsigned)nitems, kThreads, 0, st>>>(d, items);
   return cudaGetLastError();
 }
 
@@ -688,19 +1011,59 @@ cudaError_t launch_scatter_values(T* base, const int64_t* dest, const T* vals, i
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std::vector<const FrontDesc<T>*>& d,
+                                const std::vector<std::vector<FrontDesc<T>>>& host, T* Tbuf, cudaStream_t st,
+                                int64_t* launches) {
+  cudaError_t e = cudaSuccess;
+  for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
+    const FrontGroup& G = groups[g];
+    const int cnt = (int)G.idx.size();
+    if (G.kind == 0) {
+      e = launch_front_qr_warp<T>(d[g], cnt, G.param, st);
+      ++*launches;
+    } else if (G.kind == 1) {
+      e = launch_front_qr_smem<T>(const_cast<FrontDesc<T>*>(d[g]), cnt, G.param, st);
+      ++*launches;
+    } else {
+      const int nb = 32;
+      for (int j0 = 0; j0 < G.param && e == cudaSuccess; j0 += nb) {
+        int maxtiles = 0;
+        for (auto& f : host[g]) {
+          const int steps = f.c < f.m ? f.c : f.m;
+          if (j0 >= steps) continue;
+          const int b = steps - j0 < nb ? steps - j0 : nb;
+          const int tiles = (f.n - (j0 + b) + 31) / 32;
+          maxtiles = tiles > maxtiles ? tiles : maxtiles;
+        }
+        e = launch_front_panel<T>(d[g], cnt, j0, nb, Tbuf, st);
+        if (e == cudaSuccess) e = launch_front_trailing<T>(d[g], cnt, j0, nb, Tbuf, maxtiles, st);
+        *launches += 2;
+      }
+      if (e == cudaSuccess) e = launch_front_finish<T>(d[g], cnt, G.param, st);
+      ++*launches;
+    }
+  }
+  return e;
+}
+
 #define SPAQR_INST(T)                                                                                     \
+  template cudaError_t launch_front_groups<T>(const std::vector<FrontGroup>&, const std::vector<const FrontDesc<T>*>&, \
+                                              const std::vector<std::vector<FrontDesc<T>>>&, T*, cudaStream_t,       \
+                                              int64_t*);                                                             \
   template cudaError_t launch_scatter_values<T>(T*, const int64_t*, const T*, int64_t, cudaStream_t);    \
   template cudaError_t launch_copy<T>(const CopyDesc<T>*, const int*, int, int, cudaStream_t);           \
   template cudaError_t launch_identity<T>(const CopyDesc<T>*, int, cudaStream_t);                        \
   template cudaError_t launch_front_qr_smem<T>(const FrontDesc<T>*, int, int, cudaStream_t);             \
+  template cudaError_t launch_front_qr_warp<T>(const FrontDesc<T>*, int, int, cudaStream_t);             \
   template cudaError_t launch_front_panel<T>(const FrontDesc<T>*, int, int, int, T*, cudaStream_t);      \
   template cudaError_t launch_front_trailing<T>(const FrontDesc<T>*, int, int, int, const T*, int,       \
                                                 cudaStream_t);                                           \
   template cudaError_t launch_front_finish<T>(const FrontDesc<T>*, int, int, cudaStream_t);                   \
-  template cudaError_t launch_qrcp<T>(const QrcpDesc<T>*, int, double, int, cudaStream_t);               \
-  template cudaError_t launch_refl<T>(const ReflDesc<T>*, int, int, cudaStream_t);                       \
-  template cudaError_t launch_trsm<T>(const TrsmDesc<T>*, int, int, cudaStream_t);                       \
-  template cudaError_t launch_argmax<T>(const ArgmaxDesc<T>*, int, int, cudaStream_t);
+  template cudaError_t launch_qrcp<T>(const QrcpDesc<T>*, int, double, int, int, int, bool, cudaStream_t); \
+  template cudaError_t launch_refl<T>(const ReflDesc<T>*, const int2*, int, cudaStream_t);               \
+  template cudaError_t launch_trsm<T>(const TrsmDesc<T>*, const int2*, int, cudaStream_t);               \
+  template cudaError_t launch_argmax<T>(const ArgmaxDesc<T>*, const int2*, int, cudaStream_t);
 
 SPAQR_INST(double)
 SPAQR_INST(float)

@@ -42,15 +42,6 @@ DevicePool::~DevicePool() {
   for (auto& c : chunks_) cudaFree(c.base);
 }
 
-int DevicePool::find(void* p) const {
-  auto it = std::lower_bound(live_.begin(), live_.end(), std::make_pair(p, -1),
-                             [](const std::pair<void*, int>& a, const std::pair<void*, int>& b) {
-                               return a.first < b.first;
-                             });
-  if (it == live_.end() || it->first != p) return -1;
-  return (int)(it - live_.begin());
-}
-
 void* DevicePool::alloc(size_t bytes) {
   if (bytes == 0) bytes = 1;
   int cls = 0;
@@ -86,38 +77,66 @@ void* DevicePool::alloc(size_t bytes) {
     p = ch->base + ch->used;
     ch->used += sz;
   }
-  auto it = std::lower_bound(live_.begin(), live_.end(), std::make_pair(p, -1),
-                             [](const std::pair<void*, int>& a, const std::pair<void*, int>& b) {
-                               return a.first < b.first;
-                             });
-  live_.insert(it, std::make_pair(p, cls));
+  live_[p] = cls;
   in_use_ += sz;
   peak_ = std::max(peak_, in_use_);
   return p;
 }
 
 bool DevicePool::contains(const void* p, size_t bytes) const {
-  if (live_.empty()) return false;
-  auto it = std::upper_bound(live_.begin(), live_.end(), std::make_pair(const_cast<void*>(p), 1 << 30),
-                             [](const std::pair<void*, int>& a, const std::pair<void*, int>& b) {
-                               return a.first < b.first;
-                             });
-  if (it == live_.begin()) return false;
-  --it;
-  const char* base = static_cast<const char*>(it->first);
+  // a block starts at a multiple of 256 bytes inside a chunk: walk down to it
   const char* q = static_cast<const char*>(p);
-  const size_t sz = size_t(256) << it->second;
-  return q >= base && q + bytes <= base + sz;
+  for (const auto& c : chunks_) {
+    if (q < c.base || q >= c.base + c.size) continue;
+    size_t off = (size_t)(q - c.base) & ~size_t(255);
+    while (true) {
+      auto it = live_.find(c.base + off);
+      if (it != live_.end()) {
+        const size_t sz = size_t(256) << it->second;
+        return q + bytes <= c.base + off + sz;
+      }
+      if (off == 0) return false;
+      off -= 256;
+    }
+  }
+  return false;
 }
 
 void DevicePool::release(void* p) {
   if (!p) return;
-  const int i = find(p);
-  if (i < 0) return;
-  const int cls = live_[(size_t)i].second;
-  live_.erase(live_.begin() + i);
+  auto it = live_.find(p);
+  if (it == live_.end()) return;
+  const int cls = it->second;
+  live_.erase(it);
   free_[(size_t)cls].push_back(p);
   in_use_ -= size_t(256) << cls;
+}
+
+// ------------------------------------------------------------------ Arena
+Arena::~Arena() {
+  for (auto& c : chunks_) cudaFree(c.base);
+}
+
+void* Arena::alloc(size_t bytes) {
+  const size_t need = (std::max<size_t>(bytes, 1) + 255) & ~size_t(255);
+  if (chunks_.empty() || chunks_.back().used + need > chunks_.back().size) {
+    const size_t csz = std::max(chunk_, need);
+    char* base = nullptr;
+    SPAQR_CUDA(cudaMalloc(&base, csz));
+    chunks_.push_back(Chunk{base, csz, 0});
+  }
+  Chunk& c = chunks_.back();
+  void* p = c.base + c.used;
+  c.used += need;
+  used_ += need;
+  return p;
+}
+
+bool Arena::contains(const void* p, size_t bytes) const {
+  const char* q = static_cast<const char*>(p);
+  for (const auto& c : chunks_)
+    if (q >= c.base && q + bytes <= c.base + c.used) return true;
+  return false;
 }
 
 // --------------------------------------------------------------- Uploader
@@ -259,11 +278,18 @@ class Factorizer {
   std::vector<std::vector<int32_t>> slots_;
   std::vector<char> calive_;
   std::vector<Group> G_;
+  std::vector<int> live_;  // ids of live groups (dead ones dropped lazily)
   std::vector<Buf> bufs_;
   std::vector<int> p1_of_, p2_of_;
   std::vector<int> own_head_;  // scratch
   int smem_max_ = 0;
   int64_t launches_ = 0;
+  struct StageLog {
+    int fronts = 0, rounds = 0, max_m = 0, max_n = 0, max_c = 0;
+    int scaled = 0, max_rp = 0, s1 = 0, s1_max_m = 0, s1_max_n = 0, s2 = 0, colours = 0, s2_max_c = 0, s2_max_w = 0;
+    int64_t sum_c = 0, sum_k = 0;
+    double front_flops = 0;
+  } slog_;
 
   // ----------------------------------------------------------- helpers
   int level(int c) const { return sc_->level[(size_t)c]; }
@@ -292,7 +318,16 @@ class Factorizer {
     g.width = w;
     g.alive = true;
     G_.push_back(std::move(g));
+    live_.push_back((int)G_.size() - 1);
     return (int)G_.size() - 1;
+  }
+  // live group ids in ascending order (compacts the list)
+  const std::vector<int>& live() {
+    size_t w = 0;
+    for (size_t i = 0; i < live_.size(); ++i)
+      if (G_[(size_t)live_[i]].alive) live_[w++] = live_[i];
+    live_.resize(w);
+    return live_;
   }
   // one buffer for a list of new groups (zero-initialised when zero = true)
   void assign_buffer(const std::vector<int>& ids, bool zero) {
@@ -344,6 +379,14 @@ class Factorizer {
     return g.off[(size_t)(it - g.sup.begin())];
   }
   T* wstore(size_t elems) { return static_cast<T*>(h_.wpool.alloc(std::max<size_t>(elems, 1) * sizeof(T))); }
+  // (descriptor, first unit) work items covering `units(i)` units per descriptor in steps of `per`
+  template <typename F>
+  std::vector<int2> items_for(size_t count, int per, F units) const {
+    std::vector<int2> it;
+    for (size_t i = 0; i < count; ++i)
+      for (int u = 0; u < units(i); u += per) it.push_back(make_int2((int)i, u));
+    return it;
+  }
 
   // ---- optional host-side bounds checks of every descriptor (SPAQR_CHECK=1)
   bool checking_ = false;
@@ -409,72 +452,32 @@ void Factorizer<T>::copies(const std::vector<CopyDesc<T>>& cps) {
 template <typename T>
 void Factorizer<T>::front_qr(std::vector<FrontDesc<T>>& fr) {
   if (fr.empty()) return;
-  struct Scope {
-    EventTimer& t;
-    cudaStream_t s;
-    Scope(EventTimer& t_, cudaStream_t s_) : t(t_), s(s_) {}
-    ~Scope() { t.end(s); }
-  };
-  // bucket by shared-memory need
-  const int lim = smem_max_;
-  const int classes[4] = {24 << 10, 48 << 10, 100 << 10, lim};
-  std::vector<FrontDesc<T>> b[4];
-  std::vector<FrontDesc<T>> big;
+  std::vector<int> ms, ns, cs;
   for (auto& f : fr) {
-    if (f.c == 0 || f.m == 0 || f.n == 0) continue;
-    if (checking_) in_bounds(f.ptr, f.m, f.n, f.ld, sizeof(T), "front");
-    const int need = front_smem_bytes(f.m, f.n, f.c, (int)sizeof(T));
-    if ((int64_t)f.m * f.n * (int64_t)sizeof(T) + 64 > lim) {
-      big.push_back(f);
-      continue;
-    }
-    for (int q = 0; q < 4; ++q)
-      if (need <= classes[q]) {
-        b[q].push_back(f);
-        break;
-      }
+    if (checking_ && f.c > 0) in_bounds(f.ptr, f.m, f.n, f.ld, sizeof(T), "front");
+    ms.push_back(f.m);
+    ns.push_back(f.n);
+    cs.push_back(f.c);
   }
-  std::vector<FrontDesc<T>*> dq(4, nullptr);
-  for (int q = 0; q < 4; ++q)
-    if (!b[q].empty()) dq[(size_t)q] = up_.put(b[q]);
-  FrontDesc<T>* dbig = big.empty() ? nullptr : up_.put(big);
-  T* Tbuf = big.empty() ? nullptr : static_cast<T*>(up_.scratch(big.size() * 32 * 32 * sizeof(T)));
+  const auto groups = plan_fronts(ms, ns, cs, (int)sizeof(T), smem_max_);
+  if (groups.empty()) return;
+  std::vector<std::vector<FrontDesc<T>>> host(groups.size());
+  std::vector<const FrontDesc<T>*> dev(groups.size());
+  T* Tbuf = nullptr;
+  for (size_t g = 0; g < groups.size(); ++g) {
+    for (int i : groups[g].idx) host[g].push_back(fr[(size_t)i]);
+    dev[g] = up_.put(host[g]);
+    if (groups[g].kind == 2) Tbuf = static_cast<T*>(up_.scratch(host[g].size() * 32 * 32 * sizeof(T)));
+  }
   tm_.begin(st_, 1);
-  Scope scope(tm_, st_);
-  for (int q = 0; q < 4; ++q) {
-    if (b[q].empty()) continue;
-    int need = 0;
-    for (auto& f : b[q]) need = std::max(need, front_smem_bytes(f.m, f.n, f.c, (int)sizeof(T)));
-    auto* d = dq[(size_t)q];
-    check(launch_front_qr_smem<T>(d, (int)b[q].size(), need, st_), "front_qr_smem");
-  }
-  if (!big.empty()) {
-    const int nb = 32;
-    int maxc = 0, maxtiles = 0;
-    for (auto& f : big) {
-      maxc = std::max(maxc, std::min(f.c, f.m));
-    }
-    auto* d = dbig;
-    for (int j0 = 0; j0 < maxc; j0 += nb) {
-      maxtiles = 0;
-      for (auto& f : big) {
-        const int steps = std::min(f.c, f.m);
-        if (j0 >= steps) continue;
-        const int b = std::min(nb, steps - j0);
-        maxtiles = std::max(maxtiles, (f.n - (j0 + b) + 31) / 32);
-      }
-      check(launch_front_panel<T>(d, (int)big.size(), j0, nb, Tbuf, st_), "front_panel");
-      check(launch_front_trailing<T>(d, (int)big.size(), j0, nb, Tbuf, maxtiles, st_), "front_trailing");
-    }
-    check(launch_front_finish<T>(d, (int)big.size(), maxc, st_), "front_finish");
-  }
+  check(launch_front_groups<T>(groups, dev, host, Tbuf, st_, &launches_), "front_qr");
+  tm_.end(st_);
 }
 
 template <typename T>
 void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_bufs) {
   if (qs.empty()) return;
-  std::vector<QrcpDesc<T>> small, large;
-  int need_s = 0, need_l = 0;
+  std::vector<int> ms, ns;
   for (auto& q : qs) {
     if (checking_) {
       in_bounds(q.src, q.m, q.n, q.ld, sizeof(T), "qrcp src");
@@ -482,27 +485,31 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
       if (q.V) in_bounds(q.V, q.m, std::min(q.m, q.n), q.m, sizeof(T), "qrcp V");
       if (q.tau) in_bounds(q.tau, 1, std::min(q.m, q.n), 1, sizeof(T), "qrcp tau");
     }
-    const int whole = qrcp_smem_bytes(q.m, q.n, (int)sizeof(T), true);
-    if (whole <= smem_max_) {
-      small.push_back(q);
-      need_s = std::max(need_s, whole);
-    } else {
-      const int part = qrcp_smem_bytes(q.m, q.n, (int)sizeof(T), false);
-      if (part > smem_max_)
-        throw Error(SPAQR_ERR_CAPACITY, "column-pivoted QR with too many columns for shared memory");
-      T* w = static_cast<T*>(pool_.alloc((size_t)q.m * q.n * sizeof(T)));
-      work_bufs.push_back(w);
-      q.work = w;
-      large.push_back(q);
-      need_l = std::max(need_l, part);
-    }
+    ms.push_back(q.m);
+    ns.push_back(q.n);
   }
+  std::vector<QrcpGroup> groups;
+  std::vector<char> need_work;
+  if (!plan_qrcp(ms, ns, (int)sizeof(T), smem_max_, groups, need_work))
+    throw Error(SPAQR_ERR_CAPACITY, "column-pivoted QR with too many columns for 16 CTAs");
+  for (size_t i = 0; i < qs.size(); ++i)
+    if (need_work[i]) {
+      T* w = static_cast<T*>(pool_.alloc((size_t)std::max(1, qs[i].m) * std::max(1, qs[i].n) * sizeof(T)));
+      work_bufs.push_back(w);
+      qs[i].work = w;
+    }
   const double eps = h_.opt.mode == SPAQR_MODE_SPAQR ? h_.opt.eps : 0.0;
-  auto* ds = small.empty() ? nullptr : up_.put(small);
-  auto* dl = large.empty() ? nullptr : up_.put(large);
+  std::vector<QrcpDesc<T>*> dg;
+  for (auto& g : groups) {
+    std::vector<QrcpDesc<T>> part;
+    for (int i : g.idx) part.push_back(qs[(size_t)i]);
+    dg.push_back(up_.put(part));
+  }
   tm_.begin(st_, 2);
-  if (!small.empty()) check(launch_qrcp<T>(ds, (int)small.size(), eps, need_s, st_), "qrcp_smem");
-  if (!large.empty()) check(launch_qrcp<T>(dl, (int)large.size(), eps, -need_l, st_), "qrcp_global");
+  for (size_t t = 0; t < groups.size(); ++t) {
+    const auto& g = groups[t];
+    check(launch_qrcp<T>(dg[t], (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st_), "qrcp");
+  }
   tm_.end(st_);
 }
 
@@ -511,12 +518,11 @@ void Factorizer<T>::index_groups(std::vector<std::vector<int>>& own, std::vector
   const size_t nc = ccols_.size();
   own.assign(nc, {});
   touch.assign(nc, {});
-  for (size_t id = 0; id < G_.size(); ++id) {
-    const Group& g = G_[id];
-    if (!g.alive) continue;
-    own[(size_t)g.owner].push_back((int)id);
+  for (int id : live()) {
+    const Group& g = G_[(size_t)id];
+    own[(size_t)g.owner].push_back(id);
     for (int c : g.sup)
-      if (c != g.owner) touch[(size_t)c].push_back((int)id);
+      if (c != g.owner) touch[(size_t)c].push_back(id);
   }
 }
 
@@ -568,9 +574,18 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
       const size_t t = (size_t)(std::lower_bound(tmp.begin(), tmp.end(), cl_of[(size_t)j]) - tmp.begin());
       sc[t] += v * v;
     }
-    int best = 0;
-    for (size_t t = 1; t < tmp.size(); ++t) {
-      const int a = tmp[t], b = tmp[(size_t)best];
+    // candidates: every touched cluster, or (tree rule) those of the deepest level
+    int deep = 0;
+    for (int c : tmp) deep = std::max(deep, level(c));
+    int best = -1;
+    for (size_t t = 0; t < tmp.size(); ++t) {
+      const int a = tmp[t];
+      if (h_.opt.row_rule == SPAQR_ROWS_TREE && level(a) != deep) continue;
+      if (best < 0) {
+        best = (int)t;
+        continue;
+      }
+      const int b = tmp[(size_t)best];
       if (sc[t] > sc[(size_t)best] ||
           (sc[t] == sc[(size_t)best] && (level(a) > level(b) || (level(a) == level(b) && a < b))))
         best = (int)t;
@@ -682,6 +697,7 @@ void Factorizer<T>::eliminate() {
     eliminate_round(batch, round);
     todo.swap(rest);
     ++round;
+    slog_.rounds = round;
   }
 }
 
@@ -762,8 +778,15 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
     if (!f.nextra) continue;
     const int ncl = (int)f.cols.size() - 1;
     pack_off.push_back(pack.size());
+    // candidate clusters: all of them, or (tree rule) those of the deepest level; a
+    // non-candidate gets level -1, which the kernel skips
+    int deep = 0;
+    for (int t = 0; t < ncl; ++t) deep = std::max(deep, level(f.cols[(size_t)t + 1]));
     for (int t = 0; t <= ncl; ++t) pack.push_back(f.coff[(size_t)t + 1]);
-    for (int t = 0; t < ncl; ++t) pack.push_back(level(f.cols[(size_t)t + 1]));
+    for (int t = 0; t < ncl; ++t) {
+      const int lv = level(f.cols[(size_t)t + 1]);
+      pack.push_back(h_.opt.row_rule == SPAQR_ROWS_TREE && lv != deep ? -1 : lv);
+    }
     for (int t = 0; t < ncl; ++t) pack.push_back(f.cols[(size_t)t + 1]);
   }
   if (!pack_off.empty()) {
@@ -780,8 +803,10 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
     if (checking_)
       for (auto& a : am) in_bounds(a.F, a.r1, 1, a.ld, sizeof(T), "argmax rows");
     auto* d = up_.put(am);
+    auto its = items_for(am.size(), kRowsPerItem, [&](size_t i) { return am[i].r1 - am[i].r0; });
+    int2* di = up_.put(its);
     tm_.begin(st_, 3);
-    check(launch_argmax<T>(d, (int)am.size(), max_extra, st_), "argmax");
+    check(launch_argmax<T>(d, di, (int)its.size(), st_), "argmax");
     tm_.end(st_);
   }
   // R_s = [R_ss R_sn] into the W store
@@ -802,6 +827,10 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
       rc.push_back(CopyDesc<T>{W + f.foff, R, nullptr, f.m, f.c, f.c, f.n, 0, 0});
     }
     h_.stats.n_fronts++;
+    slog_.fronts++;
+    slog_.max_m = std::max(slog_.max_m, f.m);
+    slog_.max_n = std::max(slog_.max_n, f.n);
+    slog_.max_c = std::max(slog_.max_c, f.c);
     h_.stats.max_front_rows = std::max<int64_t>(h_.stats.max_front_rows, f.m);
     h_.stats.max_front_cols = std::max<int64_t>(h_.stats.max_front_cols, f.n);
     if (k_ == 1) {
@@ -949,6 +978,8 @@ void Factorizer<T>::scale() {
       row += gg.rows;
     }
     fr.push_back(FrontDesc<T>{F, s.rp, s.n, s.c, s.rp});
+    slog_.scaled++;
+    slog_.max_rp = std::max(slog_.max_rp, s.rp);
     const double m = s.rp, c = s.c, t = s.n - s.c;
     h_.stats.flops_front += 2.0 * c * c * (m - c / 3.0) + (4.0 * m * c - 2.0 * c * c) * t;
   }
@@ -1013,9 +1044,9 @@ void Factorizer<T>::scale() {
   for (auto& s : si) Rof[(size_t)s.p] = s.R;
   std::vector<TrsmDesc<T>> tr;
   int maxr = 0;
-  for (size_t id = 0; id < G_.size(); ++id) {
-    const Group& g = G_[id];
-    if (!g.alive || g.rows == 0) continue;
+  for (int id : live()) {
+    const Group& g = G_[(size_t)id];
+    if (g.rows == 0) continue;
     for (size_t t = 0; t < g.sup.size(); ++t) {
       const int c = g.sup[t];
       if (c == g.owner || !Rof[(size_t)c]) continue;
@@ -1031,8 +1062,10 @@ void Factorizer<T>::scale() {
     }
   if (!tr.empty()) {
     auto* d = up_.put(tr);
+    auto its = items_for(tr.size(), kRowsPerItem, [&](size_t i) { return tr[i].rows; });
+    int2* di = up_.put(its);
     tm_.begin(st_, 3);
-    check(launch_trsm<T>(d, (int)tr.size(), maxr, st_), "trsm");
+    check(launch_trsm<T>(d, di, (int)its.size(), st_), "trsm");
     tm_.end(st_);
   }
 }
@@ -1053,6 +1086,9 @@ void Factorizer<T>::step1() {
   int* d_rank = static_cast<int*>(up_.scratch(who.size() * sizeof(int)));
   for (size_t i = 0; i < who.size(); ++i) {
     Group& g = G_[(size_t)who[i]];
+    slog_.s1++;
+    slog_.s1_max_m = std::max(slog_.s1_max_m, g.rows);
+    slog_.s1_max_n = std::max(slog_.s1_max_n, g.width);
     qs.push_back(QrcpDesc<T>{g.ptr, nullptr, g.ptr, nullptr, nullptr, d_rank + i, g.rows, g.width, g.ld, g.ld});
   }
   std::vector<T*> work;
@@ -1094,6 +1130,11 @@ void Factorizer<T>::step2() {
   }
   std::vector<int> colour(nc, -1);
   int ncol = 0;
+  struct ColourLog {
+    StageLog& l;
+    int& n;
+    ~ColourLog() { l.colours = n; }
+  } colour_log{slog_, ncol};
   for (int p : ps) {
     std::vector<char> used((size_t)ncol + 1, 0);
     for (int q : adj[(size_t)p])
@@ -1168,6 +1209,9 @@ void Factorizer<T>::step2() {
       }
       const int ncm = x.rn + x.cn;
       const int kmax = std::min(x.cp, ncm);
+      slog_.s2++;
+      slog_.s2_max_c = std::max(slog_.s2_max_c, x.cp);
+      slog_.s2_max_w = std::max(slog_.s2_max_w, ncm);
       WOp op;
       op.kind = 2;
       op.stage = k_;
@@ -1203,11 +1247,11 @@ void Factorizer<T>::step2() {
           in_bounds(r.ptr, r.len, r.nvec, r.ld, sizeof(T), "refl cols");
       }
     if (!rf.empty()) {
-      int mv = 0;
-      for (auto& r : rf) mv = std::max(mv, r.nvec);
       auto* d = up_.put(rf);
+      auto its = items_for(rf.size(), kReflPerItem, [&](size_t i) { return rf[i].nvec; });
+      int2* di = up_.put(its);
       tm_.begin(st_, 3);
-      check(launch_refl<T>(d, (int)rf.size(), mv, st_), "refl");
+      check(launch_refl<T>(d, di, (int)its.size(), st_), "refl");
       tm_.end(st_);
     }
     pool_.release(M);
@@ -1223,6 +1267,8 @@ void Factorizer<T>::step2() {
     WOp& op = h_.ops[recs[i].op];
     const int k = ks[i], p = recs[i].p;
     op.k = k;
+    slog_.sum_c += op.c;
+    slog_.sum_k += std::min(k, op.c);
     {
       // column-pivoted QR to rank k of the c_p x ncm block, then the two-sided application
       const double m = op.c, n = recs[i].ncm, kk = k;
@@ -1274,9 +1320,8 @@ void Factorizer<T>::merge() {
   std::vector<CopyDesc<T>> cps;
   std::vector<int> ids;
   const auto old_ccols = ccols_;
-  for (size_t id = 0; id < G_.size(); ++id) {
-    Group& g = G_[id];
-    if (!g.alive) continue;
+  for (int id : live()) {
+    Group& g = G_[(size_t)id];
     std::vector<int> nsup;
     for (int c : g.sup) nsup.push_back(sc_->parent[(size_t)c]);
     std::sort(nsup.begin(), nsup.end());
@@ -1294,7 +1339,7 @@ void Factorizer<T>::merge() {
       for (auto& c : g.sup) c = sc_->parent[(size_t)c];
       continue;
     }
-    moved.push_back((int)id);
+    moved.push_back(id);
   }
   // new blocks for moved groups (one buffer, zero-filled)
   std::vector<int> tmpids;
@@ -1393,6 +1438,7 @@ void Factorizer<T>::run(const spaqr_csr& A) {
   double t0 = now();
   init_stage(A);
   double tp[6] = {0, 0, 0, 0, 0, 0};
+  tp[1] = now() - t0;
   for (k_ = L_; k_ >= 1; --k_) {
     double a = now();
     eliminate();
@@ -1416,15 +1462,19 @@ void Factorizer<T>::run(const spaqr_csr& A) {
       tp[5] += f - b;
     }
     if (h_.opt.verbose) {
-      size_t live = 0;
-      for (auto& g : G_) live += g.alive;
-      std::fprintf(stderr, "[spaqr] stage %d done: live groups %zu, pool %.1f MB (peak %.1f)\n", k_, live,
-                   pool_.in_use() / 1e6, pool_.peak() / 1e6);
+      const size_t live = this->live().size();
+      const StageLog& g = slog_;
+      std::fprintf(stderr,
+                   "[spaqr] stage %2d: fronts %5d rounds %d max m/n/c %d/%d/%d | scaled %d max r_p %d | step1 %d max "
+                   "%dx%d | step2 %d colours %d max c %d x %d, kept %lld of %lld | live groups %zu pool %.0f MB\n",
+                   k_, g.fronts, g.rounds, g.max_m, g.max_n, g.max_c, g.scaled, g.max_rp, g.s1, g.s1_max_m, g.s1_max_n,
+                   g.s2, g.colours, g.s2_max_c, g.s2_max_w, (long long)g.sum_k, (long long)g.sum_c, live,
+                   pool_.in_use() / 1e6);
     }
+    slog_ = StageLog();
   }
   sync();
-  for (auto& g : G_)
-    if (g.alive) throw Error(SPAQR_ERR_CUDA, "internal: rows left after the root");
+  if (!live().empty()) throw Error(SPAQR_ERR_CUDA, "internal: rows left after the root");
   for (int i = 0; i < 6; ++i) h_.stats.t_phase[i] = tp[i];
   h_.stats.launches = launches_;
   h_.stats.syncs = up_.syncs;

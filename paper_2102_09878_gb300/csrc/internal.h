@@ -6,6 +6,7 @@
 #include <cstring>
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/spaqr.h"
@@ -52,9 +53,30 @@ class DevicePool {
   size_t chunk_;
   std::vector<Chunk> chunks_;
   std::vector<std::vector<void*>> free_;  // by size class
-  std::vector<std::pair<void*, int>> live_;  // sorted by pointer: block -> class
+  std::unordered_map<const void*, int> live_;  // live block -> size class
   size_t in_use_ = 0, peak_ = 0, reserved_ = 0;
-  int find(void* p) const;
+};
+
+// Bump allocator for the W store: blocks are carved from large cudaMalloc
+// chunks and released only when the arena is destroyed.
+class Arena {
+ public:
+  explicit Arena(size_t chunk_bytes = size_t(64) << 20) : chunk_(chunk_bytes) {}
+  ~Arena();
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  void* alloc(size_t bytes);
+  bool contains(const void* p, size_t bytes) const;
+  size_t used() const { return used_; }
+
+ private:
+  struct Chunk {
+    char* base;
+    size_t size, used;
+  };
+  size_t chunk_;
+  std::vector<Chunk> chunks_;
+  size_t used_ = 0;
 };
 
 // Pinned staging + device arena for small descriptor arrays.  put() copies a
@@ -146,7 +168,7 @@ struct Handle {
   double* d_D = nullptr;  // column scaling
   std::vector<double> D;
   // W store
-  DevicePool wpool{size_t(64) << 20};
+  Arena wpool{size_t(64) << 20};
   std::vector<WOp> ops;
   int depth = 0;
   // device-side apply plan (built after the factorization)

@@ -3,7 +3,9 @@
 // the cudaError_t of the launch.
 #pragma once
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
+#include <vector>
 
 namespace spaqr {
 
@@ -70,7 +72,7 @@ struct TrsmDesc {
 // Extra-row destination: for rows [r0, r1) of the front F (ld), score each of
 // ncl column clusters (columns [coff[t], coff[t+1])) by the sum of squares and
 // write the argmax cluster index (ties: larger lvl, then smaller id) to
-// out[r - r0].
+// out[r - r0]; clusters with lvl < 0 are not candidates.
 template <typename T>
 struct ArgmaxDesc {
   const T* F;
@@ -87,6 +89,10 @@ cudaError_t launch_copy(const CopyDesc<T>* d_desc, const int* chunk_start, int c
 inline int copy_chunks(long long elems) { return (int)((elems + 2047) / 2048); }
 // Small fronts: whole front in shared memory (smem_bytes >= m*n*sizeof(T) for every front).
 template <typename T> cudaError_t launch_front_qr_smem(const FrontDesc<T>* d, int count, int smem_bytes, cudaStream_t st);
+// Tiny fronts (c <= 128, (m|1) * n * sizeof(T) * 8 <= shared memory): one warp per
+// front, per_warp_elems >= (m|1) * n for every front of the launch.
+template <typename T> cudaError_t launch_front_qr_warp(const FrontDesc<T>* d, int count, int per_warp_elems, cudaStream_t st);
+
 // Large fronts, blocked: panel j0..j0+nb of each front then the trailing update.
 template <typename T>
 cudaError_t launch_front_panel(const FrontDesc<T>* d, int count, int j0, int nb, T* Tbuf, cudaStream_t st);
@@ -95,22 +101,175 @@ cudaError_t launch_front_trailing(const FrontDesc<T>* d, int count, int j0, int 
                                   cudaStream_t st);
 template <typename T>
 cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, cudaStream_t st);
-// smem_bytes > 0: whole matrices in shared memory (qrcp_smem_bytes(m, n, sizeof(T), true));
-// smem_bytes < 0: matrices in `work` with -smem_bytes of shared scratch.
+// One cluster of cs CTAs per matrix (cs in 1, 2, 4, 8, 16); every matrix of a
+// launch shares cs, nl_max >= ceil(n / cs) and m_max >= m.  smem_slab: the
+// column slabs live in shared memory, else in each descriptor's work buffer
+// (m x n, ld m).
 template <typename T>
-cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int smem_bytes, cudaStream_t st);
-inline int qrcp_smem_bytes(int m, int n, int elem, bool whole) {
-  const int kmax = m < n ? m : n;
-  long long b = ((long long)n * 20 + 15) / 16 * 16 + (long long)(((kmax + 1) & ~1) + 2) * elem;
-  if (whole) b += (long long)m * n * elem;
-  return (int)(b + 16);
+cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int nl_max, int m_max, bool smem_slab,
+                        cudaStream_t st);
+// dynamic shared memory of one QRCP CTA (nl columns of m rows)
+inline int qrcp_smem_bytes(int m, int nl, int elem, bool slab) {
+  long long b = ((long long)nl * 20 + 15) / 16 * 16;  // nu, nuref, step_of
+  b += (long long)(((m + 3) & ~1) * 2) * elem;         // vbuf, taus
+  if (slab) b += (long long)m * nl * elem;
+  return (int)(b + 64);
 }
+// Launch groups for a batch of QRCPs of shapes (m_i, n_i): each matrix takes
+// the smallest cluster size whose per-CTA column slab fits in shared memory,
+// else 16 CTAs over a global work copy (needs_work); members of a group share
+// (cs, slab) and a footprint (m_max, nl_max) that fits `limit` bytes.
+struct QrcpGroup {
+  int cs = 1;  // 0: one warp per matrix (nl_max then holds the per-warp bytes)
+  bool slab = true;
+  int m_max = 0, nl_max = 0;
+  std::vector<int> idx;
+};
+// bytes of one warp's region in the warp-per-matrix QRCP (cs == 0 groups)
+inline int qrcp_warp_bytes(int m, int n, int elem) {
+  const int kmax = m < n ? m : n;
+  long long b = ((long long)n * 20 + 15) / 16 * 16 + (long long)((kmax + 3) & ~1) * elem +
+                (long long)(m | 1) * n * elem;
+  return (int)((b + 15) / 16 * 16);
+}
+constexpr int kQrcpWarpCap = 24 << 10;  // per-warp region limit for the warp QRCP
+
+inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, int elem, int limit,
+                      std::vector<QrcpGroup>& out, std::vector<char>& needs_work) {
+  const int nmat = (int)ms.size();
+  needs_work.assign((size_t)nmat, 0);
+  std::vector<int> cs((size_t)nmat), order;
+  std::vector<char> slab((size_t)nmat);
+  // warp groups first: small matrices, one warp each, packed 8 per CTA
+  std::vector<int> rest;
+  {
+    QrcpGroup wg;
+    wg.cs = 0;
+    wg.slab = true;
+    for (int i = 0; i < nmat; ++i) {
+      const int wb = qrcp_warp_bytes(ms[(size_t)i], ns[(size_t)i], elem);
+      if (ms[(size_t)i] <= 64 && wb <= kQrcpWarpCap && (long long)wb * 8 <= limit) {
+        wg.idx.push_back(i);
+        wg.nl_max = std::max(wg.nl_max, wb);  // per-warp bytes
+        wg.m_max = std::max(wg.m_max, ms[(size_t)i]);
+      } else {
+        rest.push_back(i);
+      }
+    }
+    out.clear();
+    if (!wg.idx.empty()) out.push_back(wg);
+  }
+  for (int i : rest) {
+    int c = 1;
+    while (c < 16 && qrcp_smem_bytes(ms[(size_t)i], (ns[(size_t)i] + c - 1) / c, elem, true) > limit) c *= 2;
+    const int nl = (ns[(size_t)i] + c - 1) / c;
+    if (qrcp_smem_bytes(ms[(size_t)i], nl, elem, true) <= limit) {
+      cs[(size_t)i] = c;
+      slab[(size_t)i] = 1;
+    } else {
+      cs[(size_t)i] = 16;
+      slab[(size_t)i] = 0;
+      needs_work[(size_t)i] = 1;
+      if (qrcp_smem_bytes(ms[(size_t)i], (ns[(size_t)i] + 15) / 16, elem, false) > limit) return false;
+    }
+    order.push_back(i);
+  }
+  // group by (cs, slab), larger footprints first, greedy packing under the limit
+  const size_t first_cta_group = out.size();
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (cs[(size_t)a] != cs[(size_t)b]) return cs[(size_t)a] < cs[(size_t)b];
+    if (slab[(size_t)a] != slab[(size_t)b]) return slab[(size_t)a] > slab[(size_t)b];
+    const long long fa = (long long)ms[(size_t)a] * ((ns[(size_t)a] + cs[(size_t)a] - 1) / cs[(size_t)a]);
+    const long long fb = (long long)ms[(size_t)b] * ((ns[(size_t)b] + cs[(size_t)b] - 1) / cs[(size_t)b]);
+    return fa != fb ? fa > fb : a < b;
+  });
+  for (int i : order) {
+    const int nl = (ns[(size_t)i] + cs[(size_t)i] - 1) / cs[(size_t)i];
+    QrcpGroup* g = out.size() > first_cta_group ? &out.back() : nullptr;
+    bool fits = g && g->cs == cs[(size_t)i] && g->slab == (bool)slab[(size_t)i] &&
+                qrcp_smem_bytes(std::max(g->m_max, ms[(size_t)i]), std::max(g->nl_max, nl), elem, g->slab) <= limit;
+    // keep small problems away from large footprints (occupancy)
+    if (fits && g->slab) {
+      const int cur = qrcp_smem_bytes(g->m_max, g->nl_max, elem, true);
+      const int mine = qrcp_smem_bytes(ms[(size_t)i], nl, elem, true);
+      if (cur > 4 * mine && cur > (24 << 10)) fits = false;
+    }
+    if (!fits) {
+      out.emplace_back();
+      g = &out.back();
+      g->cs = cs[(size_t)i];
+      g->slab = slab[(size_t)i];
+    }
+    g->m_max = std::max(g->m_max, ms[(size_t)i]);
+    g->nl_max = std::max(g->nl_max, nl);
+    g->idx.push_back(i);
+  }
+  return true;
+}
+
+// Routing of a batch of fronts: kind 0 = one warp per front (param = elements
+// per warp region), kind 1 = one CTA per front in shared memory (param =
+// dynamic bytes), kind 2 = blocked multi-CTA path (param = max eliminated
+// columns).  Fronts with c == 0 or an empty shape need no work and are skipped.
+struct FrontGroup {
+  int kind = 0;
+  int param = 0;
+  std::vector<int> idx;
+};
+int front_smem_bytes(int m, int n, int c, int elem);
+inline std::vector<FrontGroup> plan_fronts(const std::vector<int>& ms, const std::vector<int>& ns,
+                                           const std::vector<int>& cs, int elem, int limit) {
+  const int tiny_cap[3] = {8 << 10, 16 << 10, 28 << 10};
+  const int cta_cap[4] = {24 << 10, 48 << 10, 100 << 10, limit};
+  std::vector<FrontGroup> g(8);
+  for (int q = 0; q < 3; ++q) g[(size_t)q].kind = 0;
+  for (int q = 0; q < 4; ++q) g[(size_t)q + 3].kind = 1;
+  g[7].kind = 2;
+  for (size_t i = 0; i < ms.size(); ++i) {
+    const int m = ms[i], n = ns[i], c = cs[i];
+    if (c == 0 || m == 0 || n == 0) continue;
+    const long long wb = (long long)(m | 1) * n * elem;
+    if (c <= 128 && m <= 256 && wb <= tiny_cap[2]) {
+      int q = 0;
+      while (wb > tiny_cap[q]) ++q;
+      g[(size_t)q].idx.push_back((int)i);
+      g[(size_t)q].param = std::max(g[(size_t)q].param, (m | 1) * n);
+      continue;
+    }
+    if ((long long)m * n * elem + 64 <= limit) {
+      const int need = front_smem_bytes(m, n, c, elem);
+      int q = 0;
+      while (q < 3 && need > cta_cap[q]) ++q;
+      g[(size_t)q + 3].idx.push_back((int)i);
+      g[(size_t)q + 3].param = std::max(g[(size_t)q + 3].param, need);
+      continue;
+    }
+    g[7].idx.push_back((int)i);
+    g[7].param = std::max(g[7].param, std::min(c, m));
+  }
+  std::vector<FrontGroup> out;
+  for (auto& x : g)
+    if (!x.idx.empty()) out.push_back(std::move(x));
+  return out;
+}
+
+// Run every group of plan_fronts: d[g] are the device descriptor arrays of the
+// groups (in order), Tbuf holds 32*32 elements per front of the blocked group.
+template <typename T>
+cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std::vector<const FrontDesc<T>*>& d,
+                                const std::vector<std::vector<FrontDesc<T>>>& host, T* Tbuf, cudaStream_t st,
+                                int64_t* launches);
+
 inline int front_smem_bytes(int m, int n, int c, int elem) {
   return (int)((long long)m * n * elem + ((c + 31) / 32) * 4 + 16);
 }
-template <typename T> cudaError_t launch_refl(const ReflDesc<T>* d, int count, int max_vec, cudaStream_t st);
-template <typename T> cudaError_t launch_trsm(const TrsmDesc<T>* d, int count, int max_rows, cudaStream_t st);
-template <typename T> cudaError_t launch_argmax(const ArgmaxDesc<T>* d, int count, int max_rows, cudaStream_t st);
+// The next three take work items (descriptor index, first vector/row): one CTA
+// per item; refl covers 8 vectors per item, trsm and argmax 256 rows.
+template <typename T> cudaError_t launch_refl(const ReflDesc<T>* d, const int2* items, int nitems, cudaStream_t st);
+template <typename T> cudaError_t launch_trsm(const TrsmDesc<T>* d, const int2* items, int nitems, cudaStream_t st);
+template <typename T> cudaError_t launch_argmax(const ArgmaxDesc<T>* d, const int2* items, int nitems, cudaStream_t st);
+constexpr int kReflPerItem = 8;
+constexpr int kRowsPerItem = 256;
 // Write an identity c x c block at ptr (ld) for each desc (src/transposed unused).
 template <typename T> cudaError_t launch_identity(const CopyDesc<T>* d, int count, cudaStream_t st);
 

@@ -39,37 +39,68 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// Back substitution R y = rhs (R upper, ld c) on a shared vector y of length c.
+// Back substitution R y = rhs (R upper, ld c) on a shared vector y of length c,
+// blocked by 32 rows: warp 0 solves each diagonal block with shuffles, then all
+// threads update the rows above it.  Two block barriers per 32 rows.
 template <typename TW>
 __device__ void upper_solve(const TW* R, int c, double* y) {
-  for (int j = c - 1; j >= 0; --j) {
+  const int lane = threadIdx.x & 31;
+  for (int hi = c; hi > 0; hi -= 32) {
+    const int lo = hi > 32 ? hi - 32 : 0;
     __syncthreads();
-    const double yj = y[j] / (double)R[j + (int64_t)j * c];
+    if (threadIdx.x < 32) {
+      const int i = lo + lane;
+      double x = i < hi ? y[i] : 0.0;
+      for (int j = hi - 1; j >= lo; --j) {
+        const double yj = __shfl_sync(0xffffffffu, x, j - lo) / (double)R[j + (int64_t)j * c];
+        if (i == j) x = yj;
+        if (i < j) x -= (double)R[i + (int64_t)j * c] * yj;
+      }
+      if (i < hi) y[i] = x;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) y[j] = yj;
-    for (int i = threadIdx.x; i < j; i += kT) y[i] -= (double)R[i + (int64_t)j * c] * yj;
+    // rows above the block: y[i] -= sum_{j in [lo, hi)} R[i, j] y[j]
+    for (int i = threadIdx.x; i < lo; i += kT) {
+      double acc = 0.0;
+      for (int j = lo; j < hi; ++j) acc += (double)R[i + (int64_t)j * c] * y[j];
+      y[i] -= acc;
+    }
   }
   __syncthreads();
 }
 
-// Forward substitution R^T y = rhs.
+// Forward substitution R^T y = rhs, blocked the same way.
 template <typename TW>
 __device__ void lower_t_solve(const TW* R, int c, double* y) {
-  for (int i = 0; i < c; ++i) {
+  const int lane = threadIdx.x & 31;
+  for (int lo = 0; lo < c; lo += 32) {
+    const int hi = lo + 32 < c ? lo + 32 : c;
     __syncthreads();
-    const double yi = y[i] / (double)R[i + (int64_t)i * c];
+    if (threadIdx.x < 32) {
+      const int i = lo + lane;
+      double x = i < hi ? y[i] : 0.0;
+      for (int j = lo; j < hi; ++j) {
+        const double yj = __shfl_sync(0xffffffffu, x, j - lo) / (double)R[j + (int64_t)j * c];
+        if (i == j) x = yj;
+        if (i > j && i < hi) x -= (double)R[j + (int64_t)i * c] * yj;
+      }
+      if (i < hi) y[i] = x;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) y[i] = yi;
-    // y_j -= R_ij y_i for j > i (row i of R, stride c)
-    for (int j = i + 1 + threadIdx.x; j < c; j += kT) y[j] -= (double)R[i + (int64_t)j * c] * yi;
+    // rows below the block: y[i] -= sum_{j in [lo, hi)} R[j, i] y[j]
+    for (int i = hi + threadIdx.x; i < c; i += kT) {
+      double acc = 0.0;
+      for (int j = lo; j < hi; ++j) acc += (double)R[j + (int64_t)i * c] * y[j];
+      y[i] -= acc;
+    }
   }
   __syncthreads();
 }
 
 // W^{-1}: z_s <- R_ss^{-1} (z_s - R_sn z_n)  (kind 0) or z_p <- R_pp^{-1} z_p (kind 1)
 template <typename TW>
-__global__ void __launch_bounds__(kT) r_inv_kernel(const ApplyOp<TW>* ops, double* z) {
-  const ApplyOp<TW> op = ops[blockIdx.x];
+__global__ void __launch_bounds__(kT) r_inv_kernel(const ApplyOp<TW>* ops, const int* ids, double* z) {
+  const ApplyOp<TW> op = ops[ids[blockIdx.x]];
   extern __shared__ double sh[];
   double* y = sh;          // c
   double* part = sh + op.c;  // kW * c partials
@@ -101,8 +132,8 @@ __global__ void __launch_bounds__(kT) r_inv_kernel(const ApplyOp<TW>* ops, doubl
 
 // W^{-T}: y = R_ss^{-T} z_s, z_s <- y, z_n -= R_sn^T y (kind 0); z_p <- R_pp^{-T} z_p (kind 1)
 template <typename TW>
-__global__ void __launch_bounds__(kT) r_invT_kernel(const ApplyOp<TW>* ops, double* z) {
-  const ApplyOp<TW> op = ops[blockIdx.x];
+__global__ void __launch_bounds__(kT) r_invT_kernel(const ApplyOp<TW>* ops, const int* ids, double* z) {
+  const ApplyOp<TW> op = ops[ids[blockIdx.x]];
   extern __shared__ double sh[];
   double* y = sh;
   const int c = op.c, w = op.w;
@@ -125,8 +156,8 @@ __global__ void __launch_bounds__(kT) r_invT_kernel(const ApplyOp<TW>* ops, doub
 // z_p <- Q z_p (inverse = 0: apply H_k first ... H_1 last; used by W^{-1})
 // z_p <- Q^T z_p (apply H_1 first; used by W^{-T})
 template <typename TW>
-__global__ void __launch_bounds__(kT) q_kernel(const ApplyOp<TW>* ops, double* z, int transpose) {
-  const ApplyOp<TW> op = ops[blockIdx.x];
+__global__ void __launch_bounds__(kT) q_kernel(const ApplyOp<TW>* ops, const int* ids, double* z, int transpose) {
+  const ApplyOp<TW> op = ops[ids[blockIdx.x]];
   extern __shared__ double sh[];
   double* y = sh;
   __shared__ double red[kW];
@@ -150,6 +181,80 @@ __global__ void __launch_bounds__(kT) q_kernel(const ApplyOp<TW>* ops, double* z
     __syncthreads();
   }
   for (int i = threadIdx.x; i < c; i += kT) z[op.slots[i]] = y[i];
+}
+
+// ------------------------------------------- warp-per-op kernels (c <= 32)
+// One warp applies one stored op; lane i holds z_slots[i].  The triangular
+// solves run by shuffles (no block barriers).
+template <typename TW>
+__global__ void __launch_bounds__(kT) r_inv_warp_kernel(const ApplyOp<TW>* ops, const int* ids, int count,
+                                                        double* z) {
+  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
+  if (gw >= count) return;
+  const ApplyOp<TW> op = ops[ids[gw]];
+  const int lane = threadIdx.x & 31, c = op.c, w = op.w;
+  double x = lane < c ? z[op.slots[lane]] : 0.0;
+  if (w > 0) {
+    const TW* Rn = op.R + (int64_t)c * c;
+    double acc = 0.0;
+    for (int j0 = 0; j0 < w; j0 += 32) {
+      const double zl = (j0 + lane < w) ? z[op.nslots[j0 + lane]] : 0.0;
+      const int jn = min(32, w - j0);
+      for (int t = 0; t < jn; ++t) {
+        const double zj = __shfl_sync(0xffffffffu, zl, t);
+        if (lane < c) acc += (double)Rn[lane + (int64_t)(j0 + t) * c] * zj;
+      }
+    }
+    x -= acc;
+  }
+  for (int j = c - 1; j >= 0; --j) {
+    const double yj = __shfl_sync(0xffffffffu, x, j) / (double)op.R[j + (int64_t)j * c];
+    if (lane == j) x = yj;
+    if (lane < j) x -= (double)op.R[lane + (int64_t)j * c] * yj;
+  }
+  if (lane < c) z[op.slots[lane]] = x;
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(kT) r_invT_warp_kernel(const ApplyOp<TW>* ops, const int* ids, int count,
+                                                         double* z) {
+  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
+  if (gw >= count) return;
+  const ApplyOp<TW> op = ops[ids[gw]];
+  const int lane = threadIdx.x & 31, c = op.c, w = op.w;
+  double x = lane < c ? z[op.slots[lane]] : 0.0;
+  for (int i = 0; i < c; ++i) {
+    const double yi = __shfl_sync(0xffffffffu, x, i) / (double)op.R[i + (int64_t)i * c];
+    if (lane == i) x = yi;
+    if (lane > i && lane < c) x -= (double)op.R[i + (int64_t)lane * c] * yi;
+  }
+  if (lane < c) z[op.slots[lane]] = x;
+  if (w > 0) {
+    const TW* Rn = op.R + (int64_t)c * c;
+    for (int j = 0; j < w; ++j) {
+      double sv = lane < c ? (double)Rn[lane + (int64_t)j * c] * x : 0.0;
+      sv = wsum(sv);
+      if (lane == 0) atomicAdd(&z[op.nslots[j]], -sv);
+    }
+  }
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(kT) q_warp_kernel(const ApplyOp<TW>* ops, const int* ids, int count, double* z,
+                                                    int transpose) {
+  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
+  if (gw >= count) return;
+  const ApplyOp<TW> op = ops[ids[gw]];
+  const int lane = threadIdx.x & 31, c = op.c;
+  const int k = *op.kdev;
+  double x = lane < c ? z[op.slots[lane]] : 0.0;
+  for (int t = 0; t < k; ++t) {
+    const int i = transpose ? t : k - 1 - t;
+    const double v = lane == i ? 1.0 : ((lane > i && lane < c) ? (double)op.V[lane + (int64_t)i * c] : 0.0);
+    const double d = wsum(v * x) * (double)op.tau[i];
+    x -= d * v;
+  }
+  if (lane < c) z[op.slots[lane]] = x;
 }
 
 // ----------------------------------------------------------- CGLS kernels
@@ -235,16 +340,20 @@ int blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + kT - 1) / kT); }
 
 // ------------------------------------------------------------------ plan
 struct Segment {
-  int kind;     // 0 R_s, 1 R_p, 2 Q_p
-  int count;    // ops
-  size_t first; // index in the device op array
-  int smem;     // dynamic shared memory
+  int kind;        // 0 R_s, 1 R_p, 2 Q_p
+  int n_small;     // ops with c <= 32 (one warp each), ids at small_ids
+  int n_large;     // ops with c > 32 (one CTA each), ids at large_ids
+  const int* small_ids;
+  const int* large_ids;
+  int smem;        // dynamic shared memory of the CTA kernels
 };
 
 struct ApplyPlan {
+  cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool fp32 = false;
   void* d_ops = nullptr;         // ApplyOp<TW>[nops] (factorization order)
   int32_t* d_idx = nullptr;      // slot index arrays
+  int* d_ids = nullptr;          // op ids of every segment (small ones, then large ones)
   std::vector<Segment> segs;     // factorization order
   cudaGraphExec_t graph = nullptr;
   double* d_scal = nullptr;
@@ -281,23 +390,47 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
   SPAQR_CUDA(cudaMalloc(&P.d_ops, std::max<size_t>(ops.size(), 1) * sizeof(ApplyOp<TW>)));
   SPAQR_CUDA(cudaMemcpy(P.d_ops, ops.data(), ops.size() * sizeof(ApplyOp<TW>), cudaMemcpyHostToDevice));
   // segments: consecutive ops with equal (kind, stage, round for R_s)
+  std::vector<int> ids;
+  struct Tmp {
+    int kind, ns, nl, maxc;
+    size_t s0, l0;
+  };
+  std::vector<Tmp> tmp;
   size_t i = 0;
   while (i < h.ops.size()) {
     size_t j = i + 1;
     const WOp& a = h.ops[i];
-    int maxc = a.c;
     while (j < h.ops.size() && h.ops[j].kind == a.kind && h.ops[j].stage == a.stage &&
-           (a.kind != 0 || h.ops[j].round == a.round)) {
-      maxc = std::max(maxc, h.ops[j].c);
+           (a.kind != 0 || h.ops[j].round == a.round))
       ++j;
-    }
-    Segment s;
-    s.kind = a.kind;
-    s.count = (int)(j - i);
-    s.first = i;
-    s.smem = (int)((size_t)maxc * (kW + 1) * sizeof(double));
-    P.segs.push_back(s);
+    Tmp t{a.kind, 0, 0, 0, 0, 0};
+    t.s0 = ids.size();
+    for (size_t q = i; q < j; ++q)
+      if (h.ops[q].c <= 32) {
+        ids.push_back((int)q);
+        t.ns++;
+      }
+    t.l0 = ids.size();
+    for (size_t q = i; q < j; ++q)
+      if (h.ops[q].c > 32) {
+        ids.push_back((int)q);
+        t.nl++;
+        t.maxc = std::max(t.maxc, h.ops[q].c);
+      }
+    tmp.push_back(t);
     i = j;
+  }
+  SPAQR_CUDA(cudaMalloc(&P.d_ids, std::max<size_t>(ids.size(), 1) * sizeof(int)));
+  SPAQR_CUDA(cudaMemcpy(P.d_ids, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice));
+  for (auto& t : tmp) {
+    Segment sg;
+    sg.kind = t.kind;
+    sg.n_small = t.ns;
+    sg.n_large = t.nl;
+    sg.small_ids = P.d_ids + t.s0;
+    sg.large_ids = P.d_ids + t.l0;
+    sg.smem = (int)((size_t)t.maxc * (kW + 1) * sizeof(double));
+    P.segs.push_back(sg);
   }
 }
 
@@ -321,6 +454,27 @@ void build_apply_plan(Handle& h) {
   cudaFuncSetAttribute(r_invT_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(q_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(q_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  for (auto& e : h.plan->ev) SPAQR_CUDA(cudaEventCreate(&e));
+  // algorithmic bytes of one W^{-1} plus one W^{-T} apply: every stored entry
+  // once per direction, the slot indices, and the slot-vector reads/writes
+  {
+    const double es = h.plan->fp32 ? 4.0 : 8.0;
+    double b = 0.0;
+    for (auto& op : h.ops) {
+      const double c = op.c, w = op.kind == 0 ? op.w : 0, k = op.k;
+      double stored = 0.0;
+      if (op.kind == 0)
+        stored = c * (c + 1) / 2 + c * w;
+      else if (op.kind == 1)
+        stored = c * (c + 1) / 2;
+      else
+        stored = c * k - k * (k - 1) / 2 + k;
+      b += 2 * es * stored + 2 * 4.0 * (c + w);
+      b += 8.0 * (c + w + c);      // W^{-1}: read z_s, z_n; write z_s
+      b += 8.0 * (2 * c + 2 * w);  // W^{-T}: read/write z_s, read/write z_n
+    }
+    h.stats.bytes_apply = b;
+  }
   const int64_t big = std::max(h.m, h.n);
   h.plan->part_n = blocks(big);
   SPAQR_CUDA(cudaMalloc(&h.plan->d_scal, 8 * sizeof(double)));
@@ -329,9 +483,12 @@ void build_apply_plan(Handle& h) {
 
 void free_apply_plan(Handle& h) {
   if (!h.plan) return;
+  for (auto& e : h.plan->ev)
+    if (e) cudaEventDestroy(e);
   if (h.plan->graph) cudaGraphExecDestroy(h.plan->graph);
   cudaFree(h.plan->d_ops);
   cudaFree(h.plan->d_idx);
+  cudaFree(h.plan->d_ids);
   cudaFree(h.plan->d_scal);
   cudaFree(h.plan->d_part);
   delete h.plan;
@@ -345,13 +502,23 @@ static void apply_t(Handle& h, double* z, int transpose) {
   const int nseg = (int)P.segs.size();
   for (int t = 0; t < nseg; ++t) {
     const Segment& s = P.segs[(size_t)(transpose ? t : nseg - 1 - t)];
-    const ApplyOp<TW>* o = ops + s.first;
-    if (s.kind == 2)
-      q_kernel<TW><<<s.count, kT, (size_t)s.smem, h.st>>>(o, z, transpose);
-    else if (transpose)
-      r_invT_kernel<TW><<<s.count, kT, (size_t)s.smem, h.st>>>(o, z);
-    else
-      r_inv_kernel<TW><<<s.count, kT, (size_t)s.smem, h.st>>>(o, z);
+    if (s.n_small) {
+      const int grid = (s.n_small + kW - 1) / kW;
+      if (s.kind == 2)
+        q_warp_kernel<TW><<<grid, kT, 0, h.st>>>(ops, s.small_ids, s.n_small, z, transpose);
+      else if (transpose)
+        r_invT_warp_kernel<TW><<<grid, kT, 0, h.st>>>(ops, s.small_ids, s.n_small, z);
+      else
+        r_inv_warp_kernel<TW><<<grid, kT, 0, h.st>>>(ops, s.small_ids, s.n_small, z);
+    }
+    if (s.n_large) {
+      if (s.kind == 2)
+        q_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z, transpose);
+      else if (transpose)
+        r_invT_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z);
+      else
+        r_inv_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z);
+    }
   }
   SPAQR_CUDA(cudaGetLastError());
 }
@@ -373,25 +540,56 @@ void apply_A(Handle& h, const double* x, double* y, int forward) {
   SPAQR_CUDA(cudaGetLastError());
 }
 
-// One CGLS iteration (everything on the stream, no host wait).
+// One CGLS iteration (everything on the stream, no host wait).  Events
+// ev[0..3] bracket the two W applies, ev[4..7] the two SpMVs.
 static void cgls_body(Handle& h, double* x, double* r, double* p, double* t, double* q, double* u, double* s,
-                      const double* Dv) {
+                      const double* Dv, bool capturing) {
   ApplyPlan& P = *h.plan;
+  // inside a stream capture an event record must be an external record node
+  auto rec = [&](cudaEvent_t e) {
+    SPAQR_CUDA(capturing ? cudaEventRecordWithFlags(e, h.st, cudaEventRecordExternal) : cudaEventRecord(e, h.st));
+  };
   const int64_t m = h.m, n = h.n;
   SPAQR_CUDA(cudaMemcpyAsync(t, p, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
+  rec(P.ev[0]);
   apply_Winv(h, t, 0);
+  rec(P.ev[1]);
+  rec(P.ev[4]);
   spmv_kernel<<<blocks(m), kT, 0, h.st>>>(m, h.d_rowptr, h.d_colidx, h.d_vals, t, q, nullptr, P.d_part);
+  rec(P.ev[5]);
   finish_sum_kernel<<<1, kT, 0, h.st>>>(blocks(m), P.d_part, P.d_scal + 1);
   update_xr_kernel<<<blocks(std::max(m, n)), kT, 0, h.st>>>(n, m, x, t, r, q, P.d_scal);
+  rec(P.ev[6]);
   spmv_kernel<<<blocks(n), kT, 0, h.st>>>(n, h.d_trowptr, h.d_tcolidx, h.d_tvals, r, u, Dv, P.d_part);
+  rec(P.ev[7]);
   finish_sum_kernel<<<1, kT, 0, h.st>>>(blocks(n), P.d_part, P.d_scal + 2);
   SPAQR_CUDA(cudaMemcpyAsync(s, u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
+  rec(P.ev[2]);
   apply_Winv(h, s, 1);
+  rec(P.ev[3]);
   sumsq_kernel<<<std::min(blocks(n), P.part_n), kT, 0, h.st>>>(n, s, P.d_part);
   finish_sum_kernel<<<1, kT, 0, h.st>>>(std::min(blocks(n), P.part_n), P.d_part, P.d_scal + 3);
   beta_kernel<<<1, 1, 0, h.st>>>(P.d_scal);
   update_p_kernel<<<blocks(n), kT, 0, h.st>>>(n, p, s, P.d_scal);
   SPAQR_CUDA(cudaGetLastError());
+}
+
+static void accumulate_solve_timers(Handle& h) {
+  ApplyPlan& P = *h.plan;
+  float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
+  if (cudaEventElapsedTime(&a, P.ev[0], P.ev[1]) == cudaSuccess &&
+      cudaEventElapsedTime(&b, P.ev[2], P.ev[3]) == cudaSuccess &&
+      cudaEventElapsedTime(&c, P.ev[4], P.ev[5]) == cudaSuccess &&
+      cudaEventElapsedTime(&d, P.ev[6], P.ev[7]) == cudaSuccess) {
+    h.stats.t_kernel[4] += (a + b) * 1e-3;
+    int64_t launches = 0;
+    for (auto& sg : P.segs) launches += (sg.n_small > 0) + (sg.n_large > 0);
+    h.stats.n_kernel[4] += 2 * launches;
+    h.stats.t_kernel[5] += (c + d) * 1e-3;
+    h.stats.n_kernel[5] += 2;
+  } else {
+    cudaGetLastError();
+  }
 }
 
 void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info) {
@@ -431,6 +629,8 @@ void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info)
   SPAQR_CUDA(cudaMemcpyAsync(&res0, P.d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost, h.st));
   SPAQR_CUDA(cudaStreamSynchronize(h.st));
   const double norm0 = std::sqrt(res0);
+  h.stats.t_kernel[4] = h.stats.t_kernel[5] = 0.0;
+  h.stats.n_kernel[4] = h.stats.n_kernel[5] = 0;
   int it = 0;
   double rel = norm0 > 0.0 ? 1.0 : 0.0;
   if (norm0 > 0.0) {
@@ -438,7 +638,7 @@ void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info)
     if (graphs && !P.graph) {
       cudaGraph_t g;
       SPAQR_CUDA(cudaStreamBeginCapture(h.st, cudaStreamCaptureModeThreadLocal));
-      cgls_body(h, xt, r, p, t, q, u, sv, Dinv_w);
+      cgls_body(h, xt, r, p, t, q, u, sv, Dinv_w, true);
       SPAQR_CUDA(cudaStreamEndCapture(h.st, &g));
       SPAQR_CUDA(cudaGraphInstantiate(&P.graph, g, 0));
       cudaGraphDestroy(g);
@@ -447,10 +647,11 @@ void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info)
       if (graphs)
         SPAQR_CUDA(cudaGraphLaunch(P.graph, h.st));
       else
-        cgls_body(h, xt, r, p, t, q, u, sv, Dinv_w);
+        cgls_body(h, xt, r, p, t, q, u, sv, Dinv_w, false);
       double res = 0.0;
       SPAQR_CUDA(cudaMemcpyAsync(&res, P.d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost, h.st));
       SPAQR_CUDA(cudaStreamSynchronize(h.st));
+      accumulate_solve_timers(h);
       rel = std::sqrt(res) / norm0;
       if (!(rel >= h.opt.tol)) break;
     }

@@ -112,3 +112,26 @@ def test_qrcp_large_matrix_global_path():
     if k < A.shape[0]:
         assert _rel(rows[0], ref) < 1e-10
     assert _rel(V[0], Vo) < 1e-10
+
+
+@pytest.mark.parametrize("m,n", [(50, 500), (100, 500), (100, 1000), (100, 2000), (100, 4000), (200, 4000),
+                                 (33, 7000), (300, 70)])
+def test_qrcp_every_cluster_size(m, n):
+    """Shapes chosen so that the planner uses 1, 2, 4, 8 and 16 CTAs per matrix
+    with the column slabs in shared memory, and 16 CTAs over a global copy."""
+    import paper_2102_09878_gb300 as sq
+
+    rng = np.random.default_rng(m * 7 + n)
+    r = min(m, n)
+    A = (rng.standard_normal((m, r)) * np.logspace(0, -9, r)) @ rng.standard_normal((r, n))
+    for eps in (0.0, 1e-6):
+        ranks, rows, V, T = sq.dense_qrcp([A], eps)
+        k, Xf, perm, Vo, To = dn.qrcp(A, eps)
+        assert ranks[0] == k, (ranks[0], k)
+        good = np.abs(np.diag(Xf[:k, :k])) > 1e-6 * abs(Xf[0, 0])
+        j = k if good.all() else int(np.argmin(good))
+        assert _rel(V[0][:, :j], Vo[:, :j]) < 1e-10 and _rel(T[0][:j], To[:j]) < 1e-10
+        if k < m:
+            ref = np.zeros((k, n))
+            ref[:, perm] = Xf[:k]
+            assert _rel(rows[0], ref) < 1e-9

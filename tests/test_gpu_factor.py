@@ -57,11 +57,12 @@ def test_direct_mode_fronts_match_oracle(grid64):
     _compare_ops(g.ops(), o.ops, 1e-11)
 
 
-def test_full_pipeline_eps0_matches_oracle(grid64):
+@pytest.mark.parametrize("rows", ["tree", "maxnorm"])
+def test_full_pipeline_eps0_matches_oracle(grid64, rows):
     import torch
 
-    o = OracleSpaQR(grid64, 6, 0.0).factor()
-    g = _gpu(grid64, 6, eps=0.0)
+    o = OracleSpaQR(grid64, 6, 0.0, rows=rows).factor()
+    g = _gpu(grid64, 6, eps=0.0, rows=rows)
     _compare_ops(g.ops(), o.ops, 1e-10)
     rng = np.random.default_rng(0)
     for _ in range(3):
@@ -80,11 +81,11 @@ def test_full_pipeline_eps0_matches_oracle(grid64):
     assert _rel(x, xo) < 1e-9
 
 
-@pytest.mark.parametrize("eps", [1e-4, 1e-2])
-def test_eps_solve_matches_oracle(grid64, eps):
-    o = OracleSpaQR(grid64, 6, eps).factor()
+@pytest.mark.parametrize("eps,rows", [(1e-4, "tree"), (1e-2, "tree"), (1e-4, "maxnorm")])
+def test_eps_solve_matches_oracle(grid64, eps, rows):
+    o = OracleSpaQR(grid64, 6, eps, rows=rows).factor()
     xo, io = o.solve(grid64.b)
-    g = _gpu(grid64, 6, eps=eps)
+    g = _gpu(grid64, 6, eps=eps, rows=rows)
     x = g.solve(grid64.b)
     A = grid64.to_scipy()
     rel = np.linalg.norm(A.T @ (A @ x - grid64.b)) / np.linalg.norm(A.T @ grid64.b)
