@@ -211,6 +211,27 @@ int spaqr_dense_front_qr(int count, double* const* A, const int* m, const int* n
 int spaqr_dense_qrcp(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
                      double* const* V, double* const* taus, int* rank, void* stream);
 
+/* spaqr_dense_qrcp_static: the same batched column-pivoted QR as
+ * spaqr_dense_qrcp (same arguments, same results), for callers that cannot
+ * allocate device memory: code that runs under a memory manager which owns
+ * all device memory (a framework's caching allocator, a fixed per-process
+ * budget), or latency-critical code that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree may cause.  The paper has no
+ * counterpart; it is a deployment variant of the Section 2.5 kernel.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: the
+ * descriptor array, the rank slots and the work copies of matrices too wide
+ * for shared memory live in one static device array of 4 MiB
+ * (4,194,304 bytes), reserved on every GPU that loads the library until the
+ * process exits.  A batch whose scratch exceeds it fails with
+ * SPAQR_ERR_CAPACITY and a message giving both sizes.  The first call on a
+ * device looks up the array's device address (with that device current);
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents; nothing in it needs to start at
+ * zero.  Calls that overlap on the GPU (other streams, other host threads)
+ * race on the array: serialise them.  Returns with `stream` synchronised. */
+int spaqr_dense_qrcp_static(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
+                            double* const* V, double* const* taus, int* rank, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -124,6 +124,11 @@ SIGNATURES = {
         [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
          C.c_void_p],
     ),
+    "spaqr_dense_qrcp_static": (
+        C.c_int,
+        [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+         C.c_void_p],
+    ),
 }
 
 _lib = None

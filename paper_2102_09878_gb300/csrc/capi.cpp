@@ -55,6 +55,8 @@ double secs_since(std::chrono::steady_clock::time_point t0) {
 }  // namespace
 
 namespace spaqr {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 void Handle::wait_caller() {
   if (!ev) SPAQR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   SPAQR_CUDA(cudaEventRecord(ev, user_st));

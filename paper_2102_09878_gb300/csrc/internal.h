@@ -180,6 +180,9 @@ struct Handle {
   ~Handle();
 };
 
+// Message returned by spaqr_last_error() on this thread (capi.cpp).
+void set_last_error(const std::string& msg);
+
 // Factorization entry (factor.cpp): fills h.ops, h.stats, device CSR.
 void run_factor(Handle& h, const spaqr_csr& A, const Analysis& an);
 // Apply / solve (solve.cu)
