@@ -467,31 +467,31 @@ __global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T
   const int kmax = m < n ? m : n;
   double r11 = 0.0;
   int k = 0;
-  for (int i = 0; i < kmax; ++i) {
-    // (1) local proposal
-    __syncthreads();
-    double bv = -1.0;
-    int bj = INT_MAX;
-    for (int c = threadIdx.x; c < nloc; c += kThreads) {
-      if (step_of[c] >= 0) continue;
-      const double v = nu[c];
-      if (v > bv) {  // ascending c: strict > keeps the lowest index on ties
-        bv = v;
-        bj = j0 + c;
-      }
+  __syncthreads();
+  // warp-local proposal of the warp's columns (c = warp + kW * (lane + 32 t))
+  double wv = -1.0;
+  int wj = INT_MAX;
+  for (int c = warp + lane * kWarps; c < nloc; c += 32 * kWarps) {
+    const double v = nu[c];
+    if (v > wv || (v == wv && j0 + c < wj)) {
+      wv = v;
+      wj = j0 + c;
     }
+  }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-      if (ov > bv || (ov == bv && oj < bj)) {
-        bv = ov;
-        bj = oj;
-      }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, wv, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
+    if (ov > wv || (ov == wv && oj < wj)) {
+      wv = ov;
+      wj = oj;
     }
+  }
+  for (int i = 0; i < kmax; ++i) {
+    // (1) local proposal: reduce the warps' proposals
     if (lane == 0) {
-      red_v[warp] = bv;
-      red_i[warp] = bj;
+      red_v[warp] = wv;
+      red_i[warp] = wj;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -506,21 +506,28 @@ __global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T
       cand_j = j;
     }
     cl.sync();  // (A) proposals visible cluster-wide
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // one lane per CTA of the cluster, then a warp reduction
       double v = -1.0;
       int j = INT_MAX;
-      for (int q = 0; q < CS; ++q) {
-        const double qv = *cl.map_shared_rank(&cand_v, q);
-        const int qj = *cl.map_shared_rank(&cand_j, q);
-        if (qv > v || (qv == v && qj < j)) {
-          v = qv;
-          j = qj;
+      if (lane < CS) {
+        v = *cl.map_shared_rank(&cand_v, lane);
+        j = *cl.map_shared_rank(&cand_j, lane);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+        if (ov > v || (ov == v && oj < j)) {
+          v = ov;
+          j = oj;
         }
       }
-      s_piv = j;
+      if (lane == 0) s_piv = j;
     }
     __syncthreads();
     const int p = s_piv;
+    if (p == INT_MAX) break;  // no proposal (non-finite norms): every CTA sees the same p
     const int owner = p / nl;
     if (rank == owner) {
       // reflector of column p, rows i..m-1 (warp 0), copied into vbuf
@@ -582,32 +589,70 @@ __global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T
     if (threadIdx.x == 0) taus[i] = tau;
     if (rank == owner && threadIdx.x == 0) step_of[p - j0] = i;
     __syncthreads();
-    if (tau != T(0)) {
-      for (int c = warp; c < nloc; c += kWarps) {
-        if (step_of[c] >= 0) continue;
+    // apply H_i to the warp's columns in chunks of 32 (warp-cooperative FP32
+    // updates), then downdate their squared norms lane-per-column in FP64
+    // (one FP64 instruction covers 32 columns), recompute the flagged ones
+    // warp-parallel, and form the warp's proposal for step i + 1
+    wv = -1.0;
+    wj = INT_MAX;
+    for (int base = warp; base < nloc; base += 32 * kWarps) {
+      for (int t = 0; t < 32; ++t) {
+        const int c = base + t * kWarps;
+        if (c >= nloc) break;
+        if (step_of[c] >= 0 || tau == T(0)) continue;
         T* col = X + (int64_t)c * m;
         T sacc = T(0);
         for (int r = i + 1 + lane; r < m; r += 32) sacc += vbuf[r - i] * col[r];
         sacc = warp_sum(sacc);
         const T w = tau * (col[i] + sacc);
+        __syncwarp();
         if (lane == 0) col[i] -= w;
         for (int r = i + 1 + lane; r < m; r += 32) col[r] -= w * vbuf[r - i];
       }
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < nloc; c += kThreads) {
-      if (step_of[c] >= 0) continue;
-      const double x = (double)X[i + (int64_t)c * m];
-      double v = nu[c] - x * x;
-      if (v < kRecompute * nuref[c]) {
-        v = 0.0;
-        for (int r = i + 1; r < m; ++r) {
-          const double y = (double)X[r + (int64_t)c * m];
-          v += y * y;
-        }
-        nuref[c] = v;
+      __syncwarp();
+      const int c = base + lane * kWarps;
+      const bool mine = c < nloc && step_of[c] < 0;
+      double v = -1.0;
+      bool redo = false;
+      if (mine) {
+        const double x = (double)X[i + (int64_t)c * m];
+        v = nu[c] - x * x;
+        redo = v < kRecompute * nuref[c];
       }
-      nu[c] = v;
+      unsigned flagged = __ballot_sync(0xffffffffu, redo);
+      while (flagged) {
+        const int l = __ffs(flagged) - 1;
+        flagged &= flagged - 1;
+        const int cc = base + l * kWarps;
+        const T* col = X + (int64_t)cc * m;
+        double sq = 0.0;
+        for (int r = i + 1 + lane; r < m; r += 32) {
+          const double y = (double)col[r];
+          sq += y * y;
+        }
+        sq = warp_sum(sq);
+        if (lane == l) {
+          v = sq;
+          nuref[cc] = sq;
+        }
+      }
+      if (mine) {
+        nu[c] = v;
+        if (v > wv || (v == wv && j0 + c < wj)) {
+          wv = v;
+          wj = j0 + c;
+        }
+      }
+    }
+    // warp reduction of the proposals (lowest column index on ties)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, wv, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
+      if (ov > wv || (ov == wv && oj < wj)) {
+        wv = ov;
+        wj = oj;
+      }
     }
     k = i + 1;
   }
@@ -690,6 +735,7 @@ __global__ void __launch_bounds__(kThreads) qrcp_warp_kernel(const QrcpDesc<T>* 
       }
     }
     const int p = bj;
+    if (p == INT_MAX) break;  // no proposal (non-finite norms)
     T* col = X + p * ld;
     double sig = 0.0;
     for (int r = i + 1 + lane; r < m; r += 32) {

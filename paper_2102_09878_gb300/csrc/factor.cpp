@@ -26,6 +26,7 @@
 //   separators with disjoint fronts; step 2 by a greedy colouring of
 //   "q in support(p1 of p)"; scaling and sparsification at stages k <= L - skip.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -34,6 +35,7 @@
 
 #include "internal.h"
 #include "kernels.h"
+#include "parallel.h"
 
 namespace spaqr {
 
@@ -297,7 +299,20 @@ class Factorizer {
     ++launches_;
     if (e != cudaSuccess) throw Error(SPAQR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   }
+  // host-side section timers (verbose output): 0 waits in sync, 1 index_groups,
+  // 2 eliminate planning, 3 eliminate new groups, 4 scale planning, 5 step2 planning, 6 merge planning
+  double ht_[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  struct HT {
+    double& acc;
+    double t0;
+    explicit HT(double& a) : acc(a), t0(now_s()) {}
+    ~HT() { acc += now_s() - t0; }
+    static double now_s() {
+      return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    }
+  };
   void sync() {
+    HT w(ht_[0]);
     SPAQR_CUDA(cudaStreamSynchronize(st_));
     ++up_.syncs;
     up_.reset();
@@ -515,6 +530,7 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
 
 template <typename T>
 void Factorizer<T>::index_groups(std::vector<std::vector<int>>& own, std::vector<std::vector<int>>& touch) {
+  HT ht(ht_[1]);
   const size_t nc = ccols_.size();
   own.assign(nc, {});
   touch.assign(nc, {});
@@ -547,26 +563,25 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
   }
   // column scaling (R1)
   std::vector<double> nrm((size_t)h_.n, 0.0);
-  for (int64_t e = 0; e < A.nnz; ++e) nrm[(size_t)A.colidx[e]] += A.vals[e] * A.vals[e];
+  for (int64_t e = 0; e < A.nnz; ++e) nrm[(size_t)A.colidx[e]] += A.vals[e] * A.vals[e];  // fixed order
   h_.D.resize((size_t)h_.n);
   for (int64_t j = 0; j < h_.n; ++j) {
     if (!(nrm[(size_t)j] > 0.0)) throw Error(SPAQR_ERR_RANK_DEFICIENT, "zero column " + std::to_string(j));
     h_.D[(size_t)j] = 1.0 / std::sqrt(nrm[(size_t)j]);
   }
-  // row owners by the max-norm rule on A D (R2), grouped by (owner, support)
+  // row owners by the max-norm rule on A D (R2), grouped by (owner, support);
+  // rows are independent: two parallel passes (support sizes, then contents)
   const int64_t M = A.m;
   std::vector<int32_t> owner((size_t)M);
   std::vector<int64_t> sptr((size_t)M + 1, 0);
   std::vector<int32_t> sups;
-  sups.reserve((size_t)A.nnz);
-  std::vector<int> tmp;
-  std::vector<double> sc;
-  for (int64_t r = 0; r < M; ++r) {
+  const bool tree = h_.opt.row_rule == SPAQR_ROWS_TREE;
+  auto row_support = [&](int64_t r, std::vector<int>& tmp, std::vector<double>& sc) -> int {
     tmp.clear();
     for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) tmp.push_back(cl_of[(size_t)A.colidx[e]]);
     std::sort(tmp.begin(), tmp.end());
     tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
-    if (tmp.empty()) throw Error(SPAQR_ERR_INVALID_ARG, "empty row " + std::to_string(r));
+    if (tmp.empty()) return -1;
     sc.assign(tmp.size(), 0.0);
     for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
       const int32_t j = A.colidx[e];
@@ -580,7 +595,7 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
     int best = -1;
     for (size_t t = 0; t < tmp.size(); ++t) {
       const int a = tmp[t];
-      if (h_.opt.row_rule == SPAQR_ROWS_TREE && level(a) != deep) continue;
+      if (tree && level(a) != deep) continue;
       if (best < 0) {
         best = (int)t;
         continue;
@@ -590,10 +605,35 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
           (sc[t] == sc[(size_t)best] && (level(a) > level(b) || (level(a) == level(b) && a < b))))
         best = (int)t;
     }
-    owner[(size_t)r] = tmp[(size_t)best];
-    sups.insert(sups.end(), tmp.begin(), tmp.end());
-    sptr[(size_t)r + 1] = (int64_t)sups.size();
-  }
+    return tmp[(size_t)best];
+  };
+  std::atomic<int64_t> empty_row{-1};
+  parallel_for(M, [&](int64_t b, int64_t e, int) {
+    std::vector<int> tmp;
+    std::vector<double> sc;
+    for (int64_t r = b; r < e; ++r) {
+      const int o = row_support(r, tmp, sc);
+      if (o < 0) {
+        empty_row.store(r);
+        continue;
+      }
+      owner[(size_t)r] = o;
+      sptr[(size_t)r + 1] = (int64_t)tmp.size();
+    }
+  });
+  if (empty_row.load() >= 0) throw Error(SPAQR_ERR_INVALID_ARG, "empty row " + std::to_string(empty_row.load()));
+  for (int64_t r = 0; r < M; ++r) sptr[(size_t)r + 1] += sptr[(size_t)r];
+  sups.resize((size_t)sptr[(size_t)M]);
+  parallel_for(M, [&](int64_t b, int64_t e, int) {
+    std::vector<int> tmp;
+    for (int64_t r = b; r < e; ++r) {
+      tmp.clear();
+      for (int64_t q = A.rowptr[r]; q < A.rowptr[r + 1]; ++q) tmp.push_back(cl_of[(size_t)A.colidx[q]]);
+      std::sort(tmp.begin(), tmp.end());
+      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+      std::copy(tmp.begin(), tmp.end(), sups.begin() + sptr[(size_t)r]);
+    }
+  });
   // counting sort by owner, then (support, row) inside an owner
   std::vector<int64_t> cnt(nc + 1, 0);
   for (int64_t r = 0; r < M; ++r) cnt[(size_t)owner[(size_t)r] + 1]++;
@@ -610,7 +650,9 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
     if (std::lexicographical_compare(pb, pb + lb, pa, pa + la)) return false;
     return a < b;
   };
-  for (size_t c = 0; c < nc; ++c) std::sort(order.begin() + cnt[c], order.begin() + cnt[c + 1], sup_less);
+  parallel_for((int64_t)nc, [&](int64_t b, int64_t e, int) {
+    for (int64_t c = b; c < e; ++c) std::sort(order.begin() + cnt[(size_t)c], order.begin() + cnt[(size_t)c + 1], sup_less);
+  }, 256);
   // groups
   std::vector<int> ids;
   std::vector<int32_t> grp_of_row((size_t)M), rowpos((size_t)M);
@@ -639,16 +681,18 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
   T* base = G_[(size_t)ids.front()].ptr;  // all initial groups share one buffer, in id order
   std::vector<int64_t> dest((size_t)A.nnz);
   std::vector<T> vals((size_t)A.nnz);
-  for (int64_t r = 0; r < M; ++r) {
-    const Group& g = G_[(size_t)grp_of_row[(size_t)r]];
-    const int64_t gbase = g.ptr - base;
-    for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
-      const int32_t jcol = A.colidx[e];
-      const int co = col_off(g, cl_of[(size_t)jcol]) + pos_of[(size_t)jcol];
-      dest[(size_t)e] = gbase + rowpos[(size_t)r] + (int64_t)co * g.ld;
-      vals[(size_t)e] = (T)(A.vals[e] * h_.D[(size_t)jcol]);
+  parallel_for(M, [&](int64_t b, int64_t e0, int) {
+    for (int64_t r = b; r < e0; ++r) {
+      const Group& g = G_[(size_t)grp_of_row[(size_t)r]];
+      const int64_t gbase = g.ptr - base;
+      for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
+        const int32_t jcol = A.colidx[e];
+        const int co = col_off(g, cl_of[(size_t)jcol]) + pos_of[(size_t)jcol];
+        dest[(size_t)e] = gbase + rowpos[(size_t)r] + (int64_t)co * g.ld;
+        vals[(size_t)e] = (T)(A.vals[e] * h_.D[(size_t)jcol]);
+      }
     }
-  }
+  });
   int64_t* d_dest = static_cast<int64_t*>(pool_.alloc(dest.size() * sizeof(int64_t)));
   T* d_vals = static_cast<T*>(pool_.alloc(vals.size() * sizeof(T)));
   SPAQR_CUDA(cudaMemcpyAsync(d_dest, dest.data(), dest.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st_));
@@ -713,6 +757,7 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   std::vector<FrontInfo> fi(batch.size());
   size_t ws = 0, ndest = 0;
   std::vector<CopyDesc<T>> gat;
+  double plan_t0 = HT::now_s();
   for (size_t b = 0; b < batch.size(); ++b) {
     const int s = batch[b].first;
     const auto& fg = batch[b].second;
@@ -766,6 +811,7 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
     }
     fr.push_back(FrontDesc<T>{F, f.m, f.n, f.c, f.m});
   }
+  ht_[2] += HT::now_s() - plan_t0;
   copies(gat);
   front_qr(fr);
   // extra-row destinations (max-norm rule over the remaining front clusters)
@@ -848,6 +894,7 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   }
   sync();
   // new groups: returned rows per owner, then extra rows per destination
+  HT ht_new(ht_[3]);
   std::vector<int> ids;
   struct Pending {
     int id;
@@ -919,6 +966,7 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
 // ---------------------------------------------------------------- scale
 template <typename T>
 void Factorizer<T>::scale() {
+  HT ht(ht_[4]);
   std::vector<std::vector<int>> own, touch;
   index_groups(own, touch);
   p1_of_.assign(ccols_.size(), -1);
@@ -1114,6 +1162,7 @@ void Factorizer<T>::step1() {
 // ---------------------------------------------------------------- step 2
 template <typename T>
 void Factorizer<T>::step2() {
+  HT ht(ht_[5]);
   std::vector<int> ps;
   for (size_t p = 0; p < ccols_.size(); ++p)
     if (!p1_of_.empty() && p1_of_[p] >= 0) ps.push_back((int)p);
@@ -1146,6 +1195,9 @@ void Factorizer<T>::step2() {
   }
   std::vector<std::vector<int>> own, touch;
   index_groups(own, touch);
+  // one device rank slot per interface of this phase, read back with a single copy
+  int* kdev_all = static_cast<int*>(h_.wpool.alloc(ps.size() * sizeof(int)));
+  size_t kdev_next = 0;
   struct P2 {
     int p;
     size_t op;
@@ -1223,7 +1275,7 @@ void Factorizer<T>::step2() {
       T* tau = wstore((size_t)std::max(kmax, 1));
       op.V = V;
       op.tau = tau;
-      op.kdev = static_cast<int*>(h_.wpool.alloc(sizeof(int)));
+      op.kdev = kdev_all + kdev_next++;
       qs.push_back(QrcpDesc<T>{Mp, nullptr, nullptr, V, tau, op.kdev, x.cp, ncm, x.cp, x.cp});
       for (int g : x.nb) {
         const Group& gg = G_[(size_t)g];
@@ -1257,10 +1309,12 @@ void Factorizer<T>::step2() {
     pool_.release(M);
   }
   // ranks back; keep the ops that drop something
-  std::vector<int> ks(recs.size());
-  for (size_t i = 0; i < recs.size(); ++i)
-    SPAQR_CUDA(cudaMemcpyAsync(&ks[i], h_.ops[recs[i].op].kdev, sizeof(int), cudaMemcpyDeviceToHost, st_));
+  std::vector<int> kall(std::max<size_t>(kdev_next, 1));
+  if (kdev_next)
+    SPAQR_CUDA(cudaMemcpyAsync(kall.data(), kdev_all, kdev_next * sizeof(int), cudaMemcpyDeviceToHost, st_));
   sync();
+  std::vector<int> ks(recs.size());
+  for (size_t i = 0; i < recs.size(); ++i) ks[i] = kall[(size_t)(h_.ops[recs[i].op].kdev - kdev_all)];
   for (T* w : work_all) pool_.release(w);
   std::vector<char> drop(h_.ops.size(), 0);
   for (size_t i = 0; i < recs.size(); ++i) {
@@ -1300,6 +1354,7 @@ void Factorizer<T>::step2() {
 // ---------------------------------------------------------------- merge
 template <typename T>
 void Factorizer<T>::merge() {
+  HT ht(ht_[6]);
   const StageClusters& nxt = an_.stages[(size_t)k_ - 1];
   const size_t nnew = nxt.node.size();
   std::vector<int> nccols(nnew, 0);
@@ -1439,6 +1494,7 @@ void Factorizer<T>::run(const spaqr_csr& A) {
   init_stage(A);
   double tp[6] = {0, 0, 0, 0, 0, 0};
   tp[1] = now() - t0;
+  double kt_prev[6] = {0, 0, 0, 0, 0, 0};
   for (k_ = L_; k_ >= 1; --k_) {
     double a = now();
     eliminate();
@@ -1470,12 +1526,21 @@ void Factorizer<T>::run(const spaqr_csr& A) {
                    k_, g.fronts, g.rounds, g.max_m, g.max_n, g.max_c, g.scaled, g.max_rp, g.s1, g.s1_max_m, g.s1_max_n,
                    g.s2, g.colours, g.s2_max_c, g.s2_max_w, (long long)g.sum_k, (long long)g.sum_c, live,
                    pool_.in_use() / 1e6);
+      std::fprintf(stderr, "[spaqr]           device ms: copy %.2f front %.2f qrcp %.2f other %.2f\n",
+                   1e3 * (h_.stats.t_kernel[0] - kt_prev[0]), 1e3 * (h_.stats.t_kernel[1] - kt_prev[1]),
+                   1e3 * (h_.stats.t_kernel[2] - kt_prev[2]), 1e3 * (h_.stats.t_kernel[3] - kt_prev[3]));
+      for (int q = 0; q < 6; ++q) kt_prev[q] = h_.stats.t_kernel[q];
     }
     slog_ = StageLog();
   }
   sync();
   if (!live().empty()) throw Error(SPAQR_ERR_CUDA, "internal: rows left after the root");
   for (int i = 0; i < 6; ++i) h_.stats.t_phase[i] = tp[i];
+  if (h_.opt.verbose)
+    std::fprintf(stderr,
+                 "[spaqr] host: waits %.3f s | index %.3f | elim plan %.3f | elim groups %.3f | scale %.3f | step2 "
+                 "%.3f | merge %.3f (scale/step2/merge include their waits)\n",
+                 ht_[0], ht_[1], ht_[2], ht_[3], ht_[4], ht_[5], ht_[6]);
   h_.stats.launches = launches_;
   h_.stats.syncs = up_.syncs;
   (void)t0;

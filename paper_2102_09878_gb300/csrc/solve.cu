@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "internal.h"
@@ -23,13 +24,18 @@ constexpr int kT = 256;
 constexpr int kW = kT / 32;
 
 template <typename TW>
+constexpr size_t kWarpSmem = (size_t)kW * 32 * 33 * sizeof(TW);  // staged R_ss per warp
+
+template <typename TW>
 struct ApplyOp {
   const TW* R;  // kind 0: c x (c + w) = [R_ss R_sn]; kind 1: c x c
+  const TW* Qx; // kind 2, c > 32: explicit Q_pp (c x c, ld c)
   const TW* V;
   const TW* tau;
   const int* kdev;
   const int32_t* slots;
   const int32_t* nslots;
+  const double* rdiag;  // kinds 0, 1: 1 / R_ii (FP64), computed once when the plan is built
   int c, w;
 };
 
@@ -40,30 +46,42 @@ __device__ __forceinline__ double wsum(double v) {
 }
 
 // Back substitution R y = rhs (R upper, ld c) on a shared vector y of length c,
-// blocked by 32 rows: warp 0 solves each diagonal block with shuffles, then all
-// threads update the rows above it.  Two block barriers per 32 rows.
+// blocked by 32 rows: the 32 x 32 diagonal block is staged in shared memory
+// (blk, 33 x 32 doubles) with parallel loads, warp 0 solves it with shuffles
+// and the precomputed reciprocals, then all threads update the rows above.
 template <typename TW>
-__device__ void upper_solve(const TW* R, int c, double* y) {
+__device__ void upper_solve(const TW* R, const double* rdiag, int c, double* y, double* blk) {
   const int lane = threadIdx.x & 31;
   for (int hi = c; hi > 0; hi -= 32) {
     const int lo = hi > 32 ? hi - 32 : 0;
+    const int bs = hi - lo;
     __syncthreads();
-    if (threadIdx.x < 32) {
-      const int i = lo + lane;
-      double x = i < hi ? y[i] : 0.0;
-      for (int j = hi - 1; j >= lo; --j) {
-        const double yj = __shfl_sync(0xffffffffu, x, j - lo) / (double)R[j + (int64_t)j * c];
-        if (i == j) x = yj;
-        if (i < j) x -= (double)R[i + (int64_t)j * c] * yj;
-      }
-      if (i < hi) y[i] = x;
+    for (int e = threadIdx.x; e < bs * bs; e += kT) {
+      const int r = e % bs, q = e / bs;  // coalesced over rows
+      blk[r * 33 + q] = (double)R[(lo + r) + (int64_t)(lo + q) * c];
     }
     __syncthreads();
-    // rows above the block: y[i] -= sum_{j in [lo, hi)} R[i, j] y[j]
+    if (threadIdx.x < 32) {
+      const int r = lane;
+      double x = r < bs ? y[lo + r] : 0.0;
+      const double rd = r < bs ? rdiag[lo + r] : 0.0;
+      for (int q = bs - 1; q >= 0; --q) {
+        const double yq = __shfl_sync(0xffffffffu, x, q) * __shfl_sync(0xffffffffu, rd, q);
+        if (r == q) x = yq;
+        if (r < q) x -= blk[r * 33 + q] * yq;
+      }
+      if (r < bs) y[lo + r] = x;
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < lo; i += kT) {
-      double acc = 0.0;
-      for (int j = lo; j < hi; ++j) acc += (double)R[i + (int64_t)j * c] * y[j];
-      y[i] -= acc;
+      double a0 = 0.0, a1 = 0.0;
+      int j = lo;
+      for (; j + 1 < hi; j += 2) {
+        a0 += (double)R[i + (int64_t)j * c] * y[j];
+        a1 += (double)R[i + (int64_t)(j + 1) * c] * y[j + 1];
+      }
+      if (j < hi) a0 += (double)R[i + (int64_t)j * c] * y[j];
+      y[i] -= a0 + a1;
     }
   }
   __syncthreads();
@@ -71,27 +89,39 @@ __device__ void upper_solve(const TW* R, int c, double* y) {
 
 // Forward substitution R^T y = rhs, blocked the same way.
 template <typename TW>
-__device__ void lower_t_solve(const TW* R, int c, double* y) {
+__device__ void lower_t_solve(const TW* R, const double* rdiag, int c, double* y, double* blk) {
   const int lane = threadIdx.x & 31;
   for (int lo = 0; lo < c; lo += 32) {
     const int hi = lo + 32 < c ? lo + 32 : c;
+    const int bs = hi - lo;
     __syncthreads();
-    if (threadIdx.x < 32) {
-      const int i = lo + lane;
-      double x = i < hi ? y[i] : 0.0;
-      for (int j = lo; j < hi; ++j) {
-        const double yj = __shfl_sync(0xffffffffu, x, j - lo) / (double)R[j + (int64_t)j * c];
-        if (i == j) x = yj;
-        if (i > j && i < hi) x -= (double)R[j + (int64_t)i * c] * yj;
-      }
-      if (i < hi) y[i] = x;
+    for (int e = threadIdx.x; e < bs * bs; e += kT) {
+      const int r = e % bs, q = e / bs;
+      blk[r * 33 + q] = (double)R[(lo + r) + (int64_t)(lo + q) * c];
     }
     __syncthreads();
-    // rows below the block: y[i] -= sum_{j in [lo, hi)} R[j, i] y[j]
+    if (threadIdx.x < 32) {
+      const int r = lane;
+      double x = r < bs ? y[lo + r] : 0.0;
+      const double rd = r < bs ? rdiag[lo + r] : 0.0;
+      for (int q = 0; q < bs; ++q) {
+        const double yq = __shfl_sync(0xffffffffu, x, q) * __shfl_sync(0xffffffffu, rd, q);
+        if (r == q) x = yq;
+        if (r > q && r < bs) x -= blk[q * 33 + r] * yq;
+      }
+      if (r < bs) y[lo + r] = x;
+    }
+    __syncthreads();
     for (int i = hi + threadIdx.x; i < c; i += kT) {
-      double acc = 0.0;
-      for (int j = lo; j < hi; ++j) acc += (double)R[j + (int64_t)i * c] * y[j];
-      y[i] -= acc;
+      const TW* col = R + (int64_t)i * c;
+      double a0 = 0.0, a1 = 0.0;
+      int j = lo;
+      for (; j + 1 < hi; j += 2) {
+        a0 += (double)col[j] * y[j];
+        a1 += (double)col[j + 1] * y[j + 1];
+      }
+      if (j < hi) a0 += (double)col[j] * y[j];
+      y[i] -= a0 + a1;
     }
   }
   __syncthreads();
@@ -104,6 +134,7 @@ __global__ void __launch_bounds__(kT) r_inv_kernel(const ApplyOp<TW>* ops, const
   extern __shared__ double sh[];
   double* y = sh;          // c
   double* part = sh + op.c;  // kW * c partials
+  __shared__ double blk[33 * 32];
   const int c = op.c, w = op.w;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kW * c; i += kT) part[i] = 0.0;
@@ -126,7 +157,7 @@ __global__ void __launch_bounds__(kT) r_inv_kernel(const ApplyOp<TW>* ops, const
     for (int q = 0; q < kW; ++q) s -= part[q * c + i];
     y[i] = s;
   }
-  upper_solve(op.R, c, y);
+  upper_solve(op.R, op.rdiag, c, y, blk);
   for (int i = threadIdx.x; i < c; i += kT) z[op.slots[i]] = y[i];
 }
 
@@ -136,9 +167,10 @@ __global__ void __launch_bounds__(kT) r_invT_kernel(const ApplyOp<TW>* ops, cons
   const ApplyOp<TW> op = ops[ids[blockIdx.x]];
   extern __shared__ double sh[];
   double* y = sh;
+  __shared__ double blk[33 * 32];
   const int c = op.c, w = op.w;
   for (int i = threadIdx.x; i < c; i += kT) y[i] = z[op.slots[i]];
-  lower_t_solve(op.R, c, y);
+  lower_t_solve(op.R, op.rdiag, c, y, blk);
   for (int i = threadIdx.x; i < c; i += kT) z[op.slots[i]] = y[i];
   if (w > 0) {
     const TW* Rn = op.R + (int64_t)c * c;
@@ -153,34 +185,76 @@ __global__ void __launch_bounds__(kT) r_invT_kernel(const ApplyOp<TW>* ops, cons
   }
 }
 
-// z_p <- Q z_p (inverse = 0: apply H_k first ... H_1 last; used by W^{-1})
-// z_p <- Q^T z_p (apply H_1 first; used by W^{-T})
+// Large Q_p ops use the explicit Q_pp formed after the factorization:
+// W^{-1}: z_p <- Q_pp z_p;  W^{-T}: z_p <- Q_pp^T z_p  (one coalesced GEMV each).
 template <typename TW>
 __global__ void __launch_bounds__(kT) q_kernel(const ApplyOp<TW>* ops, const int* ids, double* z, int transpose) {
   const ApplyOp<TW> op = ops[ids[blockIdx.x]];
   extern __shared__ double sh[];
-  double* y = sh;
-  __shared__ double red[kW];
+  double* x = sh;
+  const int c = op.c;
+  for (int i = threadIdx.x; i < c; i += kT) x[i] = z[op.slots[i]];
+  __syncthreads();
+  if (!transpose) {
+    // y_i = sum_j Q[i, j] x_j: thread per row, columns in order (coalesced over i)
+    for (int i0 = 0; i0 < c; i0 += kT) {
+      const int i = i0 + threadIdx.x;
+      if (i >= c) continue;
+      double acc = 0.0;
+      for (int j = 0; j < c; ++j) acc += (double)op.Qx[i + (int64_t)j * c] * x[j];
+      z[op.slots[i]] = acc;
+    }
+  } else {
+    // y_j = sum_i Q[i, j] x_i: warp per column, lanes over i (coalesced)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < c; j += kW) {
+      const TW* col = op.Qx + (int64_t)j * c;
+      double acc = 0.0;
+      for (int i = lane; i < c; i += 32) acc += (double)col[i] * x[i];
+      acc = wsum(acc);
+      if (lane == 0) z[op.slots[j]] = acc;
+    }
+  }
+}
+
+// 1 / R_ii for every triangular op (one warp per op).
+template <typename TW>
+__global__ void __launch_bounds__(kT) recip_diag_kernel(const ApplyOp<TW>* ops, int nops) {
+  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
+  if (gw >= nops) return;
+  const ApplyOp<TW> op = ops[gw];
+  if (!op.rdiag) return;
+  double* rd = const_cast<double*>(op.rdiag);
+  for (int i = threadIdx.x & 31; i < op.c; i += 32) rd[i] = 1.0 / (double)op.R[i + (int64_t)i * op.c];
+}
+
+// Q = H_1 ... H_k applied to the identity, 32 columns per CTA (one warp per
+// column at a time, the column held in shared memory).
+template <typename TW>
+__global__ void __launch_bounds__(kT) form_q_kernel(const ApplyOp<TW>* ops, const int* ids, TW* const* outs) {
+  const ApplyOp<TW> op = ops[ids[blockIdx.y]];
+  TW* Q = outs[blockIdx.y];
   const int c = op.c;
   const int k = *op.kdev;
-  for (int i = threadIdx.x; i < c; i += kT) y[i] = z[op.slots[i]];
-  __syncthreads();
+  extern __shared__ double sh[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int t = 0; t < k; ++t) {
-    const int i = transpose ? t : k - 1 - t;
-    const TW* v = op.V + (int64_t)i * c;
-    double s = 0.0;
-    for (int l = i + threadIdx.x; l < c; l += kT) s += (l == i ? 1.0 : (double)v[l]) * y[l];
-    s = wsum(s);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    double tot = 0.0;
-    for (int q = 0; q < kW; ++q) tot += red[q];
-    tot *= (double)op.tau[i];
-    for (int l = i + threadIdx.x; l < c; l += kT) y[l] -= tot * (l == i ? 1.0 : (double)v[l]);
-    __syncthreads();
+  double* y = sh + (size_t)warp * c;
+  for (int jj = warp; jj < 32; jj += kW) {
+    const int j = blockIdx.x * 32 + jj;
+    if (j >= c) break;
+    for (int i = lane; i < c; i += 32) y[i] = (i == j) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int t = k - 1; t >= 0; --t) {  // Q e_j = H_1 (H_2 (... H_k e_j))
+      const TW* v = op.V + (int64_t)t * c;
+      double d = 0.0;
+      for (int i = t + lane; i < c; i += 32) d += (i == t ? 1.0 : (double)v[i]) * y[i];
+      d = wsum(d) * (double)op.tau[t];
+      for (int i = t + lane; i < c; i += 32) y[i] -= d * (i == t ? 1.0 : (double)v[i]);
+      __syncwarp();
+    }
+    for (int i = lane; i < c; i += 32) Q[i + (int64_t)j * c] = (TW)y[i];
+    __syncwarp();
   }
-  for (int i = threadIdx.x; i < c; i += kT) z[op.slots[i]] = y[i];
 }
 
 // ------------------------------------------- warp-per-op kernels (c <= 32)
@@ -207,10 +281,17 @@ __global__ void __launch_bounds__(kT) r_inv_warp_kernel(const ApplyOp<TW>* ops, 
     }
     x -= acc;
   }
+  // stage R_ss (c x c) in this warp's shared region, then the back substitution
+  extern __shared__ __align__(16) unsigned char wsm[];
+  TW* B = reinterpret_cast<TW*>(wsm) + (size_t)(threadIdx.x >> 5) * (32 * 33);
+  for (int q = 0; q < c; ++q)
+    if (lane < c) B[lane * 33 + q] = op.R[lane + (int64_t)q * c];
+  const double rd = lane < c ? op.rdiag[lane] : 0.0;
+  __syncwarp();
   for (int j = c - 1; j >= 0; --j) {
-    const double yj = __shfl_sync(0xffffffffu, x, j) / (double)op.R[j + (int64_t)j * c];
+    const double yj = __shfl_sync(0xffffffffu, x, j) * __shfl_sync(0xffffffffu, rd, j);
     if (lane == j) x = yj;
-    if (lane < j) x -= (double)op.R[lane + (int64_t)j * c] * yj;
+    if (lane < j) x -= (double)B[lane * 33 + j] * yj;
   }
   if (lane < c) z[op.slots[lane]] = x;
 }
@@ -223,10 +304,16 @@ __global__ void __launch_bounds__(kT) r_invT_warp_kernel(const ApplyOp<TW>* ops,
   const ApplyOp<TW> op = ops[ids[gw]];
   const int lane = threadIdx.x & 31, c = op.c, w = op.w;
   double x = lane < c ? z[op.slots[lane]] : 0.0;
+  extern __shared__ __align__(16) unsigned char wsm[];
+  TW* B = reinterpret_cast<TW*>(wsm) + (size_t)(threadIdx.x >> 5) * (32 * 33);
+  for (int q = 0; q < c; ++q)
+    if (lane < c) B[lane * 33 + q] = op.R[lane + (int64_t)q * c];
+  const double rd = lane < c ? op.rdiag[lane] : 0.0;
+  __syncwarp();
   for (int i = 0; i < c; ++i) {
-    const double yi = __shfl_sync(0xffffffffu, x, i) / (double)op.R[i + (int64_t)i * c];
+    const double yi = __shfl_sync(0xffffffffu, x, i) * __shfl_sync(0xffffffffu, rd, i);
     if (lane == i) x = yi;
-    if (lane > i && lane < c) x -= (double)op.R[i + (int64_t)lane * c] * yi;
+    if (lane > i && lane < c) x -= (double)B[i * 33 + lane] * yi;
   }
   if (lane < c) z[op.slots[lane]] = x;
   if (w > 0) {
@@ -350,6 +437,7 @@ struct Segment {
 
 struct ApplyPlan {
   cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* d_rdiag = nullptr;     // 1 / R_ii of every R_s and R_p op
   bool fp32 = false;
   void* d_ops = nullptr;         // ApplyOp<TW>[nops] (factorization order)
   int32_t* d_idx = nullptr;      // slot index arrays
@@ -360,6 +448,17 @@ struct ApplyPlan {
   double* d_part = nullptr;
   int part_n = 0;
 };
+
+// Allow a kernel the opt-in shared memory minus its static footprint.
+template <typename K>
+static void set_dyn_smem(K kernel) {
+  int dev = 0, mx = 0;
+  SPAQR_CUDA(cudaGetDevice(&dev));
+  SPAQR_CUDA(cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  SPAQR_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  SPAQR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes));
+}
 
 template <typename TW>
 static void build_plan_t(Handle& h, ApplyPlan& P) {
@@ -374,10 +473,20 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
   }
   SPAQR_CUDA(cudaMalloc(&P.d_idx, std::max<size_t>(idx.size(), 1) * sizeof(int32_t)));
   SPAQR_CUDA(cudaMemcpy(P.d_idx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  std::vector<size_t> roff(h.ops.size(), 0);
+  size_t nrd = 0;
+  for (size_t i = 0; i < h.ops.size(); ++i)
+    if (h.ops[i].kind != 2) {
+      roff[i] = nrd;
+      nrd += (size_t)h.ops[i].c;
+    }
+  SPAQR_CUDA(cudaMalloc(&P.d_rdiag, std::max<size_t>(nrd, 1) * sizeof(double)));
   for (size_t i = 0; i < h.ops.size(); ++i) {
     const WOp& op = h.ops[i];
     ApplyOp<TW> a{};
+    a.rdiag = op.kind != 2 ? P.d_rdiag + roff[i] : nullptr;
     a.R = static_cast<const TW*>(op.R);
+    a.Qx = static_cast<const TW*>(op.Qx);
     a.V = static_cast<const TW*>(op.V);
     a.tau = static_cast<const TW*>(op.tau);
     a.kdev = op.kdev;
@@ -387,8 +496,49 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
     a.w = op.kind == 0 ? op.w : 0;
     ops.push_back(a);
   }
+  // explicit Q_pp for the Q_p ops too wide for one warp
+  std::vector<int> qids;
+  std::vector<TW*> qouts;
+  int qmax = 0;
+  for (size_t i = 0; i < h.ops.size(); ++i) {
+    WOp& op = h.ops[i];
+    if (op.kind != 2 || op.c <= 32) continue;
+    op.Qx = h.wpool.alloc((size_t)op.c * op.c * sizeof(TW));
+    ops[i].Qx = static_cast<const TW*>(op.Qx);
+    qids.push_back((int)i);
+    qouts.push_back(static_cast<TW*>(op.Qx));
+    qmax = std::max(qmax, op.c);
+  }
   SPAQR_CUDA(cudaMalloc(&P.d_ops, std::max<size_t>(ops.size(), 1) * sizeof(ApplyOp<TW>)));
   SPAQR_CUDA(cudaMemcpy(P.d_ops, ops.data(), ops.size() * sizeof(ApplyOp<TW>), cudaMemcpyHostToDevice));
+  if (nrd) {
+    recip_diag_kernel<TW><<<(unsigned)((h.ops.size() + kW - 1) / kW), kT, 0, h.st>>>(
+        static_cast<const ApplyOp<TW>*>(P.d_ops), (int)h.ops.size());
+    SPAQR_CUDA(cudaGetLastError());
+  }
+  if (!qids.empty()) {
+    int* d_q = nullptr;
+    TW** d_out = nullptr;
+    SPAQR_CUDA(cudaMalloc(&d_q, qids.size() * sizeof(int)));
+    SPAQR_CUDA(cudaMalloc(&d_out, qouts.size() * sizeof(TW*)));
+    SPAQR_CUDA(cudaMemcpy(d_q, qids.data(), qids.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SPAQR_CUDA(cudaMemcpy(d_out, qouts.data(), qouts.size() * sizeof(TW*), cudaMemcpyHostToDevice));
+    const size_t smem = (size_t)qmax * kW * sizeof(double);
+    int mx = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((int)smem > mx - 1024) throw Error(SPAQR_ERR_CAPACITY, "apply: Q_pp too large to form");
+    set_dyn_smem(form_q_kernel<TW>);
+    for (size_t b0 = 0; b0 < qids.size(); b0 += 65535) {
+      const unsigned nb = (unsigned)std::min<size_t>(65535, qids.size() - b0);
+      form_q_kernel<TW><<<dim3((unsigned)((qmax + 31) / 32), nb), kT, smem, h.st>>>(
+          static_cast<const ApplyOp<TW>*>(P.d_ops), d_q + b0, d_out + b0);
+      SPAQR_CUDA(cudaGetLastError());
+    }
+    SPAQR_CUDA(cudaStreamSynchronize(h.st));
+    cudaFree(d_q);
+    cudaFree(d_out);
+  }
   // segments: consecutive ops with equal (kind, stage, round for R_s)
   std::vector<int> ids;
   struct Tmp {
@@ -448,12 +598,16 @@ void build_apply_plan(Handle& h) {
   mx -= 1024;  // margin for the kernels' static shared memory
   for (auto& s : h.plan->segs)
     if (s.smem > mx) throw Error(SPAQR_ERR_CAPACITY, "apply: cluster too large for shared memory");
-  cudaFuncSetAttribute(r_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(r_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(r_invT_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(r_invT_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(q_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(q_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  set_dyn_smem(r_inv_kernel<double>);
+  set_dyn_smem(r_inv_kernel<float>);
+  set_dyn_smem(r_invT_kernel<double>);
+  set_dyn_smem(r_invT_kernel<float>);
+  set_dyn_smem(q_kernel<double>);
+  set_dyn_smem(q_kernel<float>);
+  set_dyn_smem(r_inv_warp_kernel<double>);
+  set_dyn_smem(r_invT_warp_kernel<double>);
+  set_dyn_smem(r_inv_warp_kernel<float>);
+  set_dyn_smem(r_invT_warp_kernel<float>);
   for (auto& e : h.plan->ev) SPAQR_CUDA(cudaEventCreate(&e));
   // algorithmic bytes of one W^{-1} plus one W^{-T} apply: every stored entry
   // once per direction, the slot indices, and the slot-vector reads/writes
@@ -489,6 +643,7 @@ void free_apply_plan(Handle& h) {
   cudaFree(h.plan->d_ops);
   cudaFree(h.plan->d_idx);
   cudaFree(h.plan->d_ids);
+  cudaFree(h.plan->d_rdiag);
   cudaFree(h.plan->d_scal);
   cudaFree(h.plan->d_part);
   delete h.plan;
@@ -507,9 +662,9 @@ static void apply_t(Handle& h, double* z, int transpose) {
       if (s.kind == 2)
         q_warp_kernel<TW><<<grid, kT, 0, h.st>>>(ops, s.small_ids, s.n_small, z, transpose);
       else if (transpose)
-        r_invT_warp_kernel<TW><<<grid, kT, 0, h.st>>>(ops, s.small_ids, s.n_small, z);
+        r_invT_warp_kernel<TW><<<grid, kT, kWarpSmem<TW>, h.st>>>(ops, s.small_ids, s.n_small, z);
       else
-        r_inv_warp_kernel<TW><<<grid, kT, 0, h.st>>>(ops, s.small_ids, s.n_small, z);
+        r_inv_warp_kernel<TW><<<grid, kT, kWarpSmem<TW>, h.st>>>(ops, s.small_ids, s.n_small, z);
     }
     if (s.n_large) {
       if (s.kind == 2)
@@ -521,6 +676,63 @@ static void apply_t(Handle& h, double* z, int transpose) {
     }
   }
   SPAQR_CUDA(cudaGetLastError());
+}
+
+// Diagnostic (SPAQR_PROFILE_APPLY=1): one W^{-1} and one W^{-T} with CUDA events
+// around every segment, printed to stderr as stage/kind/ops/microseconds.
+template <typename TW>
+static void profile_apply_t(Handle& h, double* z) {
+  ApplyPlan& P = *h.plan;
+  const ApplyOp<TW>* ops = static_cast<const ApplyOp<TW>*>(P.d_ops);
+  const int nseg = (int)P.segs.size();
+  std::vector<cudaEvent_t> ev(2 * (size_t)nseg + 2);
+  for (auto& e : ev) SPAQR_CUDA(cudaEventCreate(&e));
+  for (int transpose = 0; transpose < 2; ++transpose) {
+    for (int t = 0; t < nseg; ++t) {
+      const int si = transpose ? t : nseg - 1 - t;
+      const Segment& s = P.segs[(size_t)si];
+      SPAQR_CUDA(cudaEventRecord(ev[2 * (size_t)t], h.st));
+      if (s.n_small) {
+        const int grid = (s.n_small + kW - 1) / kW;
+        if (s.kind == 2)
+          q_warp_kernel<TW><<<grid, kT, 0, h.st>>>(ops, s.small_ids, s.n_small, z, transpose);
+        else if (transpose)
+          r_invT_warp_kernel<TW><<<grid, kT, kWarpSmem<TW>, h.st>>>(ops, s.small_ids, s.n_small, z);
+        else
+          r_inv_warp_kernel<TW><<<grid, kT, kWarpSmem<TW>, h.st>>>(ops, s.small_ids, s.n_small, z);
+      }
+      if (s.n_large) {
+        if (s.kind == 2)
+          q_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z, transpose);
+        else if (transpose)
+          r_invT_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z);
+        else
+          r_inv_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z);
+      }
+      SPAQR_CUDA(cudaEventRecord(ev[2 * (size_t)t + 1], h.st));
+    }
+    SPAQR_CUDA(cudaStreamSynchronize(h.st));
+    double tot = 0.0;
+    for (int t = 0; t < nseg; ++t) {
+      const int si = transpose ? t : nseg - 1 - t;
+      const Segment& s = P.segs[(size_t)si];
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * (size_t)t], ev[2 * (size_t)t + 1]);
+      tot += ms;
+      if (ms > 0.05f)
+        std::fprintf(stderr, "[spaqr] apply %s seg %3d kind %d small %6d large %5d: %8.1f us\n",
+                     transpose ? "W^-T" : "W^-1", si, s.kind, s.n_small, s.n_large, ms * 1e3);
+    }
+    std::fprintf(stderr, "[spaqr] apply %s total %.3f ms over %d segments\n", transpose ? "W^-T" : "W^-1", tot, nseg);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+}
+
+void profile_apply(Handle& h, double* z) {
+  if (h.plan->fp32)
+    profile_apply_t<float>(h, z);
+  else
+    profile_apply_t<double>(h, z);
 }
 
 void apply_Winv(Handle& h, double* z, int transpose) {
@@ -616,6 +828,13 @@ void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info)
   (void)s;
   double* sv = s;
   const double* Dinv_w = h.d_D;  // |D^{-1} u| = |u / D|
+  {
+    const char* e = std::getenv("SPAQR_PROFILE_APPLY");
+    if (e && e[0] == '1') {
+      SPAQR_CUDA(cudaMemsetAsync(t, 0, (size_t)n * sizeof(double), h.st));
+      profile_apply(h, t);
+    }
+  }
   SPAQR_CUDA(cudaMemsetAsync(xt, 0, (size_t)n * sizeof(double), h.st));
   SPAQR_CUDA(cudaMemcpyAsync(r, b_dev, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
   spmv_kernel<<<blocks(n), kT, 0, h.st>>>(n, h.d_trowptr, h.d_tcolidx, h.d_tvals, r, u, Dinv_w, P.d_part);
