@@ -145,7 +145,7 @@ struct WOp {
   void* V = nullptr;                // c x w, ld c (kind 2)
   void* tau = nullptr;              // w (kind 2)
   int* kdev = nullptr;              // device rank (kind 2)
-  void* Qx = nullptr;               // kind 2 with c > 32: Q_pp = H_1...H_k formed explicitly (c x c, ld c)
+  void* G = nullptr;                // dense operator of a large op, formed once for the apply (solve.cu)
 };
 
 struct Handle {

@@ -1,11 +1,30 @@
-// Apply of the stored factor W and the W-preconditioned CGLS (Section 4).
+// Apply of the stored factor W and the W-preconditioned CGLS (Section 2.7,
+// Section 4).
 //
 // W = W_1 ... W_L with W_l = (prod Q_p^T)(prod R_p)(prod R_s) for the
-// operations of stage l (Section 2.7).  W^{-1} z replays the operations in
-// reverse factorization order, W^{-T} z in factorization order.  Operations
-// of one elimination round, of one scaling phase and of one step-2 phase act
-// on disjoint slots and run as one batched launch each ("segment").  Every
-// vector is FP64; the stored factor is FP64 or FP32 (mixed precision).
+// operations of stage l.  W^{-1} z replays the operations in reverse
+// factorization order, W^{-T} z in factorization order.  Operations of one
+// elimination round, of one scaling phase and of one step-2 phase act on
+// disjoint slots and form one "segment".
+//
+// Each op takes one of two forms:
+//  * small (c <= 32, and at most kWideW R_sn columns): one warp per op, the
+//    triangular solves by shuffles, Q_pp as its Householder product;
+//  * dense (all others): the op is replaced, once after the factorization, by
+//    the dense operator it applies, G = R^{-1} [I  -R_sn] (c x (c + w)) for
+//    R_s and R_p, G = Q_pp for Q_p.  With G = [X Y]:
+//      W^{-1}:  z_s <- G [z_s; z_n]
+//      W^{-T}:  z_s <- X^T z_s,  z_n <- z_n + Y^T z_s
+//    Both run as tiled GEMVs over many CTAs (one partial sum per tile),
+//    followed by a pass that reduces the partials in a fixed order and
+//    scatters them to the slot vector.
+// Q_p ops of rank 0 are the identity and are skipped.
+//
+// Slot vectors are FP64 in memory.  The arithmetic type TA is FP64 with the
+// FP64 factor and FP32 with the mixed-precision (FP32) factor: the apply is
+// the preconditioner, while the CGLS recurrences, residuals and norms stay
+// FP64 (and x, r are updated from the same computed W^{-1} p, so they stay
+// consistent).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,326 +41,301 @@ namespace spaqr {
 namespace {
 constexpr int kT = 256;
 constexpr int kW = kT / 32;
+constexpr int kWideW = 128;  // R_s ops with more R_sn columns take the dense form
+constexpr int kTile = 8192;  // entries of one GEMV tile: 32 x 256 (c <= 32) or 128 x 64
+constexpr int kStage = 256 * 33;  // staged tile of the transposed GEMV, padded
 
 template <typename TW>
 constexpr size_t kWarpSmem = (size_t)kW * 32 * 33 * sizeof(TW);  // staged R_ss per warp
 
 template <typename TW>
-struct ApplyOp {
-  const TW* R;  // kind 0: c x (c + w) = [R_ss R_sn]; kind 1: c x c
-  const TW* Qx; // kind 2, c > 32: explicit Q_pp (c x c, ld c)
-  const TW* V;
+struct SmallOp {
+  const TW* R;     // kind 0: c x (c + w) = [R_ss R_sn]; kind 1: c x c; ld c
+  const TW* V;     // kind 2: reflectors, c x k, ld c
   const TW* tau;
-  const int* kdev;
   const int32_t* slots;
   const int32_t* nslots;
-  const double* rdiag;  // kinds 0, 1: 1 / R_ii (FP64), computed once when the plan is built
-  int c, w;
+  const double* rdiag;  // kinds 0, 1: 1 / R_ii
+  int c, w, k;
 };
 
-__device__ __forceinline__ double wsum(double v) {
+template <typename TW>
+struct DenseOp {
+  TW* G;  // c x (c + w), ld c
+  const TW* R;
+  const TW* V;
+  const TW* tau;
+  const int32_t* slots;
+  const int32_t* nslots;
+  int64_t poff_f, poff_t;  // this op's partial sums in the segment scratch (W^{-1}, W^{-T})
+  int c, w, k, kind;
+  int tr, nrt, nct;  // tile rows (32 or 128), row tiles, column tiles
+  int tri;           // X = G[:, :c] upper triangular: tiles strictly below the diagonal are skipped
+};
+
+__host__ __device__ inline int tile_cols(int tr) { return kTile / tr; }
+
+template <typename TA>
+__device__ __forceinline__ TA wsum(TA v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Back substitution R y = rhs (R upper, ld c) on a shared vector y of length c,
-// blocked by 32 rows: the 32 x 32 diagonal block is staged in shared memory
-// (blk, 33 x 32 doubles) with parallel loads, warp 0 solves it with shuffles
-// and the precomputed reciprocals, then all threads update the rows above.
-template <typename TW>
-__device__ void upper_solve(const TW* R, const double* rdiag, int c, double* y, double* blk) {
-  const int lane = threadIdx.x & 31;
-  for (int hi = c; hi > 0; hi -= 32) {
-    const int lo = hi > 32 ? hi - 32 : 0;
-    const int bs = hi - lo;
-    __syncthreads();
-    for (int e = threadIdx.x; e < bs * bs; e += kT) {
-      const int r = e % bs, q = e / bs;  // coalesced over rows
-      blk[r * 33 + q] = (double)R[(lo + r) + (int64_t)(lo + q) * c];
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int r = lane;
-      double x = r < bs ? y[lo + r] : 0.0;
-      const double rd = r < bs ? rdiag[lo + r] : 0.0;
-      for (int q = bs - 1; q >= 0; --q) {
-        const double yq = __shfl_sync(0xffffffffu, x, q) * __shfl_sync(0xffffffffu, rd, q);
-        if (r == q) x = yq;
-        if (r < q) x -= blk[r * 33 + q] * yq;
-      }
-      if (r < bs) y[lo + r] = x;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < lo; i += kT) {
-      double a0 = 0.0, a1 = 0.0;
-      int j = lo;
-      for (; j + 1 < hi; j += 2) {
-        a0 += (double)R[i + (int64_t)j * c] * y[j];
-        a1 += (double)R[i + (int64_t)(j + 1) * c] * y[j + 1];
-      }
-      if (j < hi) a0 += (double)R[i + (int64_t)j * c] * y[j];
-      y[i] -= a0 + a1;
-    }
-  }
-  __syncthreads();
-}
-
-// Forward substitution R^T y = rhs, blocked the same way.
-template <typename TW>
-__device__ void lower_t_solve(const TW* R, const double* rdiag, int c, double* y, double* blk) {
-  const int lane = threadIdx.x & 31;
-  for (int lo = 0; lo < c; lo += 32) {
-    const int hi = lo + 32 < c ? lo + 32 : c;
-    const int bs = hi - lo;
-    __syncthreads();
-    for (int e = threadIdx.x; e < bs * bs; e += kT) {
-      const int r = e % bs, q = e / bs;
-      blk[r * 33 + q] = (double)R[(lo + r) + (int64_t)(lo + q) * c];
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int r = lane;
-      double x = r < bs ? y[lo + r] : 0.0;
-      const double rd = r < bs ? rdiag[lo + r] : 0.0;
-      for (int q = 0; q < bs; ++q) {
-        const double yq = __shfl_sync(0xffffffffu, x, q) * __shfl_sync(0xffffffffu, rd, q);
-        if (r == q) x = yq;
-        if (r > q && r < bs) x -= blk[q * 33 + r] * yq;
-      }
-      if (r < bs) y[lo + r] = x;
-    }
-    __syncthreads();
-    for (int i = hi + threadIdx.x; i < c; i += kT) {
-      const TW* col = R + (int64_t)i * c;
-      double a0 = 0.0, a1 = 0.0;
-      int j = lo;
-      for (; j + 1 < hi; j += 2) {
-        a0 += (double)col[j] * y[j];
-        a1 += (double)col[j + 1] * y[j + 1];
-      }
-      if (j < hi) a0 += (double)col[j] * y[j];
-      y[i] -= a0 + a1;
-    }
-  }
-  __syncthreads();
-}
-
-// W^{-1}: z_s <- R_ss^{-1} (z_s - R_sn z_n)  (kind 0) or z_p <- R_pp^{-1} z_p (kind 1)
-template <typename TW>
-__global__ void __launch_bounds__(kT) r_inv_kernel(const ApplyOp<TW>* ops, const int* ids, double* z) {
-  const ApplyOp<TW> op = ops[ids[blockIdx.x]];
-  extern __shared__ double sh[];
-  double* y = sh;          // c
-  double* part = sh + op.c;  // kW * c partials
-  __shared__ double blk[33 * 32];
-  const int c = op.c, w = op.w;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < kW * c; i += kT) part[i] = 0.0;
-  __syncthreads();
-  if (w > 0) {
-    const TW* Rn = op.R + (int64_t)c * c;
-    for (int i0 = 0; i0 < c; i0 += 32) {
-      const int i = i0 + lane;
-      double acc = 0.0;
-      for (int j = warp; j < w; j += kW) {
-        const double zj = z[op.nslots[j]];
-        if (i < c) acc += (double)Rn[i + (int64_t)j * c] * zj;
-      }
-      if (i < c) part[warp * c + i] = acc;
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < c; i += kT) {
-    double s = z[op.slots[i]];
-    for (int q = 0; q < kW; ++q) s -= part[q * c + i];
-    y[i] = s;
-  }
-  upper_solve(op.R, op.rdiag, c, y, blk);
-  for (int i = threadIdx.x; i < c; i += kT) z[op.slots[i]] = y[i];
-}
-
-// W^{-T}: y = R_ss^{-T} z_s, z_s <- y, z_n -= R_sn^T y (kind 0); z_p <- R_pp^{-T} z_p (kind 1)
-template <typename TW>
-__global__ void __launch_bounds__(kT) r_invT_kernel(const ApplyOp<TW>* ops, const int* ids, double* z) {
-  const ApplyOp<TW> op = ops[ids[blockIdx.x]];
-  extern __shared__ double sh[];
-  double* y = sh;
-  __shared__ double blk[33 * 32];
-  const int c = op.c, w = op.w;
-  for (int i = threadIdx.x; i < c; i += kT) y[i] = z[op.slots[i]];
-  lower_t_solve(op.R, op.rdiag, c, y, blk);
-  for (int i = threadIdx.x; i < c; i += kT) z[op.slots[i]] = y[i];
-  if (w > 0) {
-    const TW* Rn = op.R + (int64_t)c * c;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int j = warp; j < w; j += kW) {
-      const TW* col = Rn + (int64_t)j * c;
-      double s = 0.0;
-      for (int i = lane; i < c; i += 32) s += (double)col[i] * y[i];
-      s = wsum(s);
-      if (lane == 0) atomicAdd(&z[op.nslots[j]], -s);
-    }
-  }
-}
-
-// Large Q_p ops use the explicit Q_pp formed after the factorization:
-// W^{-1}: z_p <- Q_pp z_p;  W^{-T}: z_p <- Q_pp^T z_p  (one coalesced GEMV each).
-template <typename TW>
-__global__ void __launch_bounds__(kT) q_kernel(const ApplyOp<TW>* ops, const int* ids, double* z, int transpose) {
-  const ApplyOp<TW> op = ops[ids[blockIdx.x]];
-  extern __shared__ double sh[];
-  double* x = sh;
-  const int c = op.c;
-  for (int i = threadIdx.x; i < c; i += kT) x[i] = z[op.slots[i]];
-  __syncthreads();
-  if (!transpose) {
-    // y_i = sum_j Q[i, j] x_j: thread per row, columns in order (coalesced over i)
-    for (int i0 = 0; i0 < c; i0 += kT) {
-      const int i = i0 + threadIdx.x;
-      if (i >= c) continue;
-      double acc = 0.0;
-      for (int j = 0; j < c; ++j) acc += (double)op.Qx[i + (int64_t)j * c] * x[j];
-      z[op.slots[i]] = acc;
-    }
-  } else {
-    // y_j = sum_i Q[i, j] x_i: warp per column, lanes over i (coalesced)
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int j = warp; j < c; j += kW) {
-      const TW* col = op.Qx + (int64_t)j * c;
-      double acc = 0.0;
-      for (int i = lane; i < c; i += 32) acc += (double)col[i] * x[i];
-      acc = wsum(acc);
-      if (lane == 0) z[op.slots[j]] = acc;
-    }
-  }
-}
-
-// 1 / R_ii for every triangular op (one warp per op).
-template <typename TW>
-__global__ void __launch_bounds__(kT) recip_diag_kernel(const ApplyOp<TW>* ops, int nops) {
-  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
-  if (gw >= nops) return;
-  const ApplyOp<TW> op = ops[gw];
-  if (!op.rdiag) return;
-  double* rd = const_cast<double*>(op.rdiag);
-  for (int i = threadIdx.x & 31; i < op.c; i += 32) rd[i] = 1.0 / (double)op.R[i + (int64_t)i * op.c];
-}
-
-// Q = H_1 ... H_k applied to the identity, 32 columns per CTA (one warp per
-// column at a time, the column held in shared memory).
-template <typename TW>
-__global__ void __launch_bounds__(kT) form_q_kernel(const ApplyOp<TW>* ops, const int* ids, TW* const* outs) {
-  const ApplyOp<TW> op = ops[ids[blockIdx.y]];
-  TW* Q = outs[blockIdx.y];
-  const int c = op.c;
-  const int k = *op.kdev;
-  extern __shared__ double sh[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* y = sh + (size_t)warp * c;
-  for (int jj = warp; jj < 32; jj += kW) {
-    const int j = blockIdx.x * 32 + jj;
-    if (j >= c) break;
-    for (int i = lane; i < c; i += 32) y[i] = (i == j) ? 1.0 : 0.0;
-    __syncwarp();
-    for (int t = k - 1; t >= 0; --t) {  // Q e_j = H_1 (H_2 (... H_k e_j))
-      const TW* v = op.V + (int64_t)t * c;
-      double d = 0.0;
-      for (int i = t + lane; i < c; i += 32) d += (i == t ? 1.0 : (double)v[i]) * y[i];
-      d = wsum(d) * (double)op.tau[t];
-      for (int i = t + lane; i < c; i += 32) y[i] -= d * (i == t ? 1.0 : (double)v[i]);
-      __syncwarp();
-    }
-    for (int i = lane; i < c; i += 32) Q[i + (int64_t)j * c] = (TW)y[i];
-    __syncwarp();
-  }
-}
-
-// ------------------------------------------- warp-per-op kernels (c <= 32)
-// One warp applies one stored op; lane i holds z_slots[i].  The triangular
-// solves run by shuffles (no block barriers).
-template <typename TW>
-__global__ void __launch_bounds__(kT) r_inv_warp_kernel(const ApplyOp<TW>* ops, const int* ids, int count,
-                                                        double* z) {
+// ------------------------------------------- small ops: one warp per op
+// W^{-1}: z_s <- R_ss^{-1} (z_s - R_sn z_n) (kind 0), z_p <- R_pp^{-1} z_p (kind 1).
+// Lane i holds row i; R_ss is staged in the warp's shared region.
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) r_inv_warp_kernel(const SmallOp<TW>* ops, int count, double* z) {
   const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
   if (gw >= count) return;
-  const ApplyOp<TW> op = ops[ids[gw]];
+  const SmallOp<TW> op = ops[gw];
   const int lane = threadIdx.x & 31, c = op.c, w = op.w;
-  double x = lane < c ? z[op.slots[lane]] : 0.0;
+  TA x = lane < c ? (TA)z[op.slots[lane]] : TA(0);
   if (w > 0) {
     const TW* Rn = op.R + (int64_t)c * c;
-    double acc = 0.0;
+    TA acc = TA(0);
     for (int j0 = 0; j0 < w; j0 += 32) {
-      const double zl = (j0 + lane < w) ? z[op.nslots[j0 + lane]] : 0.0;
+      const TA zl = (j0 + lane < w) ? (TA)z[op.nslots[j0 + lane]] : TA(0);
       const int jn = min(32, w - j0);
       for (int t = 0; t < jn; ++t) {
-        const double zj = __shfl_sync(0xffffffffu, zl, t);
-        if (lane < c) acc += (double)Rn[lane + (int64_t)(j0 + t) * c] * zj;
+        const TA zj = __shfl_sync(0xffffffffu, zl, t);
+        if (lane < c) acc += (TA)Rn[lane + (int64_t)(j0 + t) * c] * zj;
       }
     }
     x -= acc;
   }
-  // stage R_ss (c x c) in this warp's shared region, then the back substitution
   extern __shared__ __align__(16) unsigned char wsm[];
   TW* B = reinterpret_cast<TW*>(wsm) + (size_t)(threadIdx.x >> 5) * (32 * 33);
   for (int q = 0; q < c; ++q)
     if (lane < c) B[lane * 33 + q] = op.R[lane + (int64_t)q * c];
-  const double rd = lane < c ? op.rdiag[lane] : 0.0;
+  const TA rd = lane < c ? (TA)op.rdiag[lane] : TA(0);
   __syncwarp();
   for (int j = c - 1; j >= 0; --j) {
-    const double yj = __shfl_sync(0xffffffffu, x, j) * __shfl_sync(0xffffffffu, rd, j);
+    const TA yj = __shfl_sync(0xffffffffu, x, j) * __shfl_sync(0xffffffffu, rd, j);
     if (lane == j) x = yj;
-    if (lane < j) x -= (double)B[lane * 33 + j] * yj;
+    if (lane < j) x -= (TA)B[lane * 33 + j] * yj;
   }
-  if (lane < c) z[op.slots[lane]] = x;
+  if (lane < c) z[op.slots[lane]] = (double)x;
 }
 
-template <typename TW>
-__global__ void __launch_bounds__(kT) r_invT_warp_kernel(const ApplyOp<TW>* ops, const int* ids, int count,
-                                                         double* z) {
+// W^{-T}: y = R_ss^{-T} z_s, z_s <- y, z_n -= R_sn^T y (kind 0); z_p <- R_pp^{-T} z_p (kind 1).
+// The R_sn^T y products run lane-per-column (y broadcast by shuffles).
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) r_invT_warp_kernel(const SmallOp<TW>* ops, int count, double* z) {
   const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
   if (gw >= count) return;
-  const ApplyOp<TW> op = ops[ids[gw]];
+  const SmallOp<TW> op = ops[gw];
   const int lane = threadIdx.x & 31, c = op.c, w = op.w;
-  double x = lane < c ? z[op.slots[lane]] : 0.0;
+  TA x = lane < c ? (TA)z[op.slots[lane]] : TA(0);
   extern __shared__ __align__(16) unsigned char wsm[];
   TW* B = reinterpret_cast<TW*>(wsm) + (size_t)(threadIdx.x >> 5) * (32 * 33);
   for (int q = 0; q < c; ++q)
     if (lane < c) B[lane * 33 + q] = op.R[lane + (int64_t)q * c];
-  const double rd = lane < c ? op.rdiag[lane] : 0.0;
+  const TA rd = lane < c ? (TA)op.rdiag[lane] : TA(0);
   __syncwarp();
   for (int i = 0; i < c; ++i) {
-    const double yi = __shfl_sync(0xffffffffu, x, i) * __shfl_sync(0xffffffffu, rd, i);
+    const TA yi = __shfl_sync(0xffffffffu, x, i) * __shfl_sync(0xffffffffu, rd, i);
     if (lane == i) x = yi;
-    if (lane > i && lane < c) x -= (double)B[i * 33 + lane] * yi;
+    if (lane > i && lane < c) x -= (TA)B[i * 33 + lane] * yi;
   }
-  if (lane < c) z[op.slots[lane]] = x;
+  if (lane < c) z[op.slots[lane]] = (double)x;
   if (w > 0) {
     const TW* Rn = op.R + (int64_t)c * c;
-    for (int j = 0; j < w; ++j) {
-      double sv = lane < c ? (double)Rn[lane + (int64_t)j * c] * x : 0.0;
-      sv = wsum(sv);
-      if (lane == 0) atomicAdd(&z[op.nslots[j]], -sv);
+    for (int j0 = 0; j0 < w; j0 += 32) {
+      const int j = j0 + lane;
+      const TW* col = Rn + (int64_t)(j < w ? j : 0) * c;
+      TA acc = TA(0);
+      for (int i = 0; i < c; ++i) acc += (TA)col[i] * __shfl_sync(0xffffffffu, x, i);
+      if (j < w) atomicAdd(&z[op.nslots[j]], -(double)acc);
     }
   }
 }
 
-template <typename TW>
-__global__ void __launch_bounds__(kT) q_warp_kernel(const ApplyOp<TW>* ops, const int* ids, int count, double* z,
-                                                    int transpose) {
+// W^{-1}: z_p <- Q_pp z_p = H_1 ... H_k z_p;  W^{-T}: z_p <- Q_pp^T z_p.
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) q_warp_kernel(const SmallOp<TW>* ops, int count, double* z, int transpose) {
   const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
   if (gw >= count) return;
-  const ApplyOp<TW> op = ops[ids[gw]];
-  const int lane = threadIdx.x & 31, c = op.c;
-  const int k = *op.kdev;
-  double x = lane < c ? z[op.slots[lane]] : 0.0;
+  const SmallOp<TW> op = ops[gw];
+  const int lane = threadIdx.x & 31, c = op.c, k = op.k;
+  TA x = lane < c ? (TA)z[op.slots[lane]] : TA(0);
   for (int t = 0; t < k; ++t) {
     const int i = transpose ? t : k - 1 - t;
-    const double v = lane == i ? 1.0 : ((lane > i && lane < c) ? (double)op.V[lane + (int64_t)i * c] : 0.0);
-    const double d = wsum(v * x) * (double)op.tau[i];
+    const TA v = lane == i ? TA(1) : ((lane > i && lane < c) ? (TA)op.V[lane + (int64_t)i * c] : TA(0));
+    const TA d = wsum(v * x) * (TA)op.tau[i];
     x -= d * v;
   }
-  if (lane < c) z[op.slots[lane]] = x;
+  if (lane < c) z[op.slots[lane]] = (double)x;
+}
+
+// ------------------------------------------- dense ops: tiled GEMVs
+// W^{-1} partials: part[poff_f + ct c + i] = sum over the tile's columns j of G[i, j] u_j,
+// u = [z_s; z_n].  Thread (row, column group); a warp reads 32 consecutive rows of a column.
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) dense_fwd_kernel(const DenseOp<TW>* dops, const int4* tiles, const double* z,
+                                                       TA* part) {
+  const int4 tl = tiles[blockIdx.x];
+  const DenseOp<TW>* op = dops + tl.x;
+  const int c = op->c, ncol = c + op->w, TR = op->tr, TC = tile_cols(TR);
+  const int r0 = tl.y * TR, c0 = tl.z * TC;
+  const int nr = min(TR, c - r0), nc = min(TC, ncol - c0);
+  const int32_t* slots = op->slots;
+  const int32_t* nslots = op->nslots;
+  __shared__ TA u[256];
+  __shared__ TA red[kT];
+  for (int j = threadIdx.x; j < nc; j += kT) {
+    const int jj = c0 + j;
+    u[j] = (TA)z[jj < c ? slots[jj] : nslots[jj - c]];
+  }
+  __syncthreads();
+  const int groups = kT / TR, ri = threadIdx.x % TR, g = threadIdx.x / TR;
+  TA acc = TA(0);
+  if (ri < nr) {
+    const TW* base = op->G + (r0 + ri) + (int64_t)c0 * c;
+#pragma unroll 8
+    for (int j = g; j < nc; j += groups) acc += (TA)base[(int64_t)j * c] * u[j];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    TA s = TA(0);
+    for (int q = 0; q < groups; ++q) s += red[q * TR + threadIdx.x];
+    part[op->poff_f + (int64_t)tl.z * c + r0 + threadIdx.x] = s;
+  }
+}
+
+// W^{-T} partials: part[poff_t + rt (c + w) + j] = sum over the tile's rows i of G[i, j] v_i,
+// v = z_s.  The tile is staged in shared memory (coalesced), then thread (column, row group).
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) dense_T_kernel(const DenseOp<TW>* dops, const int4* tiles, const double* z,
+                                                     TA* part) {
+  const int4 tl = tiles[blockIdx.x];
+  const DenseOp<TW>* op = dops + tl.x;
+  const int c = op->c, ncol = c + op->w, TR = op->tr, TC = tile_cols(TR);
+  const int r0 = tl.y * TR, c0 = tl.z * TC;
+  const int nr = min(TR, c - r0), nc = min(TC, ncol - c0);
+  extern __shared__ __align__(16) unsigned char dsm[];
+  TW* s = reinterpret_cast<TW*>(dsm);  // TC x (TR + 1)
+  __shared__ TA v[128];
+  __shared__ TA red[kT];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < nr; i += kT) v[i] = (TA)z[op->slots[r0 + i]];
+  const TW* G = op->G + r0 + (int64_t)c0 * c;
+  for (int q = warp; q < nc; q += kW)
+    for (int r = lane; r < nr; r += 32) s[q * (TR + 1) + r] = G[r + (int64_t)q * c];
+  __syncthreads();
+  const int groups = kT / TC, cj = threadIdx.x % TC, g = threadIdx.x / TC;
+  TA acc = TA(0);
+  if (cj < nc) {
+    const int i1 = min(nr, g * 32 + 32);
+    const TW* col = s + cj * (TR + 1);
+    for (int i = g * 32; i < i1; ++i) acc += (TA)col[i] * v[i];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < nc) {
+    TA t = TA(0);
+    for (int q = 0; q < groups; ++q) t += red[q * TC + threadIdx.x];
+    part[op->poff_t + (int64_t)tl.y * ncol + c0 + threadIdx.x] = t;
+  }
+}
+
+// z_s[i] <- sum over the column tiles of the partials (fixed order)
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) dense_fwd_reduce_kernel(const DenseOp<TW>* dops, const int2* items,
+                                                              const TA* part, double* z) {
+  const int2 it = items[blockIdx.x];
+  const DenseOp<TW>* op = dops + it.x;
+  const int i = it.y + threadIdx.x, c = op->c;
+  if (i >= c) return;
+  const int TR = op->tr, TC = tile_cols(TR);
+  const int ct0 = op->tri ? ((i / TR) * TR) / TC : 0;
+  TA s = TA(0);
+  for (int ct = ct0; ct < op->nct; ++ct) s += part[op->poff_f + (int64_t)ct * c + i];
+  z[op->slots[i]] = (double)s;
+}
+
+// z_s[j] <- sum over the row tiles (j < c);  z_n[j - c] += sum (j >= c)
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) dense_T_reduce_kernel(const DenseOp<TW>* dops, const int2* items,
+                                                            const TA* part, double* z) {
+  const int2 it = items[blockIdx.x];
+  const DenseOp<TW>* op = dops + it.x;
+  const int c = op->c, ncol = c + op->w, j = it.y + threadIdx.x;
+  if (j >= ncol) return;
+  const int TR = op->tr, TC = tile_cols(TR);
+  int rt1 = op->nrt - 1;
+  if (op->tri) rt1 = min(rt1, ((j / TC + 1) * TC - 1) / TR);
+  TA s = TA(0);
+  for (int rt = 0; rt <= rt1; ++rt) s += part[op->poff_t + (int64_t)rt * ncol + j];
+  if (j < c)
+    z[op->slots[j]] = (double)s;
+  else
+    atomicAdd(&z[op->nslots[j - c]], (double)s);
+}
+
+// Forms column j of every dense operator in FP64 (one warp per column, work
+// vector y in global scratch):  Q_pp e_j = H_1 (... (H_k e_j)) for Q_p ops;
+// for R ops the column-oriented back substitution R g = b with b = e_j
+// (j < c) or b = -R_sn[:, j - c].
+template <typename TW>
+__global__ void __launch_bounds__(kT) form_dense_kernel(const DenseOp<TW>* dops, const int2* items, int64_t nitems,
+                                                        double* scratch, int cmax) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * kT + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * kT) >> 5;
+  double* y = scratch + gw * cmax;
+  for (int64_t t = gw; t < nitems; t += nw) {
+    const int2 it = items[t];
+    const DenseOp<TW>* op = dops + it.x;
+    const int c = op->c, j = it.y;
+    if (op->kind == 2) {
+      for (int i = lane; i < c; i += 32) y[i] = i == j ? 1.0 : 0.0;
+      __syncwarp();
+      for (int q = op->k - 1; q >= 0; --q) {
+        const TW* v = op->V + (int64_t)q * c;
+        double d = 0.0;
+        for (int i = q + lane; i < c; i += 32) d += (i == q ? 1.0 : (double)v[i]) * y[i];
+        d = wsum(d) * (double)op->tau[q];
+        for (int i = q + lane; i < c; i += 32) y[i] -= d * (i == q ? 1.0 : (double)v[i]);
+        __syncwarp();
+      }
+    } else {
+      const TW* R = op->R;
+      int top = c - 1;
+      if (j < c) {
+        for (int i = lane; i < c; i += 32) y[i] = i == j ? 1.0 : 0.0;
+        top = j;
+      } else {
+        const TW* b = R + (int64_t)j * c;  // column j - c of R_sn
+        for (int i = lane; i < c; i += 32) y[i] = -(double)b[i];
+      }
+      __syncwarp();
+      for (int i = top; i >= 0; --i) {
+        const double yi = y[i] / (double)R[i + (int64_t)i * c];
+        __syncwarp();
+        if (lane == 0) y[i] = yi;
+        const TW* col = R + (int64_t)i * c;
+        for (int r = lane; r < i; r += 32) y[r] -= yi * (double)col[r];
+        __syncwarp();
+      }
+    }
+    TW* out = op->G + (int64_t)j * c;
+    for (int i = lane; i < c; i += 32) out[i] = (TW)y[i];
+    __syncwarp();
+  }
+}
+
+// 1 / R_ii of every small triangular op (one warp per op).
+template <typename TW>
+__global__ void __launch_bounds__(kT) recip_diag_kernel(const SmallOp<TW>* ops, int nops) {
+  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
+  if (gw >= nops) return;
+  const SmallOp<TW> op = ops[gw];
+  if (!op.rdiag) return;
+  double* rd = const_cast<double*>(op.rdiag);
+  for (int i = threadIdx.x & 31; i < op.c; i += 32) rd[i] = 1.0 / (double)op.R[i + (int64_t)i * op.c];
 }
 
 // ----------------------------------------------------------- CGLS kernels
@@ -427,22 +421,25 @@ int blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + kT - 1) / kT); }
 
 // ------------------------------------------------------------------ plan
 struct Segment {
-  int kind;        // 0 R_s, 1 R_p, 2 Q_p
-  int n_small;     // ops with c <= 32 (one warp each), ids at small_ids
-  int n_large;     // ops with c > 32 (one CTA each), ids at large_ids
-  const int* small_ids;
-  const int* large_ids;
-  int smem;        // dynamic shared memory of the CTA kernels
+  int kind;            // 0 R_s, 1 R_p, 2 Q_p
+  int small0, nsmall;  // small ops (segment-contiguous in the small-op array)
+  int tile0, ntile;    // GEMV tiles of the dense ops
+  int rf0, nrf;        // W^{-1} reduce items
+  int rt0, nrt;        // W^{-T} reduce items
 };
 
 struct ApplyPlan {
   cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  double* d_rdiag = nullptr;     // 1 / R_ii of every R_s and R_p op
   bool fp32 = false;
-  void* d_ops = nullptr;         // ApplyOp<TW>[nops] (factorization order)
-  int32_t* d_idx = nullptr;      // slot index arrays
-  int* d_ids = nullptr;          // op ids of every segment (small ones, then large ones)
-  std::vector<Segment> segs;     // factorization order
+  double* d_rdiag = nullptr;
+  void* d_small = nullptr;  // SmallOp<TW>[]
+  void* d_dense = nullptr;  // DenseOp<TW>[]
+  int32_t* d_idx = nullptr;
+  int4* d_tiles = nullptr;
+  int2* d_red = nullptr;    // reduce items (W^{-1} ones, then W^{-T} ones)
+  void* d_dpart = nullptr;  // partial sums of the dense GEMVs (TA), sized for the largest segment
+  std::vector<Segment> segs;  // factorization order
+  int64_t launches = 0;       // kernel launches of one W^{-1} (equal for W^{-T})
   cudaGraphExec_t graph = nullptr;
   double* d_scal = nullptr;
   double* d_part = nullptr;
@@ -460,128 +457,160 @@ static void set_dyn_smem(K kernel) {
   SPAQR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes));
 }
 
-template <typename TW>
+template <typename TW, typename TA>
 static void build_plan_t(Handle& h, ApplyPlan& P) {
+  const size_t nops = h.ops.size();
+  // op form: 0 skipped (identity), 1 small, 2 dense
+  std::vector<int> form(nops, 0);
+  for (size_t i = 0; i < nops; ++i) {
+    const WOp& op = h.ops[i];
+    if (op.c <= 0 || (op.kind == 2 && op.k <= 0))
+      form[i] = 0;
+    else if (op.c <= 32 && (op.kind != 0 || op.w <= kWideW))
+      form[i] = 1;
+    else
+      form[i] = 2;
+  }
   std::vector<int32_t> idx;
-  std::vector<ApplyOp<TW>> ops;
-  std::vector<size_t> soff, noff;
-  for (auto& op : h.ops) {
-    soff.push_back(idx.size());
+  std::vector<size_t> soff(nops), noff(nops);
+  for (size_t i = 0; i < nops; ++i) {
+    const WOp& op = h.ops[i];
+    soff[i] = idx.size();
     idx.insert(idx.end(), op.slots.begin(), op.slots.end());
-    noff.push_back(idx.size());
+    noff[i] = idx.size();
     idx.insert(idx.end(), op.nslots.begin(), op.nslots.end());
   }
   SPAQR_CUDA(cudaMalloc(&P.d_idx, std::max<size_t>(idx.size(), 1) * sizeof(int32_t)));
   SPAQR_CUDA(cudaMemcpy(P.d_idx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  std::vector<size_t> roff(h.ops.size(), 0);
   size_t nrd = 0;
-  for (size_t i = 0; i < h.ops.size(); ++i)
-    if (h.ops[i].kind != 2) {
-      roff[i] = nrd;
-      nrd += (size_t)h.ops[i].c;
-    }
+  for (size_t i = 0; i < nops; ++i)
+    if (form[i] == 1 && h.ops[i].kind != 2) nrd += (size_t)h.ops[i].c;
   SPAQR_CUDA(cudaMalloc(&P.d_rdiag, std::max<size_t>(nrd, 1) * sizeof(double)));
-  for (size_t i = 0; i < h.ops.size(); ++i) {
-    const WOp& op = h.ops[i];
-    ApplyOp<TW> a{};
-    a.rdiag = op.kind != 2 ? P.d_rdiag + roff[i] : nullptr;
-    a.R = static_cast<const TW*>(op.R);
-    a.Qx = static_cast<const TW*>(op.Qx);
-    a.V = static_cast<const TW*>(op.V);
-    a.tau = static_cast<const TW*>(op.tau);
-    a.kdev = op.kdev;
-    a.slots = P.d_idx + soff[i];
-    a.nslots = P.d_idx + noff[i];
-    a.c = op.c;
-    a.w = op.kind == 0 ? op.w : 0;
-    ops.push_back(a);
-  }
-  // explicit Q_pp for the Q_p ops too wide for one warp
-  std::vector<int> qids;
-  std::vector<TW*> qouts;
-  int qmax = 0;
-  for (size_t i = 0; i < h.ops.size(); ++i) {
-    WOp& op = h.ops[i];
-    if (op.kind != 2 || op.c <= 32) continue;
-    op.Qx = h.wpool.alloc((size_t)op.c * op.c * sizeof(TW));
-    ops[i].Qx = static_cast<const TW*>(op.Qx);
-    qids.push_back((int)i);
-    qouts.push_back(static_cast<TW*>(op.Qx));
-    qmax = std::max(qmax, op.c);
-  }
-  SPAQR_CUDA(cudaMalloc(&P.d_ops, std::max<size_t>(ops.size(), 1) * sizeof(ApplyOp<TW>)));
-  SPAQR_CUDA(cudaMemcpy(P.d_ops, ops.data(), ops.size() * sizeof(ApplyOp<TW>), cudaMemcpyHostToDevice));
-  if (nrd) {
-    recip_diag_kernel<TW><<<(unsigned)((h.ops.size() + kW - 1) / kW), kT, 0, h.st>>>(
-        static_cast<const ApplyOp<TW>*>(P.d_ops), (int)h.ops.size());
-    SPAQR_CUDA(cudaGetLastError());
-  }
-  if (!qids.empty()) {
-    int* d_q = nullptr;
-    TW** d_out = nullptr;
-    SPAQR_CUDA(cudaMalloc(&d_q, qids.size() * sizeof(int)));
-    SPAQR_CUDA(cudaMalloc(&d_out, qouts.size() * sizeof(TW*)));
-    SPAQR_CUDA(cudaMemcpy(d_q, qids.data(), qids.size() * sizeof(int), cudaMemcpyHostToDevice));
-    SPAQR_CUDA(cudaMemcpy(d_out, qouts.data(), qouts.size() * sizeof(TW*), cudaMemcpyHostToDevice));
-    const size_t smem = (size_t)qmax * kW * sizeof(double);
-    int mx = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if ((int)smem > mx - 1024) throw Error(SPAQR_ERR_CAPACITY, "apply: Q_pp too large to form");
-    set_dyn_smem(form_q_kernel<TW>);
-    for (size_t b0 = 0; b0 < qids.size(); b0 += 65535) {
-      const unsigned nb = (unsigned)std::min<size_t>(65535, qids.size() - b0);
-      form_q_kernel<TW><<<dim3((unsigned)((qmax + 31) / 32), nb), kT, smem, h.st>>>(
-          static_cast<const ApplyOp<TW>*>(P.d_ops), d_q + b0, d_out + b0);
-      SPAQR_CUDA(cudaGetLastError());
-    }
-    SPAQR_CUDA(cudaStreamSynchronize(h.st));
-    cudaFree(d_q);
-    cudaFree(d_out);
-  }
-  // segments: consecutive ops with equal (kind, stage, round for R_s)
-  std::vector<int> ids;
-  struct Tmp {
-    int kind, ns, nl, maxc;
-    size_t s0, l0;
-  };
-  std::vector<Tmp> tmp;
+
+  std::vector<SmallOp<TW>> small;
+  std::vector<DenseOp<TW>> dense;
+  std::vector<int4> tiles;
+  std::vector<int2> red_f, red_t;
+  std::vector<int2> form_items;
+  std::vector<Segment> segs;
+  size_t rd_next = 0, part_max = 0;
+  int cmax = 0;
   size_t i = 0;
-  while (i < h.ops.size()) {
-    size_t j = i + 1;
+  while (i < nops) {
     const WOp& a = h.ops[i];
-    while (j < h.ops.size() && h.ops[j].kind == a.kind && h.ops[j].stage == a.stage &&
+    size_t j = i + 1;
+    while (j < nops && h.ops[j].kind == a.kind && h.ops[j].stage == a.stage &&
            (a.kind != 0 || h.ops[j].round == a.round))
       ++j;
-    Tmp t{a.kind, 0, 0, 0, 0, 0};
-    t.s0 = ids.size();
-    for (size_t q = i; q < j; ++q)
-      if (h.ops[q].c <= 32) {
-        ids.push_back((int)q);
-        t.ns++;
+    Segment sg{a.kind, (int)small.size(), 0, (int)tiles.size(), 0, (int)red_f.size(), 0, (int)red_t.size(), 0};
+    int64_t pf = 0, pt = 0;
+    for (size_t q = i; q < j; ++q) {
+      WOp& op = h.ops[q];
+      const int32_t* sl = P.d_idx + soff[q];
+      const int32_t* nl = P.d_idx + noff[q];
+      if (form[q] == 1) {
+        SmallOp<TW> s{};
+        s.R = static_cast<const TW*>(op.R);
+        s.V = static_cast<const TW*>(op.V);
+        s.tau = static_cast<const TW*>(op.tau);
+        s.slots = sl;
+        s.nslots = nl;
+        s.rdiag = nullptr;
+        if (op.kind != 2) {
+          s.rdiag = P.d_rdiag + rd_next;
+          rd_next += (size_t)op.c;
+        }
+        s.c = op.c;
+        s.w = op.kind == 0 ? op.w : 0;
+        s.k = op.kind == 2 ? op.k : 0;
+        small.push_back(s);
+      } else if (form[q] == 2) {
+        DenseOp<TW> d{};
+        const int w = op.kind == 0 ? op.w : 0;
+        const int ncol = op.c + w;
+        op.G = h.wpool.alloc((size_t)op.c * ncol * sizeof(TW));
+        d.G = static_cast<TW*>(op.G);
+        d.R = static_cast<const TW*>(op.R);
+        d.V = static_cast<const TW*>(op.V);
+        d.tau = static_cast<const TW*>(op.tau);
+        d.slots = sl;
+        d.nslots = nl;
+        d.c = op.c;
+        d.w = w;
+        d.k = op.kind == 2 ? op.k : 0;
+        d.kind = op.kind;
+        d.tr = op.c <= 32 ? 32 : 128;
+        const int tc = tile_cols(d.tr);
+        d.nrt = (op.c + d.tr - 1) / d.tr;
+        d.nct = (ncol + tc - 1) / tc;
+        d.tri = op.kind != 2;
+        d.poff_f = pf;
+        d.poff_t = pt;
+        pf += (int64_t)d.nct * op.c;
+        pt += (int64_t)d.nrt * ncol;
+        const int di = (int)dense.size();
+        for (int rt = 0; rt < d.nrt; ++rt)
+          for (int ct = 0; ct < d.nct; ++ct)
+            if (!d.tri || (int64_t)(ct + 1) * tc > (int64_t)rt * d.tr) tiles.push_back(make_int4(di, rt, ct, 0));
+        for (int r = 0; r < op.c; r += kT) red_f.push_back(make_int2(di, r));
+        for (int r = 0; r < ncol; r += kT) red_t.push_back(make_int2(di, r));
+        for (int c2 = 0; c2 < ncol; ++c2) form_items.push_back(make_int2(di, c2));
+        cmax = std::max(cmax, op.c);
+        dense.push_back(d);
       }
-    t.l0 = ids.size();
-    for (size_t q = i; q < j; ++q)
-      if (h.ops[q].c > 32) {
-        ids.push_back((int)q);
-        t.nl++;
-        t.maxc = std::max(t.maxc, h.ops[q].c);
-      }
-    tmp.push_back(t);
+    }
+    sg.nsmall = (int)small.size() - sg.small0;
+    sg.ntile = (int)tiles.size() - sg.tile0;
+    sg.nrf = (int)red_f.size() - sg.rf0;
+    sg.nrt = (int)red_t.size() - sg.rt0;
+    part_max = std::max(part_max, (size_t)std::max(pf, pt));
+    if (sg.nsmall || sg.ntile) segs.push_back(sg);
     i = j;
   }
-  SPAQR_CUDA(cudaMalloc(&P.d_ids, std::max<size_t>(ids.size(), 1) * sizeof(int)));
-  SPAQR_CUDA(cudaMemcpy(P.d_ids, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice));
-  for (auto& t : tmp) {
-    Segment sg;
-    sg.kind = t.kind;
-    sg.n_small = t.ns;
-    sg.n_large = t.nl;
-    sg.small_ids = P.d_ids + t.s0;
-    sg.large_ids = P.d_ids + t.l0;
-    sg.smem = (int)((size_t)t.maxc * (kW + 1) * sizeof(double));
-    P.segs.push_back(sg);
+  auto upload = [](auto& vec, auto** dst) {
+    using E = typename std::remove_reference<decltype(vec)>::type::value_type;
+    SPAQR_CUDA(cudaMalloc(reinterpret_cast<void**>(dst), std::max<size_t>(vec.size(), 1) * sizeof(E)));
+    if (!vec.empty())
+      SPAQR_CUDA(cudaMemcpy(*dst, vec.data(), vec.size() * sizeof(E), cudaMemcpyHostToDevice));
+  };
+  SmallOp<TW>* d_small = nullptr;
+  DenseOp<TW>* d_dense = nullptr;
+  upload(small, &d_small);
+  upload(dense, &d_dense);
+  P.d_small = d_small;
+  P.d_dense = d_dense;
+  upload(tiles, &P.d_tiles);
+  std::vector<int2> red(red_f);
+  const int rt_base = (int)red_f.size();
+  red.insert(red.end(), red_t.begin(), red_t.end());
+  for (auto& sg : segs) sg.rt0 += rt_base;
+  upload(red, &P.d_red);
+  SPAQR_CUDA(cudaMalloc(&P.d_dpart, std::max<size_t>(part_max, 1) * sizeof(TA)));
+  if (!small.empty()) {
+    recip_diag_kernel<TW><<<(unsigned)((small.size() + kW - 1) / kW), kT, 0, h.st>>>(d_small, (int)small.size());
+    SPAQR_CUDA(cudaGetLastError());
   }
+  if (!form_items.empty()) {
+    // scratch: one FP64 column of length cmax per warp in flight
+    const int64_t nit = (int64_t)form_items.size();
+    const int grid = (int)std::min<int64_t>((nit + kW - 1) / kW, 1216);
+    int2* d_items = nullptr;
+    double* d_scr = nullptr;
+    upload(form_items, &d_items);
+    SPAQR_CUDA(cudaMalloc(&d_scr, (size_t)grid * kW * cmax * sizeof(double)));
+    form_dense_kernel<TW><<<grid, kT, 0, h.st>>>(d_dense, d_items, nit, d_scr, cmax);
+    SPAQR_CUDA(cudaGetLastError());
+    SPAQR_CUDA(cudaStreamSynchronize(h.st));
+    cudaFree(d_items);
+    cudaFree(d_scr);
+  }
+  SPAQR_CUDA(cudaStreamSynchronize(h.st));
+  P.segs = segs;
+  P.launches = 0;
+  for (auto& sg : segs) P.launches += (sg.nsmall > 0) + 2 * (sg.ntile > 0);
+  set_dyn_smem(r_inv_warp_kernel<TW, TA>);
+  set_dyn_smem(r_invT_warp_kernel<TW, TA>);
+  set_dyn_smem(dense_T_kernel<TW, TA>);
 }
 
 void build_apply_plan(Handle& h) {
@@ -589,25 +618,9 @@ void build_apply_plan(Handle& h) {
   h.plan = new ApplyPlan();
   h.plan->fp32 = h.precision == SPAQR_PREC_MIXED;
   if (h.plan->fp32)
-    build_plan_t<float>(h, *h.plan);
+    build_plan_t<float, float>(h, *h.plan);
   else
-    build_plan_t<double>(h, *h.plan);
-  int mx = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  mx -= 1024;  // margin for the kernels' static shared memory
-  for (auto& s : h.plan->segs)
-    if (s.smem > mx) throw Error(SPAQR_ERR_CAPACITY, "apply: cluster too large for shared memory");
-  set_dyn_smem(r_inv_kernel<double>);
-  set_dyn_smem(r_inv_kernel<float>);
-  set_dyn_smem(r_invT_kernel<double>);
-  set_dyn_smem(r_invT_kernel<float>);
-  set_dyn_smem(q_kernel<double>);
-  set_dyn_smem(q_kernel<float>);
-  set_dyn_smem(r_inv_warp_kernel<double>);
-  set_dyn_smem(r_invT_warp_kernel<double>);
-  set_dyn_smem(r_inv_warp_kernel<float>);
-  set_dyn_smem(r_invT_warp_kernel<float>);
+    build_plan_t<double, double>(h, *h.plan);
   for (auto& e : h.plan->ev) SPAQR_CUDA(cudaEventCreate(&e));
   // algorithmic bytes of one W^{-1} plus one W^{-T} apply: every stored entry
   // once per direction, the slot indices, and the slot-vector reads/writes
@@ -615,6 +628,7 @@ void build_apply_plan(Handle& h) {
     const double es = h.plan->fp32 ? 4.0 : 8.0;
     double b = 0.0;
     for (auto& op : h.ops) {
+      if (op.kind == 2 && op.k <= 0) continue;
       const double c = op.c, w = op.kind == 0 ? op.w : 0, k = op.k;
       double stored = 0.0;
       if (op.kind == 0)
@@ -640,9 +654,12 @@ void free_apply_plan(Handle& h) {
   for (auto& e : h.plan->ev)
     if (e) cudaEventDestroy(e);
   if (h.plan->graph) cudaGraphExecDestroy(h.plan->graph);
-  cudaFree(h.plan->d_ops);
+  cudaFree(h.plan->d_small);
+  cudaFree(h.plan->d_dense);
   cudaFree(h.plan->d_idx);
-  cudaFree(h.plan->d_ids);
+  cudaFree(h.plan->d_tiles);
+  cudaFree(h.plan->d_red);
+  cudaFree(h.plan->d_dpart);
   cudaFree(h.plan->d_rdiag);
   cudaFree(h.plan->d_scal);
   cudaFree(h.plan->d_part);
@@ -650,65 +667,54 @@ void free_apply_plan(Handle& h) {
   h.plan = nullptr;
 }
 
-template <typename TW>
-static void apply_t(Handle& h, double* z, int transpose) {
+// The launches of one segment of W^{-1} (transpose = 0) or W^{-T}.
+template <typename TW, typename TA>
+static void run_segment(Handle& h, const Segment& s, double* z, int transpose) {
   ApplyPlan& P = *h.plan;
-  const ApplyOp<TW>* ops = static_cast<const ApplyOp<TW>*>(P.d_ops);
-  const int nseg = (int)P.segs.size();
-  for (int t = 0; t < nseg; ++t) {
-    const Segment& s = P.segs[(size_t)(transpose ? t : nseg - 1 - t)];
-    if (s.n_small) {
-      const int grid = (s.n_small + kW - 1) / kW;
-      if (s.kind == 2)
-        q_warp_kernel<TW><<<grid, kT, 0, h.st>>>(ops, s.small_ids, s.n_small, z, transpose);
-      else if (transpose)
-        r_invT_warp_kernel<TW><<<grid, kT, kWarpSmem<TW>, h.st>>>(ops, s.small_ids, s.n_small, z);
-      else
-        r_inv_warp_kernel<TW><<<grid, kT, kWarpSmem<TW>, h.st>>>(ops, s.small_ids, s.n_small, z);
-    }
-    if (s.n_large) {
-      if (s.kind == 2)
-        q_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z, transpose);
-      else if (transpose)
-        r_invT_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z);
-      else
-        r_inv_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z);
+  if (s.nsmall) {
+    const SmallOp<TW>* ops = static_cast<const SmallOp<TW>*>(P.d_small) + s.small0;
+    const int grid = (s.nsmall + kW - 1) / kW;
+    if (s.kind == 2)
+      q_warp_kernel<TW, TA><<<grid, kT, 0, h.st>>>(ops, s.nsmall, z, transpose);
+    else if (transpose)
+      r_invT_warp_kernel<TW, TA><<<grid, kT, kWarpSmem<TW>, h.st>>>(ops, s.nsmall, z);
+    else
+      r_inv_warp_kernel<TW, TA><<<grid, kT, kWarpSmem<TW>, h.st>>>(ops, s.nsmall, z);
+  }
+  if (s.ntile) {
+    const DenseOp<TW>* d = static_cast<const DenseOp<TW>*>(P.d_dense);
+    TA* part = static_cast<TA*>(P.d_dpart);
+    if (transpose) {
+      dense_T_kernel<TW, TA><<<s.ntile, kT, kStage * sizeof(TW), h.st>>>(d, P.d_tiles + s.tile0, z, part);
+      dense_T_reduce_kernel<TW, TA><<<s.nrt, kT, 0, h.st>>>(d, P.d_red + s.rt0, part, z);
+    } else {
+      dense_fwd_kernel<TW, TA><<<s.ntile, kT, 0, h.st>>>(d, P.d_tiles + s.tile0, z, part);
+      dense_fwd_reduce_kernel<TW, TA><<<s.nrf, kT, 0, h.st>>>(d, P.d_red + s.rf0, part, z);
     }
   }
+}
+
+template <typename TW, typename TA>
+static void apply_t(Handle& h, double* z, int transpose) {
+  ApplyPlan& P = *h.plan;
+  const int nseg = (int)P.segs.size();
+  for (int t = 0; t < nseg; ++t) run_segment<TW, TA>(h, P.segs[(size_t)(transpose ? t : nseg - 1 - t)], z, transpose);
   SPAQR_CUDA(cudaGetLastError());
 }
 
 // Diagnostic (SPAQR_PROFILE_APPLY=1): one W^{-1} and one W^{-T} with CUDA events
 // around every segment, printed to stderr as stage/kind/ops/microseconds.
-template <typename TW>
+template <typename TW, typename TA>
 static void profile_apply_t(Handle& h, double* z) {
   ApplyPlan& P = *h.plan;
-  const ApplyOp<TW>* ops = static_cast<const ApplyOp<TW>*>(P.d_ops);
   const int nseg = (int)P.segs.size();
   std::vector<cudaEvent_t> ev(2 * (size_t)nseg + 2);
   for (auto& e : ev) SPAQR_CUDA(cudaEventCreate(&e));
   for (int transpose = 0; transpose < 2; ++transpose) {
     for (int t = 0; t < nseg; ++t) {
       const int si = transpose ? t : nseg - 1 - t;
-      const Segment& s = P.segs[(size_t)si];
       SPAQR_CUDA(cudaEventRecord(ev[2 * (size_t)t], h.st));
-      if (s.n_small) {
-        const int grid = (s.n_small + kW - 1) / kW;
-        if (s.kind == 2)
-          q_warp_kernel<TW><<<grid, kT, 0, h.st>>>(ops, s.small_ids, s.n_small, z, transpose);
-        else if (transpose)
-          r_invT_warp_kernel<TW><<<grid, kT, kWarpSmem<TW>, h.st>>>(ops, s.small_ids, s.n_small, z);
-        else
-          r_inv_warp_kernel<TW><<<grid, kT, kWarpSmem<TW>, h.st>>>(ops, s.small_ids, s.n_small, z);
-      }
-      if (s.n_large) {
-        if (s.kind == 2)
-          q_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z, transpose);
-        else if (transpose)
-          r_invT_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z);
-        else
-          r_inv_kernel<TW><<<s.n_large, kT, (size_t)s.smem, h.st>>>(ops, s.large_ids, z);
-      }
+      run_segment<TW, TA>(h, P.segs[(size_t)si], z, transpose);
       SPAQR_CUDA(cudaEventRecord(ev[2 * (size_t)t + 1], h.st));
     }
     SPAQR_CUDA(cudaStreamSynchronize(h.st));
@@ -720,8 +726,8 @@ static void profile_apply_t(Handle& h, double* z) {
       cudaEventElapsedTime(&ms, ev[2 * (size_t)t], ev[2 * (size_t)t + 1]);
       tot += ms;
       if (ms > 0.05f)
-        std::fprintf(stderr, "[spaqr] apply %s seg %3d kind %d small %6d large %5d: %8.1f us\n",
-                     transpose ? "W^-T" : "W^-1", si, s.kind, s.n_small, s.n_large, ms * 1e3);
+        std::fprintf(stderr, "[spaqr] apply %s seg %3d kind %d small %6d tiles %6d: %8.1f us\n",
+                     transpose ? "W^-T" : "W^-1", si, s.kind, s.nsmall, s.ntile, ms * 1e3);
     }
     std::fprintf(stderr, "[spaqr] apply %s total %.3f ms over %d segments\n", transpose ? "W^-T" : "W^-1", tot, nseg);
   }
@@ -730,17 +736,17 @@ static void profile_apply_t(Handle& h, double* z) {
 
 void profile_apply(Handle& h, double* z) {
   if (h.plan->fp32)
-    profile_apply_t<float>(h, z);
+    profile_apply_t<float, float>(h, z);
   else
-    profile_apply_t<double>(h, z);
+    profile_apply_t<double, double>(h, z);
 }
 
 void apply_Winv(Handle& h, double* z, int transpose) {
   if (!h.plan) throw Error(SPAQR_ERR_INVALID_ARG, "no factorization");
   if (h.plan->fp32)
-    apply_t<float>(h, z, transpose);
+    apply_t<float, float>(h, z, transpose);
   else
-    apply_t<double>(h, z, transpose);
+    apply_t<double, double>(h, z, transpose);
 }
 
 void apply_A(Handle& h, const double* x, double* y, int forward) {
@@ -794,9 +800,7 @@ static void accumulate_solve_timers(Handle& h) {
       cudaEventElapsedTime(&c, P.ev[4], P.ev[5]) == cudaSuccess &&
       cudaEventElapsedTime(&d, P.ev[6], P.ev[7]) == cudaSuccess) {
     h.stats.t_kernel[4] += (a + b) * 1e-3;
-    int64_t launches = 0;
-    for (auto& sg : P.segs) launches += (sg.n_small > 0) + (sg.n_large > 0);
-    h.stats.n_kernel[4] += 2 * launches;
+    h.stats.n_kernel[4] += 2 * P.launches;
     h.stats.t_kernel[5] += (c + d) * 1e-3;
     h.stats.n_kernel[5] += 2;
   } else {
