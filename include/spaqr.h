@@ -145,6 +145,52 @@ int spaqr_apply_Winv(spaqr_handle* h, double* z, int transpose);
  * y: n); device pointers.  The scaled operator the preconditioner is built for. */
 int spaqr_apply_A(spaqr_handle* h, const double* x, double* y, int forward);
 
+/* ------------------------------------------------------------------ adjoint
+ * x(A, b) = argmin ||A x - b|| = (A^T A)^{-1} A^T b (Section 1).  For a loss L
+ * with g = dL/dx, lambda = (A^T A)^{-1} g and r = b - A x give
+ *     dL/db = A lambda,     dL/dA_ij = r_i lambda_j - (A lambda)_i x_j
+ * on the nonzeros of A.  The factor is reused for lambda: A^T A =
+ * D^{-1} (A D)^T (A D) D^{-1} and (A D)^T (A D) ~= W^T W (Section 2.7). */
+
+/* spaqr_solve_normal: lambda = (A^T A)^{-1} g by conjugate gradients on
+ * (A D)^T (A D) nu = D g, lambda = D nu, preconditioned by W^{-1} W^{-T}
+ * (a triangular/orthogonal sweep with W^{-T}, then one with W^{-1}).  Stops
+ * when ||g - A^T A lambda|| / ||g|| < tol or after the handle's maxit
+ * iterations.  g and lambda have n entries; host pointers (on_device = 0,
+ * copied inside the call) or device pointers.  Returns NOT_CONVERGED (lambda
+ * and info written) at maxit; info may be NULL. */
+int spaqr_solve_normal(spaqr_handle* h, const double* g, double* lambda, int on_device, double tol,
+                       spaqr_solve_info* info);
+
+/* spaqr_lstsq_grad: from b (m), x (n) and lambda (n), write dL/db (m entries)
+ * and dL/dvals (nnz entries, in the CSR order of A) with one fused kernel (one
+ * thread per row of A).  Either output may be NULL.  Host or device pointers
+ * per on_device. */
+int spaqr_lstsq_grad(spaqr_handle* h, const double* b, const double* x, const double* lambda, double* grad_b,
+                     double* grad_vals, int on_device);
+
+/* spaqr_update_values: A <- A' with the pattern unchanged; vals holds the nnz
+ * values in the CSR order of A (host or device per on_device).
+ * refactor = 0: the solves use A' and the factor built for A stays the
+ *   preconditioner (the solves still converge to the solution for A': CGLS
+ *   stops on the residual of A'); the column scaling D is kept.
+ * refactor != 0: the factorization is redone for A' with the handle's
+ *   options and the analysis an (required then; D is recomputed).
+ * Errors: INVALID_ARG (null vals, or refactor without an analysis). */
+int spaqr_update_values(spaqr_handle* h, const spaqr_analysis* an, const double* vals, int on_device,
+                        int refactor);
+
+/* Batched solves over `count` independent handles (for example many problems
+ * with one pattern): hs[i] with b[i] -> x[i] (CGLS) or g[i] -> lambda[i]
+ * (normal equations), each as in the single-problem call.  The iterations of
+ * all handles advance side by side, each on its own handle's stream, with one
+ * residual read per handle per iteration.  infos (count entries) may be NULL.
+ * Returns the first error, else NOT_CONVERGED if some handle did not converge. */
+int spaqr_solve_batch(int count, spaqr_handle* const* hs, const double* const* b, double* const* x, int on_device,
+                      spaqr_solve_info* infos);
+int spaqr_solve_normal_batch(int count, spaqr_handle* const* hs, const double* const* g, double* const* lambda,
+                             int on_device, double tol, spaqr_solve_info* infos);
+
 typedef struct {
   double t_analyze;  /* seconds in spaqr_analyze (copied from the analysis) */
   double t_factor;   /* seconds in spaqr_factor */

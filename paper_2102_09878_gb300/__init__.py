@@ -13,7 +13,8 @@ import numpy as np
 from . import capi
 from .capi import SpaqrError
 
-__all__ = ["Analysis", "SpaQR", "SpaqrError", "dense_front_qr", "dense_qrcp", "capi"]
+__all__ = ["Analysis", "SpaQR", "SpaqrError", "dense_front_qr", "dense_qrcp", "solve_batch", "solve_normal_batch",
+           "capi"]
 
 
 def _stream_ptr(stream):
@@ -120,6 +121,57 @@ class SpaQR:
                               seconds=info.seconds)
         return x
 
+    def solve_normal(self, g, tol: float = 1e-12, check_convergence: bool = True):
+        """lambda = (A^T A)^{-1} g by CG preconditioned with W^{-1} W^{-T} (numpy or CUDA float64)."""
+        lib = capi.load()
+        info = capi.SolveInfo()
+        if hasattr(g, "is_cuda") and g.is_cuda:
+            import torch
+
+            lam = torch.empty(self.n, dtype=torch.float64, device=g.device)
+            gg = g.contiguous()
+            rc = lib.spaqr_solve_normal(self._h, capi.ptr(gg), capi.ptr(lam), 1, float(tol), C.byref(info))
+        else:
+            gg = np.ascontiguousarray(g, dtype=np.float64)
+            lam = np.zeros(self.n)
+            rc = lib.spaqr_solve_normal(self._h, capi.ptr(gg), capi.ptr(lam), 0, float(tol), C.byref(info))
+        if rc != capi.SPAQR_OK and (check_convergence or rc != 4):
+            capi.check(rc)
+        self.last_normal_info = dict(iters=info.iters, rel=info.rel_resid, converged=bool(info.converged),
+                                     seconds=info.seconds)
+        return lam
+
+    def lstsq_grad(self, b, x, lam):
+        """(dL/db, dL/dvals) of x = argmin ||A x - b|| given lambda = (A^T A)^{-1} dL/dx."""
+        lib = capi.load()
+        if hasattr(b, "is_cuda") and b.is_cuda:
+            import torch
+
+            gb = torch.empty(self.m, dtype=torch.float64, device=b.device)
+            gv = torch.empty(int(self._rowptr[-1]), dtype=torch.float64, device=b.device)
+            bb, xx, ll = b.contiguous(), x.contiguous(), lam.contiguous()
+            capi.check(lib.spaqr_lstsq_grad(self._h, capi.ptr(bb), capi.ptr(xx), capi.ptr(ll), capi.ptr(gb),
+                                            capi.ptr(gv), 1))
+        else:
+            bb, xx, ll = (np.ascontiguousarray(v, dtype=np.float64) for v in (b, x, lam))
+            gb = np.zeros(self.m)
+            gv = np.zeros(int(self._rowptr[-1]))
+            capi.check(lib.spaqr_lstsq_grad(self._h, capi.ptr(bb), capi.ptr(xx), capi.ptr(ll), capi.ptr(gb),
+                                            capi.ptr(gv), 0))
+        return gb, gv
+
+    def update_values(self, vals, refactor: bool = False):
+        """New values of A (same pattern, CSR order).  refactor=False keeps the
+        factor as the preconditioner; refactor=True redoes the factorization."""
+        lib = capi.load()
+        an = self._analysis.handle if refactor else None
+        if hasattr(vals, "is_cuda") and vals.is_cuda:
+            vv = vals.contiguous()
+            capi.check(lib.spaqr_update_values(self._h, an, capi.ptr(vv), 1, 1 if refactor else 0))
+        else:
+            vv = np.ascontiguousarray(vals, dtype=np.float64)
+            capi.check(lib.spaqr_update_values(self._h, an, capi.ptr(vv), 0, 1 if refactor else 0))
+
     def apply_Winv(self, z, transpose: bool = False):
         """In place z <- W^{-1} z (or W^{-T} z) for a CUDA float64 tensor of length n."""
         assert z.is_cuda and z.dtype.is_floating_point and z.element_size() == 8 and z.is_contiguous()
@@ -182,6 +234,36 @@ class SpaQR:
                 self._h = None
         except Exception:
             pass
+
+
+def _batch(fn, solvers, vecs, n_out, *extra):
+    lib = capi.load()
+    cnt = len(solvers)
+    hs = (C.c_void_p * cnt)(*[s._h.value for s in solvers])
+    infos = (capi.SolveInfo * cnt)()
+    on_dev = hasattr(vecs[0], "is_cuda") and vecs[0].is_cuda
+    if on_dev:
+        import torch
+
+        ins = [v.contiguous() for v in vecs]
+        outs = [torch.empty(n_out(s), dtype=torch.float64, device=v.device) for s, v in zip(solvers, vecs)]
+    else:
+        ins = [np.ascontiguousarray(v, dtype=np.float64) for v in vecs]
+        outs = [np.zeros(n_out(s)) for s in solvers]
+    ip = (C.c_void_p * cnt)(*[capi.ptr(v) for v in ins])
+    op = (C.c_void_p * cnt)(*[capi.ptr(v) for v in outs])
+    capi.check(getattr(lib, fn)(cnt, hs, ip, op, 1 if on_dev else 0, *extra, infos))
+    return outs, [dict(iters=i.iters, rel=i.rel_resid, converged=bool(i.converged)) for i in infos]
+
+
+def solve_batch(solvers, bs):
+    """x_i = argmin ||A_i x - b_i|| for several factorizations, iterated side by side."""
+    return _batch("spaqr_solve_batch", solvers, bs, lambda s: s.n)
+
+
+def solve_normal_batch(solvers, gs, tol: float = 1e-12):
+    """lambda_i = (A_i^T A_i)^{-1} g_i for several factorizations, iterated side by side."""
+    return _batch("spaqr_solve_normal_batch", solvers, gs, lambda s: s.n, C.c_double(tol))
 
 
 # ----------------------------------------------------------- dense kernels

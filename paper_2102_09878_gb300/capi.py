@@ -106,6 +106,14 @@ SIGNATURES = {
     "spaqr_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(SolveInfo)]),
     "spaqr_apply_Winv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "spaqr_apply_A": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "spaqr_solve_normal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(SolveInfo)]),
+    "spaqr_lstsq_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "spaqr_update_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    "spaqr_solve_batch": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "spaqr_solve_normal_batch": (
+        C.c_int,
+        [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p],
+    ),
     "spaqr_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "spaqr_num_ops": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "spaqr_op_info": (

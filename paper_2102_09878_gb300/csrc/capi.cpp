@@ -78,6 +78,101 @@ Handle::~Handle() {
 }
 }  // namespace spaqr
 
+namespace {
+// Checks A, factors it and builds the solve-side state (spaqr_factor and the
+// refactorization of spaqr_update_values).
+std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Analysis& a, const spaqr_options& opt) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (A->n != a.n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A has n != nx*ny*nz columns");
+  if (A->m < A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A must have m >= n");
+  if (!A->rowptr || !A->colidx || !A->vals) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "null CSR array");
+  if (A->rowptr[0] != 0 || A->rowptr[A->m] != A->nnz) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "bad rowptr");
+  for (int64_t r = 0; r < A->m; ++r)
+    if (A->rowptr[r + 1] < A->rowptr[r]) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "rowptr not monotone");
+  for (int64_t e = 0; e < A->nnz; ++e)
+    if (A->colidx[e] < 0 || A->colidx[e] >= A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "column index out of range");
+  auto hd = std::make_unique<spaqr::Handle>();
+  spaqr::Handle& h = *hd;
+  h.opt = opt;
+  if (h.opt.skip < 0) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "skip must be >= 0");
+  if (h.opt.row_rule != SPAQR_ROWS_TREE && h.opt.row_rule != SPAQR_ROWS_ANY)
+    throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "unknown row rule");
+  if (!(h.opt.eps >= 0.0)) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "eps must be >= 0");
+  // all library work runs on a non-blocking stream of its own unless the
+  // caller gives one (the legacy default stream cannot be graph-captured)
+  h.user_st = static_cast<cudaStream_t>(h.opt.stream);
+  if (h.user_st) {
+    h.st = h.user_st;
+  } else {
+    SPAQR_CUDA(cudaStreamCreateWithFlags(&h.st, cudaStreamNonBlocking));
+    h.own_stream = true;
+  }
+  h.precision = h.opt.precision;
+  h.m = A->m;
+  h.n = A->n;
+  h.nnz = A->nnz;
+  h.depth = a.depth;
+  h.t_analyze = a.seconds;
+  spaqr::run_factor(h, *A, a);
+  // scaled operator A~ = A D and its transpose on the device (FP64)
+  std::vector<double> v((size_t)A->nnz);
+  for (int64_t e = 0; e < A->nnz; ++e) v[(size_t)e] = A->vals[e] * h.D[(size_t)A->colidx[e]];
+  std::vector<int64_t> trp((size_t)A->n + 1, 0);
+  for (int64_t e = 0; e < A->nnz; ++e) trp[(size_t)A->colidx[e] + 1]++;
+  for (int64_t j = 0; j < A->n; ++j) trp[(size_t)j + 1] += trp[(size_t)j];
+  std::vector<int32_t> tci((size_t)A->nnz);
+  std::vector<double> tv((size_t)A->nnz);
+  std::vector<int64_t> tperm((size_t)A->nnz);
+  {
+    std::vector<int64_t> pos(trp.begin(), trp.end() - 1);
+    for (int64_t r = 0; r < A->m; ++r)
+      for (int64_t e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e) {
+        const int64_t q = pos[(size_t)A->colidx[e]]++;
+        tci[(size_t)q] = (int32_t)r;
+        tv[(size_t)q] = v[(size_t)e];
+        tperm[(size_t)q] = e;
+      }
+  }
+  SPAQR_CUDA(cudaMalloc(&h.d_rowptr, (size_t)(A->m + 1) * sizeof(int64_t)));
+  SPAQR_CUDA(cudaMalloc(&h.d_colidx, (size_t)A->nnz * sizeof(int32_t)));
+  SPAQR_CUDA(cudaMalloc(&h.d_vals, (size_t)A->nnz * sizeof(double)));
+  SPAQR_CUDA(cudaMalloc(&h.d_trowptr, (size_t)(A->n + 1) * sizeof(int64_t)));
+  SPAQR_CUDA(cudaMalloc(&h.d_tcolidx, (size_t)A->nnz * sizeof(int32_t)));
+  SPAQR_CUDA(cudaMalloc(&h.d_tvals, (size_t)A->nnz * sizeof(double)));
+  SPAQR_CUDA(cudaMalloc(&h.d_D, (size_t)A->n * sizeof(double)));
+  SPAQR_CUDA(cudaMalloc(&h.d_tperm, (size_t)std::max<int64_t>(A->nnz, 1) * sizeof(int64_t)));
+  SPAQR_CUDA(cudaMemcpyAsync(h.d_rowptr, A->rowptr, (size_t)(A->m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
+  SPAQR_CUDA(cudaMemcpyAsync(h.d_colidx, A->colidx, (size_t)A->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, h.st));
+  SPAQR_CUDA(cudaMemcpyAsync(h.d_vals, v.data(), (size_t)A->nnz * sizeof(double), cudaMemcpyHostToDevice, h.st));
+  SPAQR_CUDA(cudaMemcpyAsync(h.d_trowptr, trp.data(), trp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
+  SPAQR_CUDA(cudaMemcpyAsync(h.d_tcolidx, tci.data(), tci.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h.st));
+  SPAQR_CUDA(cudaMemcpyAsync(h.d_tvals, tv.data(), tv.size() * sizeof(double), cudaMemcpyHostToDevice, h.st));
+  SPAQR_CUDA(cudaMemcpyAsync(h.d_D, h.D.data(), h.D.size() * sizeof(double), cudaMemcpyHostToDevice, h.st));
+  if (A->nnz)
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_tperm, tperm.data(), tperm.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
+  h.rowptr.assign(A->rowptr, A->rowptr + A->m + 1);
+  h.colidx.assign(A->colidx, A->colidx + A->nnz);
+  spaqr::build_apply_plan(h);
+  SPAQR_CUDA(cudaStreamSynchronize(h.st));
+  int64_t nnzW = 0;
+  for (auto& op : h.ops) {
+    const int64_t c = op.c;
+    if (op.kind == 0)
+      nnzW += c * (c + 1) / 2 + c * op.w;
+    else if (op.kind == 1)
+      nnzW += c * (c + 1) / 2;
+    else
+      nnzW += c * op.k;
+  }
+  h.stats.nnz_W = nnzW;
+  h.stats.n_ops = (int64_t)h.ops.size();
+  h.stats.t_analyze = h.t_analyze;
+  h.stats.t_factor = secs_since(t0);
+  return hd;
+}
+
+}  // namespace
+
 extern "C" {
 
 void spaqr_default_options(spaqr_options* o) {
@@ -133,89 +228,12 @@ int spaqr_factor(const spaqr_csr* A, const spaqr_analysis* an, const spaqr_optio
   if (!A || !an || !out) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
   if (int rc = need_device()) return rc;
   return guarded([&] {
-    auto t0 = std::chrono::steady_clock::now();
-    const spaqr::Analysis& a = *an->an;
-    if (A->n != a.n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A has n != nx*ny*nz columns");
-    if (A->m < A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A must have m >= n");
-    if (!A->rowptr || !A->colidx || !A->vals) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "null CSR array");
-    if (A->rowptr[0] != 0 || A->rowptr[A->m] != A->nnz) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "bad rowptr");
-    for (int64_t r = 0; r < A->m; ++r)
-      if (A->rowptr[r + 1] < A->rowptr[r]) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "rowptr not monotone");
-    for (int64_t e = 0; e < A->nnz; ++e)
-      if (A->colidx[e] < 0 || A->colidx[e] >= A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "column index out of range");
-    auto hd = std::make_unique<spaqr::Handle>();
-    spaqr::Handle& h = *hd;
+    spaqr_options o;
     if (opt)
-      h.opt = *opt;
+      o = *opt;
     else
-      spaqr_default_options(&h.opt);
-    if (h.opt.skip < 0) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "skip must be >= 0");
-    if (h.opt.row_rule != SPAQR_ROWS_TREE && h.opt.row_rule != SPAQR_ROWS_ANY)
-      throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "unknown row rule");
-    if (!(h.opt.eps >= 0.0)) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "eps must be >= 0");
-    // all library work runs on a non-blocking stream of its own unless the
-    // caller gives one (the legacy default stream cannot be graph-captured)
-    h.user_st = static_cast<cudaStream_t>(h.opt.stream);
-    if (h.user_st) {
-      h.st = h.user_st;
-    } else {
-      SPAQR_CUDA(cudaStreamCreateWithFlags(&h.st, cudaStreamNonBlocking));
-      h.own_stream = true;
-    }
-    h.precision = h.opt.precision;
-    h.m = A->m;
-    h.n = A->n;
-    h.nnz = A->nnz;
-    h.depth = a.depth;
-    h.t_analyze = a.seconds;
-    spaqr::run_factor(h, *A, a);
-    // scaled operator A~ = A D and its transpose on the device (FP64)
-    std::vector<double> v((size_t)A->nnz);
-    for (int64_t e = 0; e < A->nnz; ++e) v[(size_t)e] = A->vals[e] * h.D[(size_t)A->colidx[e]];
-    std::vector<int64_t> trp((size_t)A->n + 1, 0);
-    for (int64_t e = 0; e < A->nnz; ++e) trp[(size_t)A->colidx[e] + 1]++;
-    for (int64_t j = 0; j < A->n; ++j) trp[(size_t)j + 1] += trp[(size_t)j];
-    std::vector<int32_t> tci((size_t)A->nnz);
-    std::vector<double> tv((size_t)A->nnz);
-    {
-      std::vector<int64_t> pos(trp.begin(), trp.end() - 1);
-      for (int64_t r = 0; r < A->m; ++r)
-        for (int64_t e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e) {
-          const int64_t q = pos[(size_t)A->colidx[e]]++;
-          tci[(size_t)q] = (int32_t)r;
-          tv[(size_t)q] = v[(size_t)e];
-        }
-    }
-    SPAQR_CUDA(cudaMalloc(&h.d_rowptr, (size_t)(A->m + 1) * sizeof(int64_t)));
-    SPAQR_CUDA(cudaMalloc(&h.d_colidx, (size_t)A->nnz * sizeof(int32_t)));
-    SPAQR_CUDA(cudaMalloc(&h.d_vals, (size_t)A->nnz * sizeof(double)));
-    SPAQR_CUDA(cudaMalloc(&h.d_trowptr, (size_t)(A->n + 1) * sizeof(int64_t)));
-    SPAQR_CUDA(cudaMalloc(&h.d_tcolidx, (size_t)A->nnz * sizeof(int32_t)));
-    SPAQR_CUDA(cudaMalloc(&h.d_tvals, (size_t)A->nnz * sizeof(double)));
-    SPAQR_CUDA(cudaMalloc(&h.d_D, (size_t)A->n * sizeof(double)));
-    SPAQR_CUDA(cudaMemcpyAsync(h.d_rowptr, A->rowptr, (size_t)(A->m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
-    SPAQR_CUDA(cudaMemcpyAsync(h.d_colidx, A->colidx, (size_t)A->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, h.st));
-    SPAQR_CUDA(cudaMemcpyAsync(h.d_vals, v.data(), (size_t)A->nnz * sizeof(double), cudaMemcpyHostToDevice, h.st));
-    SPAQR_CUDA(cudaMemcpyAsync(h.d_trowptr, trp.data(), trp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
-    SPAQR_CUDA(cudaMemcpyAsync(h.d_tcolidx, tci.data(), tci.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h.st));
-    SPAQR_CUDA(cudaMemcpyAsync(h.d_tvals, tv.data(), tv.size() * sizeof(double), cudaMemcpyHostToDevice, h.st));
-    SPAQR_CUDA(cudaMemcpyAsync(h.d_D, h.D.data(), h.D.size() * sizeof(double), cudaMemcpyHostToDevice, h.st));
-    spaqr::build_apply_plan(h);
-    SPAQR_CUDA(cudaStreamSynchronize(h.st));
-    int64_t nnzW = 0;
-    for (auto& op : h.ops) {
-      const int64_t c = op.c;
-      if (op.kind == 0)
-        nnzW += c * (c + 1) / 2 + c * op.w;
-      else if (op.kind == 1)
-        nnzW += c * (c + 1) / 2;
-      else
-        nnzW += c * op.k;
-    }
-    h.stats.nnz_W = nnzW;
-    h.stats.n_ops = (int64_t)h.ops.size();
-    h.stats.t_analyze = h.t_analyze;
-    h.stats.t_factor = secs_since(t0);
+      spaqr_default_options(&o);
+    auto hd = build_handle(A, *an->an, o);
     auto* out_h = new spaqr_handle();
     out_h->h = std::move(hd);
     *out = out_h;
@@ -267,6 +285,151 @@ int spaqr_apply_A(spaqr_handle* hh, const double* x, double* y, int forward) {
     hh->h->wait_caller();
     spaqr::apply_A(*hh->h, x, y, forward ? 1 : 0);
     SPAQR_CUDA(cudaStreamSynchronize(hh->h->st));
+    return SPAQR_OK;
+  });
+}
+
+namespace {
+// Device staging of host vectors for the calls that take on_device = 0.
+struct Staged {
+  double* base = nullptr;
+  ~Staged() {
+    if (base) cudaFree(base);
+  }
+};
+
+// Runs IterSolve on several handles; in/out are host or device vectors.  CGLS
+// (kind 0) stops at each handle's own tolerance, PCG (kind 1) at tol.
+int run_batch(int count, spaqr_handle* const* hs, const double* const* in, double* const* out, int on_device,
+              int kind, double tol, spaqr_solve_info* infos) {
+  if (count < 0 || (count > 0 && (!hs || !in || !out))) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  for (int i = 0; i < count; ++i)
+    if (!hs[i] || !in[i] || !out[i]) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  if (kind == 1 && !(tol > 0.0)) return fail(SPAQR_ERR_INVALID_ARG, "tol must be > 0");
+  return guarded([&] {
+    std::vector<Staged> stage((size_t)count);
+    std::vector<spaqr::IterSolve> S((size_t)count);
+    for (int i = 0; i < count; ++i) {
+      spaqr::Handle& h = *hs[i]->h;
+      const int64_t nin = kind == 0 ? h.m : h.n;
+      spaqr::IterSolve& s = S[(size_t)i];
+      s.h = &h;
+      s.kind = kind;
+      s.tol = kind == 0 ? h.opt.tol : tol;
+      s.maxit = h.opt.maxit;
+      if (on_device) {
+        h.wait_caller();
+        s.rhs = in[i];
+        s.out = out[i];
+      } else {
+        SPAQR_CUDA(cudaMalloc(&stage[(size_t)i].base, (size_t)(nin + h.n) * sizeof(double)));
+        SPAQR_CUDA(cudaMemcpyAsync(stage[(size_t)i].base, in[i], (size_t)nin * sizeof(double), cudaMemcpyHostToDevice,
+                                   h.st));
+        s.rhs = stage[(size_t)i].base;
+        s.out = stage[(size_t)i].base + nin;
+      }
+    }
+    spaqr::run_iterative(S);
+    bool all = true;
+    for (int i = 0; i < count; ++i) {
+      spaqr::Handle& h = *hs[i]->h;
+      if (!on_device) {
+        SPAQR_CUDA(cudaMemcpyAsync(out[i], S[(size_t)i].out, (size_t)h.n * sizeof(double), cudaMemcpyDeviceToHost, h.st));
+        SPAQR_CUDA(cudaStreamSynchronize(h.st));
+      }
+      spaqr_solve_info inf{};
+      S[(size_t)i].report(&inf);
+      if (infos) infos[i] = inf;
+      all = all && inf.converged;
+    }
+    return all ? SPAQR_OK : fail(SPAQR_ERR_NOT_CONVERGED, kind == 0 ? "CGLS reached maxit" : "PCG reached maxit");
+  });
+}
+}  // namespace
+
+int spaqr_solve_batch(int count, spaqr_handle* const* hs, const double* const* b, double* const* x, int on_device,
+                      spaqr_solve_info* infos) {
+  if (count == 0) return SPAQR_OK;
+  return run_batch(count, hs, b, x, on_device, 0, 0.0, infos);
+}
+
+int spaqr_solve_normal_batch(int count, spaqr_handle* const* hs, const double* const* g, double* const* lambda,
+                             int on_device, double tol, spaqr_solve_info* infos) {
+  if (count == 0) return SPAQR_OK;
+  return run_batch(count, hs, g, lambda, on_device, 1, tol, infos);
+}
+
+int spaqr_solve_normal(spaqr_handle* hh, const double* g, double* lambda, int on_device, double tol,
+                       spaqr_solve_info* info) {
+  if (!hh || !g || !lambda) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  spaqr_handle* hs[1] = {hh};
+  const double* in[1] = {g};
+  double* out[1] = {lambda};
+  return run_batch(1, hs, in, out, on_device, 1, tol, info);
+}
+
+int spaqr_lstsq_grad(spaqr_handle* hh, const double* b, const double* x, const double* lambda, double* grad_b,
+                     double* grad_vals, int on_device) {
+  if (!hh || !b || !x || !lambda) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    spaqr::Handle& h = *hh->h;
+    if (on_device) {
+      h.wait_caller();
+      spaqr::lstsq_grad(h, b, x, lambda, grad_b, grad_vals);
+      SPAQR_CUDA(cudaStreamSynchronize(h.st));
+      return SPAQR_OK;
+    }
+    Staged st;
+    const size_t m = (size_t)h.m, n = (size_t)h.n, nnz = (size_t)h.nnz;
+    SPAQR_CUDA(cudaMalloc(&st.base, (2 * m + 2 * n + nnz) * sizeof(double)));
+    double* db = st.base;
+    double* dx = db + m;
+    double* dl = dx + n;
+    double* dgb = dl + n;
+    double* dgv = dgb + m;
+    SPAQR_CUDA(cudaMemcpyAsync(db, b, m * sizeof(double), cudaMemcpyHostToDevice, h.st));
+    SPAQR_CUDA(cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, h.st));
+    SPAQR_CUDA(cudaMemcpyAsync(dl, lambda, n * sizeof(double), cudaMemcpyHostToDevice, h.st));
+    spaqr::lstsq_grad(h, db, dx, dl, grad_b ? dgb : nullptr, grad_vals ? dgv : nullptr);
+    if (grad_b) SPAQR_CUDA(cudaMemcpyAsync(grad_b, dgb, m * sizeof(double), cudaMemcpyDeviceToHost, h.st));
+    if (grad_vals) SPAQR_CUDA(cudaMemcpyAsync(grad_vals, dgv, nnz * sizeof(double), cudaMemcpyDeviceToHost, h.st));
+    SPAQR_CUDA(cudaStreamSynchronize(h.st));
+    return SPAQR_OK;
+  });
+}
+
+int spaqr_update_values(spaqr_handle* hh, const spaqr_analysis* an, const double* vals, int on_device, int refactor) {
+  if (!hh || !vals) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  if (refactor && !an) return fail(SPAQR_ERR_INVALID_ARG, "a refactorization needs the analysis");
+  return guarded([&] {
+    spaqr::Handle& h = *hh->h;
+    const size_t nnz = (size_t)h.nnz;
+    if (refactor) {
+      std::vector<double> v(nnz);
+      if (on_device) {
+        h.wait_caller();
+        SPAQR_CUDA(cudaMemcpyAsync(v.data(), vals, nnz * sizeof(double), cudaMemcpyDeviceToHost, h.st));
+        SPAQR_CUDA(cudaStreamSynchronize(h.st));
+      } else {
+        std::copy(vals, vals + nnz, v.begin());
+      }
+      spaqr_csr A{h.m, h.n, h.nnz, h.rowptr.data(), h.colidx.data(), v.data()};
+      spaqr_options o = h.opt;
+      auto fresh = build_handle(&A, *an->an, o);
+      hh->h = std::move(fresh);
+      return SPAQR_OK;
+    }
+    Staged st;
+    const double* dv = vals;
+    if (on_device) {
+      h.wait_caller();
+    } else {
+      SPAQR_CUDA(cudaMalloc(&st.base, std::max<size_t>(nnz, 1) * sizeof(double)));
+      SPAQR_CUDA(cudaMemcpyAsync(st.base, vals, nnz * sizeof(double), cudaMemcpyHostToDevice, h.st));
+      dv = st.base;
+    }
+    spaqr::set_values(h, dv);
+    SPAQR_CUDA(cudaStreamSynchronize(h.st));
     return SPAQR_OK;
   });
 }

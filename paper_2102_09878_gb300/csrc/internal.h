@@ -7,6 +7,7 @@
 #include <stdexcept>
 #include <string>
 #include <unordered_map>
+#include <chrono>
 #include <vector>
 
 #include "../../include/spaqr.h"
@@ -166,7 +167,10 @@ struct Handle {
   int64_t* d_trowptr = nullptr;
   int32_t* d_tcolidx = nullptr;
   double* d_tvals = nullptr;
+  int64_t* d_tperm = nullptr;  // transposed position -> row-major position
   double* d_D = nullptr;  // column scaling
+  std::vector<int64_t> rowptr;  // host copy of the pattern (for a refactorization)
+  std::vector<int32_t> colidx;
   std::vector<double> D;
   // W store
   Arena wpool{size_t(64) << 20};
@@ -192,5 +196,33 @@ void free_apply_plan(Handle& h);
 void apply_Winv(Handle& h, double* z, int transpose);
 void apply_A(Handle& h, const double* x, double* y, int forward);
 void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info);
+// Adjoint pieces: g_b = A lambda, g_A = r lambda^T - (A lambda) x^T on the pattern.
+void lstsq_grad(Handle& h, const double* b, const double* x, const double* lam, double* gb, double* gv);
+// New values of A (same pattern, device array in the caller's CSR order).
+void set_values(Handle& h, const double* a_dev);
+
+// One iterative solve on one handle: kind 0 = CGLS for min ||A x - b|| (rhs b,
+// out x), kind 1 = PCG for (A^T A) lambda = g (rhs g, out lambda), both
+// preconditioned by the factor W.  run_iterative() advances several of them
+// side by side, one iteration per handle per round.
+struct IterSolve {
+  Handle* h = nullptr;
+  int kind = 0;
+  const double* rhs = nullptr;
+  double* out = nullptr;
+  double tol = 1e-10;
+  int maxit = 500;
+  int it = 0;
+  bool done = false;
+  double norm0 = 0.0, rel = 0.0;
+  std::chrono::steady_clock::time_point t0;
+  void begin();
+  void begun();
+  void step();
+  void stepped();
+  void finish();
+  void report(spaqr_solve_info* info);
+};
+void run_iterative(std::vector<IterSolve>& S);
 
 }  // namespace spaqr

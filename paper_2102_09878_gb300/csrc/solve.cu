@@ -415,6 +415,63 @@ __global__ void __launch_bounds__(kT) scale_kernel(int64_t n, const double* a, c
   if (i < n) out[i] = a[i] * d[i];
 }
 
+// per-block partial sums of x_i y_i / wdiv_i^2 (wdiv may be null)
+__global__ void __launch_bounds__(kT) dot_kernel(int64_t n, const double* x, const double* y, const double* wdiv,
+                                                 double* part) {
+  __shared__ double red[kW];
+  double sq = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const double t = x[i] * y[i];
+    sq += wdiv ? t / (wdiv[i] * wdiv[i]) : t;
+  }
+  sq = wsum(sq);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kW; ++q) t += red[q];
+    part[blockIdx.x] = t;
+  }
+}
+
+// Adjoint of x = argmin ||A x - b|| = (A^T A)^{-1} A^T b.  With lambda =
+// (A^T A)^{-1} g_x and r = b - A x (one thread per row of A; A = A~ D^{-1}):
+//   g_b = A lambda,   g_A[i, j] = r_i lambda_j - (A lambda)_i x_j  on the nonzeros.
+__global__ void __launch_bounds__(kT) lstsq_grad_kernel(int64_t m, const int64_t* rp, const int32_t* ci,
+                                                        const double* vs, const double* D, const double* b,
+                                                        const double* x, const double* lam, double* gb,
+                                                        double* gv) {
+  const int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (r >= m) return;
+  double ax = 0.0, al = 0.0;
+  for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
+    const int32_t j = ci[e];
+    const double a = vs[e] / D[j];
+    ax += a * x[j];
+    al += a * lam[j];
+  }
+  const double rr = b[r] - ax;
+  if (gb) gb[r] = al;
+  if (gv)
+    for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
+      const int32_t j = ci[e];
+      gv[e] = rr * lam[j] - al * x[j];
+    }
+}
+
+// New values of A (same pattern): A~ = A D for the row-major and the transposed copies.
+__global__ void __launch_bounds__(kT) set_values_kernel(int64_t nnz, const double* a, const int32_t* ci,
+                                                        const double* D, double* vs) {
+  const int64_t e = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (e < nnz) vs[e] = a[e] * D[ci[e]];
+}
+
+__global__ void __launch_bounds__(kT) gather_values_kernel(int64_t nnz, const double* vs, const int64_t* perm,
+                                                           double* tv) {
+  const int64_t q = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (q < nnz) tv[q] = vs[perm[q]];
+}
+
 int blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + kT - 1) / kT); }
 
 }  // namespace
@@ -440,7 +497,9 @@ struct ApplyPlan {
   void* d_dpart = nullptr;  // partial sums of the dense GEMVs (TA), sized for the largest segment
   std::vector<Segment> segs;  // factorization order
   int64_t launches = 0;       // kernel launches of one W^{-1} (equal for W^{-T})
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;      // one CGLS iteration
+  cudaGraphExec_t graph_pcg = nullptr;  // one PCG iteration
+  double* h_res = nullptr;              // pinned host copy of the residual norm
   double* d_scal = nullptr;
   double* d_part = nullptr;
   int part_n = 0;
@@ -646,6 +705,7 @@ void build_apply_plan(Handle& h) {
   const int64_t big = std::max(h.m, h.n);
   h.plan->part_n = blocks(big);
   SPAQR_CUDA(cudaMalloc(&h.plan->d_scal, 8 * sizeof(double)));
+  SPAQR_CUDA(cudaMallocHost(&h.plan->h_res, sizeof(double)));
   SPAQR_CUDA(cudaMalloc(&h.plan->d_part, (size_t)h.plan->part_n * sizeof(double)));
 }
 
@@ -654,6 +714,8 @@ void free_apply_plan(Handle& h) {
   for (auto& e : h.plan->ev)
     if (e) cudaEventDestroy(e);
   if (h.plan->graph) cudaGraphExecDestroy(h.plan->graph);
+  if (h.plan->graph_pcg) cudaGraphExecDestroy(h.plan->graph_pcg);
+  if (h.plan->h_res) cudaFreeHost(h.plan->h_res);
   cudaFree(h.plan->d_small);
   cudaFree(h.plan->d_dense);
   cudaFree(h.plan->d_idx);
@@ -808,90 +870,224 @@ static void accumulate_solve_timers(Handle& h) {
   }
 }
 
-void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info) {
-  auto t0 = std::chrono::steady_clock::now();
+// One PCG iteration on A~^T A~ nu = D g with the preconditioner W^{-1} W^{-T}
+// (everything on the stream, no host wait).  scal[0] = rho = r.z, scal[1] = p.q,
+// scal[2] = |D^{-1} r|^2 (the residual of (A^T A) lambda = g), scal[3] = new rho.
+static void pcg_body(Handle& h, double* nu, double* r, double* z, double* p, double* q, double* t) {
   ApplyPlan& P = *h.plan;
   const int64_t m = h.m, n = h.n;
-  const size_t need = (size_t)3 * m + (size_t)5 * n;
-  if (h.work_elems < need) {
-    if (h.d_work) cudaFree(h.d_work);
-    SPAQR_CUDA(cudaMalloc(&h.d_work, need * sizeof(double)));
-    h.work_elems = need;
-    if (P.graph) {
-      cudaGraphExecDestroy(P.graph);
-      P.graph = nullptr;
-    }
-  }
-  double* r = h.d_work;
-  double* q = r + m;
-  double* xt = q + m;
-  double* p = xt + n;
-  double* t = p + n;
-  double* u = t + n;
-  double* s = u + n;
-  (void)s;
-  double* sv = s;
-  const double* Dinv_w = h.d_D;  // |D^{-1} u| = |u / D|
-  {
+  const int nb = std::min(blocks(n), P.part_n);
+  spmv_kernel<<<blocks(m), kT, 0, h.st>>>(m, h.d_rowptr, h.d_colidx, h.d_vals, p, t, nullptr, P.d_part);
+  spmv_kernel<<<blocks(n), kT, 0, h.st>>>(n, h.d_trowptr, h.d_tcolidx, h.d_tvals, t, q, nullptr, P.d_part);
+  dot_kernel<<<nb, kT, 0, h.st>>>(n, p, q, nullptr, P.d_part);
+  finish_sum_kernel<<<1, kT, 0, h.st>>>(nb, P.d_part, P.d_scal + 1);
+  update_xr_kernel<<<blocks(n), kT, 0, h.st>>>(n, n, nu, p, r, q, P.d_scal);
+  dot_kernel<<<nb, kT, 0, h.st>>>(n, r, r, h.d_D, P.d_part);
+  finish_sum_kernel<<<1, kT, 0, h.st>>>(nb, P.d_part, P.d_scal + 2);
+  SPAQR_CUDA(cudaMemcpyAsync(z, r, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
+  apply_Winv(h, z, 1);
+  apply_Winv(h, z, 0);
+  dot_kernel<<<nb, kT, 0, h.st>>>(n, r, z, nullptr, P.d_part);
+  finish_sum_kernel<<<1, kT, 0, h.st>>>(nb, P.d_part, P.d_scal + 3);
+  beta_kernel<<<1, 1, 0, h.st>>>(P.d_scal);
+  update_p_kernel<<<blocks(n), kT, 0, h.st>>>(n, p, z, P.d_scal);
+  SPAQR_CUDA(cudaGetLastError());
+}
+
+// Workspace of the iterative solvers: CGLS r, q (m) and x, p, t, u, s (n);
+// PCG nu, r, z, p, q (n) and t (m).
+static void ensure_work(Handle& h) {
+  ApplyPlan& P = *h.plan;
+  const size_t need = (size_t)3 * h.m + (size_t)5 * h.n;
+  if (h.work_elems >= need) return;
+  if (h.d_work) cudaFree(h.d_work);
+  h.d_work = nullptr;
+  SPAQR_CUDA(cudaMalloc(&h.d_work, need * sizeof(double)));
+  h.work_elems = need;
+  if (P.graph) cudaGraphExecDestroy(P.graph);
+  if (P.graph_pcg) cudaGraphExecDestroy(P.graph_pcg);
+  P.graph = P.graph_pcg = nullptr;
+}
+
+void IterSolve::begin() {
+  Handle& hh = *h;
+  ApplyPlan& P = *hh.plan;
+  t0 = std::chrono::steady_clock::now();
+  ensure_work(hh);
+  const int64_t m = hh.m, n = hh.n;
+  double* w = hh.d_work;
+  it = 0;
+  done = false;
+  if (kind == 0) {
+    // CGLS: x = 0, r = b, s = W^{-T} (A~^T r), p = s, gamma = |s|^2, res0 = |D^{-1} A~^T b|
+    double* r = w;
+    double* xt = w + 2 * m;
+    double* p = xt + n;
+    double* u = p + 2 * n;
+    double* sv = u + n;
     const char* e = std::getenv("SPAQR_PROFILE_APPLY");
     if (e && e[0] == '1') {
-      SPAQR_CUDA(cudaMemsetAsync(t, 0, (size_t)n * sizeof(double), h.st));
-      profile_apply(h, t);
+      SPAQR_CUDA(cudaMemsetAsync(p + n, 0, (size_t)n * sizeof(double), hh.st));
+      profile_apply(hh, p + n);
     }
+    SPAQR_CUDA(cudaMemsetAsync(xt, 0, (size_t)n * sizeof(double), hh.st));
+    SPAQR_CUDA(cudaMemcpyAsync(r, rhs, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, hh.st));
+    spmv_kernel<<<blocks(n), kT, 0, hh.st>>>(n, hh.d_trowptr, hh.d_tcolidx, hh.d_tvals, r, u, hh.d_D, P.d_part);
+    finish_sum_kernel<<<1, kT, 0, hh.st>>>(blocks(n), P.d_part, P.d_scal + 2);
+    SPAQR_CUDA(cudaMemcpyAsync(sv, u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, hh.st));
+    apply_Winv(hh, sv, 1);
+    SPAQR_CUDA(cudaMemcpyAsync(p, sv, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, hh.st));
+    sumsq_kernel<<<std::min(blocks(n), P.part_n), kT, 0, hh.st>>>(n, sv, P.d_part);
+    finish_sum_kernel<<<1, kT, 0, hh.st>>>(std::min(blocks(n), P.part_n), P.d_part, P.d_scal + 0);
+  } else {
+    // PCG: nu = 0, r = D g, z = W^{-1} W^{-T} r, p = z, rho = r.z, res0 = |g|
+    double* nu = w;
+    double* r = nu + n;
+    double* z = r + n;
+    double* p = z + n;
+    const int nb = std::min(blocks(n), P.part_n);
+    SPAQR_CUDA(cudaMemsetAsync(nu, 0, (size_t)n * sizeof(double), hh.st));
+    scale_kernel<<<blocks(n), kT, 0, hh.st>>>(n, rhs, hh.d_D, r);
+    dot_kernel<<<nb, kT, 0, hh.st>>>(n, r, r, hh.d_D, P.d_part);
+    finish_sum_kernel<<<1, kT, 0, hh.st>>>(nb, P.d_part, P.d_scal + 2);
+    SPAQR_CUDA(cudaMemcpyAsync(z, r, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, hh.st));
+    apply_Winv(hh, z, 1);
+    apply_Winv(hh, z, 0);
+    SPAQR_CUDA(cudaMemcpyAsync(p, z, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, hh.st));
+    dot_kernel<<<nb, kT, 0, hh.st>>>(n, r, z, nullptr, P.d_part);
+    finish_sum_kernel<<<1, kT, 0, hh.st>>>(nb, P.d_part, P.d_scal + 0);
   }
-  SPAQR_CUDA(cudaMemsetAsync(xt, 0, (size_t)n * sizeof(double), h.st));
-  SPAQR_CUDA(cudaMemcpyAsync(r, b_dev, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
-  spmv_kernel<<<blocks(n), kT, 0, h.st>>>(n, h.d_trowptr, h.d_tcolidx, h.d_tvals, r, u, Dinv_w, P.d_part);
-  finish_sum_kernel<<<1, kT, 0, h.st>>>(blocks(n), P.d_part, P.d_scal + 2);
-  SPAQR_CUDA(cudaMemcpyAsync(sv, u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
-  apply_Winv(h, sv, 1);
-  SPAQR_CUDA(cudaMemcpyAsync(p, sv, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
-  sumsq_kernel<<<std::min(blocks(n), P.part_n), kT, 0, h.st>>>(n, sv, P.d_part);
-  finish_sum_kernel<<<1, kT, 0, h.st>>>(std::min(blocks(n), P.part_n), P.d_part, P.d_scal + 0);
-  double res0 = 0.0;
-  SPAQR_CUDA(cudaMemcpyAsync(&res0, P.d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost, h.st));
-  SPAQR_CUDA(cudaStreamSynchronize(h.st));
-  const double norm0 = std::sqrt(res0);
-  h.stats.t_kernel[4] = h.stats.t_kernel[5] = 0.0;
-  h.stats.n_kernel[4] = h.stats.n_kernel[5] = 0;
-  int it = 0;
-  double rel = norm0 > 0.0 ? 1.0 : 0.0;
-  if (norm0 > 0.0) {
-    const bool graphs = h.opt.use_graphs != 0;
-    if (graphs && !P.graph) {
-      cudaGraph_t g;
-      SPAQR_CUDA(cudaStreamBeginCapture(h.st, cudaStreamCaptureModeThreadLocal));
-      cgls_body(h, xt, r, p, t, q, u, sv, Dinv_w, true);
-      SPAQR_CUDA(cudaStreamEndCapture(h.st, &g));
-      SPAQR_CUDA(cudaGraphInstantiate(&P.graph, g, 0));
-      cudaGraphDestroy(g);
-    }
-    for (it = 1; it <= h.opt.maxit; ++it) {
-      if (graphs)
-        SPAQR_CUDA(cudaGraphLaunch(P.graph, h.st));
-      else
-        cgls_body(h, xt, r, p, t, q, u, sv, Dinv_w, false);
-      double res = 0.0;
-      SPAQR_CUDA(cudaMemcpyAsync(&res, P.d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost, h.st));
-      SPAQR_CUDA(cudaStreamSynchronize(h.st));
-      accumulate_solve_timers(h);
-      rel = std::sqrt(res) / norm0;
-      if (!(rel >= h.opt.tol)) break;
-    }
-    if (it > h.opt.maxit) it = h.opt.maxit;
+  SPAQR_CUDA(cudaMemcpyAsync(P.h_res, P.d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost, hh.st));
+}
+
+void IterSolve::begun() {
+  norm0 = std::sqrt(*h->plan->h_res);
+  rel = norm0 > 0.0 ? 1.0 : 0.0;
+  done = !(norm0 > 0.0);
+  if (kind == 0) {
+    h->stats.t_kernel[4] = h->stats.t_kernel[5] = 0.0;
+    h->stats.n_kernel[4] = h->stats.n_kernel[5] = 0;
   }
-  scale_kernel<<<blocks(n), kT, 0, h.st>>>(n, xt, h.d_D, x_dev);
+}
+
+void IterSolve::step() {
+  Handle& hh = *h;
+  ApplyPlan& P = *hh.plan;
+  const int64_t m = hh.m, n = hh.n;
+  double* w = hh.d_work;
+  const bool graphs = hh.opt.use_graphs != 0;
+  cudaGraphExec_t* g = kind == 0 ? &P.graph : &P.graph_pcg;
+  auto body = [&](bool capturing) {
+    if (kind == 0) {
+      double* r = w;
+      double* q = r + m;
+      double* xt = q + m;
+      double* p = xt + n;
+      double* t = p + n;
+      double* u = t + n;
+      double* sv = u + n;
+      cgls_body(hh, xt, r, p, t, q, u, sv, hh.d_D, capturing);
+    } else {
+      double* nu = w;
+      double* r = nu + n;
+      double* z = r + n;
+      double* p = z + n;
+      double* q = p + n;
+      double* t = q + n;
+      pcg_body(hh, nu, r, z, p, q, t);
+    }
+  };
+  if (graphs && !*g) {
+    cudaGraph_t gr;
+    SPAQR_CUDA(cudaStreamBeginCapture(hh.st, cudaStreamCaptureModeThreadLocal));
+    body(true);
+    SPAQR_CUDA(cudaStreamEndCapture(hh.st, &gr));
+    SPAQR_CUDA(cudaGraphInstantiate(g, gr, 0));
+    cudaGraphDestroy(gr);
+  }
+  if (graphs)
+    SPAQR_CUDA(cudaGraphLaunch(*g, hh.st));
+  else
+    body(false);
+  SPAQR_CUDA(cudaMemcpyAsync(P.h_res, P.d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost, hh.st));
+}
+
+void IterSolve::stepped() {
+  ++it;
+  if (kind == 0) accumulate_solve_timers(*h);
+  rel = std::sqrt(*h->plan->h_res) / norm0;
+  if (!(rel >= tol) || it >= maxit) done = true;
+}
+
+void IterSolve::finish() {
+  Handle& hh = *h;
+  const int64_t m = hh.m, n = hh.n;
+  const double* sol = kind == 0 ? hh.d_work + 2 * m : hh.d_work;  // x~ (CGLS) or nu (PCG)
+  scale_kernel<<<blocks(n), kT, 0, hh.st>>>(n, sol, hh.d_D, out);
   SPAQR_CUDA(cudaGetLastError());
-  SPAQR_CUDA(cudaStreamSynchronize(h.st));
+}
+
+void IterSolve::report(spaqr_solve_info* info) {
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  h.stats.t_solve = secs;
-  h.stats.iters = it;
+  if (kind == 0) {
+    h->stats.t_solve = secs;
+    h->stats.iters = it;
+  }
   if (info) {
     info->iters = it;
     info->rel_resid = rel;
-    info->converged = rel < h.opt.tol;
+    info->converged = rel < tol;
     info->seconds = secs;
   }
+}
+
+// Runs the solvers of several handles side by side: every round launches one
+// iteration on each unfinished handle's stream, then reads their residuals.
+void run_iterative(std::vector<IterSolve>& S) {
+  for (auto& s : S) s.begin();
+  for (auto& s : S) {
+    SPAQR_CUDA(cudaStreamSynchronize(s.h->st));
+    s.begun();
+  }
+  for (;;) {
+    bool any = false;
+    for (auto& s : S)
+      if (!s.done) {
+        s.step();
+        any = true;
+      }
+    if (!any) break;
+    for (auto& s : S)
+      if (!s.done) {
+        SPAQR_CUDA(cudaStreamSynchronize(s.h->st));
+        s.stepped();
+      }
+  }
+  for (auto& s : S) s.finish();
+  for (auto& s : S) SPAQR_CUDA(cudaStreamSynchronize(s.h->st));
+}
+
+void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info) {
+  std::vector<IterSolve> S(1);
+  S[0].h = &h;
+  S[0].kind = 0;
+  S[0].rhs = b_dev;
+  S[0].out = x_dev;
+  S[0].tol = h.opt.tol;
+  S[0].maxit = h.opt.maxit;
+  run_iterative(S);
+  S[0].report(info);
+}
+
+void lstsq_grad(Handle& h, const double* b, const double* x, const double* lam, double* gb, double* gv) {
+  lstsq_grad_kernel<<<blocks(h.m), kT, 0, h.st>>>(h.m, h.d_rowptr, h.d_colidx, h.d_vals, h.d_D, b, x, lam, gb, gv);
+  SPAQR_CUDA(cudaGetLastError());
+}
+
+void set_values(Handle& h, const double* a_dev) {
+  set_values_kernel<<<blocks(h.nnz), kT, 0, h.st>>>(h.nnz, a_dev, h.d_colidx, h.d_D, h.d_vals);
+  gather_values_kernel<<<blocks(h.nnz), kT, 0, h.st>>>(h.nnz, h.d_vals, h.d_tperm, h.d_tvals);
+  SPAQR_CUDA(cudaGetLastError());
 }
 
 }  // namespace spaqr
