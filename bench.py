@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--eps", type=float, default=1e-6)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--compare", default="fp64", choices=["fp64", "mixed", "none"],
+                    help="also time this precision on the same workload (reported under config.compare)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample", default="grid2d_128_c3", help="oracle sample for the CPU baseline")
@@ -167,6 +169,7 @@ def run_gpu(args, rank, world):
     kt = {k: 0.0 for k in ["copy", "front_qr", "qrcp", "other", "apply", "spmv"]}
     kn = {k: 0 for k in kt}
     flops_front = 0.0
+    flops_qrcp = 0.0
     launches = 0
     iters = []
     t_factor, t_solve = [], []
@@ -178,7 +181,8 @@ def run_gpu(args, rank, world):
             kt[k] += st["t_kernel"][k]
             kn[k] += st["n_kernel"][k]
         flops_front += st["flops_front"]
-        launches += st["launches"] + st["n_kernel"]["apply"] + 12 * st["iters"]
+        flops_qrcp += st["flops_qrcp"]
+        launches += st["launches"] + st["n_kernel"]["apply"] + 9 * st["iters"]
         iters.append(st["iters"])
         t_factor.append(st["t_factor"])
         t_solve.append(st["t_solve"])
@@ -209,29 +213,57 @@ def run_gpu(args, rank, world):
         t = torch.tensor([secs], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         secs = float(t.item())
+    compare = None
+    if args.compare != "none" and args.compare != args.precision:
+        # the other precision on the same workload, same timing (device events over K steps)
+        for _ in range(max(1, args.warmup)):
+            sq.SpaQR(prob, an, eps=args.eps, precision=args.compare, stream=stream).solve(b_dev)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        its = []
+        c0.record(stream)
+        for _ in range(args.steps):
+            gc = sq.SpaQR(prob, an, eps=args.eps, precision=args.compare, stream=stream)
+            with torch.cuda.stream(stream):
+                gc.solve(b_dev)
+            its.append(gc.stats()["iters"])
+        c1.record(stream)
+        torch.cuda.synchronize()
+        sc = gc.stats()
+        compare = {"precision": args.compare, "seconds": c0.elapsed_time(c1) / 1e3 / args.steps, "iters": its,
+                   "t_factor": sc["t_factor"], "t_solve": sc["t_solve"],
+                   "kernel_seconds": {k: v for k, v in sc["t_kernel"].items()}}
     return dict(secs=secs, prob=prob, depth=depth, stats=stats, kt=kt, kn=kn, flops_front=flops_front,
+                flops_qrcp=flops_qrcp, compare=compare,
                 launches=launches, iters=iters, rel=rel, e2e=e2e, clocks=clocks, t_factor=t_factor,
                 t_solve=t_solve, t_analyze=stats["t_analyze"])
 
 
 def roofline(res, precision):
-    kt, kn = res["kt"], res["kn"]
+    """Roofline of the device kernel family with the largest share of the timed steps."""
+    kt = res["kt"]
     dom = max(kt, key=lambda k: kt[k])
     st = res["stats"]
-    steps = max(1, len(res["iters"]))
+    share = kt[dom] / max(sum(kt.values()), 1e-12)
     if dom == "apply":
-        per_launch = st["bytes_apply"] / 2.0 / max(1, st["n_kernel"]["apply"] / max(1, st["iters"]) / 2)
         ach = st["bytes_apply"] * sum(res["iters"]) / max(kt["apply"], 1e-12) / 1e9
         return {"kernel": "W^-1/W^-T apply", "bound": "hbm", "achieved": ach, "peak": 6660.3, "unit": "GB/s",
-                "frac": ach / 6660.3, "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+                "frac": ach / 6660.3, "traffic": None, "share": share,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     peak = PEAKS["fp64_alu_tflops"] if precision == "fp64" else PEAKS["fp32_alu_tflops"]
-    ach = res["flops_front"] / max(kt["front_qr"], 1e-12) / 1e12
-    out = {"kernel": "front QR (eliminate + scale)", "bound": "alu", "achieved": ach, "peak": peak,
-           "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-           "peak_source": "FP64: GB300 FP64 rate from the profiling recipe table; FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
-    if dom != "front_qr":
-        out["note"] = f"largest device family is {dom}"
-    return out
+    src = ("FP64 rate of the recipe table (1.25 TFLOP/s)" if precision == "fp64" else
+           "FP32 lanes: 152 SMs x 128 x 2 flops x 2.07 GHz = 80.5 TFLOP/s (derived, of nominal)")
+    if dom == "qrcp":
+        ach = res["flops_qrcp"] / max(kt["qrcp"], 1e-12) / 1e12
+        name = "column-pivoted QR (sparsification steps 1 and 2)"
+    else:
+        ach = res["flops_front"] / max(kt["front_qr"], 1e-12) / 1e12
+        name = "front QR (eliminate + scale)"
+        if dom != "front_qr":
+            name += f" (largest family: {dom})"
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "share": share, "peak_source": src}
 
 
 def main():
@@ -295,9 +327,11 @@ def main():
                    "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas{world}"},
         "e2e": res["e2e"], "gpu_launches": int(res["launches"]), "clocks": res["clocks"],
         "roofline": roofline(res, args.precision), "cpu_baseline": cpu,
+        "compare": res["compare"],
         "detail": {"iters": res["iters"], "rel_resid": res["rel"], "t_factor": res["t_factor"],
                    "t_solve": res["t_solve"], "t_analyze": res["t_analyze"], "nnz_W": st["nnz_W"],
                    "kernel_seconds": res["kt"], "kernel_launches": res["kn"], "flops_front": res["flops_front"],
+                   "flops_qrcp": res["flops_qrcp"],
                    "phase_seconds": st["t_phase"], "syncs": st["syncs"], "top_front": [st["top_rows"], st["top_cols"]],
                    "max_front": [st["max_front_rows"], st["max_front_cols"]]},
     }

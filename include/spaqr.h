@@ -202,7 +202,7 @@ typedef struct {
   int64_t max_front_rows, max_front_cols;
   int64_t top_cols, top_rows; /* size of the root front (Section 4.3 top separator) */
   double flops_front;  /* algorithmic flops of the front QRs (Golub-Van Loan counts) */
-  double flops_sparsify;
+  double flops_sparsify; /* step-1 and step-2 column-pivoted QRs plus the step-2 two-sided application */
   double t_phase[6];   /* wall seconds: eliminate (incl. row reassignment), prep (column scaling, row
                           owners, initial blocks), scale, step1, step2, merge */
   int64_t launches;    /* kernels launched by the factorization */
@@ -215,6 +215,7 @@ typedef struct {
   double t_kernel[6];
   int64_t n_kernel[6]; /* launches counted in each family */
   double bytes_apply;  /* algorithmic bytes of one W^{-1} plus one W^{-T} apply */
+  double flops_qrcp;   /* algorithmic flops of the column-pivoted QRs alone, 4mnk - 2k^2(m+n) + 4k^3/3 each */
 } spaqr_stats;
 
 int spaqr_get_stats(const spaqr_handle* h, spaqr_stats* st);

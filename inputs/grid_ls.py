@@ -122,6 +122,8 @@ WORKLOADS = {
     "grid2d_128_c2": dict(dims=(128, 128, 1), law="c2", depth=8),
     # 3D 128^3, w = 10^U[-3,3], depth 18.
     "grid3d_128": dict(dims=(128, 128, 128), law="c3", depth=18),
+    # 2D 256x256 of the 1024x1024 family (same leaf size), for kernel profiles.
+    "grid2d_256_c3": dict(dims=(256, 256, 1), law="c3", depth=12),
 }
 
 

@@ -92,6 +92,7 @@ class Stats(C.Structure):
         ("t_kernel", C.c_double * 6),
         ("n_kernel", C.c_int64 * 6),
         ("bytes_apply", C.c_double),
+        ("flops_qrcp", C.c_double),
     ]
 
 

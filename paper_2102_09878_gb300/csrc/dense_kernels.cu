@@ -411,6 +411,39 @@ __global__ void __launch_bounds__(kThreads) front_finish_kernel(const FrontDesc<
   }
 }
 
+// Transposed butterfly over a warp: lanes hold a[0..G) (G a power of two
+// <= 32); log2(G) halving exchanges (lanes with bit lvl set keep the upper
+// half) then plain exchanges leave every lane with the warp-wide sum of
+// column butterfly_col(lane); butterfly_lane(j) is the lowest lane holding it.
+template <int G>
+__device__ __forceinline__ int butterfly_col(int lane) {
+  int j = 0, half = G / 2;
+  for (int lvl = 16; half >= 1; lvl >>= 1, half >>= 1)
+    if (lane & lvl) j += half;
+  return j;
+}
+template <int G>
+__device__ __forceinline__ int butterfly_lane(int j) {
+  int l = 0, half = G / 2;
+  for (int lvl = 16; half >= 1; lvl >>= 1, half >>= 1)
+    if (j & half) l += lvl;
+  return l;
+}
+template <int G, typename T>
+__device__ __forceinline__ T butterfly_reduce(T (&a)[G], int lane) {
+  int lvl = 16;
+#pragma unroll
+  for (int cnt = G; cnt > 1; cnt >>= 1, lvl >>= 1) {
+    const bool up = lane & lvl;
+#pragma unroll
+    for (int q = 0; q < cnt / 2; ++q)
+      a[q] = (up ? a[q + cnt / 2] : a[q]) + __shfl_xor_sync(0xffffffffu, up ? a[q] : a[q + cnt / 2], lvl);
+  }
+  T v = a[0];
+  for (; lvl >= 1; lvl >>= 1) v += __shfl_xor_sync(0xffffffffu, v, lvl);
+  return v;
+}
+
 // ------------------------------------------------------------------- QRCP
 // Column-pivoted Householder QR stopped at the rank, one thread-block cluster
 // of CS CTAs per matrix.  CTA r of the cluster owns the column slab
@@ -420,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) front_finish_kernel(const FrontDesc<
 // index), the cluster reads all proposals through distributed shared memory,
 // the owner of the pivot builds the reflector, and every CTA copies it from
 // the owner and applies it to its own slab.  Two cluster barriers per step.
-template <typename T, bool SMEM>
+template <typename T, bool SMEM, int KG>
 __global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T>* descs, double eps, int nl_max,
                                                                 int m_max) {
   cg::cluster_group cl = cg::this_cluster();
@@ -435,14 +468,16 @@ __global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T
   double* nu = reinterpret_cast<double*>(smraw);   // nl_max
   double* nuref = nu + nl_max;                      // nl_max
   int* step_of = reinterpret_cast<int*>(nuref + nl_max);  // nl_max
-  T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 20 + 15) / 16) * 16);  // m_max + 2
+  int* act = step_of + nl_max;                            // unpivoted local columns, nl_max
+  int* pos = act + nl_max;                                // position of each column in act
+  T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // m_max + 2
   T* taus = vbuf + ((m_max + 3) & ~1);             // min(m_max, n) + 2
   T* X = SMEM ? taus + ((m_max + 3) & ~1) : d.work + (size_t)j0 * m;
   __shared__ double cand_v;
   __shared__ int cand_j;
   __shared__ double s_beta;
   __shared__ T s_tau;
-  __shared__ int s_stop, s_piv;
+  __shared__ int s_stop, s_piv, s_nact;
   __shared__ double red_v[kWarps];
   __shared__ int red_i[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -464,6 +499,11 @@ __global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T
       step_of[c] = -1;
     }
   }
+  for (int c = threadIdx.x; c < nloc; c += kThreads) {
+    act[c] = c;
+    pos[c] = c;
+  }
+  if (threadIdx.x == 0) s_nact = nloc;
   const int kmax = m < n ? m : n;
   double r11 = 0.0;
   int k = 0;
@@ -587,43 +627,76 @@ __global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T
     if (s_stop) break;
     const T tau = s_tau;
     if (threadIdx.x == 0) taus[i] = tau;
-    if (rank == owner && threadIdx.x == 0) step_of[p - j0] = i;
+    if (rank == owner && threadIdx.x == 0) {
+      const int pl = p - j0, q = pos[pl], last = act[s_nact - 1];
+      step_of[pl] = i;
+      act[q] = last;
+      pos[last] = q;
+      s_nact = s_nact - 1;
+    }
     __syncthreads();
-    // apply H_i to the warp's columns in chunks of 32 (warp-cooperative FP32
-    // updates), then downdate their squared norms lane-per-column in FP64
-    // (one FP64 instruction covers 32 columns), recompute the flagged ones
-    // warp-parallel, and form the warp's proposal for step i + 1
+    // apply H_i to the CTA's unpivoted columns (the compact list act[0..nact)):
+    // every warp takes groups of KG columns, lanes over rows with KG independent
+    // accumulators; the KG dot products are reduced by one transposed butterfly
+    // (lane L(j) ends with column j's sum), w_j = tau (x_ij + v.x_j) is
+    // broadcast, the rows are updated, and lane L(j) downdates the FP64 squared
+    // norm of column j (recomputed warp-parallel when it lost too many digits)
+    // and keeps the warp's proposal for step i + 1.
     wv = -1.0;
     wj = INT_MAX;
-    for (int base = warp; base < nloc; base += 32 * kWarps) {
-      for (int t = 0; t < 32; ++t) {
-        const int c = base + t * kWarps;
-        if (c >= nloc) break;
-        if (step_of[c] >= 0 || tau == T(0)) continue;
-        T* col = X + (int64_t)c * m;
-        T sacc = T(0);
-        for (int r = i + 1 + lane; r < m; r += 32) sacc += vbuf[r - i] * col[r];
-        sacc = warp_sum(sacc);
-        const T w = tau * (col[i] + sacc);
-        __syncwarp();
-        if (lane == 0) col[i] -= w;
-        for (int r = i + 1 + lane; r < m; r += 32) col[r] -= w * vbuf[r - i];
+    const int nact = s_nact;
+    const int jl = butterfly_col<KG>(lane);  // the column whose sum this lane ends with
+    const bool lead = lane == butterfly_lane<KG>(jl);
+    for (int g0 = warp * KG; g0 < nact; g0 += kWarps * KG) {
+      const int ng = min(KG, nact - g0);
+      T* cols[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) cols[j] = X + (int64_t)act[g0 + (j < ng ? j : 0)] * m;
+      T acc[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) acc[j] = T(0);
+      if (tau != T(0)) {
+        for (int r = i + 1 + lane; r < m; r += 32) {
+          const T vr = vbuf[r - i];
+#pragma unroll
+          for (int j = 0; j < KG; ++j) acc[j] += vr * cols[j][r];
+        }
+      }
+      const T dsum = butterfly_reduce<KG>(acc, lane);
+      const int cme = jl < ng ? act[g0 + jl] : 0;
+      T* colme = X + (int64_t)cme * m;
+      T wmine = T(0);
+      double xnew = 0.0;
+      if (jl < ng) {
+        const T xi = colme[i];
+        wmine = tau * (xi + dsum);
+        xnew = (double)(xi - wmine);
+      }
+      T wv8[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) wv8[j] = __shfl_sync(0xffffffffu, wmine, butterfly_lane<KG>(j));
+      __syncwarp();
+      if (lead && jl < ng) colme[i] = (T)xnew;
+      if (tau != T(0)) {
+        for (int r = i + 1 + lane; r < m; r += 32) {
+          const T vr = vbuf[r - i];
+#pragma unroll
+          for (int j = 0; j < KG; ++j)
+            if (j < ng) cols[j][r] -= wv8[j] * vr;
+        }
       }
       __syncwarp();
-      const int c = base + lane * kWarps;
-      const bool mine = c < nloc && step_of[c] < 0;
       double v = -1.0;
       bool redo = false;
-      if (mine) {
-        const double x = (double)X[i + (int64_t)c * m];
-        v = nu[c] - x * x;
-        redo = v < kRecompute * nuref[c];
+      if (lead && jl < ng) {
+        v = nu[cme] - xnew * xnew;
+        redo = v < kRecompute * nuref[cme];
       }
       unsigned flagged = __ballot_sync(0xffffffffu, redo);
       while (flagged) {
         const int l = __ffs(flagged) - 1;
         flagged &= flagged - 1;
-        const int cc = base + l * kWarps;
+        const int cc = __shfl_sync(0xffffffffu, cme, l);
         const T* col = X + (int64_t)cc * m;
         double sq = 0.0;
         for (int r = i + 1 + lane; r < m; r += 32) {
@@ -636,11 +709,11 @@ __global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T
           nuref[cc] = sq;
         }
       }
-      if (mine) {
-        nu[c] = v;
-        if (v > wv || (v == wv && j0 + c < wj)) {
+      if (lead && jl < ng) {
+        nu[cme] = v;
+        if (v > wv || (v == wv && j0 + cme < wj)) {
           wv = v;
-          wj = j0 + c;
+          wj = j0 + cme;
         }
       }
     }
@@ -654,6 +727,7 @@ __global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T
         wj = oj;
       }
     }
+    __syncthreads();  // every warp is done with act[] before the next pivot edits it
     k = i + 1;
   }
   __syncthreads();
@@ -986,13 +1060,13 @@ cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, cud
   return cudaGetLastError();
 }
 
-template <typename T, bool SMEM>
+template <typename T, bool SMEM, int KG>
 static cudaError_t launch_qrcp_cs(const QrcpDesc<T>* d, int count, double eps, int cs, int nl_max, int m_max,
                                   int smem, cudaStream_t st) {
   static bool init = false;
   if (!init) {
-    allow_smem(qrcp_cluster_kernel<T, SMEM>);
-    cudaFuncSetAttribute(qrcp_cluster_kernel<T, SMEM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    allow_smem(qrcp_cluster_kernel<T, SMEM, KG>);
+    cudaFuncSetAttribute(qrcp_cluster_kernel<T, SMEM, KG>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     init = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -1007,7 +1081,19 @@ static cudaError_t launch_qrcp_cs(const QrcpDesc<T>* d, int count, double eps, i
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel<T, SMEM>, d, eps, nl_max, m_max);
+  return cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel<T, SMEM, KG>, d, eps, nl_max, m_max);
+}
+
+// Columns a warp updates at once.  From shared memory: 8.  From the global work
+// copy: as many as keep the warps' columns (read by the dot products, then
+// re-read by the updates) within about 160 KB of L1.
+template <typename T>
+static int qrcp_group(bool smem_slab, int m_max) {
+  if (smem_slab) return 8;
+  const long long per = (long long)kWarps * m_max * (long long)sizeof(T);
+  int g = 8;
+  while (g > 1 && per * g > (160LL << 10)) g >>= 1;
+  return g;
 }
 
 template <typename T>
@@ -1025,8 +1111,17 @@ cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int
     return cudaGetLastError();
   }
   const int smem = qrcp_smem_bytes(m_max, nl_max, (int)sizeof(T), smem_slab);
-  if (smem_slab) return launch_qrcp_cs<T, true>(d, count, eps, cs, nl_max, m_max, smem, st);
-  return launch_qrcp_cs<T, false>(d, count, eps, cs, nl_max, m_max, smem, st);
+  if (smem_slab) return launch_qrcp_cs<T, true, 8>(d, count, eps, cs, nl_max, m_max, smem, st);
+  switch (qrcp_group<T>(false, m_max)) {
+    case 8:
+      return launch_qrcp_cs<T, false, 8>(d, count, eps, cs, nl_max, m_max, smem, st);
+    case 4:
+      return launch_qrcp_cs<T, false, 4>(d, count, eps, cs, nl_max, m_max, smem, st);
+    case 2:
+      return launch_qrcp_cs<T, false, 2>(d, count, eps, cs, nl_max, m_max, smem, st);
+    default:
+      return launch_qrcp_cs<T, false, 1>(d, count, eps, cs, nl_max, m_max, smem, st);
+  }
 }
 
 template <typename T>

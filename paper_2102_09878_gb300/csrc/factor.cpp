@@ -1149,6 +1149,7 @@ void Factorizer<T>::step1() {
     Group& g = G_[(size_t)who[i]];
     const double m = g.rows, n = g.width, k = rank[i];
     h_.stats.flops_sparsify += 4.0 * m * n * k - 2.0 * k * k * (m + n) + 4.0 * k * k * k / 3.0;
+    h_.stats.flops_qrcp += 4.0 * m * n * k - 2.0 * k * k * (m + n) + 4.0 * k * k * k / 3.0;
     if (rank[i] < g.rows) {
       g.rows = rank[i];
       if (g.rows == 0) {
@@ -1327,6 +1328,7 @@ void Factorizer<T>::step2() {
       // column-pivoted QR to rank k of the c_p x ncm block, then the two-sided application
       const double m = op.c, n = recs[i].ncm, kk = k;
       h_.stats.flops_sparsify += 4.0 * m * n * kk - 2.0 * kk * kk * (m + n) + 4.0 * kk * kk * kk / 3.0;
+      h_.stats.flops_qrcp += 4.0 * m * n * kk - 2.0 * kk * kk * (m + n) + 4.0 * kk * kk * kk / 3.0;
       h_.stats.flops_sparsify += 4.0 * kk * m * n;
     }
     if (k >= op.c) {

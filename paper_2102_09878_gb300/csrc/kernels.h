@@ -110,7 +110,7 @@ cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int
                         cudaStream_t st);
 // dynamic shared memory of one QRCP CTA (nl columns of m rows)
 inline int qrcp_smem_bytes(int m, int nl, int elem, bool slab) {
-  long long b = ((long long)nl * 20 + 15) / 16 * 16;  // nu, nuref, step_of
+  long long b = ((long long)nl * 28 + 15) / 16 * 16;  // nu, nuref, step_of, act, pos
   b += (long long)(((m + 3) & ~1) * 2) * elem;         // vbuf, taus
   if (slab) b += (long long)m * nl * elem;
   return (int)(b + 64);
@@ -173,6 +173,31 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
       if (qrcp_smem_bytes(ms[(size_t)i], (ns[(size_t)i] + 15) / 16, elem, false) > limit) return false;
     }
     order.push_back(i);
+  }
+  // spread small batches over more SMs: while the batch holds fewer CTAs than
+  // the GPU has SMs, double the cluster of the largest shared-memory problems
+  // that keep at least 64 columns per CTA
+  {
+    constexpr long long kSms = 152;
+    long long ctas = 0;
+    for (int i : order) ctas += cs[(size_t)i];
+    std::vector<int> bywork(order);
+    std::sort(bywork.begin(), bywork.end(), [&](int a, int b) {
+      const long long wa = (long long)ms[(size_t)a] * ns[(size_t)a], wb = (long long)ms[(size_t)b] * ns[(size_t)b];
+      return wa != wb ? wa > wb : a < b;
+    });
+    bool grew = true;
+    while (ctas < kSms && grew) {
+      grew = false;
+      for (int i : bywork) {
+        if (ctas >= kSms) break;
+        const int c2 = cs[(size_t)i] * 2;
+        if (!slab[(size_t)i] || c2 > 16 || ns[(size_t)i] / c2 < 64) continue;
+        ctas += cs[(size_t)i];
+        cs[(size_t)i] = c2;
+        grew = true;
+      }
+    }
   }
   // group by (cs, slab), larger footprints first, greedy packing under the limit
   const size_t first_cta_group = out.size();
