@@ -454,7 +454,7 @@ __device__ __forceinline__ T butterfly_reduce(T (&a)[G], int lane) {
 // the owner of the pivot builds the reflector, and every CTA copies it from
 // the owner and applies it to its own slab.  Two cluster barriers per step.
 template <typename T, bool SMEM, int KG>
-__global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T>* descs, double eps, int nl_max,
+__global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDesc<T>* descs, double eps, int nl_max,
                                                                 int m_max) {
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
@@ -743,6 +743,355 @@ __global__ void __launch_bounds__(kThreads) qrcp_cluster_kernel(const QrcpDesc<T
       for (int t = threadIdx.x; t < k; t += kThreads) d.tau[t] = taus[t];
   }
   // the first k rows of Q^T A in the original column order, only when k < m
+  if (d.out && k < m) {
+    for (int64_t e = threadIdx.x; e < (int64_t)k * nloc; e += kThreads) {
+      const int r = (int)(e % k), c = (int)(e / k);
+      const int t = step_of[c];
+      d.out[r + (int64_t)(j0 + c) * d.ldo] = (t >= 0 && r > t) ? T(0) : X[r + (int64_t)c * m];
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// --------------------------------------------- QRCP with delayed updates
+// The global-work variant (slabs too large for shared memory): the pivots,
+// reflectors and rank rule of qrcp_cluster_kernel, but the reflectors of a
+// panel of up to kQrcpNB steps reach the unpivoted columns only at the end of
+// the panel, as one rank-kQrcpNB update.  Within a panel each step reads every
+// unpivoted column once (v^T a) and keeps per column the coefficients f_t of
+// a_upd = a - sum_t v_t f_t, with f_j = tau_j (v_j^T a - sum_{t<j} (v_t^T v_j) f_t)
+// (the delayed-update form of column-pivoted Householder QR; Quintana-Orti,
+// Sun and Bischof, 1998).  The pivot column is brought up to date before its
+// reflector is formed, and the row-i entries that the norm downdates need are
+// formed from the coefficients.  Reflector storage: the pivot columns of the
+// shared work copy, read by every CTA of the cluster.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) qrcp_delayed_kernel(const QrcpDesc<T>* descs, double eps, int nl_max,
+                                                                int m_max) {
+  constexpr int KG = 8;
+  constexpr int NB = kQrcpNB;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const QrcpDesc<T> d = descs[blockIdx.x / CS];
+  const int m = d.m, n = d.n;
+  const int nl = (n + CS - 1) / CS;
+  const int j0 = min(n, rank * nl), j1 = min(n, j0 + nl);
+  const int nloc = j1 - j0;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* nu = reinterpret_cast<double*>(smraw);
+  double* nuref = nu + nl_max;
+  int* step_of = reinterpret_cast<int*>(nuref + nl_max);
+  int* act = step_of + nl_max;
+  int* pos = act + nl_max;
+  T* F = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // NB coefficients per column
+  T* cbuf = F + (size_t)nl_max * NB;    // rows i0..m-1: owner's pivot column, then the reflector (m_max + 2)
+  T* taus = cbuf + ((m_max + 3) & ~1);  // kmax + 2
+  T* W = d.work;                        // the whole matrix, ld m
+  T* X = W + (size_t)j0 * m;            // this CTA's columns
+  __shared__ double cand_v;
+  __shared__ int cand_j;
+  __shared__ double s_beta;
+  __shared__ T s_tau;
+  __shared__ int s_stop, s_piv, s_nact;
+  __shared__ double red_v[kWarps];
+  __shared__ int red_i[kWarps];
+  __shared__ int piv[NB];  // global column of each reflector of the panel
+  __shared__ T gco[NB];    // v_t^T v_j for the panel's earlier reflectors t
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    X[e] = d.src[r + (int64_t)(j0 + c) * d.ld];
+  }
+  __syncthreads();
+  for (int c = warp; c < nloc; c += kWarps) {
+    double sq = 0.0;
+    for (int r = lane; r < m; r += 32) {
+      const double v = (double)X[r + (int64_t)c * m];
+      sq += v * v;
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) {
+      nu[c] = sq;
+      nuref[c] = sq;
+      step_of[c] = -1;
+    }
+  }
+  for (int c = threadIdx.x; c < nloc; c += kThreads) {
+    act[c] = c;
+    pos[c] = c;
+  }
+  if (threadIdx.x == 0) s_nact = nloc;
+  for (int e = threadIdx.x; e < nl_max * NB; e += kThreads) F[e] = T(0);
+  const int kmax = m < n ? m : n;
+  double r11 = 0.0;
+  int k = 0;
+  __syncthreads();
+  double wv = -1.0;
+  int wj = INT_MAX;
+  for (int c = warp + lane * kWarps; c < nloc; c += 32 * kWarps) {
+    const double v = nu[c];
+    if (v > wv || (v == wv && j0 + c < wj)) {
+      wv = v;
+      wj = j0 + c;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, wv, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
+    if (ov > wv || (ov == wv && oj < wj)) {
+      wv = ov;
+      wj = oj;
+    }
+  }
+  // a_c <- a_c - sum_{t<nb} V[:, t] F[c, t] over rows i0..m-1 for every unpivoted
+  // column: thread per row, V[r, 0:NB] in registers, F[c, :] read as vectors
+  auto block_update = [&](int i0, int nb) {
+    __syncthreads();
+    const int nact = s_nact;
+    for (int r = i0 + threadIdx.x; r < m; r += kThreads) {
+      T vr[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t)
+        vr[t] = (t >= nb || r < i0 + t) ? T(0) : (r == i0 + t ? T(1) : __ldcg(W + r + (int64_t)piv[t] * m));
+      for (int q = 0; q < nact; ++q) {
+        const int c = act[q];
+        const T* Fc = F + (size_t)c * NB;
+        T a = X[r + (int64_t)c * m];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) a -= vr[t] * Fc[t];
+        X[r + (int64_t)c * m] = a;
+      }
+    }
+    __syncthreads();
+  };
+  int i0 = 0, jj = 0;
+  for (int i = 0; i < kmax; ++i) {
+    if (lane == 0) {
+      red_v[warp] = wv;
+      red_i[warp] = wj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = red_v[0];
+      int j = red_i[0];
+      for (int w = 1; w < kWarps; ++w)
+        if (red_v[w] > v || (red_v[w] == v && red_i[w] < j)) {
+          v = red_v[w];
+          j = red_i[w];
+        }
+      cand_v = v;
+      cand_j = j;
+    }
+    cl.sync();  // (A) proposals visible cluster-wide
+    if (threadIdx.x < 32) {
+      double v = -1.0;
+      int j = INT_MAX;
+      if (lane < CS) {
+        v = *cl.map_shared_rank(&cand_v, lane);
+        j = *cl.map_shared_rank(&cand_j, lane);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+        if (ov > v || (ov == v && oj < j)) {
+          v = ov;
+          j = oj;
+        }
+      }
+      if (lane == 0) s_piv = j;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p == INT_MAX) break;
+    const int owner = p / nl;
+    if (rank == owner) {
+      // the pivot column brought up to date over rows i0..m-1 (into cbuf)
+      const int pl = p - j0;
+      T* col = X + (int64_t)pl * m;
+      const T* Fp = F + (size_t)pl * NB;
+      for (int r = i0 + threadIdx.x; r < m; r += kThreads) {
+        T a = col[r];
+        for (int t = 0; t < jj && r >= i0 + t; ++t) {
+          const T vrt = r == i0 + t ? T(1) : __ldcg(W + r + (int64_t)piv[t] * m);
+          a -= vrt * Fp[t];
+        }
+        cbuf[r - i0] = a;
+      }
+      __syncthreads();
+      T* cv = cbuf + (i - i0);  // cv[r - i], rows i..m-1
+      if (threadIdx.x < 32) {
+        double sig = 0.0;
+        for (int r = i + 1 + lane; r < m; r += 32) {
+          const double v = (double)cv[r - i];
+          sig += v * v;
+        }
+        sig = warp_sum(sig);
+        const double alpha = (double)cv[0];
+        double beta, tau;
+        if (sig == 0.0) {
+          beta = alpha;
+          tau = 0.0;
+        } else {
+          const double nrm = sqrt(alpha * alpha + sig);
+          beta = alpha >= 0.0 ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+        }
+        const double ab = fabs(beta);
+        const double r11_here = (i == 0) ? ab : r11;
+        const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
+        if (!stop && sig != 0.0) {
+          const T den = (T)(alpha - beta);
+          for (int r = i + 1 + lane; r < m; r += 32) cv[r - i] = cv[r - i] / den;
+        } else {
+          for (int r = i + 1 + lane; r < m; r += 32) cv[r - i] = T(0);
+        }
+        __syncwarp();
+        if (lane == 0) {
+          s_tau = (T)tau;
+          s_beta = beta;
+          s_stop = stop;
+        }
+      }
+      __syncthreads();
+      if (!s_stop) {
+        // rows i0..i-1: R entries; row i: beta; below: the reflector
+        for (int r = i0 + threadIdx.x; r < m; r += kThreads) col[r] = r == i ? (T)s_beta : cbuf[r - i0];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) cv[0] = T(1);
+    }
+    cl.sync();  // (C) reflector ready (owner's cbuf and the work copy)
+    if (rank != owner) {
+      for (int r = i + threadIdx.x; r < m; r += kThreads) cbuf[r - i0] = *cl.map_shared_rank(cbuf + (r - i0), owner);
+      if (threadIdx.x == 0) {
+        s_tau = *cl.map_shared_rank(&s_tau, owner);
+        s_beta = *cl.map_shared_rank(&s_beta, owner);
+        s_stop = *cl.map_shared_rank(&s_stop, owner);
+      }
+    }
+    __syncthreads();
+    if (i == 0) r11 = fabs(s_beta);
+    if (s_stop) break;
+    const T tau = s_tau;
+    if (threadIdx.x == 0) {
+      taus[i] = tau;
+      piv[jj] = p;
+    }
+    if (rank == owner && threadIdx.x == 0) {
+      const int pl = p - j0, q = pos[pl], last = act[s_nact - 1];
+      step_of[pl] = i;
+      act[q] = last;
+      pos[last] = q;
+      s_nact = s_nact - 1;
+    }
+    // g_t = v_t^T v_i (rows i..m-1) for the panel's earlier reflectors
+    for (int t = warp; t < jj; t += kWarps) {
+      const T* vt = W + (int64_t)piv[t] * m;
+      T acc = T(0);
+      for (int r = i + lane; r < m; r += 32) acc += __ldcg(vt + r) * cbuf[r - i0];
+      acc = warp_sum(acc);
+      if (lane == 0) gco[t] = acc;
+    }
+    __syncthreads();
+    // every unpivoted column: v^T a (stale a), its coefficient f, its row-i entry, the norm downdate
+    wv = -1.0;
+    wj = INT_MAX;
+    const int nact = s_nact;
+    const int jl = butterfly_col<KG>(lane);
+    const bool lead = lane == butterfly_lane<KG>(jl);
+    const T* vcur = cbuf + (i - i0);  // vcur[r - i]
+    for (int g0 = warp * KG; g0 < nact; g0 += kWarps * KG) {
+      const int ng = min(KG, nact - g0);
+      const T* cols[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) cols[j] = X + (int64_t)act[g0 + (j < ng ? j : 0)] * m;
+      T acc[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) acc[j] = T(0);
+      if (tau != T(0)) {
+        for (int r = i + lane; r < m; r += 32) {
+          const T vr = vcur[r - i];
+#pragma unroll
+          for (int j = 0; j < KG; ++j) acc[j] += vr * cols[j][r];
+        }
+      }
+      const T dsum = butterfly_reduce<KG>(acc, lane);
+      const int cme = jl < ng ? act[g0 + jl] : 0;
+      double v = -1.0;
+      bool redo = false;
+      if (lead && jl < ng) {
+        T* Fc = F + (size_t)cme * NB;
+        T corr = T(0);
+        for (int t = 0; t < jj; ++t) corr += gco[t] * Fc[t];
+        const T f = tau * (dsum - corr);
+        Fc[jj] = f;
+        T xi = X[i + (int64_t)cme * m];
+        for (int t = 0; t < jj; ++t) xi -= __ldcg(W + i + (int64_t)piv[t] * m) * Fc[t];
+        xi -= f;
+        const double x = (double)xi;
+        v = nu[cme] - x * x;
+        redo = v < kRecompute * nuref[cme];
+      }
+      unsigned flagged = __ballot_sync(0xffffffffu, redo);
+      while (flagged) {
+        const int l = __ffs(flagged) - 1;
+        flagged &= flagged - 1;
+        const int cc = __shfl_sync(0xffffffffu, cme, l);
+        const T* col = X + (int64_t)cc * m;
+        const T* Fc = F + (size_t)cc * NB;
+        double sq = 0.0;
+        for (int r = i + 1 + lane; r < m; r += 32) {
+          T a = col[r] - vcur[r - i] * Fc[jj];
+          for (int t = 0; t < jj; ++t) a -= __ldcg(W + r + (int64_t)piv[t] * m) * Fc[t];
+          const double y = (double)a;
+          sq += y * y;
+        }
+        sq = warp_sum(sq);
+        if (lane == l) {
+          v = sq;
+          nuref[cc] = sq;
+        }
+      }
+      if (lead && jl < ng) {
+        nu[cme] = v;
+        if (v > wv || (v == wv && j0 + cme < wj)) {
+          wv = v;
+          wj = j0 + cme;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, wv, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
+      if (ov > wv || (ov == wv && oj < wj)) {
+        wv = ov;
+        wj = oj;
+      }
+    }
+    k = i + 1;
+    if (++jj == NB) {
+      block_update(i0, jj);
+      i0 = i + 1;
+      jj = 0;
+    }
+  }
+  if (jj > 0) block_update(i0, jj);
+  __syncthreads();
+  if (rank == 0 && threadIdx.x == 0) d.rank[0] = k;
+  if (d.V) {
+    for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
+      const int r = (int)(e % m), c = (int)(e / m);
+      const int t = step_of[c];
+      if (t < 0 || t >= k) continue;
+      d.V[r + (int64_t)t * m] = r < t ? T(0) : (r == t ? T(1) : X[r + (int64_t)c * m]);
+    }
+    if (rank == 0)
+      for (int t = threadIdx.x; t < k; t += kThreads) d.tau[t] = taus[t];
+  }
   if (d.out && k < m) {
     for (int64_t e = threadIdx.x; e < (int64_t)k * nloc; e += kThreads) {
       const int r = (int)(e % k), c = (int)(e / k);
@@ -1060,17 +1409,17 @@ cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, cud
   return cudaGetLastError();
 }
 
-template <typename T, bool SMEM, int KG>
-static cudaError_t launch_qrcp_cs(const QrcpDesc<T>* d, int count, double eps, int cs, int nl_max, int m_max,
-                                  int smem, cudaStream_t st) {
-  static bool init = false;
+template <typename T>
+static cudaError_t launch_cluster(void (*kernel)(const QrcpDesc<T>*, double, int, int), bool& init, unsigned grid,
+                                  int cs, int smem, cudaStream_t st, const QrcpDesc<T>* d, double eps, int nl_max,
+                                  int m_max) {
   if (!init) {
-    allow_smem(qrcp_cluster_kernel<T, SMEM, KG>);
-    cudaFuncSetAttribute(qrcp_cluster_kernel<T, SMEM, KG>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    allow_smem(kernel);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     init = true;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(count * cs));
+  cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = (size_t)smem;
   cfg.stream = st;
@@ -1081,19 +1430,7 @@ static cudaError_t launch_qrcp_cs(const QrcpDesc<T>* d, int count, double eps, i
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel<T, SMEM, KG>, d, eps, nl_max, m_max);
-}
-
-// Columns a warp updates at once.  From shared memory: 8.  From the global work
-// copy: as many as keep the warps' columns (read by the dot products, then
-// re-read by the updates) within about 160 KB of L1.
-template <typename T>
-static int qrcp_group(bool smem_slab, int m_max) {
-  if (smem_slab) return 8;
-  const long long per = (long long)kWarps * m_max * (long long)sizeof(T);
-  int g = 8;
-  while (g > 1 && per * g > (160LL << 10)) g >>= 1;
-  return g;
+  return cudaLaunchKernelEx(&cfg, kernel, d, eps, nl_max, m_max);
 }
 
 template <typename T>
@@ -1111,17 +1448,13 @@ cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int
     return cudaGetLastError();
   }
   const int smem = qrcp_smem_bytes(m_max, nl_max, (int)sizeof(T), smem_slab);
-  if (smem_slab) return launch_qrcp_cs<T, true, 8>(d, count, eps, cs, nl_max, m_max, smem, st);
-  switch (qrcp_group<T>(false, m_max)) {
-    case 8:
-      return launch_qrcp_cs<T, false, 8>(d, count, eps, cs, nl_max, m_max, smem, st);
-    case 4:
-      return launch_qrcp_cs<T, false, 4>(d, count, eps, cs, nl_max, m_max, smem, st);
-    case 2:
-      return launch_qrcp_cs<T, false, 2>(d, count, eps, cs, nl_max, m_max, smem, st);
-    default:
-      return launch_qrcp_cs<T, false, 1>(d, count, eps, cs, nl_max, m_max, smem, st);
+  const unsigned grid = (unsigned)(count * cs);
+  if (smem_slab) {
+    static bool init_s = false;
+    return launch_cluster(qrcp_cluster_kernel<T, true, 8>, init_s, grid, cs, smem, st, d, eps, nl_max, m_max);
   }
+  static bool init_g = false;
+  return launch_cluster(qrcp_delayed_kernel<T>, init_g, grid, cs, smem, st, d, eps, nl_max, m_max);
 }
 
 template <typename T>

@@ -108,11 +108,17 @@ cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, cud
 template <typename T>
 cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int nl_max, int m_max, bool smem_slab,
                         cudaStream_t st);
-// dynamic shared memory of one QRCP CTA (nl columns of m rows)
+// steps per panel of the delayed-update QRCP (slabs in global memory)
+constexpr int kQrcpNB = 16;
+// dynamic shared memory of one QRCP CTA (nl columns of m rows): the slab itself
+// (slab) or the delayed-update coefficients (nl x kQrcpNB)
 inline int qrcp_smem_bytes(int m, int nl, int elem, bool slab) {
   long long b = ((long long)nl * 28 + 15) / 16 * 16;  // nu, nuref, step_of, act, pos
   b += (long long)(((m + 3) & ~1) * 2) * elem;         // vbuf, taus
-  if (slab) b += (long long)m * nl * elem;
+  if (slab)
+    b += (long long)m * nl * elem;
+  else
+    b += (long long)nl * kQrcpNB * elem;
   return (int)(b + 64);
 }
 // Launch groups for a batch of QRCPs of shapes (m_i, n_i): each matrix takes

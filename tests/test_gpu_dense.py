@@ -118,20 +118,48 @@ def test_qrcp_large_matrix_global_path():
                                  (33, 7000), (300, 70)])
 def test_qrcp_every_cluster_size(m, n):
     """Shapes chosen so that the planner uses 1, 2, 4, 8 and 16 CTAs per matrix
-    with the column slabs in shared memory, and 16 CTAs over a global copy."""
+    with the column slabs in shared memory, and 16 CTAs over a global copy.  The
+    matrix is repeated so that the batch fills the GPU (the planner then keeps
+    the smallest cluster that fits)."""
     import paper_2102_09878_gb300 as sq
 
     rng = np.random.default_rng(m * 7 + n)
     r = min(m, n)
     A = (rng.standard_normal((m, r)) * np.logspace(0, -9, r)) @ rng.standard_normal((r, n))
     for eps in (0.0, 1e-6):
-        ranks, rows, V, T = sq.dense_qrcp([A], eps)
         k, Xf, perm, Vo, To = dn.qrcp(A, eps)
-        assert ranks[0] == k, (ranks[0], k)
         good = np.abs(np.diag(Xf[:k, :k])) > 1e-6 * abs(Xf[0, 0])
         j = k if good.all() else int(np.argmin(good))
-        assert _rel(V[0][:, :j], Vo[:, :j]) < 1e-10 and _rel(T[0][:j], To[:j]) < 1e-10
+        for reps in (1, 160):
+            ranks, rows, V, T = sq.dense_qrcp([A] * reps, eps)
+            for q in (0, reps - 1):
+                assert ranks[q] == k, (ranks[q], k)
+                assert _rel(V[q][:, :j], Vo[:, :j]) < 1e-10 and _rel(T[q][:j], To[:j]) < 1e-10
+                if k < m:
+                    ref = np.zeros((k, n))
+                    ref[:, perm] = Xf[:k]
+                    assert _rel(rows[q], ref) < 1e-9
+
+
+@pytest.mark.parametrize("m,n,eps", [(2000, 600, 0.0), (2000, 600, 1e-3), (1500, 1400, 1e-6), (600, 3000, 1e-8),
+                                     (700, 2500, 0.0)])
+def test_qrcp_delayed_update_global_path(m, n, eps):
+    """Matrices too large for the slabs of 16 CTAs: the delayed-update kernel
+    (panels of reflectors applied as one block update), including ranks that
+    stop in the middle of a panel."""
+    import paper_2102_09878_gb300 as sq
+
+    rng = np.random.default_rng(m + 3 * n)
+    r = min(m, n)
+    A = (rng.standard_normal((m, r)) * np.logspace(0, -12, r)) @ rng.standard_normal((r, n))
+    ranks, rows, V, T = sq.dense_qrcp([A, A[:, ::-1].copy()], eps)
+    for q, B in enumerate((A, A[:, ::-1].copy())):
+        k, Xf, perm, Vo, To = dn.qrcp(B, eps)
+        assert ranks[q] == k, (ranks[q], k)
+        good = np.abs(np.diag(Xf[:k, :k])) > 1e-6 * abs(Xf[0, 0])
+        j = k if good.all() else int(np.argmin(good))
+        assert _rel(V[q][:, :j], Vo[:, :j]) < 1e-9 and _rel(T[q][:j], To[:j]) < 1e-9
         if k < m:
             ref = np.zeros((k, n))
             ref[:, perm] = Xf[:k]
-            assert _rel(rows[0], ref) < 1e-9
+            assert _rel(rows[q], ref) < 1e-8
