@@ -249,6 +249,21 @@ void spaqr_destroy(spaqr_handle* h);
 int spaqr_dense_front_qr(int count, double* const* A, const int* m, const int* n, const int* c, const int* ld,
                          void* stream);
 
+/* spaqr_dense_front_qr_f32: the same Householder QR on FP32 matrices, as the
+ * mixed-precision factorization runs it: fronts too large for shared memory
+ * take the blocked path with the trailing updates C <- C - V T^T V^T C on the
+ * tensor cores (tcgen05, 3xTF32 with FP32 accumulation).  Errors as
+ * spaqr_dense_front_qr, plus TIMEOUT if a tensor-core completion wait gave up. */
+int spaqr_dense_front_qr_f32(int count, float* const* A, const int* m, const int* n, const int* c, const int* ld,
+                             void* stream);
+
+/* spaqr_dense_tc_gemm: C <- C - A B for FP32 column-major device matrices
+ * (A m x k, lda; B k x n, ldb; C m x n, ldc) on the tensor cores in 3xTF32 --
+ * the product that the FP32 trailing updates use, exposed for testing.
+ * Errors: INVALID_ARG (negative sizes, short leading dimensions), TIMEOUT. */
+int spaqr_dense_tc_gemm(int m, int n, int k, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                        void* stream);
+
 /* spaqr_dense_qrcp: column-pivoted Householder QR stopped at the rank
  * k = max r with |R_ii| >= eps |R_11| and R_ii != 0 (Section 4).  On return
  * rank[i] (host) = k; A[i] rows 0..k-1 hold the first k rows of Q^T A[i] in the

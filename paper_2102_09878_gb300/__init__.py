@@ -13,8 +13,8 @@ import numpy as np
 from . import capi
 from .capi import SpaqrError
 
-__all__ = ["Analysis", "SpaQR", "SpaqrError", "dense_front_qr", "dense_qrcp", "solve_batch", "solve_normal_batch",
-           "capi"]
+__all__ = ["Analysis", "SpaQR", "SpaqrError", "dense_front_qr", "dense_front_qr_f32", "dense_qrcp", "dense_tc_gemm",
+           "solve_batch", "solve_normal_batch", "capi"]
 
 
 def _stream_ptr(stream):
@@ -290,6 +290,40 @@ def dense_front_qr(mats, cs, stream=None):
     capi.check(lib.spaqr_dense_front_qr(len(ts), ptrs, capi.ptr(m), capi.ptr(n), capi.ptr(c), capi.ptr(ld),
                                         _stream_ptr(stream)))
     return [_from_colmajor(t, A.shape[0], A.shape[1]) for t, A in zip(ts, mats)]
+
+
+def _colmajor_cuda32(A):
+    import torch
+
+    A = np.asarray(A, dtype=np.float32)
+    return torch.from_numpy(np.ascontiguousarray(A.T)).cuda()
+
+
+def dense_front_qr_f32(mats, cs, stream=None):
+    """FP32 front QR as the mixed-precision factor runs it (tensor-core trailing
+    updates on the blocked path); numpy in, numpy (float32) out."""
+    lib = capi.load()
+    ts = [_colmajor_cuda32(A) for A in mats]
+    ptrs = (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+    m = np.array([A.shape[0] for A in mats], np.int32)
+    n = np.array([A.shape[1] for A in mats], np.int32)
+    c = np.array(cs, np.int32)
+    ld = np.maximum(m, 1).astype(np.int32)
+    capi.check(lib.spaqr_dense_front_qr_f32(len(ts), ptrs, capi.ptr(m), capi.ptr(n), capi.ptr(c), capi.ptr(ld),
+                                            _stream_ptr(stream)))
+    return [_from_colmajor(t, A.shape[0], A.shape[1]) for t, A in zip(ts, mats)]
+
+
+def dense_tc_gemm(A, B, Cm, stream=None):
+    """Cm - A @ B on the tensor cores (3xTF32, FP32 accumulation); float32 numpy in and out."""
+    lib = capi.load()
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2 and Cm.shape == (m, n)
+    a, b, c = _colmajor_cuda32(A), _colmajor_cuda32(B), _colmajor_cuda32(Cm)
+    capi.check(lib.spaqr_dense_tc_gemm(m, n, k, capi.ptr(a), max(m, 1), capi.ptr(b), max(k, 1), capi.ptr(c), max(m, 1),
+                                       _stream_ptr(stream)))
+    return _from_colmajor(c, m, n)
 
 
 def dense_qrcp(mats, eps: float, stream=None):

@@ -128,6 +128,14 @@ SIGNATURES = {
         C.c_int,
         [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     ),
+    "spaqr_dense_front_qr_f32": (
+        C.c_int,
+        [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    ),
+    "spaqr_dense_tc_gemm": (
+        C.c_int,
+        [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p],
+    ),
     "spaqr_dense_qrcp": (
         C.c_int,
         [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,

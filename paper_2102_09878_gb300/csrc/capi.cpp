@@ -490,8 +490,10 @@ int spaqr_op_copy(const spaqr_handle* hh, int64_t i, int32_t* slots, int32_t* ns
   });
 }
 
-int spaqr_dense_front_qr(int count, double* const* A, const int* m, const int* n, const int* c, const int* ld,
-                         void* stream) {
+extern "C++" {
+namespace {
+template <typename T>
+int dense_front_qr_t(int count, T* const* A, const int* m, const int* n, const int* c, const int* ld, void* stream) {
   if (count < 0 || (count > 0 && (!A || !m || !n || !c || !ld))) return fail(SPAQR_ERR_INVALID_ARG, "bad arguments");
   if (int rc = need_device()) return rc;
   return guarded([&] {
@@ -505,27 +507,61 @@ int spaqr_dense_front_qr(int count, double* const* A, const int* m, const int* n
       ns.push_back(n[i]);
       cs.push_back(c[i]);
     }
-    const auto groups = spaqr::plan_fronts(ms, ns, cs, 8, lim);
-    std::vector<std::vector<spaqr::FrontDesc<double>>> host(groups.size());
-    std::vector<const spaqr::FrontDesc<double>*> dev(groups.size());
+    const auto groups = spaqr::plan_fronts(ms, ns, cs, (int)sizeof(T), lim);
+    std::vector<std::vector<spaqr::FrontDesc<T>>> host(groups.size());
+    std::vector<const spaqr::FrontDesc<T>*> dev(groups.size());
     std::vector<void*> frees;
-    double* Tbuf = nullptr;
+    T* Tbuf = nullptr;
     for (size_t g = 0; g < groups.size(); ++g) {
-      for (int i : groups[g].idx) host[g].push_back(spaqr::FrontDesc<double>{A[i], m[i], n[i], c[i], ld[i]});
-      spaqr::FrontDesc<double>* d = nullptr;
+      for (int i : groups[g].idx) host[g].push_back(spaqr::FrontDesc<T>{A[i], m[i], n[i], c[i], ld[i]});
+      spaqr::FrontDesc<T>* d = nullptr;
       SPAQR_CUDA(cudaMalloc(&d, host[g].size() * sizeof(host[g][0])));
       frees.push_back(d);
       SPAQR_CUDA(cudaMemcpyAsync(d, host[g].data(), host[g].size() * sizeof(host[g][0]), cudaMemcpyHostToDevice, st));
       dev[g] = d;
       if (groups[g].kind == 2) {
-        SPAQR_CUDA(cudaMalloc(&Tbuf, host[g].size() * 32 * 32 * sizeof(double)));
+        SPAQR_CUDA(cudaMalloc(&Tbuf, host[g].size() * 32 * 32 * sizeof(T)));
         frees.push_back(Tbuf);
       }
     }
+    void* tc = nullptr;
+    const size_t tcb = spaqr::front_groups_tc_bytes<T>(groups, host);
+    if (tcb) {
+      SPAQR_CUDA(cudaMalloc(&tc, tcb));
+      frees.push_back(tc);
+    }
     int64_t launches = 0;
-    SPAQR_CUDA(spaqr::launch_front_groups<double>(groups, dev, host, Tbuf, st, &launches));
+    SPAQR_CUDA(spaqr::launch_front_groups<T>(groups, dev, host, Tbuf, st, &launches, tc));
     SPAQR_CUDA(cudaStreamSynchronize(st));
     for (void* p : frees) cudaFree(p);
+    if (spaqr::tc_take_timeout()) return fail(SPAQR_ERR_TIMEOUT, "tensor-core MMA completion wait timed out");
+    return SPAQR_OK;
+  });
+}
+}  // namespace
+}
+
+int spaqr_dense_front_qr(int count, double* const* A, const int* m, const int* n, const int* c, const int* ld,
+                         void* stream) {
+  return dense_front_qr_t<double>(count, A, m, n, c, ld, stream);
+}
+
+int spaqr_dense_front_qr_f32(int count, float* const* A, const int* m, const int* n, const int* c, const int* ld,
+                             void* stream) {
+  return dense_front_qr_t<float>(count, A, m, n, c, ld, stream);
+}
+
+int spaqr_dense_tc_gemm(int m, int n, int k, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                        void* stream) {
+  if (m < 0 || n < 0 || k < 0 || (m * n * k > 0 && (!A || !B || !C)) || lda < std::max(1, m) ||
+      ldb < std::max(1, k) || ldc < std::max(1, m))
+    return fail(SPAQR_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = need_device()) return rc;
+  return guarded([&] {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SPAQR_CUDA(spaqr::launch_tc_gemm(m, n, k, A, lda, B, ldb, C, ldc, st));
+    SPAQR_CUDA(cudaStreamSynchronize(st));
+    if (spaqr::tc_take_timeout()) return fail(SPAQR_ERR_TIMEOUT, "tensor-core MMA completion wait timed out");
     return SPAQR_OK;
   });
 }

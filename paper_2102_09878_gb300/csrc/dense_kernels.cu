@@ -298,6 +298,157 @@ __global__ void __launch_bounds__(kThreads) front_panel_kernel(const FrontDesc<T
   }
 }
 
+// Panel of the blocked QR on a thread-block cluster (tall panels): the rows
+// j0..m-1 of the panel columns are split over the CS CTAs of the cluster and
+// staged in shared memory (column-major, odd leading dimension).  Per column:
+// partial squared norms and the diagonal entry through distributed shared
+// memory (every CTA forms the same reflector), then partial products with the
+// remaining panel columns, summed in the same order by every CTA, and the
+// rank-1 update of the CTA's own rows -- two cluster barriers per column.  The
+// Gram matrix of the reflectors is reduced the same way and T (Q = I - V T V^T)
+// is formed warp-parallel by CTA 0.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const FrontDesc<T>* descs, int j0, int nb,
+                                                                           T* Tbuf, int per_max) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int f = blockIdx.x / CS;
+  const FrontDesc<T> d = descs[f];
+  const int steps = d.c < d.m ? d.c : d.m;
+  const int b = min(nb, steps - j0);
+  if (b <= 0) return;  // the same for every CTA of the cluster
+  const int mrows = d.m - j0;
+  const int per = (mrows + CS - 1) / CS;
+  const int r0 = j0 + rank * per, r1 = min(d.m, r0 + per);
+  const int nr = max(0, r1 - r0);
+  const int ld = per_max | 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* P = reinterpret_cast<T*>(smraw);  // nr x b, ld
+  __shared__ double sq_part, alpha_s;
+  __shared__ T dots[32], wsum[32], taus[32];
+  __shared__ T Gp[32 * 33];
+  __shared__ double s_beta;
+  __shared__ T s_tau, s_den;
+  __shared__ double red[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* X = d.ptr;
+  for (int e = threadIdx.x; e < nr * b; e += kThreads) {
+    const int r = e % nr, jj = e / nr;
+    P[r + jj * ld] = X[(r0 + r) + (int64_t)(j0 + jj) * d.ld];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < b; ++jj) {
+    const int j = j0 + jj;
+    const T* pc = P + jj * ld;
+    double sq = 0.0;
+    for (int r = max(r0, j + 1) + threadIdx.x; r < r1; r += kThreads) {
+      const double v = (double)pc[r - r0];
+      sq += v * v;
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) red[warp] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += red[w];
+      sq_part = t;
+      if (j >= r0 && j < r1) alpha_s = (double)pc[j - r0];
+    }
+    cl.sync();  // (A) partial norms and the diagonal entry visible
+    const int owner = (j - j0) / per;
+    if (threadIdx.x == 0) {
+      double sig = 0.0;
+      for (int q = 0; q < CS; ++q) sig += *cl.map_shared_rank(&sq_part, q);
+      const double alpha = *cl.map_shared_rank(&alpha_s, owner);
+      double beta, tau;
+      if (sig == 0.0) {
+        beta = alpha;
+        tau = 0.0;
+      } else {
+        const double nrm = sqrt(alpha * alpha + sig);
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+      }
+      s_beta = beta;
+      s_tau = (T)tau;
+      s_den = sig == 0.0 ? T(1) : (T)(alpha - beta);
+      taus[jj] = (T)tau;
+    }
+    __syncthreads();
+    const T tau = s_tau, den = s_den;
+    T* pcw = P + jj * ld;
+    if (tau != T(0))
+      for (int r = max(r0, j + 1) + threadIdx.x; r < r1; r += kThreads) pcw[r - r0] = pcw[r - r0] / den;
+    __syncthreads();
+    if (rank == owner && threadIdx.x == 0) pcw[j - r0] = (T)s_beta;
+    // partial products v . x_c for the panel columns c > jj (v_j = 1)
+    for (int c = jj + 1 + warp; c < b; c += kWarps) {
+      const T* xc = P + c * ld;
+      T acc = T(0);
+      for (int r = max(r0, j) + lane; r < r1; r += 32) acc += (r == j ? T(1) : pc[r - r0]) * xc[r - r0];
+      acc = warp_sum(acc);
+      if (lane == 0) dots[c] = acc;
+    }
+    cl.sync();  // (B) partial products visible
+    if (threadIdx.x > jj && threadIdx.x < b) {
+      T w = T(0);
+      for (int q = 0; q < CS; ++q) w += *cl.map_shared_rank(&dots[threadIdx.x], q);
+      wsum[threadIdx.x] = tau * w;
+    }
+    __syncthreads();
+    if (tau != T(0)) {
+      const int rbeg = max(r0, j);
+      const int cnt = r1 - rbeg;
+      for (int e = threadIdx.x; cnt > 0 && e < cnt * (b - jj - 1); e += kThreads) {
+        const int rr = e % cnt, c = jj + 1 + e / cnt;
+        const int r = rbeg + rr;
+        const T v = r == j ? T(1) : pc[r - r0];
+        P[(r - r0) + c * ld] -= wsum[c] * v;
+      }
+    }
+    __syncthreads();
+  }
+  // Gram of the unit-lower reflectors over this CTA's rows: G[l, i] = v_l . v_i, l < i
+  for (int pq = warp; pq < b * b; pq += kWarps) {
+    const int l = pq % b, i = pq / b;
+    if (l >= i) continue;
+    T acc = T(0);
+    for (int r = max(r0, j0 + i) + lane; r < r1; r += 32) {
+      const T vi = r == j0 + i ? T(1) : P[(r - r0) + i * ld];
+      acc += P[(r - r0) + l * ld] * vi;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) Gp[l + i * 33] = acc;
+  }
+  cl.sync();  // (C) partial Gram matrices visible
+  if (rank == 0 && warp == 0) {
+    // G summed over the cluster, then T column by column: T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i]
+    T* Tm = Tbuf + (int64_t)f * nb * nb;
+    for (int i = 0; i < b; ++i) {
+      T g = T(0);
+      if (lane < i)
+        for (int q = 0; q < CS; ++q) g += *cl.map_shared_rank(&Gp[lane + i * 33], q);
+      wsum[lane] = g;  // G[lane, i]
+      __syncwarp();
+      T acc = T(0);
+      if (lane < i)
+        for (int qq = lane; qq < i; ++qq) acc += Tm[lane + qq * nb] * wsum[qq];
+      __syncwarp();
+      if (lane < i) Tm[lane + i * nb] = -taus[i] * acc;
+      if (lane == i) Tm[i + i * nb] = taus[i];
+      if (lane > i && lane < nb) Tm[lane + i * nb] = T(0);
+      __syncwarp();
+    }
+  }
+  // the panel back to global memory (R above, reflectors below the diagonal)
+  for (int e = threadIdx.x; e < nr * b; e += kThreads) {
+    const int r = e % nr, jj = e / nr;
+    X[(r0 + r) + (int64_t)(j0 + jj) * d.ld] = P[r + jj * ld];
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 // Trailing update of columns [j0+b, n) in tiles of 32 columns per CTA:
 // C <- C - V (T^T (V^T C)), rows j0..m-1.
 constexpr int kTN = 32;
@@ -1387,11 +1538,40 @@ cudaError_t launch_front_qr_warp(const FrontDesc<T>* d, int count, int per_warp_
   return cudaGetLastError();
 }
 
+// rows_max = the largest m - j0 of the batch: panels that fit the shared memory
+// of at most 16 CTAs take the cluster kernel, others the one-CTA kernel.
 template <typename T>
-cudaError_t launch_front_panel(const FrontDesc<T>* d, int count, int j0, int nb, T* Tbuf, cudaStream_t st) {
+cudaError_t launch_front_panel(const FrontDesc<T>* d, int count, int j0, int nb, T* Tbuf, cudaStream_t st,
+                               int rows_max) {
   if (count <= 0) return cudaSuccess;
-  front_panel_kernel<T><<<(unsigned)count, kThreads, 0, st>>>(d, j0, nb, Tbuf);
-  return cudaGetLastError();
+  const int lim = max_smem_optin() - 12 * 1024;  // room for the kernel's static shared memory
+  const int per_cap = lim / (nb * (int)sizeof(T)) - 1;
+  int cs = 1;
+  while (cs < 16 && (rows_max + cs - 1) / cs > per_cap) cs *= 2;
+  const int per_max = (rows_max + cs - 1) / cs;
+  if (rows_max <= 0 || per_max > per_cap) {
+    front_panel_kernel<T><<<(unsigned)count, kThreads, 0, st>>>(d, j0, nb, Tbuf);
+    return cudaGetLastError();
+  }
+  static bool init = false;
+  if (!init) {
+    allow_smem(front_panel_cluster_kernel<T>);
+    cudaFuncSetAttribute(front_panel_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    init = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(count * cs));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = (size_t)(per_max | 1) * nb * sizeof(T);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, front_panel_cluster_kernel<T>, d, j0, nb, Tbuf, per_max);
 }
 
 template <typename T>
@@ -1485,10 +1665,68 @@ cudaError_t launch_scatter_values(T* base, const int64_t* dest, const T* vals, i
   return cudaGetLastError();
 }
 
+// The tensor-core panel steps of one blocked group: for every panel j0 the
+// fronts still active, with P / Wp carved from the scratch after the
+// descriptors (the same P / Wp region serves every panel: the panels run in
+// stream order).  Returns the descriptors [panel][front] and per-panel offsets.
+template <typename T>
+static size_t tc_group_layout(const std::vector<FrontDesc<T>>& fronts, const T* Tbuf, unsigned char* base,
+                              std::vector<TcPanel>& all, std::vector<size_t>& first) {
+  constexpr int nb = 32;
+  int steps_max = 0;
+  for (auto& f : fronts) steps_max = std::max(steps_max, std::min(f.c, f.m));
+  const int npan = (steps_max + nb - 1) / nb;
+  all.clear();
+  first.assign((size_t)npan + 1, 0);
+  size_t work_max = 0;
+  for (int p = 0; p < npan; ++p) {
+    const int j0 = p * nb;
+    first[(size_t)p] = all.size();
+    size_t off = 0;
+    for (size_t fi = 0; fi < fronts.size(); ++fi) {
+      const auto& f = fronts[fi];
+      const int steps = std::min(f.c, f.m);
+      if (j0 >= steps) continue;
+      TcPanel t{};
+      t.b = std::min(nb, steps - j0);
+      t.ncols = f.n - j0 - t.b;
+      t.mr = f.m - j0;
+      if (t.ncols <= 0 || t.mr <= 0) continue;
+      t.X = reinterpret_cast<float*>(f.ptr);
+      t.Tm = reinterpret_cast<const float*>(Tbuf) + fi * nb * nb;
+      t.ld = f.ld;
+      t.j0 = j0;
+      tc_plan_panel(t);
+      t.P = reinterpret_cast<float*>(base) + off;  // offsets relative to the work region, fixed below
+      off += tc_panel_scratch(t);
+      t.Wp = t.P + (size_t)t.nsl * t.ncols * 32;
+      all.push_back(t);
+    }
+    work_max = std::max(work_max, off);
+  }
+  first[(size_t)npan] = all.size();
+  return work_max;
+}
+
+template <typename T>
+size_t front_groups_tc_bytes(const std::vector<FrontGroup>& groups, const std::vector<std::vector<FrontDesc<T>>>& host) {
+  if (sizeof(T) != sizeof(float)) return 0;
+  size_t need = 0;
+  for (size_t g = 0; g < groups.size(); ++g) {
+    if (groups[g].kind != 2) continue;
+    std::vector<TcPanel> all;
+    std::vector<size_t> first;
+    const size_t work = tc_group_layout<T>(host[g], nullptr, nullptr, all, first);
+    const size_t desc = (all.size() * sizeof(TcPanel) + 255) / 256 * 256;
+    need = std::max(need, desc + work * sizeof(float));
+  }
+  return need;
+}
+
 template <typename T>
 cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std::vector<const FrontDesc<T>*>& d,
                                 const std::vector<std::vector<FrontDesc<T>>>& host, T* Tbuf, cudaStream_t st,
-                                int64_t* launches) {
+                                int64_t* launches, void* tc_scratch) {
   cudaError_t e = cudaSuccess;
   for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
     const FrontGroup& G = groups[g];
@@ -1501,18 +1739,48 @@ cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std
       ++*launches;
     } else {
       const int nb = 32;
-      for (int j0 = 0; j0 < G.param && e == cudaSuccess; j0 += nb) {
-        int maxtiles = 0;
-        for (auto& f : host[g]) {
-          const int steps = f.c < f.m ? f.c : f.m;
-          if (j0 >= steps) continue;
-          const int b = steps - j0 < nb ? steps - j0 : nb;
-          const int tiles = (f.n - (j0 + b) + 31) / 32;
-          maxtiles = tiles > maxtiles ? tiles : maxtiles;
+      const bool tc = sizeof(T) == sizeof(float) && tc_scratch != nullptr;
+      std::vector<TcPanel> all;
+      std::vector<size_t> first;
+      TcPanel* d_all = nullptr;
+      if (tc) {
+        // descriptors first, then the P / Wp work region
+        std::vector<TcPanel> probe;
+        std::vector<size_t> pf;
+        tc_group_layout<T>(host[g], Tbuf, nullptr, probe, pf);
+        const size_t dbytes = (probe.size() * sizeof(TcPanel) + 255) / 256 * 256;
+        unsigned char* work = static_cast<unsigned char*>(tc_scratch) + dbytes;
+        tc_group_layout<T>(host[g], Tbuf, work, all, first);
+        d_all = static_cast<TcPanel*>(tc_scratch);
+        if (!all.empty()) e = cudaMemcpyAsync(d_all, all.data(), all.size() * sizeof(TcPanel), cudaMemcpyHostToDevice, st);
+      }
+      int p = 0;
+      for (int j0 = 0; j0 < G.param && e == cudaSuccess; j0 += nb, ++p) {
+        int rows_max = 0;
+        for (auto& f : host[g])
+          if (j0 < std::min(f.c, f.m)) rows_max = std::max(rows_max, f.m - j0);
+        e = launch_front_panel<T>(d[g], cnt, j0, nb, Tbuf, st, rows_max);
+        ++*launches;
+        if (e != cudaSuccess) break;
+        if (tc) {
+          const size_t a = first[(size_t)p], b = first[(size_t)p + 1];
+          if (b > a) {
+            std::vector<TcPanel> cur(all.begin() + (long)a, all.begin() + (long)b);
+            e = launch_tc_panels(d_all + a, cur, st);
+            *launches += 3;
+          }
+        } else {
+          int maxtiles = 0;
+          for (auto& f : host[g]) {
+            const int steps = f.c < f.m ? f.c : f.m;
+            if (j0 >= steps) continue;
+            const int b = steps - j0 < nb ? steps - j0 : nb;
+            const int tiles = (f.n - (j0 + b) + 31) / 32;
+            maxtiles = tiles > maxtiles ? tiles : maxtiles;
+          }
+          e = launch_front_trailing<T>(d[g], cnt, j0, nb, Tbuf, maxtiles, st);
+          ++*launches;
         }
-        e = launch_front_panel<T>(d[g], cnt, j0, nb, Tbuf, st);
-        if (e == cudaSuccess) e = launch_front_trailing<T>(d[g], cnt, j0, nb, Tbuf, maxtiles, st);
-        *launches += 2;
       }
       if (e == cudaSuccess) e = launch_front_finish<T>(d[g], cnt, G.param, st);
       ++*launches;
@@ -1524,13 +1792,15 @@ cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std
 #define SPAQR_INST(T)                                                                                     \
   template cudaError_t launch_front_groups<T>(const std::vector<FrontGroup>&, const std::vector<const FrontDesc<T>*>&, \
                                               const std::vector<std::vector<FrontDesc<T>>>&, T*, cudaStream_t,       \
-                                              int64_t*);                                                             \
+                                              int64_t*, void*);                                                      \
+  template size_t front_groups_tc_bytes<T>(const std::vector<FrontGroup>&,                                          \
+                                           const std::vector<std::vector<FrontDesc<T>>>&);                         \
   template cudaError_t launch_scatter_values<T>(T*, const int64_t*, const T*, int64_t, cudaStream_t);    \
   template cudaError_t launch_copy<T>(const CopyDesc<T>*, const int*, int, int, cudaStream_t);           \
   template cudaError_t launch_identity<T>(const CopyDesc<T>*, int, cudaStream_t);                        \
   template cudaError_t launch_front_qr_smem<T>(const FrontDesc<T>*, int, int, cudaStream_t);             \
   template cudaError_t launch_front_qr_warp<T>(const FrontDesc<T>*, int, int, cudaStream_t);             \
-  template cudaError_t launch_front_panel<T>(const FrontDesc<T>*, int, int, int, T*, cudaStream_t);      \
+  template cudaError_t launch_front_panel<T>(const FrontDesc<T>*, int, int, int, T*, cudaStream_t, int); \
   template cudaError_t launch_front_trailing<T>(const FrontDesc<T>*, int, int, int, const T*, int,       \
                                                 cudaStream_t);                                           \
   template cudaError_t launch_front_finish<T>(const FrontDesc<T>*, int, int, cudaStream_t);                   \

@@ -484,8 +484,11 @@ void Factorizer<T>::front_qr(std::vector<FrontDesc<T>>& fr) {
     dev[g] = up_.put(host[g]);
     if (groups[g].kind == 2) Tbuf = static_cast<T*>(up_.scratch(host[g].size() * 32 * 32 * sizeof(T)));
   }
+  // FP32 factor: blocked fronts take the tensor-core trailing updates
+  const size_t tc_bytes = front_groups_tc_bytes<T>(groups, host);
+  void* tc_scratch = tc_bytes ? up_.scratch(tc_bytes) : nullptr;
   tm_.begin(st_, 1);
-  check(launch_front_groups<T>(groups, dev, host, Tbuf, st_, &launches_), "front_qr");
+  check(launch_front_groups<T>(groups, dev, host, Tbuf, st_, &launches_, tc_scratch), "front_qr");
   tm_.end(st_);
 }
 
@@ -1554,6 +1557,8 @@ void run_factor(Handle& h, const spaqr_csr& A, const Analysis& an) {
   if (h.precision == SPAQR_PREC_MIXED) {
     Factorizer<float> f(h, an);
     f.run(A);
+    SPAQR_CUDA(cudaStreamSynchronize(h.st));
+    if (tc_take_timeout()) throw Error(SPAQR_ERR_TIMEOUT, "tensor-core trailing update: MMA completion wait timed out");
   } else {
     Factorizer<double> f(h, an);
     f.run(A);

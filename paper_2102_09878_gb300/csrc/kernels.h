@@ -95,7 +95,8 @@ template <typename T> cudaError_t launch_front_qr_warp(const FrontDesc<T>* d, in
 
 // Large fronts, blocked: panel j0..j0+nb of each front then the trailing update.
 template <typename T>
-cudaError_t launch_front_panel(const FrontDesc<T>* d, int count, int j0, int nb, T* Tbuf, cudaStream_t st);
+cudaError_t launch_front_panel(const FrontDesc<T>* d, int count, int j0, int nb, T* Tbuf, cudaStream_t st,
+                               int rows_max);
 template <typename T>
 cudaError_t launch_front_trailing(const FrontDesc<T>* d, int count, int j0, int nb, const T* Tbuf, int max_tiles,
                                   cudaStream_t st);
@@ -286,10 +287,14 @@ inline std::vector<FrontGroup> plan_fronts(const std::vector<int>& ms, const std
 
 // Run every group of plan_fronts: d[g] are the device descriptor arrays of the
 // groups (in order), Tbuf holds 32*32 elements per front of the blocked group.
+// tc_scratch (FP32 only; may be null = SIMT trailing updates) holds
+// front_groups_tc_bytes() bytes for the tensor-core trailing updates.
 template <typename T>
 cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std::vector<const FrontDesc<T>*>& d,
                                 const std::vector<std::vector<FrontDesc<T>>>& host, T* Tbuf, cudaStream_t st,
-                                int64_t* launches);
+                                int64_t* launches, void* tc_scratch = nullptr);
+template <typename T>
+size_t front_groups_tc_bytes(const std::vector<FrontGroup>& groups, const std::vector<std::vector<FrontDesc<T>>>& host);
 
 inline int front_smem_bytes(int m, int n, int c, int elem) {
   return (int)((long long)m * n * elem + ((c + 31) / 32) * 4 + 16);
@@ -308,5 +313,28 @@ template <typename T> cudaError_t launch_identity(const CopyDesc<T>* d, int coun
 template <typename T> cudaError_t launch_scatter_values(T* base, const int64_t* dest, const T* vals, int64_t n, cudaStream_t st);
 
 int max_smem_optin();
+
+// ---------------------------------------------- tensor-core trailing update
+// One panel step of the FP32 blocked front QR on tcgen05 in 3xTF32
+// (tc_kernels.cu): with V = the b (<= 32) reflectors of columns j0..j0+b-1 of
+// X (rows j0..m-1) and T (32 x 32, ld 32) from the panel kernel,
+// C = X[j0:m, j0+b : j0+b+ncols] <- C - V T^T V^T C.  P and Wp are scratch
+// (tc_panel_scratch floats from P, Wp right after).
+struct TcPanel {
+  float* X;
+  const float* Tm;
+  float* P;
+  float* Wp;
+  int mr, ld, j0, b, ncols;  // mr = m - j0 rows
+  int nsl, rps;              // row slices of the projection and rows per slice (tc_plan_panel)
+};
+void tc_plan_panel(TcPanel& f);
+size_t tc_panel_scratch(const TcPanel& f);
+cudaError_t launch_tc_panels(const TcPanel* d_panels, const std::vector<TcPanel>& host, cudaStream_t st);
+// C[0:m, 0:n] -= A[0:m, 0:k] B[0:k, 0:n] (FP32, column-major) on tcgen05, 3xTF32
+cudaError_t launch_tc_gemm(int m, int n, int k, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                           cudaStream_t st);
+// 1 (and reset) if a tensor-core kernel gave up waiting for its MMAs since the last call
+int tc_take_timeout();
 
 }  // namespace spaqr
