@@ -170,6 +170,7 @@ def run_gpu(args, rank, world):
     kn = {k: 0 for k in kt}
     flops_front = 0.0
     flops_qrcp = 0.0
+    bytes_qrcp = 0.0
     launches = 0
     iters = []
     t_factor, t_solve = [], []
@@ -182,6 +183,7 @@ def run_gpu(args, rank, world):
             kn[k] += st["n_kernel"][k]
         flops_front += st["flops_front"]
         flops_qrcp += st["flops_qrcp"]
+        bytes_qrcp += st["bytes_qrcp"]
         launches += st["launches"] + st["n_kernel"]["apply"] + 9 * st["iters"]
         iters.append(st["iters"])
         t_factor.append(st["t_factor"])
@@ -235,35 +237,51 @@ def run_gpu(args, rank, world):
                    "t_factor": sc["t_factor"], "t_solve": sc["t_solve"],
                    "kernel_seconds": {k: v for k, v in sc["t_kernel"].items()}}
     return dict(secs=secs, prob=prob, depth=depth, stats=stats, kt=kt, kn=kn, flops_front=flops_front,
-                flops_qrcp=flops_qrcp, compare=compare,
+                flops_qrcp=flops_qrcp, bytes_qrcp=bytes_qrcp, compare=compare,
                 launches=launches, iters=iters, rel=rel, e2e=e2e, clocks=clocks, t_factor=t_factor,
                 t_solve=t_solve, t_analyze=stats["t_analyze"])
+
+
+HBM_PEAK = 6660.3  # GB/s, MEASURED_PEAKS.json hbm_gbs
+
+
+def family_rooflines(res, precision):
+    """Live roofline of every device kernel family over the timed steps (CUDA
+    events recorded by the library on its stream around each launch)."""
+    kt = res["kt"]
+    st = res["stats"]
+    alu = PEAKS["fp64_alu_tflops"] if precision == "fp64" else PEAKS["fp32_alu_tflops"]
+    alu_src = ("FP64 rate of the recipe table, 1.25 TFLOP/s (of nominal)" if precision == "fp64" else
+               "FP32 lanes: 152 SMs x 128 x 2 flops x 2.07 GHz = 80.5 TFLOP/s (derived, of nominal)")
+    out = {}
+    if kt["qrcp"] > 0:
+        ach = res["bytes_qrcp"] / kt["qrcp"] / 1e9
+        out["qrcp"] = {"kernel": "column-pivoted QR (sparsification steps 1 and 2)", "bound": "hbm", "achieved": ach,
+                       "peak": HBM_PEAK, "unit": "GB/s", "frac": ach / HBM_PEAK, "traffic": None,
+                       "algorithmic": "one read of the unpivoted trailing block per pivot step + one read/write of "
+                                      "the matrix", "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                       "alu_view": {"achieved_tflops": res["flops_qrcp"] / kt["qrcp"] / 1e12, "peak_tflops": alu}}
+    if kt["front_qr"] > 0:
+        ach = res["flops_front"] / kt["front_qr"] / 1e12
+        out["front_qr"] = {"kernel": "front QR (eliminate + scale)", "bound": "alu", "achieved": ach, "peak": alu,
+                           "unit": "TFLOP/s", "frac": ach / alu, "traffic": None, "peak_source": alu_src}
+    if kt["apply"] > 0:
+        ach = st["bytes_apply"] * sum(res["iters"]) / kt["apply"] / 1e9
+        out["apply"] = {"kernel": "W^-1/W^-T apply", "bound": "hbm", "achieved": ach, "peak": HBM_PEAK,
+                        "unit": "GB/s", "frac": ach / HBM_PEAK, "traffic": None,
+                        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    return out
 
 
 def roofline(res, precision):
     """Roofline of the device kernel family with the largest share of the timed steps."""
     kt = res["kt"]
     dom = max(kt, key=lambda k: kt[k])
-    st = res["stats"]
-    share = kt[dom] / max(sum(kt.values()), 1e-12)
-    if dom == "apply":
-        ach = st["bytes_apply"] * sum(res["iters"]) / max(kt["apply"], 1e-12) / 1e9
-        return {"kernel": "W^-1/W^-T apply", "bound": "hbm", "achieved": ach, "peak": 6660.3, "unit": "GB/s",
-                "frac": ach / 6660.3, "traffic": None, "share": share,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
-    peak = PEAKS["fp64_alu_tflops"] if precision == "fp64" else PEAKS["fp32_alu_tflops"]
-    src = ("FP64 rate of the recipe table (1.25 TFLOP/s)" if precision == "fp64" else
-           "FP32 lanes: 152 SMs x 128 x 2 flops x 2.07 GHz = 80.5 TFLOP/s (derived, of nominal)")
-    if dom == "qrcp":
-        ach = res["flops_qrcp"] / max(kt["qrcp"], 1e-12) / 1e12
-        name = "column-pivoted QR (sparsification steps 1 and 2)"
-    else:
-        ach = res["flops_front"] / max(kt["front_qr"], 1e-12) / 1e12
-        name = "front QR (eliminate + scale)"
-        if dom != "front_qr":
-            name += f" (largest family: {dom})"
-    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "share": share, "peak_source": src}
+    fam = family_rooflines(res, precision)
+    key = dom if dom in fam else max(fam, key=lambda k: kt[k])
+    out = dict(fam[key])
+    out["share"] = kt[key] / max(sum(kt.values()), 1e-12)
+    return out
 
 
 def main():
@@ -331,7 +349,8 @@ def main():
         "detail": {"iters": res["iters"], "rel_resid": res["rel"], "t_factor": res["t_factor"],
                    "t_solve": res["t_solve"], "t_analyze": res["t_analyze"], "nnz_W": st["nnz_W"],
                    "kernel_seconds": res["kt"], "kernel_launches": res["kn"], "flops_front": res["flops_front"],
-                   "flops_qrcp": res["flops_qrcp"],
+                   "flops_qrcp": res["flops_qrcp"], "bytes_qrcp": res["bytes_qrcp"],
+                   "rooflines": family_rooflines(res, args.precision),
                    "phase_seconds": st["t_phase"], "syncs": st["syncs"], "top_front": [st["top_rows"], st["top_cols"]],
                    "max_front": [st["max_front_rows"], st["max_front_cols"]]},
     }

@@ -216,6 +216,8 @@ typedef struct {
   int64_t n_kernel[6]; /* launches counted in each family */
   double bytes_apply;  /* algorithmic bytes of one W^{-1} plus one W^{-T} apply */
   double flops_qrcp;   /* algorithmic flops of the column-pivoted QRs alone, 4mnk - 2k^2(m+n) + 4k^3/3 each */
+  double bytes_qrcp;   /* algorithmic bytes of the same QRs: one read of the unpivoted trailing block per
+                          pivot step, elem * (kmn - k^2(m+n)/2 + k^3/3), plus reading and writing m x n once */
 } spaqr_stats;
 
 int spaqr_get_stats(const spaqr_handle* h, spaqr_stats* st);

@@ -93,6 +93,7 @@ class Stats(C.Structure):
         ("n_kernel", C.c_int64 * 6),
         ("bytes_apply", C.c_double),
         ("flops_qrcp", C.c_double),
+        ("bytes_qrcp", C.c_double),
     ]
 
 

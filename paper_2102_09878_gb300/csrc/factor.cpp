@@ -1153,6 +1153,7 @@ void Factorizer<T>::step1() {
     const double m = g.rows, n = g.width, k = rank[i];
     h_.stats.flops_sparsify += 4.0 * m * n * k - 2.0 * k * k * (m + n) + 4.0 * k * k * k / 3.0;
     h_.stats.flops_qrcp += 4.0 * m * n * k - 2.0 * k * k * (m + n) + 4.0 * k * k * k / 3.0;
+    h_.stats.bytes_qrcp += sizeof(T) * (k * m * n - k * k * (m + n) / 2.0 + k * k * k / 3.0 + 2.0 * m * n);
     if (rank[i] < g.rows) {
       g.rows = rank[i];
       if (g.rows == 0) {
@@ -1332,6 +1333,7 @@ void Factorizer<T>::step2() {
       const double m = op.c, n = recs[i].ncm, kk = k;
       h_.stats.flops_sparsify += 4.0 * m * n * kk - 2.0 * kk * kk * (m + n) + 4.0 * kk * kk * kk / 3.0;
       h_.stats.flops_qrcp += 4.0 * m * n * kk - 2.0 * kk * kk * (m + n) + 4.0 * kk * kk * kk / 3.0;
+      h_.stats.bytes_qrcp += sizeof(T) * (kk * m * n - kk * kk * (m + n) / 2.0 + kk * kk * kk / 3.0 + 2.0 * m * n);
       h_.stats.flops_sparsify += 4.0 * kk * m * n;
     }
     if (k >= op.c) {
