@@ -1006,7 +1006,26 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_delayed_kernel(const QrcpDes
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         vr[t] = (t >= nb || r < i0 + t) ? T(0) : (r == i0 + t ? T(1) : __ldcg(W + r + (int64_t)piv[t] * m));
-      for (int q = 0; q < nact; ++q) {
+      // four columns per pass: their loads are issued before any store
+      int q = 0;
+      for (; q + 3 < nact; q += 4) {
+        T* p4[4];
+        T a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          p4[u] = X + r + (int64_t)act[q + u] * m;
+          a[u] = *p4[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const T* Fc = F + (size_t)act[q + u] * NB;
+#pragma unroll
+          for (int t = 0; t < NB; ++t) a[u] -= vr[t] * Fc[t];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) *p4[u] = a[u];
+      }
+      for (; q < nact; ++q) {
         const int c = act[q];
         const T* Fc = F + (size_t)c * NB;
         T a = X[r + (int64_t)c * m];
@@ -1163,7 +1182,22 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_delayed_kernel(const QrcpDes
 #pragma unroll
       for (int j = 0; j < KG; ++j) acc[j] = T(0);
       if (tau != T(0)) {
-        for (int r = i + lane; r < m; r += 32) {
+        // four rows per lane per pass: 4 x KG independent loads in flight
+        int r = i + lane;
+        for (; r + 96 < m; r += 128) {
+          T vr[4], x[4][KG];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) vr[u] = vcur[r + 32 * u - i];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < KG; ++j) x[u][j] = cols[j][r + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < KG; ++j) acc[j] += vr[u] * x[u][j];
+        }
+        for (; r < m; r += 32) {
           const T vr = vcur[r - i];
 #pragma unroll
           for (int j = 0; j < KG; ++j) acc[j] += vr * cols[j][r];
