@@ -621,8 +621,8 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
   int* step_of = reinterpret_cast<int*>(nuref + nl_max);  // nl_max
   int* act = step_of + nl_max;                            // unpivoted local columns, nl_max
   int* pos = act + nl_max;                                // position of each column in act
-  T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // m_max + 2
-  T* taus = vbuf + ((m_max + 3) & ~1);             // min(m_max, n) + 2
+  T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // 2 x (m_max + 2)
+  T* taus = vbuf + 2 * ((m_max + 3) & ~1);         // min(m_max, n) + 2
   T* X = SMEM ? taus + ((m_max + 3) & ~1) : d.work + (size_t)j0 * m;
   __shared__ double cand_v;
   __shared__ int cand_j;
@@ -678,8 +678,20 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
       wj = oj;
     }
   }
+  // One cluster barrier per pivot step: every CTA forms, before the barrier,
+  // the reflector of its own best column (without writing it back); after the
+  // barrier all agree on the winner and copy the winner's reflector.  The
+  // proposal and reflector slots alternate between two buffers by step parity,
+  // so a CTA never overwrites a slot another CTA may still be reading.
+  const int vstride = (m_max + 3) & ~1;
+  __shared__ double cand_v2[2], sp_beta[2];
+  __shared__ int cand_j2[2], sp_stop[2];
+  __shared__ T sp_tau[2], s_den;
+  __shared__ double red2[kWarps];
   for (int i = 0; i < kmax; ++i) {
-    // (1) local proposal: reduce the warps' proposals
+    const int par = i & 1;
+    T* vb = vbuf + par * vstride;
+    // (1) the CTA's best column
     if (lane == 0) {
       red_v[warp] = wv;
       red_i[warp] = wj;
@@ -693,17 +705,56 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
           v = red_v[w];
           j = red_i[w];
         }
-      cand_v = v;
-      cand_j = j;
+      cand_v2[par] = v;
+      cand_j2[par] = j;
     }
-    cl.sync();  // (A) proposals visible cluster-wide
+    __syncthreads();
+    const int jloc = cand_j2[par];
+    // (2) its reflector, rows i..m-1, into vb (the column itself is untouched)
+    if (jloc != INT_MAX) {
+      const T* col = X + (int64_t)(jloc - j0) * m;
+      double sq = 0.0;
+      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) {
+        const double v = (double)col[r];
+        sq += v * v;
+      }
+      sq = warp_sum(sq);
+      if (lane == 0) red2[warp] = sq;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double sig = 0.0;
+        for (int w = 0; w < kWarps; ++w) sig += red2[w];
+        const double alpha = (double)col[i];
+        double beta, tau;
+        if (sig == 0.0) {
+          beta = alpha;
+          tau = 0.0;
+        } else {
+          const double nrm = sqrt(alpha * alpha + sig);
+          beta = alpha >= 0.0 ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+        }
+        const double ab = fabs(beta);
+        const double r11_here = (i == 0) ? ab : r11;
+        const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
+        sp_beta[par] = beta;
+        sp_tau[par] = (T)tau;
+        sp_stop[par] = stop;
+        s_den = (!stop && sig != 0.0) ? (T)(alpha - beta) : T(0);
+      }
+      __syncthreads();
+      const T den = s_den;
+      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) vb[r - i] = den != T(0) ? col[r] / den : T(0);
+      if (threadIdx.x == 0) vb[0] = T(1);
+    }
+    cl.sync();  // proposals and candidate reflectors visible cluster-wide
+    // (3) the winner: one lane per CTA of the cluster, then a warp reduction
     if (threadIdx.x < 32) {
-      // one lane per CTA of the cluster, then a warp reduction
       double v = -1.0;
       int j = INT_MAX;
       if (lane < CS) {
-        v = *cl.map_shared_rank(&cand_v, lane);
-        j = *cl.map_shared_rank(&cand_j, lane);
+        v = *cl.map_shared_rank(&cand_v2[par], lane);
+        j = *cl.map_shared_rank(&cand_j2[par], lane);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -720,70 +771,36 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
     const int p = s_piv;
     if (p == INT_MAX) break;  // no proposal (non-finite norms): every CTA sees the same p
     const int owner = p / nl;
-    if (rank == owner) {
-      // reflector of column p, rows i..m-1 (warp 0), copied into vbuf
-      const int pl = p - j0;
-      if (threadIdx.x < 32) {
-        T* col = X + (int64_t)pl * m;
-        double sig = 0.0;
-        for (int r = i + 1 + lane; r < m; r += 32) {
-          const double v = (double)col[r];
-          sig += v * v;
-        }
-        sig = warp_sum(sig);
-        const double alpha = (double)col[i];
-        double beta, tau;
-        if (sig == 0.0) {
-          beta = alpha;
-          tau = 0.0;
-        } else {
-          const double nrm = sqrt(alpha * alpha + sig);
-          beta = alpha >= 0.0 ? -nrm : nrm;
-          tau = (beta - alpha) / beta;
-        }
-        const double ab = fabs(beta);
-        const double r11_here = (i == 0) ? ab : r11;
-        const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
-        if (!stop && sig != 0.0) {
-          const T den = (T)(alpha - beta);
-          for (int r = i + 1 + lane; r < m; r += 32) {
-            const T v = col[r] / den;
-            col[r] = v;
-            vbuf[r - i] = v;
-          }
-        } else {
-          for (int r = i + 1 + lane; r < m; r += 32) vbuf[r - i] = T(0);
-        }
-        __syncwarp();
-        if (lane == 0) {
-          vbuf[0] = T(1);
-          if (!stop) col[i] = (T)beta;
-          s_tau = (T)tau;
-          s_beta = beta;
-          s_stop = stop;
-        }
-      }
-    }
-    cl.sync();  // (C) reflector ready in the owner's shared memory
     if (rank != owner) {
-      for (int r = threadIdx.x; r < m - i; r += kThreads) vbuf[r] = *cl.map_shared_rank(vbuf + r, owner);
+      for (int r = threadIdx.x; r < m - i; r += kThreads) vb[r] = *cl.map_shared_rank(vb + r, owner);
       if (threadIdx.x == 0) {
-        s_tau = *cl.map_shared_rank(&s_tau, owner);
-        s_beta = *cl.map_shared_rank(&s_beta, owner);
-        s_stop = *cl.map_shared_rank(&s_stop, owner);
+        s_tau = *cl.map_shared_rank(&sp_tau[par], owner);
+        s_beta = *cl.map_shared_rank(&sp_beta[par], owner);
+        s_stop = *cl.map_shared_rank(&sp_stop[par], owner);
       }
+    } else if (threadIdx.x == 0) {
+      s_tau = sp_tau[par];
+      s_beta = sp_beta[par];
+      s_stop = sp_stop[par];
     }
     __syncthreads();
     if (i == 0) r11 = fabs(s_beta);
     if (s_stop) break;
     const T tau = s_tau;
     if (threadIdx.x == 0) taus[i] = tau;
-    if (rank == owner && threadIdx.x == 0) {
-      const int pl = p - j0, q = pos[pl], last = act[s_nact - 1];
-      step_of[pl] = i;
-      act[q] = last;
-      pos[last] = q;
-      s_nact = s_nact - 1;
+    if (rank == owner) {
+      // the pivot column becomes beta at row i and the reflector below
+      const int pl = p - j0;
+      T* col = X + (int64_t)pl * m;
+      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) col[r] = vb[r - i];
+      if (threadIdx.x == 0) {
+        col[i] = (T)s_beta;
+        const int q = pos[pl], last = act[s_nact - 1];
+        step_of[pl] = i;
+        act[q] = last;
+        pos[last] = q;
+        s_nact = s_nact - 1;
+      }
     }
     __syncthreads();
     // apply H_i to the CTA's unpivoted columns (the compact list act[0..nact)):
@@ -808,7 +825,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
       for (int j = 0; j < KG; ++j) acc[j] = T(0);
       if (tau != T(0)) {
         for (int r = i + 1 + lane; r < m; r += 32) {
-          const T vr = vbuf[r - i];
+          const T vr = vb[r - i];
 #pragma unroll
           for (int j = 0; j < KG; ++j) acc[j] += vr * cols[j][r];
         }
@@ -830,7 +847,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
       if (lead && jl < ng) colme[i] = (T)xnew;
       if (tau != T(0)) {
         for (int r = i + 1 + lane; r < m; r += 32) {
-          const T vr = vbuf[r - i];
+          const T vr = vb[r - i];
 #pragma unroll
           for (int j = 0; j < KG; ++j)
             if (j < ng) cols[j][r] -= wv8[j] * vr;

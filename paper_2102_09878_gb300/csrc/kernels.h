@@ -115,7 +115,7 @@ constexpr int kQrcpNB = 16;
 // (slab) or the delayed-update coefficients (nl x kQrcpNB)
 inline int qrcp_smem_bytes(int m, int nl, int elem, bool slab) {
   long long b = ((long long)nl * 28 + 15) / 16 * 16;  // nu, nuref, step_of, act, pos
-  b += (long long)(((m + 3) & ~1) * 2) * elem;         // vbuf, taus
+  b += (long long)(((m + 3) & ~1) * 3) * elem;         // two reflector buffers, taus
   if (slab)
     b += (long long)m * nl * elem;
   else
