@@ -311,9 +311,40 @@ class Factorizer {
       return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
     }
   };
+  // named host timers (printed in verbose mode, largest first)
+  std::vector<std::pair<std::string, double>> nt_;
+  const char* phase_ = "start";
+  void nt_add(const std::string& n, double dt) {
+    for (auto& e : nt_)
+      if (e.first == n) {
+        e.second += dt;
+        return;
+      }
+    nt_.emplace_back(n, dt);
+  }
+  // successive sections of one function: lap("x") charges the time since the previous lap to "x"
+  struct Lap {
+    Factorizer* f;
+    double t;
+    explicit Lap(Factorizer* ff) : f(ff), t(HT::now_s()) {}
+    void operator()(const char* name) {
+      const double now = HT::now_s();
+      f->nt_add(name, now - t);
+      t = now;
+    }
+  };
+  struct NT {
+    Factorizer* f;
+    const char* name;
+    double t0;
+    NT(Factorizer* ff, const char* n) : f(ff), name(n), t0(HT::now_s()) {}
+    ~NT() { f->nt_add(name, HT::now_s() - t0); }
+  };
   void sync() {
     HT w(ht_[0]);
+    const double t0 = HT::now_s();
     SPAQR_CUDA(cudaStreamSynchronize(st_));
+    nt_add(std::string("wait in ") + phase_, HT::now_s() - t0);
     ++up_.syncs;
     up_.reset();
     tm_.drain(h_.stats.t_kernel, h_.stats.n_kernel);
@@ -447,6 +478,7 @@ class Factorizer {
 
 template <typename T>
 void Factorizer<T>::copies(const std::vector<CopyDesc<T>>& cps) {
+  NT nt_f(this, "copies (plan+launch)");
   if (cps.empty()) return;
   std::vector<int> start(cps.size() + 1, 0);
   int64_t tot = 0;
@@ -466,6 +498,7 @@ void Factorizer<T>::copies(const std::vector<CopyDesc<T>>& cps) {
 
 template <typename T>
 void Factorizer<T>::front_qr(std::vector<FrontDesc<T>>& fr) {
+  NT nt_f(this, "front_qr (plan+launch)");
   if (fr.empty()) return;
   std::vector<int> ms, ns, cs;
   for (auto& f : fr) {
@@ -494,6 +527,7 @@ void Factorizer<T>::front_qr(std::vector<FrontDesc<T>>& fr) {
 
 template <typename T>
 void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_bufs) {
+  NT nt_f(this, "qrcp (plan+launch)");
   if (qs.empty()) return;
   std::vector<int> ms, ns;
   for (auto& q : qs) {
@@ -548,6 +582,9 @@ void Factorizer<T>::index_groups(std::vector<std::vector<int>>& own, std::vector
 // ------------------------------------------------------------ init (a0)
 template <typename T>
 void Factorizer<T>::init_stage(const spaqr_csr& A) {
+  NT nt_f(this, "init_stage");
+  phase_ = "init_stage";
+  Lap lap(this);
   const StageClusters& st = an_.stages[(size_t)L_];
   sc_ = &st;
   const size_t nc = st.node.size();
@@ -564,6 +601,7 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
       pos_of[(size_t)st.verts[(size_t)t]] = (int)(t - b);
     }
   }
+  lap("init: cluster maps");
   // column scaling (R1)
   std::vector<double> nrm((size_t)h_.n, 0.0);
   for (int64_t e = 0; e < A.nnz; ++e) nrm[(size_t)A.colidx[e]] += A.vals[e] * A.vals[e];  // fixed order
@@ -572,6 +610,7 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
     if (!(nrm[(size_t)j] > 0.0)) throw Error(SPAQR_ERR_RANK_DEFICIENT, "zero column " + std::to_string(j));
     h_.D[(size_t)j] = 1.0 / std::sqrt(nrm[(size_t)j]);
   }
+  lap("init: column norms");
   // row owners by the max-norm rule on A D (R2), grouped by (owner, support);
   // rows are independent: two parallel passes (support sizes, then contents)
   const int64_t M = A.m;
@@ -624,6 +663,7 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
       sptr[(size_t)r + 1] = (int64_t)tmp.size();
     }
   });
+  lap("init: row owners");
   if (empty_row.load() >= 0) throw Error(SPAQR_ERR_INVALID_ARG, "empty row " + std::to_string(empty_row.load()));
   for (int64_t r = 0; r < M; ++r) sptr[(size_t)r + 1] += sptr[(size_t)r];
   sups.resize((size_t)sptr[(size_t)M]);
@@ -637,6 +677,7 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
       std::copy(tmp.begin(), tmp.end(), sups.begin() + sptr[(size_t)r]);
     }
   });
+  lap("init: row supports");
   // counting sort by owner, then (support, row) inside an owner
   std::vector<int64_t> cnt(nc + 1, 0);
   for (int64_t r = 0; r < M; ++r) cnt[(size_t)owner[(size_t)r] + 1]++;
@@ -656,6 +697,7 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
   parallel_for((int64_t)nc, [&](int64_t b, int64_t e, int) {
     for (int64_t c = b; c < e; ++c) std::sort(order.begin() + cnt[(size_t)c], order.begin() + cnt[(size_t)c + 1], sup_less);
   }, 256);
+  lap("init: sort rows");
   // groups
   std::vector<int> ids;
   std::vector<int32_t> grp_of_row((size_t)M), rowpos((size_t)M);
@@ -679,6 +721,7 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
     }
     i = j;
   }
+  lap("init: groups");
   assign_buffer(ids, true);
   // scatter the scaled values into the group blocks
   T* base = G_[(size_t)ids.front()].ptr;  // all initial groups share one buffer, in id order
@@ -696,12 +739,14 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
       }
     }
   });
+  lap("init: scatter plan");
   int64_t* d_dest = static_cast<int64_t*>(pool_.alloc(dest.size() * sizeof(int64_t)));
   T* d_vals = static_cast<T*>(pool_.alloc(vals.size() * sizeof(T)));
   SPAQR_CUDA(cudaMemcpyAsync(d_dest, dest.data(), dest.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st_));
   SPAQR_CUDA(cudaMemcpyAsync(d_vals, vals.data(), vals.size() * sizeof(T), cudaMemcpyHostToDevice, st_));
   check(launch_scatter_values<T>(base, d_dest, d_vals, A.nnz, st_), "scatter_values");
   sync();
+  lap("init: upload+scatter");
   pool_.release(d_dest);
   pool_.release(d_vals);
 }
@@ -709,6 +754,8 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
 // ------------------------------------------------------------ eliminate
 template <typename T>
 void Factorizer<T>::eliminate() {
+  NT nt_f(this, "eliminate");
+  phase_ = "eliminate";
   std::vector<int> todo;
   for (size_t c = 0; c < ccols_.size(); ++c)
     if (calive_[c] && level((int)c) == k_) todo.push_back((int)c);
@@ -761,6 +808,7 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   size_t ws = 0, ndest = 0;
   std::vector<CopyDesc<T>> gat;
   double plan_t0 = HT::now_s();
+  Lap lap(this);
   for (size_t b = 0; b < batch.size(); ++b) {
     const int s = batch[b].first;
     const auto& fg = batch[b].second;
@@ -796,6 +844,7 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   }
   T* W = static_cast<T*>(pool_.alloc(std::max<size_t>(ws, 1) * sizeof(T)));
   SPAQR_CUDA(cudaMemsetAsync(W, 0, std::max<size_t>(ws, 1) * sizeof(T), st_));
+  lap("elim: front info");
   std::vector<FrontDesc<T>> fr;
   for (size_t b = 0; b < batch.size(); ++b) {
     FrontInfo& f = fi[b];
@@ -815,8 +864,10 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
     fr.push_back(FrontDesc<T>{F, f.m, f.n, f.c, f.m});
   }
   ht_[2] += HT::now_s() - plan_t0;
+  lap("elim: gather plan");
   copies(gat);
   front_qr(fr);
+  lap("elim: gather+front launch");
   // extra-row destinations (max-norm rule over the remaining front clusters)
   std::vector<ArgmaxDesc<T>> am;
   std::vector<int> pack;  // per front: coff (ncl + 1), lvl (ncl), cid (ncl)
@@ -859,6 +910,7 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
     tm_.end(st_);
   }
   // R_s = [R_ss R_sn] into the W store
+  lap("elim: argmax plan+launch");
   std::vector<CopyDesc<T>> rc;
   for (auto& f : fi) {
     WOp op;
@@ -892,12 +944,12 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   }
   copies(rc);
   std::vector<int> dest(ndest);
-  if (ndest) {
-    SPAQR_CUDA(cudaMemcpyAsync(dest.data(), d_dest, ndest * sizeof(int), cudaMemcpyDeviceToHost, st_));
-  }
+  lap("elim: W ops");
   sync();
+  if (ndest) SPAQR_CUDA(cudaMemcpy(dest.data(), d_dest, ndest * sizeof(int), cudaMemcpyDeviceToHost));
   // new groups: returned rows per owner, then extra rows per destination
   HT ht_new(ht_[3]);
+  lap("elim: readback");
   std::vector<int> ids;
   struct Pending {
     int id;
@@ -944,6 +996,7 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   }
   assign_buffer(ids, false);
   std::vector<CopyDesc<T>> sc;
+  lap("elim: new groups");
   std::vector<int32_t> rowlist;
   std::vector<size_t> row_off(pend.size(), 0);
   for (size_t i = 0; i < pend.size(); ++i) {
@@ -964,11 +1017,14 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   }
   copies(sc);
   pool_.release(W);
+  lap("elim: scatter");
 }
 
 // ---------------------------------------------------------------- scale
 template <typename T>
 void Factorizer<T>::scale() {
+  NT nt_f(this, "scale");
+  phase_ = "scale";
   HT ht(ht_[4]);
   std::vector<std::vector<int>> own, touch;
   index_groups(own, touch);
@@ -1124,6 +1180,8 @@ void Factorizer<T>::scale() {
 // ---------------------------------------------------------------- step 1
 template <typename T>
 void Factorizer<T>::step1() {
+  NT nt_f(this, "step1");
+  phase_ = "step1";
   std::vector<QrcpDesc<T>> qs;
   std::vector<int> who;
   for (size_t p = 0; p < ccols_.size(); ++p) {
@@ -1145,8 +1203,8 @@ void Factorizer<T>::step1() {
   std::vector<T*> work;
   qrcp(qs, work);
   std::vector<int> rank(who.size());
-  SPAQR_CUDA(cudaMemcpyAsync(rank.data(), d_rank, who.size() * sizeof(int), cudaMemcpyDeviceToHost, st_));
   sync();
+  SPAQR_CUDA(cudaMemcpy(rank.data(), d_rank, who.size() * sizeof(int), cudaMemcpyDeviceToHost));
   for (T* w : work) pool_.release(w);
   for (size_t i = 0; i < who.size(); ++i) {
     Group& g = G_[(size_t)who[i]];
@@ -1167,6 +1225,8 @@ void Factorizer<T>::step1() {
 // ---------------------------------------------------------------- step 2
 template <typename T>
 void Factorizer<T>::step2() {
+  NT nt_f(this, "step2");
+  phase_ = "step2";
   HT ht(ht_[5]);
   std::vector<int> ps;
   for (size_t p = 0; p < ccols_.size(); ++p)
@@ -1315,9 +1375,8 @@ void Factorizer<T>::step2() {
   }
   // ranks back; keep the ops that drop something
   std::vector<int> kall(std::max<size_t>(kdev_next, 1));
-  if (kdev_next)
-    SPAQR_CUDA(cudaMemcpyAsync(kall.data(), kdev_all, kdev_next * sizeof(int), cudaMemcpyDeviceToHost, st_));
   sync();
+  if (kdev_next) SPAQR_CUDA(cudaMemcpy(kall.data(), kdev_all, kdev_next * sizeof(int), cudaMemcpyDeviceToHost));
   std::vector<int> ks(recs.size());
   for (size_t i = 0; i < recs.size(); ++i) ks[i] = kall[(size_t)(h_.ops[recs[i].op].kdev - kdev_all)];
   for (T* w : work_all) pool_.release(w);
@@ -1361,6 +1420,9 @@ void Factorizer<T>::step2() {
 // ---------------------------------------------------------------- merge
 template <typename T>
 void Factorizer<T>::merge() {
+  NT nt_f(this, "merge");
+  phase_ = "merge";
+  Lap lap(this);
   HT ht(ht_[6]);
   const StageClusters& nxt = an_.stages[(size_t)k_ - 1];
   const size_t nnew = nxt.node.size();
@@ -1376,6 +1438,7 @@ void Factorizer<T>::merge() {
     nchild[(size_t)P]++;
     nslots[(size_t)P].insert(nslots[(size_t)P].end(), slots_[c].begin(), slots_[c].end());
   }
+  lap("merge: clusters");
   // groups whose column layout changes get a new block
   std::vector<int> moved;
   std::vector<Group> newg;
@@ -1403,6 +1466,7 @@ void Factorizer<T>::merge() {
     }
     moved.push_back(id);
   }
+  lap("merge: classify groups");
   // new blocks for moved groups (one buffer, zero-filled)
   std::vector<int> tmpids;
   std::vector<std::vector<int>> oldsup(moved.size()), oldoff(moved.size());
@@ -1465,6 +1529,7 @@ void Factorizer<T>::merge() {
                                 oldld[i], g.ld, g.rows, wc, 0, 0});
     }
   }
+  lap("merge: relayout plan");
   copies(cps);
   for (size_t i = 0; i < moved.size(); ++i) {
     if (oldbuf[i] >= 0) {
@@ -1475,6 +1540,7 @@ void Factorizer<T>::merge() {
       }
     }
   }
+  lap("merge: copies");
   // adopt the stage k-1 clusters
   sc_ = &nxt;
   ccols_.swap(nccols);
@@ -1548,6 +1614,10 @@ void Factorizer<T>::run(const spaqr_csr& A) {
                  "[spaqr] host: waits %.3f s | index %.3f | elim plan %.3f | elim groups %.3f | scale %.3f | step2 "
                  "%.3f | merge %.3f (scale/step2/merge include their waits)\n",
                  ht_[0], ht_[1], ht_[2], ht_[3], ht_[4], ht_[5], ht_[6]);
+  if (h_.opt.verbose) {
+    std::sort(nt_.begin(), nt_.end(), [](const auto& a, const auto& b) { return a.second > b.second; });
+    for (auto& e : nt_) std::fprintf(stderr, "[spaqr] host timer %-28s %8.3f ms\n", e.first.c_str(), 1e3 * e.second);
+  }
   h_.stats.launches = launches_;
   h_.stats.syncs = up_.syncs;
   (void)t0;
