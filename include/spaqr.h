@@ -238,6 +238,22 @@ int spaqr_op_copy(const spaqr_handle* h, int64_t i, int32_t* slots, int32_t* nsl
 const char* spaqr_last_error(void);
 void spaqr_destroy(spaqr_handle* h);
 
+/* ---------------------------------------------------------------- autotuning
+ * spaqr_autotune: times, for every size class of the column-pivoted QRs
+ * (m and n in powers of two, 128..max_m rows, 64..max_n columns, at most 4M
+ * entries), each launch shape -- a cluster of 1, 2, 4, 8 or 16 CTAs with the
+ * column slabs in shared memory, or 16 CTAs over a global work copy -- on
+ * synthetic full-rank matrices that fill the GPU, and installs the fastest per
+ * class for every later factorization of this process in that precision
+ * (SPAQR_PREC_FP64: FP64 kernels, SPAQR_PREC_MIXED: FP32 kernels).  Writes the
+ * table (with the timings as comments) to path when path != NULL; *seconds
+ * (may be NULL) receives the tuning time.  Untuned classes keep the built-in
+ * rule.  Errors: INVALID_ARG, NO_DEVICE, OOM, CUDA.
+ * spaqr_load_tuning: installs a table written by spaqr_autotune (path = NULL
+ * removes the table).  Errors: INVALID_ARG (unreadable or malformed file). */
+int spaqr_autotune(int precision, int max_m, int max_n, const char* path, double* seconds);
+int spaqr_load_tuning(const char* path);
+
 /* ----------------------------------------------------- batched dense kernels
  * The dense building blocks of the factorization, exposed for testing.  Each
  * takes `count` problems described by host arrays; A[i] are device pointers

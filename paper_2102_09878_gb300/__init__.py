@@ -14,7 +14,7 @@ from . import capi
 from .capi import SpaqrError
 
 __all__ = ["Analysis", "SpaQR", "SpaqrError", "dense_front_qr", "dense_front_qr_f32", "dense_qrcp", "dense_tc_gemm",
-           "solve_batch", "solve_normal_batch", "capi"]
+           "solve_batch", "solve_normal_batch", "autotune", "load_tuning", "capi"]
 
 
 def _stream_ptr(stream):
@@ -234,6 +234,20 @@ class SpaQR:
                 self._h = None
         except Exception:
             pass
+
+
+def autotune(precision: str = "mixed", max_m: int = 2048, max_n: int = 4096, path: str | None = None) -> float:
+    """Time the column-pivoted QR launch shapes per size class and install the
+    fastest for later factorizations of this process; returns seconds spent."""
+    secs = C.c_double()
+    capi.check(capi.load().spaqr_autotune(capi.PREC[precision], int(max_m), int(max_n),
+                                          path.encode() if path else None, C.byref(secs)))
+    return secs.value
+
+
+def load_tuning(path: str | None):
+    """Install a table written by autotune(path=...); None removes the table."""
+    capi.check(capi.load().spaqr_load_tuning(path.encode() if path else None))
 
 
 def _batch(fn, solvers, vecs, n_out, *extra):

@@ -137,6 +137,8 @@ SIGNATURES = {
         C.c_int,
         [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p],
     ),
+    "spaqr_autotune": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_char_p, C.POINTER(C.c_double)]),
+    "spaqr_load_tuning": (C.c_int, [C.c_char_p]),
     "spaqr_dense_qrcp": (
         C.c_int,
         [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,

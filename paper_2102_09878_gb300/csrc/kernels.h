@@ -141,6 +141,11 @@ inline int qrcp_warp_bytes(int m, int n, int elem) {
 }
 constexpr int kQrcpWarpCap = 24 << 10;  // per-warp region limit for the warp QRCP
 
+// Launch shape measured by the autotuner for matrices of this size class
+// (autotune.cu): 0 = not tuned, 1..16 = CTAs with shared-memory slabs, 32 = 16
+// CTAs over a global work copy.
+int qrcp_tuned_choice(int elem, int m, int n);
+
 inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, int elem, int limit,
                       std::vector<QrcpGroup>& out, std::vector<char>& needs_work) {
   const int nmat = (int)ms.size();
@@ -169,8 +174,10 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
   for (int i : rest) {
     int c = 1;
     while (c < 16 && qrcp_smem_bytes(ms[(size_t)i], (ns[(size_t)i] + c - 1) / c, elem, true) > limit) c *= 2;
+    const int tuned = qrcp_tuned_choice(elem, ms[(size_t)i], ns[(size_t)i]);
+    if (tuned > c && tuned <= 16) c = tuned;  // a larger cluster always still fits
     const int nl = (ns[(size_t)i] + c - 1) / c;
-    if (qrcp_smem_bytes(ms[(size_t)i], nl, elem, true) <= limit) {
+    if (tuned != 32 && qrcp_smem_bytes(ms[(size_t)i], nl, elem, true) <= limit) {
       cs[(size_t)i] = c;
       slab[(size_t)i] = 1;
     } else {
