@@ -349,8 +349,7 @@ class Factorizer {
     up_.reset();
     tm_.drain(h_.stats.t_kernel, h_.stats.n_kernel);
   }
-  int new_group(int owner, int rows, std::vector<int> sup) {
-    Group g;
+  void make_group(Group& g, int owner, int rows, std::vector<int>&& sup) const {
     g.owner = owner;
     g.rows = rows;
     g.ld = std::max(rows, 1);
@@ -363,9 +362,20 @@ class Factorizer {
     }
     g.width = w;
     g.alive = true;
+  }
+  int new_group(int owner, int rows, std::vector<int> sup) {
+    Group g;
+    make_group(g, owner, rows, std::move(sup));
     G_.push_back(std::move(g));
     live_.push_back((int)G_.size() - 1);
     return (int)G_.size() - 1;
+  }
+  // n new (empty) groups with consecutive ids, appended to the live list; returns the first id
+  int add_groups(size_t n) {
+    const int base = (int)G_.size();
+    G_.resize(G_.size() + n);
+    for (size_t i = 0; i < n; ++i) live_.push_back(base + (int)i);
+    return base;
   }
   // live group ids in ascending order (compacts the list)
   const std::vector<int>& live() {
@@ -698,29 +708,39 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
     for (int64_t c = b; c < e; ++c) std::sort(order.begin() + cnt[(size_t)c], order.begin() + cnt[(size_t)c + 1], sup_less);
   }, 256);
   lap("init: sort rows");
-  // groups
-  std::vector<int> ids;
+  // groups: runs of equal (owner, support) in the sorted order, built in parallel
   std::vector<int32_t> grp_of_row((size_t)M), rowpos((size_t)M);
-  int64_t i = 0;
-  while (i < M) {
-    int64_t j = i + 1;
-    const int64_t r0 = order[(size_t)i];
-    auto same = [&](int64_t a, int64_t b) {
-      if (owner[(size_t)a] != owner[(size_t)b]) return false;
-      const int64_t la = sptr[(size_t)a + 1] - sptr[(size_t)a], lb = sptr[(size_t)b + 1] - sptr[(size_t)b];
-      return la == lb && std::equal(&sups[(size_t)sptr[(size_t)a]], &sups[(size_t)sptr[(size_t)a]] + la,
-                                    &sups[(size_t)sptr[(size_t)b]]);
-    };
-    while (j < M && same(order[(size_t)j], r0)) ++j;
-    std::vector<int> sup(&sups[(size_t)sptr[(size_t)r0]], &sups[(size_t)sptr[(size_t)r0 + 1]]);
-    const int id = new_group(owner[(size_t)r0], (int)(j - i), sup);
-    ids.push_back(id);
-    for (int64_t t = i; t < j; ++t) {
-      grp_of_row[(size_t)order[(size_t)t]] = id;
-      rowpos[(size_t)order[(size_t)t]] = (int32_t)(t - i);
+  auto same = [&](int64_t a, int64_t b) {
+    if (owner[(size_t)a] != owner[(size_t)b]) return false;
+    const int64_t la = sptr[(size_t)a + 1] - sptr[(size_t)a], lb = sptr[(size_t)b + 1] - sptr[(size_t)b];
+    return la == lb && std::equal(&sups[(size_t)sptr[(size_t)a]], &sups[(size_t)sptr[(size_t)a]] + la,
+                                  &sups[(size_t)sptr[(size_t)b]]);
+  };
+  std::vector<char> starts_here((size_t)M, 0);
+  parallel_for(M, [&](int64_t b, int64_t e, int) {
+    for (int64_t t = b; t < e; ++t) starts_here[(size_t)t] = t == 0 || !same(order[(size_t)t], order[(size_t)t - 1]);
+  });
+  std::vector<int64_t> starts;
+  for (int64_t t = 0; t < M; ++t)
+    if (starts_here[(size_t)t]) starts.push_back(t);
+  starts.push_back(M);
+  const size_t ngroups = starts.size() - 1;
+  const int gbase = add_groups(ngroups);
+  std::vector<int> ids(ngroups);
+  parallel_for((int64_t)ngroups, [&](int64_t b, int64_t e, int) {
+    for (int64_t q = b; q < e; ++q) {
+      const int64_t i = starts[(size_t)q], j = starts[(size_t)q + 1];
+      const int64_t r0 = order[(size_t)i];
+      const int id = gbase + (int)q;
+      ids[(size_t)q] = id;
+      std::vector<int> sup(&sups[(size_t)sptr[(size_t)r0]], &sups[(size_t)sptr[(size_t)r0 + 1]]);
+      make_group(G_[(size_t)id], owner[(size_t)r0], (int)(j - i), std::move(sup));
+      for (int64_t t = i; t < j; ++t) {
+        grp_of_row[(size_t)order[(size_t)t]] = id;
+        rowpos[(size_t)order[(size_t)t]] = (int32_t)(t - i);
+      }
     }
-    i = j;
-  }
+  }, 1024);
   lap("init: groups");
   assign_buffer(ids, true);
   // scatter the scaled values into the group blocks
@@ -1026,6 +1046,7 @@ void Factorizer<T>::scale() {
   NT nt_f(this, "scale");
   phase_ = "scale";
   HT ht(ht_[4]);
+  Lap lap(this);
   std::vector<std::vector<int>> own, touch;
   index_groups(own, touch);
   p1_of_.assign(ccols_.size(), -1);
@@ -1065,6 +1086,7 @@ void Factorizer<T>::scale() {
     ws += (size_t)s.rp * s.n;
     si.push_back(std::move(s));
   }
+  lap("scale: info");
   if (si.empty()) return;
   T* W = static_cast<T*>(pool_.alloc(std::max<size_t>(ws, 1) * sizeof(T)));
   SPAQR_CUDA(cudaMemsetAsync(W, 0, std::max<size_t>(ws, 1) * sizeof(T), st_));
@@ -1090,8 +1112,10 @@ void Factorizer<T>::scale() {
     const double m = s.rp, c = s.c, t = s.n - s.c;
     h_.stats.flops_front += 2.0 * c * c * (m - c / 3.0) + (4.0 * m * c - 2.0 * c * c) * t;
   }
+  lap("scale: gather plan");
   copies(gat);
   front_qr(fr);
+  lap("scale: gather+front launch");
   // R_pp into the W store; new groups p1 (identity on p) and p2
   std::vector<CopyDesc<T>> rc, idn, cp;
   std::vector<int> ids;
@@ -1119,6 +1143,7 @@ void Factorizer<T>::scale() {
       ids.push_back(id2);
     }
   }
+  lap("scale: ops+groups");
   assign_buffer(ids, false);
   for (auto& s : si) {
     const T* F = W + s.foff;
@@ -1145,6 +1170,7 @@ void Factorizer<T>::scale() {
     auto* d = up_.put(idn);
     check(launch_identity<T>(d, (int)idn.size(), st_), "identity");
   }
+  lap("scale: p1/p2 copies");
   pool_.release(W);
   // X <- X R_pp^{-1} on every block column p of the other owners' rows
   std::vector<T*> Rof(ccols_.size(), nullptr);
@@ -1162,6 +1188,7 @@ void Factorizer<T>::scale() {
       maxr = std::max(maxr, g.rows);
     }
   }
+  lap("scale: trsm plan");
   if (checking_)
     for (auto& t : tr) {
       in_bounds(t.ptr, t.rows, t.c, t.ld, sizeof(T), "trsm X");
@@ -1227,6 +1254,7 @@ template <typename T>
 void Factorizer<T>::step2() {
   NT nt_f(this, "step2");
   phase_ = "step2";
+  Lap lap(this);
   HT ht(ht_[5]);
   std::vector<int> ps;
   for (size_t p = 0; p < ccols_.size(); ++p)
@@ -1258,6 +1286,7 @@ void Factorizer<T>::step2() {
     colour[(size_t)p] = c;
     ncol = std::max(ncol, c + 1);
   }
+  lap("step2: colouring");
   std::vector<std::vector<int>> own, touch;
   index_groups(own, touch);
   // one device rank slot per interface of this phase, read back with a single copy
@@ -1373,11 +1402,13 @@ void Factorizer<T>::step2() {
     }
     pool_.release(M);
   }
+  lap("step2: per-colour plan+launch");
   // ranks back; keep the ops that drop something
   std::vector<int> kall(std::max<size_t>(kdev_next, 1));
   sync();
   if (kdev_next) SPAQR_CUDA(cudaMemcpy(kall.data(), kdev_all, kdev_next * sizeof(int), cudaMemcpyDeviceToHost));
   std::vector<int> ks(recs.size());
+  lap("step2: readback");
   for (size_t i = 0; i < recs.size(); ++i) ks[i] = kall[(size_t)(h_.ops[recs[i].op].kdev - kdev_all)];
   for (T* w : work_all) pool_.release(w);
   std::vector<char> drop(h_.ops.size(), 0);
@@ -1439,62 +1470,72 @@ void Factorizer<T>::merge() {
     nslots[(size_t)P].insert(nslots[(size_t)P].end(), slots_[c].begin(), slots_[c].end());
   }
   lap("merge: clusters");
-  // groups whose column layout changes get a new block
+  // groups whose column layout changes get a new block (groups are independent:
+  // classified in parallel, moved ones listed in ascending id)
   std::vector<int> moved;
-  std::vector<Group> newg;
   std::vector<CopyDesc<T>> cps;
-  std::vector<int> ids;
-  const auto old_ccols = ccols_;
-  for (int id : live()) {
-    Group& g = G_[(size_t)id];
-    std::vector<int> nsup;
-    for (int c : g.sup) nsup.push_back(sc_->parent[(size_t)c]);
-    std::sort(nsup.begin(), nsup.end());
-    nsup.erase(std::unique(nsup.begin(), nsup.end()), nsup.end());
-    bool same = nsup.size() == g.sup.size();
-    for (size_t t = 0; same && t < g.sup.size(); ++t) {
-      const int c = g.sup[t], P = sc_->parent[(size_t)c];
-      if (nchild[(size_t)P] != 1) same = false;
-      // columns dropped by step 2 (block width larger than the cluster now)
-      const int wold = (t + 1 < g.sup.size() ? g.off[t + 1] : g.width) - g.off[t];
-      if (wold != ccols_[(size_t)c]) same = false;
-    }
-    g.owner = sc_->parent[(size_t)g.owner];
-    if (same) {
-      for (auto& c : g.sup) c = sc_->parent[(size_t)c];
-      continue;
-    }
-    moved.push_back(id);
+  {
+    const std::vector<int>& lv = live();
+    std::vector<char> mv(lv.size(), 0);
+    parallel_for((int64_t)lv.size(), [&](int64_t b, int64_t e, int) {
+      std::vector<int> nsup;
+      for (int64_t i = b; i < e; ++i) {
+        Group& g = G_[(size_t)lv[(size_t)i]];
+        nsup.clear();
+        for (int c : g.sup) nsup.push_back(sc_->parent[(size_t)c]);
+        std::sort(nsup.begin(), nsup.end());
+        nsup.erase(std::unique(nsup.begin(), nsup.end()), nsup.end());
+        bool same = nsup.size() == g.sup.size();
+        for (size_t t = 0; same && t < g.sup.size(); ++t) {
+          const int c = g.sup[t], P = sc_->parent[(size_t)c];
+          if (nchild[(size_t)P] != 1) same = false;
+          // columns dropped by step 2 (block width larger than the cluster now)
+          const int wold = (t + 1 < g.sup.size() ? g.off[t + 1] : g.width) - g.off[t];
+          if (wold != ccols_[(size_t)c]) same = false;
+        }
+        g.owner = sc_->parent[(size_t)g.owner];
+        if (same) {
+          for (auto& c : g.sup) c = sc_->parent[(size_t)c];
+          continue;
+        }
+        mv[(size_t)i] = 1;
+      }
+    }, 4096);
+    for (size_t i = 0; i < lv.size(); ++i)
+      if (mv[i]) moved.push_back(lv[i]);
   }
   lap("merge: classify groups");
-  // new blocks for moved groups (one buffer, zero-filled)
-  std::vector<int> tmpids;
+  // new blocks for moved groups (one buffer, zero-filled); the old layout is kept for the copies
   std::vector<std::vector<int>> oldsup(moved.size()), oldoff(moved.size());
   std::vector<T*> oldptr(moved.size());
   std::vector<int> oldld(moved.size()), oldbuf(moved.size());
-  for (size_t i = 0; i < moved.size(); ++i) {
-    Group& g = G_[(size_t)moved[i]];
-    oldsup[i] = g.sup;
-    oldoff[i] = g.off;
-    oldptr[i] = g.ptr;
-    oldld[i] = g.ld;
-    oldbuf[i] = g.buf;
-    std::vector<int> nsup;
-    for (int c : g.sup) nsup.push_back(sc_->parent[(size_t)c]);
-    std::sort(nsup.begin(), nsup.end());
-    nsup.erase(std::unique(nsup.begin(), nsup.end()), nsup.end());
-    g.sup = nsup;
-    g.off.assign(nsup.size(), 0);
-    int w = 0;
-    for (size_t t = 0; t < nsup.size(); ++t) {
-      g.off[t] = w;
-      w += nccols[(size_t)nsup[t]];
+  parallel_for((int64_t)moved.size(), [&](int64_t b, int64_t e, int) {
+    for (int64_t ii = b; ii < e; ++ii) {
+      const size_t i = (size_t)ii;
+      Group& g = G_[(size_t)moved[i]];
+      oldsup[i].swap(g.sup);
+      oldoff[i].swap(g.off);
+      oldptr[i] = g.ptr;
+      oldld[i] = g.ld;
+      oldbuf[i] = g.buf;
+      std::vector<int> nsup;
+      nsup.reserve(oldsup[i].size());
+      for (int c : oldsup[i]) nsup.push_back(sc_->parent[(size_t)c]);
+      std::sort(nsup.begin(), nsup.end());
+      nsup.erase(std::unique(nsup.begin(), nsup.end()), nsup.end());
+      g.off.assign(nsup.size(), 0);
+      int w = 0;
+      for (size_t t = 0; t < nsup.size(); ++t) {
+        g.off[t] = w;
+        w += nccols[(size_t)nsup[t]];
+      }
+      g.sup.swap(nsup);
+      g.width = w;
+      g.ld = std::max(g.rows, 1);
+      g.buf = -1;
+      g.ptr = nullptr;
     }
-    g.width = w;
-    g.ld = std::max(g.rows, 1);
-    g.buf = -1;
-    g.ptr = nullptr;
-  }
+  }, 4096);
   {
     size_t total = 0;
     for (int id : moved) total += (size_t)G_[(size_t)id].ld * G_[(size_t)id].width;
@@ -1517,17 +1558,33 @@ void Factorizer<T>::merge() {
       if (bufs_[(size_t)b].refs == 0) pool_.release(base);
     }
   }
-  for (size_t i = 0; i < moved.size(); ++i) {
-    Group& g = G_[(size_t)moved[i]];
-    for (size_t t = 0; t < oldsup[i].size(); ++t) {
-      const int c = oldsup[i][t];
-      const int P = sc_->parent[(size_t)c];
-      const int wc = ccols_[(size_t)c];
-      if (wc == 0 || g.rows == 0) continue;
-      const int dcol = col_off(g, P) + choff[(size_t)c];
-      cps.push_back(CopyDesc<T>{oldptr[i] + (size_t)oldoff[i][t] * oldld[i], g.ptr + (size_t)dcol * g.ld, nullptr,
-                                oldld[i], g.ld, g.rows, wc, 0, 0});
+  // relayout copies: counted, then filled in parallel in (group, old cluster) order
+  {
+    std::vector<size_t> first(moved.size() + 1, 0);
+    for (size_t i = 0; i < moved.size(); ++i) {
+      const Group& g = G_[(size_t)moved[i]];
+      size_t cnt = 0;
+      if (g.rows)
+        for (int c : oldsup[i]) cnt += ccols_[(size_t)c] ? 1 : 0;
+      first[i + 1] = first[i] + cnt;
     }
+    cps.resize(first.back());
+    parallel_for((int64_t)moved.size(), [&](int64_t b, int64_t e, int) {
+      for (int64_t ii = b; ii < e; ++ii) {
+        const size_t i = (size_t)ii;
+        const Group& g = G_[(size_t)moved[i]];
+        size_t q = first[i];
+        for (size_t t = 0; t < oldsup[i].size(); ++t) {
+          const int c = oldsup[i][t];
+          const int P = sc_->parent[(size_t)c];
+          const int wc = ccols_[(size_t)c];
+          if (wc == 0 || g.rows == 0) continue;
+          const int dcol = col_off(g, P) + choff[(size_t)c];
+          cps[q++] = CopyDesc<T>{oldptr[i] + (size_t)oldoff[i][t] * oldld[i], g.ptr + (size_t)dcol * g.ld, nullptr,
+                                 oldld[i], g.ld, g.rows, wc, 0, 0};
+        }
+      }
+    }, 4096);
   }
   lap("merge: relayout plan");
   copies(cps);
@@ -1548,10 +1605,6 @@ void Factorizer<T>::merge() {
   calive_.assign(nnew, 1);
   p1_of_.clear();
   p2_of_.clear();
-  (void)old_ccols;
-  (void)tmpids;
-  (void)newg;
-  (void)ids;
 }
 
 template <typename T>
