@@ -422,6 +422,21 @@ class Factorizer {
     g.buf = -1;
     g.ptr = nullptr;
   }
+  // kill a list of groups: buffer references serially, the layout vectors freed in parallel
+  void kill_many(const std::vector<int>& ids) {
+    for (int id : ids) {
+      Group& g = G_[(size_t)id];
+      drop_data(g);
+      g.alive = false;
+    }
+    parallel_for((int64_t)ids.size(), [&](int64_t b, int64_t e, int) {
+      for (int64_t i = b; i < e; ++i) {
+        Group& g = G_[(size_t)ids[(size_t)i]];
+        std::vector<int>().swap(g.sup);
+        std::vector<int>().swap(g.off);
+      }
+    }, 4096);
+  }
   void kill(int id) {
     Group& g = G_[(size_t)id];
     drop_data(g);
@@ -725,6 +740,7 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
     if (starts_here[(size_t)t]) starts.push_back(t);
   starts.push_back(M);
   const size_t ngroups = starts.size() - 1;
+  G_.reserve(3 * ngroups + 1024);  // group ids only grow; avoid moving every group on growth
   const int gbase = add_groups(ngroups);
   std::vector<int> ids(ngroups);
   parallel_for((int64_t)ngroups, [&](int64_t b, int64_t e, int) {
@@ -974,13 +990,17 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   struct Pending {
     int id;
     size_t front;
-    int r0, cnt;       // contiguous rows (returned)
+    int r0, cnt;            // contiguous rows (returned)
     std::vector<int> rows;  // explicit rows (extra)
+    int owner;
   };
+  // the new groups of every front in front order (ids assigned in that order),
+  // then their layouts in parallel: every new group of a front spans the
+  // front's remaining clusters
   std::vector<Pending> pend;
   for (size_t b = 0; b < batch.size(); ++b) {
     FrontInfo& f = fi[b];
-    std::vector<int> rest(f.cols.begin() + 1, f.cols.end());
+    const size_t nrest = f.cols.size() - 1;
     int pos = f.rs;
     const auto& fg = batch[b].second;
     size_t q = 0;
@@ -989,30 +1009,45 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
       const int o = G_[(size_t)fg[q]].owner;
       int cnt = 0;
       while (q < fg.size() && G_[(size_t)fg[q]].owner == o) cnt += G_[(size_t)fg[q++]].rows;
-      if (!rest.empty()) {
-        const int id = new_group(o, cnt, rest);
-        ids.push_back(id);
-        pend.push_back(Pending{id, b, pos, cnt, {}});
-      }
+      if (nrest) pend.push_back(Pending{-1, b, pos, cnt, {}, o});
       pos += cnt;
     }
     if (f.nextra) {
-      std::vector<std::vector<int>> by((size_t)rest.size());
+      std::vector<std::vector<int>> by(nrest);
       for (int i = 0; i < f.nextra; ++i) {
         const int t = dest[f.dest_off + (size_t)i];
-        if (t < 0 || t >= (int)rest.size())
+        if (t < 0 || t >= (int)nrest)
           throw Error(SPAQR_ERR_RANK_DEFICIENT, "non-finite values in a front at stage " + std::to_string(k_));
         by[(size_t)t].push_back(f.c + i);
       }
-      for (size_t t = 0; t < rest.size(); ++t) {
+      for (size_t t = 0; t < nrest; ++t) {
         if (by[t].empty()) continue;
-        const int id = new_group(rest[t], (int)by[t].size(), rest);
-        ids.push_back(id);
-        pend.push_back(Pending{id, b, 0, (int)by[t].size(), by[t]});
+        const int cnt = (int)by[t].size();
+        pend.push_back(Pending{-1, b, 0, cnt, std::move(by[t]), f.cols[t + 1]});
       }
     }
-    for (int g : fg) kill(g);
-    calive_[(size_t)f.s] = 0;
+  }
+  {
+    const int base = add_groups(pend.size());
+    for (size_t i = 0; i < pend.size(); ++i) {
+      pend[i].id = base + (int)i;
+      ids.push_back(pend[i].id);
+    }
+    parallel_for((int64_t)pend.size(), [&](int64_t b, int64_t e, int) {
+      for (int64_t i = b; i < e; ++i) {
+        const Pending& pd = pend[(size_t)i];
+        const FrontInfo& f = fi[pd.front];
+        make_group(G_[(size_t)pd.id], pd.owner, pd.cnt, std::vector<int>(f.cols.begin() + 1, f.cols.end()));
+      }
+    }, 1024);
+  }
+  {
+    std::vector<int> dead;
+    for (size_t b = 0; b < batch.size(); ++b) {
+      dead.insert(dead.end(), batch[b].second.begin(), batch[b].second.end());
+      calive_[(size_t)fi[b].s] = 0;
+    }
+    kill_many(dead);
   }
   assign_buffer(ids, false);
   std::vector<CopyDesc<T>> sc;
@@ -1119,29 +1154,46 @@ void Factorizer<T>::scale() {
   // R_pp into the W store; new groups p1 (identity on p) and p2
   std::vector<CopyDesc<T>> rc, idn, cp;
   std::vector<int> ids;
-  for (auto& s : si) {
-    WOp op;
-    op.kind = 1;
-    op.stage = k_;
-    op.c = s.c;
-    op.slots = slots_[(size_t)s.p];
-    s.R = wstore((size_t)s.c * s.c);
-    op.R = s.R;
-    rc.push_back(CopyDesc<T>{W + s.foff, s.R, nullptr, s.rp, s.c, s.c, s.c, 0, 0});
-    h_.ops.push_back(std::move(op));
-    for (int g : own[(size_t)s.p]) kill(g);
-    std::vector<int> sup1(s.cols.begin(), s.cols.end());
-    std::sort(sup1.begin(), sup1.end());
-    const int id1 = new_group(s.p, s.c, sup1);
-    p1_of_[(size_t)s.p] = id1;
-    ids.push_back(id1);
-    std::vector<int> rest(s.cols.begin() + 1, s.cols.end());
-    if (s.rp > s.c && !rest.empty()) {
-      std::sort(rest.begin(), rest.end());
-      const int id2 = new_group(s.p, s.rp - s.c, rest);
-      p2_of_[(size_t)s.p] = id2;
-      ids.push_back(id2);
+  // serial: W store blocks, ops in order, kills and group ids; parallel: the group layouts
+  {
+    size_t ng = 0;
+    for (auto& s : si) ng += 1 + ((s.rp > s.c && s.cols.size() > 1) ? 1 : 0);
+    const int base = add_groups(ng);
+    int next = base;
+    std::vector<int> dead;
+    h_.ops.reserve(h_.ops.size() + si.size());
+    for (auto& s : si) {
+      WOp op;
+      op.kind = 1;
+      op.stage = k_;
+      op.c = s.c;
+      op.slots = slots_[(size_t)s.p];
+      s.R = wstore((size_t)s.c * s.c);
+      op.R = s.R;
+      rc.push_back(CopyDesc<T>{W + s.foff, s.R, nullptr, s.rp, s.c, s.c, s.c, 0, 0});
+      h_.ops.push_back(std::move(op));
+      dead.insert(dead.end(), own[(size_t)s.p].begin(), own[(size_t)s.p].end());
+      p1_of_[(size_t)s.p] = next;
+      ids.push_back(next++);
+      if (s.rp > s.c && s.cols.size() > 1) {
+        p2_of_[(size_t)s.p] = next;
+        ids.push_back(next++);
+      }
     }
+    kill_many(dead);
+    parallel_for((int64_t)si.size(), [&](int64_t b, int64_t e, int) {
+      for (int64_t q = b; q < e; ++q) {
+        const SInfo& s = si[(size_t)q];
+        std::vector<int> sup1(s.cols.begin(), s.cols.end());
+        std::sort(sup1.begin(), sup1.end());
+        make_group(G_[(size_t)p1_of_[(size_t)s.p]], s.p, s.c, std::move(sup1));
+        if (p2_of_[(size_t)s.p] >= 0) {
+          std::vector<int> rest(s.cols.begin() + 1, s.cols.end());
+          std::sort(rest.begin(), rest.end());
+          make_group(G_[(size_t)p2_of_[(size_t)s.p]], s.p, s.rp - s.c, std::move(rest));
+        }
+      }
+    }, 1024);
   }
   lap("scale: ops+groups");
   assign_buffer(ids, false);
