@@ -78,13 +78,16 @@ typedef struct {
                       the touched clusters of the deepest nested-dissection node, which keeps every
                       row on one root-to-leaf chain (disjoint subtrees stay disjoint, Section 2.5.2);
                       SPAQR_ROWS_ANY = every touched cluster */
+  int apply_persistent; /* 1: each W^{-1} / W^{-T} apply is one cooperative persistent launch over all
+                           stored operations (bounded grid barriers between dependent segments);
+                           0 (default): one launch per segment and operation form, graph-captured */
 } spaqr_options;
 
 #define SPAQR_ROWS_TREE 0
 #define SPAQR_ROWS_ANY 1
 
 /* Fill *opt with the defaults: eps 1e-4, skip 2, FP64, spaqr mode, tol 1e-10,
- * maxit 500, graphs on, quiet, default stream, tree row rule. */
+ * maxit 500, graphs on, quiet, default stream, tree row rule, per-segment apply. */
 void spaqr_default_options(spaqr_options* opt);
 
 /* ---------------------------------------------------------------- analysis

@@ -73,7 +73,7 @@ class SpaQR:
 
     def __init__(self, A, analysis: Analysis, eps: float = 1e-4, skip: int = 2, precision: str = "fp64",
                  mode: str = "spaqr", tol: float = 1e-10, maxit: int = 500, use_graphs: bool = True,
-                 verbose: bool = False, stream=None, rows: str = "tree"):
+                 verbose: bool = False, stream=None, rows: str = "tree", persistent_apply: bool = False):
         lib = capi.load()
         self.m, self.n = int(A.m), int(A.n)
         self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int64)
@@ -92,6 +92,7 @@ class SpaQR:
         o.verbose = 1 if verbose else 0
         o.stream = _stream_ptr(stream)
         o.row_rule = capi.ROWS[rows]
+        o.apply_persistent = 1 if persistent_apply else 0
         self.precision = precision
         self.options = o
         h = C.c_void_p()

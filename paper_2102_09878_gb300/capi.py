@@ -64,6 +64,7 @@ class Options(C.Structure):
         ("verbose", C.c_int),
         ("stream", C.c_void_p),
         ("row_rule", C.c_int),
+        ("apply_persistent", C.c_int),
     ]
 
 

@@ -187,6 +187,7 @@ void spaqr_default_options(spaqr_options* o) {
   o->verbose = 0;
   o->stream = nullptr;
   o->row_rule = SPAQR_ROWS_TREE;
+  o->apply_persistent = 0;
 }
 
 const char* spaqr_last_error(void) { return g_last_error.c_str(); }

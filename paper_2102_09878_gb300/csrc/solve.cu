@@ -84,12 +84,9 @@ __device__ __forceinline__ TA wsum(TA v) {
 
 // ------------------------------------------- small ops: one warp per op
 // W^{-1}: z_s <- R_ss^{-1} (z_s - R_sn z_n) (kind 0), z_p <- R_pp^{-1} z_p (kind 1).
-// Lane i holds row i; R_ss is staged in the warp's shared region.
+// Lane i holds row i; R_ss is staged in the warp's shared region B (32 x 33).
 template <typename TW, typename TA>
-__global__ void __launch_bounds__(kT) r_inv_warp_kernel(const SmallOp<TW>* ops, int count, double* z) {
-  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
-  if (gw >= count) return;
-  const SmallOp<TW> op = ops[gw];
+__device__ __forceinline__ void r_inv_warp_op(const SmallOp<TW>& op, double* z, TW* B) {
   const int lane = threadIdx.x & 31, c = op.c, w = op.w;
   TA x = lane < c ? (TA)z[op.slots[lane]] : TA(0);
   if (w > 0) {
@@ -105,8 +102,6 @@ __global__ void __launch_bounds__(kT) r_inv_warp_kernel(const SmallOp<TW>* ops, 
     }
     x -= acc;
   }
-  extern __shared__ __align__(16) unsigned char wsm[];
-  TW* B = reinterpret_cast<TW*>(wsm) + (size_t)(threadIdx.x >> 5) * (32 * 33);
   for (int q = 0; q < c; ++q)
     if (lane < c) B[lane * 33 + q] = op.R[lane + (int64_t)q * c];
   const TA rd = lane < c ? (TA)op.rdiag[lane] : TA(0);
@@ -117,19 +112,15 @@ __global__ void __launch_bounds__(kT) r_inv_warp_kernel(const SmallOp<TW>* ops, 
     if (lane < j) x -= (TA)B[lane * 33 + j] * yj;
   }
   if (lane < c) z[op.slots[lane]] = (double)x;
+  __syncwarp();
 }
 
 // W^{-T}: y = R_ss^{-T} z_s, z_s <- y, z_n -= R_sn^T y (kind 0); z_p <- R_pp^{-T} z_p (kind 1).
 // The R_sn^T y products run lane-per-column (y broadcast by shuffles).
 template <typename TW, typename TA>
-__global__ void __launch_bounds__(kT) r_invT_warp_kernel(const SmallOp<TW>* ops, int count, double* z) {
-  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
-  if (gw >= count) return;
-  const SmallOp<TW> op = ops[gw];
+__device__ __forceinline__ void r_invT_warp_op(const SmallOp<TW>& op, double* z, TW* B) {
   const int lane = threadIdx.x & 31, c = op.c, w = op.w;
   TA x = lane < c ? (TA)z[op.slots[lane]] : TA(0);
-  extern __shared__ __align__(16) unsigned char wsm[];
-  TW* B = reinterpret_cast<TW*>(wsm) + (size_t)(threadIdx.x >> 5) * (32 * 33);
   for (int q = 0; q < c; ++q)
     if (lane < c) B[lane * 33 + q] = op.R[lane + (int64_t)q * c];
   const TA rd = lane < c ? (TA)op.rdiag[lane] : TA(0);
@@ -150,14 +141,12 @@ __global__ void __launch_bounds__(kT) r_invT_warp_kernel(const SmallOp<TW>* ops,
       if (j < w) atomicAdd(&z[op.nslots[j]], -(double)acc);
     }
   }
+  __syncwarp();
 }
 
 // W^{-1}: z_p <- Q_pp z_p = H_1 ... H_k z_p;  W^{-T}: z_p <- Q_pp^T z_p.
 template <typename TW, typename TA>
-__global__ void __launch_bounds__(kT) q_warp_kernel(const SmallOp<TW>* ops, int count, double* z, int transpose) {
-  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
-  if (gw >= count) return;
-  const SmallOp<TW> op = ops[gw];
+__device__ __forceinline__ void q_warp_op(const SmallOp<TW>& op, double* z, int transpose) {
   const int lane = threadIdx.x & 31, c = op.c, k = op.k;
   TA x = lane < c ? (TA)z[op.slots[lane]] : TA(0);
   for (int t = 0; t < k; ++t) {
@@ -169,21 +158,41 @@ __global__ void __launch_bounds__(kT) q_warp_kernel(const SmallOp<TW>* ops, int 
   if (lane < c) z[op.slots[lane]] = (double)x;
 }
 
-// ------------------------------------------- dense ops: tiled GEMVs
-// W^{-1} partials: part[poff_f + ct c + i] = sum over the tile's columns j of G[i, j] u_j,
-// u = [z_s; z_n].  Thread (row, column group); a warp reads 32 consecutive rows of a column.
 template <typename TW, typename TA>
-__global__ void __launch_bounds__(kT) dense_fwd_kernel(const DenseOp<TW>* dops, const int4* tiles, const double* z,
-                                                       TA* part) {
-  const int4 tl = tiles[blockIdx.x];
+__global__ void __launch_bounds__(kT) r_inv_warp_kernel(const SmallOp<TW>* ops, int count, double* z) {
+  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
+  if (gw >= count) return;
+  extern __shared__ __align__(16) unsigned char wsm[];
+  r_inv_warp_op<TW, TA>(ops[gw], z, reinterpret_cast<TW*>(wsm) + (size_t)(threadIdx.x >> 5) * (32 * 33));
+}
+
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) r_invT_warp_kernel(const SmallOp<TW>* ops, int count, double* z) {
+  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
+  if (gw >= count) return;
+  extern __shared__ __align__(16) unsigned char wsm[];
+  r_invT_warp_op<TW, TA>(ops[gw], z, reinterpret_cast<TW*>(wsm) + (size_t)(threadIdx.x >> 5) * (32 * 33));
+}
+
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) q_warp_kernel(const SmallOp<TW>* ops, int count, double* z, int transpose) {
+  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
+  if (gw >= count) return;
+  q_warp_op<TW, TA>(ops[gw], z, transpose);
+}
+
+// ------------------------------------------- dense ops: tiled GEMVs
+// W^{-1} partials of one tile: part[poff_f + ct c + i] = sum over the tile's
+// columns j of G[i, j] u_j, u = [z_s; z_n].  Thread (row, column group); a warp
+// reads 32 consecutive rows of a column.  u (256) and red (kT) in shared memory.
+template <typename TW, typename TA>
+__device__ void dense_fwd_tile(const DenseOp<TW>* dops, int4 tl, const double* z, TA* part, TA* u, TA* red) {
   const DenseOp<TW>* op = dops + tl.x;
   const int c = op->c, ncol = c + op->w, TR = op->tr, TC = tile_cols(TR);
   const int r0 = tl.y * TR, c0 = tl.z * TC;
   const int nr = min(TR, c - r0), nc = min(TC, ncol - c0);
   const int32_t* slots = op->slots;
   const int32_t* nslots = op->nslots;
-  __shared__ TA u[256];
-  __shared__ TA red[kT];
   for (int j = threadIdx.x; j < nc; j += kT) {
     const int jj = c0 + j;
     u[j] = (TA)z[jj < c ? slots[jj] : nslots[jj - c]];
@@ -205,20 +214,15 @@ __global__ void __launch_bounds__(kT) dense_fwd_kernel(const DenseOp<TW>* dops, 
   }
 }
 
-// W^{-T} partials: part[poff_t + rt (c + w) + j] = sum over the tile's rows i of G[i, j] v_i,
-// v = z_s.  The tile is staged in shared memory (coalesced), then thread (column, row group).
+// W^{-T} partials of one tile: part[poff_t + rt (c + w) + j] = sum over the
+// tile's rows i of G[i, j] v_i, v = z_s.  The tile is staged in shared memory
+// (s, TC x (TR + 1)), then thread (column, row group).
 template <typename TW, typename TA>
-__global__ void __launch_bounds__(kT) dense_T_kernel(const DenseOp<TW>* dops, const int4* tiles, const double* z,
-                                                     TA* part) {
-  const int4 tl = tiles[blockIdx.x];
+__device__ void dense_T_tile(const DenseOp<TW>* dops, int4 tl, const double* z, TA* part, TW* s, TA* v, TA* red) {
   const DenseOp<TW>* op = dops + tl.x;
   const int c = op->c, ncol = c + op->w, TR = op->tr, TC = tile_cols(TR);
   const int r0 = tl.y * TR, c0 = tl.z * TC;
   const int nr = min(TR, c - r0), nc = min(TC, ncol - c0);
-  extern __shared__ __align__(16) unsigned char dsm[];
-  TW* s = reinterpret_cast<TW*>(dsm);  // TC x (TR + 1)
-  __shared__ TA v[128];
-  __shared__ TA red[kT];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < nr; i += kT) v[i] = (TA)z[op->slots[r0 + i]];
   const TW* G = op->G + r0 + (int64_t)c0 * c;
@@ -243,9 +247,7 @@ __global__ void __launch_bounds__(kT) dense_T_kernel(const DenseOp<TW>* dops, co
 
 // z_s[i] <- sum over the column tiles of the partials (fixed order)
 template <typename TW, typename TA>
-__global__ void __launch_bounds__(kT) dense_fwd_reduce_kernel(const DenseOp<TW>* dops, const int2* items,
-                                                              const TA* part, double* z) {
-  const int2 it = items[blockIdx.x];
+__device__ __forceinline__ void dense_fwd_reduce(const DenseOp<TW>* dops, int2 it, const TA* part, double* z) {
   const DenseOp<TW>* op = dops + it.x;
   const int i = it.y + threadIdx.x, c = op->c;
   if (i >= c) return;
@@ -258,9 +260,7 @@ __global__ void __launch_bounds__(kT) dense_fwd_reduce_kernel(const DenseOp<TW>*
 
 // z_s[j] <- sum over the row tiles (j < c);  z_n[j - c] += sum (j >= c)
 template <typename TW, typename TA>
-__global__ void __launch_bounds__(kT) dense_T_reduce_kernel(const DenseOp<TW>* dops, const int2* items,
-                                                            const TA* part, double* z) {
-  const int2 it = items[blockIdx.x];
+__device__ __forceinline__ void dense_T_reduce(const DenseOp<TW>* dops, int2 it, const TA* part, double* z) {
   const DenseOp<TW>* op = dops + it.x;
   const int c = op->c, ncol = c + op->w, j = it.y + threadIdx.x;
   if (j >= ncol) return;
@@ -273,6 +273,121 @@ __global__ void __launch_bounds__(kT) dense_T_reduce_kernel(const DenseOp<TW>* d
     z[op->slots[j]] = (double)s;
   else
     atomicAdd(&z[op->nslots[j - c]], (double)s);
+}
+
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) dense_fwd_kernel(const DenseOp<TW>* dops, const int4* tiles, const double* z,
+                                                       TA* part) {
+  __shared__ TA u[256];
+  __shared__ TA red[kT];
+  dense_fwd_tile<TW, TA>(dops, tiles[blockIdx.x], z, part, u, red);
+}
+
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) dense_T_kernel(const DenseOp<TW>* dops, const int4* tiles, const double* z,
+                                                     TA* part) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ TA v[128];
+  __shared__ TA red[kT];
+  dense_T_tile<TW, TA>(dops, tiles[blockIdx.x], z, part, reinterpret_cast<TW*>(dsm), v, red);
+}
+
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) dense_fwd_reduce_kernel(const DenseOp<TW>* dops, const int2* items,
+                                                              const TA* part, double* z) {
+  dense_fwd_reduce<TW, TA>(dops, items[blockIdx.x], part, z);
+}
+
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) dense_T_reduce_kernel(const DenseOp<TW>* dops, const int2* items,
+                                                            const TA* part, double* z) {
+  dense_T_reduce<TW, TA>(dops, items[blockIdx.x], part, z);
+}
+
+// ------------------------------------------- the whole apply in one launch
+// Segments on the device; the persistent kernel below walks them in order.
+struct SegDev {
+  int kind, small0, nsmall, tile0, ntile, rf0, nrf, rt0, nrt;
+};
+
+constexpr long long kBarrierLimit = 1LL << 28;  // polls before a barrier gives up (seconds)
+
+// Software barrier of all CTAs of a cooperative launch (all co-resident):
+// bar[0] counts arrivals, bar[1] is the generation.  Bounded: a CTA that waits
+// too long records the error and proceeds.
+__device__ __forceinline__ void grid_sync(unsigned* bar, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (++it > kBarrierLimit) {
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// W^{-1} (transpose = 0) or W^{-T} in one cooperative launch: per segment the
+// small ops (one warp each over all warps of the grid) and the dense tiles
+// (one CTA each), a grid barrier, the ordered reductions, a grid barrier.
+template <typename TW, typename TA>
+__global__ void __launch_bounds__(kT) apply_persistent_kernel(const SegDev* segs, int nseg, const SmallOp<TW>* small,
+                                                              const DenseOp<TW>* dense, const int4* tiles,
+                                                              const int2* red, TA* part, double* z, int transpose,
+                                                              unsigned* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  __shared__ TA s_u[256];
+  __shared__ TA s_red[kT];
+  __shared__ TA s_v[128];
+  TW* B = reinterpret_cast<TW*>(psm) + (size_t)(threadIdx.x >> 5) * (32 * 33);
+  TW* stage = reinterpret_cast<TW*>(psm);
+  const int gw = (int)((blockIdx.x * (unsigned)kT + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * (unsigned)kT) >> 5);
+  for (int t = 0; t < nseg; ++t) {
+    const SegDev s = segs[transpose ? t : nseg - 1 - t];
+    const SmallOp<TW>* ops = small + s.small0;
+    for (int o = gw; o < s.nsmall; o += nw) {
+      const SmallOp<TW> op = ops[o];
+      if (s.kind == 2)
+        q_warp_op<TW, TA>(op, z, transpose);
+      else if (transpose)
+        r_invT_warp_op<TW, TA>(op, z, B);
+      else
+        r_inv_warp_op<TW, TA>(op, z, B);
+    }
+    if (s.ntile) {
+      __syncthreads();  // the warps' shared regions are free before a tile stages into them
+      for (int q = blockIdx.x; q < s.ntile; q += gridDim.x) {
+        const int4 tl = tiles[s.tile0 + q];
+        if (transpose)
+          dense_T_tile<TW, TA>(dense, tl, z, part, stage, s_v, s_red);
+        else
+          dense_fwd_tile<TW, TA>(dense, tl, z, part, s_u, s_red);
+        __syncthreads();
+      }
+      grid_sync(bar, err);
+      const int nred = transpose ? s.nrt : s.nrf, r0 = transpose ? s.rt0 : s.rf0;
+      for (int q = blockIdx.x; q < nred; q += gridDim.x) {
+        if (transpose)
+          dense_T_reduce<TW, TA>(dense, red[r0 + q], part, z);
+        else
+          dense_fwd_reduce<TW, TA>(dense, red[r0 + q], part, z);
+      }
+    }
+    grid_sync(bar, err);
+  }
 }
 
 // Forms column j of every dense operator in FP64 (one warp per column, work
@@ -497,6 +612,11 @@ struct ApplyPlan {
   void* d_dpart = nullptr;  // partial sums of the dense GEMVs (TA), sized for the largest segment
   std::vector<Segment> segs;  // factorization order
   int64_t launches = 0;       // kernel launches of one W^{-1} (equal for W^{-T})
+  SegDev* d_segs = nullptr;      // the segments for the persistent apply
+  unsigned* d_bar = nullptr;     // its grid barrier (count, generation)
+  int* d_err = nullptr;          // set when a grid barrier gave up
+  int pgrid = 0;                 // CTAs of the persistent launch (all co-resident); 0 = per-segment launches
+  size_t psmem = 0;
   cudaGraphExec_t graph = nullptr;      // one CGLS iteration
   cudaGraphExec_t graph_pcg = nullptr;  // one PCG iteration
   double* h_res = nullptr;              // pinned host copy of the residual norm
@@ -514,6 +634,27 @@ static void set_dyn_smem(K kernel) {
   cudaFuncAttributes fa;
   SPAQR_CUDA(cudaFuncGetAttributes(&fa, kernel));
   SPAQR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes));
+}
+
+// one cooperative launch of the persistent apply (W^{-1}: transpose = 0)
+template <typename TW, typename TA>
+static cudaError_t launch_persistent(Handle& h, double* z, int transpose) {
+  ApplyPlan& P = *h.plan;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)P.pgrid);
+  cfg.blockDim = dim3(kT);
+  cfg.dynamicSmemBytes = P.psmem;
+  cfg.stream = h.st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, apply_persistent_kernel<TW, TA>, static_cast<const SegDev*>(P.d_segs),
+                            (int)P.segs.size(), static_cast<const SmallOp<TW>*>(P.d_small),
+                            static_cast<const DenseOp<TW>*>(P.d_dense), static_cast<const int4*>(P.d_tiles),
+                            static_cast<const int2*>(P.d_red), static_cast<TA*>(P.d_dpart), z, transpose, P.d_bar,
+                            P.d_err);
 }
 
 template <typename TW, typename TA>
@@ -670,6 +811,56 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
   set_dyn_smem(r_inv_warp_kernel<TW, TA>);
   set_dyn_smem(r_invT_warp_kernel<TW, TA>);
   set_dyn_smem(dense_T_kernel<TW, TA>);
+  // persistent apply: segments on the device, a co-resident grid, and a probe
+  // (one launch and one captured launch on a zero vector) before it is used
+  P.pgrid = 0;
+  if (h.opt.apply_persistent && !segs.empty()) {
+    std::vector<SegDev> sd;
+    for (auto& g : segs) sd.push_back(SegDev{g.kind, g.small0, g.nsmall, g.tile0, g.ntile, g.rf0, g.nrf, g.rt0, g.nrt});
+    upload(sd, &P.d_segs);
+    SPAQR_CUDA(cudaMalloc(&P.d_bar, 2 * sizeof(unsigned)));
+    SPAQR_CUDA(cudaMemset(P.d_bar, 0, 2 * sizeof(unsigned)));
+    SPAQR_CUDA(cudaMalloc(&P.d_err, sizeof(int)));
+    SPAQR_CUDA(cudaMemset(P.d_err, 0, sizeof(int)));
+    P.psmem = std::max(kWarpSmem<TW>, (size_t)kStage * sizeof(TW));
+    set_dyn_smem(apply_persistent_kernel<TW, TA>);
+    int dev = 0, sms = 0, per = 0;
+    SPAQR_CUDA(cudaGetDevice(&dev));
+    SPAQR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SPAQR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_persistent_kernel<TW, TA>, kT, P.psmem));
+    if (per > 0) {
+      P.pgrid = sms * per;
+      double* zt = nullptr;
+      bool ok = cudaMalloc(&zt, (size_t)std::max<int64_t>(h.n, 1) * sizeof(double)) == cudaSuccess;
+      if (ok) ok = cudaMemsetAsync(zt, 0, (size_t)std::max<int64_t>(h.n, 1) * sizeof(double), h.st) == cudaSuccess;
+      if (ok) {
+        const cudaError_t e0 = launch_persistent<TW, TA>(h, zt, 0);
+        ok = e0 == cudaSuccess && cudaStreamSynchronize(h.st) == cudaSuccess;
+      }
+      if (ok) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        ok = cudaStreamBeginCapture(h.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          const cudaError_t e1 = launch_persistent<TW, TA>(h, zt, 1);
+          const bool launched = e1 == cudaSuccess;
+          ok = cudaStreamEndCapture(h.st, &g) == cudaSuccess && launched;
+        }
+        if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+        if (ok) ok = cudaGraphLaunch(ge, h.st) == cudaSuccess && cudaStreamSynchronize(h.st) == cudaSuccess;
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+      }
+      int err = 0;
+      if (ok) ok = cudaMemcpy(&err, P.d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && err == 0;
+      if (zt) cudaFree(zt);
+      if (!ok) {
+        cudaGetLastError();
+        P.pgrid = 0;  // per-segment launches
+      }
+    }
+  }
+  if (P.pgrid > 0) P.launches = 1;
 }
 
 void build_apply_plan(Handle& h) {
@@ -716,6 +907,9 @@ void free_apply_plan(Handle& h) {
   if (h.plan->graph) cudaGraphExecDestroy(h.plan->graph);
   if (h.plan->graph_pcg) cudaGraphExecDestroy(h.plan->graph_pcg);
   if (h.plan->h_res) cudaFreeHost(h.plan->h_res);
+  cudaFree(h.plan->d_segs);
+  cudaFree(h.plan->d_bar);
+  cudaFree(h.plan->d_err);
   cudaFree(h.plan->d_small);
   cudaFree(h.plan->d_dense);
   cudaFree(h.plan->d_idx);
@@ -759,6 +953,11 @@ static void run_segment(Handle& h, const Segment& s, double* z, int transpose) {
 template <typename TW, typename TA>
 static void apply_t(Handle& h, double* z, int transpose) {
   ApplyPlan& P = *h.plan;
+  if (P.pgrid > 0) {
+    const cudaError_t e = launch_persistent<TW, TA>(h, z, transpose);
+    SPAQR_CUDA(e);
+    return;
+  }
   const int nseg = (int)P.segs.size();
   for (int t = 0; t < nseg; ++t) run_segment<TW, TA>(h, P.segs[(size_t)(transpose ? t : nseg - 1 - t)], z, transpose);
   SPAQR_CUDA(cudaGetLastError());
@@ -1065,6 +1264,18 @@ void run_iterative(std::vector<IterSolve>& S) {
   }
   for (auto& s : S) s.finish();
   for (auto& s : S) SPAQR_CUDA(cudaStreamSynchronize(s.h->st));
+  for (auto& s : S) {
+    ApplyPlan& P = *s.h->plan;
+    int err = 0;
+    if (P.d_err) {
+      SPAQR_CUDA(cudaMemcpy(&err, P.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (err) {
+        SPAQR_CUDA(cudaMemset(P.d_err, 0, sizeof(int)));
+        SPAQR_CUDA(cudaMemset(P.d_bar, 0, 2 * sizeof(unsigned)));
+        throw Error(SPAQR_ERR_TIMEOUT, "persistent apply: a grid barrier wait timed out");
+      }
+    }
+  }
 }
 
 void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info) {

@@ -128,3 +128,26 @@ def test_device_solve_and_graphs_off(grid64):
     g2 = _gpu(grid64, 6, eps=1e-4, use_graphs=True)
     x2 = g2.solve(b).cpu().numpy()
     assert _rel(x1, x2) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_persistent_apply_matches_segment_launches(precision):
+    """W^{-1} z and W^{-T} z from the one-launch persistent apply (grid barriers
+    between segments) equal those of one launch per segment; same CGLS count."""
+    import torch
+
+    p = grid_problem(96, 80, 1, "c3", 3)
+    a = _gpu(p, 7, eps=1e-4, precision=precision, persistent_apply=True)
+    b = _gpu(p, 7, eps=1e-4, precision=precision, persistent_apply=False)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    rng = np.random.default_rng(1)
+    for transpose in (False, True):
+        z = rng.standard_normal(p.n)
+        za = torch.tensor(z, device="cuda")
+        zb = torch.tensor(z, device="cuda")
+        a.apply_Winv(za, transpose)
+        b.apply_Winv(zb, transpose)
+        assert _rel(za.cpu().numpy(), zb.cpu().numpy()) < tol
+    xa, xb = a.solve(p.b), b.solve(p.b)
+    assert a.last_info["iters"] == b.last_info["iters"]
+    assert _rel(xa, xb) < 1e-8
