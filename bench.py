@@ -341,7 +341,7 @@ def main():
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32-factor/f64-cgls",
         "data": "synthetic",
         "config": {"workload": args.workload, "grid": list(prob.dims), "n": prob.n, "m": prob.m, "depth": res["depth"],
-                   "eps": args.eps, "precision": args.precision, "weights": "10^U[-3,3]", "tol": 1e-10,
+                   "eps": args.eps, "precision": args.precision, "weights": {"u12": "U[1,2)", "c3": "10^U[-3,3]", "c2": "10^U[-2,2]"}[prob.law], "tol": 1e-10,
                    "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas{world}"},
         "e2e": res["e2e"], "gpu_launches": int(res["launches"]), "clocks": res["clocks"],
         "roofline": roofline(res, args.precision), "cpu_baseline": cpu,

@@ -82,14 +82,15 @@ float time_choice(int m, int n, int count, int choice, cudaStream_t st) {
   }
   QrcpDesc<T>* d = sc.get<QrcpDesc<T>>((size_t)count);
   SPAQR_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice, st));
-  if (qrcp_smem_bytes(m, nl, (int)sizeof(T), slab) > limit) return -1.f;
+  const int nb = slab ? kQrcpNB : qrcp_panel_depth(m, nl, (int)sizeof(T), limit);
+  if (slab ? qrcp_smem_bytes(m, nl, (int)sizeof(T), true) > limit : nb == 0) return -1.f;
   cudaEvent_t e0, e1;
   SPAQR_CUDA(cudaEventCreate(&e0));
   SPAQR_CUDA(cudaEventCreate(&e1));
   float best = -1.f;
   for (int rep = 0; rep < 3; ++rep) {
     SPAQR_CUDA(cudaEventRecord(e0, st));
-    SPAQR_CUDA(launch_qrcp<T>(d, count, 0.0, cs, nl, m, slab, st));
+    SPAQR_CUDA(launch_qrcp<T>(d, count, 0.0, cs, nl, m, slab, st, nb));
     SPAQR_CUDA(cudaEventRecord(e1, st));
     SPAQR_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;

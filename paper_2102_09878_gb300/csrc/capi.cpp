@@ -603,7 +603,7 @@ int spaqr_dense_qrcp(int count, double* const* A, const int* m, const int* n, co
       std::vector<spaqr::QrcpDesc<double>> part;
       for (int i : g.idx) part.push_back(qs[(size_t)i]);
       SPAQR_CUDA(cudaMemcpyAsync(d + off, part.data(), part.size() * sizeof(part[0]), cudaMemcpyHostToDevice, st));
-      SPAQR_CUDA(spaqr::launch_qrcp<double>(d + off, (int)part.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st));
+      SPAQR_CUDA(spaqr::launch_qrcp<double>(d + off, (int)part.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st, g.nb));
       off += part.size();
     }
     SPAQR_CUDA(cudaMemcpyAsync(rank, d_rank, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st));

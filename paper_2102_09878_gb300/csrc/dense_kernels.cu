@@ -933,11 +933,10 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
 // reflector is formed, and the row-i entries that the norm downdates need are
 // formed from the coefficients.  Reflector storage: the pivot columns of the
 // shared work copy, read by every CTA of the cluster.
-template <typename T>
+template <typename T, int NB>
 __global__ void __launch_bounds__(kThreads, 1) qrcp_delayed_kernel(const QrcpDesc<T>* descs, double eps, int nl_max,
                                                                 int m_max) {
   constexpr int KG = 8;
-  constexpr int NB = kQrcpNB;
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -1666,7 +1665,7 @@ static cudaError_t launch_cluster(void (*kernel)(const QrcpDesc<T>*, double, int
 
 template <typename T>
 cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int nl_max, int m_max, bool smem_slab,
-                        cudaStream_t st) {
+                        cudaStream_t st, int nb) {
   if (count <= 0) return cudaSuccess;
   if (cs == 0) {  // one warp per matrix; nl_max = per-warp bytes
     static bool init = false;
@@ -1678,14 +1677,34 @@ cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int
         d, count, eps, nl_max);
     return cudaGetLastError();
   }
-  const int smem = qrcp_smem_bytes(m_max, nl_max, (int)sizeof(T), smem_slab);
+  const int smem = qrcp_smem_bytes(m_max, nl_max, (int)sizeof(T), smem_slab, nb);
   const unsigned grid = (unsigned)(count * cs);
   if (smem_slab) {
     static bool init_s = false;
     return launch_cluster(qrcp_cluster_kernel<T, true, 8>, init_s, grid, cs, smem, st, d, eps, nl_max, m_max);
   }
-  static bool init_g = false;
-  return launch_cluster(qrcp_delayed_kernel<T>, init_g, grid, cs, smem, st, d, eps, nl_max, m_max);
+  switch (nb) {
+    case 16: {
+      static bool i16 = false;
+      return launch_cluster(qrcp_delayed_kernel<T, 16>, i16, grid, cs, smem, st, d, eps, nl_max, m_max);
+    }
+    case 8: {
+      static bool i8 = false;
+      return launch_cluster(qrcp_delayed_kernel<T, 8>, i8, grid, cs, smem, st, d, eps, nl_max, m_max);
+    }
+    case 4: {
+      static bool i4 = false;
+      return launch_cluster(qrcp_delayed_kernel<T, 4>, i4, grid, cs, smem, st, d, eps, nl_max, m_max);
+    }
+    case 2: {
+      static bool i2 = false;
+      return launch_cluster(qrcp_delayed_kernel<T, 2>, i2, grid, cs, smem, st, d, eps, nl_max, m_max);
+    }
+    default: {
+      static bool i1 = false;
+      return launch_cluster(qrcp_delayed_kernel<T, 1>, i1, grid, cs, smem, st, d, eps, nl_max, m_max);
+    }
+  }
 }
 
 template <typename T>
@@ -1855,7 +1874,7 @@ cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std
   template cudaError_t launch_front_trailing<T>(const FrontDesc<T>*, int, int, int, const T*, int,       \
                                                 cudaStream_t);                                           \
   template cudaError_t launch_front_finish<T>(const FrontDesc<T>*, int, int, cudaStream_t);                   \
-  template cudaError_t launch_qrcp<T>(const QrcpDesc<T>*, int, double, int, int, int, bool, cudaStream_t); \
+  template cudaError_t launch_qrcp<T>(const QrcpDesc<T>*, int, double, int, int, int, bool, cudaStream_t, int); \
   template cudaError_t launch_refl<T>(const ReflDesc<T>*, const int2*, int, cudaStream_t);               \
   template cudaError_t launch_trsm<T>(const TrsmDesc<T>*, const int2*, int, cudaStream_t);               \
   template cudaError_t launch_argmax<T>(const ArgmaxDesc<T>*, const int2*, int, cudaStream_t);

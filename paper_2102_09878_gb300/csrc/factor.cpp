@@ -585,7 +585,7 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
   tm_.begin(st_, 2);
   for (size_t t = 0; t < groups.size(); ++t) {
     const auto& g = groups[t];
-    check(launch_qrcp<T>(dg[t], (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st_), "qrcp");
+    check(launch_qrcp<T>(dg[t], (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st_, g.nb), "qrcp");
   }
   tm_.end(st_);
 }

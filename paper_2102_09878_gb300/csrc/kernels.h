@@ -12,6 +12,10 @@ namespace spaqr {
 // One 2D block copy dst[r + c*dld] = src[row(r) + c*sld], row(r) = r or
 // rowidx[r]; src == nullptr writes zeros.  Optionally transposed:
 // dst[c + r*dld] = src[row(r) + c*sld].
+// steps per panel of the delayed-update QRCP (slabs in global memory); wide
+// matrices whose coefficients would not fit use shallower panels (8, 4, 2, 1)
+constexpr int kQrcpNB = 16;
+
 template <typename T>
 struct CopyDesc {
   const T* src;
@@ -108,19 +112,24 @@ cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, cud
 // (m x n, ld m).
 template <typename T>
 cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int nl_max, int m_max, bool smem_slab,
-                        cudaStream_t st);
-// steps per panel of the delayed-update QRCP (slabs in global memory)
-constexpr int kQrcpNB = 16;
-// dynamic shared memory of one QRCP CTA (nl columns of m rows): the slab itself
-// (slab) or the delayed-update coefficients (nl x kQrcpNB)
-inline int qrcp_smem_bytes(int m, int nl, int elem, bool slab) {
+                        cudaStream_t st, int nb = kQrcpNB);
+// dynamic shared memory of one QRCP CTA (nl columns of m rows): with the slab
+// in shared memory (slab: two reflector buffers, taus, the slab), or the
+// delayed-update form (reflector, taus, nb coefficients per column)
+inline int qrcp_smem_bytes(int m, int nl, int elem, bool slab, int nb = kQrcpNB) {
   long long b = ((long long)nl * 28 + 15) / 16 * 16;  // nu, nuref, step_of, act, pos
-  b += (long long)(((m + 3) & ~1) * 3) * elem;         // two reflector buffers, taus
+  const long long vs = (long long)((m + 3) & ~1) * elem;
   if (slab)
-    b += (long long)m * nl * elem;
+    b += 3 * vs + (long long)m * nl * elem;
   else
-    b += (long long)nl * kQrcpNB * elem;
+    b += 2 * vs + (long long)nl * nb * elem;
   return (int)(b + 64);
+}
+// deepest panel (16, 8, 4, 2, 1) of the delayed-update QRCP that fits, 0 if none
+inline int qrcp_panel_depth(int m, int nl, int elem, int limit) {
+  for (int nb = kQrcpNB; nb >= 1; nb /= 2)
+    if (qrcp_smem_bytes(m, nl, elem, false, nb) <= limit) return nb;
+  return 0;
 }
 // Launch groups for a batch of QRCPs of shapes (m_i, n_i): each matrix takes
 // the smallest cluster size whose per-CTA column slab fits in shared memory,
@@ -129,6 +138,7 @@ inline int qrcp_smem_bytes(int m, int nl, int elem, bool slab) {
 struct QrcpGroup {
   int cs = 1;  // 0: one warp per matrix (nl_max then holds the per-warp bytes)
   bool slab = true;
+  int nb = kQrcpNB;  // panel depth of the delayed-update form (slab == false)
   int m_max = 0, nl_max = 0;
   std::vector<int> idx;
 };
@@ -184,7 +194,7 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
       cs[(size_t)i] = 16;
       slab[(size_t)i] = 0;
       needs_work[(size_t)i] = 1;
-      if (qrcp_smem_bytes(ms[(size_t)i], (ns[(size_t)i] + 15) / 16, elem, false) > limit) return false;
+      if (!qrcp_panel_depth(ms[(size_t)i], (ns[(size_t)i] + 15) / 16, elem, limit)) return false;
     }
     order.push_back(i);
   }
@@ -226,7 +236,10 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
     const int nl = (ns[(size_t)i] + cs[(size_t)i] - 1) / cs[(size_t)i];
     QrcpGroup* g = out.size() > first_cta_group ? &out.back() : nullptr;
     bool fits = g && g->cs == cs[(size_t)i] && g->slab == (bool)slab[(size_t)i] &&
-                qrcp_smem_bytes(std::max(g->m_max, ms[(size_t)i]), std::max(g->nl_max, nl), elem, g->slab) <= limit;
+                (g->slab ? qrcp_smem_bytes(std::max(g->m_max, ms[(size_t)i]), std::max(g->nl_max, nl), elem, true) <= limit
+                         : (qrcp_panel_depth(std::max(g->m_max, ms[(size_t)i]), std::max(g->nl_max, nl), elem, limit) ==
+                                qrcp_panel_depth(g->m_max, g->nl_max, elem, limit) &&
+                            qrcp_panel_depth(ms[(size_t)i], nl, elem, limit) == qrcp_panel_depth(g->m_max, g->nl_max, elem, limit)));
     // keep small problems away from large footprints (occupancy)
     if (fits && g->slab) {
       const int cur = qrcp_smem_bytes(g->m_max, g->nl_max, elem, true);
@@ -243,6 +256,8 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
     g->nl_max = std::max(g->nl_max, nl);
     g->idx.push_back(i);
   }
+  for (auto& g : out)
+    if (!g.slab && g.cs > 0) g.nb = qrcp_panel_depth(g.m_max, g.nl_max, elem, limit);
   return true;
 }
 

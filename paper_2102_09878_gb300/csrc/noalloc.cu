@@ -105,7 +105,7 @@ extern "C" int spaqr_dense_qrcp_static(int count, double* const* A, const int* m
   size_t pos = 0;
   for (auto& g : groups) {
     if (e != cudaSuccess) break;
-    e = spaqr::launch_qrcp<double>(d_desc + pos, (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st);
+    e = spaqr::launch_qrcp<double>(d_desc + pos, (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st, g.nb);
     pos += g.idx.size();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(rank, d_rank, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -163,3 +163,22 @@ def test_qrcp_delayed_update_global_path(m, n, eps):
             ref = np.zeros((k, n))
             ref[:, perm] = Xf[:k]
             assert _rel(rows[q], ref) < 1e-8
+
+
+def test_qrcp_wide_fp64_shallow_panels():
+    """A wide FP64 matrix whose delayed-update coefficients for 16-step panels
+    exceed shared memory: the planner takes shallower panels (same results)."""
+    import paper_2102_09878_gb300 as sq
+
+    rng = np.random.default_rng(21)
+    m, n, r = 2048, 20000, 120
+    A = (rng.standard_normal((m, r)) * np.logspace(0, -8, r)) @ rng.standard_normal((r, n))
+    ranks, rows, V, T = sq.dense_qrcp([A], 1e-5)
+    k, Xf, perm, Vo, To = dn.qrcp(A, 1e-5)
+    assert ranks[0] == k
+    good = np.abs(np.diag(Xf[:k, :k])) > 1e-6 * abs(Xf[0, 0])
+    j = k if good.all() else int(np.argmin(good))
+    assert _rel(V[0][:, :j], Vo[:, :j]) < 1e-9 and _rel(T[0][:j], To[:j]) < 1e-9
+    ref = np.zeros((k, n))
+    ref[:, perm] = Xf[:k]
+    assert _rel(rows[0], ref) < 1e-8
