@@ -965,6 +965,8 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_delayed_kernel(const QrcpDes
   __shared__ int red_i[kWarps];
   __shared__ int piv[NB];  // global column of each reflector of the panel
   __shared__ T gco[NB];    // v_t^T v_j for the panel's earlier reflectors t
+  __shared__ T gred[kWarps * NB];
+  __shared__ T s_den;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
     const int r = (int)(e % m), c = (int)(e / m);
@@ -1108,38 +1110,40 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_delayed_kernel(const QrcpDes
       }
       __syncthreads();
       T* cv = cbuf + (i - i0);  // cv[r - i], rows i..m-1
-      if (threadIdx.x < 32) {
-        double sig = 0.0;
-        for (int r = i + 1 + lane; r < m; r += 32) {
+      {
+        // squared norm below the diagonal: the whole CTA, then one thread forms the reflector
+        double sq = 0.0;
+        for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) {
           const double v = (double)cv[r - i];
-          sig += v * v;
+          sq += v * v;
         }
-        sig = warp_sum(sig);
-        const double alpha = (double)cv[0];
-        double beta, tau;
-        if (sig == 0.0) {
-          beta = alpha;
-          tau = 0.0;
-        } else {
-          const double nrm = sqrt(alpha * alpha + sig);
-          beta = alpha >= 0.0 ? -nrm : nrm;
-          tau = (beta - alpha) / beta;
-        }
-        const double ab = fabs(beta);
-        const double r11_here = (i == 0) ? ab : r11;
-        const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
-        if (!stop && sig != 0.0) {
-          const T den = (T)(alpha - beta);
-          for (int r = i + 1 + lane; r < m; r += 32) cv[r - i] = cv[r - i] / den;
-        } else {
-          for (int r = i + 1 + lane; r < m; r += 32) cv[r - i] = T(0);
-        }
-        __syncwarp();
-        if (lane == 0) {
+        sq = warp_sum(sq);
+        if (lane == 0) red_v[warp] = sq;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double sig = 0.0;
+          for (int w = 0; w < kWarps; ++w) sig += red_v[w];
+          const double alpha = (double)cv[0];
+          double beta, tau;
+          if (sig == 0.0) {
+            beta = alpha;
+            tau = 0.0;
+          } else {
+            const double nrm = sqrt(alpha * alpha + sig);
+            beta = alpha >= 0.0 ? -nrm : nrm;
+            tau = (beta - alpha) / beta;
+          }
+          const double ab = fabs(beta);
+          const double r11_here = (i == 0) ? ab : r11;
+          const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
           s_tau = (T)tau;
           s_beta = beta;
           s_stop = stop;
+          s_den = (!stop && sig != 0.0) ? (T)(alpha - beta) : T(0);
         }
+        __syncthreads();
+        const T den = s_den;
+        for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) cv[r - i] = den != T(0) ? cv[r - i] / den : T(0);
       }
       __syncthreads();
       if (!s_stop) {
@@ -1173,13 +1177,30 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_delayed_kernel(const QrcpDes
       pos[last] = q;
       s_nact = s_nact - 1;
     }
-    // g_t = v_t^T v_i (rows i..m-1) for the panel's earlier reflectors
-    for (int t = warp; t < jj; t += kWarps) {
-      const T* vt = W + (int64_t)piv[t] * m;
-      T acc = T(0);
-      for (int r = i + lane; r < m; r += 32) acc += __ldcg(vt + r) * cbuf[r - i0];
-      acc = warp_sum(acc);
-      if (lane == 0) gco[t] = acc;
+    // g_t = v_t^T v_i (rows i..m-1) for the panel's earlier reflectors: one pass
+    // over the rows for all t (independent loads), then a CTA reduction per t
+    if (jj > 0) {
+      T gacc[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) gacc[t] = T(0);
+      for (int r = i + threadIdx.x; r < m; r += kThreads) {
+        const T vr = cbuf[r - i0];
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+          if (t < jj) gacc[t] += __ldcg(W + r + (int64_t)piv[t] * m) * vr;
+      }
+#pragma unroll
+      for (int t = 0; t < NB; ++t) {
+        if (t >= jj) break;
+        const T v = warp_sum(gacc[t]);
+        if (lane == 0) gred[warp * NB + t] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < jj) {
+        T v = T(0);
+        for (int w = 0; w < kWarps; ++w) v += gred[w * NB + threadIdx.x];
+        gco[threadIdx.x] = v;
+      }
     }
     __syncthreads();
     // every unpivoted column: v^T a (stale a), its coefficient f, its row-i entry, the norm downdate
