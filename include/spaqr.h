@@ -126,6 +126,15 @@ int spaqr_analysis_stage_clusters(const spaqr_analysis* an, int k, int32_t* node
 typedef struct spaqr_handle spaqr_handle;
 int spaqr_factor(const spaqr_csr* A, const spaqr_analysis* an, const spaqr_options* opt, spaqr_handle** out);
 
+/* spaqr_factor_batch: spaqr_factor of count matrices with one analysis (for
+ * example many problems on one grid), run concurrently: every problem gets its
+ * own handle and non-blocking stream, and the host planning of different
+ * problems runs on different threads.  opt applies to all (its stream must be
+ * NULL).  out[i] receives the handle of A[i]; on an error no handle is created
+ * and the message names the problem.  Errors as spaqr_factor. */
+int spaqr_factor_batch(int count, const spaqr_csr* const* A, const spaqr_analysis* an, const spaqr_options* opt,
+                       spaqr_handle** out);
+
 typedef struct {
   int iters;         /* CGLS iterations taken */
   double rel_resid;  /* final ||A^T (A x - b)|| / ||A^T b|| */

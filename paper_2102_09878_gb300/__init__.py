@@ -14,7 +14,7 @@ from . import capi
 from .capi import SpaqrError
 
 __all__ = ["Analysis", "SpaQR", "SpaqrError", "dense_front_qr", "dense_front_qr_f32", "dense_qrcp", "dense_tc_gemm",
-           "solve_batch", "solve_normal_batch", "autotune", "load_tuning", "capi"]
+           "factor_batch", "solve_batch", "solve_normal_batch", "autotune", "load_tuning", "capi"]
 
 
 def _stream_ptr(stream):
@@ -65,6 +65,22 @@ class Analysis:
             pass
 
 
+def _options(eps, skip, precision, mode, tol, maxit, use_graphs, verbose, stream, rows, persistent_apply):
+    o = capi.default_options()
+    o.eps = float(eps)
+    o.skip = int(skip)
+    o.precision = capi.PREC[precision]
+    o.mode = capi.MODE[mode]
+    o.tol = float(tol)
+    o.maxit = int(maxit)
+    o.use_graphs = 1 if use_graphs else 0
+    o.verbose = 1 if verbose else 0
+    o.stream = _stream_ptr(stream)
+    o.row_rule = capi.ROWS[rows]
+    o.apply_persistent = 1 if persistent_apply else 0
+    return o
+
+
 class SpaQR:
     """spaQR factorization of A (CSR arrays on the host) and its CGLS solve.
 
@@ -73,32 +89,30 @@ class SpaQR:
 
     def __init__(self, A, analysis: Analysis, eps: float = 1e-4, skip: int = 2, precision: str = "fp64",
                  mode: str = "spaqr", tol: float = 1e-10, maxit: int = 500, use_graphs: bool = True,
-                 verbose: bool = False, stream=None, rows: str = "tree", persistent_apply: bool = False):
+                 verbose: bool = False, stream=None, rows: str = "tree", persistent_apply: bool = False,
+                 _handle=None):
         lib = capi.load()
+        self._keep_csr(A)
+        o = _options(eps, skip, precision, mode, tol, maxit, use_graphs, verbose, stream, rows, persistent_apply)
+        self.precision = precision
+        self.options = o
+        if _handle is None:
+            csr = self._csr()
+            h = C.c_void_p()
+            capi.check(lib.spaqr_factor(C.byref(csr), analysis.handle, C.byref(o), C.byref(h)))
+            _handle = h
+        self._h = _handle
+        self._analysis = analysis
+
+    def _keep_csr(self, A):
         self.m, self.n = int(A.m), int(A.n)
         self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int64)
         self._colidx = np.ascontiguousarray(A.colidx, dtype=np.int32)
         self._vals = np.ascontiguousarray(A.vals, dtype=np.float64)
-        csr = capi.Csr(self.m, self.n, int(self._rowptr[-1]), capi.ptr(self._rowptr), capi.ptr(self._colidx),
-                       capi.ptr(self._vals))
-        o = capi.default_options()
-        o.eps = float(eps)
-        o.skip = int(skip)
-        o.precision = capi.PREC[precision]
-        o.mode = capi.MODE[mode]
-        o.tol = float(tol)
-        o.maxit = int(maxit)
-        o.use_graphs = 1 if use_graphs else 0
-        o.verbose = 1 if verbose else 0
-        o.stream = _stream_ptr(stream)
-        o.row_rule = capi.ROWS[rows]
-        o.apply_persistent = 1 if persistent_apply else 0
-        self.precision = precision
-        self.options = o
-        h = C.c_void_p()
-        capi.check(lib.spaqr_factor(C.byref(csr), analysis.handle, C.byref(o), C.byref(h)))
-        self._h = h
-        self._analysis = analysis
+
+    def _csr(self):
+        return capi.Csr(self.m, self.n, int(self._rowptr[-1]), capi.ptr(self._rowptr), capi.ptr(self._colidx),
+                        capi.ptr(self._vals))
 
     # ------------------------------------------------------------- solve
     def solve(self, b, check_convergence: bool = True):
@@ -269,6 +283,34 @@ def _batch(fn, solvers, vecs, n_out, *extra):
     op = (C.c_void_p * cnt)(*[capi.ptr(v) for v in outs])
     capi.check(getattr(lib, fn)(cnt, hs, ip, op, 1 if on_dev else 0, *extra, infos))
     return outs, [dict(iters=i.iters, rel=i.rel_resid, converged=bool(i.converged)) for i in infos]
+
+
+def factor_batch(problems, analysis: Analysis, **kw):
+    """Factor several matrices with one analysis concurrently (own handle and
+    stream each, host planning on several threads); returns SpaQR objects."""
+    lib = capi.load()
+    kw = dict(kw)
+    args = dict(eps=1e-4, skip=2, precision="fp64", mode="spaqr", tol=1e-10, maxit=500, use_graphs=True,
+                verbose=False, stream=None, rows="tree", persistent_apply=False)
+    args.update(kw)
+    o = _options(**args)
+    holders = []
+    for A in problems:
+        s = SpaQR.__new__(SpaQR)
+        s._keep_csr(A)
+        holders.append(s)
+    csrs = [s._csr() for s in holders]
+    arr = (C.c_void_p * len(csrs))(*[C.addressof(c) for c in csrs])
+    out = (C.c_void_p * len(csrs))()
+    capi.check(lib.spaqr_factor_batch(len(csrs), arr, analysis.handle, C.byref(o), out))
+    res = []
+    for s, A, hv in zip(holders, problems, out):
+        s.precision = args["precision"]
+        s.options = o
+        s._h = C.c_void_p(hv)
+        s._analysis = analysis
+        res.append(s)
+    return res
 
 
 def solve_batch(solvers, bs):

@@ -107,6 +107,7 @@ SIGNATURES = {
     "spaqr_analysis_stage_clusters": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spaqr_factor": (C.c_int, [C.POINTER(Csr), C.c_void_p, C.POINTER(Options), C.POINTER(C.c_void_p)]),
     "spaqr_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(SolveInfo)]),
+    "spaqr_factor_batch": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.POINTER(Options), C.c_void_p]),
     "spaqr_apply_Winv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "spaqr_apply_A": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "spaqr_solve_normal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(SolveInfo)]),

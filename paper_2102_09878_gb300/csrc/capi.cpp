@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -240,6 +241,55 @@ int spaqr_factor(const spaqr_csr* A, const spaqr_analysis* an, const spaqr_optio
     *out = out_h;
     return SPAQR_OK;
   });
+}
+
+int spaqr_factor_batch(int count, const spaqr_csr* const* A, const spaqr_analysis* an, const spaqr_options* opt,
+                       spaqr_handle** out) {
+  if (count < 0 || (count > 0 && (!A || !an || !out))) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  for (int i = 0; i < count; ++i)
+    if (!A[i]) return fail(SPAQR_ERR_INVALID_ARG, "null matrix");
+  if (opt && opt->stream) return fail(SPAQR_ERR_INVALID_ARG, "a batch gives every handle its own stream");
+  if (count == 0) return SPAQR_OK;
+  if (int rc = need_device()) return rc;
+  spaqr_options o;
+  if (opt)
+    o = *opt;
+  else
+    spaqr_default_options(&o);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<std::unique_ptr<spaqr::Handle>> hs((size_t)count);
+  std::vector<int> codes((size_t)count, SPAQR_OK);
+  std::vector<std::string> msgs((size_t)count);
+  const int nt = std::max(1, std::min({count, (int)std::thread::hardware_concurrency(), 16}));
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      cudaSetDevice(dev);
+      for (int i = t; i < count; i += nt) {
+        try {
+          hs[(size_t)i] = build_handle(A[i], *an->an, o);
+        } catch (const spaqr::Error& e) {
+          codes[(size_t)i] = e.code;
+          msgs[(size_t)i] = e.what();
+        } catch (const std::bad_alloc&) {
+          codes[(size_t)i] = SPAQR_ERR_OOM;
+          msgs[(size_t)i] = "host allocation failed";
+        } catch (const std::exception& e) {
+          codes[(size_t)i] = SPAQR_ERR_CUDA;
+          msgs[(size_t)i] = e.what();
+        }
+      }
+    });
+  for (auto& t : th) t.join();
+  for (int i = 0; i < count; ++i)
+    if (codes[(size_t)i] != SPAQR_OK) return fail(codes[(size_t)i], "problem " + std::to_string(i) + ": " + msgs[(size_t)i]);
+  for (int i = 0; i < count; ++i) {
+    auto* h = new spaqr_handle();
+    h->h = std::move(hs[(size_t)i]);
+    out[i] = h;
+  }
+  return SPAQR_OK;
 }
 
 void spaqr_destroy(spaqr_handle* h) { delete h; }

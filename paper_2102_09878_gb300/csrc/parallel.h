@@ -25,7 +25,10 @@ class ThreadPool {
   template <typename F>
   void parallel_for(int64_t n, F&& f, int64_t min_chunk = 2048) {
     const int nw = workers();
-    if (n <= min_chunk || nw == 1) {
+    // one job at a time: a caller that finds the pool busy (another thread's
+    // job, or a nested call from inside a job) runs its loop inline
+    std::unique_lock<std::mutex> busy(busy_, std::try_to_lock);
+    if (n <= min_chunk || nw == 1 || !busy.owns_lock()) {
       f((int64_t)0, n, 0);
       return;
     }
@@ -39,7 +42,7 @@ class ThreadPool {
 
  private:
   std::vector<std::thread> threads_;
-  std::mutex mu_;
+  std::mutex mu_, busy_;
   std::condition_variable cv_, done_cv_;
   std::function<void(int)>* job_ = nullptr;
   int parts_ = 0;

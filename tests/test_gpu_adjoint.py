@@ -121,7 +121,7 @@ def _batch_check(nx, depth, count, sample, eps):
 
     probs = [grid_problem(nx, nx, 1, "c2", q) for q in range(count)]
     an = sq.Analysis(probs[0].dims, depth)
-    solvers = [sq.SpaQR(p, an, eps=eps, tol=1e-13) for p in probs]
+    solvers = sq.factor_batch(probs, an, eps=eps, tol=1e-13)  # concurrent factorizations
     vals = torch.tensor(np.stack([p.vals for p in probs]), device="cuda", requires_grad=True)
     bs = torch.tensor(np.stack([p.b for p in probs]), device="cuda", requires_grad=True)
     C = torch.tensor(np.random.default_rng(11).standard_normal((count, probs[0].n)), device="cuda")
@@ -166,3 +166,20 @@ def test_update_values_refactor():
     s.update_values(r.vals, refactor=True)
     x2 = s.solve(r.b)
     assert _rel(x2, adjoint.lstsq(r.to_scipy().tocsr(), r.b)) < 1e-8
+
+
+def test_factor_batch_matches_single_factorizations():
+    import paper_2102_09878_gb300 as sq
+
+    probs = [grid_problem(48, 40, 1, "c2", q) for q in range(6)]
+    an = sq.Analysis(probs[0].dims, 6)
+    batch = sq.factor_batch(probs, an, eps=1e-3)
+    for p, b in zip(probs, batch):
+        s = sq.SpaQR(p, an, eps=1e-3)
+        xb, xs = b.solve(p.b), s.solve(p.b)
+        assert b.last_info["iters"] == s.last_info["iters"]
+        assert _rel(xb, xs) < 1e-12
+        ob, os_ = b.ops(), s.ops()
+        assert len(ob) == len(os_)
+        for u, v in zip(ob, os_):
+            assert u["kind"] == v["kind"] and np.array_equal(u["slots"], v["slots"])
