@@ -236,13 +236,16 @@ def run_gpu(args, rank, world):
         compare = {"precision": args.compare, "seconds": c0.elapsed_time(c1) / 1e3 / args.steps, "iters": its,
                    "t_factor": sc["t_factor"], "t_solve": sc["t_solve"],
                    "kernel_seconds": {k: v for k, v in sc["t_kernel"].items()}}
-    return dict(secs=secs, prob=prob, depth=depth, stats=stats, kt=kt, kn=kn, flops_front=flops_front,
+    return dict(secs=secs, prob=prob, depth=depth, stats=stats, kt=kt, kn=kn, flops_front=flops_front, workload=args.workload,
                 flops_qrcp=flops_qrcp, bytes_qrcp=bytes_qrcp, compare=compare,
                 launches=launches, iters=iters, rel=rel, e2e=e2e, clocks=clocks, t_factor=t_factor,
                 t_solve=t_solve, t_analyze=stats["t_analyze"])
 
 
 HBM_PEAK = 6660.3  # GB/s, MEASURED_PEAKS.json hbm_gbs
+# DRAM bytes of all QRCP launches of one factorization, from one ncu capture
+# (profiles/qrcp_dram_grid2d_1024_mixed.md); kernels changed since -> remove
+QRCP_DRAM_BYTES = {("grid2d_1024", "mixed"): 1.809e9}
 
 
 def family_rooflines(res, precision):
@@ -255,12 +258,20 @@ def family_rooflines(res, precision):
                "FP32 lanes: 152 SMs x 128 x 2 flops x 2.07 GHz = 80.5 TFLOP/s (derived, of nominal)")
     out = {}
     if kt["qrcp"] > 0:
-        ach = res["bytes_qrcp"] / kt["qrcp"] / 1e9
-        out["qrcp"] = {"kernel": "column-pivoted QR (sparsification steps 1 and 2)", "bound": "hbm", "achieved": ach,
-                       "peak": HBM_PEAK, "unit": "GB/s", "frac": ach / HBM_PEAK, "traffic": None,
-                       "algorithmic": "one read of the unpivoted trailing block per pivot step + one read/write of "
-                                      "the matrix", "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                       "alu_view": {"achieved_tflops": res["flops_qrcp"] / kt["qrcp"] / 1e12, "peak_tflops": alu}}
+        steps = max(1, len(res["iters"]))
+        ach = res["flops_qrcp"] / kt["qrcp"] / 1e12
+        dram = QRCP_DRAM_BYTES.get((res["workload"], precision))
+        out["qrcp"] = {"kernel": "column-pivoted QR (sparsification steps 1 and 2)", "bound": "alu", "achieved": ach,
+                       "peak": alu, "unit": "TFLOP/s", "frac": ach / alu,
+                       "traffic": dram, "traffic_basis": "DRAM bytes of all QRCP launches of one factorization (ncu, "
+                                                         "profiles/qrcp_dram_grid2d_1024_mixed.md)" if dram else None,
+                       "peak_source": alu_src,
+                       "memory_view": {"algorithmic_bytes_per_step": res["bytes_qrcp"] / steps,
+                                       "algorithmic_gbs": res["bytes_qrcp"] / kt["qrcp"] / 1e9,
+                                       "dram_gbs": (dram * steps / kt["qrcp"] / 1e9) if dram else None,
+                                       "note": "per-step passes over the trailing block stay on chip (shared "
+                                               "memory or L2); the kernels are bound by the sequential pivot "
+                                               "chain"}}
     if kt["front_qr"] > 0:
         ach = res["flops_front"] / kt["front_qr"] / 1e12
         out["front_qr"] = {"kernel": "front QR (eliminate + scale)", "bound": "alu", "achieved": ach, "peak": alu,
