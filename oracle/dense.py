@@ -112,11 +112,17 @@ def qrcp(X: np.ndarray, eps: float):
     return k, X, perm, V[:, :k], taus[:k]
 
 
-def qrcp_rows(X: np.ndarray, eps: float):
-    """Rank k and the first k rows of Q^T X (columns in their original order)."""
+def qrcp_rows(X: np.ndarray, eps: float, sign_fix: bool = False):
+    """Rank k and the first k rows of Q^T X (columns in their original order).
+    sign_fix: flip each row i whose diagonal entry R_ii (column perm[i]) is
+    negative, so that the rows no longer depend on the reflector signs."""
     k, Xf, perm, _, _ = qrcp(X, eps)
     out = np.zeros((k, X.shape[1]))
     out[:, perm] = Xf[:k, :]
+    if sign_fix:
+        for i in range(k):
+            if Xf[i, i] < 0.0:
+                out[i, :] *= -1.0
     return k, out
 
 

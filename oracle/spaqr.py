@@ -37,7 +37,10 @@ R5  Same-level eliminations run in rounds: each round takes, in ascending
 R6  Scaling (Section 2.4) of every remaining interface p; p's rows become a
     group p1 (c_p rows, identity on p) and a group p2 (r_p - c_p rows, zero on
     p); every other row touching p gets X <- X R_pp^{-1}.
-R7  Step 1 (Section 2.5.1) replaces p2 by the first k' rows of Q'^T A_{p2 n}.
+R7  Step 1 (Section 2.5.1) replaces p2 by the first k' rows of Q'^T A_{p2 n},
+    each row signed so that its diagonal entry R_ii is >= 0 (the sign of a
+    row of R is a free choice of the orthogonal factor Q'; the same
+    convention as the front R factors, Section 2.3).
 R8  Step 2 (Section 2.5.2): M_p = [A_np^T  A_{p1 n}]; coarse = the first k
     pivoted directions, fine = the last c_p - k slots of p; nothing happens
     when k = c_p.  Interfaces are processed by a greedy colouring (ascending
@@ -348,7 +351,7 @@ class OracleSpaQR:
             g = self.groups[self.p2_of[p]]
             cols = sorted(g.blocks)
             X, offs = self._stack([g], cols)
-            kk, Rrows = dn.qrcp_rows(X, self.eps)
+            kk, Rrows = dn.qrcp_rows(X, self.eps, sign_fix=True)
             self.stats.step1.append((k, X.shape[0], X.shape[1], kk))
             if kk < g.rows:
                 if kk == 0:

@@ -202,3 +202,24 @@ def test_3d_small_exact_and_converges():
     o = OracleSpaQR(prob, 6, 1e-3).factor()
     x, info = o.solve(prob.b)
     assert info["converged"]
+
+
+def test_step1_rows_sign_fixed_are_unique():
+    """Step 1 keeps the first k rows of the pivoted R with R_ii >= 0: for a
+    full-rank tall block these rows are the Cholesky factor of the pivoted
+    normal matrix, so a QR of the block followed by the pivoted QR of its
+    triangle gives the same rows (the route the GPU takes for tall blocks)."""
+    import numpy as np
+
+    from oracle import dense as dn
+
+    rng = np.random.default_rng(17)
+    X = rng.standard_normal((60, 25)) * np.logspace(0, -3, 25)
+    k, rows = dn.qrcp_rows(X, 0.0, sign_fix=True)
+    _, Xf, perm, _, _ = dn.qrcp(X, 0.0)
+    L = np.linalg.cholesky(X[:, perm].T @ X[:, perm])
+    np.testing.assert_allclose(rows[:, perm], L.T, rtol=1e-9, atol=1e-12 * np.abs(L).max())
+    R0 = np.linalg.qr(X, mode="r")
+    k2, rows2 = dn.qrcp_rows(R0, 0.0, sign_fix=True)
+    assert k2 == k
+    np.testing.assert_allclose(rows2, rows, rtol=1e-9, atol=1e-12 * np.abs(rows).max())
