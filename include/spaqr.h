@@ -81,13 +81,17 @@ typedef struct {
   int apply_persistent; /* 1: each W^{-1} / W^{-T} apply is one cooperative persistent launch over all
                            stored operations (bounded grid barriers between dependent segments);
                            0 (default): one launch per segment and operation form, graph-captured */
+  int step1_qr_width; /* a step-1 block (Section 2.5.1) at least this wide and at least 1.1 times taller
+                         than wide is first reduced by a Householder QR to its square triangle, whose
+                         column-pivoted QR has the same pivots, rank and rows; 0 = never (default 1280) */
 } spaqr_options;
 
 #define SPAQR_ROWS_TREE 0
 #define SPAQR_ROWS_ANY 1
 
 /* Fill *opt with the defaults: eps 1e-4, skip 2, FP64, spaqr mode, tol 1e-10,
- * maxit 500, graphs on, quiet, default stream, tree row rule, per-segment apply. */
+ * maxit 500, graphs on, quiet, default stream, tree row rule, per-segment apply,
+ * step-1 QR from width 1280. */
 void spaqr_default_options(spaqr_options* opt);
 
 /* ---------------------------------------------------------------- analysis
@@ -213,14 +217,15 @@ typedef struct {
   int64_t n_fronts;  /* eliminated separator fronts */
   int64_t max_front_rows, max_front_cols;
   int64_t top_cols, top_rows; /* size of the root front (Section 4.3 top separator) */
-  double flops_front;  /* algorithmic flops of the front QRs (Golub-Van Loan counts) */
+  double flops_front;  /* algorithmic flops of the front QRs (Golub-Van Loan counts; includes the Householder
+                          QR that precedes the step-1 pivoted QR of a tall block) */
   double flops_sparsify; /* step-1 and step-2 column-pivoted QRs plus the step-2 two-sided application */
   double t_phase[6];   /* wall seconds: eliminate (incl. row reassignment), prep (column scaling, row
                           owners, initial blocks), scale, step1, step2, merge */
   int64_t launches;    /* kernels launched by the factorization */
   int64_t syncs;       /* device-to-host waits during the factorization */
   /* device time (CUDA events on the library stream) summed per kernel family:
-   * [0] block copies, [1] front QR (eliminate + scale), [2] column-pivoted QR,
+   * [0] block copies, [1] front QR (eliminate, scale, tall step-1 blocks), [2] column-pivoted QR,
    * [3] other factor kernels (argmax, trsm, reflector apply),
    * [4] W^{-1}/W^{-T} apply in the last solve, [5] SpMV + vector kernels in
    * the last solve.  Seconds. */

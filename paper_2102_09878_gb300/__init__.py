@@ -65,7 +65,8 @@ class Analysis:
             pass
 
 
-def _options(eps, skip, precision, mode, tol, maxit, use_graphs, verbose, stream, rows, persistent_apply):
+def _options(eps, skip, precision, mode, tol, maxit, use_graphs, verbose, stream, rows, persistent_apply,
+             step1_qr_width=1280):
     o = capi.default_options()
     o.eps = float(eps)
     o.skip = int(skip)
@@ -78,6 +79,7 @@ def _options(eps, skip, precision, mode, tol, maxit, use_graphs, verbose, stream
     o.stream = _stream_ptr(stream)
     o.row_rule = capi.ROWS[rows]
     o.apply_persistent = 1 if persistent_apply else 0
+    o.step1_qr_width = int(step1_qr_width)
     return o
 
 
@@ -90,10 +92,11 @@ class SpaQR:
     def __init__(self, A, analysis: Analysis, eps: float = 1e-4, skip: int = 2, precision: str = "fp64",
                  mode: str = "spaqr", tol: float = 1e-10, maxit: int = 500, use_graphs: bool = True,
                  verbose: bool = False, stream=None, rows: str = "tree", persistent_apply: bool = False,
-                 _handle=None):
+                 step1_qr_width: int = 1280, _handle=None):
         lib = capi.load()
         self._keep_csr(A)
-        o = _options(eps, skip, precision, mode, tol, maxit, use_graphs, verbose, stream, rows, persistent_apply)
+        o = _options(eps, skip, precision, mode, tol, maxit, use_graphs, verbose, stream, rows, persistent_apply,
+                     step1_qr_width)
         self.precision = precision
         self.options = o
         if _handle is None:
@@ -291,7 +294,7 @@ def factor_batch(problems, analysis: Analysis, **kw):
     lib = capi.load()
     kw = dict(kw)
     args = dict(eps=1e-4, skip=2, precision="fp64", mode="spaqr", tol=1e-10, maxit=500, use_graphs=True,
-                verbose=False, stream=None, rows="tree", persistent_apply=False)
+                verbose=False, stream=None, rows="tree", persistent_apply=False, step1_qr_width=1280)
     args.update(kw)
     o = _options(**args)
     holders = []

@@ -65,6 +65,7 @@ class Options(C.Structure):
         ("stream", C.c_void_p),
         ("row_rule", C.c_int),
         ("apply_persistent", C.c_int),
+        ("step1_qr_width", C.c_int),
     ]
 
 

@@ -189,6 +189,7 @@ void spaqr_default_options(spaqr_options* o) {
   o->stream = nullptr;
   o->row_rule = SPAQR_ROWS_TREE;
   o->apply_persistent = 0;
+  o->step1_qr_width = 1280;
 }
 
 const char* spaqr_last_error(void) { return g_last_error.c_str(); }

@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
     if (i == 0) r11 = fabs(s_beta);
     if (s_stop) break;
     const T tau = s_tau;
-    if (threadIdx.x == 0) taus[i] = tau;
+    if (threadIdx.x == 0) taus[i] = copysign(tau, (T)s_beta);  // tau >= 0; the sign is that of R_ii
     if (rank == owner) {
       // the pivot column becomes beta at row i and the reflector below
       const int pl = p - j0;
@@ -908,14 +908,16 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
       d.V[r + (int64_t)t * m] = r < t ? T(0) : (r == t ? T(1) : X[r + (int64_t)c * m]);
     }
     if (rank == 0)
-      for (int t = threadIdx.x; t < k; t += kThreads) d.tau[t] = taus[t];
+      for (int t = threadIdx.x; t < k; t += kThreads) d.tau[t] = fabs(taus[t]);
   }
   // the first k rows of Q^T A in the original column order, only when k < m
-  if (d.out && k < m) {
+  if (d.out && (k < m || (d.flags & kQrcpAlwaysOut))) {
+    const bool fix = d.flags & kQrcpSignFix;
     for (int64_t e = threadIdx.x; e < (int64_t)k * nloc; e += kThreads) {
       const int r = (int)(e % k), c = (int)(e / k);
       const int t = step_of[c];
-      d.out[r + (int64_t)(j0 + c) * d.ldo] = (t >= 0 && r > t) ? T(0) : X[r + (int64_t)c * m];
+      const T x = (t >= 0 && r > t) ? T(0) : X[r + (int64_t)c * m];
+      d.out[r + (int64_t)(j0 + c) * d.ldo] = fix && signbit(taus[r]) ? -x : x;
     }
   }
   cl.sync();  // no CTA leaves while another may still read its shared memory
@@ -1167,7 +1169,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_delayed_kernel(const QrcpDes
     if (s_stop) break;
     const T tau = s_tau;
     if (threadIdx.x == 0) {
-      taus[i] = tau;
+      taus[i] = copysign(tau, (T)s_beta);  // tau >= 0; the sign is that of R_ii
       piv[jj] = p;
     }
     if (rank == owner && threadIdx.x == 0) {
@@ -1312,13 +1314,15 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_delayed_kernel(const QrcpDes
       d.V[r + (int64_t)t * m] = r < t ? T(0) : (r == t ? T(1) : X[r + (int64_t)c * m]);
     }
     if (rank == 0)
-      for (int t = threadIdx.x; t < k; t += kThreads) d.tau[t] = taus[t];
+      for (int t = threadIdx.x; t < k; t += kThreads) d.tau[t] = fabs(taus[t]);
   }
-  if (d.out && k < m) {
+  if (d.out && (k < m || (d.flags & kQrcpAlwaysOut))) {
+    const bool fix = d.flags & kQrcpSignFix;
     for (int64_t e = threadIdx.x; e < (int64_t)k * nloc; e += kThreads) {
       const int r = (int)(e % k), c = (int)(e / k);
       const int t = step_of[c];
-      d.out[r + (int64_t)(j0 + c) * d.ldo] = (t >= 0 && r > t) ? T(0) : X[r + (int64_t)c * m];
+      const T x = (t >= 0 && r > t) ? T(0) : X[r + (int64_t)c * m];
+      d.out[r + (int64_t)(j0 + c) * d.ldo] = fix && signbit(taus[r]) ? -x : x;
     }
   }
   cl.sync();  // no CTA leaves while another may still read its shared memory
@@ -1408,7 +1412,7 @@ __global__ void __launch_bounds__(kThreads) qrcp_warp_kernel(const QrcpDesc<T>* 
     __syncwarp();
     if (lane == 0) {
       col[i] = (T)beta;
-      taus[i] = (T)tau;
+      taus[i] = copysign((T)tau, (T)beta);  // tau >= 0; the sign is that of R_ii
       step_of[p] = i;
     }
     __syncwarp();
@@ -1447,12 +1451,16 @@ __global__ void __launch_bounds__(kThreads) qrcp_warp_kernel(const QrcpDesc<T>* 
       for (int r = lane; r < m; r += 32)
         d.V[r + (int64_t)t * m] = r < t ? T(0) : (r == t ? T(1) : X[r + c * ld]);
     }
-    for (int t = lane; t < k; t += 32) d.tau[t] = taus[t];
+    for (int t = lane; t < k; t += 32) d.tau[t] = fabs(taus[t]);
   }
-  if (d.out && k < m) {
+  if (d.out && (k < m || (d.flags & kQrcpAlwaysOut))) {
+    const bool fix = d.flags & kQrcpSignFix;
     for (int c = 0; c < n; ++c) {
       const int t = step_of[c];
-      for (int r = lane; r < k; r += 32) d.out[r + (int64_t)c * d.ldo] = (t >= 0 && r > t) ? T(0) : X[r + c * ld];
+      for (int r = lane; r < k; r += 32) {
+        const T x = (t >= 0 && r > t) ? T(0) : X[r + c * ld];
+        d.out[r + (int64_t)c * d.ldo] = fix && signbit(taus[r]) ? -x : x;
+      }
     }
   }
 }

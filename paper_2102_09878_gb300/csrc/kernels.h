@@ -41,7 +41,12 @@ struct FrontDesc {
 // in shared memory or, for large matrices, in `work` (m x n, ld m).  Writes
 // rank[0]; if out != nullptr and k < m, the first k rows of Q^T A in the
 // original column order are written to rows 0..k-1 of out (ldo); if V != nullptr
-// the reflectors go to V (m x k, ld m, unit diagonal) and tau.
+// the reflectors go to V (m x k, ld m, unit diagonal) and tau.  flags:
+// kQrcpSignFix negates every written row i whose R_ii is negative (the rows
+// then no longer depend on the reflector signs); kQrcpAlwaysOut writes out also
+// when k == m (src is the triangular factor of a taller matrix).
+constexpr int kQrcpSignFix = 1;
+constexpr int kQrcpAlwaysOut = 2;
 template <typename T>
 struct QrcpDesc {
   const T* src;
@@ -51,6 +56,7 @@ struct QrcpDesc {
   T* tau;
   int* rank;
   int m, n, ld, ldo;
+  int flags = 0;
 };
 
 // Reflector application on a block X: mode 0: each row x^T <- x^T H_1..H_k

@@ -57,12 +57,14 @@ def test_direct_mode_fronts_match_oracle(grid64):
     _compare_ops(g.ops(), o.ops, 1e-11)
 
 
-@pytest.mark.parametrize("rows", ["tree", "maxnorm"])
-def test_full_pipeline_eps0_matches_oracle(grid64, rows):
+@pytest.mark.parametrize("rows,qrw", [("tree", 1280), ("maxnorm", 1280), ("tree", 32)])
+def test_full_pipeline_eps0_matches_oracle(grid64, rows, qrw):
+    """qrw = 32 routes every tall step-1 block of width >= 32 (here up to
+    2048 x 64) through the Householder QR before its pivoted QR."""
     import torch
 
     o = OracleSpaQR(grid64, 6, 0.0, rows=rows).factor()
-    g = _gpu(grid64, 6, eps=0.0, rows=rows)
+    g = _gpu(grid64, 6, eps=0.0, rows=rows, step1_qr_width=qrw)
     _compare_ops(g.ops(), o.ops, 1e-10)
     rng = np.random.default_rng(0)
     for _ in range(3):
@@ -131,23 +133,31 @@ def test_device_solve_and_graphs_off(grid64):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_persistent_apply_matches_segment_launches(precision):
-    """W^{-1} z and W^{-T} z from the one-launch persistent apply (grid barriers
-    between segments) equal those of one launch per segment; same CGLS count."""
-    import torch
-
-    p = grid_problem(96, 80, 1, "c3", 3)
-    a = _gpu(p, 7, eps=1e-4, precision=precision, persistent_apply=True)
-    b = _gpu(p, 7, eps=1e-4, precision=precision, persistent_apply=False)
-    tol = 1e-12 if precision == "fp64" else 1e-5
-    rng = np.random.default_rng(1)
-    for transpose in (False, True):
-        z = rng.standard_normal(p.n)
-        za = torch.tensor(z, device="cuda")
-        zb = torch.tensor(z, device="cuda")
-        a.apply_Winv(za, transpose)
-        b.apply_Winv(zb, transpose)
-        assert _rel(za.cpu().numpy(), zb.cpu().numpy()) < tol
-    xa, xb = a.solve(p.b), b.solve(p.b)
-    assert a.last_info["iters"] == b.last_info["iters"]
-    assert _rel(xa, xb) < 1e-8
+@pytest.mark.parametrize("dims,depth,law,eps", [((64, 64, 1), 6, "u12", 1e-4), ((12, 12, 12), 7, "u12", 1e-3)])
+def test_step1_qr_route_matches_direct_route(dims, depth, law, eps, precision):
+    """Section 2.5.1 step 1 through a Householder QR first (tall blocks of width
+    >= 32: up to 2048 x 64 in 2D, 648 x 108 in 3D) or directly.  FP64: same
+    ranks and the same stored factors (the pivoted QR of the triangle takes the
+    pivots of the block itself; both routes write the kept rows with R_ii >= 0).
+    FP32 factor: rank decisions at eps may differ in the last bits, so both
+    preconditioners are checked through the solve."""
+    prob = grid_problem(*dims, law=law, seed=3)
+    a = _gpu(prob, depth, eps=eps, precision=precision, step1_qr_width=32)
+    b = _gpu(prob, depth, eps=eps, precision=precision, step1_qr_width=0)
+    if precision == "fp64":
+        oa, ob = a.ops(), b.ops()
+        assert len(oa) == len(ob)
+        for x, y in zip(oa, ob):
+            assert x["kind"] == y["kind"] and x["stage"] == y["stage"]
+            np.testing.assert_array_equal(x["slots"], y["slots"])
+            if "nslots" in x:
+                np.testing.assert_array_equal(x["nslots"], y["nslots"])
+            for key in ("R", "Rn", "V", "taus"):
+                if key in x and np.size(x[key]):
+                    assert x[key].shape == y[key].shape, key
+                    assert _rel(x[key], y[key]) < 1e-9, (key, _rel(x[key], y[key]))
+    xa, xb = a.solve(prob.b), b.solve(prob.b)
+    A = prob.to_scipy()
+    for x in (xa, xb):
+        assert np.linalg.norm(A.T @ (A @ x - prob.b)) / np.linalg.norm(A.T @ prob.b) < 1e-10
+    assert abs(a.last_info["iters"] - b.last_info["iters"]) <= 1
