@@ -308,6 +308,27 @@ int spaqr_dense_tc_gemm(int m, int n, int k, const float* A, int lda, const floa
 int spaqr_dense_qrcp(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
                      double* const* V, double* const* taus, int* rank, void* stream);
 
+/* spaqr_dense_qrcp_route: spaqr_dense_qrcp with the launch form chosen by
+ * route: SPAQR_QRCP_CLUSTER = one thread-block cluster of at most 16 CTAs per
+ * matrix, column slabs in shared memory or, when they do not fit, a global
+ * work copy with delayed updates (what spaqr_dense_qrcp runs);
+ * SPAQR_QRCP_AUTO = as the factorization runs it: matrices whose slabs need
+ * more than 16 CTAs take a group of up to one CTA per SM, exchanging pivots and
+ * reflectors through global memory (cooperative launch; bounded waits end in
+ * SPAQR_ERR_TIMEOUT); SPAQR_QRCP_GRID = every matrix above the one-warp size
+ * takes such a CTA group (for testing the group form on small matrices).
+ * Results agree with spaqr_dense_qrcp up to rounding. */
+#define SPAQR_QRCP_AUTO 0
+#define SPAQR_QRCP_CLUSTER 1
+#define SPAQR_QRCP_GRID 2
+int spaqr_dense_qrcp_route(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
+                           double* const* V, double* const* taus, int* rank, int route, void* stream);
+/* spaqr_dense_qrcp_f32: spaqr_dense_qrcp_route in FP32 (the arithmetic of the
+ * mixed-precision factorization's pivoted QRs: FP32 data, squared column norms
+ * and reflector norms accumulated in FP64), exposed for testing. */
+int spaqr_dense_qrcp_f32(int count, float* const* A, const int* m, const int* n, const int* ld, double eps,
+                         float* const* V, float* const* taus, int* rank, int route, void* stream);
+
 /* spaqr_dense_qrcp_static: the same batched column-pivoted QR as
  * spaqr_dense_qrcp (same arguments, same results), for callers that cannot
  * allocate device memory: code that runs under a memory manager which owns

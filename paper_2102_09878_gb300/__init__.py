@@ -386,14 +386,17 @@ def dense_tc_gemm(A, B, Cm, stream=None):
     return _from_colmajor(c, m, n)
 
 
-def dense_qrcp(mats, eps: float, stream=None):
-    """Batched rank-revealing QR; returns (ranks, leading rows of Q^T A, V, taus)."""
+_QRCP_ROUTE = {"cluster": 1, "auto": 0, "grid": 2}
+
+
+def _dense_qrcp(mats, eps, stream, route, f32):
     import torch
 
     lib = capi.load()
-    ts = [_colmajor_cuda(A) for A in mats]
-    Vs = [torch.zeros(max(min(A.shape), 1) * max(A.shape[0], 1), dtype=torch.float64, device="cuda") for A in mats]
-    Ts = [torch.zeros(max(min(A.shape), 1), dtype=torch.float64, device="cuda") for A in mats]
+    dt = torch.float32 if f32 else torch.float64
+    ts = [(_colmajor_cuda32 if f32 else _colmajor_cuda)(A) for A in mats]
+    Vs = [torch.zeros(max(min(A.shape), 1) * max(A.shape[0], 1), dtype=dt, device="cuda") for A in mats]
+    Ts = [torch.zeros(max(min(A.shape), 1), dtype=dt, device="cuda") for A in mats]
     ptrs = (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
     vp = (C.c_void_p * len(ts))(*[t.data_ptr() for t in Vs])
     tp = (C.c_void_p * len(ts))(*[t.data_ptr() for t in Ts])
@@ -401,13 +404,28 @@ def dense_qrcp(mats, eps: float, stream=None):
     n = np.array([A.shape[1] for A in mats], np.int32)
     ld = np.maximum(m, 1).astype(np.int32)
     rank = np.zeros(len(ts), np.int32)
-    capi.check(lib.spaqr_dense_qrcp(len(ts), ptrs, capi.ptr(m), capi.ptr(n), capi.ptr(ld), float(eps), vp, tp,
-                                    capi.ptr(rank), _stream_ptr(stream)))
+    fn = lib.spaqr_dense_qrcp_f32 if f32 else lib.spaqr_dense_qrcp_route
+    capi.check(fn(len(ts), ptrs, capi.ptr(m), capi.ptr(n), capi.ptr(ld), float(eps), vp, tp, capi.ptr(rank),
+                  _QRCP_ROUTE[route], _stream_ptr(stream)))
     rows, Vout, Tout = [], [], []
     for i, A in enumerate(mats):
         k = int(rank[i])
-        out = _from_colmajor(ts[i], A.shape[0], A.shape[1])
-        rows.append(out[:k] if k < A.shape[0] else A.copy())
-        Vout.append(Vs[i].cpu().numpy()[: A.shape[0] * k].reshape(k, A.shape[0]).T.copy())
-        Tout.append(Ts[i].cpu().numpy()[:k].copy())
+        out = _from_colmajor(ts[i], A.shape[0], A.shape[1]).astype(np.float64)
+        rows.append(out[:k] if k < A.shape[0] else np.array(A, dtype=np.float64))
+        Vout.append(Vs[i].double().cpu().numpy()[: A.shape[0] * k].reshape(k, A.shape[0]).T.copy())
+        Tout.append(Ts[i].double().cpu().numpy()[:k].copy())
     return rank, rows, Vout, Tout
+
+
+def dense_qrcp(mats, eps: float, stream=None, route: str = "cluster"):
+    """Batched rank-revealing QR; returns (ranks, leading rows of Q^T A, V, taus).
+    route: "cluster" (clusters of <= 16 CTAs), "auto" (as the factorization:
+    CTA groups over global memory for matrices too large for a cluster) or
+    "grid" (CTA groups for every matrix above the one-warp size)."""
+    return _dense_qrcp(mats, eps, stream, route, False)
+
+
+def dense_qrcp_f32(mats, eps: float, stream=None, route: str = "cluster"):
+    """dense_qrcp in FP32 (the mixed-precision factorization's kernels); results
+    are returned in float64 arrays."""
+    return _dense_qrcp(mats, eps, stream, route, True)

@@ -147,6 +147,16 @@ SIGNATURES = {
         [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
          C.c_void_p],
     ),
+    "spaqr_dense_qrcp_route": (
+        C.c_int,
+        [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+         C.c_int, C.c_void_p],
+    ),
+    "spaqr_dense_qrcp_f32": (
+        C.c_int,
+        [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+         C.c_int, C.c_void_p],
+    ),
     "spaqr_dense_qrcp_static": (
         C.c_int,
         [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,

@@ -174,6 +174,87 @@ std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Ana
 
 }  // namespace
 
+namespace {
+template <typename T>
+int dense_qrcp_route_t(int count, T* const* A, const int* m, const int* n, const int* ld, double eps, T* const* V,
+                       T* const* taus, int* rank, int route, void* stream) {
+  if (count < 0 || (count > 0 && (!A || !m || !n || !ld || !rank)) ||
+      (route != SPAQR_QRCP_AUTO && route != SPAQR_QRCP_CLUSTER && route != SPAQR_QRCP_GRID))
+    return fail(SPAQR_ERR_INVALID_ARG, "bad arguments");
+  if (int rc = need_device()) return rc;
+  return guarded([&] {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int lim = spaqr::max_smem_optin();
+    std::vector<spaqr::QrcpDesc<T>> qs;
+    std::vector<int> ms, ns;
+    std::vector<void*> bufs;
+    struct Free {
+      std::vector<void*>& b;
+      ~Free() {
+        for (void* p : b) cudaFree(p);
+      }
+    } free_all{bufs};
+    auto dev_alloc = [&](size_t bytes) {
+      void* p = nullptr;
+      SPAQR_CUDA(cudaMalloc(&p, std::max<size_t>(bytes, 1)));
+      bufs.push_back(p);
+      return p;
+    };
+    int* d_rank = static_cast<int*>(dev_alloc(std::max(count, 1) * sizeof(int)));
+    for (int i = 0; i < count; ++i) {
+      if (m[i] < 0 || n[i] < 0 || ld[i] < std::max(1, m[i])) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "bad shape");
+      qs.push_back(spaqr::QrcpDesc<T>{A[i], nullptr, A[i], V ? V[i] : nullptr, taus ? taus[i] : nullptr,
+                                           d_rank + i, m[i], n[i], ld[i], ld[i]});
+      ms.push_back(m[i]);
+      ns.push_back(n[i]);
+    }
+    const int gctas = route == SPAQR_QRCP_CLUSTER ? 0 : spaqr::qrcp_grid_capacity(lim, (int)sizeof(T));
+    std::vector<spaqr::QrcpGroup> groups;
+    std::vector<char> need_work;
+    if (!spaqr::plan_qrcp(ms, ns, (int)sizeof(T), lim, groups, need_work, gctas, route == SPAQR_QRCP_GRID))
+      throw spaqr::Error(SPAQR_ERR_CAPACITY, "too many columns");
+    for (int i = 0; i < count; ++i)
+      if (need_work[(size_t)i])
+        qs[(size_t)i].work =
+            static_cast<T*>(dev_alloc((size_t)std::max(1, m[i]) * std::max(1, n[i]) * sizeof(T)));
+    auto* d = static_cast<spaqr::QrcpDesc<T>*>(dev_alloc(std::max<size_t>(qs.size(), 1) * sizeof(qs[0])));
+    size_t off = 0;
+    for (auto& g : groups) {
+      std::vector<spaqr::QrcpDesc<T>> part;
+      for (int i : g.idx) part.push_back(qs[(size_t)i]);
+      SPAQR_CUDA(cudaMemcpyAsync(d + off, part.data(), part.size() * sizeof(part[0]), cudaMemcpyHostToDevice, st));
+      if (g.grid) {
+        size_t bytes = 0;
+        for (int c : g.ctas) bytes += spaqr::qrcp_grid_xchg_bytes(c, g.m_max, (int)sizeof(T));
+        unsigned char* x = static_cast<unsigned char*>(dev_alloc(bytes));
+        SPAQR_CUDA(cudaMemsetAsync(x, 0, bytes, st));
+        std::vector<spaqr::QrcpGridDesc> gd;
+        int cta0 = 0;
+        for (int c : g.ctas) {
+          const size_t tb = (std::max<size_t>((size_t)2 * c, 64) * sizeof(int) + 255) & ~size_t(255);
+          const size_t sb = ((size_t)2 * c * sizeof(spaqr::QrcpSlot) + 255) & ~size_t(255);
+          gd.push_back(spaqr::QrcpGridDesc{cta0, c, reinterpret_cast<int*>(x), reinterpret_cast<spaqr::QrcpSlot*>(x + tb),
+                                           x + tb + sb});
+          x += spaqr::qrcp_grid_xchg_bytes(c, g.m_max, (int)sizeof(T));
+          cta0 += c;
+        }
+        auto* dgd = static_cast<spaqr::QrcpGridDesc*>(dev_alloc(gd.size() * sizeof(gd[0])));
+        SPAQR_CUDA(cudaMemcpyAsync(dgd, gd.data(), gd.size() * sizeof(gd[0]), cudaMemcpyHostToDevice, st));
+        SPAQR_CUDA(spaqr::launch_qrcp_grid<T>(d + off, dgd, (int)part.size(), cta0, eps, g.nl_max, g.m_max, st));
+      } else {
+        SPAQR_CUDA(spaqr::launch_qrcp<T>(d + off, (int)part.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st, g.nb));
+      }
+      off += part.size();
+    }
+    SPAQR_CUDA(cudaMemcpyAsync(rank, d_rank, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SPAQR_CUDA(cudaStreamSynchronize(st));
+    if (spaqr::qrcp_take_timeout()) return fail(SPAQR_ERR_TIMEOUT, "column-pivoted QR exchange wait timed out");
+    return SPAQR_OK;
+  });
+}
+
+}  // namespace
+
 extern "C" {
 
 void spaqr_default_options(spaqr_options* o) {
@@ -620,50 +701,17 @@ int spaqr_dense_tc_gemm(int m, int n, int k, const float* A, int lda, const floa
 
 int spaqr_dense_qrcp(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
                      double* const* V, double* const* taus, int* rank, void* stream) {
-  if (count < 0 || (count > 0 && (!A || !m || !n || !ld || !rank))) return fail(SPAQR_ERR_INVALID_ARG, "bad arguments");
-  if (int rc = need_device()) return rc;
-  return guarded([&] {
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int lim = spaqr::max_smem_optin();
-    std::vector<spaqr::QrcpDesc<double>> qs;
-    std::vector<int> ms, ns;
-    std::vector<double*> work;
-    int* d_rank = nullptr;
-    SPAQR_CUDA(cudaMalloc(&d_rank, std::max(count, 1) * sizeof(int)));
-    for (int i = 0; i < count; ++i) {
-      if (m[i] < 0 || n[i] < 0 || ld[i] < std::max(1, m[i])) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "bad shape");
-      qs.push_back(spaqr::QrcpDesc<double>{A[i], nullptr, A[i], V ? V[i] : nullptr, taus ? taus[i] : nullptr,
-                                           d_rank + i, m[i], n[i], ld[i], ld[i]});
-      ms.push_back(m[i]);
-      ns.push_back(n[i]);
-    }
-    std::vector<spaqr::QrcpGroup> groups;
-    std::vector<char> need_work;
-    if (!spaqr::plan_qrcp(ms, ns, 8, lim, groups, need_work)) throw spaqr::Error(SPAQR_ERR_CAPACITY, "too many columns");
-    for (int i = 0; i < count; ++i)
-      if (need_work[(size_t)i]) {
-        double* w = nullptr;
-        SPAQR_CUDA(cudaMalloc(&w, (size_t)std::max(1, m[i]) * std::max(1, n[i]) * sizeof(double)));
-        work.push_back(w);
-        qs[(size_t)i].work = w;
-      }
-    spaqr::QrcpDesc<double>* d = nullptr;
-    SPAQR_CUDA(cudaMalloc(&d, std::max<size_t>(qs.size(), 1) * sizeof(spaqr::QrcpDesc<double>)));
-    size_t off = 0;
-    for (auto& g : groups) {
-      std::vector<spaqr::QrcpDesc<double>> part;
-      for (int i : g.idx) part.push_back(qs[(size_t)i]);
-      SPAQR_CUDA(cudaMemcpyAsync(d + off, part.data(), part.size() * sizeof(part[0]), cudaMemcpyHostToDevice, st));
-      SPAQR_CUDA(spaqr::launch_qrcp<double>(d + off, (int)part.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st, g.nb));
-      off += part.size();
-    }
-    SPAQR_CUDA(cudaMemcpyAsync(rank, d_rank, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st));
-    SPAQR_CUDA(cudaStreamSynchronize(st));
-    cudaFree(d);
-    cudaFree(d_rank);
-    for (double* w : work) cudaFree(w);
-    return SPAQR_OK;
-  });
+  return spaqr_dense_qrcp_route(count, A, m, n, ld, eps, V, taus, rank, SPAQR_QRCP_CLUSTER, stream);
+}
+
+int spaqr_dense_qrcp_route(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
+                           double* const* V, double* const* taus, int* rank, int route, void* stream) {
+  return dense_qrcp_route_t<double>(count, A, m, n, ld, eps, V, taus, rank, route, stream);
+}
+
+int spaqr_dense_qrcp_f32(int count, float* const* A, const int* m, const int* n, const int* ld, double eps,
+                         float* const* V, float* const* taus, int* rank, int route, void* stream) {
+  return dense_qrcp_route_t<float>(count, A, m, n, ld, eps, V, taus, rank, route, stream);
 }
 
 }  // extern "C"

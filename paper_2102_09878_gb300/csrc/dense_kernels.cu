@@ -595,6 +595,21 @@ __device__ __forceinline__ T butterfly_reduce(T (&a)[G], int lane) {
   return v;
 }
 
+// Partial column norms are downdated and recomputed exactly once they have
+// lost more than this fraction of the last exact value: the reference
+// algorithm's FP64 threshold, and sqrt(FP32 epsilon) (single-precision LAPACK's
+// tol3z) for norms kept in FP32.
+template <typename N>
+__device__ __forceinline__ N recompute_frac();
+template <>
+__device__ __forceinline__ double recompute_frac<double>() {
+  return kRecompute;
+}
+template <>
+__device__ __forceinline__ float recompute_frac<float>() {
+  return 3.4527e-4f;
+}
+
 // ------------------------------------------------------------------- QRCP
 // Column-pivoted Householder QR stopped at the rank, one thread-block cluster
 // of CS CTAs per matrix.  CTA r of the cluster owns the column slab
@@ -616,20 +631,21 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
   const int j0 = min(n, rank * nl), j1 = min(n, j0 + nl);
   const int nloc = j1 - j0;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* nu = reinterpret_cast<double*>(smraw);   // nl_max
-  double* nuref = nu + nl_max;                      // nl_max
+  using N = T;  // norms, pivots and reflector scalars in the data's precision
+  N* nu = reinterpret_cast<N*>(smraw);  // nl_max
+  N* nuref = nu + nl_max;               // nl_max
   int* step_of = reinterpret_cast<int*>(nuref + nl_max);  // nl_max
   int* act = step_of + nl_max;                            // unpivoted local columns, nl_max
   int* pos = act + nl_max;                                // position of each column in act
   T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // 2 x (m_max + 2)
   T* taus = vbuf + 2 * ((m_max + 3) & ~1);         // min(m_max, n) + 2
   T* X = SMEM ? taus + ((m_max + 3) & ~1) : d.work + (size_t)j0 * m;
-  __shared__ double cand_v;
+  __shared__ N cand_v;
   __shared__ int cand_j;
-  __shared__ double s_beta;
+  __shared__ N s_beta;
   __shared__ T s_tau;
   __shared__ int s_stop, s_piv, s_nact;
-  __shared__ double red_v[kWarps];
+  __shared__ N red_v[kWarps];
   __shared__ int red_i[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
@@ -638,9 +654,9 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
   }
   __syncthreads();
   for (int c = warp; c < nloc; c += kWarps) {
-    double sq = 0.0;
+    N sq = N(0);
     for (int r = lane; r < m; r += 32) {
-      const double v = (double)X[r + (int64_t)c * m];
+      const N v = (N)X[r + (int64_t)c * m];
       sq += v * v;
     }
     sq = warp_sum(sq);
@@ -656,14 +672,14 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
   }
   if (threadIdx.x == 0) s_nact = nloc;
   const int kmax = m < n ? m : n;
-  double r11 = 0.0;
+  N r11 = N(0);
   int k = 0;
   __syncthreads();
   // warp-local proposal of the warp's columns (c = warp + kW * (lane + 32 t))
-  double wv = -1.0;
+  N wv = N(-1);
   int wj = INT_MAX;
   for (int c = warp + lane * kWarps; c < nloc; c += 32 * kWarps) {
-    const double v = nu[c];
+    const N v = nu[c];
     if (v > wv || (v == wv && j0 + c < wj)) {
       wv = v;
       wj = j0 + c;
@@ -671,7 +687,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, wv, o);
+    const N ov = __shfl_xor_sync(0xffffffffu, wv, o);
     const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
     if (ov > wv || (ov == wv && oj < wj)) {
       wv = ov;
@@ -684,10 +700,10 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
   // proposal and reflector slots alternate between two buffers by step parity,
   // so a CTA never overwrites a slot another CTA may still be reading.
   const int vstride = (m_max + 3) & ~1;
-  __shared__ double cand_v2[2], sp_beta[2];
+  __shared__ N cand_v2[2], sp_beta[2];
   __shared__ int cand_j2[2], sp_stop[2];
   __shared__ T sp_tau[2], s_den;
-  __shared__ double red2[kWarps];
+  __shared__ N red2[kWarps];
   for (int i = 0; i < kmax; ++i) {
     const int par = i & 1;
     T* vb = vbuf + par * vstride;
@@ -698,7 +714,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double v = red_v[0];
+      N v = red_v[0];
       int j = red_i[0];
       for (int w = 1; w < kWarps; ++w)
         if (red_v[w] > v || (red_v[w] == v && red_i[w] < j)) {
@@ -713,34 +729,34 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
     // (2) its reflector, rows i..m-1, into vb (the column itself is untouched)
     if (jloc != INT_MAX) {
       const T* col = X + (int64_t)(jloc - j0) * m;
-      double sq = 0.0;
+      N sq = N(0);
       for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) {
-        const double v = (double)col[r];
+        const N v = (N)col[r];
         sq += v * v;
       }
       sq = warp_sum(sq);
       if (lane == 0) red2[warp] = sq;
       __syncthreads();
       if (threadIdx.x == 0) {
-        double sig = 0.0;
+        N sig = N(0);
         for (int w = 0; w < kWarps; ++w) sig += red2[w];
-        const double alpha = (double)col[i];
-        double beta, tau;
-        if (sig == 0.0) {
+        const N alpha = (N)col[i];
+        N beta, tau;
+        if (sig == N(0)) {
           beta = alpha;
-          tau = 0.0;
+          tau = N(0);
         } else {
-          const double nrm = sqrt(alpha * alpha + sig);
-          beta = alpha >= 0.0 ? -nrm : nrm;
+          const N nrm = sqrt(alpha * alpha + sig);
+          beta = alpha >= N(0) ? -nrm : nrm;
           tau = (beta - alpha) / beta;
         }
-        const double ab = fabs(beta);
-        const double r11_here = (i == 0) ? ab : r11;
-        const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
+        const N ab = fabs(beta);
+        const N r11_here = (i == 0) ? ab : r11;
+        const int stop = (beta == N(0) || ab < (N)eps * r11_here) ? 1 : 0;
         sp_beta[par] = beta;
         sp_tau[par] = (T)tau;
         sp_stop[par] = stop;
-        s_den = (!stop && sig != 0.0) ? (T)(alpha - beta) : T(0);
+        s_den = (!stop && sig != N(0)) ? (T)(alpha - beta) : T(0);
       }
       __syncthreads();
       const T den = s_den;
@@ -750,7 +766,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
     cl.sync();  // proposals and candidate reflectors visible cluster-wide
     // (3) the winner: one lane per CTA of the cluster, then a warp reduction
     if (threadIdx.x < 32) {
-      double v = -1.0;
+      N v = N(-1);
       int j = INT_MAX;
       if (lane < CS) {
         v = *cl.map_shared_rank(&cand_v2[par], lane);
@@ -758,7 +774,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const N ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oj = __shfl_xor_sync(0xffffffffu, j, o);
         if (ov > v || (ov == v && oj < j)) {
           v = ov;
@@ -810,7 +826,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
     // broadcast, the rows are updated, and lane L(j) downdates the FP64 squared
     // norm of column j (recomputed warp-parallel when it lost too many digits)
     // and keeps the warp's proposal for step i + 1.
-    wv = -1.0;
+    wv = N(-1);
     wj = INT_MAX;
     const int nact = s_nact;
     const int jl = butterfly_col<KG>(lane);  // the column whose sum this lane ends with
@@ -834,11 +850,11 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
       const int cme = jl < ng ? act[g0 + jl] : 0;
       T* colme = X + (int64_t)cme * m;
       T wmine = T(0);
-      double xnew = 0.0;
+      N xnew = N(0);
       if (jl < ng) {
         const T xi = colme[i];
         wmine = tau * (xi + dsum);
-        xnew = (double)(xi - wmine);
+        xnew = (N)(xi - wmine);
       }
       T wv8[KG];
 #pragma unroll
@@ -854,11 +870,11 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
         }
       }
       __syncwarp();
-      double v = -1.0;
+      N v = N(-1);
       bool redo = false;
       if (lead && jl < ng) {
         v = nu[cme] - xnew * xnew;
-        redo = v < kRecompute * nuref[cme];
+        redo = v < recompute_frac<N>() * nuref[cme];
       }
       unsigned flagged = __ballot_sync(0xffffffffu, redo);
       while (flagged) {
@@ -866,9 +882,9 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
         flagged &= flagged - 1;
         const int cc = __shfl_sync(0xffffffffu, cme, l);
         const T* col = X + (int64_t)cc * m;
-        double sq = 0.0;
+        N sq = N(0);
         for (int r = i + 1 + lane; r < m; r += 32) {
-          const double y = (double)col[r];
+          const N y = (N)col[r];
           sq += y * y;
         }
         sq = warp_sum(sq);
@@ -888,7 +904,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
     // warp reduction of the proposals (lowest column index on ties)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, wv, o);
+      const N ov = __shfl_xor_sync(0xffffffffu, wv, o);
       const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
       if (ov > wv || (ov == wv && oj < wj)) {
         wv = ov;
@@ -921,6 +937,493 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
     }
   }
   cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// ------------------------------------------- QRCP over a group of CTAs
+// The same slab-in-shared-memory pivoted QR for matrices whose slabs need more
+// CTAs than one cluster holds: matrix f of a launch takes CTAs
+// [cta0, cta0 + ctas) (all resident at once: cooperative launch) and the
+// cluster barrier plus distributed-shared-memory reads become a message
+// exchange through global memory (L2).  At step i every CTA writes its
+// proposal and the speculative reflector of its best column into buffer
+// (i & 1), then adds one to that buffer's arrival counter; every CTA waits
+// until the counter shows all G arrivals of the step (a bounded wait: on
+// expiry it raises g_qrcp_timeout, writes rank -1 and returns), picks the same
+// winner and copies the winner's reflector.  A CTA can only reach step i + 2,
+// which rewrites buffer (i & 1), after every CTA has arrived at step i + 1,
+// i.e. after every CTA has finished reading step i.
+__device__ int g_qrcp_timeout = 0;
+constexpr long long kQrcpGridWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void add_release(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T, int KG>
+__global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T>* descs, const QrcpGridDesc* gds,
+                                                             int count, double eps, int nl_max, int m_max) {
+  int f = 0;
+  {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (gds[mid].cta0 <= (int)blockIdx.x)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    f = lo;
+  }
+  const QrcpGridDesc gd = gds[f];
+  const int G = gd.ctas;
+  const int rank = (int)blockIdx.x - gd.cta0;
+  const QrcpDesc<T> d = descs[f];
+  const int m = d.m, n = d.n;
+  const int nl = (n + G - 1) / G;
+  const int j0 = min(n, rank * nl), j1 = min(n, j0 + nl);
+  const int nloc = j1 - j0;
+  const int vstride = (m_max + 3) & ~1;
+  int* tags = gd.tags;                        // arrival counters of the two buffers, 128 bytes apart
+  QrcpSlot* slots = gd.slots;                 // [2][G]
+  T* vg = static_cast<T*>(gd.vg);             // [2][G][vstride]
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using N = T;  // norms, pivots and reflector scalars in the data's precision
+  N* nu = reinterpret_cast<N*>(smraw);
+  N* nuref = nu + nl_max;
+  int* step_of = reinterpret_cast<int*>(nuref + nl_max);
+  int* act = step_of + nl_max;
+  int* pos = act + nl_max;
+  T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // 2 x vstride
+  T* taus = vbuf + 2 * vstride;
+  T* X = taus + vstride;
+  __shared__ N s_beta;
+  __shared__ T s_tau;
+  __shared__ int s_stop, s_piv, s_nact, s_late;
+  __shared__ N red_v[kWarps];
+  __shared__ int red_i[kWarps];
+  __shared__ N cand_v2[2], sp_beta[2];
+  __shared__ int cand_j2[2], sp_stop[2];
+  __shared__ T sp_tau[2], s_den;
+  __shared__ N red2[kWarps];
+  __shared__ T s_part[kWarps * KG];  // partial dot products (few-column apply)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    X[e] = d.src[r + (int64_t)(j0 + c) * d.ld];
+  }
+  __syncthreads();
+  for (int c = warp; c < nloc; c += kWarps) {
+    N sq = N(0);
+    for (int r = lane; r < m; r += 32) {
+      const N v = (N)X[r + (int64_t)c * m];
+      sq += v * v;
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) {
+      nu[c] = sq;
+      nuref[c] = sq;
+      step_of[c] = -1;
+    }
+  }
+  for (int c = threadIdx.x; c < nloc; c += kThreads) {
+    act[c] = c;
+    pos[c] = c;
+  }
+  if (threadIdx.x == 0) {
+    s_nact = nloc;
+    s_late = 0;
+  }
+  const int kmax = m < n ? m : n;
+  N r11 = N(0);
+  int k = 0;
+  __syncthreads();
+  N wv = N(-1);
+  int wj = INT_MAX;
+  for (int c = warp + lane * kWarps; c < nloc; c += 32 * kWarps) {
+    const N v = nu[c];
+    if (v > wv || (v == wv && j0 + c < wj)) {
+      wv = v;
+      wj = j0 + c;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const N ov = __shfl_xor_sync(0xffffffffu, wv, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
+    if (ov > wv || (ov == wv && oj < wj)) {
+      wv = ov;
+      wj = oj;
+    }
+  }
+  for (int i = 0; i < kmax; ++i) {
+    const int par = i & 1;
+    T* vb = vbuf + par * vstride;
+    T* vmine = vg + ((size_t)par * G + rank) * vstride;
+    // (1) the CTA's best column
+    if (lane == 0) {
+      red_v[warp] = wv;
+      red_i[warp] = wj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      N v = red_v[0];
+      int j = red_i[0];
+      for (int w = 1; w < kWarps; ++w)
+        if (red_v[w] > v || (red_v[w] == v && red_i[w] < j)) {
+          v = red_v[w];
+          j = red_i[w];
+        }
+      cand_v2[par] = v;
+      cand_j2[par] = j;
+    }
+    __syncthreads();
+    const int jloc = cand_j2[par];
+    // (2) its reflector, rows i..m-1, into vb and the CTA's global slot
+    if (jloc != INT_MAX) {
+      const T* col = X + (int64_t)(jloc - j0) * m;
+      N sq = N(0);
+      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) {
+        const N v = (N)col[r];
+        sq += v * v;
+      }
+      sq = warp_sum(sq);
+      if (lane == 0) red2[warp] = sq;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        N sig = N(0);
+        for (int w = 0; w < kWarps; ++w) sig += red2[w];
+        const N alpha = (N)col[i];
+        N beta, tau;
+        if (sig == N(0)) {
+          beta = alpha;
+          tau = N(0);
+        } else {
+          const N nrm = sqrt(alpha * alpha + sig);
+          beta = alpha >= N(0) ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+        }
+        const N ab = fabs(beta);
+        const N r11_here = (i == 0) ? ab : r11;
+        const int stop = (beta == N(0) || ab < (N)eps * r11_here) ? 1 : 0;
+        sp_beta[par] = beta;
+        sp_tau[par] = (T)tau;
+        sp_stop[par] = stop;
+        s_den = (!stop && sig != N(0)) ? (T)(alpha - beta) : T(0);
+        QrcpSlot* sl = slots + (size_t)par * G + rank;
+        sl->v = cand_v2[par];
+        sl->beta = beta;
+        sl->tau = (double)(T)tau;
+        sl->j = jloc;
+        sl->stop = stop;
+      }
+      __syncthreads();
+      const T den = s_den;
+      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) {
+        const T x = den != T(0) ? col[r] / den : T(0);
+        vb[r - i] = x;
+        vmine[r - i] = x;
+      }
+      if (threadIdx.x == 0) {
+        vb[0] = T(1);
+        vmine[0] = T(1);
+      }
+    } else if (threadIdx.x == 0) {
+      QrcpSlot* sl = slots + (size_t)par * G + rank;
+      sl->v = -1.0;
+      sl->beta = 0.0;
+      sl->tau = N(0);
+      sl->j = INT_MAX;
+      sl->stop = 1;
+    }
+    // (3) publish: the CTA barrier orders every thread's stores before thread 0's
+    // release increment of the step counter (cumulative at gpu scope); buffer
+    // par counts G arrivals every second step
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      add_release(tags + 32 * par, 1);
+      // (4) wait for every CTA of the matrix (bounded); the acquire load makes
+      // the step's slots and reflectors visible to the CTA after the barrier
+      const int target = G * (i / 2 + 1);
+      const long long t0 = clock64();
+      int spins = 0;
+      while (ld_acquire(tags + 32 * par) < target) {
+        if (((++spins) & 255) == 0 && clock64() - t0 > kQrcpGridWaitCycles) {
+          s_late = 1;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_late) {
+      if (threadIdx.x == 0) {
+        atomicExch(&g_qrcp_timeout, 1);
+        d.rank[0] = -1;
+      }
+      return;
+    }
+    // (5) the winner (lowest column index on ties), read from L2
+    if (threadIdx.x < 32) {
+      N v = N(-1);
+      int j = INT_MAX;
+      for (int t = lane; t < G; t += 32) {
+        const QrcpSlot* sl = slots + (size_t)par * G + t;
+        const N tv = (N)__ldcg(&sl->v);
+        const int tj = __ldcg(&sl->j);
+        if (tv > v || (tv == v && tj < j)) {
+          v = tv;
+          j = tj;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const N ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+        if (ov > v || (ov == v && oj < j)) {
+          v = ov;
+          j = oj;
+        }
+      }
+      if (lane == 0) s_piv = j;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p == INT_MAX) break;  // no proposal (non-finite norms): every CTA sees the same p
+    const int owner = p / nl;
+    if (rank != owner) {
+      const T* vo = vg + ((size_t)par * G + owner) * vstride;
+      for (int r = threadIdx.x; r < m - i; r += kThreads) vb[r] = __ldcg(vo + r);
+      if (threadIdx.x == 0) {
+        const QrcpSlot* sl = slots + (size_t)par * G + owner;
+        s_tau = (T)__ldcg(&sl->tau);
+        s_beta = (N)__ldcg(&sl->beta);
+        s_stop = __ldcg(&sl->stop);
+      }
+    } else if (threadIdx.x == 0) {
+      s_tau = sp_tau[par];
+      s_beta = sp_beta[par];
+      s_stop = sp_stop[par];
+    }
+    __syncthreads();
+    if (i == 0) r11 = fabs(s_beta);
+    if (s_stop) break;
+    const T tau = s_tau;
+    if (threadIdx.x == 0) taus[i] = copysign(tau, (T)s_beta);  // tau >= 0; the sign is that of R_ii
+    if (rank == owner) {
+      const int pl = p - j0;
+      T* col = X + (int64_t)pl * m;
+      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) col[r] = vb[r - i];
+      if (threadIdx.x == 0) {
+        col[i] = (T)s_beta;
+        const int q = pos[pl], last = act[s_nact - 1];
+        step_of[pl] = i;
+        act[q] = last;
+        pos[last] = q;
+        s_nact = s_nact - 1;
+      }
+    }
+    __syncthreads();
+    // (6) apply H_i to the CTA's unpivoted columns.  Many columns: warps take
+    // groups of KG columns as in the cluster kernel.  Few columns (at most four
+    // groups): RS warps share a group, each over every RS-th 32-row block; the
+    // partial dot products meet in shared memory, every warp of the group forms
+    // the same w_j (same summation order) and updates its rows, and after a
+    // barrier the group's first warp updates row i, the norms and the proposal.
+    wv = N(-1);
+    wj = INT_MAX;
+    const int nact = s_nact;
+    const int jl = butterfly_col<KG>(lane);
+    const bool lead = lane == butterfly_lane<KG>(jl);
+    const int ngrp = (nact + KG - 1) / KG;
+    int RS = 1;
+    if (ngrp > 0)
+      while (RS * 2 * ngrp <= kWarps) RS *= 2;
+    if (RS == 1) {
+      for (int g0 = warp * KG; g0 < nact; g0 += kWarps * KG) {
+        const int ng = min(KG, nact - g0);
+        T* cols[KG];
+  #pragma unroll
+        for (int j = 0; j < KG; ++j) cols[j] = X + (int64_t)act[g0 + (j < ng ? j : 0)] * m;
+        T acc[KG];
+  #pragma unroll
+        for (int j = 0; j < KG; ++j) acc[j] = T(0);
+        if (tau != T(0)) {
+          for (int r = i + 1 + lane; r < m; r += 32) {
+            const T vr = vb[r - i];
+  #pragma unroll
+            for (int j = 0; j < KG; ++j) acc[j] += vr * cols[j][r];
+          }
+        }
+        const T dsum = butterfly_reduce<KG>(acc, lane);
+        const int cme = jl < ng ? act[g0 + jl] : 0;
+        T* colme = X + (int64_t)cme * m;
+        T wmine = T(0);
+        N xnew = N(0);
+        if (jl < ng) {
+          const T xi = colme[i];
+          wmine = tau * (xi + dsum);
+          xnew = (N)(xi - wmine);
+        }
+        T wv8[KG];
+  #pragma unroll
+        for (int j = 0; j < KG; ++j) wv8[j] = __shfl_sync(0xffffffffu, wmine, butterfly_lane<KG>(j));
+        __syncwarp();
+        if (lead && jl < ng) colme[i] = (T)xnew;
+        if (tau != T(0)) {
+          for (int r = i + 1 + lane; r < m; r += 32) {
+            const T vr = vb[r - i];
+  #pragma unroll
+            for (int j = 0; j < KG; ++j)
+              if (j < ng) cols[j][r] -= wv8[j] * vr;
+          }
+        }
+        __syncwarp();
+        N v = N(-1);
+        bool redo = false;
+        if (lead && jl < ng) {
+          v = nu[cme] - xnew * xnew;
+          redo = v < recompute_frac<N>() * nuref[cme];
+        }
+        unsigned flagged = __ballot_sync(0xffffffffu, redo);
+        while (flagged) {
+          const int l = __ffs(flagged) - 1;
+          flagged &= flagged - 1;
+          const int cc = __shfl_sync(0xffffffffu, cme, l);
+          const T* col = X + (int64_t)cc * m;
+          N sq = N(0);
+          for (int r = i + 1 + lane; r < m; r += 32) {
+            const N y = (N)col[r];
+            sq += y * y;
+          }
+          sq = warp_sum(sq);
+          if (lane == l) {
+            v = sq;
+            nuref[cc] = sq;
+          }
+        }
+        if (lead && jl < ng) {
+          nu[cme] = v;
+          if (v > wv || (v == wv && j0 + cme < wj)) {
+            wv = v;
+            wj = j0 + cme;
+          }
+        }
+      }
+    } else {
+      const int cg = warp / RS, rs = warp % RS;
+      const bool active = cg < ngrp;
+      const int g0 = cg * KG;
+      const int ng = active ? min(KG, nact - g0) : 0;
+      T* cols[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) cols[j] = X + (int64_t)act[active ? g0 + (j < ng ? j : 0) : 0] * m;
+      T acc[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) acc[j] = T(0);
+      if (active && tau != T(0)) {
+        for (int r = i + 1 + lane + 32 * rs; r < m; r += 32 * RS) {
+          const T vr = vb[r - i];
+#pragma unroll
+          for (int j = 0; j < KG; ++j) acc[j] += vr * cols[j][r];
+        }
+      }
+      const T dpart = butterfly_reduce<KG>(acc, lane);
+      if (active && lead && jl < ng) s_part[(g0 + jl) * RS + rs] = dpart;
+      __syncthreads();
+      const int cme = (active && jl < ng) ? act[g0 + jl] : 0;
+      T* colme = X + (int64_t)cme * m;
+      T wmine = T(0);
+      N xnew = N(0);
+      if (active && jl < ng) {
+        T dsum = T(0);
+        for (int q = 0; q < RS; ++q) dsum += s_part[(g0 + jl) * RS + q];
+        const T xi = colme[i];
+        wmine = tau * (xi + dsum);
+        xnew = (N)(xi - wmine);
+      }
+      T wv8[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) wv8[j] = __shfl_sync(0xffffffffu, wmine, butterfly_lane<KG>(j));
+      if (active && tau != T(0)) {
+        for (int r = i + 1 + lane + 32 * rs; r < m; r += 32 * RS) {
+          const T vr = vb[r - i];
+#pragma unroll
+          for (int j = 0; j < KG; ++j)
+            if (j < ng) cols[j][r] -= wv8[j] * vr;
+        }
+      }
+      __syncthreads();  // every row slice is updated before row i and the norms
+      if (active && rs == 0) {
+        if (lead && jl < ng) colme[i] = (T)xnew;
+        N v = N(-1);
+        bool redo = false;
+        if (lead && jl < ng) {
+          v = nu[cme] - xnew * xnew;
+          redo = v < recompute_frac<N>() * nuref[cme];
+        }
+        unsigned flagged = __ballot_sync(0xffffffffu, redo);
+        while (flagged) {
+          const int l = __ffs(flagged) - 1;
+          flagged &= flagged - 1;
+          const int cc = __shfl_sync(0xffffffffu, cme, l);
+          const T* col = X + (int64_t)cc * m;
+          N sq = N(0);
+          for (int r = i + 1 + lane; r < m; r += 32) {
+            const N y = (N)col[r];
+            sq += y * y;
+          }
+          sq = warp_sum(sq);
+          if (lane == l) {
+            v = sq;
+            nuref[cc] = sq;
+          }
+        }
+        if (lead && jl < ng) {
+          nu[cme] = v;
+          if (v > wv || (v == wv && j0 + cme < wj)) {
+            wv = v;
+            wj = j0 + cme;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const N ov = __shfl_xor_sync(0xffffffffu, wv, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
+      if (ov > wv || (ov == wv && oj < wj)) {
+        wv = ov;
+        wj = oj;
+      }
+    }
+    __syncthreads();  // every warp is done with act[] before the next pivot edits it
+    k = i + 1;
+  }
+  __syncthreads();
+  if (rank == 0 && threadIdx.x == 0) d.rank[0] = k;
+  if (d.V) {
+    for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
+      const int r = (int)(e % m), c = (int)(e / m);
+      const int t = step_of[c];
+      if (t < 0 || t >= k) continue;
+      d.V[r + (int64_t)t * m] = r < t ? T(0) : (r == t ? T(1) : X[r + (int64_t)c * m]);
+    }
+    if (rank == 0)
+      for (int t = threadIdx.x; t < k; t += kThreads) d.tau[t] = fabs(taus[t]);
+  }
+  if (d.out && (k < m || (d.flags & kQrcpAlwaysOut))) {
+    const bool fix = d.flags & kQrcpSignFix;
+    for (int64_t e = threadIdx.x; e < (int64_t)k * nloc; e += kThreads) {
+      const int r = (int)(e % k), c = (int)(e / k);
+      const int t = step_of[c];
+      const T x = (t >= 0 && r > t) ? T(0) : X[r + (int64_t)c * m];
+      d.out[r + (int64_t)(j0 + c) * d.ldo] = fix && signbit(taus[r]) ? -x : x;
+    }
+  }
 }
 
 // --------------------------------------------- QRCP with delayed updates
@@ -1736,6 +2239,61 @@ cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int
   }
 }
 
+int qrcp_grid_capacity(int smem_bytes, int elem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  if (elem == 4) {
+    allow_smem(qrcp_grid_kernel<float, 8>);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, qrcp_grid_kernel<float, 8>, kThreads, smem_bytes);
+  } else {
+    allow_smem(qrcp_grid_kernel<double, 8>);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, qrcp_grid_kernel<double, 8>, kThreads, smem_bytes);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    per = 0;
+  }
+  return std::min(sms * per, kThreads);  // the tag wait takes one thread per CTA of a matrix
+}
+
+int qrcp_take_timeout() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_qrcp_timeout, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_qrcp_timeout, &zero, sizeof(int));
+  }
+  return v;
+}
+
+template <typename T>
+cudaError_t launch_qrcp_grid(const QrcpDesc<T>* d, const QrcpGridDesc* gd, int count, int total_ctas, double eps,
+                             int nl_max, int m_max, cudaStream_t st) {
+  if (count <= 0 || total_ctas <= 0) return cudaSuccess;
+  const int smem = qrcp_smem_bytes(m_max, nl_max, (int)sizeof(T), true);
+  static bool init = false;
+  if (!init) {
+    allow_smem(qrcp_grid_kernel<T, 8>);
+    init = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)total_ctas);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, qrcp_grid_kernel<T, 8>, d, gd, count, eps, nl_max, m_max);
+}
+
 template <typename T>
 cudaError_t launch_refl(const ReflDesc<T>* d, const int2* items, int nitems, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
@@ -1904,6 +2462,8 @@ cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std
                                                 cudaStream_t);                                           \
   template cudaError_t launch_front_finish<T>(const FrontDesc<T>*, int, int, cudaStream_t);                   \
   template cudaError_t launch_qrcp<T>(const QrcpDesc<T>*, int, double, int, int, int, bool, cudaStream_t, int); \
+  template cudaError_t launch_qrcp_grid<T>(const QrcpDesc<T>*, const QrcpGridDesc*, int, int, double, int, int,    \
+                                           cudaStream_t);                                                         \
   template cudaError_t launch_refl<T>(const ReflDesc<T>*, const int2*, int, cudaStream_t);               \
   template cudaError_t launch_trsm<T>(const TrsmDesc<T>*, const int2*, int, cudaStream_t);               \
   template cudaError_t launch_argmax<T>(const ArgmaxDesc<T>*, const int2*, int, cudaStream_t);

@@ -285,6 +285,7 @@ class Factorizer {
   std::vector<int> p1_of_, p2_of_;
   std::vector<int> own_head_;  // scratch
   int smem_max_ = 0;
+  int grid_ctas_ = 0;  // CTAs of one grid-mode QRCP launch (all resident)
   int64_t launches_ = 0;
   struct StageLog {
     int fronts = 0, rounds = 0, max_m = 0, max_n = 0, max_c = 0;
@@ -578,7 +579,7 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
   }
   std::vector<QrcpGroup> groups;
   std::vector<char> need_work;
-  if (!plan_qrcp(ms, ns, (int)sizeof(T), smem_max_, groups, need_work))
+  if (!plan_qrcp(ms, ns, (int)sizeof(T), smem_max_, groups, need_work, grid_ctas_))
     throw Error(SPAQR_ERR_CAPACITY, "column-pivoted QR with too many columns for 16 CTAs");
   for (size_t i = 0; i < qs.size(); ++i)
     if (need_work[i]) {
@@ -593,10 +594,36 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
     for (int i : g.idx) part.push_back(qs[(size_t)i]);
     dg.push_back(up_.put(part));
   }
+  // grid-mode groups: exchange areas (tags zeroed) and CTA ranges
+  std::vector<QrcpGridDesc*> dgd(groups.size(), nullptr);
+  std::vector<int> gtot(groups.size(), 0);
+  for (size_t t = 0; t < groups.size(); ++t) {
+    const auto& g = groups[t];
+    if (!g.grid) continue;
+    size_t bytes = 0;
+    for (int c : g.ctas) bytes += qrcp_grid_xchg_bytes(c, g.m_max, (int)sizeof(T));
+    unsigned char* x = static_cast<unsigned char*>(pool_.alloc(bytes));
+    work_bufs.push_back(reinterpret_cast<T*>(x));
+    SPAQR_CUDA(cudaMemsetAsync(x, 0, bytes, st_));
+    std::vector<QrcpGridDesc> gd;
+    int cta0 = 0;
+    for (int c : g.ctas) {
+      const size_t tb = (std::max<size_t>((size_t)2 * c, 64) * sizeof(int) + 255) & ~size_t(255);
+      const size_t sb = ((size_t)2 * c * sizeof(QrcpSlot) + 255) & ~size_t(255);
+      gd.push_back(QrcpGridDesc{cta0, c, reinterpret_cast<int*>(x), reinterpret_cast<QrcpSlot*>(x + tb), x + tb + sb});
+      x += qrcp_grid_xchg_bytes(c, g.m_max, (int)sizeof(T));
+      cta0 += c;
+    }
+    gtot[t] = cta0;
+    dgd[t] = up_.put(gd);
+  }
   tm_.begin(st_, 2);
   for (size_t t = 0; t < groups.size(); ++t) {
     const auto& g = groups[t];
-    check(launch_qrcp<T>(dg[t], (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st_, g.nb), "qrcp");
+    if (g.grid)
+      check(launch_qrcp_grid<T>(dg[t], dgd[t], (int)g.idx.size(), gtot[t], eps, g.nl_max, g.m_max, st_), "qrcp grid");
+    else
+      check(launch_qrcp<T>(dg[t], (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st_, g.nb), "qrcp");
   }
   tm_.end(st_);
 }
@@ -1316,6 +1343,8 @@ void Factorizer<T>::step1() {
   for (T* w : work) pool_.release(w);
   for (size_t i = 0; i < who.size(); ++i) {
     Group& g = G_[(size_t)who[i]];
+    if (rank[i] < 0 && qrcp_take_timeout())
+      throw Error(SPAQR_ERR_TIMEOUT, "step 1: column-pivoted QR exchange wait timed out");
     if (rank[i] < 0 || rank[i] > std::min(g.rows, g.width))
       throw Error(SPAQR_ERR_CUDA, "step 1: rank " + std::to_string(rank[i]) + " out of range for a " +
                                       std::to_string(g.rows) + " x " + std::to_string(g.width) + " block at stage " +
@@ -1500,6 +1529,8 @@ void Factorizer<T>::step2() {
   lap("step2: readback");
   for (size_t i = 0; i < recs.size(); ++i) {
     ks[i] = kall[(size_t)(h_.ops[recs[i].op].kdev - kdev_all)];
+    if (ks[i] < 0 && qrcp_take_timeout())
+      throw Error(SPAQR_ERR_TIMEOUT, "step 2: column-pivoted QR exchange wait timed out");
     if (ks[i] < 0 || ks[i] > std::min(h_.ops[recs[i].op].c, recs[i].ncm))
       throw Error(SPAQR_ERR_CUDA, "step 2: rank " + std::to_string(ks[i]) + " out of range at stage " +
                                       std::to_string(k_));
@@ -1705,6 +1736,7 @@ template <typename T>
 void Factorizer<T>::run(const spaqr_csr& A) {
   L_ = an_.depth;
   smem_max_ = max_smem_optin();
+  grid_ctas_ = qrcp_grid_capacity(smem_max_, (int)sizeof(T));
   {
     const char* e = std::getenv("SPAQR_CHECK");
     checking_ = e && e[0] == '1';
@@ -1782,6 +1814,7 @@ void run_factor(Handle& h, const spaqr_csr& A, const Analysis& an) {
     Factorizer<double> f(h, an);
     f.run(A);
   }
+  if (qrcp_take_timeout()) throw Error(SPAQR_ERR_TIMEOUT, "column-pivoted QR exchange wait timed out");
 }
 
 }  // namespace spaqr

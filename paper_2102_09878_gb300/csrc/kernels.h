@@ -147,6 +147,8 @@ struct QrcpGroup {
   int nb = kQrcpNB;  // panel depth of the delayed-update form (slab == false)
   int m_max = 0, nl_max = 0;
   std::vector<int> idx;
+  bool grid = false;      // CTA groups exchanging through global memory (qrcp_grid_kernel)
+  std::vector<int> ctas;  // grid: CTAs of each member (parallel to idx)
 };
 // bytes of one warp's region in the warp-per-matrix QRCP (cs == 0 groups)
 inline int qrcp_warp_bytes(int m, int n, int elem) {
@@ -157,19 +159,53 @@ inline int qrcp_warp_bytes(int m, int n, int elem) {
 }
 constexpr int kQrcpWarpCap = 24 << 10;  // per-warp region limit for the warp QRCP
 
+// Grid-mode QRCP (slabs in shared memory, more CTAs per matrix than a cluster
+// holds): matrix f of a launch runs on CTAs [cta0, cta0 + ctas) and exchanges
+// proposals and reflectors through tags / slots / vg (device memory; tags holds
+// the two arrival counters at ints 0 and 32, zeroed before the launch; vg
+// holds 2 x ctas x ((m_max + 3) & ~1) elements).
+struct QrcpSlot {
+  double v, beta, tau;
+  int j, stop;
+};
+struct QrcpGridDesc {
+  int cta0, ctas;
+  int* tags;        // two arrival counters (ints 0 and 32)
+  QrcpSlot* slots;  // 2 x ctas
+  void* vg;
+};
+// bytes of the exchange area of one grid-mode matrix (tags first)
+inline size_t qrcp_grid_xchg_bytes(int ctas, int m_max, int elem) {
+  auto a = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return a(std::max<size_t>((size_t)2 * ctas, 64) * sizeof(int)) + a((size_t)2 * ctas * sizeof(QrcpSlot)) +
+         a((size_t)2 * ctas * ((m_max + 3) & ~1) * elem);
+}
+// Cooperative launch of one grid-mode group: gd[f].cta0 ascending, total_ctas
+// = sum of ctas (all resident at once or the launch fails).
+template <typename T>
+cudaError_t launch_qrcp_grid(const QrcpDesc<T>* d, const QrcpGridDesc* gd, int count, int total_ctas, double eps,
+                             int nl_max, int m_max, cudaStream_t st);
+// CTAs of the grid-mode QRCP that fit on the device at once (SM count x
+// resident CTAs per SM at the given dynamic shared memory, element size elem),
+// at most one per thread of a CTA
+int qrcp_grid_capacity(int smem_bytes, int elem);
+// 1 if a grid-mode wait expired since the last call (then cleared)
+int qrcp_take_timeout();
+
 // Launch shape measured by the autotuner for matrices of this size class
 // (autotune.cu): 0 = not tuned, 1..16 = CTAs with shared-memory slabs, 32 = 16
 // CTAs over a global work copy.
 int qrcp_tuned_choice(int elem, int m, int n);
 
 inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, int elem, int limit,
-                      std::vector<QrcpGroup>& out, std::vector<char>& needs_work) {
+                      std::vector<QrcpGroup>& out, std::vector<char>& needs_work, int grid_ctas = 0,
+                      bool force_grid = false) {
   const int nmat = (int)ms.size();
   needs_work.assign((size_t)nmat, 0);
   std::vector<int> cs((size_t)nmat), order;
   std::vector<char> slab((size_t)nmat);
   // warp groups first: small matrices, one warp each, packed 8 per CTA
-  std::vector<int> rest;
+  std::vector<int> rest, gridm;
   {
     QrcpGroup wg;
     wg.cs = 0;
@@ -188,6 +224,11 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
     if (!wg.idx.empty()) out.push_back(wg);
   }
   for (int i : rest) {
+    if (force_grid && grid_ctas > 16 &&
+        qrcp_smem_bytes(ms[(size_t)i], (ns[(size_t)i] + grid_ctas - 1) / grid_ctas, elem, true) <= limit) {
+      gridm.push_back(i);
+      continue;
+    }
     int c = 1;
     while (c < 16 && qrcp_smem_bytes(ms[(size_t)i], (ns[(size_t)i] + c - 1) / c, elem, true) > limit) c *= 2;
     const int tuned = qrcp_tuned_choice(elem, ms[(size_t)i], ns[(size_t)i]);
@@ -196,6 +237,10 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
     if (tuned != 32 && qrcp_smem_bytes(ms[(size_t)i], nl, elem, true) <= limit) {
       cs[(size_t)i] = c;
       slab[(size_t)i] = 1;
+    } else if (tuned != 32 && grid_ctas > 16 &&
+               qrcp_smem_bytes(ms[(size_t)i], (ns[(size_t)i] + grid_ctas - 1) / grid_ctas, elem, true) <= limit) {
+      gridm.push_back(i);  // slabs in shared memory over more CTAs than a cluster holds
+      continue;
     } else {
       cs[(size_t)i] = 16;
       slab[(size_t)i] = 0;
@@ -203,6 +248,20 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
       if (!qrcp_panel_depth(ms[(size_t)i], (ns[(size_t)i] + 15) / 16, elem, limit)) return false;
     }
     order.push_back(i);
+  }
+  // FP64 pivoted QR is bound by the FP64 pipe: the delayed-update form on 16
+  // SMs per matrix runs at about twice the FP64 efficiency of the CTA groups,
+  // so once more than four such matrices fill the GPU it is the faster choice
+  // (measured on 1 to 12 matrices of 1650 x 879); FP32 takes the groups always
+  if (!force_grid && elem == 8 && gridm.size() > 4) {
+    for (int i : gridm) {
+      cs[(size_t)i] = 16;
+      slab[(size_t)i] = 0;
+      needs_work[(size_t)i] = 1;
+      if (!qrcp_panel_depth(ms[(size_t)i], (ns[(size_t)i] + 15) / 16, elem, limit)) return false;
+      order.push_back(i);
+    }
+    gridm.clear();
   }
   // spread small batches over more SMs: while the batch holds fewer CTAs than
   // the GPU has SMs, double the cluster of the largest shared-memory problems
@@ -264,6 +323,60 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
   }
   for (auto& g : out)
     if (!g.slab && g.cs > 0) g.nb = qrcp_panel_depth(g.m_max, g.nl_max, elem, limit);
+  // grid mode: each matrix takes the fewest CTAs whose slabs fit, matrices are
+  // packed (taller first) into launches of at most grid_ctas CTAs whose common
+  // footprint fits, then each launch spreads its spare CTAs over its widest
+  // members (one CTA at a time, while a member keeps >= 32 columns per CTA)
+  if (!gridm.empty()) {
+    std::sort(gridm.begin(), gridm.end(), [&](int a, int b) {
+      return ms[(size_t)a] != ms[(size_t)b] ? ms[(size_t)a] > ms[(size_t)b] : a < b;
+    });
+    auto min_ctas = [&](int i) {
+      int g = 17;
+      while (g < grid_ctas && qrcp_smem_bytes(ms[(size_t)i], (ns[(size_t)i] + g - 1) / g, elem, true) > limit) ++g;
+      return g;
+    };
+    QrcpGroup* cur = nullptr;
+    int used = 0;
+    for (int i : gridm) {
+      const int g = min_ctas(i);
+      const int nl = (ns[(size_t)i] + g - 1) / g;
+      const bool fits = cur && used + g <= grid_ctas &&
+                        qrcp_smem_bytes(std::max(cur->m_max, ms[(size_t)i]), std::max(cur->nl_max, nl), elem, true) <= limit;
+      if (!fits) {
+        out.emplace_back();
+        cur = &out.back();
+        cur->grid = true;
+        cur->slab = true;
+        cur->cs = 0;
+        used = 0;
+      }
+      cur->idx.push_back(i);
+      cur->ctas.push_back(g);
+      cur->m_max = std::max(cur->m_max, ms[(size_t)i]);
+      cur->nl_max = std::max(cur->nl_max, nl);
+      used += g;
+    }
+    for (auto& g : out) {
+      if (!g.grid) continue;
+      int tot = 0;
+      for (int c : g.ctas) tot += c;
+      bool grew = true;
+      while (tot < grid_ctas && grew) {
+        grew = false;
+        for (size_t q = 0; q < g.idx.size() && tot < grid_ctas; ++q) {
+          const int n = ns[(size_t)g.idx[q]];
+          if (n / (g.ctas[q] + 1) < 32) continue;
+          ++g.ctas[q];
+          ++tot;
+          grew = true;
+        }
+      }
+      g.nl_max = 0;
+      for (size_t q = 0; q < g.idx.size(); ++q)
+        g.nl_max = std::max(g.nl_max, (ns[(size_t)g.idx[q]] + g.ctas[q] - 1) / g.ctas[q]);
+    }
+  }
   return true;
 }
 

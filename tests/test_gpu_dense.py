@@ -71,20 +71,25 @@ def test_front_qr_zero_column_and_rank_one():
         np.testing.assert_allclose(F, ref, atol=1e-12 * max(1.0, np.abs(M).max()))
 
 
+@pytest.mark.parametrize("route", ["cluster", "grid"])
 @pytest.mark.parametrize("eps", [0.0, 1e-3, 1e-8])
-def test_qrcp_batch_matches_oracle(eps):
+def test_qrcp_batch_matches_oracle(eps, route):
+    """route "grid": every matrix taller than 64 rows runs on a group of >= 17
+    CTAs exchanging through global memory (9 columns over 17 CTAs leaves most
+    of them empty; the batch spans several launches)."""
     import paper_2102_09878_gb300 as sq
 
     rng = np.random.default_rng(2)
     mats = []
     for (m, n, r) in [(12, 30, 12), (40, 25, 25), (20, 20, 8), (7, 100, 7), (60, 9, 9), (1, 1, 1), (30, 30, 4),
-                      (150, 400, 60)]:
+                      (150, 400, 60), (80, 30, 30), (100, 9, 9), (65, 200, 40), (300, 70, 70), (257, 257, 100)]:
         U = rng.standard_normal((m, r))
         Vt = rng.standard_normal((r, n))
         s = np.logspace(0, -10, r)
         mats.append((U * s) @ Vt)
     mats.append(np.zeros((5, 6)))
-    ranks, rows, V, T = sq.dense_qrcp(mats, eps)
+    mats.append(np.zeros((90, 40)))
+    ranks, rows, V, T = sq.dense_qrcp(mats, eps, route=route)
     for i, A in enumerate(mats):
         k, Xf, perm, Vo, To = dn.qrcp(A, eps)
         assert ranks[i] == k, (i, ranks[i], k)
@@ -92,8 +97,10 @@ def test_qrcp_batch_matches_oracle(eps):
             ref = np.zeros((k, A.shape[1]))
             ref[:, perm] = Xf[:k]
             assert _rel(rows[i], ref) < 1e-10, (i, _rel(rows[i], ref))
-        # reflectors of pivots far above the noise are well determined
-        good = np.abs(np.diag(Xf[:k, :k])) > 1e-6 * abs(Xf[0, 0]) if k else []
+        # reflectors of pivots far above the noise are well determined: reflector j
+        # carries an error of about u |R_11| / |R_jj| (u = 1.1e-16), below 1e-10 for
+        # |R_jj| > 1e-5 |R_11|
+        good = np.abs(np.diag(Xf[:k, :k])) > 1e-5 * abs(Xf[0, 0]) if k else []
         if k and good.any():
             j = int(np.argmin(good)) if not good.all() else k
             assert _rel(V[i][:, :j], Vo[:, :j]) < 1e-10 and _rel(T[i][:j], To[:j]) < 1e-10, i
@@ -141,18 +148,21 @@ def test_qrcp_every_cluster_size(m, n):
                     assert _rel(rows[q], ref) < 1e-9
 
 
+@pytest.mark.parametrize("route", ["cluster", "auto"])
 @pytest.mark.parametrize("m,n,eps", [(2000, 600, 0.0), (2000, 600, 1e-3), (1500, 1400, 1e-6), (600, 3000, 1e-8),
                                      (700, 2500, 0.0)])
-def test_qrcp_delayed_update_global_path(m, n, eps):
-    """Matrices too large for the slabs of 16 CTAs: the delayed-update kernel
-    (panels of reflectors applied as one block update), including ranks that
-    stop in the middle of a panel."""
+def test_qrcp_delayed_update_global_path(m, n, eps, route):
+    """Matrices too large for the slabs of 16 CTAs.  route "cluster": the
+    delayed-update kernel (panels of reflectors applied as one block update),
+    including ranks that stop in the middle of a panel; route "auto": slabs in
+    shared memory over CTA groups of up to one CTA per SM (55 to 88 CTAs per
+    matrix here), exchanging through global memory."""
     import paper_2102_09878_gb300 as sq
 
     rng = np.random.default_rng(m + 3 * n)
     r = min(m, n)
     A = (rng.standard_normal((m, r)) * np.logspace(0, -12, r)) @ rng.standard_normal((r, n))
-    ranks, rows, V, T = sq.dense_qrcp([A, A[:, ::-1].copy()], eps)
+    ranks, rows, V, T = sq.dense_qrcp([A, A[:, ::-1].copy()], eps, route=route)
     for q, B in enumerate((A, A[:, ::-1].copy())):
         k, Xf, perm, Vo, To = dn.qrcp(B, eps)
         assert ranks[q] == k, (ranks[q], k)
@@ -182,3 +192,32 @@ def test_qrcp_wide_fp64_shallow_panels():
     ref = np.zeros((k, n))
     ref[:, perm] = Xf[:k]
     assert _rel(rows[0], ref) < 1e-8
+
+
+@pytest.mark.parametrize("route", ["cluster", "grid", "auto"])
+def test_qrcp_f32_matches_oracle(route):
+    """The FP32 pivoted QR of the mixed-precision factorization (FP32 data,
+    norms and pivot decisions in FP32 as in single-precision LAPACK) against the
+    FP64 oracle on matrices whose spectrum leaves no doubt about the rank at
+    eps = 1e-4 (singular values in [1e-2, 1] above a gap to 1e-7): same rank,
+    same pivots, rows and reflectors within FP32 accuracy (5e-4 relative: FP32
+    rounding, 6e-8 per operation, grown by the 1e2 condition of the kept block
+    and by sums of up to 1650 terms).  Shapes cover one warp, clusters, and
+    (route "auto") CTA groups over global memory (1650 x 879)."""
+    import paper_2102_09878_gb300 as sq
+
+    rng = np.random.default_rng(31)
+    mats = []
+    for (m, n, r) in [(60, 40, 25), (300, 200, 120), (257, 700, 150), (800, 300, 200), (1650, 879, 300)]:
+        s = np.concatenate([np.logspace(0, -2, r), 1e-7 * np.ones(min(m, n) - r)])
+        U, _ = np.linalg.qr(rng.standard_normal((m, min(m, n))))
+        W, _ = np.linalg.qr(rng.standard_normal((n, min(m, n))))
+        mats.append((U * s) @ W.T)
+    ranks, rows, V, T = sq.dense_qrcp_f32(mats, 1e-4, route=route)
+    for i, A in enumerate(mats):
+        k, Xf, perm, Vo, To = dn.qrcp(A, 1e-4)
+        assert ranks[i] == k, (i, ranks[i], k)
+        ref = np.zeros((k, A.shape[1]))
+        ref[:, perm] = Xf[:k]
+        assert _rel(rows[i], ref) < 5e-4, (i, _rel(rows[i], ref))
+        assert _rel(V[i], Vo) < 5e-4 and _rel(T[i], To) < 5e-4, i
