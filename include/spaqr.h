@@ -316,7 +316,8 @@ int spaqr_dense_qrcp(int count, double* const* A, const int* m, const int* n, co
  * more than 16 CTAs take a group of up to one CTA per SM, exchanging pivots and
  * reflectors through global memory (cooperative launch; bounded waits end in
  * SPAQR_ERR_TIMEOUT); SPAQR_QRCP_GRID = every matrix above the one-warp size
- * takes such a CTA group (for testing the group form on small matrices).
+ * takes such a CTA group, over a global work copy when even the shared memory
+ * of every SM cannot hold it (for testing the group forms).
  * Results agree with spaqr_dense_qrcp up to rounding. */
 #define SPAQR_QRCP_AUTO 0
 #define SPAQR_QRCP_CLUSTER 1

@@ -240,7 +240,7 @@ int dense_qrcp_route_t(int count, T* const* A, const int* m, const int* n, const
         }
         auto* dgd = static_cast<spaqr::QrcpGridDesc*>(dev_alloc(gd.size() * sizeof(gd[0])));
         SPAQR_CUDA(cudaMemcpyAsync(dgd, gd.data(), gd.size() * sizeof(gd[0]), cudaMemcpyHostToDevice, st));
-        SPAQR_CUDA(spaqr::launch_qrcp_grid<T>(d + off, dgd, (int)part.size(), cta0, eps, g.nl_max, g.m_max, st));
+        SPAQR_CUDA(spaqr::launch_qrcp_grid<T>(d + off, dgd, (int)part.size(), cta0, eps, g.nl_max, g.m_max, g.slab, st));
       } else {
         SPAQR_CUDA(spaqr::launch_qrcp<T>(d + off, (int)part.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st, g.nb));
       }

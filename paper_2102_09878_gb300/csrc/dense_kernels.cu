@@ -964,7 +964,7 @@ __device__ __forceinline__ void add_release(int* p, int v) {
   asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <typename T, int KG>
+template <typename T, int KG, bool SMEM>
 __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T>* descs, const QrcpGridDesc* gds,
                                                              int count, double eps, int nl_max, int m_max) {
   int f = 0;
@@ -1000,7 +1000,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
   int* pos = act + nl_max;
   T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // 2 x vstride
   T* taus = vbuf + 2 * vstride;
-  T* X = taus + vstride;
+  T* X = SMEM ? taus + vstride : d.work + (size_t)j0 * m;  // the slab, or this CTA's columns of the work copy
   __shared__ N s_beta;
   __shared__ T s_tau;
   __shared__ int s_stop, s_piv, s_nact, s_late;
@@ -2245,11 +2245,11 @@ int qrcp_grid_capacity(int smem_bytes, int elem) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
   if (elem == 4) {
-    allow_smem(qrcp_grid_kernel<float, 8>);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, qrcp_grid_kernel<float, 8>, kThreads, smem_bytes);
+    allow_smem(qrcp_grid_kernel<float, 8, true>);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, qrcp_grid_kernel<float, 8, true>, kThreads, smem_bytes);
   } else {
-    allow_smem(qrcp_grid_kernel<double, 8>);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, qrcp_grid_kernel<double, 8>, kThreads, smem_bytes);
+    allow_smem(qrcp_grid_kernel<double, 8, true>);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, qrcp_grid_kernel<double, 8, true>, kThreads, smem_bytes);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -2273,12 +2273,14 @@ int qrcp_take_timeout() {
 
 template <typename T>
 cudaError_t launch_qrcp_grid(const QrcpDesc<T>* d, const QrcpGridDesc* gd, int count, int total_ctas, double eps,
-                             int nl_max, int m_max, cudaStream_t st) {
+                             int nl_max, int m_max, bool smem_slab, cudaStream_t st) {
   if (count <= 0 || total_ctas <= 0) return cudaSuccess;
-  const int smem = qrcp_smem_bytes(m_max, nl_max, (int)sizeof(T), true);
-  static bool init = false;
+  const int smem = qrcp_grid_smem_bytes(m_max, nl_max, (int)sizeof(T), smem_slab);
+  static bool init_s = false, init_g = false;
+  auto kernel = smem_slab ? qrcp_grid_kernel<T, 8, true> : qrcp_grid_kernel<T, 8, false>;
+  bool& init = smem_slab ? init_s : init_g;
   if (!init) {
-    allow_smem(qrcp_grid_kernel<T, 8>);
+    allow_smem(kernel);
     init = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -2291,7 +2293,7 @@ cudaError_t launch_qrcp_grid(const QrcpDesc<T>* d, const QrcpGridDesc* gd, int c
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, qrcp_grid_kernel<T, 8>, d, gd, count, eps, nl_max, m_max);
+  return cudaLaunchKernelEx(&cfg, kernel, d, gd, count, eps, nl_max, m_max);
 }
 
 template <typename T>
@@ -2463,7 +2465,7 @@ cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std
   template cudaError_t launch_front_finish<T>(const FrontDesc<T>*, int, int, cudaStream_t);                   \
   template cudaError_t launch_qrcp<T>(const QrcpDesc<T>*, int, double, int, int, int, bool, cudaStream_t, int); \
   template cudaError_t launch_qrcp_grid<T>(const QrcpDesc<T>*, const QrcpGridDesc*, int, int, double, int, int,    \
-                                           cudaStream_t);                                                         \
+                                           bool, cudaStream_t);                                                   \
   template cudaError_t launch_refl<T>(const ReflDesc<T>*, const int2*, int, cudaStream_t);               \
   template cudaError_t launch_trsm<T>(const TrsmDesc<T>*, const int2*, int, cudaStream_t);               \
   template cudaError_t launch_argmax<T>(const ArgmaxDesc<T>*, const int2*, int, cudaStream_t);

@@ -621,7 +621,7 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
   for (size_t t = 0; t < groups.size(); ++t) {
     const auto& g = groups[t];
     if (g.grid)
-      check(launch_qrcp_grid<T>(dg[t], dgd[t], (int)g.idx.size(), gtot[t], eps, g.nl_max, g.m_max, st_), "qrcp grid");
+      check(launch_qrcp_grid<T>(dg[t], dgd[t], (int)g.idx.size(), gtot[t], eps, g.nl_max, g.m_max, g.slab, st_), "qrcp grid");
     else
       check(launch_qrcp<T>(dg[t], (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st_, g.nb), "qrcp");
   }

@@ -131,6 +131,11 @@ inline int qrcp_smem_bytes(int m, int nl, int elem, bool slab, int nb = kQrcpNB)
     b += 2 * vs + (long long)nl * nb * elem;
   return (int)(b + 64);
 }
+// dynamic shared memory of one grid-mode QRCP CTA: the slab layout, without
+// the slab itself when the columns stay in the work copy
+inline int qrcp_grid_smem_bytes(int m, int nl, int elem, bool slab) {
+  return qrcp_smem_bytes(m, nl, elem, true) - (slab ? 0 : m * nl * elem);
+}
 // deepest panel (16, 8, 4, 2, 1) of the delayed-update QRCP that fits, 0 if none
 inline int qrcp_panel_depth(int m, int nl, int elem, int limit) {
   for (int nb = kQrcpNB; nb >= 1; nb /= 2)
@@ -148,7 +153,7 @@ struct QrcpGroup {
   int m_max = 0, nl_max = 0;
   std::vector<int> idx;
   bool grid = false;      // CTA groups exchanging through global memory (qrcp_grid_kernel)
-  std::vector<int> ctas;  // grid: CTAs of each member (parallel to idx)
+  std::vector<int> ctas;  // grid: CTAs of each member (parallel to idx); slab: shared-memory slabs
 };
 // bytes of one warp's region in the warp-per-matrix QRCP (cs == 0 groups)
 inline int qrcp_warp_bytes(int m, int n, int elem) {
@@ -181,10 +186,12 @@ inline size_t qrcp_grid_xchg_bytes(int ctas, int m_max, int elem) {
          a((size_t)2 * ctas * ((m_max + 3) & ~1) * elem);
 }
 // Cooperative launch of one grid-mode group: gd[f].cta0 ascending, total_ctas
-// = sum of ctas (all resident at once or the launch fails).
+// = sum of ctas (all resident at once or the launch fails).  smem_slab: the
+// column slabs live in shared memory, else in each descriptor's work buffer
+// (m x n, ld m; the kernel copies src there first).
 template <typename T>
 cudaError_t launch_qrcp_grid(const QrcpDesc<T>* d, const QrcpGridDesc* gd, int count, int total_ctas, double eps,
-                             int nl_max, int m_max, cudaStream_t st);
+                             int nl_max, int m_max, bool smem_slab, cudaStream_t st);
 // CTAs of the grid-mode QRCP that fit on the device at once (SM count x
 // resident CTAs per SM at the given dynamic shared memory, element size elem),
 // at most one per thread of a CTA
@@ -205,7 +212,7 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
   std::vector<int> cs((size_t)nmat), order;
   std::vector<char> slab((size_t)nmat);
   // warp groups first: small matrices, one warp each, packed 8 per CTA
-  std::vector<int> rest, gridm;
+  std::vector<int> rest, gridm, gridg;
   {
     QrcpGroup wg;
     wg.cs = 0;
@@ -241,6 +248,9 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
                qrcp_smem_bytes(ms[(size_t)i], (ns[(size_t)i] + grid_ctas - 1) / grid_ctas, elem, true) <= limit) {
       gridm.push_back(i);  // slabs in shared memory over more CTAs than a cluster holds
       continue;
+    } else if (force_grid && grid_ctas > 16 && qrcp_grid_smem_bytes(ms[(size_t)i], 1, elem, false) <= limit) {
+      gridg.push_back(i);  // too large for the slabs of every SM: CTA groups over a work copy
+      continue;
     } else {
       cs[(size_t)i] = 16;
       slab[(size_t)i] = 0;
@@ -253,16 +263,23 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
   // SMs per matrix runs at about twice the FP64 efficiency of the CTA groups,
   // so once more than four such matrices fill the GPU it is the faster choice
   // (measured on 1 to 12 matrices of 1650 x 879); FP32 takes the groups always
-  if (!force_grid && elem == 8 && gridm.size() > 4) {
-    for (int i : gridm) {
+  // Matrices too large for shared memory even over every SM take CTA groups
+  // over a work copy only when forced (measured slower than the delayed form
+  // on the 3D separator blocks: three passes through L2 per step against
+  // about one); at most four share a launch.
+  auto to_delayed = [&](std::vector<int>& v) {
+    for (int i : v) {
       cs[(size_t)i] = 16;
       slab[(size_t)i] = 0;
       needs_work[(size_t)i] = 1;
       if (!qrcp_panel_depth(ms[(size_t)i], (ns[(size_t)i] + 15) / 16, elem, limit)) return false;
       order.push_back(i);
     }
-    gridm.clear();
-  }
+    v.clear();
+    return true;
+  };
+  if (!force_grid && elem == 8 && gridm.size() > 4 && !to_delayed(gridm)) return false;
+  if (!force_grid && gridg.size() > 4 && !to_delayed(gridg)) return false;
   // spread small batches over more SMs: while the batch holds fewer CTAs than
   // the GPU has SMs, double the cluster of the largest shared-memory problems
   // that keep at least 64 columns per CTA
@@ -376,6 +393,39 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
       for (size_t q = 0; q < g.idx.size(); ++q)
         g.nl_max = std::max(g.nl_max, (ns[(size_t)g.idx[q]] + g.ctas[q] - 1) / g.ctas[q]);
     }
+  }
+  // work-copy groups (at most four matrices): one launch, the CTAs shared in
+  // proportion to the column counts (at least 17 each)
+  if (!gridg.empty()) {
+    QrcpGroup g;
+    g.grid = true;
+    g.slab = false;
+    g.cs = 0;
+    long long ntot = 0;
+    for (int i : gridg) ntot += ns[(size_t)i];
+    int used = 0;
+    for (int i : gridg) {
+      int c = (int)std::max<long long>(17, (long long)grid_ctas * ns[(size_t)i] / std::max<long long>(ntot, 1));
+      c = std::min(c, std::max(1, ns[(size_t)i]));
+      c = std::max(c, 1);
+      g.idx.push_back(i);
+      g.ctas.push_back(c);
+      used += c;
+      needs_work[(size_t)i] = 1;
+    }
+    while (used > grid_ctas) {  // trim the largest share
+      size_t q = 0;
+      for (size_t t = 1; t < g.ctas.size(); ++t)
+        if (g.ctas[t] > g.ctas[q]) q = t;
+      --g.ctas[q];
+      --used;
+    }
+    for (size_t q = 0; q < g.idx.size(); ++q) {
+      g.m_max = std::max(g.m_max, ms[(size_t)g.idx[q]]);
+      g.nl_max = std::max(g.nl_max, (ns[(size_t)g.idx[q]] + g.ctas[q] - 1) / g.ctas[q]);
+    }
+    if (qrcp_grid_smem_bytes(g.m_max, g.nl_max, elem, false) > limit) return false;
+    out.push_back(std::move(g));
   }
   return true;
 }
