@@ -246,7 +246,7 @@ HBM_PEAK = 6660.3  # GB/s, MEASURED_PEAKS.json hbm_gbs
 # DRAM bytes of all QRCP launches of one factorization, from one ncu capture of
 # the current kernels (profiles/qrcp_dram_grid2d_1024_mixed.md); empty while the
 # kernels have changed since the last capture
-QRCP_DRAM_BYTES = {}
+QRCP_DRAM_BYTES = {("grid2d_1024", "mixed"): 1.851e9}
 
 
 def family_rooflines(res, precision):
