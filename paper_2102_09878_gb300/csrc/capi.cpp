@@ -229,15 +229,7 @@ int dense_qrcp_route_t(int count, T* const* A, const int* m, const int* n, const
         unsigned char* x = static_cast<unsigned char*>(dev_alloc(bytes));
         SPAQR_CUDA(cudaMemsetAsync(x, 0, bytes, st));
         std::vector<spaqr::QrcpGridDesc> gd;
-        int cta0 = 0;
-        for (int c : g.ctas) {
-          const size_t tb = (std::max<size_t>((size_t)2 * c, 64) * sizeof(int) + 255) & ~size_t(255);
-          const size_t sb = ((size_t)2 * c * sizeof(spaqr::QrcpSlot) + 255) & ~size_t(255);
-          gd.push_back(spaqr::QrcpGridDesc{cta0, c, reinterpret_cast<int*>(x), reinterpret_cast<spaqr::QrcpSlot*>(x + tb),
-                                           x + tb + sb});
-          x += spaqr::qrcp_grid_xchg_bytes(c, g.m_max, (int)sizeof(T));
-          cta0 += c;
-        }
+        const int cta0 = spaqr::qrcp_grid_descs(g.ctas, g.m_max, (int)sizeof(T), x, gd);
         auto* dgd = static_cast<spaqr::QrcpGridDesc*>(dev_alloc(gd.size() * sizeof(gd[0])));
         SPAQR_CUDA(cudaMemcpyAsync(dgd, gd.data(), gd.size() * sizeof(gd[0]), cudaMemcpyHostToDevice, st));
         SPAQR_CUDA(spaqr::launch_qrcp_grid<T>(d + off, dgd, (int)part.size(), cta0, eps, g.nl_max, g.m_max, g.slab, st));

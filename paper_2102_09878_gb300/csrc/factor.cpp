@@ -606,15 +606,7 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
     work_bufs.push_back(reinterpret_cast<T*>(x));
     SPAQR_CUDA(cudaMemsetAsync(x, 0, bytes, st_));
     std::vector<QrcpGridDesc> gd;
-    int cta0 = 0;
-    for (int c : g.ctas) {
-      const size_t tb = (std::max<size_t>((size_t)2 * c, 64) * sizeof(int) + 255) & ~size_t(255);
-      const size_t sb = ((size_t)2 * c * sizeof(QrcpSlot) + 255) & ~size_t(255);
-      gd.push_back(QrcpGridDesc{cta0, c, reinterpret_cast<int*>(x), reinterpret_cast<QrcpSlot*>(x + tb), x + tb + sb});
-      x += qrcp_grid_xchg_bytes(c, g.m_max, (int)sizeof(T));
-      cta0 += c;
-    }
-    gtot[t] = cta0;
+    gtot[t] = qrcp_grid_descs(g.ctas, g.m_max, (int)sizeof(T), x, gd);
     dgd[t] = up_.put(gd);
   }
   tm_.begin(st_, 2);

@@ -179,11 +179,30 @@ struct QrcpGridDesc {
   QrcpSlot* slots;  // 2 x ctas
   void* vg;
 };
-// bytes of the exchange area of one grid-mode matrix (tags first)
+// Exchange area of one grid-mode matrix: the counters (at least 64 ints, so
+// that ints 0 and 32 exist), the slots, the reflector buffers, each part
+// starting on a 256-byte boundary.
+inline size_t qrcp_grid_tag_bytes(int ctas) {
+  return (std::max<size_t>((size_t)2 * ctas, 64) * sizeof(int) + 255) & ~size_t(255);
+}
+inline size_t qrcp_grid_slot_bytes(int ctas) { return ((size_t)2 * ctas * sizeof(QrcpSlot) + 255) & ~size_t(255); }
 inline size_t qrcp_grid_xchg_bytes(int ctas, int m_max, int elem) {
-  auto a = [](size_t b) { return (b + 255) & ~size_t(255); };
-  return a(std::max<size_t>((size_t)2 * ctas, 64) * sizeof(int)) + a((size_t)2 * ctas * sizeof(QrcpSlot)) +
-         a((size_t)2 * ctas * ((m_max + 3) & ~1) * elem);
+  return qrcp_grid_tag_bytes(ctas) + qrcp_grid_slot_bytes(ctas) +
+         (((size_t)2 * ctas * ((m_max + 3) & ~1) * elem + 255) & ~size_t(255));
+}
+// descriptors of one grid-mode group whose exchange areas are laid out back to
+// back from x (qrcp_grid_xchg_bytes each); returns the total CTA count
+inline int qrcp_grid_descs(const std::vector<int>& ctas, int m_max, int elem, unsigned char* x,
+                           std::vector<QrcpGridDesc>& out) {
+  out.clear();
+  int cta0 = 0;
+  for (int c : ctas) {
+    const size_t tb = qrcp_grid_tag_bytes(c), sb = qrcp_grid_slot_bytes(c);
+    out.push_back(QrcpGridDesc{cta0, c, reinterpret_cast<int*>(x), reinterpret_cast<QrcpSlot*>(x + tb), x + tb + sb});
+    x += qrcp_grid_xchg_bytes(c, m_max, elem);
+    cta0 += c;
+  }
+  return cta0;
 }
 // Cooperative launch of one grid-mode group: gd[f].cta0 ascending, total_ctas
 // = sum of ctas (all resident at once or the launch fails).  smem_slab: the
