@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
   T* X = SMEM ? taus + ((m_max + 3) & ~1) : d.work + (size_t)j0 * m;
   __shared__ N cand_v;
   __shared__ int cand_j;
-  __shared__ N s_beta;
+  __shared__ double s_beta;
   __shared__ T s_tau;
   __shared__ int s_stop, s_piv, s_nact;
   __shared__ N red_v[kWarps];
@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
   }
   if (threadIdx.x == 0) s_nact = nloc;
   const int kmax = m < n ? m : n;
-  N r11 = N(0);
+  double r11 = 0.0;
   int k = 0;
   __syncthreads();
   // warp-local proposal of the warp's columns (c = warp + kW * (lane + 32 t))
@@ -700,10 +700,11 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
   // proposal and reflector slots alternate between two buffers by step parity,
   // so a CTA never overwrites a slot another CTA may still be reading.
   const int vstride = (m_max + 3) & ~1;
-  __shared__ N cand_v2[2], sp_beta[2];
+  __shared__ N cand_v2[2];
+  __shared__ double sp_beta[2];
   __shared__ int cand_j2[2], sp_stop[2];
   __shared__ T sp_tau[2], s_den;
-  __shared__ N red2[kWarps];
+  __shared__ double red2[kWarps];
   for (int i = 0; i < kmax; ++i) {
     const int par = i & 1;
     T* vb = vbuf + par * vstride;
@@ -729,34 +730,34 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
     // (2) its reflector, rows i..m-1, into vb (the column itself is untouched)
     if (jloc != INT_MAX) {
       const T* col = X + (int64_t)(jloc - j0) * m;
-      N sq = N(0);
+      double sq = 0.0;  // R_ii and the rank test in FP64 whatever the data precision
       for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) {
-        const N v = (N)col[r];
+        const double v = (double)col[r];
         sq += v * v;
       }
       sq = warp_sum(sq);
       if (lane == 0) red2[warp] = sq;
       __syncthreads();
       if (threadIdx.x == 0) {
-        N sig = N(0);
+        double sig = 0.0;
         for (int w = 0; w < kWarps; ++w) sig += red2[w];
-        const N alpha = (N)col[i];
-        N beta, tau;
-        if (sig == N(0)) {
+        const double alpha = (double)col[i];
+        double beta, tau;
+        if (sig == 0.0) {
           beta = alpha;
-          tau = N(0);
+          tau = 0.0;
         } else {
-          const N nrm = sqrt(alpha * alpha + sig);
-          beta = alpha >= N(0) ? -nrm : nrm;
+          const double nrm = sqrt(alpha * alpha + sig);
+          beta = alpha >= 0.0 ? -nrm : nrm;
           tau = (beta - alpha) / beta;
         }
-        const N ab = fabs(beta);
-        const N r11_here = (i == 0) ? ab : r11;
-        const int stop = (beta == N(0) || ab < (N)eps * r11_here) ? 1 : 0;
+        const double ab = fabs(beta);
+        const double r11_here = (i == 0) ? ab : r11;
+        const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
         sp_beta[par] = beta;
         sp_tau[par] = (T)tau;
         sp_stop[par] = stop;
-        s_den = (!stop && sig != N(0)) ? (T)(alpha - beta) : T(0);
+        s_den = (!stop && sig != 0.0) ? (T)(alpha - beta) : T(0);
       }
       __syncthreads();
       const T den = s_den;
@@ -1001,15 +1002,16 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
   T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // 2 x vstride
   T* taus = vbuf + 2 * vstride;
   T* X = SMEM ? taus + vstride : d.work + (size_t)j0 * m;  // the slab, or this CTA's columns of the work copy
-  __shared__ N s_beta;
+  __shared__ double s_beta;
   __shared__ T s_tau;
   __shared__ int s_stop, s_piv, s_nact, s_late;
   __shared__ N red_v[kWarps];
   __shared__ int red_i[kWarps];
-  __shared__ N cand_v2[2], sp_beta[2];
+  __shared__ N cand_v2[2];
+  __shared__ double sp_beta[2];
   __shared__ int cand_j2[2], sp_stop[2];
   __shared__ T sp_tau[2], s_den;
-  __shared__ N red2[kWarps];
+  __shared__ double red2[kWarps];
   __shared__ T s_part[kWarps * KG];  // partial dot products (few-column apply)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
@@ -1039,7 +1041,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
     s_late = 0;
   }
   const int kmax = m < n ? m : n;
-  N r11 = N(0);
+  double r11 = 0.0;
   int k = 0;
   __syncthreads();
   N wv = N(-1);
@@ -1086,34 +1088,34 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
     // (2) its reflector, rows i..m-1, into vb and the CTA's global slot
     if (jloc != INT_MAX) {
       const T* col = X + (int64_t)(jloc - j0) * m;
-      N sq = N(0);
+      double sq = 0.0;  // R_ii and the rank test in FP64 whatever the data precision
       for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) {
-        const N v = (N)col[r];
+        const double v = (double)col[r];
         sq += v * v;
       }
       sq = warp_sum(sq);
       if (lane == 0) red2[warp] = sq;
       __syncthreads();
       if (threadIdx.x == 0) {
-        N sig = N(0);
+        double sig = 0.0;
         for (int w = 0; w < kWarps; ++w) sig += red2[w];
-        const N alpha = (N)col[i];
-        N beta, tau;
-        if (sig == N(0)) {
+        const double alpha = (double)col[i];
+        double beta, tau;
+        if (sig == 0.0) {
           beta = alpha;
-          tau = N(0);
+          tau = 0.0;
         } else {
-          const N nrm = sqrt(alpha * alpha + sig);
-          beta = alpha >= N(0) ? -nrm : nrm;
+          const double nrm = sqrt(alpha * alpha + sig);
+          beta = alpha >= 0.0 ? -nrm : nrm;
           tau = (beta - alpha) / beta;
         }
-        const N ab = fabs(beta);
-        const N r11_here = (i == 0) ? ab : r11;
-        const int stop = (beta == N(0) || ab < (N)eps * r11_here) ? 1 : 0;
+        const double ab = fabs(beta);
+        const double r11_here = (i == 0) ? ab : r11;
+        const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
         sp_beta[par] = beta;
         sp_tau[par] = (T)tau;
         sp_stop[par] = stop;
-        s_den = (!stop && sig != N(0)) ? (T)(alpha - beta) : T(0);
+        s_den = (!stop && sig != 0.0) ? (T)(alpha - beta) : T(0);
         QrcpSlot* sl = slots + (size_t)par * G + rank;
         sl->v = cand_v2[par];
         sl->beta = beta;
@@ -1200,7 +1202,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
       if (threadIdx.x == 0) {
         const QrcpSlot* sl = slots + (size_t)par * G + owner;
         s_tau = (T)__ldcg(&sl->tau);
-        s_beta = (N)__ldcg(&sl->beta);
+        s_beta = __ldcg(&sl->beta);
         s_stop = __ldcg(&sl->stop);
       }
     } else if (threadIdx.x == 0) {
