@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
   const int j0 = min(n, rank * nl), j1 = min(n, j0 + nl);
   const int nloc = j1 - j0;
   extern __shared__ __align__(16) unsigned char smraw[];
-  using N = T;  // norms, pivots and reflector scalars in the data's precision
+  using N = T;  // partial column norms and pivot proposals in the data's precision
   N* nu = reinterpret_cast<N*>(smraw);  // nl_max
   N* nuref = nu + nl_max;               // nl_max
   int* step_of = reinterpret_cast<int*>(nuref + nl_max);  // nl_max
@@ -993,7 +993,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
   QrcpSlot* slots = gd.slots;                 // [2][G]
   T* vg = static_cast<T*>(gd.vg);             // [2][G][vstride]
   extern __shared__ __align__(16) unsigned char smraw[];
-  using N = T;  // norms, pivots and reflector scalars in the data's precision
+  using N = T;  // partial column norms and pivot proposals in the data's precision
   N* nu = reinterpret_cast<N*>(smraw);
   N* nuref = nu + nl_max;
   int* step_of = reinterpret_cast<int*>(nuref + nl_max);
