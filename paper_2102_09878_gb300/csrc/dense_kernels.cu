@@ -11,6 +11,8 @@
 //  * reflector application, triangular solve X R^{-1}, batched block copies
 //    and the max-norm row assignment (Section 2.2).
 #include <cooperative_groups.h>
+
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -2100,11 +2102,10 @@ cudaError_t launch_identity(const CopyDesc<T>* d, int count, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_front_qr_smem(const FrontDesc<T>* d, int count, int smem_bytes, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  static bool init = false;
-  if (!init) {
+  static std::once_flag init;  // attributes set once, whichever host thread launches first
+  std::call_once(init, [] {
     allow_smem(front_qr_smem_kernel<T>);
-    init = true;
-  }
+  });
   front_qr_smem_kernel<T><<<(unsigned)count, kThreads, (size_t)smem_bytes, st>>>(d);
   return cudaGetLastError();
 }
@@ -2112,11 +2113,10 @@ cudaError_t launch_front_qr_smem(const FrontDesc<T>* d, int count, int smem_byte
 template <typename T>
 cudaError_t launch_front_qr_warp(const FrontDesc<T>* d, int count, int per_warp_elems, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  static bool init = false;
-  if (!init) {
+  static std::once_flag init;  // attributes set once, whichever host thread launches first
+  std::call_once(init, [] {
     allow_smem(front_qr_warp_kernel<T>);
-    init = true;
-  }
+  });
   const size_t smem = (size_t)per_warp_elems * sizeof(T) * kWarps;
   front_qr_warp_kernel<T><<<(unsigned)((count + kWarps - 1) / kWarps), kThreads, smem, st>>>(d, count, per_warp_elems);
   return cudaGetLastError();
@@ -2137,12 +2137,11 @@ cudaError_t launch_front_panel(const FrontDesc<T>* d, int count, int j0, int nb,
     front_panel_kernel<T><<<(unsigned)count, kThreads, 0, st>>>(d, j0, nb, Tbuf);
     return cudaGetLastError();
   }
-  static bool init = false;
-  if (!init) {
+  static std::once_flag init;  // attributes set once, whichever host thread launches first
+  std::call_once(init, [] {
     allow_smem(front_panel_cluster_kernel<T>);
     cudaFuncSetAttribute(front_panel_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    init = true;
-  }
+  });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(count * cs));
   cfg.blockDim = dim3(kThreads);
@@ -2174,14 +2173,13 @@ cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, cud
 }
 
 template <typename T>
-static cudaError_t launch_cluster(void (*kernel)(const QrcpDesc<T>*, double, int, int), bool& init, unsigned grid,
+static cudaError_t launch_cluster(void (*kernel)(const QrcpDesc<T>*, double, int, int), std::once_flag& init, unsigned grid,
                                   int cs, int smem, cudaStream_t st, const QrcpDesc<T>* d, double eps, int nl_max,
                                   int m_max) {
-  if (!init) {
+  std::call_once(init, [kernel] {
     allow_smem(kernel);
     cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    init = true;
-  }
+  });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kThreads);
@@ -2202,11 +2200,10 @@ cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int
                         cudaStream_t st, int nb) {
   if (count <= 0) return cudaSuccess;
   if (cs == 0) {  // one warp per matrix; nl_max = per-warp bytes
-    static bool init = false;
-    if (!init) {
+    static std::once_flag init;  // attributes set once, whichever host thread launches first
+    std::call_once(init, [] {
       allow_smem(qrcp_warp_kernel<T>);
-      init = true;
-    }
+    });
     qrcp_warp_kernel<T><<<(unsigned)((count + kWarps - 1) / kWarps), kThreads, (size_t)nl_max * kWarps, st>>>(
         d, count, eps, nl_max);
     return cudaGetLastError();
@@ -2214,28 +2211,28 @@ cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int
   const int smem = qrcp_smem_bytes(m_max, nl_max, (int)sizeof(T), smem_slab, nb);
   const unsigned grid = (unsigned)(count * cs);
   if (smem_slab) {
-    static bool init_s = false;
+    static std::once_flag init_s;
     return launch_cluster(qrcp_cluster_kernel<T, true, 8>, init_s, grid, cs, smem, st, d, eps, nl_max, m_max);
   }
   switch (nb) {
     case 16: {
-      static bool i16 = false;
+      static std::once_flag i16;
       return launch_cluster(qrcp_delayed_kernel<T, 16>, i16, grid, cs, smem, st, d, eps, nl_max, m_max);
     }
     case 8: {
-      static bool i8 = false;
+      static std::once_flag i8;
       return launch_cluster(qrcp_delayed_kernel<T, 8>, i8, grid, cs, smem, st, d, eps, nl_max, m_max);
     }
     case 4: {
-      static bool i4 = false;
+      static std::once_flag i4;
       return launch_cluster(qrcp_delayed_kernel<T, 4>, i4, grid, cs, smem, st, d, eps, nl_max, m_max);
     }
     case 2: {
-      static bool i2 = false;
+      static std::once_flag i2;
       return launch_cluster(qrcp_delayed_kernel<T, 2>, i2, grid, cs, smem, st, d, eps, nl_max, m_max);
     }
     default: {
-      static bool i1 = false;
+      static std::once_flag i1;
       return launch_cluster(qrcp_delayed_kernel<T, 1>, i1, grid, cs, smem, st, d, eps, nl_max, m_max);
     }
   }
@@ -2278,13 +2275,9 @@ cudaError_t launch_qrcp_grid(const QrcpDesc<T>* d, const QrcpGridDesc* gd, int c
                              int nl_max, int m_max, bool smem_slab, cudaStream_t st) {
   if (count <= 0 || total_ctas <= 0) return cudaSuccess;
   const int smem = qrcp_grid_smem_bytes(m_max, nl_max, (int)sizeof(T), smem_slab);
-  static bool init_s = false, init_g = false;
+  static std::once_flag init_s, init_g;
   auto kernel = smem_slab ? qrcp_grid_kernel<T, 8, true> : qrcp_grid_kernel<T, 8, false>;
-  bool& init = smem_slab ? init_s : init_g;
-  if (!init) {
-    allow_smem(kernel);
-    init = true;
-  }
+  std::call_once(smem_slab ? init_s : init_g, [kernel] { allow_smem(kernel); });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)total_ctas);
   cfg.blockDim = dim3(kThreads);

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "kernels.h"
@@ -333,12 +334,12 @@ constexpr int kUpdateSmem = 4 * 4096 * (int)sizeof(float);
 constexpr int kProjectSmem = (2 * 4096 + 2 * 1024) * (int)sizeof(float);
 
 void tc_setup() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpdateSmem);
-  cudaFuncSetAttribute(tc_panel_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpdateSmem);
-  cudaFuncSetAttribute(tc_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kProjectSmem);
-  done = true;
+  static std::once_flag done;  // attributes set once, whichever host thread launches first
+  std::call_once(done, [] {
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpdateSmem);
+    cudaFuncSetAttribute(tc_panel_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kUpdateSmem);
+    cudaFuncSetAttribute(tc_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kProjectSmem);
+  });
 }
 
 }  // namespace
