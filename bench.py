@@ -133,6 +133,22 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------------- main
+def reduce_max(value, device=None):
+    """Largest value over all ranks (the timing of the slowest replica)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_seconds(max_secs, world):
+    """Whole-job seconds per problem: `world` independent replicas finish in the
+    slowest rank's time."""
+    return max_secs / world
+
+
 def run_gpu(args, rank, world):
     import numpy as np
     import torch
@@ -212,9 +228,7 @@ def run_gpu(args, rank, world):
                                                                      + prob.vals.nbytes + prob.b.nbytes),
                "d2h_bytes_per_step": int(xh2.nbytes)}
     if dist:
-        t = torch.tensor([secs], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
+        secs = reduce_max(secs, dev)
     compare = None
     if args.compare != "none" and args.compare != args.precision:
         # the other precision on the same workload, same timing (device events over K steps)
@@ -346,7 +360,7 @@ def main():
                              f"(depth {r['depth']}, eps {args.eps}) took {r['seconds']:.2f} s, scaled by M log2 N"}
         except Exception as e:  # pragma: no cover
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
-    value = res["secs"] / world
+    value = job_seconds(res["secs"], world)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["secs"] * 1e3, "higher_is_better": False, "scaling": "weak",
