@@ -47,15 +47,21 @@ def parse():
                     help="also time this precision on the same workload (reported under config.compare)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sample", default="grid2d_128_c3", help="oracle sample for the CPU baseline")
-    return ap.parse_args()
+    ap.add_argument("--sample", default=None,
+                    help="oracle sample for the CPU baseline (default: a 128^2 grid of the workload's family)")
+    args = ap.parse_args()
+    if args.sample is None:
+        args.sample = "invpoisson2d_128" if args.workload.startswith("invpoisson") else "grid2d_128_c3"
+    return args
 
 
 # --------------------------------------------------------------------- oracle
 def _oracle_sample_spec(name):
-    # same family (2D grid, w = 10^U[-3,3]), smaller size; depth from the paper's
-    # default ceil(log2(N/64)) so that leaves keep the full-size leaf size
-    sizes = {"grid2d_64_c3": 64, "grid2d_96_c3": 96, "grid2d_128_c3": 128, "grid2d_160_c3": 160}
+    # same family (2D grid, w = 10^U[-3,3], or the Inverse-Poisson J^T), smaller
+    # size; depth from the paper's default ceil(log2(N/64)) so that leaves keep
+    # the full-size leaf size
+    sizes = {"grid2d_64_c3": 64, "grid2d_96_c3": 96, "grid2d_128_c3": 128, "grid2d_160_c3": 160,
+             "invpoisson2d_64": 64, "invpoisson2d_128": 128}
     nx = sizes[name]
     depth = max(2, math.ceil(math.log2(nx * nx / 64)))
     return nx, depth
@@ -64,14 +70,16 @@ def _oracle_sample_spec(name):
 def oracle_sample_seconds(name: str, eps: float) -> dict:
     """Time the oracle (factor + solve) on the sample in a fresh single-threaded process."""
     nx, depth = _oracle_sample_spec(name)
+    make = ("from inputs.inverse_poisson import inverse_poisson\np = inverse_poisson(%d, 2, seed=0)\n" % nx
+            if name.startswith("invpoisson") else
+            "from inputs.grid_ls import grid_problem\np = grid_problem(%d, %d, 1, 'c3', 0)\n" % (nx, nx))
     code = (
         "import sys,time,json; sys.path.insert(0, %r)\n"
-        "from inputs.grid_ls import grid_problem\n"
+        "%s"
         "from oracle.spaqr import OracleSpaQR\n"
-        "p = grid_problem(%d, %d, 1, 'c3', 0)\n"
         "t = time.perf_counter(); o = OracleSpaQR(p, %d, %r).factor(); x, info = o.solve(p.b); t = time.perf_counter() - t\n"
         "print(json.dumps(dict(seconds=t, iters=info['iters'], m=p.m, n=p.n)))\n"
-    ) % (ROOT, nx, nx, depth, eps)
+    ) % (ROOT, make, depth, eps)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     r = json.loads(out.stdout.strip().splitlines()[-1])
@@ -322,7 +330,7 @@ def main():
         nx, ny, nz = WORKLOADS[args.workload]["dims"]
         n_full = nx * ny * nz
         m_full = (nx - 1) * ny * nz + nx * (ny - 1) * nz + (nx * ny * (nz - 1) if nz > 1 else 0) + n_full
-        sample = "grid2d_64_c3"
+        sample = "invpoisson2d_64" if args.workload.startswith("invpoisson") else "grid2d_64_c3"
         vals = []
         for i in range(args.warmup + args.steps):
             r = oracle_sample_seconds(sample, args.eps)
@@ -367,7 +375,8 @@ def main():
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32-factor/f64-cgls",
         "data": "synthetic",
         "config": {"workload": args.workload, "grid": list(prob.dims), "n": prob.n, "m": prob.m, "depth": res["depth"],
-                   "eps": args.eps, "precision": args.precision, "weights": {"u12": "U[1,2)", "c3": "10^U[-3,3]", "c2": "10^U[-2,2]"}[prob.law], "tol": 1e-10,
+                   "eps": args.eps, "precision": args.precision, "weights": {"u12": "U[1,2)", "c3": "10^U[-3,3]", "c2": "10^U[-2,2]",
+                                                         "ip": "Inverse-Poisson J^T, u ~ U[-1,1), z ~ U[1,2)"}[prob.law], "tol": 1e-10,
                    "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas{world}"},
         "e2e": res["e2e"], "gpu_launches": int(res["launches"]), "clocks": res["clocks"],
         "roofline": roofline(res, args.precision), "cpu_baseline": cpu,

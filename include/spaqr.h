@@ -54,6 +54,11 @@ typedef struct {
   const int64_t* rowptr; /* m + 1 entries */
   const int32_t* colidx; /* nnz entries */
   const double* vals;    /* nnz entries */
+  const int32_t* match;  /* optional (NULL = none), n entries: match[j] = the row matched to column j
+                            (Section 2.2's matching step; distinct rows, each with an entry in its
+                            column); a matched row belongs to its column's cluster, every other row
+                            follows the max-norm rule.  Without it a row with a single entry is
+                            matched by that rule anyway.  Invalid matchings fail with INVALID_ARG. */
 } spaqr_csr;
 
 /* Geometric ordering of a structured grid (Section 4.1, "regular geometric

@@ -41,6 +41,7 @@ class GridProblem:
     b: np.ndarray  # float64, length m
     law: str
     seed: int
+    match: np.ndarray | None = None  # optional row matching: match[j] = the row matched to column j
 
     @property
     def dims(self):
@@ -124,6 +125,10 @@ WORKLOADS = {
     "grid3d_128": dict(dims=(128, 128, 128), law="c3", depth=18),
     # 2D 256x256 of the 1024x1024 family (same leaf size), for kernel profiles.
     "grid2d_256_c3": dict(dims=(256, 256, 1), law="c3", depth=12),
+    # The paper's Inverse-Poisson J^T (inputs/inverse_poisson.py): 2D 1024^2 and 3D 64^3 grids of
+    # equations, random u and z, aspect ratio about 2.
+    "invpoisson2d_1024": dict(dims=(1024, 1024, 1), law="ip", depth=16),
+    "invpoisson3d_64": dict(dims=(64, 64, 64), law="ip", depth=15),
 }
 
 
@@ -131,4 +136,8 @@ def workload(name: str, seed: int = 0) -> tuple[GridProblem, int]:
     """Return (problem, nested-dissection depth) for a named workload."""
     spec = WORKLOADS[name]
     nx, ny, nz = spec["dims"]
+    if spec["law"] == "ip":
+        from inputs.inverse_poisson import inverse_poisson
+
+        return inverse_poisson(nx, 2 if nz == 1 else 3, seed=seed), spec["depth"]
     return grid_problem(nx, ny, nz, spec["law"], seed), spec["depth"]

@@ -11,7 +11,9 @@ these open):
 
 R1  Column scaling (Section 2.7): D = diag(1 / ||A[:, j]||_2), A~ = A D.  The
     row heuristics run on A~ (Section 2.7 scales before it reorders rows).
-R2  Rows (Section 2.2): the vertex row of v is matched to column v; every
+R2  Rows (Section 2.2): a row matched to column v (the problem's matching,
+    prob.match[v] = row, when it has one; otherwise the vertex row of v, which
+    the max-norm rule sends to v's cluster anyway) belongs to v's cluster; every
     other row goes to argmax_c sum_{j in c} A~[r, j]^2, the candidates being
     the clusters it touches that belong to the deepest nested-dissection node
     among them (rows="tree", the default; rows="maxnorm" takes every touched
@@ -193,6 +195,10 @@ class OracleSpaQR:
         assert np.all(cid_of >= 0), "vertex without a cluster"
         self.alive = set(self.slots)
         At = self.At
+        # R2: a row matched to column j belongs to j's cluster (the problem's
+        # matching when it has one, else no row is matched explicitly)
+        match = getattr(self.prob, "match", None)
+        matched = {} if match is None else {int(match[j]): int(cid_of[j]) for j in range(nvert)}
         rows_by = {}
         for r in range(At.shape[0]):
             a, b = At.indptr[r], At.indptr[r + 1]
@@ -200,8 +206,11 @@ class OracleSpaQR:
             vals = At.data[a:b]
             cls = cid_of[cols]
             support = tuple(sorted(set(cls.tolist())))
-            scores = [(c, float(np.sum(vals[cls == c] ** 2))) for c in support]
-            owner = self._argmax_cluster(scores)
+            if r in matched:
+                owner = matched[r]
+            else:
+                scores = [(c, float(np.sum(vals[cls == c] ** 2))) for c in support]
+                owner = self._argmax_cluster(scores)
             rows_by.setdefault((owner, support), []).append(r)
         self.groups = {}
         for (owner, support) in sorted(rows_by):

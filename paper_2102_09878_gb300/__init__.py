@@ -112,10 +112,12 @@ class SpaQR:
         self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int64)
         self._colidx = np.ascontiguousarray(A.colidx, dtype=np.int32)
         self._vals = np.ascontiguousarray(A.vals, dtype=np.float64)
+        match = getattr(A, "match", None)  # optional row matching: match[j] = row of column j
+        self._match = None if match is None else np.ascontiguousarray(match, dtype=np.int32)
 
     def _csr(self):
         return capi.Csr(self.m, self.n, int(self._rowptr[-1]), capi.ptr(self._rowptr), capi.ptr(self._colidx),
-                        capi.ptr(self._vals))
+                        capi.ptr(self._vals), None if self._match is None else capi.ptr(self._match))
 
     # ------------------------------------------------------------- solve
     def solve(self, b, check_convergence: bool = True):

@@ -45,6 +45,7 @@ class Csr(C.Structure):
         ("rowptr", C.c_void_p),
         ("colidx", C.c_void_p),
         ("vals", C.c_void_p),
+        ("match", C.c_void_p),
     ]
 
 

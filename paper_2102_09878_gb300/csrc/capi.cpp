@@ -92,6 +92,18 @@ std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Ana
     if (A->rowptr[r + 1] < A->rowptr[r]) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "rowptr not monotone");
   for (int64_t e = 0; e < A->nnz; ++e)
     if (A->colidx[e] < 0 || A->colidx[e] >= A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "column index out of range");
+  if (A->match) {
+    std::vector<char> used((size_t)A->m, 0);
+    for (int64_t j = 0; j < A->n; ++j) {
+      const int64_t r = A->match[j];
+      if (r < 0 || r >= A->m || used[(size_t)r]) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "match is not a matching");
+      used[(size_t)r] = 1;
+      bool has = false;
+      for (int64_t e = A->rowptr[r]; e < A->rowptr[r + 1] && !has; ++e) has = A->colidx[e] == j;
+      if (!has) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "matched row " + std::to_string(r) + " has no entry in column " +
+                                                              std::to_string(j));
+    }
+  }
   auto hd = std::make_unique<spaqr::Handle>();
   spaqr::Handle& h = *hd;
   h.opt = opt;
@@ -153,6 +165,7 @@ std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Ana
     SPAQR_CUDA(cudaMemcpyAsync(h.d_tperm, tperm.data(), tperm.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
   h.rowptr.assign(A->rowptr, A->rowptr + A->m + 1);
   h.colidx.assign(A->colidx, A->colidx + A->nnz);
+  if (A->match) h.match.assign(A->match, A->match + A->n);
   spaqr::build_apply_plan(h);
   SPAQR_CUDA(cudaStreamSynchronize(h.st));
   int64_t nnzW = 0;
@@ -538,7 +551,7 @@ int spaqr_update_values(spaqr_handle* hh, const spaqr_analysis* an, const double
       } else {
         std::copy(vals, vals + nnz, v.begin());
       }
-      spaqr_csr A{h.m, h.n, h.nnz, h.rowptr.data(), h.colidx.data(), v.data()};
+      spaqr_csr A{h.m, h.n, h.nnz, h.rowptr.data(), h.colidx.data(), v.data(), h.match.empty() ? nullptr : h.match.data()};
       spaqr_options o = h.opt;
       auto fresh = build_handle(&A, *an->an, o);
       hh->h = std::move(fresh);

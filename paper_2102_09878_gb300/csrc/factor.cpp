@@ -18,8 +18,9 @@
 //     merge       relayout of the groups onto the merged clusters (Section 2.6)
 //
 // Readings of the paper (identical to the ones the CPU oracle implements):
-//   column scaling to unit norms, max-norm row rule on A D with ties to the
-//   deeper then lower-id cluster; front rows = own groups (by creation
+//   column scaling to unit norms, rows of the caller's matching to their
+//   column's cluster, the max-norm row rule on A D for every other row with
+//   ties to the deeper then lower-id cluster; front rows = own groups (by creation
 //   number) then the other owners' groups touching s (by owner, number);
 //   rows at positions >= r_s return to their owners, positions c_s..r_s-1 are
 //   reassigned; same-level separators run in rounds of a greedy maximal set of
@@ -704,16 +705,23 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
     }
     return tmp[(size_t)best];
   };
+  // a row matched to column j (the caller's matching) belongs to j's cluster
+  std::vector<int32_t> matched;
+  if (A.match) {
+    matched.assign((size_t)M, -1);
+    for (int64_t j = 0; j < h_.n; ++j) matched[(size_t)A.match[j]] = cl_of[(size_t)j];
+  }
   std::atomic<int64_t> empty_row{-1};
   parallel_for(M, [&](int64_t b, int64_t e, int) {
     std::vector<int> tmp;
     std::vector<double> sc;
     for (int64_t r = b; r < e; ++r) {
-      const int o = row_support(r, tmp, sc);
+      int o = row_support(r, tmp, sc);
       if (o < 0) {
         empty_row.store(r);
         continue;
       }
+      if (!matched.empty() && matched[(size_t)r] >= 0) o = matched[(size_t)r];
       owner[(size_t)r] = o;
       sptr[(size_t)r + 1] = (int64_t)tmp.size();
     }

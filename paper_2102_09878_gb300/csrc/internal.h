@@ -171,6 +171,7 @@ struct Handle {
   double* d_D = nullptr;  // column scaling
   std::vector<int64_t> rowptr;  // host copy of the pattern (for a refactorization)
   std::vector<int32_t> colidx;
+  std::vector<int32_t> match;   // the caller's row matching, if any
   std::vector<double> D;
   // W store
   Arena wpool{size_t(64) << 20};
