@@ -80,10 +80,9 @@ Handle::~Handle() {
 }  // namespace spaqr
 
 namespace {
-// Checks A, factors it and builds the solve-side state (spaqr_factor and the
-// refactorization of spaqr_update_values).
-std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Analysis& a, const spaqr_options& opt) {
-  auto t0 = std::chrono::steady_clock::now();
+// Host-side checks of a matrix and options (before any device work, so that
+// they also answer without a GPU).
+void check_input(const spaqr_csr* A, const spaqr::Analysis& a, const spaqr_options& opt) {
   if (A->n != a.n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A has n != nx*ny*nz columns");
   if (A->m < A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A must have m >= n");
   if (!A->rowptr || !A->colidx || !A->vals) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "null CSR array");
@@ -104,13 +103,24 @@ std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Ana
                                                               std::to_string(j));
     }
   }
+  if (opt.skip < 0) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "skip must be >= 0");
+  if (opt.row_rule != SPAQR_ROWS_TREE && opt.row_rule != SPAQR_ROWS_ANY)
+    throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "unknown row rule");
+  if (!(opt.eps >= 0.0)) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "eps must be >= 0");
+  if (opt.precision != SPAQR_PREC_FP64 && opt.precision != SPAQR_PREC_MIXED)
+    throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "unknown precision");
+  if (opt.mode != SPAQR_MODE_SPAQR && opt.mode != SPAQR_MODE_DIRECT) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "unknown mode");
+  if (opt.step1_qr_width < 0) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "step1_qr_width must be >= 0");
+}
+
+// Checks A, factors it and builds the solve-side state (spaqr_factor and the
+// refactorization of spaqr_update_values).
+std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Analysis& a, const spaqr_options& opt) {
+  auto t0 = std::chrono::steady_clock::now();
+  check_input(A, a, opt);
   auto hd = std::make_unique<spaqr::Handle>();
   spaqr::Handle& h = *hd;
   h.opt = opt;
-  if (h.opt.skip < 0) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "skip must be >= 0");
-  if (h.opt.row_rule != SPAQR_ROWS_TREE && h.opt.row_rule != SPAQR_ROWS_ANY)
-    throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "unknown row rule");
-  if (!(h.opt.eps >= 0.0)) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "eps must be >= 0");
   // all library work runs on a non-blocking stream of its own unless the
   // caller gives one (the legacy default stream cannot be graph-captured)
   h.user_st = static_cast<cudaStream_t>(h.opt.stream);
@@ -315,13 +325,18 @@ int spaqr_analysis_stage_clusters(const spaqr_analysis* an, int k, int32_t* node
 
 int spaqr_factor(const spaqr_csr* A, const spaqr_analysis* an, const spaqr_options* opt, spaqr_handle** out) {
   if (!A || !an || !out) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  spaqr_options o;
+  if (opt)
+    o = *opt;
+  else
+    spaqr_default_options(&o);
+  if (int rc = guarded([&] {
+        check_input(A, *an->an, o);
+        return SPAQR_OK;
+      }))
+    return rc;
   if (int rc = need_device()) return rc;
   return guarded([&] {
-    spaqr_options o;
-    if (opt)
-      o = *opt;
-    else
-      spaqr_default_options(&o);
     auto hd = build_handle(A, *an->an, o);
     auto* out_h = new spaqr_handle();
     out_h->h = std::move(hd);

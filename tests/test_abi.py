@@ -79,3 +79,53 @@ def test_symbolic_analysis_matches_oracle(lib, dims, depth):
         for i, c in enumerate(cl):
             assert c.node == node[i] and c.level == level[i]
             np.testing.assert_array_equal(c.verts, verts[vptr[i] : vptr[i + 1]])
+
+
+def test_factor_checks_its_input_before_the_device(lib):
+    """spaqr_factor validates the matrix, the matching and the options on the
+    host (INVALID_ARG with a message), before it asks for a GPU; valid input
+    on a machine without one then gets NO_DEVICE."""
+    import torch
+
+    import paper_2102_09878_gb300 as sq
+    from inputs.inverse_poisson import inverse_poisson
+    from paper_2102_09878_gb300 import capi
+
+    p = inverse_poisson(8, 2, seed=0)
+    an = sq.Analysis(p.dims, 3)
+
+    def factor(rowptr=None, colidx=None, m=None, match="keep", **opt):
+        rp = np.ascontiguousarray(p.rowptr if rowptr is None else rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(p.colidx if colidx is None else colidx, dtype=np.int32)
+        va = np.ascontiguousarray(p.vals, dtype=np.float64)
+        mt = p.match if isinstance(match, str) else match
+        mt = None if mt is None else np.ascontiguousarray(mt, dtype=np.int32)
+        csr = capi.Csr(p.m if m is None else m, p.n, int(rp[-1]), capi.ptr(rp), capi.ptr(ci), capi.ptr(va),
+                       None if mt is None else capi.ptr(mt))
+        o = capi.default_options()
+        for k, v in opt.items():
+            setattr(o, k, v)
+        h = ctypes.c_void_p()
+        rc = lib.spaqr_factor(ctypes.byref(csr), an.handle, ctypes.byref(o), ctypes.byref(h))
+        return rc, lib.spaqr_last_error().decode()
+
+    bad_rowptr = p.rowptr.copy()
+    bad_rowptr[0] = 1
+    bad_cols = p.colidx.copy()
+    bad_cols[3] = p.n
+    dup = p.match.copy()
+    dup[1] = dup[0]
+    # a row with no entry in column 0: some z row far from grid point 0
+    A = p.to_scipy().tocsc()
+    far = next(r for r in range(p.n, p.m) if A[r, 0] == 0)
+    nomatch = p.match.copy()
+    nomatch[0] = far
+    for kw, msg in [(dict(m=p.n - 1), "m >= n"), (dict(rowptr=bad_rowptr), "rowptr"),
+                    (dict(colidx=bad_cols), "column index"), (dict(match=dup), "matching"),
+                    (dict(match=nomatch), "no entry"), (dict(row_rule=7), "row rule"), (dict(eps=-1.0), "eps"),
+                    (dict(precision=5), "precision"), (dict(step1_qr_width=-1), "step1_qr_width")]:
+        rc, err = factor(**kw)
+        assert rc == 1 and msg in err, (kw.keys(), rc, err)
+    if not torch.cuda.is_available():
+        assert factor()[0] == 8  # SPAQR_ERR_NO_DEVICE
+        assert factor(match=None)[0] == 8
