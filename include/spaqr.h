@@ -130,8 +130,9 @@ int spaqr_analysis_stage_clusters(const spaqr_analysis* an, int k, int32_t* node
  * step 1 (2.5.1) and step 2 (2.5.2), merge (2.6).  A is read from host memory.
  * The handle owns every device allocation.  The analysis must outlive nothing:
  * the handle keeps what it needs.
- * Errors: INVALID_ARG (shape mismatch, n != grid size, m < n), RANK_DEFICIENT,
- * OOM, CUDA, NO_DEVICE. */
+ * Errors: INVALID_ARG (shape mismatch, n != grid size, m < n, a bad CSR pattern,
+ * a match that is not a matching, unknown options; all checked on the host
+ * before any device work), RANK_DEFICIENT, OOM, CUDA, NO_DEVICE, TIMEOUT. */
 typedef struct spaqr_handle spaqr_handle;
 int spaqr_factor(const spaqr_csr* A, const spaqr_analysis* an, const spaqr_options* opt, spaqr_handle** out);
 
