@@ -527,3 +527,61 @@ class OracleSpaQR:
             gamma = gamma_new
             p = s + beta * p
         return D * xt, dict(iters=it, rel=rel, hist=hist, converged=rel < tol)
+
+    def solve_csne(self, b: np.ndarray, tol: float = 1e-10, maxit: int = 100):
+        """Corrected seminormal equations (Section 1, after Bjorck): W^T W
+        xt = A~^T b, then refinement steps xt += W^{-1} W^{-T} A~^T (b - A~ xt)
+        until ||A^T (A x - b)|| / ||A^T b|| < tol with the unscaled A.  With
+        eps = 0 the first solve is exact up to rounding; with eps > 0 the
+        refinement is a stationary iteration that converges when W^T W is
+        close enough to A~^T A~."""
+        At, D = self.At, self.D
+        b = np.asarray(b, dtype=np.float64)
+        xt = np.zeros(At.shape[1])
+        r = b.copy()
+        norm0 = float(np.linalg.norm((At.T @ b) / D))
+        hist = [1.0]
+        if norm0 == 0.0:
+            return xt, dict(iters=0, rel=0.0, hist=hist, converged=True)
+        rel, it = 1.0, 0
+        for it in range(1, maxit + 1):
+            xt += self.apply_Winv(self.apply_WinvT(At.T @ r))
+            r = b - At @ xt
+            rel = float(np.linalg.norm((At.T @ r) / D)) / norm0
+            hist.append(rel)
+            if rel < tol:
+                break
+        return D * xt, dict(iters=it, rel=rel, hist=hist, converged=rel < tol)
+
+
+def solve_diag_cgls(prob, b: np.ndarray, tol: float = 1e-10, maxit: int = 100000):
+    """The paper's "Diag." comparator (Section 4): CGLS preconditioned by the
+    diagonal of A^T A only, i.e. CGLS on A~ = A D with D the column scaling
+    (R1) and no W; same stopping rule as OracleSpaQR.solve."""
+    A = prob.to_scipy()
+    D, At = column_scaling(A)
+    b = np.asarray(b, dtype=np.float64)
+    xt = np.zeros(At.shape[1])
+    r = b.copy()
+    s = At.T @ r
+    norm0 = float(np.linalg.norm(s / D))
+    hist = [1.0]
+    if norm0 == 0.0:
+        return xt, dict(iters=0, rel=0.0, hist=hist, converged=True)
+    p = s.copy()
+    gamma = float(s @ s)
+    rel, it = 1.0, 0
+    for it in range(1, maxit + 1):
+        q = At @ p
+        alpha = gamma / float(q @ q)
+        xt += alpha * p
+        r -= alpha * q
+        s = At.T @ r
+        rel = float(np.linalg.norm(s / D)) / norm0
+        hist.append(rel)
+        if rel < tol:
+            break
+        gamma_new = float(s @ s)
+        p = s + (gamma_new / gamma) * p
+        gamma = gamma_new
+    return D * xt, dict(iters=it, rel=rel, hist=hist, converged=rel < tol)
