@@ -47,6 +47,8 @@ def parse():
                     help="also time this precision on the same workload (reported under config.compare)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None, help="where the nvidia-smi clock samples of the timed region go "
+                                                        "(default: the system temporary directory)")
     ap.add_argument("--sample", default=None,
                     help="oracle sample for the CPU baseline (default: a 128^2 grid of the workload's family)")
     args = ap.parse_args()
@@ -97,10 +99,12 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, directory: str | None = None):
+        import tempfile
+
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(directory or tempfile.gettempdir(), f"spaqr_clocks_rank{index}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -186,7 +190,7 @@ def run_gpu(args, rank, world):
 
         dist.barrier()
     torch.cuda.synchronize()
-    clk = ClockSampler(dev.index)
+    clk = ClockSampler(dev.index, args.clocks_dir)
     clk.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
