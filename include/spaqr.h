@@ -343,8 +343,7 @@ int spaqr_dense_qrcp_f32(int count, float* const* A, const int* m, const int* n,
  * all device memory (a framework's caching allocator, a fixed per-process
  * budget), or latency-critical code that cannot afford the device-wide
  * synchronisation that cudaMalloc and cudaFree may cause.  The paper has no
- * counterpart; it is a deployment variant of the Section 2.5 kernel.
- * It calls no cudaMalloc, cudaFree or allocating library routine: the
+ * counterpart.  It calls no cudaMalloc, cudaFree or allocating library routine: the
  * descriptor array, the rank slots and the work copies of matrices too wide
  * for shared memory live in one static device array of 4 MiB
  * (4,194,304 bytes), reserved on every GPU that loads the library until the
@@ -354,7 +353,8 @@ int spaqr_dense_qrcp_f32(int count, float* const* A, const int* m, const int* n,
  * make that first call before any stream capture.  All calls share the array
  * and it keeps the last call's contents; nothing in it needs to start at
  * zero.  Calls that overlap on the GPU (other streams, other host threads)
- * race on the array: serialise them.  Returns with `stream` synchronised. */
+ * race on the array: serialise them.  Returns with `stream` synchronised.
+ * Host exceptions (a failed host allocation) come back as SPAQR_ERR_OOM. */
 int spaqr_dense_qrcp_static(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
                             double* const* V, double* const* taus, int* rank, void* stream);
 

@@ -26,20 +26,7 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
-template <typename F>
-int guarded(F&& f) {
-  try {
-    return f();
-  } catch (const spaqr::Error& e) {
-    return fail(e.code, e.what());
-  } catch (const std::bad_alloc&) {
-    return fail(SPAQR_ERR_OOM, "host allocation failed");
-  } catch (const std::invalid_argument& e) {
-    return fail(SPAQR_ERR_INVALID_ARG, e.what());
-  } catch (const std::exception& e) {
-    return fail(SPAQR_ERR_CUDA, e.what());
-  }
-}
+using spaqr::guarded;
 
 int need_device() {
   int n = 0;

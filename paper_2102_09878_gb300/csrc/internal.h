@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <new>
 #include <stdexcept>
 #include <string>
 #include <unordered_map>
@@ -188,6 +189,29 @@ struct Handle {
 
 // Message returned by spaqr_last_error() on this thread (capi.cpp).
 void set_last_error(const std::string& msg);
+
+// Runs the body of a C entry point and maps every host exception to a return
+// code, so that none crosses the extern "C" boundary: library errors keep
+// their code, a failed host allocation is SPAQR_ERR_OOM, anything else
+// SPAQR_ERR_CUDA (INVALID_ARG for std::invalid_argument).
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return SPAQR_ERR_OOM;
+  } catch (const std::invalid_argument& e) {
+    set_last_error(e.what());
+    return SPAQR_ERR_INVALID_ARG;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return SPAQR_ERR_CUDA;
+  }
+}
 
 // Factorization entry (factor.cpp): fills h.ops, h.stats, device CSR.
 void run_factor(Handle& h, const spaqr_csr& A, const Analysis& an);

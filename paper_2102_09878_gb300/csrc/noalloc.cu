@@ -51,6 +51,9 @@ int scratch_for_current_device(unsigned char** out) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+int run_static(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
+               double* const* V, double* const* taus, int* rank, void* stream, unsigned char* base);
+
 }  // namespace
 
 extern "C" int spaqr_dense_qrcp_static(int count, double* const* A, const int* m, const int* n, const int* ld,
@@ -65,6 +68,12 @@ extern "C" int spaqr_dense_qrcp_static(int count, double* const* A, const int* m
   }
   unsigned char* base = nullptr;
   if (int rc = scratch_for_current_device(&base)) return rc;
+  return spaqr::guarded([&]() -> int { return run_static(count, A, m, n, ld, eps, V, taus, rank, stream, base); });
+}
+
+namespace {
+int run_static(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,
+               double* const* V, double* const* taus, int* rank, void* stream, unsigned char* base) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int lim = spaqr::max_smem_optin();
   std::vector<int> ms, ns;
@@ -113,3 +122,4 @@ extern "C" int spaqr_dense_qrcp_static(int count, double* const* A, const int* m
   if (e != cudaSuccess) return fail(SPAQR_ERR_CUDA, cudaGetErrorString(e));
   return SPAQR_OK;
 }
+}  // namespace
