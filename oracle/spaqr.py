@@ -127,7 +127,37 @@ class OracleSpaQR:
         g = Group(self.next_gid, owner, rows, blocks)
         self.next_gid += 1
         self.groups[g.gid] = g
+        self._index(g)
         return g
+
+    # Lookup tables only (no arithmetic): the groups each cluster owns and the
+    # groups whose support contains each cluster.  A group's support changes
+    # only at a merge, which rebuilds both tables.
+    def _index(self, g):
+        self.owned.setdefault(g.owner, set()).add(g.gid)
+        for c in g.blocks:
+            self.touch.setdefault(c, set()).add(g.gid)
+
+    def _del_group(self, gid):
+        g = self.groups.pop(gid)
+        self.owned[g.owner].discard(gid)
+        for c in g.blocks:
+            self.touch[c].discard(gid)
+
+    def _reindex(self):
+        self.owned, self.touch = {}, {}
+        for g in self.groups.values():
+            self._index(g)
+
+    def _owned_by(self, c):
+        return sorted((self.groups[i] for i in self.owned.get(c, ())), key=lambda g: g.gid)
+
+    def _touching(self, c):
+        """Groups of other owners whose support contains c, by (owner, number)."""
+        return sorted(
+            (self.groups[i] for i in self.touch.get(c, ()) if self.groups[i].owner != c),
+            key=lambda g: (g.owner, g.gid),
+        )
 
     def _argmax_cluster(self, scores):
         """R2/R4 max-norm rule with the deeper-then-lower-id tie break."""
@@ -212,7 +242,7 @@ class OracleSpaQR:
                 scores = [(c, float(np.sum(vals[cls == c] ** 2))) for c in support]
                 owner = self._argmax_cluster(scores)
             rows_by.setdefault((owner, support), []).append(r)
-        self.groups = {}
+        self.groups, self.owned, self.touch = {}, {}, {}
         for (owner, support) in sorted(rows_by):
             rlist = rows_by[(owner, support)]
             blocks = {c: np.zeros((len(rlist), self.slots[c].size)) for c in support}
@@ -223,12 +253,7 @@ class OracleSpaQR:
             self._new_group(owner, len(rlist), blocks)
 
     def _front_groups(self, s):
-        own = sorted((g for g in self.groups.values() if g.owner == s), key=lambda g: g.gid)
-        oth = sorted(
-            (g for g in self.groups.values() if g.owner != s and s in g.blocks),
-            key=lambda g: (g.owner, g.gid),
-        )
-        return own, oth
+        return self._owned_by(s), self._touching(s)
 
     @staticmethod
     def _greedy_colour(items, conflicts):
@@ -298,7 +323,7 @@ class OracleSpaQR:
             )
         roffs = offs[1:] - offs[1]
         for g in fg:
-            del self.groups[g.gid]
+            self._del_group(g.gid)
         # rows at positions r_s.. go back to their owners (R4)
         pos = rs
         owners = sorted({g.owner for g in oth})
@@ -325,7 +350,7 @@ class OracleSpaQR:
             cp = self.slots[p].size
             if cp == 0:
                 continue
-            own = sorted((g for g in self.groups.values() if g.owner == p), key=lambda g: g.gid)
+            own = self._owned_by(p)
             rp = sum(g.rows for g in own)
             if rp < cp:
                 raise RankDeficient(f"interface {p}: {rp} rows < {cp} columns")
@@ -342,7 +367,7 @@ class OracleSpaQR:
             self.stats.scale.append((k, rp, cp))
             self.ops.append(Op("Rp", k, self.slots[p].copy(), R=Rpp))
             for g in own:
-                del self.groups[g.gid]
+                self._del_group(g.gid)
             rest = cols[1:]
             roffs = offs[1:] - offs[1]
             b1 = self._split(F[:cp, cp:], rest, roffs)
@@ -350,10 +375,9 @@ class OracleSpaQR:
             self.p1_of[p] = self._new_group(p, cp, b1).gid
             if rp > cp and rest:
                 self.p2_of[p] = self._new_group(p, rp - cp, self._split(F[cp:, cp:], rest, roffs)).gid
-            for g in self.groups.values():
-                if g.owner != p and p in g.blocks:
-                    # X <- X R_pp^{-1}  (solve Y R_pp = X)
-                    g.blocks[p] = sla.solve_triangular(Rpp, g.blocks[p].T, trans="T", lower=False).T
+            for g in self._touching(p):
+                # X <- X R_pp^{-1}  (solve Y R_pp = X)
+                g.blocks[p] = sla.solve_triangular(Rpp, g.blocks[p].T, trans="T", lower=False).T
 
     def _step1(self, k):
         for p in sorted(self.p2_of):
@@ -364,7 +388,7 @@ class OracleSpaQR:
             self.stats.step1.append((k, X.shape[0], X.shape[1], kk))
             if kk < g.rows:
                 if kk == 0:
-                    del self.groups[g.gid]
+                    self._del_group(g.gid)
                     continue
                 g.blocks = self._split(Rrows, cols, offs)
                 g.rows = kk
@@ -383,10 +407,7 @@ class OracleSpaQR:
 
     def _step2_one(self, k, p, g1, col):
         cp = self.slots[p].size
-        nb = sorted(
-            (g for g in self.groups.values() if g.owner != p and p in g.blocks),
-            key=lambda g: (g.owner, g.gid),
-        )
+        nb = self._touching(p)
         Anp = np.vstack([g.blocks[p] for g in nb]) if nb else np.zeros((0, cp))
         ncols = sorted(c for c in g1.blocks if c != p)
         Ap1n = np.hstack([g1.blocks[c] for c in ncols]) if ncols else np.zeros((cp, 0))
@@ -404,7 +425,7 @@ class OracleSpaQR:
         g1.rows = kk
         self.slots[p] = self.slots[p][:kk]
         if kk == 0:
-            del self.groups[g1.gid]
+            self._del_group(g1.gid)
 
     def _merge(self, k):
         new = nd.clusters_at_stage(self.nodes, self.keys, self.L, k - 1)
@@ -425,6 +446,7 @@ class OracleSpaQR:
                     [g.blocks[c] if c in g.blocks else np.zeros((g.rows, self.slots[c].size)) for c in children[P]]
                 )
             g.blocks = nb
+        self._reindex()
         self.clusters = new
         self.slots = slots
         self.level = {P: new[P].level for P in slots}
