@@ -111,8 +111,19 @@ def column_scaling(A: sp.csr_matrix):
 
 
 class OracleSpaQR:
-    def __init__(self, prob, depth: int, eps: float, skip: int = 2, mode: str = "spaqr", rows: str = "tree"):
+    def __init__(self, prob, depth: int, eps: float, skip: int = 2, mode: str = "spaqr", rows: str = "tree",
+                 within: str = "asc"):
         self.rows_rule = rows
+        # Order inside one elimination round (R5) and one step-2 colour (R8):
+        # "asc" (the reading) or "desc".  Members of a round or a colour are
+        # independent, so both orders give identical results; tests use
+        # "desc" to check that independence.
+        self.within = within
+        # Records for tests (no arithmetic): the owner cluster of every row at
+        # the finest stage, and (stage, cluster, position, destination) of
+        # every extra row sent on by the max-norm rule (R4).
+        self.row_owner = None
+        self.extra_dest = []
         self.prob = prob
         self.L = depth
         self.eps = eps
@@ -230,6 +241,7 @@ class OracleSpaQR:
         match = getattr(self.prob, "match", None)
         matched = {} if match is None else {int(match[j]): int(cid_of[j]) for j in range(nvert)}
         rows_by = {}
+        self.row_owner = np.full(At.shape[0], -1, dtype=np.int64)
         for r in range(At.shape[0]):
             a, b = At.indptr[r], At.indptr[r + 1]
             cols = At.indices[a:b]
@@ -242,6 +254,7 @@ class OracleSpaQR:
                 scores = [(c, float(np.sum(vals[cls == c] ** 2))) for c in support]
                 owner = self._argmax_cluster(scores)
             rows_by.setdefault((owner, support), []).append(r)
+            self.row_owner[r] = owner
         self.groups, self.owned, self.touch = {}, {}, {}
         for (owner, support) in sorted(rows_by):
             rlist = rows_by[(owner, support)]
@@ -282,6 +295,8 @@ class OracleSpaQR:
                     continue
                 used |= ids
                 batch.append((s, own, oth))
+            if self.within == "desc":
+                batch = batch[::-1]
             for s, own, oth in batch:
                 self._eliminate_one(k, s, own, oth, rnd)
                 taken.add(s)
@@ -339,7 +354,9 @@ class OracleSpaQR:
                     (c, float(np.sum(F[i, cs + roffs[t] : cs + roffs[t + 1]] ** 2)))
                     for t, c in enumerate(rest)
                 ]
-                dest.setdefault(self._argmax_cluster(scores), []).append(i)
+                c_to = self._argmax_cluster(scores)
+                dest.setdefault(c_to, []).append(i)
+                self.extra_dest.append((k, s, i, c_to))
             for c in sorted(dest):
                 idx = dest[c]
                 self._new_group(c, len(idx), self._split(F[idx, cs:], rest, roffs))
@@ -402,7 +419,8 @@ class OracleSpaQR:
         colour = self._greedy_colour(ps, conflicts)
         ncol = max(colour.values()) + 1 if colour else 0
         for col in range(ncol):
-            for p in [q for q in ps if colour[q] == col]:
+            members = [q for q in ps if colour[q] == col]
+            for p in (members[::-1] if self.within == "desc" else members):
                 self._step2_one(k, p, p1[p], col)
 
     def _step2_one(self, k, p, g1, col):
