@@ -337,6 +337,19 @@ int spaqr_dense_qrcp_route(int count, double* const* A, const int* m, const int*
 int spaqr_dense_qrcp_f32(int count, float* const* A, const int* m, const int* n, const int* ld, double eps,
                          float* const* V, float* const* taus, int* rank, int route, void* stream);
 
+/* spaqr_debug_set_qrcp_wait: failure-detection hook for tests.  The CTA
+ * groups of the column-pivoted QR (the SPAQR_QRCP_GRID / AUTO forms above and
+ * the factorization's large matrices) exchange pivots through arrival
+ * counters in global memory; every wait on a counter gives up after `cycles`
+ * SM clock cycles (<= 0 restores the default, about 2 s at the maximum SM
+ * clock), writes rank -1 for its matrix and returns, and the host then
+ * reports SPAQR_ERR_TIMEOUT.  missing_arrivals > 0 makes every wait expect
+ * that many arrivals more than there are CTAs, so that it expires without
+ * fail (the CUDA context stays usable); 0 restores normal operation.
+ * Process-wide; affects launches issued after the call.  Host only; always
+ * returns SPAQR_OK. */
+int spaqr_debug_set_qrcp_wait(long long cycles, int missing_arrivals);
+
 /* spaqr_dense_qrcp_static: the same batched column-pivoted QR as
  * spaqr_dense_qrcp (same arguments, same results), for callers that cannot
  * allocate device memory: code that runs under a memory manager which owns

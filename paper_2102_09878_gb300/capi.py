@@ -25,6 +25,8 @@ ERRORS = {
     7: "OOM",
     8: "NO_DEVICE",
 }
+SPAQR_ERR_INVALID_ARG, SPAQR_ERR_RANK_DEFICIENT, SPAQR_ERR_CAPACITY, SPAQR_ERR_NOT_CONVERGED = 1, 2, 3, 4
+SPAQR_ERR_TIMEOUT, SPAQR_ERR_CUDA, SPAQR_ERR_OOM, SPAQR_ERR_NO_DEVICE = 5, 6, 7, 8
 PREC = {"fp64": 0, "mixed": 1}
 MODE = {"spaqr": 0, "direct": 1}
 ROWS = {"tree": 0, "maxnorm": 1}
@@ -158,6 +160,7 @@ SIGNATURES = {
         [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
          C.c_int, C.c_void_p],
     ),
+    "spaqr_debug_set_qrcp_wait": (C.c_int, [C.c_longlong, C.c_int]),
     "spaqr_dense_qrcp_static": (
         C.c_int,
         [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,

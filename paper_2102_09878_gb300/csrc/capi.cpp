@@ -62,6 +62,7 @@ Handle::~Handle() {
   cudaFree(d_tvals);
   cudaFree(d_D);
   cudaFree(d_work);
+  cudaFree(d_flag);
   if (own_stream && st) cudaStreamDestroy(st);
 }
 }  // namespace spaqr
@@ -250,7 +251,9 @@ int dense_qrcp_route_t(int count, T* const* A, const int* m, const int* n, const
     }
     SPAQR_CUDA(cudaMemcpyAsync(rank, d_rank, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st));
     SPAQR_CUDA(cudaStreamSynchronize(st));
-    if (spaqr::qrcp_take_timeout()) return fail(SPAQR_ERR_TIMEOUT, "column-pivoted QR exchange wait timed out");
+    for (int i = 0; i < count; ++i)  // only an expired exchange wait writes a negative rank
+      if (rank[i] < 0)
+        return fail(SPAQR_ERR_TIMEOUT, "column-pivoted QR exchange wait timed out (matrix " + std::to_string(i) + ")");
     return SPAQR_OK;
   });
 }
@@ -670,11 +673,17 @@ int dense_front_qr_t(int count, T* const* A, const int* m, const int* n, const i
       SPAQR_CUDA(cudaMalloc(&tc, tcb));
       frees.push_back(tc);
     }
+    int* flag = nullptr;  // this call's tensor-core timeout flag
+    SPAQR_CUDA(cudaMalloc(&flag, sizeof(int)));
+    frees.push_back(flag);
+    SPAQR_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
     int64_t launches = 0;
-    SPAQR_CUDA(spaqr::launch_front_groups<T>(groups, dev, host, Tbuf, st, &launches, tc));
+    SPAQR_CUDA(spaqr::launch_front_groups<T>(groups, dev, host, Tbuf, st, &launches, tc, flag));
+    int late = 0;
+    SPAQR_CUDA(cudaMemcpyAsync(&late, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     SPAQR_CUDA(cudaStreamSynchronize(st));
     for (void* p : frees) cudaFree(p);
-    if (spaqr::tc_take_timeout()) return fail(SPAQR_ERR_TIMEOUT, "tensor-core MMA completion wait timed out");
+    if (late) return fail(SPAQR_ERR_TIMEOUT, "tensor-core MMA completion wait timed out");
     return SPAQR_OK;
   });
 }
@@ -699,11 +708,23 @@ int spaqr_dense_tc_gemm(int m, int n, int k, const float* A, int lda, const floa
   if (int rc = need_device()) return rc;
   return guarded([&] {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    SPAQR_CUDA(spaqr::launch_tc_gemm(m, n, k, A, lda, B, ldb, C, ldc, st));
-    SPAQR_CUDA(cudaStreamSynchronize(st));
-    if (spaqr::tc_take_timeout()) return fail(SPAQR_ERR_TIMEOUT, "tensor-core MMA completion wait timed out");
+    int* flag = nullptr;  // this call's tensor-core timeout flag
+    SPAQR_CUDA(cudaMalloc(&flag, sizeof(int)));
+    int late = 0;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = spaqr::launch_tc_gemm(m, n, k, A, lda, B, ldb, C, ldc, flag, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&late, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(flag);
+    SPAQR_CUDA(e);
+    if (late) return fail(SPAQR_ERR_TIMEOUT, "tensor-core MMA completion wait timed out");
     return SPAQR_OK;
   });
+}
+
+int spaqr_debug_set_qrcp_wait(long long cycles, int missing_arrivals) {
+  spaqr::qrcp_grid_set_wait(cycles, missing_arrivals);
+  return SPAQR_OK;
 }
 
 int spaqr_dense_qrcp(int count, double* const* A, const int* m, const int* n, const int* ld, double eps,

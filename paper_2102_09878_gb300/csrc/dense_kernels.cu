@@ -12,6 +12,7 @@
 //    and the max-norm row assignment (Section 2.2).
 #include <cooperative_groups.h>
 
+#include <atomic>
 #include <mutex>
 #include <cuda_runtime.h>
 
@@ -951,12 +952,11 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDes
 // proposal and the speculative reflector of its best column into buffer
 // (i & 1), then adds one to that buffer's arrival counter; every CTA waits
 // until the counter shows all G arrivals of the step (a bounded wait: on
-// expiry it raises g_qrcp_timeout, writes rank -1 and returns), picks the same
+// expiry it raises the matrix's timeout tag, writes rank -1 and returns), picks the same
 // winner and copies the winner's reflector.  A CTA can only reach step i + 2,
 // which rewrites buffer (i & 1), after every CTA has arrived at step i + 1,
 // i.e. after every CTA has finished reading step i.
-__device__ int g_qrcp_timeout = 0;
-constexpr long long kQrcpGridWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
+constexpr int kQrcpLateTag = 48;  // int of a matrix's tag area raised when a wait expired
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -969,7 +969,8 @@ __device__ __forceinline__ void add_release(int* p, int v) {
 
 template <typename T, int KG, bool SMEM>
 __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T>* descs, const QrcpGridDesc* gds,
-                                                             int count, double eps, int nl_max, int m_max) {
+                                                             int count, double eps, int nl_max, int m_max,
+                                                             long long wait_cycles, int missing) {
   int f = 0;
   {
     int lo = 0, hi = count - 1;
@@ -1152,11 +1153,11 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
       add_release(tags + 32 * par, 1);
       // (4) wait for every CTA of the matrix (bounded); the acquire load makes
       // the step's slots and reflectors visible to the CTA after the barrier
-      const int target = G * (i / 2 + 1);
+      const int target = G * (i / 2 + 1) + missing;  // missing > 0 only in failure-path tests
       const long long t0 = clock64();
       int spins = 0;
       while (ld_acquire(tags + 32 * par) < target) {
-        if (((++spins) & 255) == 0 && clock64() - t0 > kQrcpGridWaitCycles) {
+        if (((++spins) & 255) == 0 && clock64() - t0 > wait_cycles) {
           s_late = 1;
           break;
         }
@@ -1165,7 +1166,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
     __syncthreads();
     if (s_late) {
       if (threadIdx.x == 0) {
-        atomicExch(&g_qrcp_timeout, 1);
+        atomicExch(tags + kQrcpLateTag, 1);
         d.rank[0] = -1;
       }
       return;
@@ -1408,7 +1409,8 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
     k = i + 1;
   }
   __syncthreads();
-  if (rank == 0 && threadIdx.x == 0) d.rank[0] = k;
+  // a CTA whose wait expired has written rank -1; keep it
+  if (rank == 0 && threadIdx.x == 0 && ld_acquire(tags + kQrcpLateTag) == 0) d.rank[0] = k;
   if (d.V) {
     for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
       const int r = (int)(e % m), c = (int)(e / m);
@@ -2257,17 +2259,14 @@ int qrcp_grid_capacity(int smem_bytes, int elem) {
   return std::min(sms * per, kThreads);  // the tag wait takes one thread per CTA of a matrix
 }
 
-int qrcp_take_timeout() {
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_qrcp_timeout, sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  if (v) {
-    const int zero = 0;
-    cudaMemcpyToSymbol(g_qrcp_timeout, &zero, sizeof(int));
-  }
-  return v;
+// Wait limit and missing arrivals of the CTA-group exchange (failure-path tests
+// lower the limit and ask for an arrival that never comes).
+std::atomic<long long> g_grid_wait_cycles{kQrcpGridWaitCyclesDefault};
+std::atomic<int> g_grid_missing{0};
+
+void qrcp_grid_set_wait(long long cycles, int missing) {
+  g_grid_wait_cycles.store(cycles > 0 ? cycles : kQrcpGridWaitCyclesDefault);
+  g_grid_missing.store(missing > 0 ? missing : 0);
 }
 
 template <typename T>
@@ -2288,7 +2287,9 @@ cudaError_t launch_qrcp_grid(const QrcpDesc<T>* d, const QrcpGridDesc* gd, int c
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, d, gd, count, eps, nl_max, m_max);
+  const long long wait = g_grid_wait_cycles.load();
+  const int missing = g_grid_missing.load();
+  return cudaLaunchKernelEx(&cfg, kernel, d, gd, count, eps, nl_max, m_max, wait, missing);
 }
 
 template <typename T>
@@ -2325,7 +2326,7 @@ cudaError_t launch_scatter_values(T* base, const int64_t* dest, const T* vals, i
 // stream order).  Returns the descriptors [panel][front] and per-panel offsets.
 template <typename T>
 static size_t tc_group_layout(const std::vector<FrontDesc<T>>& fronts, const T* Tbuf, unsigned char* base,
-                              std::vector<TcPanel>& all, std::vector<size_t>& first) {
+                              std::vector<TcPanel>& all, std::vector<size_t>& first, int* flag = nullptr) {
   constexpr int nb = 32;
   int steps_max = 0;
   for (auto& f : fronts) steps_max = std::max(steps_max, std::min(f.c, f.m));
@@ -2350,6 +2351,7 @@ static size_t tc_group_layout(const std::vector<FrontDesc<T>>& fronts, const T* 
       t.Tm = reinterpret_cast<const float*>(Tbuf) + fi * nb * nb;
       t.ld = f.ld;
       t.j0 = j0;
+      t.flag = flag;
       tc_plan_panel(t);
       t.P = reinterpret_cast<float*>(base) + off;  // offsets relative to the work region, fixed below
       off += tc_panel_scratch(t);
@@ -2380,7 +2382,7 @@ size_t front_groups_tc_bytes(const std::vector<FrontGroup>& groups, const std::v
 template <typename T>
 cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std::vector<const FrontDesc<T>*>& d,
                                 const std::vector<std::vector<FrontDesc<T>>>& host, T* Tbuf, cudaStream_t st,
-                                int64_t* launches, void* tc_scratch) {
+                                int64_t* launches, void* tc_scratch, int* tc_flag) {
   cudaError_t e = cudaSuccess;
   for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
     const FrontGroup& G = groups[g];
@@ -2404,7 +2406,7 @@ cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std
         tc_group_layout<T>(host[g], Tbuf, nullptr, probe, pf);
         const size_t dbytes = (probe.size() * sizeof(TcPanel) + 255) / 256 * 256;
         unsigned char* work = static_cast<unsigned char*>(tc_scratch) + dbytes;
-        tc_group_layout<T>(host[g], Tbuf, work, all, first);
+        tc_group_layout<T>(host[g], Tbuf, work, all, first, tc_flag);
         d_all = static_cast<TcPanel*>(tc_scratch);
         if (!all.empty()) e = cudaMemcpyAsync(d_all, all.data(), all.size() * sizeof(TcPanel), cudaMemcpyHostToDevice, st);
       }
@@ -2446,7 +2448,7 @@ cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std
 #define SPAQR_INST(T)                                                                                     \
   template cudaError_t launch_front_groups<T>(const std::vector<FrontGroup>&, const std::vector<const FrontDesc<T>*>&, \
                                               const std::vector<std::vector<FrontDesc<T>>>&, T*, cudaStream_t,       \
-                                              int64_t*, void*);                                                      \
+                                              int64_t*, void*, int*);                                                \
   template size_t front_groups_tc_bytes<T>(const std::vector<FrontGroup>&,                                          \
                                            const std::vector<std::vector<FrontDesc<T>>>&);                         \
   template cudaError_t launch_scatter_values<T>(T*, const int64_t*, const T*, int64_t, cudaStream_t);    \

@@ -559,7 +559,7 @@ void Factorizer<T>::front_qr(std::vector<FrontDesc<T>>& fr) {
   const size_t tc_bytes = front_groups_tc_bytes<T>(groups, host);
   void* tc_scratch = tc_bytes ? up_.scratch(tc_bytes) : nullptr;
   tm_.begin(st_, 1);
-  check(launch_front_groups<T>(groups, dev, host, Tbuf, st_, &launches_, tc_scratch), "front_qr");
+  check(launch_front_groups<T>(groups, dev, host, Tbuf, st_, &launches_, tc_scratch, h_.d_flag), "front_qr");
   tm_.end(st_);
 }
 
@@ -1343,7 +1343,7 @@ void Factorizer<T>::step1() {
   for (T* w : work) pool_.release(w);
   for (size_t i = 0; i < who.size(); ++i) {
     Group& g = G_[(size_t)who[i]];
-    if (rank[i] < 0 && qrcp_take_timeout())
+    if (rank[i] < 0)  // only an expired exchange wait writes a negative rank
       throw Error(SPAQR_ERR_TIMEOUT, "step 1: column-pivoted QR exchange wait timed out");
     if (rank[i] < 0 || rank[i] > std::min(g.rows, g.width))
       throw Error(SPAQR_ERR_CUDA, "step 1: rank " + std::to_string(rank[i]) + " out of range for a " +
@@ -1529,7 +1529,7 @@ void Factorizer<T>::step2() {
   lap("step2: readback");
   for (size_t i = 0; i < recs.size(); ++i) {
     ks[i] = kall[(size_t)(h_.ops[recs[i].op].kdev - kdev_all)];
-    if (ks[i] < 0 && qrcp_take_timeout())
+    if (ks[i] < 0)  // only an expired exchange wait writes a negative rank
       throw Error(SPAQR_ERR_TIMEOUT, "step 2: column-pivoted QR exchange wait timed out");
     if (ks[i] < 0 || ks[i] > std::min(h_.ops[recs[i].op].c, recs[i].ncm))
       throw Error(SPAQR_ERR_CUDA, "step 2: rank " + std::to_string(ks[i]) + " out of range at stage " +
@@ -1805,16 +1805,20 @@ void Factorizer<T>::run(const spaqr_csr& A) {
 }  // namespace
 
 void run_factor(Handle& h, const spaqr_csr& A, const Analysis& an) {
+  // the handle's timeout flag of the tensor-core kernels, cleared for this factorization
+  if (!h.d_flag) SPAQR_CUDA(cudaMalloc(&h.d_flag, sizeof(int)));
+  SPAQR_CUDA(cudaMemsetAsync(h.d_flag, 0, sizeof(int), h.st));
   if (h.precision == SPAQR_PREC_MIXED) {
     Factorizer<float> f(h, an);
     f.run(A);
-    SPAQR_CUDA(cudaStreamSynchronize(h.st));
-    if (tc_take_timeout()) throw Error(SPAQR_ERR_TIMEOUT, "tensor-core trailing update: MMA completion wait timed out");
   } else {
     Factorizer<double> f(h, an);
     f.run(A);
   }
-  if (qrcp_take_timeout()) throw Error(SPAQR_ERR_TIMEOUT, "column-pivoted QR exchange wait timed out");
+  int late = 0;
+  SPAQR_CUDA(cudaMemcpyAsync(&late, h.d_flag, sizeof(int), cudaMemcpyDeviceToHost, h.st));
+  SPAQR_CUDA(cudaStreamSynchronize(h.st));
+  if (late) throw Error(SPAQR_ERR_TIMEOUT, "tensor-core trailing update: MMA completion wait timed out");
 }
 
 }  // namespace spaqr

@@ -181,6 +181,8 @@ struct Handle {
   // device-side apply plan (built after the factorization)
   struct ApplyPlan* plan = nullptr;
   spaqr_stats stats{};
+  // device int raised by a tensor-core kernel whose MMA completion wait gave up
+  int* d_flag = nullptr;
   // solve workspace
   double* d_work = nullptr;
   size_t work_elems = 0;

@@ -215,8 +215,12 @@ cudaError_t launch_qrcp_grid(const QrcpDesc<T>* d, const QrcpGridDesc* gd, int c
 // resident CTAs per SM at the given dynamic shared memory, element size elem),
 // at most one per thread of a CTA
 int qrcp_grid_capacity(int smem_bytes, int elem);
-// 1 if a grid-mode wait expired since the last call (then cleared)
-int qrcp_take_timeout();
+// Wait limit of the grid-mode exchange in SM clock cycles (default about 2 s at
+// the maximum SM clock) and a number of arrivals every wait expects beyond the
+// CTAs that exist (0 in normal use; failure-path tests set it so that every
+// wait expires).  An expired wait writes rank -1 for its matrix.
+constexpr long long kQrcpGridWaitCyclesDefault = 4000000000LL;
+void qrcp_grid_set_wait(long long cycles, int missing);
 
 // Launch shape measured by the autotuner for matrices of this size class
 // (autotune.cu): 0 = not tuned, 1..16 = CTAs with shared-memory slabs, 32 = 16
@@ -502,7 +506,7 @@ inline std::vector<FrontGroup> plan_fronts(const std::vector<int>& ms, const std
 template <typename T>
 cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std::vector<const FrontDesc<T>*>& d,
                                 const std::vector<std::vector<FrontDesc<T>>>& host, T* Tbuf, cudaStream_t st,
-                                int64_t* launches, void* tc_scratch = nullptr);
+                                int64_t* launches, void* tc_scratch = nullptr, int* tc_flag = nullptr);
 template <typename T>
 size_t front_groups_tc_bytes(const std::vector<FrontGroup>& groups, const std::vector<std::vector<FrontDesc<T>>>& host);
 
@@ -537,14 +541,14 @@ struct TcPanel {
   float* Wp;
   int mr, ld, j0, b, ncols;  // mr = m - j0 rows
   int nsl, rps;              // row slices of the projection and rows per slice (tc_plan_panel)
+  int* flag;                 // device int set to 1 when an MMA completion wait gives up (may be null)
 };
 void tc_plan_panel(TcPanel& f);
 size_t tc_panel_scratch(const TcPanel& f);
 cudaError_t launch_tc_panels(const TcPanel* d_panels, const std::vector<TcPanel>& host, cudaStream_t st);
 // C[0:m, 0:n] -= A[0:m, 0:k] B[0:k, 0:n] (FP32, column-major) on tcgen05, 3xTF32
+// (flag: device int set to 1 if an MMA completion wait gives up; may be null)
 cudaError_t launch_tc_gemm(int m, int n, int k, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                           cudaStream_t st);
-// 1 (and reset) if a tensor-core kernel gave up waiting for its MMAs since the last call
-int tc_take_timeout();
+                           int* flag, cudaStream_t st);
 
 }  // namespace spaqr

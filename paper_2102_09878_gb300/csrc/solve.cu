@@ -1161,6 +1161,9 @@ void IterSolve::begin() {
 
 void IterSolve::begun() {
   norm0 = std::sqrt(*h->plan->h_res);
+  if (!std::isfinite(norm0))
+    throw Error(SPAQR_ERR_INVALID_ARG, kind == 0 ? "right-hand side b has non-finite entries (||A^T b|| is not finite)"
+                                                 : "right-hand side g has non-finite entries");
   rel = norm0 > 0.0 ? 1.0 : 0.0;
   done = !(norm0 > 0.0);
   if (kind == 0) {

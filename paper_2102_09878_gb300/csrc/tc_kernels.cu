@@ -32,8 +32,6 @@ namespace {
 constexpr int kTcThreads = 128;  // one warpgroup: the four TMEM lane quarters
 constexpr long long kWaitLimit = 1LL << 28;
 
-__device__ int g_tc_timeout = 0;
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -98,8 +96,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Bounded wait for the phase `parity` of the mbarrier; records a timeout.
-__device__ __forceinline__ void mbar_wait(uint64_t* mbar, uint32_t parity) {
+// Bounded wait for the phase `parity` of the mbarrier; on expiry it raises the
+// launch's timeout flag (owned by the caller, read after the launch).
+__device__ __forceinline__ void mbar_wait(uint64_t* mbar, uint32_t parity, int* flag) {
   const uint32_t a = smem_u32(mbar);
   for (long long it = 0; it < kWaitLimit; ++it) {
     uint32_t done;
@@ -110,7 +109,7 @@ __device__ __forceinline__ void mbar_wait(uint64_t* mbar, uint32_t parity) {
         : "memory");
     if (done) return;
   }
-  atomicExch(&g_tc_timeout, 1);
+  if (flag) atomicExch(flag, 1);
 }
 
 // 16 consecutive FP32 accumulator columns of this thread's TMEM lane
@@ -154,7 +153,7 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, const float* Ahi, con
 // one on it, stored below).  K in stages of 32.
 template <bool UNIT>
 __device__ __forceinline__ void tc_update_tile(int m, int n, int k, const float* A, int lda, const float* B, int ldb,
-                                               float* C, int ldc, int row0, int col0) {
+                                               float* C, int ldc, int row0, int col0, int* flag) {
   extern __shared__ __align__(1024) float tsm[];
   float* Ahi = tsm;           // 128 x 32, K-major
   float* Alo = Ahi + 4096;
@@ -197,7 +196,7 @@ __device__ __forceinline__ void tc_update_tile(int m, int n, int k, const float*
       issue_stage(tmem, Ahi, Alo, Bhi, Blo, 32, 32, idesc, k0 == 0);
       mma_commit(&mbar);
     }
-    mbar_wait(&mbar, phase);
+    mbar_wait(&mbar, phase, flag);
     phase ^= 1u;
     fence_after_sync();
   }
@@ -219,8 +218,9 @@ __device__ __forceinline__ void tc_update_tile(int m, int n, int k, const float*
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(int m, int n, int k, const float* A, int lda,
-                                                                 const float* B, int ldb, float* C, int ldc) {
-  tc_update_tile<false>(m, n, k, A, lda, B, ldb, C, ldc, blockIdx.x * 128, blockIdx.y * 128);
+                                                                 const float* B, int ldb, float* C, int ldc,
+                                                                 int* flag) {
+  tc_update_tile<false>(m, n, k, A, lda, B, ldb, C, ldc, blockIdx.x * 128, blockIdx.y * 128, flag);
 }
 
 // P[s][c][t] = sum over rows r in slice s of C[r, c] V[r, t]  (V unit lower
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_project_kernel(const TcPanel
       issue_stage(tmem, Ahi, Alo, Bhi, Blo, 32, 32, idesc, first);
       mma_commit(&mbar);
     }
-    mbar_wait(&mbar, phase);
+    mbar_wait(&mbar, phase, f.flag);
     phase ^= 1u;
     fence_after_sync();
     first = false;
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_panel_update_kernel(const Tc
   if (row0 >= f.mr || col0 >= f.ncols) return;  // before any TMEM allocation
   const float* V = f.X + f.j0 + (int64_t)f.j0 * f.ld;
   float* C = f.X + f.j0 + (int64_t)(f.j0 + f.b) * f.ld;
-  tc_update_tile<true>(f.mr, f.ncols, f.b, V, f.ld, f.Wp, 32, C, f.ld, row0, col0);
+  tc_update_tile<true>(f.mr, f.ncols, f.b, V, f.ld, f.Wp, 32, C, f.ld, row0, col0, f.flag);
 }
 
 constexpr int kUpdateSmem = 4 * 4096 * (int)sizeof(float);
@@ -345,11 +345,11 @@ void tc_setup() {
 }  // namespace
 
 cudaError_t launch_tc_gemm(int m, int n, int k, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                           cudaStream_t st) {
+                           int* flag, cudaStream_t st) {
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
   tc_setup();
   tc_gemm_kernel<<<dim3((unsigned)((m + 127) / 128), (unsigned)((n + 127) / 128)), kTcThreads, kUpdateSmem, st>>>(
-      m, n, k, A, lda, B, ldb, C, ldc);
+      m, n, k, A, lda, B, ldb, C, ldc, flag);
   return cudaGetLastError();
 }
 
@@ -380,19 +380,6 @@ cudaError_t launch_tc_panels(const TcPanel* d_panels, const std::vector<TcPanel>
   tc_reduce_kernel<<<dim3((unsigned)((ct * 128 + 255) / 256), nf), 256, 0, st>>>(d_panels);
   tc_panel_update_kernel<<<dim3((unsigned)rt, (unsigned)ct, nf), kTcThreads, kUpdateSmem, st>>>(d_panels);
   return cudaGetLastError();
-}
-
-int tc_take_timeout() {
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_tc_timeout, sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  if (v) {
-    const int zero = 0;
-    cudaMemcpyToSymbol(g_tc_timeout, &zero, sizeof(int));
-  }
-  return v;
 }
 
 }  // namespace spaqr
