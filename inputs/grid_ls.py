@@ -141,3 +141,48 @@ def workload(name: str, seed: int = 0) -> tuple[GridProblem, int]:
 
         return inverse_poisson(nx, 2 if nz == 1 else 3, seed=seed), spec["depth"]
     return grid_problem(nx, ny, nz, spec["law"], seed), spec["depth"]
+
+
+def tile_problem(prob: GridProblem, t: int) -> GridProblem:
+    """The corner tile [0, t)^d of a grid problem as a problem of its own: the
+    rows of `prob` whose entries all lie in the tile (edges with both
+    endpoints inside, vertex rows inside), in the generator's row order, with
+    the values and right-hand side of `prob` (a sample of the same matrix)."""
+    nx, ny, nz = prob.dims
+    tx, ty = min(t, nx), min(t, ny)
+    tz = min(t, nz) if nz > 1 else 1
+    sub = grid_problem(tx, ty, tz, "u12", 0)  # the tile's structure; values replaced below
+    nex = (nx - 1) * ny * nz
+    ney = nx * (ny - 1) * nz
+    nez = nx * ny * (nz - 1) if nz > 1 else 0
+    rows = []
+    if tx > 1:
+        I, J, K = np.meshgrid(np.arange(tx - 1), np.arange(ty), np.arange(tz), indexing="ij")
+        o = np.lexsort((I.ravel(), J.ravel(), K.ravel()))
+        I, J, K = I.ravel()[o], J.ravel()[o], K.ravel()[o]
+        rows.append(K * ny * (nx - 1) + J * (nx - 1) + I)
+    if ty > 1:
+        I, J, K = np.meshgrid(np.arange(tx), np.arange(ty - 1), np.arange(tz), indexing="ij")
+        o = np.lexsort((I.ravel(), J.ravel(), K.ravel()))
+        I, J, K = I.ravel()[o], J.ravel()[o], K.ravel()[o]
+        rows.append(nex + K * (ny - 1) * nx + J * nx + I)
+    if tz > 1:
+        I, J, K = np.meshgrid(np.arange(tx), np.arange(ty), np.arange(tz - 1), indexing="ij")
+        o = np.lexsort((I.ravel(), J.ravel(), K.ravel()))
+        I, J, K = I.ravel()[o], J.ravel()[o], K.ravel()[o]
+        rows.append(nex + ney + K * ny * nx + J * nx + I)
+    V = np.arange(tx * ty * tz)
+    vi, vj, vk = V % tx, (V // tx) % ty, V // (tx * ty)
+    rows.append(nex + ney + nez + vk * nx * ny + vj * nx + vi)
+    rows = np.concatenate(rows)
+    assert rows.size == sub.m
+    vals = np.empty_like(sub.vals)
+    # gather the values row by row: every row of the tile has the same number
+    # of entries (2 for an edge, 1 for a vertex) as its row in prob
+    src_start = prob.rowptr[rows]
+    cnt = sub.rowptr[1:] - sub.rowptr[:-1]
+    assert np.array_equal(cnt, prob.rowptr[rows + 1] - src_start)
+    idx = np.repeat(src_start - sub.rowptr[:-1], cnt) + np.arange(sub.nnz)
+    vals[:] = prob.vals[idx]
+    return GridProblem(tx, ty, tz, sub.m, sub.n, sub.rowptr, sub.colidx, vals, prob.b[rows].copy(), prob.law,
+                       prob.seed)

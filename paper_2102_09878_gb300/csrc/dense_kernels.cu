@@ -613,7 +613,449 @@ __device__ __forceinline__ float recompute_frac<float>() {
   return 3.4527e-4f;
 }
 
+// Sum of squares of the entries of a column to FP64 accuracy.  For FP32 data
+// every term x^2 is split exactly into p + e (p = fl(x^2), e = fma(x, x, -p))
+// and accumulated with Knuth's two-sum, the rounding errors collected in a
+// second FP32 word (the Sum2 scheme of Ogita, Rump and Oishi, "Accurate sum
+// and dot product", 2005): s + c is the exact sum up to relative errors of
+// order (n u)^2, u = 2^-24, which for the column lengths here is about 1e-11.
+// FP64 data are summed in FP64.
+template <typename T>
+struct SqSum;
+template <>
+struct SqSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s = fma(x, x, s); }
+  // the warp's total, valid in lane 0
+  __device__ __forceinline__ double warp_total() { return warp_sum(s); }
+};
+template <>
+struct SqSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float p = x * x;
+    const float e = fmaf(x, x, -p);
+    const float t = s + p;
+    const float z = t - s;
+    c += ((s - (t - z)) + (p - z)) + e;
+    s = t;
+  }
+  // the warp's total, valid in lane 0: the (s, c) pairs meet by two-sums in
+  // FP32, and only lane 0 forms the FP64 value (FP64 instructions issued by a
+  // whole warp are expensive on this GPU)
+  __device__ __forceinline__ double warp_total() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+      const float t = s + s2;
+      const float z = t - s;
+      c = (c + c2) + ((s - (t - z)) + (s2 - z));
+      s = t;
+    }
+    double r = 0.0;
+    if ((threadIdx.x & 31) == 0) r = (double)s + (double)c;
+    return r;
+  }
+};
+
+// One warp's proposal for the next pivot step, as the slab QRCP exchanges it:
+// the squared partial norm that orders the pivots (v), the column (j, original
+// index; INT_MAX = none), its entry at the next diagonal position (alpha), and
+// the Householder data of that column formed in FP64 from alpha and the
+// FP64-accurate sum of squares below it: R_ii = beta, tau, and
+// den = alpha - beta (0 when the column is zero below alpha).
+template <typename T, typename N>
+struct QrcpProp {
+  N v;
+  int j;
+  T alpha;
+  double beta, tau;
+  T den;
+};
+
+// Lowest original column index among equal norms: the pivot rule of the oracle.
+template <typename N>
+__device__ __forceinline__ bool prop_better(N v, int j, N bv, int bj) {
+  return v > bv || (v == bv && j < bj);
+}
+
+// Every lane of the warp ends with the best of the warp's (v, j) and the lane
+// holding it.
+template <typename N>
+__device__ __forceinline__ int warp_argmax(N& v, int& j) {
+  int who = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const N ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+    const int ow = __shfl_xor_sync(0xffffffffu, who, o);
+    if (prop_better(ov, oj, v, j)) {
+      v = ov;
+      j = oj;
+      who = ow;
+    }
+  }
+  return who;
+}
+
+// The warp's record for step i_next: best column (v, j) of the warp (every lane
+// holds it); the sum of squares over rows i_next+1..m-1, R_ii and tau of that
+// column are formed in lane 0 only.  Valid in lane 0.
+template <typename T, typename N>
+__device__ __forceinline__ QrcpProp<T, N> warp_record(const T* X, int m, int ldx, int j0, int i_next, N v, int j) {
+  QrcpProp<T, N> r{v, j, T(0), 0.0, 0.0, T(0)};
+  if (j == INT_MAX || i_next >= m) return r;
+  const T* col = X + (int64_t)(j - j0) * ldx;
+  SqSum<T> acc;
+  for (int q = i_next + 1 + (int)(threadIdx.x & 31); q < m; q += 32) acc.add(col[q]);
+  const double sig = acc.warp_total();
+  if ((threadIdx.x & 31) == 0) {
+    const double alpha = (double)col[i_next];
+    r.alpha = col[i_next];
+    if (sig == 0.0) {
+      r.beta = alpha;
+      r.tau = 0.0;
+      r.den = T(0);
+    } else {
+      const double nrm = sqrt(alpha * alpha + sig);
+      r.beta = alpha >= 0.0 ? -nrm : nrm;
+      r.tau = (r.beta - alpha) / r.beta;
+      r.den = (T)(alpha - r.beta);
+    }
+  }
+  return r;
+}
+
+// 16-byte shared-memory vectors: four FP32 or two FP64 consecutive rows
+template <typename T>
+__device__ __forceinline__ void ld16(const T* p, T (&a)[16 / sizeof(T)]);
+template <>
+__device__ __forceinline__ void ld16<float>(const float* p, float (&a)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a[0] = v.x;
+  a[1] = v.y;
+  a[2] = v.z;
+  a[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void ld16<double>(const double* p, double (&a)[2]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a[0] = v.x;
+  a[1] = v.y;
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* p, const T (&a)[16 / sizeof(T)]);
+template <>
+__device__ __forceinline__ void st16<float>(float* p, const float (&a)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(a[0], a[1], a[2], a[3]);
+}
+template <>
+__device__ __forceinline__ void st16<double>(double* p, const double (&a)[2]) {
+  *reinterpret_cast<double2*>(p) = make_double2(a[0], a[1]);
+}
+
 // ------------------------------------------------------------------- QRCP
+// Column-pivoted Householder QR stopped at the rank, one thread-block cluster
+// of CS CTAs (CS = 1 allowed) per matrix.  CTA r of the cluster owns the
+// column slab [r*nl, (r+1)*nl) (nl = ceil(n/CS)) in its shared memory, columns
+// of ldx = m rounded up to four rows (zero below m).  Columns never move.  One
+// pivot step is
+//   B1  every warp has left, from its share of the previous update, the record
+//       of its best column (partial norm, index, FP64-accurate sum of squares
+//       below the next diagonal entry, that entry); CTA barrier;
+//   every warp reduces the CTA's records with shuffles (same result in every
+//       warp); with CS > 1 the CTA's best is published and, after one cluster
+//       barrier, every warp reduces the CS published records the same way;
+//   R_ii = beta and tau follow in FP64 from the winner's record alone, the
+//       rank test |R_ii| >= eps |R_11| stops the loop uniformly;
+//   every thread scales its rows of the winner's column, read from the owner's
+//       slab (distributed shared memory), into the local reflector buffer, which
+//       is indexed by row (zero above row i, one at row i);
+//   B2  CTA barrier; the update x_j <- x_j - tau (v^T x_j) v of the unpivoted
+//       columns (compact list act[]) in 16-byte row vectors with the downdate of
+//       their partial norms, and each warp's record for the next step.
+// The owner writes beta and the reflector into the pivot column once no CTA
+// can still read it: at once when CS = 1, otherwise after the next cluster
+// barrier (double-buffered records and reflector buffers keep every read of
+// step i apart from the writes of step i + 1).
+template <typename T, int KG, int NT>
+__global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* descs, double eps, int nl_max,
+                                                       int m_max) {
+  constexpr int NW = NT / 32;
+  constexpr int VW = 16 / (int)sizeof(T);
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const QrcpDesc<T> d = descs[blockIdx.x / CS];
+  const int m = d.m, n = d.n;
+  const int ldx = qrcp_ldx(m);
+  const int nl = (n + CS - 1) / CS;
+  const int j0 = min(n, rank * nl), j1 = min(n, j0 + nl);
+  const int nloc = j1 - j0;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  using N = T;  // partial column norms and pivot order in the data's precision
+  N* nu = reinterpret_cast<N*>(smraw);  // nl_max
+  N* nuref = nu + nl_max;               // nl_max
+  int* step_of = reinterpret_cast<int*>(nuref + nl_max);  // nl_max
+  int* act = step_of + nl_max;                            // unpivoted local columns, nl_max
+  int* pos = act + nl_max;                                // position of each column in act
+  const int vstride = qrcp_vstride(m_max);
+  T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // 2 x vstride
+  T* taus = vbuf + 2 * vstride;                                                    // vstride
+  T* X = taus + vstride;                                                           // ldx x nloc slab
+  __shared__ QrcpProp<T, N> rec[NW];  // per-warp records of the coming step
+  __shared__ QrcpProp<T, N> pub[2];   // the CTA's best, read by the cluster (by step parity)
+  __shared__ int s_nact;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t e = threadIdx.x; e < (int64_t)ldx * nloc; e += NT) {
+    const int r = (int)(e % ldx), c = (int)(e / ldx);
+    X[e] = r < m ? d.src[r + (int64_t)(j0 + c) * d.ld] : T(0);
+  }
+  for (int e = threadIdx.x; e < 2 * vstride; e += NT) vbuf[e] = T(0);
+  __syncthreads();
+  for (int c = warp; c < nloc; c += NW) {
+    N sq = N(0);
+    for (int r = lane; r < m; r += 32) {
+      const N v = (N)X[r + (int64_t)c * ldx];
+      sq += v * v;
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) {
+      nu[c] = sq;
+      nuref[c] = sq;
+      step_of[c] = -1;
+    }
+  }
+  for (int c = threadIdx.x; c < nloc; c += NT) {
+    act[c] = c;
+    pos[c] = c;
+  }
+  if (threadIdx.x == 0) s_nact = nloc;
+  const int kmax = m < n ? m : n;
+  __syncthreads();
+  {  // records for step 0: every warp over its columns c = warp + NW * (lane + 32 t)
+    N wv = N(-1);
+    int wj = INT_MAX;
+    for (int c = warp + lane * NW; c < nloc; c += 32 * NW)
+      if (prop_better(nu[c], j0 + c, wv, wj)) {
+        wv = nu[c];
+        wj = j0 + c;
+      }
+    warp_argmax(wv, wj);
+    const QrcpProp<T, N> r = warp_record<T, N>(X, m, ldx, j0, 0, wv, wj);
+    if (lane == 0) rec[warp] = r;
+  }
+  double r11 = 0.0;
+  int k = 0;
+  int pend_p = -1, pend_i = -1;  // pivot column this CTA still has to write (CS > 1)
+  T pend_beta = T(0);
+  const int jl = butterfly_col<KG>(lane);  // the column whose sum this lane ends with
+  const bool lead = lane == butterfly_lane<KG>(jl);
+  for (int i = 0; i < kmax; ++i) {
+    const int par = i & 1;
+    T* vb = vbuf + par * vstride;
+    __syncthreads();  // B1: the records of step i
+    // the CTA's best, reduced in every warp
+    QrcpProp<T, N> best;
+    {
+      N v = lane < NW ? rec[lane].v : N(-1);
+      int j = lane < NW ? rec[lane].j : INT_MAX;
+      const int who = warp_argmax(v, j);
+      best = rec[who < NW ? who : 0];
+      best.v = v;
+      best.j = j;
+    }
+    if (CS > 1) {
+      if (threadIdx.x == 0) pub[par] = best;
+      cl.sync();  // the CTAs' bests of step i visible cluster-wide; step i - 1 reads finished
+      N v = N(-1);
+      int j = INT_MAX;
+      if (lane < CS) {
+        const QrcpProp<T, N>* o = cl.map_shared_rank(&pub[par], lane);
+        v = o->v;
+        j = o->j;
+      }
+      const int who = warp_argmax(v, j);
+      if (j != INT_MAX) best = *cl.map_shared_rank(&pub[par], who);
+      best.v = v;
+      best.j = j;
+      if (pend_p >= 0) {  // the previous pivot column: nobody reads it any more
+        T* col = X + (int64_t)(pend_p - j0) * ldx;
+        const T* vp = vbuf + (pend_i & 1) * vstride;
+        for (int r = pend_i + 1 + threadIdx.x; r < m; r += NT) col[r] = vp[r];
+        if (threadIdx.x == 0) col[pend_i] = pend_beta;
+        pend_p = -1;
+      }
+    }
+    const int p = best.j;
+    if (p == INT_MAX) break;  // no proposal (non-finite norms): the same p everywhere
+    // the rank test in FP64, in lane 0 of every warp (same record, same answer)
+    int stop = 0;
+    if (lane == 0) {
+      const double ab = fabs(best.beta);
+      if (i == 0) r11 = ab;
+      stop = (best.beta == 0.0 || ab < eps * r11) ? 1 : 0;
+    }
+    if (__shfl_sync(0xffffffffu, stop, 0)) break;  // rank reached: the same decision everywhere
+    const T den = __shfl_sync(0xffffffffu, best.den, 0);
+    const T tau_t = __shfl_sync(0xffffffffu, (T)best.tau, 0);
+    const T beta_t = __shfl_sync(0xffffffffu, (T)best.beta, 0);
+    const int owner = p / nl;
+    const int rb = i & ~(VW - 1);  // first row of the vectors the update touches
+    {  // the reflector by row: 0 above row i, 1 at row i, the scaled column below
+      const T* Xo = owner == rank ? X : cl.map_shared_rank(X, owner);
+      const T* src = Xo + (int64_t)(p - owner * nl) * ldx;
+      for (int r = rb + threadIdx.x; r < ldx; r += NT)
+        vb[r] = r < i ? T(0) : (r == i ? T(1) : (r < m && den != T(0) ? src[r] / den : T(0)));
+      if (threadIdx.x == 0) taus[i] = copysign(tau_t, beta_t);  // tau >= 0; the sign is that of R_ii
+    }
+    if (rank == owner && threadIdx.x == 0) {
+      const int pl = p - j0;
+      const int q = pos[pl], last = act[s_nact - 1];
+      step_of[pl] = i;
+      act[q] = last;
+      pos[last] = q;
+      s_nact = s_nact - 1;
+    }
+    __syncthreads();  // B2: vb complete, act[] updated
+    if (rank == owner) {
+      if (CS == 1) {
+        T* col = X + (int64_t)(p - j0) * ldx;
+        for (int r = i + 1 + threadIdx.x; r < m; r += NT) col[r] = vb[r];
+        if (threadIdx.x == 0) col[i] = beta_t;
+      } else {
+        pend_p = p;
+        pend_i = i;
+        pend_beta = beta_t;
+      }
+    }
+    // apply H_i to the CTA's unpivoted columns: every warp takes groups of KG
+    // columns, each lane VW consecutive rows per 16-byte access, KG independent
+    // accumulators; the KG dot products (row i included: v_i = 1) are reduced
+    // by one transposed butterfly (lane L(j) ends with column j's sum),
+    // w_j = tau v^T x_j is broadcast, the rows are updated, and lane L(j)
+    // downdates the squared norm of column j (recomputed warp-parallel when it
+    // lost too many digits)
+    N wv = N(-1);
+    int wj = INT_MAX;
+    const int nact = s_nact;
+    for (int g0 = warp * KG; g0 < nact; g0 += NW * KG) {
+      const int ng = min(KG, nact - g0);
+      T* cols[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) cols[j] = X + (int64_t)act[g0 + (j < ng ? j : 0)] * ldx;
+      T acc[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) acc[j] = T(0);
+      if (tau_t != T(0)) {
+        for (int r = rb + lane * VW; r < ldx; r += 32 * VW) {
+          T v[VW];
+          ld16(vb + r, v);
+#pragma unroll
+          for (int j = 0; j < KG; ++j) {
+            T x[VW];
+            ld16(cols[j] + r, x);
+#pragma unroll
+            for (int q = 0; q < VW; ++q) acc[j] += v[q] * x[q];
+          }
+        }
+      }
+      const T dsum = butterfly_reduce<KG>(acc, lane);
+      const int cme = jl < ng ? act[g0 + jl] : 0;
+      const T wmine = jl < ng ? tau_t * dsum : T(0);
+      T wv8[KG];
+#pragma unroll
+      for (int j = 0; j < KG; ++j) wv8[j] = __shfl_sync(0xffffffffu, wmine, butterfly_lane<KG>(j));
+      if (tau_t != T(0)) {
+        for (int r = rb + lane * VW; r < ldx; r += 32 * VW) {
+          T v[VW];
+          ld16(vb + r, v);
+#pragma unroll
+          for (int j = 0; j < KG; ++j)
+            if (j < ng) {
+              T x[VW];
+              ld16(cols[j] + r, x);
+#pragma unroll
+              for (int q = 0; q < VW; ++q) x[q] -= wv8[j] * v[q];
+              st16(cols[j] + r, x);
+            }
+        }
+      }
+      __syncwarp();
+      N v = N(-1);
+      bool redo = false;
+      if (lead && jl < ng) {
+        const N xnew = (N)X[i + (int64_t)cme * ldx];
+        v = nu[cme] - xnew * xnew;
+        redo = v < recompute_frac<N>() * nuref[cme];
+      }
+      unsigned flagged = __ballot_sync(0xffffffffu, redo);
+      while (flagged) {
+        const int l = __ffs(flagged) - 1;
+        flagged &= flagged - 1;
+        const int cc = __shfl_sync(0xffffffffu, cme, l);
+        const T* col = X + (int64_t)cc * ldx;
+        N sq = N(0);
+        for (int r = i + 1 + lane; r < m; r += 32) {
+          const N y = (N)col[r];
+          sq += y * y;
+        }
+        sq = warp_sum(sq);
+        if (lane == l) {
+          v = sq;
+          nuref[cc] = sq;
+        }
+      }
+      if (lead && jl < ng) {
+        nu[cme] = v;
+        if (prop_better(v, j0 + cme, wv, wj)) {
+          wv = v;
+          wj = j0 + cme;
+        }
+      }
+    }
+    // the warp's record for step i + 1 (its columns are all updated: __syncwarp above)
+    warp_argmax(wv, wj);
+    const QrcpProp<T, N> r = warp_record<T, N>(X, m, ldx, j0, i + 1, wv, wj);
+    if (lane == 0) rec[warp] = r;
+    k = i + 1;
+  }
+  if (CS > 1) {
+    cl.sync();  // every read of the last pivot column is done
+    if (pend_p >= 0) {
+      T* col = X + (int64_t)(pend_p - j0) * ldx;
+      const T* vp = vbuf + (pend_i & 1) * vstride;
+      for (int r = pend_i + 1 + threadIdx.x; r < m; r += NT) col[r] = vp[r];
+      if (threadIdx.x == 0) col[pend_i] = pend_beta;
+    }
+  }
+  __syncthreads();
+  if (rank == 0 && threadIdx.x == 0) d.rank[0] = k;
+  if (d.V) {
+    for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += NT) {
+      const int r = (int)(e % m), c = (int)(e / m);
+      const int t = step_of[c];
+      if (t < 0 || t >= k) continue;
+      d.V[r + (int64_t)t * m] = r < t ? T(0) : (r == t ? T(1) : X[r + (int64_t)c * ldx]);
+    }
+    if (rank == 0)
+      for (int t = threadIdx.x; t < k; t += NT) d.tau[t] = fabs(taus[t]);
+  }
+  // the first k rows of Q^T A in the original column order, only when k < m
+  if (d.out && (k < m || (d.flags & kQrcpAlwaysOut))) {
+    const bool fix = d.flags & kQrcpSignFix;
+    for (int64_t e = threadIdx.x; e < (int64_t)k * nloc; e += NT) {
+      const int r = (int)(e % k), c = (int)(e / k);
+      const int t = step_of[c];
+      const T x = (t >= 0 && r > t) ? T(0) : X[r + (int64_t)c * ldx];
+      d.out[r + (int64_t)(j0 + c) * d.ldo] = fix && signbit(taus[r]) ? -x : x;
+    }
+  }
+  if (CS > 1) cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// ----------------------------------------------------- QRCP (earlier form)
 // Column-pivoted Householder QR stopped at the rank, one thread-block cluster
 // of CS CTAs per matrix.  CTA r of the cluster owns the column slab
 // [r*nl, (r+1)*nl) (nl = ceil(n/CS)), staged in its shared memory (SMEM) or in
@@ -2177,14 +2619,14 @@ cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, cud
 template <typename T>
 static cudaError_t launch_cluster(void (*kernel)(const QrcpDesc<T>*, double, int, int), std::once_flag& init, unsigned grid,
                                   int cs, int smem, cudaStream_t st, const QrcpDesc<T>* d, double eps, int nl_max,
-                                  int m_max) {
+                                  int m_max, int threads = kThreads) {
   std::call_once(init, [kernel] {
     allow_smem(kernel);
     cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = (size_t)smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
@@ -2214,7 +2656,7 @@ cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int
   const unsigned grid = (unsigned)(count * cs);
   if (smem_slab) {
     static std::once_flag init_s;
-    return launch_cluster(qrcp_cluster_kernel<T, true, 8>, init_s, grid, cs, smem, st, d, eps, nl_max, m_max);
+    return launch_cluster(qrcp_slab_kernel<T, 8, kThreads>, init_s, grid, cs, smem, st, d, eps, nl_max, m_max, kThreads);
   }
   switch (nb) {
     case 16: {

@@ -122,11 +122,21 @@ cudaError_t launch_qrcp(const QrcpDesc<T>* d, int count, double eps, int cs, int
 // dynamic shared memory of one QRCP CTA (nl columns of m rows): with the slab
 // in shared memory (slab: two reflector buffers, taus, the slab), or the
 // delayed-update form (reflector, taus, nb coefficients per column)
+// Slab layout of the shared-memory QRCP: columns of ldx = m rounded up to four
+// rows (16-byte vector rows for FP32 and FP64), reflector buffers of vstride
+// elements (row-aligned, a multiple of four).
+#ifdef __CUDACC__
+#define SPAQR_HD __host__ __device__
+#else
+#define SPAQR_HD
+#endif
+SPAQR_HD inline int qrcp_ldx(int m) { return (m + 3) & ~3; }
+SPAQR_HD inline int qrcp_vstride(int m) { return qrcp_ldx(m) + 4; }
 inline int qrcp_smem_bytes(int m, int nl, int elem, bool slab, int nb = kQrcpNB) {
   long long b = ((long long)nl * 28 + 15) / 16 * 16;  // nu, nuref, step_of, act, pos
-  const long long vs = (long long)((m + 3) & ~1) * elem;
+  const long long vs = (long long)qrcp_vstride(m) * elem;
   if (slab)
-    b += 3 * vs + (long long)m * nl * elem;
+    b += 3 * vs + (long long)qrcp_ldx(m) * nl * elem;
   else
     b += 2 * vs + (long long)nl * nb * elem;
   return (int)(b + 64);
@@ -134,7 +144,7 @@ inline int qrcp_smem_bytes(int m, int nl, int elem, bool slab, int nb = kQrcpNB)
 // dynamic shared memory of one grid-mode QRCP CTA: the slab layout, without
 // the slab itself when the columns stay in the work copy
 inline int qrcp_grid_smem_bytes(int m, int nl, int elem, bool slab) {
-  return qrcp_smem_bytes(m, nl, elem, true) - (slab ? 0 : m * nl * elem);
+  return qrcp_smem_bytes(m, nl, elem, true) - (slab ? 0 : qrcp_ldx(m) * nl * elem);
 }
 // deepest panel (16, 8, 4, 2, 1) of the delayed-update QRCP that fits, 0 if none
 inline int qrcp_panel_depth(int m, int nl, int elem, int limit) {
@@ -306,10 +316,18 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
   // spread small batches over more SMs: while the batch holds fewer CTAs than
   // the GPU has SMs, double the cluster of the largest shared-memory problems
   // that keep at least 64 columns per CTA
+  // A cluster must sit inside one GPC (about 19 SMs on this GPU), so clusters
+  // of 4 to 16 CTAs can hold only about 128 SMs at once (144 for pairs); a
+  // size class is not grown past that (a second wave would double the time).
   {
     constexpr long long kSms = 152;
+    auto cap = [](int c) -> long long { return c <= 1 ? 152 : (c == 2 ? 144 : 128); };
     long long ctas = 0;
-    for (int i : order) ctas += cs[(size_t)i];
+    long long at[17] = {0};
+    for (int i : order) {
+      ctas += cs[(size_t)i];
+      if (slab[(size_t)i]) at[cs[(size_t)i]] += cs[(size_t)i];
+    }
     std::vector<int> bywork(order);
     std::sort(bywork.begin(), bywork.end(), [&](int a, int b) {
       const long long wa = (long long)ms[(size_t)a] * ns[(size_t)a], wb = (long long)ms[(size_t)b] * ns[(size_t)b];
@@ -322,6 +340,9 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
         if (ctas >= kSms) break;
         const int c2 = cs[(size_t)i] * 2;
         if (!slab[(size_t)i] || c2 > 16 || ns[(size_t)i] / c2 < 64) continue;
+        if (at[c2] + c2 > cap(c2)) continue;
+        at[cs[(size_t)i]] -= cs[(size_t)i];
+        at[c2] += c2;
         ctas += cs[(size_t)i];
         cs[(size_t)i] = c2;
         grew = true;
