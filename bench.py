@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-extra", dest="extra", action="store_false",
                     help="skip the eps sweep and the 3D 64^3 lines reported under detail.extra")
     ap.add_argument("--extra-steps", type=int, default=2, help="timed runs per extra configuration")
+    ap.add_argument("--diag-maxit", type=int, default=3000, help="iteration cap of the Diag. comparator line")
     ap.add_argument("--clocks-dir", default=None, help="where the nvidia-smi clock samples of the timed region go "
                                                         "(default: the system temporary directory)")
     ap.add_argument("--sample", default=None,
@@ -277,24 +278,29 @@ def vs_oracle(golden, x, iters):
             "x_samples": int(pos.size)}
 
 
-def timed_runs(sq, prob, an, eps, precision, steps, warmup, stream, b_dev):
+def timed_runs(sq, prob, an, eps, precision, steps, warmup, stream, b_dev, mode="spaqr", solver="cgls", maxit=500):
     """Factor + solve `steps` times after `warmup` untimed runs; device-timed
     seconds per run (CUDA events on the library stream), iterations, the last
-    solution (host) and the last run's stats."""
+    solution (host) and the last run's stats.  mode: "spaqr", "direct" (no
+    compression) or "diag" (no factor, the column scaling alone); solver:
+    "cgls" or "csne" (corrected seminormal equations)."""
     import torch
 
-    for _ in range(warmup):
+    def one():
+        g = sq.SpaQR(prob, an, eps=eps, precision=precision, stream=stream, mode=mode, maxit=maxit)
         with torch.cuda.stream(stream):
-            sq.SpaQR(prob, an, eps=eps, precision=precision, stream=stream).solve(b_dev, check_convergence=False)
+            fn = g.solve_csne if solver == "csne" else g.solve
+            return g, fn(b_dev, check_convergence=False)
+
+    for _ in range(warmup):
+        one()
     torch.cuda.synchronize()
     c0 = torch.cuda.Event(enable_timing=True)
     c1 = torch.cuda.Event(enable_timing=True)
     its = []
     c0.record(stream)
     for _ in range(steps):
-        g = sq.SpaQR(prob, an, eps=eps, precision=precision, stream=stream)
-        with torch.cuda.stream(stream):
-            x = g.solve(b_dev, check_convergence=False)
+        g, x = one()
         its.append(g.stats()["iters"])
     c1.record(stream)
     torch.cuda.synchronize()
@@ -429,25 +435,40 @@ def extra_configs(args, sq, stream, dev):
     from inputs.grid_ls import workload
 
     out = {}
-    runs = []
+    runs = []  # (workload, eps, mode, solver, maxit)
     if args.workload == "grid2d_1024":
-        runs += [("grid2d_1024", e) for e in (1e-2, 1e-4) if e != args.eps]
-        runs += [("grid3d_64", 1e-3)]
-    for name, eps in runs:
-        prob, depth = workload(name, seed=0)
-        an = sq.Analysis(prob.dims, depth)
-        b_dev = torch.from_numpy(prob.b).to(dev)
-        A = prob.to_scipy()
-        g = golden_for(name, eps)
-        for prec in ("mixed", "fp64"):
-            secs, its, x, st = timed_runs(sq, prob, an, eps, prec, args.extra_steps, 1, stream, b_dev)
+        runs += [("grid2d_1024", e, "spaqr", "cgls", 500) for e in (1e-2, 1e-4) if e != args.eps]
+        # the paper's other solve (CSNE) and comparators (Direct, Diag.) on the headline workload
+        runs += [("grid2d_1024", args.eps, "spaqr", "csne", 500), ("grid2d_1024", 0.0, "diag", "cgls", args.diag_maxit)]
+        # Direct (no compression) against spaQR where the direct factor still takes seconds: the 256^2 grid of
+        # the same family (at 1024^2 the direct factor takes minutes)
+        runs += [("grid2d_256_c3", args.eps, "spaqr", "cgls", 500), ("grid2d_256_c3", 0.0, "direct", "cgls", 500)]
+        runs += [("grid3d_64", 1e-3, "spaqr", "cgls", 500)]
+    cache = {}
+    for name, eps, mode, solver, maxit in runs:
+        if name not in cache:
+            cache.clear()
+            torch.cuda.empty_cache()
+            prob, depth = workload(name, seed=0)
+            cache[name] = (prob, sq.Analysis(prob.dims, depth), torch.from_numpy(prob.b).to(dev), prob.to_scipy())
+        prob, an, b_dev, A = cache[name]
+        g = golden_for(name, eps) if mode == "spaqr" and solver == "cgls" else None
+        for prec in (("mixed", "fp64") if mode != "diag" else ("fp64",)):
+            key = f"{name}_eps{eps:g}_{prec}" if (mode, solver) == ("spaqr", "cgls") else f"{name}_{mode}_{solver}_{prec}"
+            try:
+                secs, its, x, st = timed_runs(sq, prob, an, eps, prec, args.extra_steps, 1, stream, b_dev,
+                                              mode=mode, solver=solver, maxit=maxit)
+            except Exception as e:  # reported, not fatal: e.g. the direct factor's memory
+                out[key] = {"error": str(e)}
+                continue
             rel = float(np.linalg.norm(A.T @ (A @ x - prob.b)) / np.linalg.norm(A.T @ prob.b))
-            out[f"{name}_eps{eps:g}_{prec}"] = {
-                "seconds": secs, "iters": its, "rel_resid": rel, "converged": rel < 1e-10, "t_factor": st["t_factor"],
-                "t_solve": st["t_solve"], "nnz_W": st["nnz_W"],
-                "kernel_seconds": {k: v for k, v in st["t_kernel"].items()}, "vs_oracle": vs_oracle(g, x, its[-1])}
-        del b_dev, an
-        torch.cuda.empty_cache()
+            out[key] = {
+                "mode": mode, "solver": solver, "eps": eps, "seconds": secs, "iters": its, "maxit": maxit,
+                "rel_resid": rel, "converged": rel < 1e-10, "t_factor": st["t_factor"], "t_solve": st["t_solve"],
+                "nnz_W": st["nnz_W"], "kernel_seconds": {k: v for k, v in st["t_kernel"].items()},
+                "vs_oracle": vs_oracle(g, x, its[-1])}
+    cache.clear()
+    torch.cuda.empty_cache()
     return out
 
 

@@ -46,6 +46,9 @@ extern "C" {
 
 #define SPAQR_MODE_SPAQR 0  /* scaling + two-step sparsification (Algorithm 1) */
 #define SPAQR_MODE_DIRECT 1 /* no compression: multifrontal QR ("Direct", Section 4) */
+#define SPAQR_MODE_DIAG 2   /* no factorization, W = I: the solve is CGLS preconditioned by the column
+                               scaling D alone (the "Diag." comparator of Section 4); the analysis is
+                               still required and only its n is used */
 
 /* Sparse A in CSR form (host pointers).  Column indices in [0, n) and
  * ascending within a row; no explicit zeros are required to be absent. */
@@ -157,6 +160,18 @@ typedef struct {
  * on_device == 0 (copied in / out inside the call) or device pointers when
  * on_device != 0.  Returns NOT_CONVERGED (x and info written) at maxit. */
 int spaqr_solve(spaqr_handle* h, const double* b, double* x, int on_device, spaqr_solve_info* info);
+
+/* spaqr_solve_csne: the corrected seminormal equations with iterative
+ * refinement (Section 1, after Bjorck: R^T R x = A^T b solved with the factor,
+ * then corrected with the residual).  With W^T W ~= (A D)^T (A D), each step is
+ *     x~ <- x~ + W^{-1} W^{-T} (A D)^T (b - A D x~),     x = D x~,
+ * from x~ = 0, until ||A^T (A x - b)|| / ||A^T b|| < tol (handle options) or
+ * maxit steps.  At eps = 0 the first step is exact up to rounding; at eps > 0
+ * it is a stationary iteration that converges when W is close enough to the
+ * exact factor (no Krylov acceleration, unlike spaqr_solve).  Arguments,
+ * return codes and info as spaqr_solve (NOT_CONVERGED with x and info written
+ * at maxit; INVALID_ARG for a non-finite b). */
+int spaqr_solve_csne(spaqr_handle* h, const double* b, double* x, int on_device, spaqr_solve_info* info);
 
 /* z <- W^{-1} z (transpose = 0) or z <- W^{-T} z (transpose = 1) for a device
  * vector z of n entries in column (slot) order (Section 2.7: W is stored as a

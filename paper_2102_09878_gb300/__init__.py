@@ -121,20 +121,28 @@ class SpaQR:
 
     # ------------------------------------------------------------- solve
     def solve(self, b, check_convergence: bool = True):
-        """x = argmin ||A x - b||.  numpy in -> numpy out (host copies inside the
-        call); a CUDA float64 tensor in -> a CUDA tensor out (device pointers)."""
-        lib = capi.load()
+        """x = argmin ||A x - b|| by W-preconditioned CGLS.  numpy in -> numpy out
+        (host copies inside the call); a CUDA float64 tensor in -> a CUDA tensor
+        out (device pointers)."""
+        return self._solve(b, check_convergence, capi.load().spaqr_solve)
+
+    def solve_csne(self, b, check_convergence: bool = True):
+        """x = argmin ||A x - b|| by the corrected seminormal equations with
+        refinement (spaqr_solve_csne); same conventions as solve()."""
+        return self._solve(b, check_convergence, capi.load().spaqr_solve_csne)
+
+    def _solve(self, b, check_convergence, fn):
         info = capi.SolveInfo()
         if hasattr(b, "is_cuda") and b.is_cuda:
             import torch
 
             x = torch.empty(self.n, dtype=torch.float64, device=b.device)
             bb = b.contiguous()
-            rc = lib.spaqr_solve(self._h, capi.ptr(bb), capi.ptr(x), 1, C.byref(info))
+            rc = fn(self._h, capi.ptr(bb), capi.ptr(x), 1, C.byref(info))
         else:
             bb = np.ascontiguousarray(b, dtype=np.float64)
             x = np.zeros(self.n)
-            rc = lib.spaqr_solve(self._h, capi.ptr(bb), capi.ptr(x), 0, C.byref(info))
+            rc = fn(self._h, capi.ptr(bb), capi.ptr(x), 0, C.byref(info))
         if rc != capi.SPAQR_OK and (check_convergence or rc != 4):
             capi.check(rc)
         self.last_info = dict(iters=info.iters, rel=info.rel_resid, converged=bool(info.converged),

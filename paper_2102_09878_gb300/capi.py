@@ -28,7 +28,7 @@ ERRORS = {
 SPAQR_ERR_INVALID_ARG, SPAQR_ERR_RANK_DEFICIENT, SPAQR_ERR_CAPACITY, SPAQR_ERR_NOT_CONVERGED = 1, 2, 3, 4
 SPAQR_ERR_TIMEOUT, SPAQR_ERR_CUDA, SPAQR_ERR_OOM, SPAQR_ERR_NO_DEVICE = 5, 6, 7, 8
 PREC = {"fp64": 0, "mixed": 1}
-MODE = {"spaqr": 0, "direct": 1}
+MODE = {"spaqr": 0, "direct": 1, "diag": 2}
 ROWS = {"tree": 0, "maxnorm": 1}
 
 
@@ -111,6 +111,7 @@ SIGNATURES = {
     "spaqr_analysis_stage_clusters": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spaqr_factor": (C.c_int, [C.POINTER(Csr), C.c_void_p, C.POINTER(Options), C.POINTER(C.c_void_p)]),
     "spaqr_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(SolveInfo)]),
+    "spaqr_solve_csne": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(SolveInfo)]),
     "spaqr_factor_batch": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.POINTER(Options), C.c_void_p]),
     "spaqr_apply_Winv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "spaqr_apply_A": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),

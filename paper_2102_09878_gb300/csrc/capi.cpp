@@ -97,7 +97,8 @@ void check_input(const spaqr_csr* A, const spaqr::Analysis& a, const spaqr_optio
   if (!(opt.eps >= 0.0)) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "eps must be >= 0");
   if (opt.precision != SPAQR_PREC_FP64 && opt.precision != SPAQR_PREC_MIXED)
     throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "unknown precision");
-  if (opt.mode != SPAQR_MODE_SPAQR && opt.mode != SPAQR_MODE_DIRECT) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "unknown mode");
+  if (opt.mode != SPAQR_MODE_SPAQR && opt.mode != SPAQR_MODE_DIRECT && opt.mode != SPAQR_MODE_DIAG)
+    throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "unknown mode");
   if (opt.step1_qr_width < 0) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "step1_qr_width must be >= 0");
 }
 
@@ -124,7 +125,19 @@ std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Ana
   h.nnz = A->nnz;
   h.depth = a.depth;
   h.t_analyze = a.seconds;
-  spaqr::run_factor(h, *A, a);
+  if (h.opt.mode == SPAQR_MODE_DIAG) {
+    // no factorization: W = I, only the column scaling D (Section 2.7) of the
+    // diagonally preconditioned comparator ("Diag.", Section 4)
+    std::vector<double> nrm((size_t)A->n, 0.0);
+    for (int64_t e = 0; e < A->nnz; ++e) nrm[(size_t)A->colidx[e]] += A->vals[e] * A->vals[e];
+    h.D.resize((size_t)A->n);
+    for (int64_t j = 0; j < A->n; ++j) {
+      if (!(nrm[(size_t)j] > 0.0)) throw spaqr::Error(SPAQR_ERR_RANK_DEFICIENT, "zero column " + std::to_string(j));
+      h.D[(size_t)j] = 1.0 / std::sqrt(nrm[(size_t)j]);
+    }
+  } else {
+    spaqr::run_factor(h, *A, a);
+  }
   // scaled operator A~ = A D and its transpose on the device (FP64)
   std::vector<double> v((size_t)A->nnz);
   for (int64_t e = 0; e < A->nnz; ++e) v[(size_t)e] = A->vals[e] * h.D[(size_t)A->colidx[e]];
@@ -258,6 +271,44 @@ int dense_qrcp_route_t(int count, T* const* A, const int* m, const int* n, const
   });
 }
 
+// spaqr_solve (CGLS, Section 4) and spaqr_solve_csne (corrected seminormal
+// equations, Section 1) with host or device b and x.
+int solve_any(spaqr_handle* hh, const double* b, double* x, int on_device, spaqr_solve_info* info, bool csne) {
+  if (!hh || !b || !x) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    spaqr::Handle& h = *hh->h;
+    const double* bd = b;
+    double* xd = x;
+    double* tmp = nullptr;
+    if (on_device) h.wait_caller();
+    if (!on_device) {
+      SPAQR_CUDA(cudaMalloc(&tmp, (size_t)(h.m + h.n) * sizeof(double)));
+      SPAQR_CUDA(cudaMemcpyAsync(tmp, b, (size_t)h.m * sizeof(double), cudaMemcpyHostToDevice, h.st));
+      bd = tmp;
+      xd = tmp + h.m;
+    }
+    spaqr_solve_info inf{};
+    try {
+      if (csne)
+        spaqr::csne(h, bd, xd, &inf);
+      else
+        spaqr::cgls(h, bd, xd, &inf);
+    } catch (...) {
+      cudaStreamSynchronize(h.st);
+      cudaFree(tmp);
+      throw;
+    }
+    if (!on_device) {
+      SPAQR_CUDA(cudaMemcpyAsync(x, xd, (size_t)h.n * sizeof(double), cudaMemcpyDeviceToHost, h.st));
+      SPAQR_CUDA(cudaStreamSynchronize(h.st));
+      cudaFree(tmp);
+    }
+    if (info) *info = inf;
+    return inf.converged ? SPAQR_OK
+                         : fail(SPAQR_ERR_NOT_CONVERGED, csne ? "CSNE refinement reached maxit" : "CGLS reached maxit");
+  });
+}
+
 }  // namespace
 
 extern "C" {
@@ -387,29 +438,11 @@ int spaqr_factor_batch(int count, const spaqr_csr* const* A, const spaqr_analysi
 void spaqr_destroy(spaqr_handle* h) { delete h; }
 
 int spaqr_solve(spaqr_handle* hh, const double* b, double* x, int on_device, spaqr_solve_info* info) {
-  if (!hh || !b || !x) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
-  return guarded([&] {
-    spaqr::Handle& h = *hh->h;
-    const double* bd = b;
-    double* xd = x;
-    double* tmp = nullptr;
-    if (on_device) h.wait_caller();
-    if (!on_device) {
-      SPAQR_CUDA(cudaMalloc(&tmp, (size_t)(h.m + h.n) * sizeof(double)));
-      SPAQR_CUDA(cudaMemcpyAsync(tmp, b, (size_t)h.m * sizeof(double), cudaMemcpyHostToDevice, h.st));
-      bd = tmp;
-      xd = tmp + h.m;
-    }
-    spaqr_solve_info inf{};
-    spaqr::cgls(h, bd, xd, &inf);
-    if (!on_device) {
-      SPAQR_CUDA(cudaMemcpyAsync(x, xd, (size_t)h.n * sizeof(double), cudaMemcpyDeviceToHost, h.st));
-      SPAQR_CUDA(cudaStreamSynchronize(h.st));
-      cudaFree(tmp);
-    }
-    if (info) *info = inf;
-    return inf.converged ? SPAQR_OK : fail(SPAQR_ERR_NOT_CONVERGED, "CGLS reached maxit");
-  });
+  return solve_any(hh, b, x, on_device, info, false);
+}
+
+int spaqr_solve_csne(spaqr_handle* hh, const double* b, double* x, int on_device, spaqr_solve_info* info) {
+  return solve_any(hh, b, x, on_device, info, true);
 }
 
 int spaqr_apply_Winv(spaqr_handle* hh, double* z, int transpose) {

@@ -223,14 +223,17 @@ void free_apply_plan(Handle& h);
 void apply_Winv(Handle& h, double* z, int transpose);
 void apply_A(Handle& h, const double* x, double* y, int forward);
 void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info);
+// Corrected seminormal equations with refinement: x <- x + W^{-1} W^{-T} A~^T (b - A~ x).
+void csne(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info);
 // Adjoint pieces: g_b = A lambda, g_A = r lambda^T - (A lambda) x^T on the pattern.
 void lstsq_grad(Handle& h, const double* b, const double* x, const double* lam, double* gb, double* gv);
 // New values of A (same pattern, device array in the caller's CSR order).
 void set_values(Handle& h, const double* a_dev);
 
 // One iterative solve on one handle: kind 0 = CGLS for min ||A x - b|| (rhs b,
-// out x), kind 1 = PCG for (A^T A) lambda = g (rhs g, out lambda), both
-// preconditioned by the factor W.  run_iterative() advances several of them
+// out x), kind 1 = PCG for (A^T A) lambda = g (rhs g, out lambda), kind 2 =
+// corrected seminormal equations for min ||A x - b|| (rhs b, out x), all with
+// the factor W.  run_iterative() advances several of them
 // side by side, one iteration per handle per round.
 struct IterSolve {
   Handle* h = nullptr;

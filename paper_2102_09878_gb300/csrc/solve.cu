@@ -525,6 +525,15 @@ __global__ void __launch_bounds__(kT) update_p_kernel(int64_t n, double* p, cons
   if (i < n) p[i] = s[i] + beta * p[i];
 }
 
+// x <- x + s (n entries), r <- r - q (m entries): one refinement step of the
+// corrected seminormal equations
+__global__ void __launch_bounds__(kT) csne_update_kernel(int64_t n, int64_t m, double* x, const double* s, double* r,
+                                                         const double* q) {
+  const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (i < n) x[i] += s[i];
+  if (i < m) r[i] -= q[i];
+}
+
 __global__ void __launch_bounds__(kT) scale_kernel(int64_t n, const double* a, const double* d, double* out) {
   const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
   if (i < n) out[i] = a[i] * d[i];
@@ -619,6 +628,7 @@ struct ApplyPlan {
   size_t psmem = 0;
   cudaGraphExec_t graph = nullptr;      // one CGLS iteration
   cudaGraphExec_t graph_pcg = nullptr;  // one PCG iteration
+  cudaGraphExec_t graph_csne = nullptr;  // one CSNE refinement step
   double* h_res = nullptr;              // pinned host copy of the residual norm
   double* d_scal = nullptr;
   double* d_part = nullptr;
@@ -906,6 +916,7 @@ void free_apply_plan(Handle& h) {
     if (e) cudaEventDestroy(e);
   if (h.plan->graph) cudaGraphExecDestroy(h.plan->graph);
   if (h.plan->graph_pcg) cudaGraphExecDestroy(h.plan->graph_pcg);
+  if (h.plan->graph_csne) cudaGraphExecDestroy(h.plan->graph_csne);
   if (h.plan->h_res) cudaFreeHost(h.plan->h_res);
   cudaFree(h.plan->d_segs);
   cudaFree(h.plan->d_bar);
@@ -1093,6 +1104,23 @@ static void pcg_body(Handle& h, double* nu, double* r, double* z, double* p, dou
   SPAQR_CUDA(cudaGetLastError());
 }
 
+// One refinement step of the corrected seminormal equations (Section 1: the
+// factor gives W^T W ~= A~^T A~): s = W^{-1} W^{-T} u with u = A~^T r,
+// x <- x + s, r <- r - A~ s, u <- A~^T r and scal[2] = |D^{-1} u|^2, the
+// unscaled normal-equation residual of the stopping test.  No host wait.
+static void csne_body(Handle& h, double* x, double* r, double* q, double* u, double* s, const double* Dv) {
+  ApplyPlan& P = *h.plan;
+  const int64_t m = h.m, n = h.n;
+  SPAQR_CUDA(cudaMemcpyAsync(s, u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h.st));
+  apply_Winv(h, s, 1);
+  apply_Winv(h, s, 0);
+  spmv_kernel<<<blocks(m), kT, 0, h.st>>>(m, h.d_rowptr, h.d_colidx, h.d_vals, s, q, nullptr, P.d_part);
+  csne_update_kernel<<<blocks(std::max(m, n)), kT, 0, h.st>>>(n, m, x, s, r, q);
+  spmv_kernel<<<blocks(n), kT, 0, h.st>>>(n, h.d_trowptr, h.d_tcolidx, h.d_tvals, r, u, Dv, P.d_part);
+  finish_sum_kernel<<<1, kT, 0, h.st>>>(blocks(n), P.d_part, P.d_scal + 2);
+  SPAQR_CUDA(cudaGetLastError());
+}
+
 // Workspace of the iterative solvers: CGLS r, q (m) and x, p, t, u, s (n);
 // PCG nu, r, z, p, q (n) and t (m).
 static void ensure_work(Handle& h) {
@@ -1105,7 +1133,8 @@ static void ensure_work(Handle& h) {
   h.work_elems = need;
   if (P.graph) cudaGraphExecDestroy(P.graph);
   if (P.graph_pcg) cudaGraphExecDestroy(P.graph_pcg);
-  P.graph = P.graph_pcg = nullptr;
+  if (P.graph_csne) cudaGraphExecDestroy(P.graph_csne);
+  P.graph = P.graph_pcg = P.graph_csne = nullptr;
 }
 
 void IterSolve::begin() {
@@ -1117,7 +1146,16 @@ void IterSolve::begin() {
   double* w = hh.d_work;
   it = 0;
   done = false;
-  if (kind == 0) {
+  if (kind == 2) {
+    // CSNE: x = 0, r = b, u = A~^T r, res0 = |D^{-1} A~^T b|
+    double* r = w;
+    double* xt = w + 2 * m;
+    double* u = xt + 3 * n;
+    SPAQR_CUDA(cudaMemsetAsync(xt, 0, (size_t)n * sizeof(double), hh.st));
+    SPAQR_CUDA(cudaMemcpyAsync(r, rhs, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, hh.st));
+    spmv_kernel<<<blocks(n), kT, 0, hh.st>>>(n, hh.d_trowptr, hh.d_tcolidx, hh.d_tvals, r, u, hh.d_D, P.d_part);
+    finish_sum_kernel<<<1, kT, 0, hh.st>>>(blocks(n), P.d_part, P.d_scal + 2);
+  } else if (kind == 0) {
     // CGLS: x = 0, r = b, s = W^{-T} (A~^T r), p = s, gamma = |s|^2, res0 = |D^{-1} A~^T b|
     double* r = w;
     double* xt = w + 2 * m;
@@ -1166,7 +1204,7 @@ void IterSolve::begun() {
                                                  : "right-hand side g has non-finite entries");
   rel = norm0 > 0.0 ? 1.0 : 0.0;
   done = !(norm0 > 0.0);
-  if (kind == 0) {
+  if (kind != 1) {
     h->stats.t_kernel[4] = h->stats.t_kernel[5] = 0.0;
     h->stats.n_kernel[4] = h->stats.n_kernel[5] = 0;
   }
@@ -1178,9 +1216,16 @@ void IterSolve::step() {
   const int64_t m = hh.m, n = hh.n;
   double* w = hh.d_work;
   const bool graphs = hh.opt.use_graphs != 0;
-  cudaGraphExec_t* g = kind == 0 ? &P.graph : &P.graph_pcg;
+  cudaGraphExec_t* g = kind == 0 ? &P.graph : (kind == 1 ? &P.graph_pcg : &P.graph_csne);
   auto body = [&](bool capturing) {
-    if (kind == 0) {
+    if (kind == 2) {
+      double* r = w;
+      double* q = r + m;
+      double* xt = q + m;
+      double* u = xt + 3 * n;
+      double* sv = u + n;
+      csne_body(hh, xt, r, q, u, sv, hh.d_D);
+    } else if (kind == 0) {
       double* r = w;
       double* q = r + m;
       double* xt = q + m;
@@ -1224,14 +1269,14 @@ void IterSolve::stepped() {
 void IterSolve::finish() {
   Handle& hh = *h;
   const int64_t m = hh.m, n = hh.n;
-  const double* sol = kind == 0 ? hh.d_work + 2 * m : hh.d_work;  // x~ (CGLS) or nu (PCG)
+  const double* sol = kind != 1 ? hh.d_work + 2 * m : hh.d_work;  // x~ (CGLS, CSNE) or nu (PCG)
   scale_kernel<<<blocks(n), kT, 0, hh.st>>>(n, sol, hh.d_D, out);
   SPAQR_CUDA(cudaGetLastError());
 }
 
 void IterSolve::report(spaqr_solve_info* info) {
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (kind == 0) {
+  if (kind != 1) {
     h->stats.t_solve = secs;
     h->stats.iters = it;
   }
@@ -1285,6 +1330,18 @@ void cgls(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info)
   std::vector<IterSolve> S(1);
   S[0].h = &h;
   S[0].kind = 0;
+  S[0].rhs = b_dev;
+  S[0].out = x_dev;
+  S[0].tol = h.opt.tol;
+  S[0].maxit = h.opt.maxit;
+  run_iterative(S);
+  S[0].report(info);
+}
+
+void csne(Handle& h, const double* b_dev, double* x_dev, spaqr_solve_info* info) {
+  std::vector<IterSolve> S(1);
+  S[0].h = &h;
+  S[0].kind = 2;
   S[0].rhs = b_dev;
   S[0].out = x_dev;
   S[0].tol = h.opt.tol;
