@@ -111,6 +111,28 @@ typedef struct spaqr_analysis spaqr_analysis;
 
 /* Errors: INVALID_ARG for non-positive sizes or depth outside [1, 30]. */
 int spaqr_analyze(const spaqr_grid_ordering* ord, spaqr_analysis** out);
+
+/* spaqr_analyze_matrix: the same analysis for a matrix without a grid, from
+ * the pattern of A alone (host only; values are not read): nested dissection
+ * of graph(A^T A) (columns adjacent when a row holds both) to `depth` levels by
+ * level structures of breadth-first searches, the interfaces of every
+ * separator at every stage from the adjacency of its vertices to the
+ * subdomains and interfaces below it, and the merge hierarchy (Section 2.2,
+ * Fig. 2-3; Section 2.6).  On a grid with the geometric tree the interfaces
+ * are those of spaqr_analyze.  The result is used with spaqr_factor like any
+ * analysis (A's n must equal the analysed n).  A is caller-owned host CSR;
+ * nothing is kept.  Errors: INVALID_ARG (bad CSR arrays, depth outside [1, 30]). */
+int spaqr_analyze_matrix(const spaqr_csr* A, int depth, spaqr_analysis** out);
+
+/* spaqr_match: the row-to-column matching of Section 2.2 for matrices without
+ * a natural one: match[j] (n entries, caller-owned host memory) receives the
+ * row matched to column j, distinct rows, each with a nonzero in its column,
+ * chosen to maximise the sum of log|a_ij| over the matched entries (a
+ * maximum-product matching; the paper uses a third-party routine for it).
+ * Pass it to spaqr_factor in spaqr_csr.match.  Host only.  Errors: INVALID_ARG
+ * (bad CSR arrays, m < n), RANK_DEFICIENT (no column-perfect matching exists:
+ * A is structurally rank deficient). */
+int spaqr_match(const spaqr_csr* A, int32_t* match);
 void spaqr_analysis_destroy(spaqr_analysis* an);
 
 /* Number of clusters alive at stage k (1 <= k <= depth) and the total number

@@ -110,9 +110,27 @@ def column_scaling(A: sp.csr_matrix):
     return D, sp.csr_matrix(A @ sp.diags(D))
 
 
+class GeometricOrdering:
+    """The geometric nested dissection of a grid (oracle/nd.py readings)."""
+
+    def __init__(self, dims, depth: int):
+        self.dims, self.L = dims, depth
+        self.nodes = nd.build_tree(dims, depth)
+        self.keys = nd.finest_keys(self.nodes, dims, depth)
+
+    def clusters_at_stage(self, k: int):
+        return nd.clusters_at_stage(self.nodes, self.keys, self.L, k)
+
+    def parent_key(self, key: tuple, k: int) -> tuple:
+        return nd.parent_key(key, self.nodes, k)
+
+
 class OracleSpaQR:
     def __init__(self, prob, depth: int, eps: float, skip: int = 2, mode: str = "spaqr", rows: str = "tree",
-                 within: str = "asc"):
+                 within: str = "asc", ordering=None):
+        # the clusters of every stage and their merge map: the geometric tree of
+        # the grid (oracle/nd.py) unless an ordering (oracle/algebraic.py) is given
+        self.ordering = ordering
         self.rows_rule = rows
         # Order inside one elimination round (R5) and one step-2 colour (R8):
         # "asc" (the reading) or "desc".  Members of a round or a colour are
@@ -206,8 +224,8 @@ class OracleSpaQR:
         prob = self.prob
         A = prob.to_scipy()
         self.D, self.At = column_scaling(A)
-        self.nodes = nd.build_tree(prob.dims, self.L)
-        self.keys = nd.finest_keys(self.nodes, prob.dims, self.L)
+        if self.ordering is None:
+            self.ordering = GeometricOrdering(prob.dims, self.L)
         self._init_stage(self.L)
         for k in range(self.L, 0, -1):
             self.stage = k
@@ -222,7 +240,7 @@ class OracleSpaQR:
         return self
 
     def _init_stage(self, L):
-        self.clusters = nd.clusters_at_stage(self.nodes, self.keys, L, L)
+        self.clusters = self.ordering.clusters_at_stage(L)
         nvert = self.prob.n
         cid_of = np.full(nvert, -1, dtype=np.int64)
         pos_in = np.zeros(nvert, dtype=np.int64)
@@ -446,12 +464,12 @@ class OracleSpaQR:
             self._del_group(g1.gid)
 
     def _merge(self, k):
-        new = nd.clusters_at_stage(self.nodes, self.keys, self.L, k - 1)
+        new = self.ordering.clusters_at_stage(k - 1)
         index = {(c.node, c.key): i for i, c in enumerate(new)}
         parent = {}
         for cid in sorted(self.alive):
             c = self.clusters[cid]
-            parent[cid] = index[(c.node, nd.parent_key(c.key, self.nodes, k))]
+            parent[cid] = index[(c.node, self.ordering.parent_key(c.key, k))]
         children = {}
         for cid in sorted(self.alive):
             children.setdefault(parent[cid], []).append(cid)

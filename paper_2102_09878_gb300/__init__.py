@@ -13,7 +13,7 @@ import numpy as np
 from . import capi
 from .capi import SpaqrError
 
-__all__ = ["Analysis", "SpaQR", "SpaqrError", "dense_front_qr", "dense_front_qr_f32", "dense_qrcp", "dense_tc_gemm",
+__all__ = ["Analysis", "SpaQR", "SpaqrError", "match", "dense_front_qr", "dense_front_qr_f32", "dense_qrcp", "dense_tc_gemm",
            "factor_batch", "solve_batch", "solve_normal_batch", "autotune", "load_tuning", "capi"]
 
 
@@ -23,18 +23,49 @@ def _stream_ptr(stream):
     return C.c_void_p(int(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream))
 
 
-class Analysis:
-    """Symbolic analysis of an nx*ny*nz grid to nested-dissection depth L (host only)."""
+def _csr_struct(A):
+    """(spaqr_csr, arrays kept alive) for any object with m, n, rowptr, colidx, vals (and optional match)."""
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
+    va = np.ascontiguousarray(A.vals, dtype=np.float64)
+    mt = getattr(A, "match", None)
+    mt = None if mt is None else np.ascontiguousarray(mt, dtype=np.int32)
+    csr = capi.Csr(int(A.m), int(A.n), int(rp[-1]), capi.ptr(rp), capi.ptr(ci), capi.ptr(va),
+                   None if mt is None else capi.ptr(mt))
+    return csr, (rp, ci, va, mt)
 
-    def __init__(self, dims, depth: int):
+
+def match(A) -> np.ndarray:
+    """Maximum-weight row-to-column matching of A (spaqr_match): match[j] = row of column j."""
+    csr, keep = _csr_struct(A)
+    out = np.zeros(int(A.n), np.int32)
+    capi.check(capi.load().spaqr_match(C.byref(csr), capi.ptr(out)))
+    return out
+
+
+class Analysis:
+    """Symbolic analysis of an nx*ny*nz grid to nested-dissection depth L (host only);
+    Analysis.from_matrix builds it from graph(A^T A) of a matrix without a grid."""
+
+    def __init__(self, dims, depth: int, _handle=None):
         lib = capi.load()
         nx, ny, nz = (tuple(dims) + (1, 1))[:3]
         self.dims = (int(nx), int(ny), int(nz))
         self.depth = int(depth)
+        if _handle is not None:
+            self._h = _handle
+            return
         ordg = capi.GridOrdering(self.dims[0], self.dims[1], self.dims[2], self.depth)
         h = C.c_void_p()
         capi.check(lib.spaqr_analyze(C.byref(ordg), C.byref(h)))
         self._h = h
+
+    @classmethod
+    def from_matrix(cls, A, depth: int):
+        csr, keep = _csr_struct(A)
+        h = C.c_void_p()
+        capi.check(capi.load().spaqr_analyze_matrix(C.byref(csr), int(depth), C.byref(h)))
+        return cls((int(A.n), 1, 1), depth, _handle=h)
 
     @property
     def handle(self):

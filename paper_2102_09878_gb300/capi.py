@@ -107,6 +107,8 @@ SIGNATURES = {
     "spaqr_default_options": (None, [C.POINTER(Options)]),
     "spaqr_analyze": (C.c_int, [C.POINTER(GridOrdering), C.POINTER(C.c_void_p)]),
     "spaqr_analysis_destroy": (None, [C.c_void_p]),
+    "spaqr_analyze_matrix": (C.c_int, [C.POINTER(Csr), C.c_int, C.POINTER(C.c_void_p)]),
+    "spaqr_match": (C.c_int, [C.POINTER(Csr), C.c_void_p]),
     "spaqr_analysis_stage_size": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "spaqr_analysis_stage_clusters": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spaqr_factor": (C.c_int, [C.POINTER(Csr), C.c_void_p, C.POINTER(Options), C.POINTER(C.c_void_p)]),

@@ -68,17 +68,23 @@ Handle::~Handle() {
 }  // namespace spaqr
 
 namespace {
-// Host-side checks of a matrix and options (before any device work, so that
-// they also answer without a GPU).
-void check_input(const spaqr_csr* A, const spaqr::Analysis& a, const spaqr_options& opt) {
-  if (A->n != a.n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A has n != nx*ny*nz columns");
-  if (A->m < A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A must have m >= n");
+// The CSR arrays of A are well formed (sizes, monotone rowptr, column indices in range).
+void check_csr(const spaqr_csr* A) {
+  if (A->m < 0 || A->n <= 0 || A->nnz < 0) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "bad sizes");
   if (!A->rowptr || !A->colidx || !A->vals) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "null CSR array");
   if (A->rowptr[0] != 0 || A->rowptr[A->m] != A->nnz) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "bad rowptr");
   for (int64_t r = 0; r < A->m; ++r)
     if (A->rowptr[r + 1] < A->rowptr[r]) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "rowptr not monotone");
   for (int64_t e = 0; e < A->nnz; ++e)
     if (A->colidx[e] < 0 || A->colidx[e] >= A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "column index out of range");
+}
+
+// Host-side checks of a matrix and options (before any device work, so that
+// they also answer without a GPU).
+void check_input(const spaqr_csr* A, const spaqr::Analysis& a, const spaqr_options& opt) {
+  if (A->n != a.n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A has n != nx*ny*nz columns");
+  if (A->m < A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A must have m >= n");
+  check_csr(A);
   if (A->match) {
     std::vector<char> used((size_t)A->m, 0);
     for (int64_t j = 0; j < A->n; ++j) {
@@ -337,6 +343,29 @@ int spaqr_analyze(const spaqr_grid_ordering* ord, spaqr_analysis** out) {
     auto* a = new spaqr_analysis();
     a->an.reset(spaqr::build_analysis(ord->nx, ord->ny, ord->nz, ord->depth));
     *out = a;
+    return SPAQR_OK;
+  });
+}
+
+int spaqr_analyze_matrix(const spaqr_csr* A, int depth, spaqr_analysis** out) {
+  if (!A || !out) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    check_csr(A);
+    auto* a = new spaqr_analysis();
+    a->an.reset(spaqr::build_analysis_matrix(A->m, A->n, A->rowptr, A->colidx, depth));
+    *out = a;
+    return SPAQR_OK;
+  });
+}
+
+int spaqr_match(const spaqr_csr* A, int32_t* match) {
+  if (!A || !match) return fail(SPAQR_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    check_csr(A);
+    if (A->m < A->n) throw spaqr::Error(SPAQR_ERR_INVALID_ARG, "A must have m >= n");
+    if (!spaqr::max_weight_matching(A->m, A->n, A->rowptr, A->colidx, A->vals, match))
+      throw spaqr::Error(SPAQR_ERR_RANK_DEFICIENT, "A has no matching of every column to a distinct row (structurally "
+                                                   "rank deficient)");
     return SPAQR_OK;
   });
 }

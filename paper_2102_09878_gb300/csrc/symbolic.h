@@ -45,5 +45,11 @@ struct Analysis {
 
 // Builds the full analysis; throws std::invalid_argument on bad sizes.
 Analysis* build_analysis(int nx, int ny, int nz, int depth);
+// The same structure from graph(A^T A) of a CSR matrix (symbolic_alg.cpp):
+// algebraic nested dissection, interfaces by adjacency, merge hierarchy.
+Analysis* build_analysis_matrix(int64_t m, int64_t n, const int64_t* rowptr, const int32_t* colidx, int depth);
+// Maximum-weight column-perfect row matching (sum of log|a_ij|); false if none exists.
+bool max_weight_matching(int64_t m, int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* vals,
+                         int32_t* match);
 
 }  // namespace spaqr

@@ -1,0 +1,89 @@
+"""GPU spaQR on irregular matrices with the algebraic ordering, against the
+oracle (Section 2.2 ordering and matching; Algorithm 1; CGLS, Section 4).
+
+The library's analysis (spaqr_analyze_matrix) equals the oracle's cluster by
+cluster (tests/test_algebraic_ordering.py), so both factor the same problem;
+the matching is the oracle's maximum-weight matching, passed to both sides
+(its optimum is not unique, and the row owners depend on it).
+* eps = 0: every stored op equals the oracle's to 1e-10 (same readings, same
+  order), and CGLS stops at once.
+* eps > 0: ||A^T r|| / ||A^T b|| < 1e-10 with an iteration count within
+  max(1, ceil(0.1 it_oracle)) of the oracle's; the mixed-precision factor
+  reaches the same residual.
+* The library's own matching (spaqr_match) gives a converging solve too.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from inputs.irregular import knn_problem
+from oracle.algebraic import AlgebraicOrdering, max_weight_matching
+from oracle.spaqr import OracleSpaQR
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _res(p, x):
+    A = p.to_scipy()
+    return np.linalg.norm(A.T @ (A @ x - p.b)) / np.linalg.norm(A.T @ p.b)
+
+
+CASES = [(2000, 6, "u12", 1, 8), (3000, 4, "c2", 2, 9)]
+
+
+@pytest.mark.parametrize("n,k,law,seed,depth", CASES)
+def test_eps0_ops_match_oracle(n, k, law, seed, depth):
+    import paper_2102_09878_gb300 as sq
+
+    p = knn_problem(n, k=k, law=law, seed=seed)
+    A = p.to_scipy()
+    p.match = max_weight_matching(A)
+    o = OracleSpaQR(p, depth, 0.0, ordering=AlgebraicOrdering(A, depth)).factor()
+    g = sq.SpaQR(p, sq.Analysis.from_matrix(p, depth), eps=0.0)
+    gops = g.ops()
+    assert len(gops) == len(o.ops)
+    for go, oo in zip(gops, o.ops):
+        assert go["kind"] == oo.kind and go["stage"] == oo.stage
+        np.testing.assert_array_equal(go["slots"], oo.slots)
+        if oo.kind == "Rs":
+            np.testing.assert_array_equal(go["nslots"], oo.nslots)
+            assert _rel(np.hstack([go["R"], go["Rn"]]), np.hstack([oo.R, oo.Rn])) < 1e-10
+        elif oo.kind == "Rp":
+            assert _rel(go["R"], oo.R) < 1e-10
+    x = g.solve(p.b)
+    assert g.last_info["iters"] <= 2 and _res(p, x) < 1e-10
+
+
+@pytest.mark.parametrize("n,k,law,seed,depth", CASES)
+def test_eps_positive_matches_oracle(n, k, law, seed, depth):
+    import paper_2102_09878_gb300 as sq
+
+    p = knn_problem(n, k=k, law=law, seed=seed)
+    A = p.to_scipy()
+    p.match = max_weight_matching(A)
+    eps = 1e-3
+    xo, io = OracleSpaQR(p, depth, eps, ordering=AlgebraicOrdering(A, depth)).factor().solve(p.b)
+    an = sq.Analysis.from_matrix(p, depth)
+    g = sq.SpaQR(p, an, eps=eps)
+    x = g.solve(p.b)
+    it, it_o = g.last_info["iters"], io["iters"]
+    assert _res(p, x) < 1e-10 and abs(it - it_o) <= max(1, math.ceil(0.1 * it_o)), (it, it_o)
+    assert _rel(x, xo) < 1e-7
+    gm = sq.SpaQR(p, an, eps=eps, precision="mixed")
+    xm = gm.solve(p.b)
+    assert gm.last_info["converged"] and _res(p, xm) < 1e-10
+
+
+def test_library_matching_drives_the_factor():
+    import paper_2102_09878_gb300 as sq
+
+    p = knn_problem(5000, k=5, seed=9)
+    p.match = sq.match(p)
+    g = sq.SpaQR(p, sq.Analysis.from_matrix(p, 10), eps=1e-3)
+    x = g.solve(p.b)
+    assert g.last_info["converged"] and _res(p, x) < 1e-10
