@@ -201,20 +201,20 @@ class AlgebraicOrdering:
         out.sort(key=lambda c: (c.node, c.key))
         return out
 
-    def parent_key(self, key: tuple, k: int) -> tuple:
-        """The stage-(k-1) key of the vertices whose stage-k key is `key`:
-        the stage-(k-1) key of any one of them (A3 makes it the same for all)."""
-        label, kk = self._stages[k]
+    def parent_key(self, key: tuple, k: int, node: int) -> tuple:
+        """The stage-(k-1) key of the vertices of separator `node` whose stage-k
+        key is `key`: the stage-(k-1) key of any one of them (A3 makes it the
+        same for all).  Two separators can share a key, hence the node."""
+        if node_level(node) >= k - 1:  # eliminated at stage k - 1: one cluster
+            return ()
+        kk = self._stages[k][1]
         if not hasattr(self, "_first"):
             self._first = {}
         idx = self._first.setdefault(k, {})
         if not idx:
             for v, x in kk.items():
-                idx.setdefault(x, v)
-        v = idx[key]
-        if node_level(int(self.node_of[v])) >= k - 1:  # its separator is eliminated at stage k - 1: one cluster
-            return ()
-        return self._stages[k - 1][1][v]
+                idx.setdefault((int(self.node_of[v]), x), v)
+        return self._stages[k - 1][1][idx[(node, key)]]
 
 
 def max_weight_matching(A) -> np.ndarray:

@@ -121,7 +121,7 @@ class GeometricOrdering:
     def clusters_at_stage(self, k: int):
         return nd.clusters_at_stage(self.nodes, self.keys, self.L, k)
 
-    def parent_key(self, key: tuple, k: int) -> tuple:
+    def parent_key(self, key: tuple, k: int, node: int = -1) -> tuple:
         return nd.parent_key(key, self.nodes, k)
 
 
@@ -469,7 +469,7 @@ class OracleSpaQR:
         parent = {}
         for cid in sorted(self.alive):
             c = self.clusters[cid]
-            parent[cid] = index[(c.node, self.ordering.parent_key(c.key, k))]
+            parent[cid] = index[(c.node, self.ordering.parent_key(c.key, k, c.node))]
         children = {}
         for cid in sorted(self.alive):
             children.setdefault(parent[cid], []).append(cid)

@@ -19,6 +19,7 @@
 #include <cfloat>
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 namespace cg = cooperative_groups;
@@ -613,65 +614,146 @@ __device__ __forceinline__ float recompute_frac<float>() {
   return 3.4527e-4f;
 }
 
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi) / 2), the operations built from the error-free
+// two-sum (Knuth) and two-product (one fused multiply-add) transformations
+// (Dekker 1971; Ogita, Rump and Oishi 2005).  About 44 significant bits.  The
+// FP32 pivoted QR forms R_ii and takes the rank decision with it: on this GPU
+// every FP64 instruction of a warp holds the FP64 pipe for tens of cycles, so
+// a handful of them per pivot step would dominate the step.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_quick(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float z = s - a;
+  return DF{s, (a - (s - z)) + (b - z)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = df_two_sum(a.hi, b.hi);
+  return df_quick(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF df_sqr(float a) {
+  const float p = a * a;
+  return DF{p, fmaf(a, a, -p)};
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);
+  return df_quick(p, e + (a.hi * b.lo + a.lo * b.hi));
+}
+__device__ __forceinline__ DF df_sqrt(DF a) {  // a >= 0; one Newton step from the FP32 root
+  if (!(a.hi > 0.f)) return DF{0.f, 0.f};
+  const float r = sqrtf(a.hi);
+  const float res = fmaf(-r, r, a.hi) + a.lo;
+  return df_quick(r, res * (0.5f / r));
+}
+__device__ __forceinline__ bool df_less(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
 // Sum of squares of the entries of a column to FP64 accuracy.  For FP32 data
 // every term x^2 is split exactly into p + e (p = fl(x^2), e = fma(x, x, -p))
-// and accumulated with Knuth's two-sum, the rounding errors collected in a
-// second FP32 word (the Sum2 scheme of Ogita, Rump and Oishi, "Accurate sum
-// and dot product", 2005): s + c is the exact sum up to relative errors of
-// order (n u)^2, u = 2^-24, which for the column lengths here is about 1e-11.
-// FP64 data are summed in FP64.
+// and accumulated with two-sums, the rounding errors collected in a second
+// FP32 word (the Sum2 scheme of Ogita, Rump and Oishi): s + c is the exact sum
+// up to relative errors of order (n u)^2, u = 2^-24.  FP64 data are summed in
+// FP64.  warp_total() leaves the warp's total, as a (hi, lo) pair, in every lane.
 template <typename T>
 struct SqSum;
 template <>
 struct SqSum<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s = fma(x, x, s); }
-  // the warp's total, valid in lane 0
-  __device__ __forceinline__ double warp_total() { return warp_sum(s); }
+  __device__ __forceinline__ void warp_total(double& hi, double& lo) {
+    hi = warp_sum(s);
+    lo = 0.0;
+  }
 };
 template <>
 struct SqSum<float> {
   float s = 0.f, c = 0.f;
   __device__ __forceinline__ void add(float x) {
-    const float p = x * x;
-    const float e = fmaf(x, x, -p);
-    const float t = s + p;
-    const float z = t - s;
-    c += ((s - (t - z)) + (p - z)) + e;
-    s = t;
+    const DF p = df_sqr(x);
+    const DF t = df_two_sum(s, p.hi);
+    c += t.lo + p.lo;
+    s = t.hi;
   }
-  // the warp's total, valid in lane 0: the (s, c) pairs meet by two-sums in
-  // FP32, and only lane 0 forms the FP64 value (FP64 instructions issued by a
-  // whole warp are expensive on this GPU)
-  __device__ __forceinline__ double warp_total() {
+  __device__ __forceinline__ void warp_total(float& hi, float& lo) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
       const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-      const float t = s + s2;
-      const float z = t - s;
-      c = (c + c2) + ((s - (t - z)) + (s2 - z));
-      s = t;
+      const DF t = df_two_sum(s, s2);
+      c = (c + c2) + t.lo;
+      s = t.hi;
     }
-    double r = 0.0;
-    if ((threadIdx.x & 31) == 0) r = (double)s + (double)c;
-    return r;
+    const DF r = df_quick(s, c);
+    hi = r.hi;
+    lo = r.lo;
   }
 };
 
+// The Householder data of a pivot step from alpha (the diagonal entry) and the
+// sum of squares below it (sh + sl): R_ii = beta = -sign(alpha) sqrt(alpha^2 +
+// sigma), tau = (beta - alpha) / beta, den = alpha - beta (the reflector is the
+// column below alpha divided by den), and the rank test |R_ii| < eps |R_11|
+// (stop; also when beta = 0).  r11 holds |R_11| from step 0 on (set when
+// first = true).  FP64 data: in FP64.  FP32 data: in double-float.
+template <typename T>
+struct HouseStep {
+  T beta, tau, den;
+  bool stop;
+};
+__device__ __forceinline__ HouseStep<double> house_step(double alpha, double sh, double, double eps, double& r11,
+                                                        bool first) {
+  HouseStep<double> h;
+  if (sh == 0.0) {
+    h.beta = alpha;
+    h.tau = 0.0;
+    h.den = 0.0;
+  } else {
+    const double nrm = sqrt(alpha * alpha + sh);
+    h.beta = alpha >= 0.0 ? -nrm : nrm;
+    h.tau = (h.beta - alpha) / h.beta;
+    h.den = alpha - h.beta;
+  }
+  const double ab = fabs(h.beta);
+  if (first) r11 = ab;
+  h.stop = h.beta == 0.0 || ab < eps * r11;
+  return h;
+}
+__device__ __forceinline__ HouseStep<float> house_step(float alpha, float sh, float sl, DF eps, DF& r11, bool first) {
+  HouseStep<float> h;
+  DF b;  // |beta|
+  if (sh == 0.f && sl == 0.f) {
+    b = DF{fabsf(alpha), 0.f};
+    h.beta = alpha;
+    h.tau = 0.f;
+    h.den = 0.f;
+  } else {
+    b = df_sqrt(df_add(df_sqr(alpha), DF{sh, sl}));
+    const float sg = alpha >= 0.f ? -1.f : 1.f;  // beta = sg * b
+    const DF den = df_add(DF{alpha, 0.f}, DF{-sg * b.hi, -sg * b.lo});  // alpha - beta, no cancellation
+    h.beta = sg * (b.hi + b.lo);
+    h.den = den.hi + den.lo;
+    h.tau = -h.den / h.beta;  // (beta - alpha) / beta
+  }
+  if (first) r11 = b;
+  h.stop = (b.hi == 0.f) || df_less(b, df_mul(eps, r11));
+  return h;
+}
+
 // One warp's proposal for the next pivot step, as the slab QRCP exchanges it:
 // the squared partial norm that orders the pivots (v), the column (j, original
-// index; INT_MAX = none), its entry at the next diagonal position (alpha), and
-// the Householder data of that column formed in FP64 from alpha and the
-// FP64-accurate sum of squares below it: R_ii = beta, tau, and
-// den = alpha - beta (0 when the column is zero below alpha).
+// index; INT_MAX = none), its entry at the next diagonal position (alpha) and
+// the FP64-accurate sum of squares of its entries below (sh + sl).
 template <typename T, typename N>
 struct QrcpProp {
   N v;
   int j;
-  T alpha;
-  double beta, tau;
-  T den;
+  T alpha, sh, sl;
 };
 
 // Lowest original column index among equal norms: the pivot rule of the oracle.
@@ -700,30 +782,17 @@ __device__ __forceinline__ int warp_argmax(N& v, int& j) {
 }
 
 // The warp's record for step i_next: best column (v, j) of the warp (every lane
-// holds it); the sum of squares over rows i_next+1..m-1, R_ii and tau of that
-// column are formed in lane 0 only.  Valid in lane 0.
+// holds it), the sum of squares over rows i_next+1..m-1 of that column and its
+// row i_next.  Valid in every lane.
 template <typename T, typename N>
 __device__ __forceinline__ QrcpProp<T, N> warp_record(const T* X, int m, int ldx, int j0, int i_next, N v, int j) {
-  QrcpProp<T, N> r{v, j, T(0), 0.0, 0.0, T(0)};
+  QrcpProp<T, N> r{v, j, T(0), T(0), T(0)};
   if (j == INT_MAX || i_next >= m) return r;
   const T* col = X + (int64_t)(j - j0) * ldx;
   SqSum<T> acc;
   for (int q = i_next + 1 + (int)(threadIdx.x & 31); q < m; q += 32) acc.add(col[q]);
-  const double sig = acc.warp_total();
-  if ((threadIdx.x & 31) == 0) {
-    const double alpha = (double)col[i_next];
-    r.alpha = col[i_next];
-    if (sig == 0.0) {
-      r.beta = alpha;
-      r.tau = 0.0;
-      r.den = T(0);
-    } else {
-      const double nrm = sqrt(alpha * alpha + sig);
-      r.beta = alpha >= 0.0 ? -nrm : nrm;
-      r.tau = (r.beta - alpha) / r.beta;
-      r.den = (T)(alpha - r.beta);
-    }
-  }
+  acc.warp_total(r.sh, r.sl);
+  r.alpha = col[i_next];
   return r;
 }
 
@@ -846,7 +915,17 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
     const QrcpProp<T, N> r = warp_record<T, N>(X, m, ldx, j0, 0, wv, wj);
     if (lane == 0) rec[warp] = r;
   }
-  double r11 = 0.0;
+  // eps and |R_11| in the arithmetic of the rank test (FP64, or double-float for FP32 data)
+  using Acc = typename std::conditional<sizeof(T) == 8, double, DF>::type;
+  Acc eps_x, r11;
+  if constexpr (sizeof(T) == 8) {
+    eps_x = eps;
+    r11 = 0.0;
+  } else {
+    const float e_hi = (float)eps;
+    eps_x = DF{e_hi, (float)(eps - (double)e_hi)};
+    r11 = DF{0.f, 0.f};
+  }
   int k = 0;
   int pend_p = -1, pend_i = -1;  // pivot column this CTA still has to write (CS > 1)
   T pend_beta = T(0);
@@ -890,17 +969,12 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
     }
     const int p = best.j;
     if (p == INT_MAX) break;  // no proposal (non-finite norms): the same p everywhere
-    // the rank test in FP64, in lane 0 of every warp (same record, same answer)
-    int stop = 0;
-    if (lane == 0) {
-      const double ab = fabs(best.beta);
-      if (i == 0) r11 = ab;
-      stop = (best.beta == 0.0 || ab < eps * r11) ? 1 : 0;
-    }
-    if (__shfl_sync(0xffffffffu, stop, 0)) break;  // rank reached: the same decision everywhere
-    const T den = __shfl_sync(0xffffffffu, best.den, 0);
-    const T tau_t = __shfl_sync(0xffffffffu, (T)best.tau, 0);
-    const T beta_t = __shfl_sync(0xffffffffu, (T)best.beta, 0);
+    // R_ii, tau and the rank test, the same arithmetic in every thread
+    const HouseStep<T> hs = house_step(best.alpha, best.sh, best.sl, eps_x, r11, i == 0);
+    if (hs.stop) break;  // rank reached: the same decision everywhere
+    const T den = hs.den;
+    const T tau_t = hs.tau;
+    const T beta_t = hs.beta;
     const int owner = p / nl;
     const int rb = i & ~(VW - 1);  // first row of the vectors the update touches
     {  // the reflector by row: 0 above row i, 1 at row i, the scaled column below

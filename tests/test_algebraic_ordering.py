@@ -79,7 +79,7 @@ def test_interfaces_reduce_to_the_geometric_ones(dims, depth):
             Gp = {(c.node, c.key): tuple(c.verts) for c in geo.clusters_at_stage(k - 1)}
             Ap = {(c.node, c.key): tuple(c.verts) for c in alg.clusters_at_stage(k - 1)}
             pg = {tuple(c.verts): Gp[(c.node, geo.parent_key(c.key, k))] for c in G if c.level < k}
-            pa = {tuple(c.verts): Ap[(c.node, alg.parent_key(c.key, k))] for c in Al if c.level < k}
+            pa = {tuple(c.verts): Ap[(c.node, alg.parent_key(c.key, k, c.node))] for c in Al if c.level < k}
             assert pg == pa
 
 
@@ -116,6 +116,25 @@ def test_library_analysis_matches_oracle(prob, depth):
     o = AlgebraicOrdering(prob.to_scipy(), depth)
     for k in range(1, depth + 1):
         assert _lib_stage(an, k) == [(c.node, tuple(int(v) for v in c.verts)) for c in o.clusters_at_stage(k)]
+
+
+@pytest.mark.parametrize("prob,depth", [(knn_problem(2000, k=6, seed=1), 8), (knn_problem(3000, k=4, law="c2", seed=2), 9)])
+def test_merge_map_is_containment(prob, depth):
+    """The oracle's merge map (parent_key) sends every stage-k interface to the
+    stage-(k-1) interface of the same separator that contains its vertices."""
+    o = AlgebraicOrdering(prob.to_scipy(), depth)
+    for k in range(depth, 1, -1):
+        nxt = o.clusters_at_stage(k - 1)
+        where = {}
+        for i, c in enumerate(nxt):
+            for v in c.verts:
+                where[int(v)] = i
+        index = {(c.node, c.key): i for i, c in enumerate(nxt)}
+        for c in o.clusters_at_stage(k):
+            if c.level >= k:
+                continue
+            i = index[(c.node, o.parent_key(c.key, k, c.node))]
+            assert all(where[int(v)] == i for v in c.verts)
 
 
 @pytest.mark.parametrize("prob", [knn_problem(300, seed=1), knn_problem(5000, k=6, law="c2", seed=3),

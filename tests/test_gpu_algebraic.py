@@ -5,8 +5,11 @@ The library's analysis (spaqr_analyze_matrix) equals the oracle's cluster by
 cluster (tests/test_algebraic_ordering.py), so both factor the same problem;
 the matching is the oracle's maximum-weight matching, passed to both sides
 (its optimum is not unique, and the row owners depend on it).
-* eps = 0: every stored op equals the oracle's to 1e-10 (same readings, same
-  order), and CGLS stops at once.
+* Direct mode (no compression): every stored front R = [R_ss R_sn] equals the
+  oracle's to 1e-10, i.e. the analysis, the matching and the row rule agree.
+* eps = 0 with scaling and sparsification: the factor is exact -- A D W^{-1}
+  has orthonormal columns (Q^T A W^{-1} = I, Section 2.7) and CGLS stops at
+  once on the normal-equation solution.
 * eps > 0: ||A^T r|| / ||A^T b|| < 1e-10 with an iteration count within
   max(1, ceil(0.1 it_oracle)) of the oracle's; the mixed-precision factor
   reaches the same residual.
@@ -37,24 +40,38 @@ CASES = [(2000, 6, "u12", 1, 8), (3000, 4, "c2", 2, 9)]
 
 
 @pytest.mark.parametrize("n,k,law,seed,depth", CASES)
-def test_eps0_ops_match_oracle(n, k, law, seed, depth):
+def test_direct_mode_fronts_match_oracle(n, k, law, seed, depth):
     import paper_2102_09878_gb300 as sq
 
     p = knn_problem(n, k=k, law=law, seed=seed)
     A = p.to_scipy()
     p.match = max_weight_matching(A)
-    o = OracleSpaQR(p, depth, 0.0, ordering=AlgebraicOrdering(A, depth)).factor()
-    g = sq.SpaQR(p, sq.Analysis.from_matrix(p, depth), eps=0.0)
+    o = OracleSpaQR(p, depth, 0.0, mode="direct", ordering=AlgebraicOrdering(A, depth)).factor()
+    g = sq.SpaQR(p, sq.Analysis.from_matrix(p, depth), mode="direct")
     gops = g.ops()
     assert len(gops) == len(o.ops)
     for go, oo in zip(gops, o.ops):
-        assert go["kind"] == oo.kind and go["stage"] == oo.stage
+        assert go["kind"] == oo.kind == "Rs" and go["stage"] == oo.stage
         np.testing.assert_array_equal(go["slots"], oo.slots)
-        if oo.kind == "Rs":
-            np.testing.assert_array_equal(go["nslots"], oo.nslots)
-            assert _rel(np.hstack([go["R"], go["Rn"]]), np.hstack([oo.R, oo.Rn])) < 1e-10
-        elif oo.kind == "Rp":
-            assert _rel(go["R"], oo.R) < 1e-10
+        np.testing.assert_array_equal(go["nslots"], oo.nslots)
+        assert _rel(np.hstack([go["R"], go["Rn"]]), np.hstack([oo.R, oo.Rn])) < 1e-10
+
+
+@pytest.mark.parametrize("n,k,law,seed,depth", CASES)
+def test_eps0_factor_is_exact(n, k, law, seed, depth):
+    import torch
+
+    import paper_2102_09878_gb300 as sq
+
+    p = knn_problem(n, k=k, law=law, seed=seed)
+    p.match = max_weight_matching(p.to_scipy())
+    g = sq.SpaQR(p, sq.Analysis.from_matrix(p, depth), eps=0.0)
+    assert sum(op["kind"] == "Rp" for op in g.ops()) > 0
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        z = torch.from_numpy(rng.standard_normal(p.n)).cuda()
+        q = g.apply_A(g.apply_Winv(z.clone()))
+        assert abs(q.norm().item() / z.norm().item() - 1.0) < 1e-10
     x = g.solve(p.b)
     assert g.last_info["iters"] <= 2 and _res(p, x) < 1e-10
 
@@ -82,8 +99,12 @@ def test_eps_positive_matches_oracle(n, k, law, seed, depth):
 def test_library_matching_drives_the_factor():
     import paper_2102_09878_gb300 as sq
 
-    p = knn_problem(5000, k=5, seed=9)
+    # (with k = 5 nearest neighbours some interfaces of this family lose full
+    # rank at eps = 1e-3 -- the oracle stops there with a singular A_pp -- so
+    # k = 6, where both matchings factor and converge in the oracle)
+    p = knn_problem(5000, k=6, seed=9)
     p.match = sq.match(p)
     g = sq.SpaQR(p, sq.Analysis.from_matrix(p, 10), eps=1e-3)
     x = g.solve(p.b)
     assert g.last_info["converged"] and _res(p, x) < 1e-10
+    assert g.last_info["iters"] <= 6
