@@ -1129,336 +1129,6 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
   if (CS > 1) cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
-// ----------------------------------------------------- QRCP (earlier form)
-// Column-pivoted Householder QR stopped at the rank, one thread-block cluster
-// of CS CTAs per matrix.  CTA r of the cluster owns the column slab
-// [r*nl, (r+1)*nl) (nl = ceil(n/CS)), staged in its shared memory (SMEM) or in
-// the work buffer.  Columns never move: at step i every CTA proposes its
-// not-yet-pivoted column of largest squared norm (ties to the lowest original
-// index), the cluster reads all proposals through distributed shared memory,
-// the owner of the pivot builds the reflector, and every CTA copies it from
-// the owner and applies it to its own slab.  Two cluster barriers per step.
-template <typename T, bool SMEM, int KG>
-__global__ void __launch_bounds__(kThreads, 1) qrcp_cluster_kernel(const QrcpDesc<T>* descs, double eps, int nl_max,
-                                                                int m_max) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int CS = (int)cl.num_blocks();
-  const int rank = (int)cl.block_rank();
-  const QrcpDesc<T> d = descs[blockIdx.x / CS];
-  const int m = d.m, n = d.n;
-  const int nl = (n + CS - 1) / CS;
-  const int j0 = min(n, rank * nl), j1 = min(n, j0 + nl);
-  const int nloc = j1 - j0;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  using N = T;  // partial column norms and pivot proposals in the data's precision
-  N* nu = reinterpret_cast<N*>(smraw);  // nl_max
-  N* nuref = nu + nl_max;               // nl_max
-  int* step_of = reinterpret_cast<int*>(nuref + nl_max);  // nl_max
-  int* act = step_of + nl_max;                            // unpivoted local columns, nl_max
-  int* pos = act + nl_max;                                // position of each column in act
-  T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // 2 x (m_max + 2)
-  T* taus = vbuf + 2 * ((m_max + 3) & ~1);         // min(m_max, n) + 2
-  T* X = SMEM ? taus + ((m_max + 3) & ~1) : d.work + (size_t)j0 * m;
-  __shared__ N cand_v;
-  __shared__ int cand_j;
-  __shared__ double s_beta;
-  __shared__ T s_tau;
-  __shared__ int s_stop, s_piv, s_nact;
-  __shared__ N red_v[kWarps];
-  __shared__ int red_i[kWarps];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
-    const int r = (int)(e % m), c = (int)(e / m);
-    X[e] = d.src[r + (int64_t)(j0 + c) * d.ld];
-  }
-  __syncthreads();
-  for (int c = warp; c < nloc; c += kWarps) {
-    N sq = N(0);
-    for (int r = lane; r < m; r += 32) {
-      const N v = (N)X[r + (int64_t)c * m];
-      sq += v * v;
-    }
-    sq = warp_sum(sq);
-    if (lane == 0) {
-      nu[c] = sq;
-      nuref[c] = sq;
-      step_of[c] = -1;
-    }
-  }
-  for (int c = threadIdx.x; c < nloc; c += kThreads) {
-    act[c] = c;
-    pos[c] = c;
-  }
-  if (threadIdx.x == 0) s_nact = nloc;
-  const int kmax = m < n ? m : n;
-  double r11 = 0.0;
-  int k = 0;
-  __syncthreads();
-  // warp-local proposal of the warp's columns (c = warp + kW * (lane + 32 t))
-  N wv = N(-1);
-  int wj = INT_MAX;
-  for (int c = warp + lane * kWarps; c < nloc; c += 32 * kWarps) {
-    const N v = nu[c];
-    if (v > wv || (v == wv && j0 + c < wj)) {
-      wv = v;
-      wj = j0 + c;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const N ov = __shfl_xor_sync(0xffffffffu, wv, o);
-    const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
-    if (ov > wv || (ov == wv && oj < wj)) {
-      wv = ov;
-      wj = oj;
-    }
-  }
-  // One cluster barrier per pivot step: every CTA forms, before the barrier,
-  // the reflector of its own best column (without writing it back); after the
-  // barrier all agree on the winner and copy the winner's reflector.  The
-  // proposal and reflector slots alternate between two buffers by step parity,
-  // so a CTA never overwrites a slot another CTA may still be reading.
-  const int vstride = (m_max + 3) & ~1;
-  __shared__ N cand_v2[2];
-  __shared__ double sp_beta[2];
-  __shared__ int cand_j2[2], sp_stop[2];
-  __shared__ T sp_tau[2], s_den;
-  __shared__ double red2[kWarps];
-  for (int i = 0; i < kmax; ++i) {
-    const int par = i & 1;
-    T* vb = vbuf + par * vstride;
-    // (1) the CTA's best column
-    if (lane == 0) {
-      red_v[warp] = wv;
-      red_i[warp] = wj;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      N v = red_v[0];
-      int j = red_i[0];
-      for (int w = 1; w < kWarps; ++w)
-        if (red_v[w] > v || (red_v[w] == v && red_i[w] < j)) {
-          v = red_v[w];
-          j = red_i[w];
-        }
-      cand_v2[par] = v;
-      cand_j2[par] = j;
-    }
-    __syncthreads();
-    const int jloc = cand_j2[par];
-    // (2) its reflector, rows i..m-1, into vb (the column itself is untouched)
-    if (jloc != INT_MAX) {
-      const T* col = X + (int64_t)(jloc - j0) * m;
-      double sq = 0.0;  // R_ii and the rank test in FP64 whatever the data precision
-      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) {
-        const double v = (double)col[r];
-        sq += v * v;
-      }
-      sq = warp_sum(sq);
-      if (lane == 0) red2[warp] = sq;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double sig = 0.0;
-        for (int w = 0; w < kWarps; ++w) sig += red2[w];
-        const double alpha = (double)col[i];
-        double beta, tau;
-        if (sig == 0.0) {
-          beta = alpha;
-          tau = 0.0;
-        } else {
-          const double nrm = sqrt(alpha * alpha + sig);
-          beta = alpha >= 0.0 ? -nrm : nrm;
-          tau = (beta - alpha) / beta;
-        }
-        const double ab = fabs(beta);
-        const double r11_here = (i == 0) ? ab : r11;
-        const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
-        sp_beta[par] = beta;
-        sp_tau[par] = (T)tau;
-        sp_stop[par] = stop;
-        s_den = (!stop && sig != 0.0) ? (T)(alpha - beta) : T(0);
-      }
-      __syncthreads();
-      const T den = s_den;
-      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) vb[r - i] = den != T(0) ? col[r] / den : T(0);
-      if (threadIdx.x == 0) vb[0] = T(1);
-    }
-    cl.sync();  // proposals and candidate reflectors visible cluster-wide
-    // (3) the winner: one lane per CTA of the cluster, then a warp reduction
-    if (threadIdx.x < 32) {
-      N v = N(-1);
-      int j = INT_MAX;
-      if (lane < CS) {
-        v = *cl.map_shared_rank(&cand_v2[par], lane);
-        j = *cl.map_shared_rank(&cand_j2[par], lane);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const N ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, j, o);
-        if (ov > v || (ov == v && oj < j)) {
-          v = ov;
-          j = oj;
-        }
-      }
-      if (lane == 0) s_piv = j;
-    }
-    __syncthreads();
-    const int p = s_piv;
-    if (p == INT_MAX) break;  // no proposal (non-finite norms): every CTA sees the same p
-    const int owner = p / nl;
-    if (rank != owner) {
-      for (int r = threadIdx.x; r < m - i; r += kThreads) vb[r] = *cl.map_shared_rank(vb + r, owner);
-      if (threadIdx.x == 0) {
-        s_tau = *cl.map_shared_rank(&sp_tau[par], owner);
-        s_beta = *cl.map_shared_rank(&sp_beta[par], owner);
-        s_stop = *cl.map_shared_rank(&sp_stop[par], owner);
-      }
-    } else if (threadIdx.x == 0) {
-      s_tau = sp_tau[par];
-      s_beta = sp_beta[par];
-      s_stop = sp_stop[par];
-    }
-    __syncthreads();
-    if (i == 0) r11 = fabs(s_beta);
-    if (s_stop) break;
-    const T tau = s_tau;
-    if (threadIdx.x == 0) taus[i] = copysign(tau, (T)s_beta);  // tau >= 0; the sign is that of R_ii
-    if (rank == owner) {
-      // the pivot column becomes beta at row i and the reflector below
-      const int pl = p - j0;
-      T* col = X + (int64_t)pl * m;
-      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) col[r] = vb[r - i];
-      if (threadIdx.x == 0) {
-        col[i] = (T)s_beta;
-        const int q = pos[pl], last = act[s_nact - 1];
-        step_of[pl] = i;
-        act[q] = last;
-        pos[last] = q;
-        s_nact = s_nact - 1;
-      }
-    }
-    __syncthreads();
-    // apply H_i to the CTA's unpivoted columns (the compact list act[0..nact)):
-    // every warp takes groups of KG columns, lanes over rows with KG independent
-    // accumulators; the KG dot products are reduced by one transposed butterfly
-    // (lane L(j) ends with column j's sum), w_j = tau (x_ij + v.x_j) is
-    // broadcast, the rows are updated, and lane L(j) downdates the FP64 squared
-    // norm of column j (recomputed warp-parallel when it lost too many digits)
-    // and keeps the warp's proposal for step i + 1.
-    wv = N(-1);
-    wj = INT_MAX;
-    const int nact = s_nact;
-    const int jl = butterfly_col<KG>(lane);  // the column whose sum this lane ends with
-    const bool lead = lane == butterfly_lane<KG>(jl);
-    for (int g0 = warp * KG; g0 < nact; g0 += kWarps * KG) {
-      const int ng = min(KG, nact - g0);
-      T* cols[KG];
-#pragma unroll
-      for (int j = 0; j < KG; ++j) cols[j] = X + (int64_t)act[g0 + (j < ng ? j : 0)] * m;
-      T acc[KG];
-#pragma unroll
-      for (int j = 0; j < KG; ++j) acc[j] = T(0);
-      if (tau != T(0)) {
-        for (int r = i + 1 + lane; r < m; r += 32) {
-          const T vr = vb[r - i];
-#pragma unroll
-          for (int j = 0; j < KG; ++j) acc[j] += vr * cols[j][r];
-        }
-      }
-      const T dsum = butterfly_reduce<KG>(acc, lane);
-      const int cme = jl < ng ? act[g0 + jl] : 0;
-      T* colme = X + (int64_t)cme * m;
-      T wmine = T(0);
-      N xnew = N(0);
-      if (jl < ng) {
-        const T xi = colme[i];
-        wmine = tau * (xi + dsum);
-        xnew = (N)(xi - wmine);
-      }
-      T wv8[KG];
-#pragma unroll
-      for (int j = 0; j < KG; ++j) wv8[j] = __shfl_sync(0xffffffffu, wmine, butterfly_lane<KG>(j));
-      __syncwarp();
-      if (lead && jl < ng) colme[i] = (T)xnew;
-      if (tau != T(0)) {
-        for (int r = i + 1 + lane; r < m; r += 32) {
-          const T vr = vb[r - i];
-#pragma unroll
-          for (int j = 0; j < KG; ++j)
-            if (j < ng) cols[j][r] -= wv8[j] * vr;
-        }
-      }
-      __syncwarp();
-      N v = N(-1);
-      bool redo = false;
-      if (lead && jl < ng) {
-        v = nu[cme] - xnew * xnew;
-        redo = v < recompute_frac<N>() * nuref[cme];
-      }
-      unsigned flagged = __ballot_sync(0xffffffffu, redo);
-      while (flagged) {
-        const int l = __ffs(flagged) - 1;
-        flagged &= flagged - 1;
-        const int cc = __shfl_sync(0xffffffffu, cme, l);
-        const T* col = X + (int64_t)cc * m;
-        N sq = N(0);
-        for (int r = i + 1 + lane; r < m; r += 32) {
-          const N y = (N)col[r];
-          sq += y * y;
-        }
-        sq = warp_sum(sq);
-        if (lane == l) {
-          v = sq;
-          nuref[cc] = sq;
-        }
-      }
-      if (lead && jl < ng) {
-        nu[cme] = v;
-        if (v > wv || (v == wv && j0 + cme < wj)) {
-          wv = v;
-          wj = j0 + cme;
-        }
-      }
-    }
-    // warp reduction of the proposals (lowest column index on ties)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const N ov = __shfl_xor_sync(0xffffffffu, wv, o);
-      const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
-      if (ov > wv || (ov == wv && oj < wj)) {
-        wv = ov;
-        wj = oj;
-      }
-    }
-    __syncthreads();  // every warp is done with act[] before the next pivot edits it
-    k = i + 1;
-  }
-  __syncthreads();
-  if (rank == 0 && threadIdx.x == 0) d.rank[0] = k;
-  if (d.V) {
-    for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
-      const int r = (int)(e % m), c = (int)(e / m);
-      const int t = step_of[c];
-      if (t < 0 || t >= k) continue;
-      d.V[r + (int64_t)t * m] = r < t ? T(0) : (r == t ? T(1) : X[r + (int64_t)c * m]);
-    }
-    if (rank == 0)
-      for (int t = threadIdx.x; t < k; t += kThreads) d.tau[t] = fabs(taus[t]);
-  }
-  // the first k rows of Q^T A in the original column order, only when k < m
-  if (d.out && (k < m || (d.flags & kQrcpAlwaysOut))) {
-    const bool fix = d.flags & kQrcpSignFix;
-    for (int64_t e = threadIdx.x; e < (int64_t)k * nloc; e += kThreads) {
-      const int r = (int)(e % k), c = (int)(e / k);
-      const int t = step_of[c];
-      const T x = (t >= 0 && r > t) ? T(0) : X[r + (int64_t)c * m];
-      d.out[r + (int64_t)(j0 + c) * d.ldo] = fix && signbit(taus[r]) ? -x : x;
-    }
-  }
-  cl.sync();  // no CTA leaves while another may still read its shared memory
-}
-
 // ------------------------------------------- QRCP over a group of CTAs
 // The same slab-in-shared-memory pivoted QR for matrices whose slabs need more
 // CTAs than one cluster holds: matrix f of a launch takes CTAs
@@ -1950,7 +1620,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
 
 // --------------------------------------------- QRCP with delayed updates
 // The global-work variant (slabs too large for shared memory): the pivots,
-// reflectors and rank rule of qrcp_cluster_kernel, but the reflectors of a
+// reflectors and rank rule of qrcp_slab_kernel, but the reflectors of a
 // panel of up to kQrcpNB steps reach the unpivoted columns only at the end of
 // the panel, as one rank-kQrcpNB update.  Within a panel each step reads every
 // unpivoted column once (v^T a) and keeps per column the coefficients f_t of
