@@ -253,6 +253,14 @@ template <typename T>
 class Factorizer {
  public:
   Factorizer(Handle& h, const Analysis& an) : h_(h), an_(an), st_(h.st) {}
+  ~Factorizer() {
+    for (auto& x : aux_)
+      if (x.st) {
+        cudaStreamDestroy(x.st);
+        cudaEventDestroy(x.done);
+      }
+    if (fork_) cudaEventDestroy(fork_);
+  }
   void run(const spaqr_csr& A);
 
  private:
@@ -272,6 +280,13 @@ class Factorizer {
   Handle& h_;
   const Analysis& an_;
   cudaStream_t st_;
+  // side streams for independent launches of one phase (forked from and joined back into st_)
+  struct Aux {
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+  Aux aux_[3];
+  cudaEvent_t fork_ = nullptr;
   DevicePool pool_;
   Uploader up_;
   EventTimer tm_;
@@ -611,12 +626,38 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
     dgd[t] = up_.put(gd);
   }
   tm_.begin(st_, 2);
+  // the shared-memory and warp groups are independent launches: they run side by side on st_ and
+  // the side streams (forked after the uploads above, joined before anything that follows); the
+  // cooperative CTA-group launches run alone on st_ afterwards
+  std::vector<size_t> plain;
+  for (size_t t = 0; t < groups.size(); ++t)
+    if (!groups[t].grid) plain.push_back(t);
+  const size_t nside = std::min<size_t>(plain.size() > 0 ? plain.size() - 1 : 0, 3);
+  if (nside) {
+    if (!fork_) SPAQR_CUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
+    SPAQR_CUDA(cudaEventRecord(fork_, st_));
+    for (size_t a = 0; a < nside; ++a) {
+      if (!aux_[a].st) {
+        SPAQR_CUDA(cudaStreamCreateWithFlags(&aux_[a].st, cudaStreamNonBlocking));
+        SPAQR_CUDA(cudaEventCreateWithFlags(&aux_[a].done, cudaEventDisableTiming));
+      }
+      SPAQR_CUDA(cudaStreamWaitEvent(aux_[a].st, fork_, 0));
+    }
+  }
+  for (size_t q = 0; q < plain.size(); ++q) {
+    const size_t t = plain[q];
+    const auto& g = groups[t];
+    cudaStream_t s = (q == 0 || nside == 0) ? st_ : aux_[(q - 1) % nside].st;
+    check(launch_qrcp<T>(dg[t], (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, s, g.nb), "qrcp");
+  }
+  for (size_t a = 0; a < nside; ++a) {
+    SPAQR_CUDA(cudaEventRecord(aux_[a].done, aux_[a].st));
+    SPAQR_CUDA(cudaStreamWaitEvent(st_, aux_[a].done, 0));
+  }
   for (size_t t = 0; t < groups.size(); ++t) {
     const auto& g = groups[t];
     if (g.grid)
       check(launch_qrcp_grid<T>(dg[t], dgd[t], (int)g.idx.size(), gtot[t], eps, g.nl_max, g.m_max, g.slab, st_), "qrcp grid");
-    else
-      check(launch_qrcp<T>(dg[t], (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, st_, g.nb), "qrcp");
   }
   tm_.end(st_);
 }
