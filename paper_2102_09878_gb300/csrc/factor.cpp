@@ -249,6 +249,23 @@ double now() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Group ids per cluster in CSR form (ascending ids per cluster): index_groups()
+// builds one for the groups each cluster owns and one for the groups of other
+// owners that touch it.
+struct IdRange {
+  const int* b;
+  const int* e;
+  const int* begin() const { return b; }
+  const int* end() const { return e; }
+  size_t size() const { return (size_t)(e - b); }
+  operator std::vector<int>() const { return std::vector<int>(b, e); }
+};
+struct GroupIndex {
+  std::vector<int64_t> ptr;
+  std::vector<int> ids;
+  IdRange operator[](size_t c) const { return IdRange{ids.data() + ptr[c], ids.data() + ptr[c + 1]}; }
+};
+
 template <typename T>
 class Factorizer {
  public:
@@ -526,7 +543,7 @@ class Factorizer {
   bool sparsify_here() const {
     return h_.opt.mode == SPAQR_MODE_SPAQR && k_ <= L_ - h_.opt.skip && k_ >= 2;
   }
-  void index_groups(std::vector<std::vector<int>>& own, std::vector<std::vector<int>>& touch);
+  void index_groups(GroupIndex& own, GroupIndex& touch);
 };
 
 template <typename T>
@@ -663,16 +680,30 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
 }
 
 template <typename T>
-void Factorizer<T>::index_groups(std::vector<std::vector<int>>& own, std::vector<std::vector<int>>& touch) {
+void Factorizer<T>::index_groups(GroupIndex& own, GroupIndex& touch) {
   HT ht(ht_[1]);
   const size_t nc = ccols_.size();
-  own.assign(nc, {});
-  touch.assign(nc, {});
-  for (int id : live()) {
+  const std::vector<int>& lv = live();  // ascending ids
+  own.ptr.assign(nc + 1, 0);
+  touch.ptr.assign(nc + 1, 0);
+  for (int id : lv) {
     const Group& g = G_[(size_t)id];
-    own[(size_t)g.owner].push_back(id);
+    own.ptr[(size_t)g.owner + 1]++;
     for (int c : g.sup)
-      if (c != g.owner) touch[(size_t)c].push_back(id);
+      if (c != g.owner) touch.ptr[(size_t)c + 1]++;
+  }
+  for (size_t c = 0; c < nc; ++c) {
+    own.ptr[c + 1] += own.ptr[c];
+    touch.ptr[c + 1] += touch.ptr[c];
+  }
+  own.ids.resize((size_t)own.ptr[nc]);
+  touch.ids.resize((size_t)touch.ptr[nc]);
+  std::vector<int64_t> po(own.ptr.begin(), own.ptr.end() - 1), pt(touch.ptr.begin(), touch.ptr.end() - 1);
+  for (int id : lv) {
+    const Group& g = G_[(size_t)id];
+    own.ids[(size_t)po[(size_t)g.owner]++] = id;
+    for (int c : g.sup)
+      if (c != g.owner) touch.ids[(size_t)pt[(size_t)c]++] = id;
   }
 }
 
@@ -874,7 +905,7 @@ void Factorizer<T>::eliminate() {
   std::vector<int> todo;
   for (size_t c = 0; c < ccols_.size(); ++c)
     if (calive_[c] && level((int)c) == k_) todo.push_back((int)c);
-  std::vector<std::vector<int>> own, touch;
+  GroupIndex own, touch;
   std::vector<int64_t> stamp(G_.size() + 1, -1);
   int round = 0;
   while (!todo.empty()) {
@@ -1160,7 +1191,7 @@ void Factorizer<T>::scale() {
   phase_ = "scale";
   HT ht(ht_[4]);
   Lap lap(this);
-  std::vector<std::vector<int>> own, touch;
+  GroupIndex own, touch;
   index_groups(own, touch);
   p1_of_.assign(ccols_.size(), -1);
   p2_of_.assign(ccols_.size(), -1);
@@ -1446,7 +1477,7 @@ void Factorizer<T>::step2() {
     ncol = std::max(ncol, c + 1);
   }
   lap("step2: colouring");
-  std::vector<std::vector<int>> own, touch;
+  GroupIndex own, touch;
   index_groups(own, touch);
   // one device rank slot per interface of this phase, read back with a single copy
   int* kdev_all = static_cast<int*>(h_.wpool.alloc(ps.size() * sizeof(int)));
