@@ -10,6 +10,7 @@
 
 #include "internal.h"
 #include "kernels.h"
+#include "parallel.h"
 
 struct spaqr_analysis {
   std::unique_ptr<spaqr::Analysis> an;
@@ -39,6 +40,55 @@ int need_device() {
 
 double secs_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// successive sections of handle construction, printed in verbose mode
+struct Tick {
+  bool on;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  explicit Tick(int verbose) : on(verbose != 0) {}
+  void operator()(const char* what) {
+    if (!on) return;
+    std::fprintf(stderr, "[spaqr] handle: %-28s %8.3f ms\n", what, 1e3 * secs_since(t));
+    t = std::chrono::steady_clock::now();
+  }
+};
+
+// The pattern of A^T in CSR form (column pointers, row indices) and, per
+// transposed entry, its position in A; the entries of a column keep the row
+// order.  Threads own disjoint column ranges and each scans all of A, so the
+// result does not depend on the thread count.
+void transpose_pattern(const spaqr_csr& A, std::vector<int64_t>& trp, std::vector<int32_t>& tci,
+                       std::vector<int64_t>& tperm) {
+  const int64_t n = A.n, m = A.m;
+  const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(spaqr::ThreadPool::get().workers(), n / 4096));
+  auto range = [&](int p) { return std::make_pair(n * p / parts, n * (p + 1) / parts); };
+  spaqr::parallel_for(parts, [&](int64_t b, int64_t e, int) {
+    for (int64_t p = b; p < e; ++p) {
+      const auto [c0, c1] = range((int)p);
+      const uint32_t w = (uint32_t)(c1 - c0);
+      for (int64_t q = 0; q < A.nnz; ++q) {
+        const uint32_t d = (uint32_t)(A.colidx[q] - c0);
+        if (d < w) trp[(size_t)A.colidx[q] + 1]++;
+      }
+    }
+  }, 1);
+  for (int64_t j = 0; j < n; ++j) trp[(size_t)j + 1] += trp[(size_t)j];
+  spaqr::parallel_for(parts, [&](int64_t b, int64_t e, int) {
+    for (int64_t p = b; p < e; ++p) {
+      const auto [c0, c1] = range((int)p);
+      const uint32_t w = (uint32_t)(c1 - c0);
+      std::vector<int64_t> pos(trp.begin() + c0, trp.begin() + c1);
+      for (int64_t r = 0; r < m; ++r)
+        for (int64_t q = A.rowptr[r]; q < A.rowptr[r + 1]; ++q) {
+          const uint32_t d = (uint32_t)(A.colidx[q] - c0);
+          if (d >= w) continue;
+          const int64_t t = pos[d]++;
+          tci[(size_t)t] = (int32_t)r;
+          tperm[(size_t)t] = q;
+        }
+    }
+  }, 1);
 }
 }  // namespace
 
@@ -144,25 +194,22 @@ std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Ana
   } else {
     spaqr::run_factor(h, *A, a);
   }
+  Tick tick(h.opt.verbose);
+  tick("factor");
   // scaled operator A~ = A D and its transpose on the device (FP64)
   std::vector<double> v((size_t)A->nnz);
-  for (int64_t e = 0; e < A->nnz; ++e) v[(size_t)e] = A->vals[e] * h.D[(size_t)A->colidx[e]];
+  spaqr::parallel_for(A->nnz, [&](int64_t b, int64_t e, int) {
+    for (int64_t q = b; q < e; ++q) v[(size_t)q] = A->vals[q] * h.D[(size_t)A->colidx[q]];
+  });
   std::vector<int64_t> trp((size_t)A->n + 1, 0);
-  for (int64_t e = 0; e < A->nnz; ++e) trp[(size_t)A->colidx[e] + 1]++;
-  for (int64_t j = 0; j < A->n; ++j) trp[(size_t)j + 1] += trp[(size_t)j];
   std::vector<int32_t> tci((size_t)A->nnz);
   std::vector<double> tv((size_t)A->nnz);
   std::vector<int64_t> tperm((size_t)A->nnz);
-  {
-    std::vector<int64_t> pos(trp.begin(), trp.end() - 1);
-    for (int64_t r = 0; r < A->m; ++r)
-      for (int64_t e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e) {
-        const int64_t q = pos[(size_t)A->colidx[e]]++;
-        tci[(size_t)q] = (int32_t)r;
-        tv[(size_t)q] = v[(size_t)e];
-        tperm[(size_t)q] = e;
-      }
-  }
+  transpose_pattern(*A, trp, tci, tperm);
+  spaqr::parallel_for(A->nnz, [&](int64_t b, int64_t e, int) {
+    for (int64_t q = b; q < e; ++q) tv[(size_t)q] = v[(size_t)tperm[(size_t)q]];
+  });
+  tick("scaled values + transpose");
   SPAQR_CUDA(cudaMalloc(&h.d_rowptr, (size_t)(A->m + 1) * sizeof(int64_t)));
   SPAQR_CUDA(cudaMalloc(&h.d_colidx, (size_t)A->nnz * sizeof(int32_t)));
   SPAQR_CUDA(cudaMalloc(&h.d_vals, (size_t)A->nnz * sizeof(double)));
@@ -183,8 +230,11 @@ std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Ana
   h.rowptr.assign(A->rowptr, A->rowptr + A->m + 1);
   h.colidx.assign(A->colidx, A->colidx + A->nnz);
   if (A->match) h.match.assign(A->match, A->match + A->n);
+  tick("operator upload");
   spaqr::build_apply_plan(h);
+  tick("apply plan");
   SPAQR_CUDA(cudaStreamSynchronize(h.st));
+  tick("final wait");
   int64_t nnzW = 0;
   for (auto& op : h.ops) {
     const int64_t c = op.c;

@@ -955,60 +955,83 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   std::vector<CopyDesc<T>> gat;
   double plan_t0 = HT::now_s();
   Lap lap(this);
-  for (size_t b = 0; b < batch.size(); ++b) {
-    const int s = batch[b].first;
-    const auto& fg = batch[b].second;
-    FrontInfo& f = fi[b];
-    f.s = s;
-    f.c = ccols_[(size_t)s];
-    f.rs = 0;
-    f.m = 0;
+  // fronts are independent: their column lists and sizes in parallel, then the
+  // workspace and destination offsets in front order
+  std::vector<size_t> gfirst(batch.size() + 1, 0);
+  parallel_for((int64_t)batch.size(), [&](int64_t b0, int64_t b1, int) {
     std::vector<int> u;
-    for (int g : fg) {
-      const Group& gg = G_[(size_t)g];
-      if (gg.owner == s) f.rs += gg.rows;
-      f.m += gg.rows;
-      u.insert(u.end(), gg.sup.begin(), gg.sup.end());
+    for (int64_t bb = b0; bb < b1; ++bb) {
+      const size_t b = (size_t)bb;
+      const int s = batch[b].first;
+      const auto& fg = batch[b].second;
+      FrontInfo& f = fi[b];
+      f.s = s;
+      f.c = ccols_[(size_t)s];
+      f.rs = 0;
+      f.m = 0;
+      u.clear();
+      size_t ng = 0;
+      for (int g : fg) {
+        const Group& gg = G_[(size_t)g];
+        if (gg.owner == s) f.rs += gg.rows;
+        f.m += gg.rows;
+        u.insert(u.end(), gg.sup.begin(), gg.sup.end());
+        if (gg.rows)
+          for (int c : gg.sup) ng += ccols_[(size_t)c] ? 1 : 0;
+      }
+      std::sort(u.begin(), u.end());
+      u.erase(std::unique(u.begin(), u.end()), u.end());
+      f.cols.clear();
+      f.cols.push_back(s);
+      for (int c : u)
+        if (c != s) f.cols.push_back(c);
+      f.coff.assign(f.cols.size() + 1, 0);
+      for (size_t t = 0; t < f.cols.size(); ++t) f.coff[t + 1] = f.coff[t] + ccols_[(size_t)f.cols[t]];
+      f.n = f.coff.back();
+      f.nextra = (f.cols.size() > 1 && f.rs > f.c) ? f.rs - f.c : 0;
+      gfirst[b + 1] = ng;
     }
-    std::sort(u.begin(), u.end());
-    u.erase(std::unique(u.begin(), u.end()), u.end());
-    f.cols.push_back(s);
-    for (int c : u)
-      if (c != s) f.cols.push_back(c);
-    f.coff.assign(f.cols.size() + 1, 0);
-    for (size_t t = 0; t < f.cols.size(); ++t) f.coff[t + 1] = f.coff[t] + ccols_[(size_t)f.cols[t]];
-    f.n = f.coff.back();
+  }, 64);
+  for (size_t b = 0; b < batch.size(); ++b) {
+    FrontInfo& f = fi[b];
     if (f.rs < f.c)
       throw Error(SPAQR_ERR_RANK_DEFICIENT,
-                  "cluster " + std::to_string(s) + " at stage " + std::to_string(k_) + ": " + std::to_string(f.rs) +
+                  "cluster " + std::to_string(f.s) + " at stage " + std::to_string(k_) + ": " + std::to_string(f.rs) +
                       " rows < " + std::to_string(f.c) + " columns");
     f.foff = ws;
     ws += (size_t)f.m * f.n;
-    f.nextra = (f.cols.size() > 1 && f.rs > f.c) ? f.rs - f.c : 0;
     f.dest_off = ndest;
     ndest += (size_t)f.nextra;
+    gfirst[b + 1] += gfirst[b];
   }
   T* W = static_cast<T*>(pool_.alloc(std::max<size_t>(ws, 1) * sizeof(T)));
   SPAQR_CUDA(cudaMemsetAsync(W, 0, std::max<size_t>(ws, 1) * sizeof(T), st_));
   lap("elim: front info");
-  std::vector<FrontDesc<T>> fr;
-  for (size_t b = 0; b < batch.size(); ++b) {
-    FrontInfo& f = fi[b];
-    T* F = W + f.foff;
-    int row = 0;
-    for (int g : batch[b].second) {
-      const Group& gg = G_[(size_t)g];
-      for (size_t t = 0; t < gg.sup.size(); ++t) {
-        const int c = gg.sup[t];
-        const size_t ci = (size_t)(std::find(f.cols.begin(), f.cols.end(), c) - f.cols.begin());
-        if (gg.rows == 0 || ccols_[(size_t)c] == 0) continue;
-        gat.push_back(CopyDesc<T>{gg.ptr + (size_t)gg.off[t] * gg.ld, F + row + (size_t)f.coff[ci] * f.m, nullptr,
-                                  gg.ld, f.m, gg.rows, ccols_[(size_t)c], 0, 0});
+  std::vector<FrontDesc<T>> fr(batch.size());
+  gat.resize(gfirst.back());
+  parallel_for((int64_t)batch.size(), [&](int64_t b0, int64_t b1, int) {
+    for (int64_t bb = b0; bb < b1; ++bb) {
+      const size_t b = (size_t)bb;
+      const FrontInfo& f = fi[b];
+      T* F = W + f.foff;
+      int row = 0;
+      size_t q = gfirst[b];
+      for (int g : batch[b].second) {
+        const Group& gg = G_[(size_t)g];
+        for (size_t t = 0; t < gg.sup.size(); ++t) {
+          const int c = gg.sup[t];
+          if (gg.rows == 0 || ccols_[(size_t)c] == 0) continue;
+          // f.cols = s, then the other clusters ascending
+          const size_t ci = c == f.s ? 0
+                                     : (size_t)(std::lower_bound(f.cols.begin() + 1, f.cols.end(), c) - f.cols.begin());
+          gat[q++] = CopyDesc<T>{gg.ptr + (size_t)gg.off[t] * gg.ld, F + row + (size_t)f.coff[ci] * f.m, nullptr,
+                                 gg.ld, f.m, gg.rows, ccols_[(size_t)c], 0, 0};
+        }
+        row += gg.rows;
       }
-      row += gg.rows;
+      fr[b] = FrontDesc<T>{F, f.m, f.n, f.c, f.m};
     }
-    fr.push_back(FrontDesc<T>{F, f.m, f.n, f.c, f.m});
-  }
+  }, 64);
   ht_[2] += HT::now_s() - plan_t0;
   lap("elim: gather plan");
   copies(gat);
@@ -1058,16 +1081,29 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   // R_s = [R_ss R_sn] into the W store
   lap("elim: argmax plan+launch");
   std::vector<CopyDesc<T>> rc;
-  for (auto& f : fi) {
-    WOp op;
-    op.kind = 0;
-    op.stage = k_;
-    op.round = round;
-    op.c = f.c;
-    op.w = f.n - f.c;
-    op.slots = slots_[(size_t)f.s];
-    for (size_t t = 1; t < f.cols.size(); ++t)
-      op.nslots.insert(op.nslots.end(), slots_[(size_t)f.cols[t]].begin(), slots_[(size_t)f.cols[t]].end());
+  std::vector<WOp> nops(fi.size());
+  parallel_for((int64_t)fi.size(), [&](int64_t b0, int64_t b1, int) {
+    for (int64_t bb = b0; bb < b1; ++bb) {
+      const FrontInfo& f = fi[(size_t)bb];
+      WOp& op = nops[(size_t)bb];
+      op.kind = 0;
+      op.stage = k_;
+      op.round = round;
+      op.c = f.c;
+      op.w = f.n - f.c;
+      if (f.c <= 0) continue;
+      op.slots = slots_[(size_t)f.s];
+      size_t nsl = 0;
+      for (size_t t = 1; t < f.cols.size(); ++t) nsl += slots_[(size_t)f.cols[t]].size();
+      op.nslots.reserve(nsl);
+      for (size_t t = 1; t < f.cols.size(); ++t)
+        op.nslots.insert(op.nslots.end(), slots_[(size_t)f.cols[t]].begin(), slots_[(size_t)f.cols[t]].end());
+    }
+  }, 256);
+  h_.ops.reserve(h_.ops.size() + fi.size());
+  for (size_t b = 0; b < fi.size(); ++b) {
+    const FrontInfo& f = fi[b];
+    WOp& op = nops[b];
     if (f.c > 0) {
       T* R = wstore((size_t)f.c * f.n);
       op.R = R;
@@ -1095,61 +1131,106 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
   // new groups: returned rows per owner, then extra rows per destination
   HT ht_new(ht_[3]);
   lap("elim: readback");
-  std::vector<int> ids;
+  // the new groups of every front in front order (ids assigned in that order):
+  // first the returned rows, one group per other owner (contiguous rows from
+  // position r_s on), then the extra rows c_s..r_s-1, one group per destination
+  // cluster (rows listed in rowlist, by destination, ascending); every new
+  // group of a front spans the front's remaining clusters
   struct Pending {
     int id;
-    size_t front;
-    int r0, cnt;            // contiguous rows (returned)
-    std::vector<int> rows;  // explicit rows (extra)
+    int front;
+    int r0, cnt;  // contiguous rows (returned)
+    int64_t roff; // first entry in rowlist (extra rows), -1 for returned rows
     int owner;
   };
-  // the new groups of every front in front order (ids assigned in that order),
-  // then their layouts in parallel: every new group of a front spans the
-  // front's remaining clusters
-  std::vector<Pending> pend;
-  for (size_t b = 0; b < batch.size(); ++b) {
-    FrontInfo& f = fi[b];
-    const size_t nrest = f.cols.size() - 1;
-    int pos = f.rs;
-    const auto& fg = batch[b].second;
-    size_t q = 0;
-    while (q < fg.size() && G_[(size_t)fg[q]].owner == f.s) ++q;
-    while (q < fg.size()) {
-      const int o = G_[(size_t)fg[q]].owner;
-      int cnt = 0;
-      while (q < fg.size() && G_[(size_t)fg[q]].owner == o) cnt += G_[(size_t)fg[q++]].rows;
-      if (nrest) pend.push_back(Pending{-1, b, pos, cnt, {}, o});
-      pos += cnt;
-    }
-    if (f.nextra) {
-      std::vector<std::vector<int>> by(nrest);
-      for (int i = 0; i < f.nextra; ++i) {
-        const int t = dest[f.dest_off + (size_t)i];
-        if (t < 0 || t >= (int)nrest)
-          throw Error(SPAQR_ERR_RANK_DEFICIENT, "non-finite values in a front at stage " + std::to_string(k_));
-        by[(size_t)t].push_back(f.c + i);
+  std::vector<size_t> pfirst(batch.size() + 1, 0);
+  std::vector<int32_t> rowlist(ndest);
+  std::atomic<int> bad_dest{0};
+  parallel_for((int64_t)batch.size(), [&](int64_t b0, int64_t b1, int) {
+    std::vector<int> cnt;
+    for (int64_t bb = b0; bb < b1; ++bb) {
+      const size_t b = (size_t)bb;
+      const FrontInfo& f = fi[b];
+      const size_t nrest = f.cols.size() - 1;
+      const auto& fg = batch[b].second;
+      size_t np = 0;
+      if (nrest) {
+        size_t q = 0;
+        while (q < fg.size() && G_[(size_t)fg[q]].owner == f.s) ++q;
+        while (q < fg.size()) {
+          const int o = G_[(size_t)fg[q]].owner;
+          while (q < fg.size() && G_[(size_t)fg[q]].owner == o) ++q;
+          ++np;
+        }
       }
-      for (size_t t = 0; t < nrest; ++t) {
-        if (by[t].empty()) continue;
-        const int cnt = (int)by[t].size();
-        pend.push_back(Pending{-1, b, 0, cnt, std::move(by[t]), f.cols[t + 1]});
+      if (f.nextra) {
+        cnt.assign(nrest + 1, 0);
+        bool ok = true;
+        for (int i = 0; i < f.nextra; ++i) {
+          const int t = dest[f.dest_off + (size_t)i];
+          if (t < 0 || t >= (int)nrest) {
+            ok = false;
+            break;
+          }
+          cnt[(size_t)t + 1]++;
+        }
+        if (!ok) {
+          bad_dest.store(1);
+          continue;
+        }
+        for (size_t t = 0; t < nrest; ++t) {
+          np += cnt[t + 1] ? 1 : 0;
+          cnt[t + 1] += cnt[t];
+        }
+        for (int i = 0; i < f.nextra; ++i) {
+          const int t = dest[f.dest_off + (size_t)i];
+          rowlist[f.dest_off + (size_t)cnt[(size_t)t]++] = f.c + i;
+        }
       }
+      pfirst[b + 1] = np;
     }
-  }
-  {
-    const int base = add_groups(pend.size());
-    for (size_t i = 0; i < pend.size(); ++i) {
-      pend[i].id = base + (int)i;
-      ids.push_back(pend[i].id);
-    }
-    parallel_for((int64_t)pend.size(), [&](int64_t b, int64_t e, int) {
-      for (int64_t i = b; i < e; ++i) {
-        const Pending& pd = pend[(size_t)i];
-        const FrontInfo& f = fi[pd.front];
-        make_group(G_[(size_t)pd.id], pd.owner, pd.cnt, std::vector<int>(f.cols.begin() + 1, f.cols.end()));
+  }, 64);
+  if (bad_dest.load()) throw Error(SPAQR_ERR_RANK_DEFICIENT, "non-finite values in a front at stage " + std::to_string(k_));
+  for (size_t b = 0; b < batch.size(); ++b) pfirst[b + 1] += pfirst[b];
+  std::vector<Pending> pend(pfirst.back());
+  const int base = add_groups(pend.size());
+  parallel_for((int64_t)batch.size(), [&](int64_t b0, int64_t b1, int) {
+    for (int64_t bb = b0; bb < b1; ++bb) {
+      const size_t b = (size_t)bb;
+      const FrontInfo& f = fi[b];
+      const size_t nrest = f.cols.size() - 1;
+      const auto& fg = batch[b].second;
+      size_t p = pfirst[b];
+      if (nrest) {
+        int pos = f.rs;
+        size_t q = 0;
+        while (q < fg.size() && G_[(size_t)fg[q]].owner == f.s) ++q;
+        while (q < fg.size()) {
+          const int o = G_[(size_t)fg[q]].owner;
+          int c = 0;
+          while (q < fg.size() && G_[(size_t)fg[q]].owner == o) c += G_[(size_t)fg[q++]].rows;
+          pend[p] = Pending{base + (int)p, (int)b, pos, c, -1, o};
+          ++p;
+          pos += c;
+        }
       }
-    }, 1024);
-  }
+      // extra rows: runs of equal destination in rowlist (destinations ascending)
+      int64_t i = 0;
+      while (i < f.nextra) {
+        const int t = dest[f.dest_off + (size_t)(rowlist[f.dest_off + (size_t)i] - f.c)];
+        int64_t j = i + 1;
+        while (j < f.nextra && dest[f.dest_off + (size_t)(rowlist[f.dest_off + (size_t)j] - f.c)] == t) ++j;
+        pend[p] = Pending{base + (int)p, (int)b, 0, (int)(j - i), (int64_t)f.dest_off + i, f.cols[(size_t)t + 1]};
+        ++p;
+        i = j;
+      }
+      for (size_t q = pfirst[b]; q < p; ++q)
+        make_group(G_[(size_t)pend[q].id], pend[q].owner, pend[q].cnt, std::vector<int>(f.cols.begin() + 1, f.cols.end()));
+    }
+  }, 64);
+  lap("elim: pending groups");
+  std::vector<int> ids(pend.size());
+  std::iota(ids.begin(), ids.end(), base);
   {
     std::vector<int> dead;
     for (size_t b = 0; b < batch.size(); ++b) {
@@ -1158,26 +1239,21 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
     }
     kill_many(dead);
   }
+  lap("elim: kill");
   assign_buffer(ids, false);
   std::vector<CopyDesc<T>> sc;
   lap("elim: new groups");
-  std::vector<int32_t> rowlist;
-  std::vector<size_t> row_off(pend.size(), 0);
-  for (size_t i = 0; i < pend.size(); ++i) {
-    row_off[i] = rowlist.size();
-    rowlist.insert(rowlist.end(), pend[i].rows.begin(), pend[i].rows.end());
-  }
   int32_t* d_rows = rowlist.empty() ? nullptr : up_.put(rowlist);
   for (size_t i = 0; i < pend.size(); ++i) {
     const Pending& p = pend[i];
     const Group& g = G_[(size_t)p.id];
-    const FrontInfo& f = fi[p.front];
+    const FrontInfo& f = fi[(size_t)p.front];
     if (g.rows == 0 || g.width == 0) continue;
     const T* src = W + f.foff + (size_t)f.c * f.m;
-    if (p.rows.empty())
+    if (p.roff < 0)
       sc.push_back(CopyDesc<T>{src + p.r0, g.ptr, nullptr, f.m, g.ld, g.rows, g.width, 0, 0});
     else
-      sc.push_back(CopyDesc<T>{src, g.ptr, d_rows + row_off[i], f.m, g.ld, g.rows, g.width, 0, 0});
+      sc.push_back(CopyDesc<T>{src, g.ptr, d_rows + p.roff, f.m, g.ld, g.rows, g.width, 0, 0});
   }
   copies(sc);
   pool_.release(W);
@@ -1208,49 +1284,75 @@ void Factorizer<T>::scale() {
     SInfo s;
     s.p = (int)p;
     s.c = ccols_[p];
-    s.rp = 0;
+    si.push_back(std::move(s));
+  }
+  // interfaces are independent: rows, column lists and gather counts in parallel
+  std::vector<size_t> gfirst(si.size() + 1, 0);
+  parallel_for((int64_t)si.size(), [&](int64_t q0, int64_t q1, int) {
     std::vector<int> u;
-    for (int g : own[p]) {
-      s.rp += G_[(size_t)g].rows;
-      u.insert(u.end(), G_[(size_t)g].sup.begin(), G_[(size_t)g].sup.end());
+    for (int64_t qq = q0; qq < q1; ++qq) {
+      SInfo& s = si[(size_t)qq];
+      const size_t p = (size_t)s.p;
+      s.rp = 0;
+      u.clear();
+      size_t ng = 0;
+      for (int g : own[p]) {
+        const Group& gg = G_[(size_t)g];
+        s.rp += gg.rows;
+        u.insert(u.end(), gg.sup.begin(), gg.sup.end());
+        if (gg.rows)
+          for (int c : gg.sup) ng += ccols_[(size_t)c] ? 1 : 0;
+      }
+      std::sort(u.begin(), u.end());
+      u.erase(std::unique(u.begin(), u.end()), u.end());
+      s.cols.push_back((int)p);
+      for (int c : u)
+        if (c != (int)p) s.cols.push_back(c);
+      s.coff.assign(s.cols.size() + 1, 0);
+      for (size_t t = 0; t < s.cols.size(); ++t) s.coff[t + 1] = s.coff[t] + ccols_[(size_t)s.cols[t]];
+      s.n = s.coff.back();
+      gfirst[(size_t)qq + 1] = ng;
     }
+  }, 64);
+  for (size_t q = 0; q < si.size(); ++q) {
+    SInfo& s = si[q];
     if (s.rp < s.c)
-      throw Error(SPAQR_ERR_RANK_DEFICIENT, "interface " + std::to_string(p) + " at stage " + std::to_string(k_) +
+      throw Error(SPAQR_ERR_RANK_DEFICIENT, "interface " + std::to_string(s.p) + " at stage " + std::to_string(k_) +
                                                 ": " + std::to_string(s.rp) + " rows < " + std::to_string(s.c) +
                                                 " columns");
-    std::sort(u.begin(), u.end());
-    u.erase(std::unique(u.begin(), u.end()), u.end());
-    s.cols.push_back((int)p);
-    for (int c : u)
-      if (c != (int)p) s.cols.push_back(c);
-    s.coff.assign(s.cols.size() + 1, 0);
-    for (size_t t = 0; t < s.cols.size(); ++t) s.coff[t + 1] = s.coff[t] + ccols_[(size_t)s.cols[t]];
-    s.n = s.coff.back();
     s.foff = ws;
     ws += (size_t)s.rp * s.n;
-    si.push_back(std::move(s));
+    gfirst[q + 1] += gfirst[q];
   }
   lap("scale: info");
   if (si.empty()) return;
   T* W = static_cast<T*>(pool_.alloc(std::max<size_t>(ws, 1) * sizeof(T)));
   SPAQR_CUDA(cudaMemsetAsync(W, 0, std::max<size_t>(ws, 1) * sizeof(T), st_));
-  std::vector<CopyDesc<T>> gat;
-  std::vector<FrontDesc<T>> fr;
-  for (auto& s : si) {
-    T* F = W + s.foff;
-    int row = 0;
-    for (int g : own[(size_t)s.p]) {
-      const Group& gg = G_[(size_t)g];
-      for (size_t t = 0; t < gg.sup.size(); ++t) {
-        const int c = gg.sup[t];
-        const size_t ci = (size_t)(std::find(s.cols.begin(), s.cols.end(), c) - s.cols.begin());
-        if (gg.rows == 0 || ccols_[(size_t)c] == 0) continue;
-        gat.push_back(CopyDesc<T>{gg.ptr + (size_t)gg.off[t] * gg.ld, F + row + (size_t)s.coff[ci] * s.rp, nullptr,
-                                  gg.ld, s.rp, gg.rows, ccols_[(size_t)c], 0, 0});
+  std::vector<CopyDesc<T>> gat(gfirst.back());
+  std::vector<FrontDesc<T>> fr(si.size());
+  parallel_for((int64_t)si.size(), [&](int64_t q0, int64_t q1, int) {
+    for (int64_t qq = q0; qq < q1; ++qq) {
+      const SInfo& s = si[(size_t)qq];
+      T* F = W + s.foff;
+      int row = 0;
+      size_t q = gfirst[(size_t)qq];
+      for (int g : own[(size_t)s.p]) {
+        const Group& gg = G_[(size_t)g];
+        for (size_t t = 0; t < gg.sup.size(); ++t) {
+          const int c = gg.sup[t];
+          if (gg.rows == 0 || ccols_[(size_t)c] == 0) continue;
+          // s.cols = p, then the other clusters ascending
+          const size_t ci = c == s.p ? 0
+                                     : (size_t)(std::lower_bound(s.cols.begin() + 1, s.cols.end(), c) - s.cols.begin());
+          gat[q++] = CopyDesc<T>{gg.ptr + (size_t)gg.off[t] * gg.ld, F + row + (size_t)s.coff[ci] * s.rp, nullptr,
+                                 gg.ld, s.rp, gg.rows, ccols_[(size_t)c], 0, 0};
+        }
+        row += gg.rows;
       }
-      row += gg.rows;
+      fr[(size_t)qq] = FrontDesc<T>{F, s.rp, s.n, s.c, s.rp};
     }
-    fr.push_back(FrontDesc<T>{F, s.rp, s.n, s.c, s.rp});
+  }, 64);
+  for (auto& s : si) {
     slog_.scaled++;
     slog_.max_rp = std::max(slog_.max_rp, s.rp);
     const double m = s.rp, c = s.c, t = s.n - s.c;
@@ -1271,16 +1373,20 @@ void Factorizer<T>::scale() {
     int next = base;
     std::vector<int> dead;
     h_.ops.reserve(h_.ops.size() + si.size());
+    const size_t op0 = h_.ops.size();
+    h_.ops.resize(op0 + si.size());
+    parallel_for((int64_t)si.size(), [&](int64_t q0, int64_t q1, int) {
+      for (int64_t q = q0; q < q1; ++q) h_.ops[op0 + (size_t)q].slots = slots_[(size_t)si[(size_t)q].p];
+    }, 256);
+    size_t opi = op0;
     for (auto& s : si) {
-      WOp op;
+      WOp& op = h_.ops[opi++];
       op.kind = 1;
       op.stage = k_;
       op.c = s.c;
-      op.slots = slots_[(size_t)s.p];
       s.R = wstore((size_t)s.c * s.c);
       op.R = s.R;
       rc.push_back(CopyDesc<T>{W + s.foff, s.R, nullptr, s.rp, s.c, s.c, s.c, 0, 0});
-      h_.ops.push_back(std::move(op));
       dead.insert(dead.end(), own[(size_t)s.p].begin(), own[(size_t)s.p].end());
       p1_of_[(size_t)s.p] = next;
       ids.push_back(next++);
@@ -1489,90 +1595,113 @@ void Factorizer<T>::step2() {
   };
   std::vector<P2> recs;
   std::vector<T*> work_all;
+  std::vector<std::vector<int>> members((size_t)ncol);
+  for (int p : ps) members[(size_t)colour[(size_t)p]].push_back(p);
   for (int col = 0; col < ncol; ++col) {
-    std::vector<CopyDesc<T>> cps;
-    std::vector<QrcpDesc<T>> qs;
-    std::vector<ReflDesc<T>> rf;
-    std::vector<size_t> opidx;
-    size_t ws = 0;
     struct MInfo {
       int p, cp, rn, cn;
       std::vector<int> nb, ncols;
-      size_t moff;
+      size_t moff, cfirst, rfirst;
     };
-    std::vector<MInfo> mi;
-    for (int p : ps) {
-      if (colour[(size_t)p] != col) continue;
-      MInfo x;
-      x.p = p;
-      x.cp = ccols_[(size_t)p];
-      x.nb = touch[(size_t)p];
-      x.nb.erase(std::remove_if(x.nb.begin(), x.nb.end(), [&](int g) { return !G_[(size_t)g].alive; }), x.nb.end());
-      std::sort(x.nb.begin(), x.nb.end(), [&](int a, int b) {
-        const int oa = G_[(size_t)a].owner, ob = G_[(size_t)b].owner;
-        return oa != ob ? oa < ob : a < b;
-      });
-      x.rn = 0;
-      for (int g : x.nb) x.rn += G_[(size_t)g].rows;
-      const Group& g1 = G_[(size_t)p1_of_[(size_t)p]];
-      x.cn = 0;
-      for (int c : g1.sup)
-        if (c != p) {
-          x.ncols.push_back(c);
-          x.cn += ccols_[(size_t)c];
+    const auto& mem = members[(size_t)col];
+    std::vector<MInfo> mi(mem.size());
+    // members of a colour are independent: M_p's blocks and descriptor counts in parallel
+    parallel_for((int64_t)mem.size(), [&](int64_t q0, int64_t q1, int) {
+      for (int64_t qq = q0; qq < q1; ++qq) {
+        MInfo& x = mi[(size_t)qq];
+        const int p = mem[(size_t)qq];
+        x.p = p;
+        x.cp = ccols_[(size_t)p];
+        for (int g : touch[(size_t)p])
+          if (G_[(size_t)g].alive) x.nb.push_back(g);
+        std::sort(x.nb.begin(), x.nb.end(), [&](int a, int b) {
+          const int oa = G_[(size_t)a].owner, ob = G_[(size_t)b].owner;
+          return oa != ob ? oa < ob : a < b;
+        });
+        x.rn = 0;
+        size_t nc = 0;
+        for (int g : x.nb) {
+          x.rn += G_[(size_t)g].rows;
+          nc += G_[(size_t)g].rows ? 1 : 0;
         }
+        const Group& g1 = G_[(size_t)p1_of_[(size_t)p]];
+        x.cn = 0;
+        for (int c : g1.sup)
+          if (c != p) {
+            x.ncols.push_back(c);
+            x.cn += ccols_[(size_t)c];
+            nc += ccols_[(size_t)c] ? 1 : 0;
+          }
+        x.cfirst = nc;  // a count here, offsets below
+      }
+    }, 16);
+    size_t ws = 0, ncps = 0;
+    for (auto& x : mi) {
       x.moff = ws;
       ws += (size_t)x.cp * (x.rn + x.cn);
-      mi.push_back(std::move(x));
+      const size_t n = x.cfirst;
+      x.cfirst = ncps;
+      x.rfirst = ncps;  // one reflector descriptor per copied block
+      ncps += n;
     }
     T* M = static_cast<T*>(pool_.alloc(std::max<size_t>(ws, 1) * sizeof(T)));
-    for (auto& x : mi) {
-      T* Mp = M + x.moff;
-      int colm = 0;
-      for (int g : x.nb) {
-        const Group& gg = G_[(size_t)g];
-        if (gg.rows)
-          cps.push_back(CopyDesc<T>{gg.ptr + (size_t)col_off(gg, x.p) * gg.ld, Mp + (size_t)colm * x.cp, nullptr,
-                                    gg.ld, x.cp, gg.rows, x.cp, 1, 0});
-        colm += gg.rows;
-      }
-      const Group& g1 = G_[(size_t)p1_of_[(size_t)x.p]];
-      for (int c : x.ncols) {
-        if (ccols_[(size_t)c])
-          cps.push_back(CopyDesc<T>{g1.ptr + (size_t)col_off(g1, c) * g1.ld, Mp + (size_t)colm * x.cp, nullptr, g1.ld,
-                                    x.cp, x.cp, ccols_[(size_t)c], 0, 0});
-        colm += ccols_[(size_t)c];
-      }
+    std::vector<CopyDesc<T>> cps(ncps);
+    std::vector<ReflDesc<T>> rf(ncps);
+    std::vector<QrcpDesc<T>> qs(mi.size());
+    const size_t op0 = h_.ops.size();
+    h_.ops.resize(op0 + mi.size());
+    for (size_t q = 0; q < mi.size(); ++q) {
+      const MInfo& x = mi[q];
       const int ncm = x.rn + x.cn;
       const int kmax = std::min(x.cp, ncm);
       slog_.s2++;
       slog_.s2_max_c = std::max(slog_.s2_max_c, x.cp);
       slog_.s2_max_w = std::max(slog_.s2_max_w, ncm);
-      WOp op;
+      WOp& op = h_.ops[op0 + q];
       op.kind = 2;
       op.stage = k_;
       op.round = col;
       op.c = x.cp;
       op.w = kmax;
-      op.slots = slots_[(size_t)x.p];
-      T* V = wstore((size_t)x.cp * std::max(kmax, 1));
-      T* tau = wstore((size_t)std::max(kmax, 1));
-      op.V = V;
-      op.tau = tau;
+      op.V = wstore((size_t)x.cp * std::max(kmax, 1));
+      op.tau = wstore((size_t)std::max(kmax, 1));
       op.kdev = kdev_all + kdev_next++;
-      qs.push_back(QrcpDesc<T>{Mp, nullptr, nullptr, V, tau, op.kdev, x.cp, ncm, x.cp, x.cp});
-      for (int g : x.nb) {
-        const Group& gg = G_[(size_t)g];
-        if (gg.rows)
-          rf.push_back(ReflDesc<T>{gg.ptr + (size_t)col_off(gg, x.p) * gg.ld, V, tau, op.kdev, gg.ld, x.cp, gg.rows, 0});
-      }
-      for (int c : x.ncols)
-        if (ccols_[(size_t)c])
-          rf.push_back(ReflDesc<T>{g1.ptr + (size_t)col_off(g1, c) * g1.ld, V, tau, op.kdev, g1.ld, x.cp,
-                                   ccols_[(size_t)c], 1});
-      recs.push_back(P2{x.p, h_.ops.size(), ncm});
-      h_.ops.push_back(std::move(op));
+      qs[q] = QrcpDesc<T>{M + x.moff, nullptr, nullptr, static_cast<T*>(op.V), static_cast<T*>(op.tau), op.kdev,
+                          x.cp, ncm, x.cp, x.cp};
+      recs.push_back(P2{x.p, op0 + q, ncm});
     }
+    parallel_for((int64_t)mi.size(), [&](int64_t q0, int64_t q1, int) {
+      for (int64_t qq = q0; qq < q1; ++qq) {
+        const MInfo& x = mi[(size_t)qq];
+        const WOp& op = h_.ops[op0 + (size_t)qq];
+        h_.ops[op0 + (size_t)qq].slots = slots_[(size_t)x.p];
+        T* Mp = M + x.moff;
+        T* V = static_cast<T*>(op.V);
+        T* tau = static_cast<T*>(op.tau);
+        size_t ci = x.cfirst;
+        int colm = 0;
+        for (int g : x.nb) {
+          const Group& gg = G_[(size_t)g];
+          if (gg.rows) {
+            T* blk = gg.ptr + (size_t)col_off(gg, x.p) * gg.ld;
+            cps[ci] = CopyDesc<T>{blk, Mp + (size_t)colm * x.cp, nullptr, gg.ld, x.cp, gg.rows, x.cp, 1, 0};
+            rf[ci] = ReflDesc<T>{blk, V, tau, op.kdev, gg.ld, x.cp, gg.rows, 0};
+            ++ci;
+          }
+          colm += gg.rows;
+        }
+        const Group& g1 = G_[(size_t)p1_of_[(size_t)x.p]];
+        for (int c : x.ncols) {
+          if (ccols_[(size_t)c]) {
+            T* blk = g1.ptr + (size_t)col_off(g1, c) * g1.ld;
+            cps[ci] = CopyDesc<T>{blk, Mp + (size_t)colm * x.cp, nullptr, g1.ld, x.cp, x.cp, ccols_[(size_t)c], 0, 0};
+            rf[ci] = ReflDesc<T>{blk, V, tau, op.kdev, g1.ld, x.cp, ccols_[(size_t)c], 1};
+            ++ci;
+          }
+          colm += ccols_[(size_t)c];
+        }
+      }
+    }, 16);
     copies(cps);
     qrcp(qs, work_all);
     if (checking_)
@@ -1813,8 +1942,9 @@ void Factorizer<T>::run(const spaqr_csr& A) {
     const char* e = std::getenv("SPAQR_CHECK");
     checking_ = e && e[0] == '1';
   }
-  up_.init(st_, size_t(32) << 20);
   double t0 = now();
+  up_.init(st_, size_t(32) << 20);
+  nt_add("upload arena", now() - t0);
   init_stage(A);
   double tp[6] = {0, 0, 0, 0, 0, 0};
   tp[1] = now() - t0;
@@ -1880,13 +2010,19 @@ void run_factor(Handle& h, const spaqr_csr& A, const Analysis& an) {
   // the handle's timeout flag of the tensor-core kernels, cleared for this factorization
   if (!h.d_flag) SPAQR_CUDA(cudaMalloc(&h.d_flag, sizeof(int)));
   SPAQR_CUDA(cudaMemsetAsync(h.d_flag, 0, sizeof(int), h.st));
+  double t_run = 0.0;
+  const double t0 = now();
   if (h.precision == SPAQR_PREC_MIXED) {
     Factorizer<float> f(h, an);
     f.run(A);
+    t_run = now() - t0;
   } else {
     Factorizer<double> f(h, an);
     f.run(A);
+    t_run = now() - t0;
   }
+  if (h.opt.verbose)
+    std::fprintf(stderr, "[spaqr] factor: run %.3f ms, teardown %.3f ms\n", 1e3 * t_run, 1e3 * (now() - t0 - t_run));
   int late = 0;
   SPAQR_CUDA(cudaMemcpyAsync(&late, h.d_flag, sizeof(int), cudaMemcpyDeviceToHost, h.st));
   SPAQR_CUDA(cudaStreamSynchronize(h.st));
