@@ -181,35 +181,42 @@ std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Ana
   h.nnz = A->nnz;
   h.depth = a.depth;
   h.t_analyze = a.seconds;
-  if (h.opt.mode == SPAQR_MODE_DIAG) {
-    // no factorization: W = I, only the column scaling D (Section 2.7) of the
-    // diagonally preconditioned comparator ("Diag.", Section 4)
-    std::vector<double> nrm((size_t)A->n, 0.0);
-    for (int64_t e = 0; e < A->nnz; ++e) nrm[(size_t)A->colidx[e]] += A->vals[e] * A->vals[e];
-    h.D.resize((size_t)A->n);
-    for (int64_t j = 0; j < A->n; ++j) {
-      if (!(nrm[(size_t)j] > 0.0)) throw spaqr::Error(SPAQR_ERR_RANK_DEFICIENT, "zero column " + std::to_string(j));
-      h.D[(size_t)j] = 1.0 / std::sqrt(nrm[(size_t)j]);
-    }
-  } else {
-    spaqr::run_factor(h, *A, a);
-  }
   Tick tick(h.opt.verbose);
+  // the pattern of A^T, then the column scaling D (Section 2.7): each column's
+  // squared norm summed over its entries in row order, columns in parallel
+  std::vector<int64_t> trp((size_t)A->n + 1, 0);
+  std::vector<int32_t> tci((size_t)A->nnz);
+  std::vector<int64_t> tperm((size_t)A->nnz);
+  transpose_pattern(*A, trp, tci, tperm);
+  h.D.resize((size_t)A->n);
+  std::vector<char> zero_col((size_t)A->n, 0);
+  spaqr::parallel_for(A->n, [&](int64_t b, int64_t e, int) {
+    for (int64_t j = b; j < e; ++j) {
+      double nrm = 0.0;
+      for (int64_t q = trp[(size_t)j]; q < trp[(size_t)j + 1]; ++q) {
+        const double x = A->vals[tperm[(size_t)q]];
+        nrm += x * x;
+      }
+      zero_col[(size_t)j] = !(nrm > 0.0);
+      h.D[(size_t)j] = zero_col[(size_t)j] ? 0.0 : 1.0 / std::sqrt(nrm);
+    }
+  });
+  for (int64_t j = 0; j < A->n; ++j)
+    if (zero_col[(size_t)j]) throw spaqr::Error(SPAQR_ERR_RANK_DEFICIENT, "zero column " + std::to_string(j));
+  tick("transpose + column scaling");
+  // Diag. comparator (Section 4): no factorization, W = I
+  if (h.opt.mode != SPAQR_MODE_DIAG) spaqr::run_factor(h, *A, a);
   tick("factor");
   // scaled operator A~ = A D and its transpose on the device (FP64)
   std::vector<double> v((size_t)A->nnz);
   spaqr::parallel_for(A->nnz, [&](int64_t b, int64_t e, int) {
     for (int64_t q = b; q < e; ++q) v[(size_t)q] = A->vals[q] * h.D[(size_t)A->colidx[q]];
   });
-  std::vector<int64_t> trp((size_t)A->n + 1, 0);
-  std::vector<int32_t> tci((size_t)A->nnz);
   std::vector<double> tv((size_t)A->nnz);
-  std::vector<int64_t> tperm((size_t)A->nnz);
-  transpose_pattern(*A, trp, tci, tperm);
   spaqr::parallel_for(A->nnz, [&](int64_t b, int64_t e, int) {
     for (int64_t q = b; q < e; ++q) tv[(size_t)q] = v[(size_t)tperm[(size_t)q]];
   });
-  tick("scaled values + transpose");
+  tick("scaled values");
   SPAQR_CUDA(cudaMalloc(&h.d_rowptr, (size_t)(A->m + 1) * sizeof(int64_t)));
   SPAQR_CUDA(cudaMalloc(&h.d_colidx, (size_t)A->nnz * sizeof(int32_t)));
   SPAQR_CUDA(cudaMalloc(&h.d_vals, (size_t)A->nnz * sizeof(double)));

@@ -88,6 +88,157 @@ __global__ void __launch_bounds__(kThreads) identity_kernel(const CopyDesc<T>* d
   }
 }
 
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi) / 2), the operations built from the error-free
+// two-sum (Knuth) and two-product (one fused multiply-add) transformations
+// (Dekker 1971; Ogita, Rump and Oishi 2005).  About 44 significant bits.  The
+// FP32 pivoted QR forms R_ii and takes the rank decision with it: on this GPU
+// every FP64 instruction of a warp holds the FP64 pipe for tens of cycles, so
+// a handful of them per pivot step would dominate the step.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_quick(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float z = s - a;
+  return DF{s, (a - (s - z)) + (b - z)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = df_two_sum(a.hi, b.hi);
+  return df_quick(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF df_sqr(float a) {
+  const float p = a * a;
+  return DF{p, fmaf(a, a, -p)};
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);
+  return df_quick(p, e + (a.hi * b.lo + a.lo * b.hi));
+}
+__device__ __forceinline__ DF df_sqrt(DF a) {  // a >= 0; one Newton step from the FP32 root
+  if (!(a.hi > 0.f)) return DF{0.f, 0.f};
+  const float r = sqrtf(a.hi);
+  const float res = fmaf(-r, r, a.hi) + a.lo;
+  return df_quick(r, res * (0.5f / r));
+}
+__device__ __forceinline__ bool df_less(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+// Sum of squares of the entries of a column to FP64 accuracy.  For FP32 data
+// every term x^2 is split exactly into p + e (p = fl(x^2), e = fma(x, x, -p))
+// and accumulated with two-sums, the rounding errors collected in a second
+// FP32 word (the Sum2 scheme of Ogita, Rump and Oishi): s + c is the exact sum
+// up to relative errors of order (n u)^2, u = 2^-24.  FP64 data are summed in
+// FP64.  warp_total() leaves the warp's total, as a (hi, lo) pair, in every lane.
+template <typename T>
+struct SqSum;
+template <>
+struct SqSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s = fma(x, x, s); }
+  __device__ __forceinline__ void warp_total(double& hi, double& lo) {
+    hi = warp_sum(s);
+    lo = 0.0;
+  }
+};
+template <>
+struct SqSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const DF p = df_sqr(x);
+    const DF t = df_two_sum(s, p.hi);
+    c += t.lo + p.lo;
+    s = t.hi;
+  }
+  __device__ __forceinline__ void warp_total(float& hi, float& lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+      const DF t = df_two_sum(s, s2);
+      c = (c + c2) + t.lo;
+      s = t.hi;
+    }
+    const DF r = df_quick(s, c);
+    hi = r.hi;
+    lo = r.lo;
+  }
+};
+
+// The Householder data of a pivot step from alpha (the diagonal entry) and the
+// sum of squares below it (sh + sl): R_ii = beta = -sign(alpha) sqrt(alpha^2 +
+// sigma), tau = (beta - alpha) / beta, den = alpha - beta (the reflector is the
+// column below alpha divided by den), and the rank test |R_ii| < eps |R_11|
+// (stop; also when beta = 0).  r11 holds |R_11| from step 0 on (set when
+// first = true).  FP64 data: in FP64.  FP32 data: in double-float.
+template <typename T>
+struct HouseStep {
+  T beta, tau, den;
+  bool stop;
+};
+__device__ __forceinline__ HouseStep<double> house_step(double alpha, double sh, double, double eps, double& r11,
+                                                        bool first) {
+  HouseStep<double> h;
+  if (sh == 0.0) {
+    h.beta = alpha;
+    h.tau = 0.0;
+    h.den = 0.0;
+  } else {
+    const double nrm = sqrt(alpha * alpha + sh);
+    h.beta = alpha >= 0.0 ? -nrm : nrm;
+    h.tau = (h.beta - alpha) / h.beta;
+    h.den = alpha - h.beta;
+  }
+  const double ab = fabs(h.beta);
+  if (first) r11 = ab;
+  h.stop = h.beta == 0.0 || ab < eps * r11;
+  return h;
+}
+__device__ __forceinline__ HouseStep<float> house_step(float alpha, float sh, float sl, DF eps, DF& r11, bool first) {
+  HouseStep<float> h;
+  DF b;  // |beta|
+  if (sh == 0.f && sl == 0.f) {
+    b = DF{fabsf(alpha), 0.f};
+    h.beta = alpha;
+    h.tau = 0.f;
+    h.den = 0.f;
+  } else {
+    b = df_sqrt(df_add(df_sqr(alpha), DF{sh, sl}));
+    const float sg = alpha >= 0.f ? -1.f : 1.f;  // beta = sg * b
+    const DF den = df_add(DF{alpha, 0.f}, DF{-sg * b.hi, -sg * b.lo});  // alpha - beta, no cancellation
+    h.beta = sg * (b.hi + b.lo);
+    h.den = den.hi + den.lo;
+    h.tau = -h.den / h.beta;  // (beta - alpha) / beta
+  }
+  if (first) r11 = b;
+  h.stop = (b.hi == 0.f) || df_less(b, df_mul(eps, r11));
+  return h;
+}
+
+// Householder data of a front column (no rank test): FP64 for FP64 data,
+// double-float for FP32 data, as in the pivoted QR.
+__device__ __forceinline__ HouseStep<double> front_house(double alpha, double sh, double sl) {
+  double r11 = 0.0;
+  return house_step(alpha, sh, sl, 0.0, r11, true);
+}
+__device__ __forceinline__ HouseStep<float> front_house(float alpha, float sh, float sl) {
+  DF r11{0.f, 0.f};
+  return house_step(alpha, sh, sl, DF{0.f, 0.f}, r11, true);
+}
+
+// (hi, lo) sums of squares combined in a fixed order: double-float for FP32,
+// plain addition for FP64 (lo = 0)
+__device__ __forceinline__ void sq_combine(float& h, float& l, float h2, float l2) {
+  const DF t = df_add(DF{h, l}, DF{h2, l2});
+  h = t.hi;
+  l = t.lo;
+}
+__device__ __forceinline__ void sq_combine(double& h, double& l, double h2, double) { h += h2; (void)l; }
+
 // --------------------------------------------------------- reflector maths
 // Computes the Householder reflector of x = X[j:m, j] (column j of X with
 // leading dimension ld) by warp 0: beta = -sign(alpha) ||x|| (sign(0) = +1),
@@ -95,33 +246,22 @@ __global__ void __launch_bounds__(kThreads) identity_kernel(const CopyDesc<T>* d
 // tau = 0 (H = I) when x[1:] = 0.  Writes v in place and beta at X[j, j].
 // Returns (through shared memory) tau and beta.
 template <typename T>
-__device__ void make_reflector_warp0(T* X, int ld, int m, int j, T* s_tau, double* s_beta) {
+__device__ void make_reflector_warp0(T* X, int ld, int m, int j, T* s_tau, T* s_beta) {
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
   T* col = X + (int64_t)j * ld;
-  double sig = 0.0;
-  for (int i = j + 1 + lane; i < m; i += 32) {
-    const double v = (double)col[i];
-    sig += v * v;
-  }
-  sig = warp_sum(sig);
-  const double alpha = (double)col[j];
-  double beta, tau;
-  if (sig == 0.0) {
-    beta = alpha;
-    tau = 0.0;
-  } else {
-    const double nrm = sqrt(alpha * alpha + sig);
-    beta = alpha >= 0.0 ? -nrm : nrm;
-    tau = (beta - alpha) / beta;
-    const T den = (T)(alpha - beta);
-    for (int i = j + 1 + lane; i < m; i += 32) col[i] = col[i] / den;
-  }
+  SqSum<T> acc;
+  for (int i = j + 1 + lane; i < m; i += 32) acc.add(col[i]);
+  T sh, sl;
+  acc.warp_total(sh, sl);
+  const HouseStep<T> h = front_house(col[j], sh, sl);
+  if (h.tau != T(0))
+    for (int i = j + 1 + lane; i < m; i += 32) col[i] = col[i] / h.den;
   __syncwarp();
   if (lane == 0) {
-    col[j] = (T)beta;
-    *s_tau = (T)tau;
-    *s_beta = beta;
+    col[j] = h.beta;
+    *s_tau = h.tau;
+    *s_beta = h.beta;
   }
 }
 
@@ -148,8 +288,7 @@ __global__ void __launch_bounds__(kThreads) front_qr_smem_kernel(const FrontDesc
   const FrontDesc<T> d = descs[blockIdx.x];
   extern __shared__ __align__(16) unsigned char smraw[];
   T* S = reinterpret_cast<T*>(smraw);
-  __shared__ T s_tau;
-  __shared__ double s_beta;
+  __shared__ T s_tau, s_beta;
   const int m = d.m, n = d.n, c = d.c;
   if (m == 0 || n == 0) return;
   const int64_t tot = (int64_t)m * n;
@@ -165,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) front_qr_smem_kernel(const FrontDesc
     make_reflector_warp0(S, m, m, j, &s_tau, &s_beta);
     __syncthreads();
     const T tau = s_tau;
-    if (threadIdx.x == 0 && s_beta < 0.0) negmask[j >> 5] |= 1u << (j & 31);
+    if (threadIdx.x == 0 && s_beta < T(0)) negmask[j >> 5] |= 1u << (j & 31);
     if (tau != T(0)) apply_reflector_cols(S, m, m, j, tau, j + 1, n);
     __syncthreads();
   }
@@ -203,30 +342,19 @@ __global__ void __launch_bounds__(kThreads) front_qr_warp_kernel(const FrontDesc
   unsigned negs[4] = {0u, 0u, 0u, 0u};  // steps <= 128 for this kernel
   for (int j = 0; j < steps; ++j) {
     T* col = S + j * ld;
-    double sig = 0.0;
-    for (int r = j + 1 + lane; r < m; r += 32) {
-      const double v = (double)col[r];
-      sig += v * v;
-    }
-    sig = warp_sum(sig);
-    const double alpha = (double)col[j];
-    double beta, tau;
-    if (sig == 0.0) {
-      beta = alpha;
-      tau = 0.0;
-    } else {
-      const double nrm = sqrt(alpha * alpha + sig);
-      beta = alpha >= 0.0 ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      const T den = (T)(alpha - beta);
-      for (int r = j + 1 + lane; r < m; r += 32) col[r] = col[r] / den;
-    }
-    if (beta < 0.0) negs[j >> 5] |= 1u << (j & 31);
+    SqSum<T> acc;
+    for (int r = j + 1 + lane; r < m; r += 32) acc.add(col[r]);
+    T sh, sl;
+    acc.warp_total(sh, sl);
+    const HouseStep<T> h = front_house(col[j], sh, sl);
+    if (h.tau != T(0))
+      for (int r = j + 1 + lane; r < m; r += 32) col[r] = col[r] / h.den;
+    if (h.beta < T(0)) negs[j >> 5] |= 1u << (j & 31);
     __syncwarp();
-    if (lane == 0) col[j] = (T)beta;
+    if (lane == 0) col[j] = h.beta;
     __syncwarp();
-    if (tau != 0.0) {
-      const T tt = (T)tau;
+    if (h.tau != T(0)) {
+      const T tt = h.tau;
       for (int cc = j + 1 + lane; cc < n; cc += 32) {
         T* x = S + cc * ld;
         T sacc = x[j];
@@ -258,8 +386,7 @@ __global__ void __launch_bounds__(kThreads) front_panel_kernel(const FrontDesc<T
   const int steps = d.c < d.m ? d.c : d.m;
   const int b = min(nb, steps - j0);
   if (b <= 0) return;
-  __shared__ T s_tau;
-  __shared__ double s_beta;
+  __shared__ T s_tau, s_beta;
   __shared__ T taus[64];
   __shared__ T G[64 * 64];  // G[l + i*64] = V_l . V_i (l < i)
   T* X = d.ptr;
@@ -329,12 +456,11 @@ __global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const 
   const int ld = per_max | 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* P = reinterpret_cast<T*>(smraw);  // nr x b, ld
-  __shared__ double sq_part, alpha_s;
+  __shared__ T sq_h, sq_l, alpha_s;  // this CTA's partial sum of squares (hi, lo) and the diagonal entry
   __shared__ T dots[32], wsum[32], taus[32];
   __shared__ T Gp[32 * 33];
-  __shared__ double s_beta;
-  __shared__ T s_tau, s_den;
-  __shared__ double red[kWarps];
+  __shared__ T s_beta, s_tau, s_den;
+  __shared__ T red_h[kWarps], red_l[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* X = d.ptr;
   for (int e = threadIdx.x; e < nr * b; e += kThreads) {
@@ -345,39 +471,44 @@ __global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const 
   for (int jj = 0; jj < b; ++jj) {
     const int j = j0 + jj;
     const T* pc = P + jj * ld;
-    double sq = 0.0;
-    for (int r = max(r0, j + 1) + threadIdx.x; r < r1; r += kThreads) {
-      const double v = (double)pc[r - r0];
-      sq += v * v;
+    // (1) this CTA's sum of squares below the diagonal (FP64-accurate)
+    {
+      SqSum<T> acc;
+      for (int r = max(r0, j + 1) + threadIdx.x; r < r1; r += kThreads) acc.add(pc[r - r0]);
+      T h, l;
+      acc.warp_total(h, l);
+      if (lane == 0) {
+        red_h[warp] = h;
+        red_l[warp] = l;
+      }
     }
-    sq = warp_sum(sq);
-    if (lane == 0) red[warp] = sq;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kWarps; ++w) t += red[w];
-      sq_part = t;
-      if (j >= r0 && j < r1) alpha_s = (double)pc[j - r0];
+      T h = red_h[0], l = red_l[0];
+      for (int w = 1; w < kWarps; ++w) sq_combine(h, l, red_h[w], red_l[w]);
+      sq_h = h;
+      sq_l = l;
+      if (j >= r0 && j < r1) alpha_s = pc[j - r0];
     }
     cl.sync();  // (A) partial norms and the diagonal entry visible
     const int owner = (j - j0) / per;
-    if (threadIdx.x == 0) {
-      double sig = 0.0;
-      for (int q = 0; q < CS; ++q) sig += *cl.map_shared_rank(&sq_part, q);
-      const double alpha = *cl.map_shared_rank(&alpha_s, owner);
-      double beta, tau;
-      if (sig == 0.0) {
-        beta = alpha;
-        tau = 0.0;
-      } else {
-        const double nrm = sqrt(alpha * alpha + sig);
-        beta = alpha >= 0.0 ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
+    if (warp == 0) {
+      // the CS partials read side by side (one lane each), combined in rank order
+      T h = T(0), l = T(0);
+      if (lane < CS) {
+        h = *cl.map_shared_rank(&sq_h, lane);
+        l = *cl.map_shared_rank(&sq_l, lane);
       }
-      s_beta = beta;
-      s_tau = (T)tau;
-      s_den = sig == 0.0 ? T(1) : (T)(alpha - beta);
-      taus[jj] = (T)tau;
+      const T alpha = *cl.map_shared_rank(&alpha_s, owner);
+      T th = __shfl_sync(0xffffffffu, h, 0), tl = __shfl_sync(0xffffffffu, l, 0);
+      for (int q = 1; q < CS; ++q) sq_combine(th, tl, __shfl_sync(0xffffffffu, h, q), __shfl_sync(0xffffffffu, l, q));
+      if (lane == 0) {
+        const HouseStep<T> hs = front_house(alpha, th, tl);
+        s_beta = hs.beta;
+        s_tau = hs.tau;
+        s_den = hs.tau != T(0) ? hs.den : T(1);
+        taus[jj] = hs.tau;
+      }
     }
     __syncthreads();
     const T tau = s_tau, den = s_den;
@@ -385,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const 
     if (tau != T(0))
       for (int r = max(r0, j + 1) + threadIdx.x; r < r1; r += kThreads) pcw[r - r0] = pcw[r - r0] / den;
     __syncthreads();
-    if (rank == owner && threadIdx.x == 0) pcw[j - r0] = (T)s_beta;
+    if (rank == owner && threadIdx.x == 0) pcw[j - r0] = s_beta;
     // partial products v . x_c for the panel columns c > jj (v_j = 1)
     for (int c = jj + 1 + warp; c < b; c += kWarps) {
       const T* xc = P + c * ld;
@@ -396,19 +527,27 @@ __global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const 
     }
     cl.sync();  // (B) partial products visible
     if (threadIdx.x > jj && threadIdx.x < b) {
+      // all CS loads issued before the sum (rank order)
+      T v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = q < CS ? *cl.map_shared_rank(&dots[threadIdx.x], q) : T(0);
       T w = T(0);
-      for (int q = 0; q < CS; ++q) w += *cl.map_shared_rank(&dots[threadIdx.x], q);
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (q < CS) w += v[q];
       wsum[threadIdx.x] = tau * w;
     }
     __syncthreads();
     if (tau != T(0)) {
+      // rank-1 update of this CTA's rows: a warp per column, lanes over rows
       const int rbeg = max(r0, j);
-      const int cnt = r1 - rbeg;
-      for (int e = threadIdx.x; cnt > 0 && e < cnt * (b - jj - 1); e += kThreads) {
-        const int rr = e % cnt, c = jj + 1 + e / cnt;
-        const int r = rbeg + rr;
-        const T v = r == j ? T(1) : pc[r - r0];
-        P[(r - r0) + c * ld] -= wsum[c] * v;
+      for (int c = jj + 1 + warp; c < b; c += kWarps) {
+        T* xc = P + c * ld;
+        const T wc = wsum[c];
+        for (int r = rbeg + lane; r < r1; r += 32) {
+          const T vr = r == j ? T(1) : pc[r - r0];
+          xc[r - r0] -= wc * vr;
+        }
       }
     }
     __syncthreads();
@@ -612,137 +751,6 @@ __device__ __forceinline__ double recompute_frac<double>() {
 template <>
 __device__ __forceinline__ float recompute_frac<float>() {
   return 3.4527e-4f;
-}
-
-// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
-// numbers (|lo| <= ulp(hi) / 2), the operations built from the error-free
-// two-sum (Knuth) and two-product (one fused multiply-add) transformations
-// (Dekker 1971; Ogita, Rump and Oishi 2005).  About 44 significant bits.  The
-// FP32 pivoted QR forms R_ii and takes the rank decision with it: on this GPU
-// every FP64 instruction of a warp holds the FP64 pipe for tens of cycles, so
-// a handful of them per pivot step would dominate the step.
-struct DF {
-  float hi, lo;
-};
-__device__ __forceinline__ DF df_quick(float a, float b) {  // |a| >= |b|
-  const float s = a + b;
-  return DF{s, b - (s - a)};
-}
-__device__ __forceinline__ DF df_two_sum(float a, float b) {
-  const float s = a + b;
-  const float z = s - a;
-  return DF{s, (a - (s - z)) + (b - z)};
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  const DF s = df_two_sum(a.hi, b.hi);
-  return df_quick(s.hi, s.lo + (a.lo + b.lo));
-}
-__device__ __forceinline__ DF df_sqr(float a) {
-  const float p = a * a;
-  return DF{p, fmaf(a, a, -p)};
-}
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-  const float p = a.hi * b.hi;
-  const float e = fmaf(a.hi, b.hi, -p);
-  return df_quick(p, e + (a.hi * b.lo + a.lo * b.hi));
-}
-__device__ __forceinline__ DF df_sqrt(DF a) {  // a >= 0; one Newton step from the FP32 root
-  if (!(a.hi > 0.f)) return DF{0.f, 0.f};
-  const float r = sqrtf(a.hi);
-  const float res = fmaf(-r, r, a.hi) + a.lo;
-  return df_quick(r, res * (0.5f / r));
-}
-__device__ __forceinline__ bool df_less(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
-
-// Sum of squares of the entries of a column to FP64 accuracy.  For FP32 data
-// every term x^2 is split exactly into p + e (p = fl(x^2), e = fma(x, x, -p))
-// and accumulated with two-sums, the rounding errors collected in a second
-// FP32 word (the Sum2 scheme of Ogita, Rump and Oishi): s + c is the exact sum
-// up to relative errors of order (n u)^2, u = 2^-24.  FP64 data are summed in
-// FP64.  warp_total() leaves the warp's total, as a (hi, lo) pair, in every lane.
-template <typename T>
-struct SqSum;
-template <>
-struct SqSum<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double x) { s = fma(x, x, s); }
-  __device__ __forceinline__ void warp_total(double& hi, double& lo) {
-    hi = warp_sum(s);
-    lo = 0.0;
-  }
-};
-template <>
-struct SqSum<float> {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const DF p = df_sqr(x);
-    const DF t = df_two_sum(s, p.hi);
-    c += t.lo + p.lo;
-    s = t.hi;
-  }
-  __device__ __forceinline__ void warp_total(float& hi, float& lo) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-      const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-      const DF t = df_two_sum(s, s2);
-      c = (c + c2) + t.lo;
-      s = t.hi;
-    }
-    const DF r = df_quick(s, c);
-    hi = r.hi;
-    lo = r.lo;
-  }
-};
-
-// The Householder data of a pivot step from alpha (the diagonal entry) and the
-// sum of squares below it (sh + sl): R_ii = beta = -sign(alpha) sqrt(alpha^2 +
-// sigma), tau = (beta - alpha) / beta, den = alpha - beta (the reflector is the
-// column below alpha divided by den), and the rank test |R_ii| < eps |R_11|
-// (stop; also when beta = 0).  r11 holds |R_11| from step 0 on (set when
-// first = true).  FP64 data: in FP64.  FP32 data: in double-float.
-template <typename T>
-struct HouseStep {
-  T beta, tau, den;
-  bool stop;
-};
-__device__ __forceinline__ HouseStep<double> house_step(double alpha, double sh, double, double eps, double& r11,
-                                                        bool first) {
-  HouseStep<double> h;
-  if (sh == 0.0) {
-    h.beta = alpha;
-    h.tau = 0.0;
-    h.den = 0.0;
-  } else {
-    const double nrm = sqrt(alpha * alpha + sh);
-    h.beta = alpha >= 0.0 ? -nrm : nrm;
-    h.tau = (h.beta - alpha) / h.beta;
-    h.den = alpha - h.beta;
-  }
-  const double ab = fabs(h.beta);
-  if (first) r11 = ab;
-  h.stop = h.beta == 0.0 || ab < eps * r11;
-  return h;
-}
-__device__ __forceinline__ HouseStep<float> house_step(float alpha, float sh, float sl, DF eps, DF& r11, bool first) {
-  HouseStep<float> h;
-  DF b;  // |beta|
-  if (sh == 0.f && sl == 0.f) {
-    b = DF{fabsf(alpha), 0.f};
-    h.beta = alpha;
-    h.tau = 0.f;
-    h.den = 0.f;
-  } else {
-    b = df_sqrt(df_add(df_sqr(alpha), DF{sh, sl}));
-    const float sg = alpha >= 0.f ? -1.f : 1.f;  // beta = sg * b
-    const DF den = df_add(DF{alpha, 0.f}, DF{-sg * b.hi, -sg * b.lo});  // alpha - beta, no cancellation
-    h.beta = sg * (b.hi + b.lo);
-    h.den = den.hi + den.lo;
-    h.tau = -h.den / h.beta;  // (beta - alpha) / beta
-  }
-  if (first) r11 = b;
-  h.stop = (b.hi == 0.f) || df_less(b, df_mul(eps, r11));
-  return h;
 }
 
 // One warp's proposal for the next pivot step, as the slab QRCP exchanges it:

@@ -249,6 +249,93 @@ double now() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// A short int list stored inline up to kInline entries (most row-group
+// supports), on the heap beyond: groups are created and dropped by the hundred
+// thousand per stage, in parallel, and this keeps the allocator out of it.
+class SmallInts {
+ public:
+  static constexpr int kInline = 8;
+  SmallInts() = default;
+  SmallInts(const SmallInts& o) { assign(o.begin(), o.end()); }
+  SmallInts(SmallInts&& o) noexcept { take(o); }
+  SmallInts& operator=(const SmallInts& o) {
+    if (this != &o) assign(o.begin(), o.end());
+    return *this;
+  }
+  SmallInts& operator=(SmallInts&& o) noexcept {
+    if (this != &o) {
+      clear_free();
+      take(o);
+    }
+    return *this;
+  }
+  ~SmallInts() { clear_free(); }
+  void assign(const int* b, const int* e) {
+    const size_t n = (size_t)(e - b);
+    reserve_exact(n);
+    std::copy(b, e, data());
+    n_ = (int)n;
+  }
+  void resize(size_t n) {
+    if (n > (size_t)cap()) {
+      SmallInts t;
+      t.reserve_exact(n);
+      std::copy(begin(), end(), t.data());
+      t.n_ = n_;
+      *this = std::move(t);
+    }
+    n_ = (int)n;
+  }
+  void clear_free() {
+    if (heap_) delete[] heap_;
+    heap_ = nullptr;
+    hcap_ = 0;
+    n_ = 0;
+  }
+  void swap(SmallInts& o) noexcept {
+    SmallInts t(std::move(o));
+    o = std::move(*this);
+    *this = std::move(t);
+  }
+  size_t size() const { return (size_t)n_; }
+  bool empty() const { return n_ == 0; }
+  int* data() { return heap_ ? heap_ : in_; }
+  const int* data() const { return heap_ ? heap_ : in_; }
+  int* begin() { return data(); }
+  int* end() { return data() + n_; }
+  const int* begin() const { return data(); }
+  const int* end() const { return data() + n_; }
+  int& operator[](size_t i) { return data()[i]; }
+  int operator[](size_t i) const { return data()[i]; }
+
+ private:
+  int cap() const { return heap_ ? hcap_ : kInline; }
+  // room for n entries; the contents are not kept
+  void reserve_exact(size_t n) {
+    if (n <= (size_t)cap()) return;
+    clear_free();
+    if (n > (size_t)kInline) {
+      heap_ = new int[n];
+      hcap_ = (int)n;
+    }
+  }
+  void take(SmallInts& o) {
+    n_ = o.n_;
+    if (o.heap_) {
+      heap_ = o.heap_;
+      hcap_ = o.hcap_;
+      o.heap_ = nullptr;
+      o.hcap_ = 0;
+    } else {
+      std::copy(o.in_, o.in_ + o.n_, in_);
+    }
+    o.n_ = 0;
+  }
+  int* heap_ = nullptr;
+  int hcap_ = 0, n_ = 0;
+  int in_[kInline];
+};
+
 // Group ids per cluster in CSR form (ascending ids per cluster): index_groups()
 // builds one for the groups each cluster owns and one for the groups of other
 // owners that touch it.
@@ -284,7 +371,7 @@ class Factorizer {
   struct Group {
     int owner = -1;
     int rows = 0, ld = 0, width = 0;
-    std::vector<int> sup, off;
+    SmallInts sup, off;  // support clusters (ascending) and their first column in the block
     T* ptr = nullptr;
     int buf = -1;
     bool alive = false;
@@ -394,11 +481,11 @@ class Factorizer {
     if (n) SPAQR_CUDA(cudaMemcpy(host, dev, n * sizeof(X), cudaMemcpyDeviceToHost));
     up_.reset();
   }
-  void make_group(Group& g, int owner, int rows, std::vector<int>&& sup) const {
+  void make_group(Group& g, int owner, int rows, const int* sb, const int* se) const {
     g.owner = owner;
     g.rows = rows;
     g.ld = std::max(rows, 1);
-    g.sup = std::move(sup);
+    g.sup.assign(sb, se);
     g.off.resize(g.sup.size());
     int w = 0;
     for (size_t t = 0; t < g.sup.size(); ++t) {
@@ -407,13 +494,6 @@ class Factorizer {
     }
     g.width = w;
     g.alive = true;
-  }
-  int new_group(int owner, int rows, std::vector<int> sup) {
-    Group g;
-    make_group(g, owner, rows, std::move(sup));
-    G_.push_back(std::move(g));
-    live_.push_back((int)G_.size() - 1);
-    return (int)G_.size() - 1;
   }
   // n new (empty) groups with consecutive ids, appended to the live list; returns the first id
   int add_groups(size_t n) {
@@ -467,27 +547,37 @@ class Factorizer {
     g.buf = -1;
     g.ptr = nullptr;
   }
-  // kill a list of groups: buffer references serially, the layout vectors freed in parallel
+  // kill a list of groups in parallel: buffer references drop atomically, the
+  // buffers that lose their last reference go back to the pool afterwards (in
+  // ascending buffer number)
   void kill_many(const std::vector<int>& ids) {
-    for (int id : ids) {
-      Group& g = G_[(size_t)id];
-      drop_data(g);
-      g.alive = false;
-    }
-    parallel_for((int64_t)ids.size(), [&](int64_t b, int64_t e, int) {
+    std::vector<std::vector<int>> freed((size_t)ThreadPool::get().workers());
+    parallel_for((int64_t)ids.size(), [&](int64_t b, int64_t e, int w) {
       for (int64_t i = b; i < e; ++i) {
         Group& g = G_[(size_t)ids[(size_t)i]];
-        std::vector<int>().swap(g.sup);
-        std::vector<int>().swap(g.off);
+        if (g.buf >= 0 && __atomic_sub_fetch(&bufs_[(size_t)g.buf].refs, 1, __ATOMIC_ACQ_REL) == 0)
+          freed[(size_t)w].push_back(g.buf);
+        g.buf = -1;
+        g.ptr = nullptr;
+        g.alive = false;
+        g.sup.clear_free();
+        g.off.clear_free();
       }
     }, 4096);
+    std::vector<int> all;
+    for (auto& v : freed) all.insert(all.end(), v.begin(), v.end());
+    std::sort(all.begin(), all.end());
+    for (int b : all) {
+      pool_.release(bufs_[(size_t)b].p);
+      bufs_[(size_t)b].p = nullptr;
+    }
   }
   void kill(int id) {
     Group& g = G_[(size_t)id];
     drop_data(g);
     g.alive = false;
-    std::vector<int>().swap(g.sup);
-    std::vector<int>().swap(g.off);
+    g.sup.clear_free();
+    g.off.clear_free();
   }
   int col_off(const Group& g, int c) const {
     auto it = std::lower_bound(g.sup.begin(), g.sup.end(), c);
@@ -720,24 +810,21 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
   slots_.assign(nc, {});
   calive_.assign(nc, 1);
   std::vector<int32_t> cl_of((size_t)h_.n, -1), pos_of((size_t)h_.n, 0);
-  for (size_t c = 0; c < nc; ++c) {
-    const int64_t b = st.vptr[c], e = st.vptr[c + 1];
-    ccols_[c] = (int)(e - b);
-    slots_[c].assign(st.verts.begin() + b, st.verts.begin() + e);
-    for (int64_t t = b; t < e; ++t) {
-      cl_of[(size_t)st.verts[(size_t)t]] = (int)c;
-      pos_of[(size_t)st.verts[(size_t)t]] = (int)(t - b);
+  parallel_for((int64_t)nc, [&](int64_t b0, int64_t b1, int) {
+    for (int64_t cc = b0; cc < b1; ++cc) {
+      const size_t c = (size_t)cc;
+      const int64_t b = st.vptr[c], e = st.vptr[c + 1];
+      ccols_[c] = (int)(e - b);
+      slots_[c].assign(st.verts.begin() + b, st.verts.begin() + e);
+      for (int64_t t = b; t < e; ++t) {  // clusters hold disjoint vertex sets
+        cl_of[(size_t)st.verts[(size_t)t]] = (int)c;
+        pos_of[(size_t)st.verts[(size_t)t]] = (int)(t - b);
+      }
     }
-  }
+  }, 256);
   lap("init: cluster maps");
-  // column scaling (R1)
-  std::vector<double> nrm((size_t)h_.n, 0.0);
-  for (int64_t e = 0; e < A.nnz; ++e) nrm[(size_t)A.colidx[e]] += A.vals[e] * A.vals[e];  // fixed order
-  h_.D.resize((size_t)h_.n);
-  for (int64_t j = 0; j < h_.n; ++j) {
-    if (!(nrm[(size_t)j] > 0.0)) throw Error(SPAQR_ERR_RANK_DEFICIENT, "zero column " + std::to_string(j));
-    h_.D[(size_t)j] = 1.0 / std::sqrt(nrm[(size_t)j]);
-  }
+  // column scaling D (Section 2.7), computed by the caller
+  if ((int64_t)h_.D.size() != h_.n) throw Error(SPAQR_ERR_CUDA, "internal: column scaling missing");
   lap("init: column norms");
   // row owners by the max-norm rule on A D (R2), grouped by (owner, support);
   // rows are independent: two parallel passes (support sizes, then contents)
@@ -829,8 +916,30 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
     if (std::lexicographical_compare(pb, pb + lb, pa, pa + la)) return false;
     return a < b;
   };
+  // a support of at most two clusters packs into one integer key that orders
+  // like the lists themselves ([a] < [a, b]); owners whose rows all have such
+  // supports sort (key, row) pairs, the others compare the lists
   parallel_for((int64_t)nc, [&](int64_t b, int64_t e, int) {
-    for (int64_t c = b; c < e; ++c) std::sort(order.begin() + cnt[(size_t)c], order.begin() + cnt[(size_t)c + 1], sup_less);
+    std::vector<std::pair<uint64_t, int64_t>> kv;
+    for (int64_t c = b; c < e; ++c) {
+      const int64_t i0 = cnt[(size_t)c], i1 = cnt[(size_t)c + 1];
+      bool packed = true;
+      for (int64_t i = i0; i < i1 && packed; ++i) packed = sptr[(size_t)order[(size_t)i] + 1] - sptr[(size_t)order[(size_t)i]] <= 2;
+      if (!packed) {
+        std::sort(order.begin() + i0, order.begin() + i1, sup_less);
+        continue;
+      }
+      kv.resize((size_t)(i1 - i0));
+      for (int64_t i = i0; i < i1; ++i) {
+        const int64_t r = order[(size_t)i];
+        const int32_t* sp = &sups[(size_t)sptr[(size_t)r]];
+        const int64_t len = sptr[(size_t)r + 1] - sptr[(size_t)r];
+        const uint64_t key = ((uint64_t)(uint32_t)sp[0] << 32) | (len == 2 ? (uint64_t)(uint32_t)sp[1] + 1 : 0);
+        kv[(size_t)(i - i0)] = {key, r};
+      }
+      std::sort(kv.begin(), kv.end());
+      for (int64_t i = i0; i < i1; ++i) order[(size_t)i] = kv[(size_t)(i - i0)].second;
+    }
   }, 256);
   lap("init: sort rows");
   // groups: runs of equal (owner, support) in the sorted order, built in parallel
@@ -859,8 +968,8 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
       const int64_t r0 = order[(size_t)i];
       const int id = gbase + (int)q;
       ids[(size_t)q] = id;
-      std::vector<int> sup(&sups[(size_t)sptr[(size_t)r0]], &sups[(size_t)sptr[(size_t)r0 + 1]]);
-      make_group(G_[(size_t)id], owner[(size_t)r0], (int)(j - i), std::move(sup));
+      make_group(G_[(size_t)id], owner[(size_t)r0], (int)(j - i), &sups[(size_t)sptr[(size_t)r0]],
+                 &sups[(size_t)sptr[(size_t)r0]] + (sptr[(size_t)r0 + 1] - sptr[(size_t)r0]));
       for (int64_t t = i; t < j; ++t) {
         grp_of_row[(size_t)order[(size_t)t]] = id;
         rowpos[(size_t)order[(size_t)t]] = (int32_t)(t - i);
@@ -1225,7 +1334,7 @@ void Factorizer<T>::eliminate_round(const std::vector<std::pair<int, std::vector
         i = j;
       }
       for (size_t q = pfirst[b]; q < p; ++q)
-        make_group(G_[(size_t)pend[q].id], pend[q].owner, pend[q].cnt, std::vector<int>(f.cols.begin() + 1, f.cols.end()));
+        make_group(G_[(size_t)pend[q].id], pend[q].owner, pend[q].cnt, f.cols.data() + 1, f.cols.data() + f.cols.size());
     }
   }, 64);
   lap("elim: pending groups");
@@ -1395,22 +1504,24 @@ void Factorizer<T>::scale() {
         ids.push_back(next++);
       }
     }
+    lap("scale: ops");
     kill_many(dead);
+    lap("scale: kill");
     parallel_for((int64_t)si.size(), [&](int64_t b, int64_t e, int) {
       for (int64_t q = b; q < e; ++q) {
         const SInfo& s = si[(size_t)q];
         std::vector<int> sup1(s.cols.begin(), s.cols.end());
         std::sort(sup1.begin(), sup1.end());
-        make_group(G_[(size_t)p1_of_[(size_t)s.p]], s.p, s.c, std::move(sup1));
+        make_group(G_[(size_t)p1_of_[(size_t)s.p]], s.p, s.c, sup1.data(), sup1.data() + sup1.size());
         if (p2_of_[(size_t)s.p] >= 0) {
           std::vector<int> rest(s.cols.begin() + 1, s.cols.end());
           std::sort(rest.begin(), rest.end());
-          make_group(G_[(size_t)p2_of_[(size_t)s.p]], s.p, s.rp - s.c, std::move(rest));
+          make_group(G_[(size_t)p2_of_[(size_t)s.p]], s.p, s.rp - s.c, rest.data(), rest.data() + rest.size());
         }
       }
     }, 1024);
   }
-  lap("scale: ops+groups");
+  lap("scale: groups");
   assign_buffer(ids, false);
   for (auto& s : si) {
     const T* F = W + s.foff;
@@ -1585,6 +1696,7 @@ void Factorizer<T>::step2() {
   lap("step2: colouring");
   GroupIndex own, touch;
   index_groups(own, touch);
+  lap("step2: index groups");
   // one device rank slot per interface of this phase, read back with a single copy
   int* kdev_all = static_cast<int*>(h_.wpool.alloc(ps.size() * sizeof(int)));
   size_t kdev_next = 0;
@@ -1595,6 +1707,7 @@ void Factorizer<T>::step2() {
   };
   std::vector<P2> recs;
   std::vector<T*> work_all;
+  const size_t ops0 = h_.ops.size();  // this phase's ops are appended from here
   std::vector<std::vector<int>> members((size_t)ncol);
   for (int p : ps) members[(size_t)colour[(size_t)p]].push_back(p);
   for (int col = 0; col < ncol; ++col) {
@@ -1702,6 +1815,7 @@ void Factorizer<T>::step2() {
         }
       }
     }, 16);
+    lap("step2: colour plan");
     copies(cps);
     qrcp(qs, work_all);
     if (checking_)
@@ -1720,8 +1834,8 @@ void Factorizer<T>::step2() {
       tm_.end(st_);
     }
     pool_.release(M);
+    lap("step2: colour launches");
   }
-  lap("step2: per-colour plan+launch");
   // ranks back; keep the ops that drop something
   std::vector<int> kall(std::max<size_t>(kdev_next, 1));
   sync();
@@ -1737,7 +1851,7 @@ void Factorizer<T>::step2() {
                                       std::to_string(k_));
   }
   for (T* w : work_all) pool_.release(w);
-  std::vector<char> drop(h_.ops.size(), 0);
+  std::vector<char> drop(h_.ops.size() - ops0, 0);
   for (size_t i = 0; i < recs.size(); ++i) {
     WOp& op = h_.ops[recs[i].op];
     const int k = ks[i], p = recs[i].p;
@@ -1753,7 +1867,7 @@ void Factorizer<T>::step2() {
       h_.stats.flops_sparsify += 4.0 * kk * m * n;
     }
     if (k >= op.c) {
-      drop[recs[i].op] = 1;
+      drop[recs[i].op - ops0] = 1;
       continue;
     }
     ccols_[(size_t)p] = k;
@@ -1766,11 +1880,14 @@ void Factorizer<T>::step2() {
     }
   }
   // remove identity ops (k == c) -- their device blocks stay in the W pool
-  std::vector<WOp> kept;
-  kept.reserve(h_.ops.size());
-  for (size_t i = 0; i < h_.ops.size(); ++i)
-    if (!drop[i]) kept.push_back(std::move(h_.ops[i]));
-  h_.ops.swap(kept);
+  size_t w = ops0;
+  for (size_t i = ops0; i < h_.ops.size(); ++i)
+    if (!drop[i - ops0]) {
+      if (w != i) h_.ops[w] = std::move(h_.ops[i]);
+      ++w;
+    }
+  h_.ops.resize(w);
+  lap("step2: rank bookkeeping");
   (void)own;
 }
 
@@ -1786,6 +1903,8 @@ void Factorizer<T>::merge() {
   std::vector<int> nccols(nnew, 0);
   std::vector<std::vector<int32_t>> nslots(nnew);
   std::vector<int> choff(ccols_.size(), 0), nchild(nnew, 0);
+  // children of every parent in ascending id (CSR), then each parent's slots in parallel
+  std::vector<int64_t> cptr(nnew + 1, 0);
   for (size_t c = 0; c < ccols_.size(); ++c) {
     if (!calive_[c]) continue;
     const int P = sc_->parent[c];
@@ -1793,8 +1912,25 @@ void Factorizer<T>::merge() {
     choff[c] = nccols[(size_t)P];
     nccols[(size_t)P] += ccols_[c];
     nchild[(size_t)P]++;
-    nslots[(size_t)P].insert(nslots[(size_t)P].end(), slots_[c].begin(), slots_[c].end());
+    cptr[(size_t)P + 1]++;
   }
+  for (size_t P = 0; P < nnew; ++P) cptr[P + 1] += cptr[P];
+  std::vector<int> kids((size_t)cptr[nnew]);
+  {
+    std::vector<int64_t> at(cptr.begin(), cptr.end() - 1);
+    for (size_t c = 0; c < ccols_.size(); ++c)
+      if (calive_[c]) kids[(size_t)at[(size_t)sc_->parent[c]]++] = (int)c;
+  }
+  parallel_for((int64_t)nnew, [&](int64_t b, int64_t e, int) {
+    for (int64_t P = b; P < e; ++P) {
+      auto& v = nslots[(size_t)P];
+      v.reserve((size_t)nccols[(size_t)P]);
+      for (int64_t q = cptr[(size_t)P]; q < cptr[(size_t)P + 1]; ++q) {
+        const auto& sl = slots_[(size_t)kids[(size_t)q]];
+        v.insert(v.end(), sl.begin(), sl.end());
+      }
+    }
+  }, 256);
   lap("merge: clusters");
   // groups whose column layout changes get a new block (groups are independent:
   // classified in parallel, moved ones listed in ascending id)
@@ -1832,7 +1968,7 @@ void Factorizer<T>::merge() {
   }
   lap("merge: classify groups");
   // new blocks for moved groups (one buffer, zero-filled); the old layout is kept for the copies
-  std::vector<std::vector<int>> oldsup(moved.size()), oldoff(moved.size());
+  std::vector<SmallInts> oldsup(moved.size()), oldoff(moved.size());
   std::vector<T*> oldptr(moved.size());
   std::vector<int> oldld(moved.size()), oldbuf(moved.size());
   parallel_for((int64_t)moved.size(), [&](int64_t b, int64_t e, int) {
@@ -1849,19 +1985,20 @@ void Factorizer<T>::merge() {
       for (int c : oldsup[i]) nsup.push_back(sc_->parent[(size_t)c]);
       std::sort(nsup.begin(), nsup.end());
       nsup.erase(std::unique(nsup.begin(), nsup.end()), nsup.end());
-      g.off.assign(nsup.size(), 0);
+      g.off.resize(nsup.size());
       int w = 0;
       for (size_t t = 0; t < nsup.size(); ++t) {
         g.off[t] = w;
         w += nccols[(size_t)nsup[t]];
       }
-      g.sup.swap(nsup);
+      g.sup.assign(nsup.data(), nsup.data() + nsup.size());
       g.width = w;
       g.ld = std::max(g.rows, 1);
       g.buf = -1;
       g.ptr = nullptr;
     }
   }, 4096);
+  lap("merge: new layouts");
   {
     size_t total = 0;
     for (int id : moved) total += (size_t)G_[(size_t)id].ld * G_[(size_t)id].width;
