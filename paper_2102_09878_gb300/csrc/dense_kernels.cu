@@ -140,6 +140,7 @@ template <>
 struct SqSum<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s = fma(x, x, s); }
+  __device__ __forceinline__ void merge(const SqSum& o) { s += o.s; }
   __device__ __forceinline__ void warp_total(double& hi, double& lo) {
     hi = warp_sum(s);
     lo = 0.0;
@@ -152,6 +153,11 @@ struct SqSum<float> {
     const DF p = df_sqr(x);
     const DF t = df_two_sum(s, p.hi);
     c += t.lo + p.lo;
+    s = t.hi;
+  }
+  __device__ __forceinline__ void merge(const SqSum& o) {
+    const DF t = df_two_sum(s, o.s);
+    c = (c + o.c) + t.lo;
     s = t.hi;
   }
   __device__ __forceinline__ void warp_total(float& hi, float& lo) {
@@ -179,6 +185,7 @@ template <typename T>
 struct HouseStep {
   T beta, tau, den;
   bool stop;
+  T bh, bl;  // |beta| in the arithmetic of the rank test (bl = 0 for FP64)
 };
 __device__ __forceinline__ HouseStep<double> house_step(double alpha, double sh, double, double eps, double& r11,
                                                         bool first) {
@@ -196,6 +203,8 @@ __device__ __forceinline__ HouseStep<double> house_step(double alpha, double sh,
   const double ab = fabs(h.beta);
   if (first) r11 = ab;
   h.stop = h.beta == 0.0 || ab < eps * r11;
+  h.bh = ab;
+  h.bl = 0.0;
   return h;
 }
 __device__ __forceinline__ HouseStep<float> house_step(float alpha, float sh, float sl, DF eps, DF& r11, bool first) {
@@ -216,6 +225,8 @@ __device__ __forceinline__ HouseStep<float> house_step(float alpha, float sh, fl
   }
   if (first) r11 = b;
   h.stop = (b.hi == 0.f) || df_less(b, df_mul(eps, r11));
+  h.bh = b.hi;
+  h.bl = b.lo;
   return h;
 }
 
@@ -797,9 +808,20 @@ __device__ __forceinline__ QrcpProp<T, N> warp_record(const T* X, int m, int ldx
   QrcpProp<T, N> r{v, j, T(0), T(0), T(0)};
   if (j == INT_MAX || i_next >= m) return r;
   const T* col = X + (int64_t)(j - j0) * ldx;
-  SqSum<T> acc;
-  for (int q = i_next + 1 + (int)(threadIdx.x & 31); q < m; q += 32) acc.add(col[q]);
-  acc.warp_total(r.sh, r.sl);
+  // four independent sums per lane (rows 128 apart), merged at the end
+  SqSum<T> a0, a1, a2, a3;
+  int q = i_next + 1 + (int)(threadIdx.x & 31);
+  for (; q + 96 < m; q += 128) {
+    a0.add(col[q]);
+    a1.add(col[q + 32]);
+    a2.add(col[q + 64]);
+    a3.add(col[q + 96]);
+  }
+  for (; q < m; q += 32) a0.add(col[q]);
+  a0.merge(a1);
+  a2.merge(a3);
+  a0.merge(a2);
+  a0.warp_total(r.sh, r.sl);
   r.alpha = col[i_next];
   return r;
 }
@@ -956,15 +978,16 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
     if (CS > 1) {
       if (threadIdx.x == 0) pub[par] = best;
       cl.sync();  // the CTAs' bests of step i visible cluster-wide; step i - 1 reads finished
-      N v = N(-1);
-      int j = INT_MAX;
-      if (lane < CS) {
-        const QrcpProp<T, N>* o = cl.map_shared_rank(&pub[par], lane);
-        v = o->v;
-        j = o->j;
-      }
+      // every CTA's whole record in one round of remote loads (lane q: CTA q),
+      // the winner's fields then shuffled from its lane
+      QrcpProp<T, N> o{N(-1), INT_MAX, T(0), T(0), T(0)};
+      if (lane < CS) o = *cl.map_shared_rank(&pub[par], lane);
+      N v = o.v;
+      int j = o.j;
       const int who = warp_argmax(v, j);
-      if (j != INT_MAX) best = *cl.map_shared_rank(&pub[par], who);
+      best.alpha = __shfl_sync(0xffffffffu, o.alpha, who);
+      best.sh = __shfl_sync(0xffffffffu, o.sh, who);
+      best.sl = __shfl_sync(0xffffffffu, o.sl, who);
       best.v = v;
       best.j = j;
       if (pend_p >= 0) {  // the previous pivot column: nobody reads it any more
@@ -988,8 +1011,9 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
     {  // the reflector by row: 0 above row i, 1 at row i, the scaled column below
       const T* Xo = owner == rank ? X : cl.map_shared_rank(X, owner);
       const T* src = Xo + (int64_t)(p - owner * nl) * ldx;
+      const T rden = den != T(0) ? T(1) / den : T(0);  // the reflector scaled by 1 / (alpha - beta)
       for (int r = rb + threadIdx.x; r < ldx; r += NT)
-        vb[r] = r < i ? T(0) : (r == i ? T(1) : (r < m && den != T(0) ? src[r] / den : T(0)));
+        vb[r] = r < i ? T(0) : (r == i ? T(1) : (r < m ? src[r] * rden : T(0)));
       if (threadIdx.x == 0) taus[i] = copysign(tau_t, beta_t);  // tau >= 0; the sign is that of R_ii
     }
     if (rank == owner && threadIdx.x == 0) {
@@ -1150,6 +1174,37 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
 // winner and copies the winner's reflector.  A CTA can only reach step i + 2,
 // which rewrites buffer (i & 1), after every CTA has arrived at step i + 1,
 // i.e. after every CTA has finished reading step i.
+// One CTA's proposal of a grid-mode step as it sits in global memory (the 32
+// bytes of a QrcpSlot): the squared partial norm and column of its best
+// column, that column's Householder data and rank decision, and |beta| in the
+// arithmetic of the rank test (double-float for FP32: R_11 at step 0).
+template <typename T>
+struct GridSlot;
+template <>
+struct GridSlot<double> {
+  double v, beta, tau;
+  int j, stop;
+  __device__ __forceinline__ void set_b(double, double) {}
+  __device__ __forceinline__ void load_b(const GridSlot*) {}
+  __device__ __forceinline__ double b_acc() const { return fabs(beta); }
+};
+template <>
+struct GridSlot<float> {
+  float v, beta, tau, bh, bl;
+  int j, stop, pad;
+  __device__ __forceinline__ void set_b(float h, float l) {
+    bh = h;
+    bl = l;
+  }
+  __device__ __forceinline__ void load_b(const GridSlot* s) {
+    bh = __ldcg(&s->bh);
+    bl = __ldcg(&s->bl);
+  }
+  __device__ __forceinline__ DF b_acc() const { return DF{bh, bl}; }
+};
+static_assert(sizeof(GridSlot<double>) == sizeof(QrcpSlot) && sizeof(GridSlot<float>) == sizeof(QrcpSlot),
+              "grid slots keep the QrcpSlot size");
+
 constexpr int kQrcpLateTag = 48;  // int of a matrix's tag area raised when a wait expired
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -1187,7 +1242,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
   const int nloc = j1 - j0;
   const int vstride = (m_max + 3) & ~1;
   int* tags = gd.tags;                        // arrival counters of the two buffers, 128 bytes apart
-  QrcpSlot* slots = gd.slots;                 // [2][G]
+  GridSlot<T>* slots = reinterpret_cast<GridSlot<T>*>(gd.slots);  // [2][G]
   T* vg = static_cast<T*>(gd.vg);             // [2][G][vstride]
   extern __shared__ __align__(16) unsigned char smraw[];
   using N = T;  // partial column norms and pivot proposals in the data's precision
@@ -1199,16 +1254,8 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
   T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // 2 x vstride
   T* taus = vbuf + 2 * vstride;
   T* X = SMEM ? taus + vstride : d.work + (size_t)j0 * m;  // the slab, or this CTA's columns of the work copy
-  __shared__ double s_beta;
-  __shared__ T s_tau;
-  __shared__ int s_stop, s_piv, s_nact, s_late;
-  __shared__ N red_v[kWarps];
-  __shared__ int red_i[kWarps];
-  __shared__ N cand_v2[2];
-  __shared__ double sp_beta[2];
-  __shared__ int cand_j2[2], sp_stop[2];
-  __shared__ T sp_tau[2], s_den;
-  __shared__ double red2[kWarps];
+  __shared__ int s_nact, s_late;
+  __shared__ QrcpProp<T, N> rec[kWarps];
   __shared__ T s_part[kWarps * KG];  // partial dot products (few-column apply)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
@@ -1238,114 +1285,89 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
     s_late = 0;
   }
   const int kmax = m < n ? m : n;
-  double r11 = 0.0;
+  // eps and |R_11| in the arithmetic of the rank test (FP64, or double-float for FP32 data)
+  using Acc = typename std::conditional<sizeof(T) == 8, double, DF>::type;
+  Acc eps_x, r11;
+  if constexpr (sizeof(T) == 8) {
+    eps_x = eps;
+    r11 = 0.0;
+  } else {
+    const float e_hi = (float)eps;
+    eps_x = DF{e_hi, (float)(eps - (double)e_hi)};
+    r11 = DF{0.f, 0.f};
+  }
   int k = 0;
   __syncthreads();
-  N wv = N(-1);
-  int wj = INT_MAX;
-  for (int c = warp + lane * kWarps; c < nloc; c += 32 * kWarps) {
-    const N v = nu[c];
-    if (v > wv || (v == wv && j0 + c < wj)) {
-      wv = v;
-      wj = j0 + c;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const N ov = __shfl_xor_sync(0xffffffffu, wv, o);
-    const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
-    if (ov > wv || (ov == wv && oj < wj)) {
-      wv = ov;
-      wj = oj;
-    }
+  {  // records for step 0: every warp over its columns c = warp + kWarps * (lane + 32 t)
+    N wv = N(-1);
+    int wj = INT_MAX;
+    for (int c = warp + lane * kWarps; c < nloc; c += 32 * kWarps)
+      if (prop_better(nu[c], j0 + c, wv, wj)) {
+        wv = nu[c];
+        wj = j0 + c;
+      }
+    warp_argmax(wv, wj);
+    const QrcpProp<T, N> r = warp_record<T, N>(X, m, m, j0, 0, wv, wj);
+    if (lane == 0) rec[warp] = r;
   }
   for (int i = 0; i < kmax; ++i) {
     const int par = i & 1;
     T* vb = vbuf + par * vstride;
     T* vmine = vg + ((size_t)par * G + rank) * vstride;
-    // (1) the CTA's best column
-    if (lane == 0) {
-      red_v[warp] = wv;
-      red_i[warp] = wj;
+    GridSlot<T>* myslot = slots + (size_t)par * G + rank;
+    __syncthreads();  // B1: the records of step i
+    // (1) the CTA's best column from the warps' records (every warp), its
+    // Householder data (every thread, the same arithmetic), its speculative
+    // reflector into vb and the CTA's global buffer, its slot
+    QrcpProp<T, N> best;
+    {
+      N v = lane < kWarps ? rec[lane].v : N(-1);
+      int j = lane < kWarps ? rec[lane].j : INT_MAX;
+      const int who = warp_argmax(v, j);
+      best = rec[who < kWarps ? who : 0];
+      best.v = v;
+      best.j = j;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      N v = red_v[0];
-      int j = red_i[0];
-      for (int w = 1; w < kWarps; ++w)
-        if (red_v[w] > v || (red_v[w] == v && red_i[w] < j)) {
-          v = red_v[w];
-          j = red_i[w];
-        }
-      cand_v2[par] = v;
-      cand_j2[par] = j;
-    }
-    __syncthreads();
-    const int jloc = cand_j2[par];
-    // (2) its reflector, rows i..m-1, into vb and the CTA's global slot
+    const int jloc = best.j;
     if (jloc != INT_MAX) {
+      Acc r11c = r11;  // at step 0 the winner's |R_11| is known only after the exchange
+      const HouseStep<T> hs = house_step(best.alpha, best.sh, best.sl, eps_x, r11c, i == 0);
       const T* col = X + (int64_t)(jloc - j0) * m;
-      double sq = 0.0;  // R_ii and the rank test in FP64 whatever the data precision
+      const T rden = hs.den != T(0) ? T(1) / hs.den : T(0);  // the reflector scaled by 1 / (alpha - beta)
       for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) {
-        const double v = (double)col[r];
-        sq += v * v;
-      }
-      sq = warp_sum(sq);
-      if (lane == 0) red2[warp] = sq;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double sig = 0.0;
-        for (int w = 0; w < kWarps; ++w) sig += red2[w];
-        const double alpha = (double)col[i];
-        double beta, tau;
-        if (sig == 0.0) {
-          beta = alpha;
-          tau = 0.0;
-        } else {
-          const double nrm = sqrt(alpha * alpha + sig);
-          beta = alpha >= 0.0 ? -nrm : nrm;
-          tau = (beta - alpha) / beta;
-        }
-        const double ab = fabs(beta);
-        const double r11_here = (i == 0) ? ab : r11;
-        const int stop = (beta == 0.0 || ab < eps * r11_here) ? 1 : 0;
-        sp_beta[par] = beta;
-        sp_tau[par] = (T)tau;
-        sp_stop[par] = stop;
-        s_den = (!stop && sig != 0.0) ? (T)(alpha - beta) : T(0);
-        QrcpSlot* sl = slots + (size_t)par * G + rank;
-        sl->v = cand_v2[par];
-        sl->beta = beta;
-        sl->tau = (double)(T)tau;
-        sl->j = jloc;
-        sl->stop = stop;
-      }
-      __syncthreads();
-      const T den = s_den;
-      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) {
-        const T x = den != T(0) ? col[r] / den : T(0);
+        const T x = col[r] * rden;
         vb[r - i] = x;
         vmine[r - i] = x;
       }
       if (threadIdx.x == 0) {
         vb[0] = T(1);
         vmine[0] = T(1);
+        GridSlot<T> sl;
+        sl.v = best.v;
+        sl.beta = hs.beta;
+        sl.tau = hs.tau;
+        sl.set_b(hs.bh, hs.bl);
+        sl.j = jloc;
+        sl.stop = hs.stop ? 1 : 0;
+        *myslot = sl;
       }
     } else if (threadIdx.x == 0) {
-      QrcpSlot* sl = slots + (size_t)par * G + rank;
-      sl->v = -1.0;
-      sl->beta = 0.0;
-      sl->tau = N(0);
-      sl->j = INT_MAX;
-      sl->stop = 1;
+      GridSlot<T> sl;
+      sl.v = N(-1);
+      sl.beta = T(0);
+      sl.tau = T(0);
+      sl.set_b(T(0), T(0));
+      sl.j = INT_MAX;
+      sl.stop = 1;
+      *myslot = sl;
     }
-    // (3) publish: the CTA barrier orders every thread's stores before thread 0's
+    // (2) publish: the CTA barrier orders every thread's stores before thread 0's
     // release increment of the step counter (cumulative at gpu scope); buffer
     // par counts G arrivals every second step
-    __syncthreads();
+    __syncthreads();  // B2
     if (threadIdx.x == 0) {
       add_release(tags + 32 * par, 1);
-      // (4) wait for every CTA of the matrix (bounded); the acquire load makes
+      // (3) wait for every CTA of the matrix (bounded); the acquire load makes
       // the step's slots and reflectors visible to the CTA after the barrier
       const int target = G * (i / 2 + 1) + missing;  // missing > 0 only in failure-path tests
       const long long t0 = clock64();
@@ -1357,7 +1379,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
         }
       }
     }
-    __syncthreads();
+    __syncthreads();  // B3
     if (s_late) {
       if (threadIdx.x == 0) {
         atomicExch(tags + kQrcpLateTag, 1);
@@ -1365,75 +1387,67 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
       }
       return;
     }
-    // (5) the winner (lowest column index on ties), read from L2
-    if (threadIdx.x < 32) {
+    // (4) every warp finds the winner (lowest column index on ties) in the
+    // slots, reads its Householder data and its share of the winner's reflector
+    int owner;
+    GridSlot<T> win;
+    {
       N v = N(-1);
-      int j = INT_MAX;
+      int j = INT_MAX, t_best = 0;
       for (int t = lane; t < G; t += 32) {
-        const QrcpSlot* sl = slots + (size_t)par * G + t;
-        const N tv = (N)__ldcg(&sl->v);
+        const GridSlot<T>* sl = slots + (size_t)par * G + t;
+        const N tv = __ldcg(&sl->v);
         const int tj = __ldcg(&sl->j);
-        if (tv > v || (tv == v && tj < j)) {
+        if (prop_better(tv, tj, v, j)) {
           v = tv;
           j = tj;
+          t_best = t;
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const N ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, j, o);
-        if (ov > v || (ov == v && oj < j)) {
-          v = ov;
-          j = oj;
-        }
-      }
-      if (lane == 0) s_piv = j;
+      const int who = warp_argmax(v, j);
+      owner = __shfl_sync(0xffffffffu, t_best, who);
+      if (j == INT_MAX) owner = -1;
     }
-    __syncthreads();
-    const int p = s_piv;
-    if (p == INT_MAX) break;  // no proposal (non-finite norms): every CTA sees the same p
-    const int owner = p / nl;
+    if (owner < 0) break;  // no proposal (non-finite norms): every CTA sees the same
+    {
+      const GridSlot<T>* sl = slots + (size_t)par * G + owner;
+      win.beta = __ldcg(&sl->beta);
+      win.tau = __ldcg(&sl->tau);
+      win.load_b(sl);
+      win.j = __ldcg(&sl->j);
+      win.stop = __ldcg(&sl->stop);
+    }
+    if (i == 0) r11 = win.b_acc();
+    if (win.stop) break;  // rank reached: the same decision everywhere
+    const int p = win.j;
     if (rank != owner) {
       const T* vo = vg + ((size_t)par * G + owner) * vstride;
       for (int r = threadIdx.x; r < m - i; r += kThreads) vb[r] = __ldcg(vo + r);
-      if (threadIdx.x == 0) {
-        const QrcpSlot* sl = slots + (size_t)par * G + owner;
-        s_tau = (T)__ldcg(&sl->tau);
-        s_beta = __ldcg(&sl->beta);
-        s_stop = __ldcg(&sl->stop);
-      }
-    } else if (threadIdx.x == 0) {
-      s_tau = sp_tau[par];
-      s_beta = sp_beta[par];
-      s_stop = sp_stop[par];
     }
-    __syncthreads();
-    if (i == 0) r11 = fabs(s_beta);
-    if (s_stop) break;
-    const T tau = s_tau;
-    if (threadIdx.x == 0) taus[i] = copysign(tau, (T)s_beta);  // tau >= 0; the sign is that of R_ii
-    if (rank == owner) {
+    const T tau = win.tau;
+    if (threadIdx.x == 0) taus[i] = copysign(tau, win.beta);  // tau >= 0; the sign is that of R_ii
+    if (rank == owner && threadIdx.x == 0) {
       const int pl = p - j0;
-      T* col = X + (int64_t)pl * m;
-      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) col[r] = vb[r - i];
-      if (threadIdx.x == 0) {
-        col[i] = (T)s_beta;
-        const int q = pos[pl], last = act[s_nact - 1];
-        step_of[pl] = i;
-        act[q] = last;
-        pos[last] = q;
-        s_nact = s_nact - 1;
-      }
+      const int q = pos[pl], last = act[s_nact - 1];
+      step_of[pl] = i;
+      act[q] = last;
+      pos[last] = q;
+      s_nact = s_nact - 1;
     }
-    __syncthreads();
+    __syncthreads();  // B4: vb complete, act[] updated
+    if (rank == owner) {  // the pivot column (out of act[]: no warp updates it)
+      T* col = X + (int64_t)(p - j0) * m;
+      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) col[r] = vb[r - i];
+      if (threadIdx.x == 0) col[i] = win.beta;
+    }
     // (6) apply H_i to the CTA's unpivoted columns.  Many columns: warps take
     // groups of KG columns as in the cluster kernel.  Few columns (at most four
     // groups): RS warps share a group, each over every RS-th 32-row block; the
     // partial dot products meet in shared memory, every warp of the group forms
     // the same w_j (same summation order) and updates its rows, and after a
     // barrier the group's first warp updates row i, the norms and the proposal.
-    wv = N(-1);
-    wj = INT_MAX;
+    N wv = N(-1);
+    int wj = INT_MAX;
     const int nact = s_nact;
     const int jl = butterfly_col<KG>(lane);
     const bool lead = lane == butterfly_lane<KG>(jl);
@@ -1590,16 +1604,10 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
         }
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const N ov = __shfl_xor_sync(0xffffffffu, wv, o);
-      const int oj = __shfl_xor_sync(0xffffffffu, wj, o);
-      if (ov > wv || (ov == wv && oj < wj)) {
-        wv = ov;
-        wj = oj;
-      }
-    }
-    __syncthreads();  // every warp is done with act[] before the next pivot edits it
+    // the warp's record for step i + 1 (every warp is past B4: rec[] of step i is read)
+    warp_argmax(wv, wj);
+    const QrcpProp<T, N> r = warp_record<T, N>(X, m, m, j0, i + 1, wv, wj);
+    if (lane == 0) rec[warp] = r;
     k = i + 1;
   }
   __syncthreads();
