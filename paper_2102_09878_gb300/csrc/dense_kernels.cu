@@ -800,32 +800,6 @@ __device__ __forceinline__ int warp_argmax(N& v, int& j) {
   return who;
 }
 
-// The warp's record for step i_next: best column (v, j) of the warp (every lane
-// holds it), the sum of squares over rows i_next+1..m-1 of that column and its
-// row i_next.  Valid in every lane.
-template <typename T, typename N>
-__device__ __forceinline__ QrcpProp<T, N> warp_record(const T* X, int m, int ldx, int j0, int i_next, N v, int j) {
-  QrcpProp<T, N> r{v, j, T(0), T(0), T(0)};
-  if (j == INT_MAX || i_next >= m) return r;
-  const T* col = X + (int64_t)(j - j0) * ldx;
-  // four independent sums per lane (rows 128 apart), merged at the end
-  SqSum<T> a0, a1, a2, a3;
-  int q = i_next + 1 + (int)(threadIdx.x & 31);
-  for (; q + 96 < m; q += 128) {
-    a0.add(col[q]);
-    a1.add(col[q + 32]);
-    a2.add(col[q + 64]);
-    a3.add(col[q + 96]);
-  }
-  for (; q < m; q += 32) a0.add(col[q]);
-  a0.merge(a1);
-  a2.merge(a3);
-  a0.merge(a2);
-  a0.warp_total(r.sh, r.sl);
-  r.alpha = col[i_next];
-  return r;
-}
-
 // 16-byte shared-memory vectors: four FP32 or two FP64 consecutive rows
 template <typename T>
 __device__ __forceinline__ void ld16(const T* p, T (&a)[16 / sizeof(T)]);
@@ -860,20 +834,23 @@ __device__ __forceinline__ void st16<double>(double* p, const double (&a)[2]) {
 // column slab [r*nl, (r+1)*nl) (nl = ceil(n/CS)) in its shared memory, columns
 // of ldx = m rounded up to four rows (zero below m).  Columns never move.  One
 // pivot step is
-//   B1  every warp has left, from its share of the previous update, the record
-//       of its best column (partial norm, index, FP64-accurate sum of squares
-//       below the next diagonal entry, that entry); CTA barrier;
-//   every warp reduces the CTA's records with shuffles (same result in every
-//       warp); with CS > 1 the CTA's best is published and, after one cluster
-//       barrier, every warp reduces the CS published records the same way;
-//   R_ii = beta and tau follow in FP64 from the winner's record alone, the
-//       rank test |R_ii| >= eps |R_11| stops the loop uniformly;
+//   B1  every warp has left, from its share of the previous update, its best
+//       column (partial norm, index); CTA barrier; every thread reduces them to
+//       the CTA's best, all threads sum the squares below the next diagonal
+//       entry of that column (FP64-accurate), B1b combines the warps' parts in
+//       a fixed order: the CTA's record (norm, index, sum, diagonal entry);
+//   with CS > 1 each CTA pushes its record into every CTA's shared memory and,
+//       after one cluster barrier, every warp reduces the CS records the same
+//       way (local reads only);
+//   R_ii = beta and tau follow from the winner's record alone (FP64, or
+//       double-float for FP32 data), the rank test |R_ii| >= eps |R_11| stops
+//       the loop uniformly;
 //   every thread scales its rows of the winner's column, read from the owner's
 //       slab (distributed shared memory), into the local reflector buffer, which
 //       is indexed by row (zero above row i, one at row i);
 //   B2  CTA barrier; the update x_j <- x_j - tau (v^T x_j) v of the unpivoted
 //       columns (compact list act[]) in 16-byte row vectors with the downdate of
-//       their partial norms, and each warp's record for the next step.
+//       their partial norms, and each warp's best column for the next step.
 // The owner writes beta and the reflector into the pivot column once no CTA
 // can still read it: at once when CS = 1, otherwise after the next cluster
 // barrier (double-buffered records and reflector buffers keep every read of
@@ -903,8 +880,10 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
   T* vbuf = reinterpret_cast<T*>(smraw + (((size_t)nl_max * 28 + 15) / 16) * 16);  // 2 x vstride
   T* taus = vbuf + 2 * vstride;                                                    // vstride
   T* X = taus + vstride;                                                           // ldx x nloc slab
-  __shared__ QrcpProp<T, N> rec[NW];  // per-warp records of the coming step
-  __shared__ QrcpProp<T, N> pub[2];   // the CTA's best, read by the cluster (by step parity)
+  __shared__ N wb_v[NW];  // every warp's best (v, j) after an update
+  __shared__ int wb_j[NW];
+  __shared__ T red_h[NW], red_l[NW];        // partial sums of squares of the CTA's best column
+  __shared__ QrcpProp<T, N> pubs[2][16];  // every CTA's best of the step, pushed here by its owner (by parity)
   __shared__ int s_nact;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t e = threadIdx.x; e < (int64_t)ldx * nloc; e += NT) {
@@ -942,8 +921,10 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
         wj = j0 + c;
       }
     warp_argmax(wv, wj);
-    const QrcpProp<T, N> r = warp_record<T, N>(X, m, ldx, j0, 0, wv, wj);
-    if (lane == 0) rec[warp] = r;
+    if (lane == 0) {
+      wb_v[warp] = wv;
+      wb_j[warp] = wj;
+    }
   }
   // eps and |R_11| in the arithmetic of the rank test (FP64, or double-float for FP32 data)
   using Acc = typename std::conditional<sizeof(T) == 8, double, DF>::type;
@@ -964,24 +945,41 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
   for (int i = 0; i < kmax; ++i) {
     const int par = i & 1;
     T* vb = vbuf + par * vstride;
-    __syncthreads();  // B1: the records of step i
-    // the CTA's best, reduced in every warp
-    QrcpProp<T, N> best;
-    {
-      N v = lane < NW ? rec[lane].v : N(-1);
-      int j = lane < NW ? rec[lane].j : INT_MAX;
-      const int who = warp_argmax(v, j);
-      best = rec[who < NW ? who : 0];
-      best.v = v;
-      best.j = j;
+    __syncthreads();  // B1: the warps' proposals of step i
+    // the CTA's best column (every thread reduces the warps' proposals) and the
+    // sum of squares below row i of that column, by all threads
+    QrcpProp<T, N> best{N(-1), INT_MAX, T(0), T(0), T(0)};
+    for (int w = 0; w < NW; ++w)
+      if (prop_better(wb_v[w], wb_j[w], best.v, best.j)) {
+        best.v = wb_v[w];
+        best.j = wb_j[w];
+      }
+    if (best.j != INT_MAX) {
+      const T* col = X + (int64_t)(best.j - j0) * ldx;
+      SqSum<T> acc;
+      for (int r = i + 1 + threadIdx.x; r < m; r += NT) acc.add(col[r]);
+      T h, l;
+      acc.warp_total(h, l);
+      if (lane == 0) {
+        red_h[warp] = h;
+        red_l[warp] = l;
+      }
+    }
+    __syncthreads();  // B1b
+    if (best.j != INT_MAX) {
+      T h = red_h[0], l = red_l[0];
+      for (int w = 1; w < NW; ++w) sq_combine(h, l, red_h[w], red_l[w]);
+      best.sh = h;
+      best.sl = l;
+      best.alpha = X[i + (int64_t)(best.j - j0) * ldx];
     }
     if (CS > 1) {
-      if (threadIdx.x == 0) pub[par] = best;
+      // the CTA's best pushed into every CTA's shared memory (lane q: CTA q);
+      // after the cluster barrier all bests of the step are local
+      if (warp == 0 && lane < CS) *cl.map_shared_rank(&pubs[par][rank], lane) = best;
       cl.sync();  // the CTAs' bests of step i visible cluster-wide; step i - 1 reads finished
-      // every CTA's whole record in one round of remote loads (lane q: CTA q),
-      // the winner's fields then shuffled from its lane
       QrcpProp<T, N> o{N(-1), INT_MAX, T(0), T(0), T(0)};
-      if (lane < CS) o = *cl.map_shared_rank(&pub[par], lane);
+      if (lane < CS) o = pubs[par][lane];
       N v = o.v;
       int j = o.j;
       const int who = warp_argmax(v, j);
@@ -1000,20 +998,34 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
     }
     const int p = best.j;
     if (p == INT_MAX) break;  // no proposal (non-finite norms): the same p everywhere
+    const int owner = p / nl;
+    const int rb = i & ~(VW - 1);  // first row of the vectors the update touches
+    const T* Xo = owner == rank ? X : cl.map_shared_rank(X, owner);
+    const T* src = Xo + (int64_t)(p - owner * nl) * ldx;
+    // this thread's first kPre rows of the winner's column, loaded before the
+    // Householder arithmetic so that the (remote) loads overlap it
+    constexpr int kPre = 8;
+    T pre[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+      const int r = rb + (int)threadIdx.x + q * NT;
+      pre[q] = (r > i && r < m) ? src[r] : T(0);
+    }
     // R_ii, tau and the rank test, the same arithmetic in every thread
     const HouseStep<T> hs = house_step(best.alpha, best.sh, best.sl, eps_x, r11, i == 0);
     if (hs.stop) break;  // rank reached: the same decision everywhere
     const T den = hs.den;
     const T tau_t = hs.tau;
     const T beta_t = hs.beta;
-    const int owner = p / nl;
-    const int rb = i & ~(VW - 1);  // first row of the vectors the update touches
     {  // the reflector by row: 0 above row i, 1 at row i, the scaled column below
-      const T* Xo = owner == rank ? X : cl.map_shared_rank(X, owner);
-      const T* src = Xo + (int64_t)(p - owner * nl) * ldx;
       const T rden = den != T(0) ? T(1) / den : T(0);  // the reflector scaled by 1 / (alpha - beta)
-      for (int r = rb + threadIdx.x; r < ldx; r += NT)
-        vb[r] = r < i ? T(0) : (r == i ? T(1) : (r < m ? src[r] * rden : T(0)));
+#pragma unroll
+      for (int q = 0; q < kPre; ++q) {
+        const int r = rb + (int)threadIdx.x + q * NT;
+        if (r < ldx) vb[r] = r < i ? T(0) : (r == i ? T(1) : pre[q] * rden);
+      }
+      for (int r = rb + (int)threadIdx.x + kPre * NT; r < ldx; r += NT)
+        vb[r] = r < m ? src[r] * rden : T(0);
       if (threadIdx.x == 0) taus[i] = copysign(tau_t, beta_t);  // tau >= 0; the sign is that of R_ii
     }
     if (rank == owner && threadIdx.x == 0) {
@@ -1121,10 +1133,12 @@ __global__ void __launch_bounds__(NT, 1) qrcp_slab_kernel(const QrcpDesc<T>* des
         }
       }
     }
-    // the warp's record for step i + 1 (its columns are all updated: __syncwarp above)
+    // the warp's proposal for step i + 1 (its columns are all updated: __syncwarp above)
     warp_argmax(wv, wj);
-    const QrcpProp<T, N> r = warp_record<T, N>(X, m, ldx, j0, i + 1, wv, wj);
-    if (lane == 0) rec[warp] = r;
+    if (lane == 0) {
+      wb_v[warp] = wv;
+      wb_j[warp] = wj;
+    }
     k = i + 1;
   }
   if (CS > 1) {
@@ -1255,7 +1269,10 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
   T* taus = vbuf + 2 * vstride;
   T* X = SMEM ? taus + vstride : d.work + (size_t)j0 * m;  // the slab, or this CTA's columns of the work copy
   __shared__ int s_nact, s_late;
-  __shared__ QrcpProp<T, N> rec[kWarps];
+  __shared__ N wb_v[kWarps];             // every warp's best (v, j) after an update
+  __shared__ int wb_j[kWarps];
+  __shared__ T red_h[kWarps], red_l[kWarps];  // partial sums of squares of the CTA's best column
+  __shared__ GridSlot<T> wslot[kWarps];  // best slot among each warp's 32 (winner search)
   __shared__ T s_part[kWarps * KG];  // partial dot products (few-column apply)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
@@ -1298,7 +1315,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
   }
   int k = 0;
   __syncthreads();
-  {  // records for step 0: every warp over its columns c = warp + kWarps * (lane + 32 t)
+  {  // proposals for step 0: every warp over its columns c = warp + kWarps * (lane + 32 t)
     N wv = N(-1);
     int wj = INT_MAX;
     for (int c = warp + lane * kWarps; c < nloc; c += 32 * kWarps)
@@ -1307,26 +1324,45 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
         wj = j0 + c;
       }
     warp_argmax(wv, wj);
-    const QrcpProp<T, N> r = warp_record<T, N>(X, m, m, j0, 0, wv, wj);
-    if (lane == 0) rec[warp] = r;
+    if (lane == 0) {
+      wb_v[warp] = wv;
+      wb_j[warp] = wj;
+    }
   }
   for (int i = 0; i < kmax; ++i) {
     const int par = i & 1;
     T* vb = vbuf + par * vstride;
     T* vmine = vg + ((size_t)par * G + rank) * vstride;
     GridSlot<T>* myslot = slots + (size_t)par * G + rank;
-    __syncthreads();  // B1: the records of step i
-    // (1) the CTA's best column from the warps' records (every warp), its
+    __syncthreads();  // B1: the warps' proposals of step i
+    // (1) the CTA's best column (every thread reduces the warps' proposals),
+    // the sum of squares below row i of that column by all threads, then its
     // Householder data (every thread, the same arithmetic), its speculative
     // reflector into vb and the CTA's global buffer, its slot
-    QrcpProp<T, N> best;
-    {
-      N v = lane < kWarps ? rec[lane].v : N(-1);
-      int j = lane < kWarps ? rec[lane].j : INT_MAX;
-      const int who = warp_argmax(v, j);
-      best = rec[who < kWarps ? who : 0];
-      best.v = v;
-      best.j = j;
+    QrcpProp<T, N> best{N(-1), INT_MAX, T(0), T(0), T(0)};
+    for (int w = 0; w < kWarps; ++w)
+      if (prop_better(wb_v[w], wb_j[w], best.v, best.j)) {
+        best.v = wb_v[w];
+        best.j = wb_j[w];
+      }
+    if (best.j != INT_MAX) {
+      const T* col = X + (int64_t)(best.j - j0) * m;
+      SqSum<T> acc;
+      for (int r = i + 1 + threadIdx.x; r < m; r += kThreads) acc.add(col[r]);
+      T h, l;
+      acc.warp_total(h, l);
+      if (lane == 0) {
+        red_h[warp] = h;
+        red_l[warp] = l;
+      }
+    }
+    __syncthreads();  // B1b
+    if (best.j != INT_MAX) {
+      T h = red_h[0], l = red_l[0];
+      for (int w = 1; w < kWarps; ++w) sq_combine(h, l, red_h[w], red_l[w]);
+      best.sh = h;
+      best.sl = l;
+      best.alpha = X[i + (int64_t)(best.j - j0) * m];
     }
     const int jloc = best.j;
     if (jloc != INT_MAX) {
@@ -1387,36 +1423,38 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
       }
       return;
     }
-    // (4) every warp finds the winner (lowest column index on ties) in the
-    // slots, reads its Householder data and its share of the winner's reflector
-    int owner;
-    GridSlot<T> win;
-    {
-      N v = N(-1);
-      int j = INT_MAX, t_best = 0;
-      for (int t = lane; t < G; t += 32) {
+    // (4) the winner (lowest column index on ties): warp w loads slots
+    // 32 w .. 32 w + 31 (one per lane, all in one round), keeps its best whole
+    // slot; after a barrier every thread reduces those
+    const int nsw = (G + 31) >> 5;
+    if (warp < nsw) {
+      const int t = (warp << 5) + lane;
+      GridSlot<T> mine;
+      mine.v = N(-1);
+      mine.j = INT_MAX;
+      if (t < G) {
         const GridSlot<T>* sl = slots + (size_t)par * G + t;
-        const N tv = __ldcg(&sl->v);
-        const int tj = __ldcg(&sl->j);
-        if (prop_better(tv, tj, v, j)) {
-          v = tv;
-          j = tj;
-          t_best = t;
-        }
+        mine.v = __ldcg(&sl->v);
+        mine.j = __ldcg(&sl->j);
+        mine.beta = __ldcg(&sl->beta);
+        mine.tau = __ldcg(&sl->tau);
+        mine.stop = __ldcg(&sl->stop);
+        mine.load_b(sl);
       }
+      N v = mine.v;
+      int j = mine.j;
       const int who = warp_argmax(v, j);
-      owner = __shfl_sync(0xffffffffu, t_best, who);
-      if (j == INT_MAX) owner = -1;
+      if (lane == who) wslot[warp] = mine;
     }
+    __syncthreads();  // B3b
+    int owner = -1;
+    GridSlot<T> win;
+    win.v = N(-1);
+    win.j = INT_MAX;
+    for (int w = 0; w < nsw; ++w)
+      if (prop_better(wslot[w].v, wslot[w].j, win.v, win.j)) win = wslot[w];
+    if (win.j != INT_MAX) owner = win.j / nl;  // CTA t holds columns [t nl, (t + 1) nl)
     if (owner < 0) break;  // no proposal (non-finite norms): every CTA sees the same
-    {
-      const GridSlot<T>* sl = slots + (size_t)par * G + owner;
-      win.beta = __ldcg(&sl->beta);
-      win.tau = __ldcg(&sl->tau);
-      win.load_b(sl);
-      win.j = __ldcg(&sl->j);
-      win.stop = __ldcg(&sl->stop);
-    }
     if (i == 0) r11 = win.b_acc();
     if (win.stop) break;  // rank reached: the same decision everywhere
     const int p = win.j;
@@ -1455,7 +1493,41 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
     int RS = 1;
     if (ngrp > 0)
       while (RS * 2 * ngrp <= kWarps) RS *= 2;
-    if (RS == 1) {
+    if (nact <= 2 * kWarps) {
+      // at most two columns per warp: warp w updates columns act[w] and
+      // act[w + kWarps] alone (lanes over rows, no CTA barrier), downdates
+      // their norms and proposes the better one
+      for (int q = warp; q < nact; q += kWarps) {
+        const int cme = act[q];
+        T* col = X + (int64_t)cme * m;
+        T acc = T(0);
+        if (tau != T(0))
+          for (int r = i + 1 + lane; r < m; r += 32) acc += vb[r - i] * col[r];
+        acc = warp_sum(acc);
+        const T xi = col[i];
+        const T w = tau * (xi + acc);
+        const N xnew = (N)(xi - w);
+        if (tau != T(0))
+          for (int r = i + 1 + lane; r < m; r += 32) col[r] -= w * vb[r - i];
+        __syncwarp();
+        if (lane == 0) col[i] = (T)xnew;
+        N v = nu[cme] - xnew * xnew;
+        if (v < recompute_frac<N>() * nuref[cme]) {  // the same decision in every lane
+          N sq = N(0);
+          for (int r = i + 1 + lane; r < m; r += 32) {
+            const N y = (N)col[r];
+            sq += y * y;
+          }
+          v = warp_sum(sq);
+          if (lane == 0) nuref[cme] = v;
+        }
+        if (lane == 0) nu[cme] = v;
+        if (prop_better(v, j0 + cme, wv, wj)) {
+          wv = v;
+          wj = j0 + cme;
+        }
+      }
+    } else if (RS == 1) {
       for (int g0 = warp * KG; g0 < nact; g0 += kWarps * KG) {
         const int ng = min(KG, nact - g0);
         T* cols[KG];
@@ -1604,10 +1676,12 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
         }
       }
     }
-    // the warp's record for step i + 1 (every warp is past B4: rec[] of step i is read)
+    // the warp's proposal for step i + 1 (every thread is past B1b: wb_* of step i are read)
     warp_argmax(wv, wj);
-    const QrcpProp<T, N> r = warp_record<T, N>(X, m, m, j0, i + 1, wv, wj);
-    if (lane == 0) rec[warp] = r;
+    if (lane == 0) {
+      wb_v[warp] = wv;
+      wb_j[warp] = wj;
+    }
     k = i + 1;
   }
   __syncthreads();
@@ -2458,7 +2532,7 @@ int qrcp_grid_capacity(int smem_bytes, int elem) {
     cudaGetLastError();
     per = 0;
   }
-  return std::min(sms * per, kThreads);  // the tag wait takes one thread per CTA of a matrix
+  return std::min(sms * per, kThreads);  // the winner search takes one thread per CTA of a matrix
 }
 
 // Wait limit and missing arrivals of the CTA-group exchange (failure-path tests

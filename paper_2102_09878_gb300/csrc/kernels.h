@@ -387,8 +387,8 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
   // grid mode: each matrix takes the fewest CTAs whose slabs fit, matrices are
   // packed (taller first) into launches of at most grid_ctas CTAs whose common
   // footprint fits, then each launch spreads its spare CTAs over its widest
-  // members (one CTA at a time, while a member keeps >= 8 columns per CTA: one
-  // column group, whose rows the warps then share)
+  // members (one CTA at a time, until a member has at most 8 columns per CTA:
+  // one per warp)
   if (!gridm.empty()) {
     std::sort(gridm.begin(), gridm.end(), [&](int a, int b) {
       return ms[(size_t)a] != ms[(size_t)b] ? ms[(size_t)a] > ms[(size_t)b] : a < b;
@@ -428,7 +428,7 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
         grew = false;
         for (size_t q = 0; q < g.idx.size() && tot < grid_ctas; ++q) {
           const int n = ns[(size_t)g.idx[q]];
-          if (n / (g.ctas[q] + 1) < 8) continue;
+          if ((n + g.ctas[q] - 1) / g.ctas[q] <= 8) continue;
           ++g.ctas[q];
           ++tot;
           grew = true;
