@@ -443,12 +443,16 @@ __global__ void __launch_bounds__(kThreads) front_panel_kernel(const FrontDesc<T
 // Panel of the blocked QR on a thread-block cluster (tall panels): the rows
 // j0..m-1 of the panel columns are split over the CS CTAs of the cluster and
 // staged in shared memory (column-major, odd leading dimension).  Per column:
-// partial squared norms and the diagonal entry through distributed shared
-// memory (every CTA forms the same reflector), then partial products with the
-// remaining panel columns, summed in the same order by every CTA, and the
-// rank-1 update of the CTA's own rows -- two cluster barriers per column.  The
-// Gram matrix of the reflectors is reduced the same way and T (Q = I - V T V^T)
-// is formed warp-parallel by CTA 0.
+// every CTA pushes its partial sum of squares (FP64-accurate) and, for the
+// owner of the diagonal, the diagonal entry into every CTA's shared memory;
+// after a cluster barrier every thread forms the same reflector from them
+// (summed in rank order); the partial products with the remaining panel
+// columns are pushed the same way; after the second cluster barrier each CTA
+// applies the rank-1 update to its own rows (the reflector's scaling by
+// 1 / (alpha - beta) is folded into the reads and written back one column
+// later) -- two cluster barriers and no remote loads per column.  The Gram
+// matrix of the reflectors is reduced through distributed shared memory once
+// per panel and T (Q = I - V T V^T) is formed warp-parallel by CTA 0.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const FrontDesc<T>* descs, int j0, int nb,
                                                                            T* Tbuf, int per_max) {
@@ -467,11 +471,16 @@ __global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const 
   const int ld = per_max | 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* P = reinterpret_cast<T*>(smraw);  // nr x b, ld
-  __shared__ T sq_h, sq_l, alpha_s;  // this CTA's partial sum of squares (hi, lo) and the diagonal entry
-  __shared__ T dots[32], wsum[32], taus[32];
-  __shared__ T Gp[32 * 33];
-  __shared__ T s_beta, s_tau, s_den;
+  // exchange areas, written by the other CTAs of the cluster (index = source rank):
+  // partial sums of squares (hi, lo) with the diagonal entry, and partial products
+  // (pd shares its storage with the Gram partials Gp used after the last column)
+  __shared__ T px_h[16], px_l[16], px_a[16];
+  __shared__ T xbuf[32 * 33];
+  T(*pd)[32] = reinterpret_cast<T(*)[32]>(xbuf);  // [16][32]
+  T* Gp = xbuf;
+  __shared__ T taus[32];
   __shared__ T red_h[kWarps], red_l[kWarps];
+  __shared__ T wsum[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* X = d.ptr;
   for (int e = threadIdx.x; e < nr * b; e += kThreads) {
@@ -479,10 +488,16 @@ __global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const 
     P[r + jj * ld] = X[(r0 + r) + (int64_t)(j0 + jj) * d.ld];
   }
   __syncthreads();
+  T prev_rden = T(0);  // scale of the previous column's reflector, applied one step late
   for (int jj = 0; jj < b; ++jj) {
     const int j = j0 + jj;
-    const T* pc = P + jj * ld;
-    // (1) this CTA's sum of squares below the diagonal (FP64-accurate)
+    T* pc = P + jj * ld;
+    if (jj > 0 && prev_rden != T(1)) {  // the previous reflector: its rows below its diagonal scaled in place
+      T* pp = P + (jj - 1) * ld;
+      for (int r = max(r0, j) + threadIdx.x; r < r1; r += kThreads) pp[r - r0] *= prev_rden;
+    }
+    // (1) this CTA's sum of squares below the diagonal (FP64-accurate), pushed
+    // with the diagonal entry (owner) into every CTA of the cluster
     {
       SqSum<T> acc;
       for (int r = max(r0, j + 1) + threadIdx.x; r < r1; r += kThreads) acc.add(pc[r - r0]);
@@ -494,58 +509,39 @@ __global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const 
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
       T h = red_h[0], l = red_l[0];
       for (int w = 1; w < kWarps; ++w) sq_combine(h, l, red_h[w], red_l[w]);
-      sq_h = h;
-      sq_l = l;
-      if (j >= r0 && j < r1) alpha_s = pc[j - r0];
-    }
-    cl.sync();  // (A) partial norms and the diagonal entry visible
-    const int owner = (j - j0) / per;
-    if (warp == 0) {
-      // the CS partials read side by side (one lane each), combined in rank order
-      T h = T(0), l = T(0);
+      const T a = (j >= r0 && j < r1) ? pc[j - r0] : T(0);
       if (lane < CS) {
-        h = *cl.map_shared_rank(&sq_h, lane);
-        l = *cl.map_shared_rank(&sq_l, lane);
-      }
-      const T alpha = *cl.map_shared_rank(&alpha_s, owner);
-      T th = __shfl_sync(0xffffffffu, h, 0), tl = __shfl_sync(0xffffffffu, l, 0);
-      for (int q = 1; q < CS; ++q) sq_combine(th, tl, __shfl_sync(0xffffffffu, h, q), __shfl_sync(0xffffffffu, l, q));
-      if (lane == 0) {
-        const HouseStep<T> hs = front_house(alpha, th, tl);
-        s_beta = hs.beta;
-        s_tau = hs.tau;
-        s_den = hs.tau != T(0) ? hs.den : T(1);
-        taus[jj] = hs.tau;
+        *cl.map_shared_rank(&px_h[rank], lane) = h;
+        *cl.map_shared_rank(&px_l[rank], lane) = l;
+        *cl.map_shared_rank(&px_a[rank], lane) = a;
       }
     }
-    __syncthreads();
-    const T tau = s_tau, den = s_den;
-    T* pcw = P + jj * ld;
-    if (tau != T(0))
-      for (int r = max(r0, j + 1) + threadIdx.x; r < r1; r += kThreads) pcw[r - r0] = pcw[r - r0] / den;
-    __syncthreads();
-    if (rank == owner && threadIdx.x == 0) pcw[j - r0] = s_beta;
-    // partial products v . x_c for the panel columns c > jj (v_j = 1)
+    cl.sync();  // (A) every CTA's partial norm and the diagonal entry are local
+    const int owner = (j - j0) / per;
+    // every thread: the partials combined in rank order, the Householder data
+    T th = px_h[0], tl = px_l[0];
+    for (int q = 1; q < CS; ++q) sq_combine(th, tl, px_h[q], px_l[q]);
+    const HouseStep<T> hs = front_house(px_a[owner], th, tl);
+    const T tau = hs.tau;
+    const T rden = tau != T(0) ? T(1) / hs.den : T(1);  // v = x / (alpha - beta) below the diagonal
+    if (threadIdx.x == 0) taus[jj] = tau;
+    if (rank == owner && threadIdx.x == 0) pc[j - r0] = hs.beta;  // row j is read as v_j = 1 from here on
+    // partial products v . x_c for the panel columns c > jj (v_j = 1), pushed
+    // into every CTA of the cluster
     for (int c = jj + 1 + warp; c < b; c += kWarps) {
       const T* xc = P + c * ld;
       T acc = T(0);
-      for (int r = max(r0, j) + lane; r < r1; r += 32) acc += (r == j ? T(1) : pc[r - r0]) * xc[r - r0];
+      for (int r = max(r0, j) + lane; r < r1; r += 32) acc += (r == j ? T(1) : pc[r - r0] * rden) * xc[r - r0];
       acc = warp_sum(acc);
-      if (lane == 0) dots[c] = acc;
+      if (lane < CS) *cl.map_shared_rank(&pd[rank][c], lane) = acc;
     }
-    cl.sync();  // (B) partial products visible
+    cl.sync();  // (B) every CTA's partial products are local
     if (threadIdx.x > jj && threadIdx.x < b) {
-      // all CS loads issued before the sum (rank order)
-      T v[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = q < CS ? *cl.map_shared_rank(&dots[threadIdx.x], q) : T(0);
       T w = T(0);
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (q < CS) w += v[q];
+      for (int q = 0; q < CS; ++q) w += pd[q][threadIdx.x];  // rank order
       wsum[threadIdx.x] = tau * w;
     }
     __syncthreads();
@@ -556,13 +552,19 @@ __global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const 
         T* xc = P + c * ld;
         const T wc = wsum[c];
         for (int r = rbeg + lane; r < r1; r += 32) {
-          const T vr = r == j ? T(1) : pc[r - r0];
+          const T vr = r == j ? T(1) : pc[r - r0] * rden;
           xc[r - r0] -= wc * vr;
         }
       }
     }
+    prev_rden = rden;
     __syncthreads();
   }
+  if (prev_rden != T(1)) {  // the last reflector's rows below its diagonal
+    T* pp = P + (b - 1) * ld;
+    for (int r = max(r0, j0 + b) + threadIdx.x; r < r1; r += kThreads) pp[r - r0] *= prev_rden;
+  }
+  __syncthreads();
   // Gram of the unit-lower reflectors over this CTA's rows: G[l, i] = v_l . v_i, l < i
   for (int pq = warp; pq < b * b; pq += kWarps) {
     const int l = pq % b, i = pq / b;
@@ -1500,15 +1502,34 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
       for (int q = warp; q < nact; q += kWarps) {
         const int cme = act[q];
         T* col = X + (int64_t)cme * m;
-        T acc = T(0);
-        if (tau != T(0))
-          for (int r = i + 1 + lane; r < m; r += 32) acc += vb[r - i] * col[r];
-        acc = warp_sum(acc);
+        // four rows per lane per iteration (independent loads and sums): with
+        // one CTA per SM there are too few warps to hide shared-memory latency
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int r = i + 1 + lane;
+        if (tau != T(0)) {
+          for (; r + 96 < m; r += 128) {
+            a0 += vb[r - i] * col[r];
+            a1 += vb[r + 32 - i] * col[r + 32];
+            a2 += vb[r + 64 - i] * col[r + 64];
+            a3 += vb[r + 96 - i] * col[r + 96];
+          }
+          for (; r < m; r += 32) a0 += vb[r - i] * col[r];
+        }
+        const T acc = warp_sum((a0 + a1) + (a2 + a3));
         const T xi = col[i];
         const T w = tau * (xi + acc);
         const N xnew = (N)(xi - w);
-        if (tau != T(0))
-          for (int r = i + 1 + lane; r < m; r += 32) col[r] -= w * vb[r - i];
+        if (tau != T(0)) {
+          r = i + 1 + lane;
+          for (; r + 96 < m; r += 128) {
+            const T c0 = col[r], c1 = col[r + 32], c2 = col[r + 64], c3 = col[r + 96];
+            col[r] = c0 - w * vb[r - i];
+            col[r + 32] = c1 - w * vb[r + 32 - i];
+            col[r + 64] = c2 - w * vb[r + 64 - i];
+            col[r + 96] = c3 - w * vb[r + 96 - i];
+          }
+          for (; r < m; r += 32) col[r] -= w * vb[r - i];
+        }
         __syncwarp();
         if (lane == 0) col[i] = (T)xnew;
         N v = nu[cme] - xnew * xnew;
