@@ -25,6 +25,7 @@
 #ifndef SPAQR_H
 #define SPAQR_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -297,6 +298,17 @@ int spaqr_op_copy(const spaqr_handle* h, int64_t i, int32_t* slots, int32_t* nsl
 
 const char* spaqr_last_error(void);
 void spaqr_destroy(spaqr_handle* h);
+
+/* Device and pinned host blocks that the library freed (a factorization's
+ * working pools, upload arena, W store and operator) are kept in a
+ * process-wide cache and handed out again to later factorizations of the
+ * same or smaller sizes; the cache waits for the device before it takes a
+ * block back, as cudaFree does.  spaqr_release_cached_memory returns every
+ * cached block to the driver (after cudaDeviceSynchronize on the current
+ * device); spaqr_cached_bytes reports their total size.  Blocks owned by live
+ * handles are not affected.  Thread-safe; host only. */
+void spaqr_release_cached_memory(void);
+size_t spaqr_cached_bytes(void);
 
 /* ---------------------------------------------------------------- autotuning
  * spaqr_autotune: times, for every size class of the column-pivoted QRs

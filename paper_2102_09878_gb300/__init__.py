@@ -458,6 +458,16 @@ def _dense_qrcp(mats, eps, stream, route, f32):
     return rank, rows, Vout, Tout
 
 
+def release_cached_memory():
+    """Return the device and pinned host blocks the library keeps for reuse
+    (freed by earlier factorizations) to the driver; returns the bytes that
+    were cached."""
+    lib = capi.load()
+    n = int(lib.spaqr_cached_bytes())
+    lib.spaqr_release_cached_memory()
+    return n
+
+
 def dense_qrcp(mats, eps: float, stream=None, route: str = "cluster"):
     """Batched rank-revealing QR; returns (ranks, leading rows of Q^T A, V, taus).
     route: "cluster" (clusters of <= 16 CTAs), "auto" (as the factorization:

@@ -134,6 +134,8 @@ SIGNATURES = {
     "spaqr_op_copy": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spaqr_last_error": (C.c_char_p, []),
     "spaqr_destroy": (None, [C.c_void_p]),
+    "spaqr_release_cached_memory": (None, []),
+    "spaqr_cached_bytes": (C.c_size_t, []),
     "spaqr_dense_front_qr": (
         C.c_int,
         [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],

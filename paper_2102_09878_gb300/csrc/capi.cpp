@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <exception>
 #include <memory>
 #include <string>
 #include <thread>
@@ -56,39 +57,73 @@ struct Tick {
 
 // The pattern of A^T in CSR form (column pointers, row indices) and, per
 // transposed entry, its position in A; the entries of a column keep the row
-// order.  Threads own disjoint column ranges and each scans all of A, so the
-// result does not depend on the thread count.
+// order.  Serial: it runs on a helper thread beside the factorization.
 void transpose_pattern(const spaqr_csr& A, std::vector<int64_t>& trp, std::vector<int32_t>& tci,
                        std::vector<int64_t>& tperm) {
-  const int64_t n = A.n, m = A.m;
+  for (int64_t q = 0; q < A.nnz; ++q) trp[(size_t)A.colidx[q] + 1]++;
+  for (int64_t j = 0; j < A.n; ++j) trp[(size_t)j + 1] += trp[(size_t)j];
+  std::vector<int64_t> pos(trp.begin(), trp.end() - 1);
+  for (int64_t r = 0; r < A.m; ++r)
+    for (int64_t q = A.rowptr[r]; q < A.rowptr[r + 1]; ++q) {
+      const int64_t t = pos[(size_t)A.colidx[q]]++;
+      tci[(size_t)t] = (int32_t)r;
+      tperm[(size_t)t] = q;
+    }
+}
+
+// Column scaling D (Section 2.7): D_j = 1 / ||A e_j||, each squared norm summed
+// over the column's entries in row order.  Threads own disjoint column ranges
+// and each scans all of A, so the result does not depend on the thread count.
+void column_scaling(const spaqr_csr& A, std::vector<double>& D) {
+  const int64_t n = A.n;
+  D.assign((size_t)n, 0.0);
   const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(spaqr::ThreadPool::get().workers(), n / 4096));
-  auto range = [&](int p) { return std::make_pair(n * p / parts, n * (p + 1) / parts); };
   spaqr::parallel_for(parts, [&](int64_t b, int64_t e, int) {
     for (int64_t p = b; p < e; ++p) {
-      const auto [c0, c1] = range((int)p);
+      const int64_t c0 = n * p / parts, c1 = n * (p + 1) / parts;
       const uint32_t w = (uint32_t)(c1 - c0);
       for (int64_t q = 0; q < A.nnz; ++q) {
         const uint32_t d = (uint32_t)(A.colidx[q] - c0);
-        if (d < w) trp[(size_t)A.colidx[q] + 1]++;
+        if (d < w) D[(size_t)A.colidx[q]] += A.vals[q] * A.vals[q];
       }
     }
   }, 1);
-  for (int64_t j = 0; j < n; ++j) trp[(size_t)j + 1] += trp[(size_t)j];
-  spaqr::parallel_for(parts, [&](int64_t b, int64_t e, int) {
-    for (int64_t p = b; p < e; ++p) {
-      const auto [c0, c1] = range((int)p);
-      const uint32_t w = (uint32_t)(c1 - c0);
-      std::vector<int64_t> pos(trp.begin() + c0, trp.begin() + c1);
-      for (int64_t r = 0; r < m; ++r)
-        for (int64_t q = A.rowptr[r]; q < A.rowptr[r + 1]; ++q) {
-          const uint32_t d = (uint32_t)(A.colidx[q] - c0);
-          if (d >= w) continue;
-          const int64_t t = pos[d]++;
-          tci[(size_t)t] = (int32_t)r;
-          tperm[(size_t)t] = q;
-        }
-    }
-  }, 1);
+  for (int64_t j = 0; j < n; ++j) {
+    if (!(D[(size_t)j] > 0.0)) throw spaqr::Error(SPAQR_ERR_RANK_DEFICIENT, "zero column " + std::to_string(j));
+    D[(size_t)j] = 1.0 / std::sqrt(D[(size_t)j]);
+  }
+}
+
+// The scaled operator A~ = A D (FP64) and its transpose on the device, built
+// and uploaded on a stream of its own (the host copies are kept until the
+// uploads are done).
+void upload_operator(spaqr::Handle& h, const spaqr_csr& A, cudaStream_t st) {
+  std::vector<int64_t> trp((size_t)A.n + 1, 0);
+  std::vector<int32_t> tci((size_t)A.nnz);
+  std::vector<int64_t> tperm((size_t)A.nnz);
+  transpose_pattern(A, trp, tci, tperm);
+  std::vector<double> v((size_t)A.nnz), tv((size_t)A.nnz);
+  for (int64_t q = 0; q < A.nnz; ++q) v[(size_t)q] = A.vals[q] * h.D[(size_t)A.colidx[q]];
+  for (int64_t q = 0; q < A.nnz; ++q) tv[(size_t)q] = v[(size_t)tperm[(size_t)q]];
+  SPAQR_CUDA(spaqr::dmalloc(&h.d_rowptr, (size_t)(A.m + 1) * sizeof(int64_t)));
+  SPAQR_CUDA(spaqr::dmalloc(&h.d_colidx, (size_t)std::max<int64_t>(A.nnz, 1) * sizeof(int32_t)));
+  SPAQR_CUDA(spaqr::dmalloc(&h.d_vals, (size_t)std::max<int64_t>(A.nnz, 1) * sizeof(double)));
+  SPAQR_CUDA(spaqr::dmalloc(&h.d_trowptr, (size_t)(A.n + 1) * sizeof(int64_t)));
+  SPAQR_CUDA(spaqr::dmalloc(&h.d_tcolidx, (size_t)std::max<int64_t>(A.nnz, 1) * sizeof(int32_t)));
+  SPAQR_CUDA(spaqr::dmalloc(&h.d_tvals, (size_t)std::max<int64_t>(A.nnz, 1) * sizeof(double)));
+  SPAQR_CUDA(spaqr::dmalloc(&h.d_D, (size_t)A.n * sizeof(double)));
+  SPAQR_CUDA(spaqr::dmalloc(&h.d_tperm, (size_t)std::max<int64_t>(A.nnz, 1) * sizeof(int64_t)));
+  SPAQR_CUDA(cudaMemcpyAsync(h.d_rowptr, A.rowptr, (size_t)(A.m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  SPAQR_CUDA(cudaMemcpyAsync(h.d_trowptr, trp.data(), trp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  SPAQR_CUDA(cudaMemcpyAsync(h.d_D, h.D.data(), h.D.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (A.nnz) {
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_colidx, A.colidx, (size_t)A.nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_vals, v.data(), (size_t)A.nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_tcolidx, tci.data(), tci.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_tvals, tv.data(), tv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    SPAQR_CUDA(cudaMemcpyAsync(h.d_tperm, tperm.data(), tperm.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  }
+  SPAQR_CUDA(cudaStreamSynchronize(st));
 }
 }  // namespace
 
@@ -104,13 +139,14 @@ void Handle::wait_caller() {
 Handle::~Handle() {
   free_apply_plan(*this);
   if (ev) cudaEventDestroy(ev);
-  cudaFree(d_rowptr);
-  cudaFree(d_colidx);
-  cudaFree(d_vals);
-  cudaFree(d_trowptr);
-  cudaFree(d_tcolidx);
-  cudaFree(d_tvals);
-  cudaFree(d_D);
+  dfree(d_rowptr);
+  dfree(d_colidx);
+  dfree(d_vals);
+  dfree(d_trowptr);
+  dfree(d_tcolidx);
+  dfree(d_tvals);
+  dfree(d_D);
+  dfree(d_tperm);
   cudaFree(d_work);
   cudaFree(d_flag);
   if (own_stream && st) cudaStreamDestroy(st);
@@ -182,62 +218,40 @@ std::unique_ptr<spaqr::Handle> build_handle(const spaqr_csr* A, const spaqr::Ana
   h.depth = a.depth;
   h.t_analyze = a.seconds;
   Tick tick(h.opt.verbose);
-  // the pattern of A^T, then the column scaling D (Section 2.7): each column's
-  // squared norm summed over its entries in row order, columns in parallel
-  std::vector<int64_t> trp((size_t)A->n + 1, 0);
-  std::vector<int32_t> tci((size_t)A->nnz);
-  std::vector<int64_t> tperm((size_t)A->nnz);
-  transpose_pattern(*A, trp, tci, tperm);
-  h.D.resize((size_t)A->n);
-  std::vector<char> zero_col((size_t)A->n, 0);
-  spaqr::parallel_for(A->n, [&](int64_t b, int64_t e, int) {
-    for (int64_t j = b; j < e; ++j) {
-      double nrm = 0.0;
-      for (int64_t q = trp[(size_t)j]; q < trp[(size_t)j + 1]; ++q) {
-        const double x = A->vals[tperm[(size_t)q]];
-        nrm += x * x;
-      }
-      zero_col[(size_t)j] = !(nrm > 0.0);
-      h.D[(size_t)j] = zero_col[(size_t)j] ? 0.0 : 1.0 / std::sqrt(nrm);
+  column_scaling(*A, h.D);
+  tick("column scaling");
+  // the scaled operator and its transpose are built and uploaded by a helper
+  // thread on a stream of its own while this thread runs the factorization
+  int dev = 0;
+  SPAQR_CUDA(cudaGetDevice(&dev));
+  cudaStream_t up_st = nullptr;
+  SPAQR_CUDA(cudaStreamCreateWithFlags(&up_st, cudaStreamNonBlocking));
+  std::exception_ptr up_err;
+  std::thread up_thread([&] {
+    try {
+      SPAQR_CUDA(cudaSetDevice(dev));
+      upload_operator(h, *A, up_st);
+    } catch (...) {
+      up_err = std::current_exception();
     }
   });
-  for (int64_t j = 0; j < A->n; ++j)
-    if (zero_col[(size_t)j]) throw spaqr::Error(SPAQR_ERR_RANK_DEFICIENT, "zero column " + std::to_string(j));
-  tick("transpose + column scaling");
+  struct Finish {  // the helper joined and its stream released however this scope is left
+    std::thread& t;
+    cudaStream_t s;
+    ~Finish() {
+      if (t.joinable()) t.join();
+      if (s) cudaStreamDestroy(s);
+    }
+  } finish{up_thread, up_st};
   // Diag. comparator (Section 4): no factorization, W = I
   if (h.opt.mode != SPAQR_MODE_DIAG) spaqr::run_factor(h, *A, a);
   tick("factor");
-  // scaled operator A~ = A D and its transpose on the device (FP64)
-  std::vector<double> v((size_t)A->nnz);
-  spaqr::parallel_for(A->nnz, [&](int64_t b, int64_t e, int) {
-    for (int64_t q = b; q < e; ++q) v[(size_t)q] = A->vals[q] * h.D[(size_t)A->colidx[q]];
-  });
-  std::vector<double> tv((size_t)A->nnz);
-  spaqr::parallel_for(A->nnz, [&](int64_t b, int64_t e, int) {
-    for (int64_t q = b; q < e; ++q) tv[(size_t)q] = v[(size_t)tperm[(size_t)q]];
-  });
-  tick("scaled values");
-  SPAQR_CUDA(cudaMalloc(&h.d_rowptr, (size_t)(A->m + 1) * sizeof(int64_t)));
-  SPAQR_CUDA(cudaMalloc(&h.d_colidx, (size_t)A->nnz * sizeof(int32_t)));
-  SPAQR_CUDA(cudaMalloc(&h.d_vals, (size_t)A->nnz * sizeof(double)));
-  SPAQR_CUDA(cudaMalloc(&h.d_trowptr, (size_t)(A->n + 1) * sizeof(int64_t)));
-  SPAQR_CUDA(cudaMalloc(&h.d_tcolidx, (size_t)A->nnz * sizeof(int32_t)));
-  SPAQR_CUDA(cudaMalloc(&h.d_tvals, (size_t)A->nnz * sizeof(double)));
-  SPAQR_CUDA(cudaMalloc(&h.d_D, (size_t)A->n * sizeof(double)));
-  SPAQR_CUDA(cudaMalloc(&h.d_tperm, (size_t)std::max<int64_t>(A->nnz, 1) * sizeof(int64_t)));
-  SPAQR_CUDA(cudaMemcpyAsync(h.d_rowptr, A->rowptr, (size_t)(A->m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
-  SPAQR_CUDA(cudaMemcpyAsync(h.d_colidx, A->colidx, (size_t)A->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, h.st));
-  SPAQR_CUDA(cudaMemcpyAsync(h.d_vals, v.data(), (size_t)A->nnz * sizeof(double), cudaMemcpyHostToDevice, h.st));
-  SPAQR_CUDA(cudaMemcpyAsync(h.d_trowptr, trp.data(), trp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
-  SPAQR_CUDA(cudaMemcpyAsync(h.d_tcolidx, tci.data(), tci.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h.st));
-  SPAQR_CUDA(cudaMemcpyAsync(h.d_tvals, tv.data(), tv.size() * sizeof(double), cudaMemcpyHostToDevice, h.st));
-  SPAQR_CUDA(cudaMemcpyAsync(h.d_D, h.D.data(), h.D.size() * sizeof(double), cudaMemcpyHostToDevice, h.st));
-  if (A->nnz)
-    SPAQR_CUDA(cudaMemcpyAsync(h.d_tperm, tperm.data(), tperm.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h.st));
+  up_thread.join();
+  if (up_err) std::rethrow_exception(up_err);
+  tick("operator upload (wait)");
   h.rowptr.assign(A->rowptr, A->rowptr + A->m + 1);
   h.colidx.assign(A->colidx, A->colidx + A->nnz);
   if (A->match) h.match.assign(A->match, A->match + A->n);
-  tick("operator upload");
   spaqr::build_apply_plan(h);
   tick("apply plan");
   SPAQR_CUDA(cudaStreamSynchronize(h.st));
@@ -522,6 +536,10 @@ int spaqr_factor_batch(int count, const spaqr_csr* const* A, const spaqr_analysi
 }
 
 void spaqr_destroy(spaqr_handle* h) { delete h; }
+
+void spaqr_release_cached_memory(void) { spaqr::release_cached_memory(); }
+
+size_t spaqr_cached_bytes(void) { return spaqr::cached_bytes(); }
 
 int spaqr_solve(spaqr_handle* hh, const double* b, double* x, int on_device, spaqr_solve_info* info) {
   return solve_any(hh, b, x, on_device, info, false);

@@ -42,7 +42,7 @@ namespace spaqr {
 
 // ------------------------------------------------------------- DevicePool
 DevicePool::~DevicePool() {
-  for (auto& c : chunks_) cudaFree(c.base);
+  for (auto& c : chunks_) dfree(c.base);
 }
 
 void* DevicePool::alloc(size_t bytes) {
@@ -72,7 +72,7 @@ void* DevicePool::alloc(size_t bytes) {
       }
       const size_t csz = std::max(chunk_, sz);
       char* base = nullptr;
-      SPAQR_CUDA(cudaMalloc(&base, csz));
+      SPAQR_CUDA(dmalloc(&base, csz));
       chunks_.push_back(Chunk{base, csz, 0});
       reserved_ += csz;
       ch = &chunks_.back();
@@ -117,7 +117,7 @@ void DevicePool::release(void* p) {
 
 // ------------------------------------------------------------------ Arena
 Arena::~Arena() {
-  for (auto& c : chunks_) cudaFree(c.base);
+  for (auto& c : chunks_) dfree(c.base);
 }
 
 void* Arena::alloc(size_t bytes) {
@@ -125,7 +125,7 @@ void* Arena::alloc(size_t bytes) {
   if (chunks_.empty() || chunks_.back().used + need > chunks_.back().size) {
     const size_t csz = std::max(chunk_, need);
     char* base = nullptr;
-    SPAQR_CUDA(cudaMalloc(&base, csz));
+    SPAQR_CUDA(dmalloc(&base, csz));
     chunks_.push_back(Chunk{base, csz, 0});
   }
   Chunk& c = chunks_.back();
@@ -144,8 +144,8 @@ bool Arena::contains(const void* p, size_t bytes) const {
 
 // --------------------------------------------------------------- Uploader
 void Uploader::free_block(Block& b) {
-  if (b.host) cudaFreeHost(b.host);
-  if (b.dev) cudaFree(b.dev);
+  if (b.host) hfree(b.host);
+  if (b.dev) dfree(b.dev);
   b = Block();
 }
 
@@ -159,8 +159,8 @@ void Uploader::init(cudaStream_t st, size_t bytes) {
   if (cur_.cap < bytes) {
     free_block(cur_);
     cur_.cap = bytes;
-    SPAQR_CUDA(cudaMallocHost(&cur_.host, cur_.cap));
-    SPAQR_CUDA(cudaMalloc(&cur_.dev, cur_.cap));
+    SPAQR_CUDA(hmalloc(&cur_.host, cur_.cap));
+    SPAQR_CUDA(dmalloc(&cur_.dev, cur_.cap));
   }
   off_ = 0;
 }
@@ -178,8 +178,8 @@ void* Uploader::take(size_t bytes, const void* src) {
     retired_.push_back(cur_);
     cur_ = Block();
     cur_.cap = std::max(need, 2 * retired_.back().cap);
-    SPAQR_CUDA(cudaMallocHost(&cur_.host, cur_.cap));
-    SPAQR_CUDA(cudaMalloc(&cur_.dev, cur_.cap));
+    SPAQR_CUDA(hmalloc(&cur_.host, cur_.cap));
+    SPAQR_CUDA(dmalloc(&cur_.dev, cur_.cap));
     off_ = 0;
   }
   char* d = cur_.dev + off_;

@@ -192,6 +192,24 @@ struct Handle {
 // Message returned by spaqr_last_error() on this thread (capi.cpp).
 void set_last_error(const std::string& msg);
 
+// Process-wide block cache (memcache.cpp): cudaMalloc / cudaFree and
+// cudaMallocHost / cudaFreeHost with freed blocks kept for reuse (a free waits
+// for the device, as cudaFree does); release_cached_memory() hands them back.
+cudaError_t dmalloc(void** p, size_t bytes);
+void dfree(void* p);
+cudaError_t hmalloc(void** p, size_t bytes);
+void hfree(void* p);
+void release_cached_memory();
+size_t cached_bytes();
+template <typename X>
+cudaError_t dmalloc(X** p, size_t bytes) {
+  return dmalloc(reinterpret_cast<void**>(p), bytes);
+}
+template <typename X>
+cudaError_t hmalloc(X** p, size_t bytes) {
+  return hmalloc(reinterpret_cast<void**>(p), bytes);
+}
+
 // Runs the body of a C entry point and maps every host exception to a return
 // code, so that none crosses the extern "C" boundary: library errors keep
 // their code, a failed host allocation is SPAQR_ERR_OOM, anything else

@@ -690,12 +690,12 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
     noff[i] = idx.size();
     idx.insert(idx.end(), op.nslots.begin(), op.nslots.end());
   }
-  SPAQR_CUDA(cudaMalloc(&P.d_idx, std::max<size_t>(idx.size(), 1) * sizeof(int32_t)));
+  SPAQR_CUDA(dmalloc(&P.d_idx, std::max<size_t>(idx.size(), 1) * sizeof(int32_t)));
   SPAQR_CUDA(cudaMemcpy(P.d_idx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   size_t nrd = 0;
   for (size_t i = 0; i < nops; ++i)
     if (form[i] == 1 && h.ops[i].kind != 2) nrd += (size_t)h.ops[i].c;
-  SPAQR_CUDA(cudaMalloc(&P.d_rdiag, std::max<size_t>(nrd, 1) * sizeof(double)));
+  SPAQR_CUDA(dmalloc(&P.d_rdiag, std::max<size_t>(nrd, 1) * sizeof(double)));
 
   std::vector<SmallOp<TW>> small;
   std::vector<DenseOp<TW>> dense;
@@ -779,7 +779,7 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
   }
   auto upload = [](auto& vec, auto** dst) {
     using E = typename std::remove_reference<decltype(vec)>::type::value_type;
-    SPAQR_CUDA(cudaMalloc(reinterpret_cast<void**>(dst), std::max<size_t>(vec.size(), 1) * sizeof(E)));
+    SPAQR_CUDA(dmalloc(reinterpret_cast<void**>(dst), std::max<size_t>(vec.size(), 1) * sizeof(E)));
     if (!vec.empty())
       SPAQR_CUDA(cudaMemcpy(*dst, vec.data(), vec.size() * sizeof(E), cudaMemcpyHostToDevice));
   };
@@ -795,7 +795,7 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
   red.insert(red.end(), red_t.begin(), red_t.end());
   for (auto& sg : segs) sg.rt0 += rt_base;
   upload(red, &P.d_red);
-  SPAQR_CUDA(cudaMalloc(&P.d_dpart, std::max<size_t>(part_max, 1) * sizeof(TA)));
+  SPAQR_CUDA(dmalloc(&P.d_dpart, std::max<size_t>(part_max, 1) * sizeof(TA)));
   if (!small.empty()) {
     recip_diag_kernel<TW><<<(unsigned)((small.size() + kW - 1) / kW), kT, 0, h.st>>>(d_small, (int)small.size());
     SPAQR_CUDA(cudaGetLastError());
@@ -807,12 +807,12 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
     int2* d_items = nullptr;
     double* d_scr = nullptr;
     upload(form_items, &d_items);
-    SPAQR_CUDA(cudaMalloc(&d_scr, (size_t)grid * kW * cmax * sizeof(double)));
+    SPAQR_CUDA(dmalloc(&d_scr, (size_t)grid * kW * cmax * sizeof(double)));
     form_dense_kernel<TW><<<grid, kT, 0, h.st>>>(d_dense, d_items, nit, d_scr, cmax);
     SPAQR_CUDA(cudaGetLastError());
     SPAQR_CUDA(cudaStreamSynchronize(h.st));
-    cudaFree(d_items);
-    cudaFree(d_scr);
+    dfree(d_items);
+    dfree(d_scr);
   }
   SPAQR_CUDA(cudaStreamSynchronize(h.st));
   P.segs = segs;
@@ -828,9 +828,9 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
     std::vector<SegDev> sd;
     for (auto& g : segs) sd.push_back(SegDev{g.kind, g.small0, g.nsmall, g.tile0, g.ntile, g.rf0, g.nrf, g.rt0, g.nrt});
     upload(sd, &P.d_segs);
-    SPAQR_CUDA(cudaMalloc(&P.d_bar, 2 * sizeof(unsigned)));
+    SPAQR_CUDA(dmalloc(&P.d_bar, 2 * sizeof(unsigned)));
     SPAQR_CUDA(cudaMemset(P.d_bar, 0, 2 * sizeof(unsigned)));
-    SPAQR_CUDA(cudaMalloc(&P.d_err, sizeof(int)));
+    SPAQR_CUDA(dmalloc(&P.d_err, sizeof(int)));
     SPAQR_CUDA(cudaMemset(P.d_err, 0, sizeof(int)));
     P.psmem = std::max(kWarpSmem<TW>, (size_t)kStage * sizeof(TW));
     set_dyn_smem(apply_persistent_kernel<TW, TA>);
@@ -841,7 +841,7 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
     if (per > 0) {
       P.pgrid = sms * per;
       double* zt = nullptr;
-      bool ok = cudaMalloc(&zt, (size_t)std::max<int64_t>(h.n, 1) * sizeof(double)) == cudaSuccess;
+      bool ok = dmalloc(&zt, (size_t)std::max<int64_t>(h.n, 1) * sizeof(double)) == cudaSuccess;
       if (ok) ok = cudaMemsetAsync(zt, 0, (size_t)std::max<int64_t>(h.n, 1) * sizeof(double), h.st) == cudaSuccess;
       if (ok) {
         const cudaError_t e0 = launch_persistent<TW, TA>(h, zt, 0);
@@ -863,7 +863,7 @@ static void build_plan_t(Handle& h, ApplyPlan& P) {
       }
       int err = 0;
       if (ok) ok = cudaMemcpy(&err, P.d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && err == 0;
-      if (zt) cudaFree(zt);
+      if (zt) dfree(zt);
       if (!ok) {
         cudaGetLastError();
         P.pgrid = 0;  // per-segment launches
@@ -905,9 +905,9 @@ void build_apply_plan(Handle& h) {
   }
   const int64_t big = std::max(h.m, h.n);
   h.plan->part_n = blocks(big);
-  SPAQR_CUDA(cudaMalloc(&h.plan->d_scal, 8 * sizeof(double)));
+  SPAQR_CUDA(dmalloc(&h.plan->d_scal, 8 * sizeof(double)));
   SPAQR_CUDA(cudaMallocHost(&h.plan->h_res, sizeof(double)));
-  SPAQR_CUDA(cudaMalloc(&h.plan->d_part, (size_t)h.plan->part_n * sizeof(double)));
+  SPAQR_CUDA(dmalloc(&h.plan->d_part, (size_t)h.plan->part_n * sizeof(double)));
 }
 
 void free_apply_plan(Handle& h) {
@@ -918,18 +918,18 @@ void free_apply_plan(Handle& h) {
   if (h.plan->graph_pcg) cudaGraphExecDestroy(h.plan->graph_pcg);
   if (h.plan->graph_csne) cudaGraphExecDestroy(h.plan->graph_csne);
   if (h.plan->h_res) cudaFreeHost(h.plan->h_res);
-  cudaFree(h.plan->d_segs);
-  cudaFree(h.plan->d_bar);
-  cudaFree(h.plan->d_err);
-  cudaFree(h.plan->d_small);
-  cudaFree(h.plan->d_dense);
-  cudaFree(h.plan->d_idx);
-  cudaFree(h.plan->d_tiles);
-  cudaFree(h.plan->d_red);
-  cudaFree(h.plan->d_dpart);
-  cudaFree(h.plan->d_rdiag);
-  cudaFree(h.plan->d_scal);
-  cudaFree(h.plan->d_part);
+  dfree(h.plan->d_segs);
+  dfree(h.plan->d_bar);
+  dfree(h.plan->d_err);
+  dfree(h.plan->d_small);
+  dfree(h.plan->d_dense);
+  dfree(h.plan->d_idx);
+  dfree(h.plan->d_tiles);
+  dfree(h.plan->d_red);
+  dfree(h.plan->d_dpart);
+  dfree(h.plan->d_rdiag);
+  dfree(h.plan->d_scal);
+  dfree(h.plan->d_part);
   delete h.plan;
   h.plan = nullptr;
 }

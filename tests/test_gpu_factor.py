@@ -161,3 +161,34 @@ def test_step1_qr_route_matches_direct_route(dims, depth, law, eps, precision):
     for x in (xa, xb):
         assert np.linalg.norm(A.T @ (A @ x - prob.b)) / np.linalg.norm(A.T @ prob.b) < 1e-10
     assert abs(a.last_info["iters"] - b.last_info["iters"]) <= 1
+
+
+def test_block_cache_reuse_and_release():
+    """Freed working blocks are kept for the next factorization (the same
+    sizes come back), reuse changes no result, and release empties the cache."""
+    import gc
+
+    import paper_2102_09878_gb300 as sq
+
+    p = grid_problem(64, 64, 1, "u12", 3)
+    an = sq.Analysis(p.dims, 6)
+    s1 = sq.SpaQR(p, an, eps=1e-2, precision="mixed")
+    x1 = s1.solve(p.b)
+    ops1 = s1.ops()
+    del s1
+    gc.collect()
+    lib = sq.capi.load()
+    assert lib.spaqr_cached_bytes() > 0
+    s2 = sq.SpaQR(p, an, eps=1e-2, precision="mixed")
+    x2 = s2.solve(p.b)
+    ops2 = s2.ops()
+    assert len(ops1) == len(ops2)
+    for a, b in zip(ops1, ops2):
+        for key in ("R", "Rn", "V", "taus"):
+            if a.get(key) is not None:
+                np.testing.assert_allclose(a[key], b[key], rtol=1e-6, atol=1e-6 * np.abs(a[key]).max())
+    np.testing.assert_allclose(x1, x2, rtol=1e-8, atol=1e-8 * np.abs(x1).max())
+    del s2
+    gc.collect()
+    assert sq.release_cached_memory() > 0
+    assert lib.spaqr_cached_bytes() == 0
