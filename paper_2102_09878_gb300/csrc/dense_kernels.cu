@@ -2272,57 +2272,103 @@ __global__ void __launch_bounds__(kThreads) qrcp_warp_kernel(const QrcpDesc<T>* 
 }
 
 // ------------------------------------------------------ reflector applies
+// A warp applies the k reflectors to kReflVPW vectors at once (lanes over the
+// vector's entries): the vectors' dot products and warp sums are independent,
+// so their latencies overlap, and for row vectors (mode 0) the vectors are
+// neighbours in memory.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) refl_kernel(const ReflDesc<T>* descs, const int2* items) {
+  constexpr int VPW = kReflPerItem / kWarps;
   const int2 it = items[blockIdx.x];  // (descriptor, first vector)
   const ReflDesc<T> d = descs[it.x];
   const int k = *d.k;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int vec = it.y + warp;
-  if (vec >= d.nvec) return;
+  const int vec0 = it.y + warp * VPW;
+  if (vec0 >= d.nvec) return;
+  const int nv = min(VPW, d.nvec - vec0);
   const int len = d.len;
-  if (d.mode == 0) {
-    // row vector x (elements x[l] = ptr[vec + l*ld]) <- x^T H_1 ... H_k
-    T* x = d.ptr + vec;
-    if (k < len) {
-      for (int i = 0; i < k; ++i) {
-        const T* v = d.V + (int64_t)i * len;
-        T s = T(0);
-        for (int l = i + lane; l < len; l += 32) s += x[(int64_t)l * d.ld] * (l == i ? T(1) : v[l]);
-        s = warp_sum(s) * d.tau[i];
-        for (int l = i + lane; l < len; l += 32) x[(int64_t)l * d.ld] -= s * (l == i ? T(1) : v[l]);
-      }
-      for (int l = k + lane; l < len; l += 32) x[(int64_t)l * d.ld] = T(0);
+  if (k >= len) return;
+  // entry l of vector q
+  const int64_t sl = d.mode == 0 ? d.ld : 1, sq = d.mode == 0 ? 1 : d.ld;
+  T* x = d.ptr + (int64_t)vec0 * sq;
+  for (int i = 0; i < k; ++i) {
+    const T* v = d.V + (int64_t)i * len;
+    T s[VPW];
+#pragma unroll
+    for (int q = 0; q < VPW; ++q) s[q] = T(0);
+    for (int l = i + lane; l < len; l += 32) {
+      const T vl = l == i ? T(1) : v[l];
+#pragma unroll
+      for (int q = 0; q < VPW; ++q)
+        if (q < nv) s[q] += x[(int64_t)l * sl + q * sq] * vl;
     }
-  } else {
-    // column vector y (contiguous) <- H_k ... H_1 y
-    T* y = d.ptr + (int64_t)vec * d.ld;
-    if (k < len) {
-      for (int i = 0; i < k; ++i) {
-        const T* v = d.V + (int64_t)i * len;
-        T s = T(0);
-        for (int l = i + lane; l < len; l += 32) s += y[l] * (l == i ? T(1) : v[l]);
-        s = warp_sum(s) * d.tau[i];
-        for (int l = i + lane; l < len; l += 32) y[l] -= s * (l == i ? T(1) : v[l]);
-      }
-      for (int l = k + lane; l < len; l += 32) y[l] = T(0);
+#pragma unroll
+    for (int q = 0; q < VPW; ++q) s[q] = warp_sum(s[q]) * d.tau[i];
+    for (int l = i + lane; l < len; l += 32) {
+      const T vl = l == i ? T(1) : v[l];
+#pragma unroll
+      for (int q = 0; q < VPW; ++q)
+        if (q < nv) x[(int64_t)l * sl + q * sq] -= s[q] * vl;
     }
   }
+  for (int l = k + lane; l < len; l += 32)
+#pragma unroll
+    for (int q = 0; q < VPW; ++q)
+      if (q < nv) x[(int64_t)l * sl + q * sq] = T(0);
 }
 
 // ---------------------------------------------------------- X <- X R^{-1}
+// One thread per row of X, the columns in blocks of 32: a block's 32 entries
+// are accumulated in registers, first minus the solved blocks times the
+// matching tiles of R (staged in shared memory, shared by the CTA's rows),
+// then solved against the block's diagonal triangle.
+constexpr int kTrsmB = 32;
 template <typename T>
 __global__ void __launch_bounds__(kThreads) trsm_kernel(const TrsmDesc<T>* descs, const int2* items) {
   const int2 it = items[blockIdx.x];  // (descriptor, first row)
   const TrsmDesc<T> d = descs[it.x];
   const int r = it.y + threadIdx.x;
-  if (r >= d.rows) return;
-  T* x = d.ptr + r;
-  for (int j = 0; j < d.c; ++j) {
-    T s = x[(int64_t)j * d.ld];
-    const T* Rj = d.R + (int64_t)j * d.rld;
-    for (int i = 0; i < j; ++i) s -= x[(int64_t)i * d.ld] * Rj[i];
-    x[(int64_t)j * d.ld] = s / Rj[j];
+  const bool live = r < d.rows;
+  __shared__ T Rt[kTrsmB][kTrsmB + 1];  // Rt[i][k] = R[i0 + i, j0 + k]
+  T* x = d.ptr + (live ? r : 0);
+  for (int j0 = 0; j0 < d.c; j0 += kTrsmB) {
+    const int nb = min(kTrsmB, d.c - j0);
+    T s[kTrsmB];
+#pragma unroll
+    for (int k = 0; k < kTrsmB; ++k) s[k] = (live && k < nb) ? x[(int64_t)(j0 + k) * d.ld] : T(0);
+    for (int i0 = 0; i0 < j0; i0 += kTrsmB) {  // s_k -= x_i R[i, j0 + k] over the solved blocks
+      __syncthreads();
+      for (int e = threadIdx.x; e < kTrsmB * kTrsmB; e += kThreads) {
+        const int i = e % kTrsmB, k = e / kTrsmB;
+        Rt[i][k] = k < nb ? d.R[(i0 + i) + (int64_t)(j0 + k) * d.rld] : T(0);
+      }
+      __syncthreads();
+      if (live) {
+#pragma unroll 4
+        for (int i = 0; i < kTrsmB; ++i) {
+          const T xi = x[(int64_t)(i0 + i) * d.ld];
+#pragma unroll
+          for (int k = 0; k < kTrsmB; ++k) s[k] -= xi * Rt[i][k];
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kTrsmB * kTrsmB; e += kThreads) {
+      const int i = e % kTrsmB, k = e / kTrsmB;
+      Rt[i][k] = (i < nb && k < nb) ? d.R[(j0 + i) + (int64_t)(j0 + k) * d.rld] : T(1);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kTrsmB; ++k) {  // the diagonal triangle: s[i], i < k, already solved
+      T v = s[k];
+#pragma unroll
+      for (int i = 0; i < k; ++i) v -= s[i] * Rt[i][k];
+      s[k] = v / Rt[k][k];
+    }
+    if (live)
+#pragma unroll
+      for (int k = 0; k < kTrsmB; ++k)
+        if (k < nb) x[(int64_t)(j0 + k) * d.ld] = s[k];
   }
 }
 
@@ -2377,11 +2423,12 @@ void allow_smem(K kernel) {
 int max_smem_optin() {
   // dynamic shared memory any kernel here may request: the opt-in maximum
   // less a margin that covers the largest static footprint of the
-  // dynamic-smem kernels (a few hundred bytes)
+  // dynamic-smem pivoted-QR kernels (at most 1.5 KB: the FP64 slab kernel's
+  // per-CTA records of a 16-CTA cluster)
   int dev = 0, mx = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return mx - 1024;
+  return mx - 2048;
 }
 
 template <typename T>

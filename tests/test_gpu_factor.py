@@ -185,7 +185,7 @@ def test_block_cache_reuse_and_release():
     assert len(ops1) == len(ops2)
     for a, b in zip(ops1, ops2):
         for key in ("R", "Rn", "V", "taus"):
-            if a.get(key) is not None:
+            if a.get(key) is not None and np.size(a[key]):
                 np.testing.assert_allclose(a[key], b[key], rtol=1e-6, atol=1e-6 * np.abs(a[key]).max())
     np.testing.assert_allclose(x1, x2, rtol=1e-8, atol=1e-8 * np.abs(x1).max())
     del s2
