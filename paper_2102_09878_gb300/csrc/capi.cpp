@@ -799,8 +799,11 @@ int dense_front_qr_t(int count, T* const* A, const int* m, const int* n, const i
       frees.push_back(d);
       SPAQR_CUDA(cudaMemcpyAsync(d, host[g].data(), host[g].size() * sizeof(host[g][0]), cudaMemcpyHostToDevice, st));
       dev[g] = d;
-      if (groups[g].kind == 2) {
-        SPAQR_CUDA(cudaMalloc(&Tbuf, host[g].size() * 32 * 32 * sizeof(T)));
+      if (groups[g].kind == 2) {  // per front: a 32 x 32 T factor, later the sign mask of diag(R)
+        int maxc = 0;
+        for (auto& f : host[g]) maxc = std::max(maxc, f.c);
+        const size_t per = std::max<size_t>(32 * 32 * sizeof(T), (size_t)((maxc + 31) / 32) * sizeof(unsigned));
+        SPAQR_CUDA(cudaMalloc(&Tbuf, host[g].size() * per));
         frees.push_back(Tbuf);
       }
     }

@@ -293,13 +293,31 @@ __device__ void apply_reflector_cols(T* X, int ld, int m, int j, T tau, int c0, 
   }
 }
 
+// Applies H_j to column cc alone (one warp).
+template <typename T>
+__device__ __forceinline__ void apply_reflector_col(T* X, int ld, int m, int j, T tau, int cc) {
+  const int lane = threadIdx.x & 31;
+  const T* v = X + (int64_t)j * ld;
+  T* col = X + (int64_t)cc * ld;
+  T s = T(0);
+  for (int i = j + 1 + lane; i < m; i += 32) s += v[i] * col[i];
+  s = warp_sum(s);
+  const T w = tau * (col[j] + s);
+  if (lane == 0) col[j] -= w;
+  for (int i = j + 1 + lane; i < m; i += 32) col[i] -= w * v[i];
+}
+
 // ------------------------------------------------- front QR, shared memory
+// One CTA per front.  Look-ahead by one column: while warps 1..7 apply H_j to
+// columns j+2.., warp 0 applies it to column j+1 and forms H_{j+1} from it,
+// so the reflector's reductions overlap the trailing update (one CTA barrier
+// per column).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) front_qr_smem_kernel(const FrontDesc<T>* descs) {
   const FrontDesc<T> d = descs[blockIdx.x];
   extern __shared__ __align__(16) unsigned char smraw[];
   T* S = reinterpret_cast<T*>(smraw);
-  __shared__ T s_tau, s_beta;
+  __shared__ T s_tau2[2], s_beta2[2];  // reflector data by column parity
   const int m = d.m, n = d.n, c = d.c;
   if (m == 0 || n == 0) return;
   const int64_t tot = (int64_t)m * n;
@@ -311,12 +329,23 @@ __global__ void __launch_bounds__(kThreads) front_qr_smem_kernel(const FrontDesc
   for (int t = threadIdx.x; t < (c + 31) / 32; t += kThreads) negmask[t] = 0u;
   __syncthreads();
   const int steps = c < m ? c : m;
+  const int warp = threadIdx.x >> 5;
+  if (steps > 0) make_reflector_warp0(S, m, m, 0, &s_tau2[0], &s_beta2[0]);
+  __syncthreads();
   for (int j = 0; j < steps; ++j) {
-    make_reflector_warp0(S, m, m, j, &s_tau, &s_beta);
-    __syncthreads();
-    const T tau = s_tau;
-    if (threadIdx.x == 0 && s_beta < T(0)) negmask[j >> 5] |= 1u << (j & 31);
-    if (tau != T(0)) apply_reflector_cols(S, m, m, j, tau, j + 1, n);
+    const T tau = s_tau2[j & 1];
+    if (warp == 0) {
+      if (threadIdx.x == 0 && s_beta2[j & 1] < T(0)) negmask[j >> 5] |= 1u << (j & 31);
+      if (j + 1 < n) {
+        if (tau != T(0)) apply_reflector_col(S, m, m, j, tau, j + 1);
+        if (j + 1 < steps) {
+          __syncwarp();
+          make_reflector_warp0(S, m, m, j + 1, &s_tau2[(j + 1) & 1], &s_beta2[(j + 1) & 1]);
+        }
+      }
+    } else if (tau != T(0)) {
+      for (int cc = j + 2 + (warp - 1); cc < n; cc += kWarps - 1) apply_reflector_col(S, m, m, j, tau, cc);
+    }
     __syncthreads();
   }
   // zero below the diagonal of the eliminated columns; flip rows with R_ii < 0
@@ -696,25 +725,50 @@ __global__ void __launch_bounds__(kThreads) front_trailing_kernel(const FrontDes
 
 // After the panels: zero below the diagonal of the eliminated columns and flip
 // rows of R with a negative diagonal.
+// The signs of the diagonal entries R_ii of every front, as bit masks (front f
+// at masks + f * words_per_front), taken before any row is flipped.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) front_finish_kernel(const FrontDesc<T>* descs) {
+__global__ void __launch_bounds__(kThreads) front_signs_kernel(const FrontDesc<T>* descs, unsigned* masks,
+                                                               int words_per_front) {
   const FrontDesc<T> d = descs[blockIdx.x];
   const int steps = d.c < d.m ? d.c : d.m;
-  T* X = d.ptr;
-  extern __shared__ unsigned negmask[];  // ceil(steps / 32) words
-  for (int t = threadIdx.x; t < (steps + 31) / 32; t += kThreads) negmask[t] = 0u;
-  __syncthreads();
-  for (int i = threadIdx.x; i < steps; i += kThreads)
-    if (X[i + (int64_t)i * d.ld] < T(0)) atomicOr(&negmask[i >> 5], 1u << (i & 31));
-  __syncthreads();
-  // rows r < steps, columns >= r: flip; columns < steps, rows > column: zero
-  for (int64_t e = threadIdx.x; e < (int64_t)steps * d.n; e += kThreads) {
-    const int r = (int)(e % steps), cc = (int)(e / steps);
-    if (cc >= r && ((negmask[r >> 5] >> (r & 31)) & 1u)) X[r + (int64_t)cc * d.ld] = -X[r + (int64_t)cc * d.ld];
+  const int words = (steps + 31) / 32;
+  __shared__ unsigned sm[kThreads];
+  unsigned* out = masks + (size_t)blockIdx.x * words_per_front;
+  for (int w0 = 0; w0 < words; w0 += kThreads) {
+    __syncthreads();
+    if (w0 + (int)threadIdx.x < words) sm[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int i = w0 * 32 + threadIdx.x; i < steps && i < (w0 + kThreads) * 32; i += kThreads)
+      if (d.ptr[i + (int64_t)i * d.ld] < T(0)) atomicOr(&sm[(i >> 5) - w0], 1u << (i & 31));
+    __syncthreads();
+    if (w0 + (int)threadIdx.x < words) out[w0 + threadIdx.x] = sm[threadIdx.x];
   }
-  for (int64_t e = threadIdx.x; e < (int64_t)d.m * steps; e += kThreads) {
-    const int r = (int)(e % d.m), cc = (int)(e / d.m);
-    if (r > cc) X[r + (int64_t)cc * d.ld] = T(0);
+}
+
+// Blocked fronts, after the last panel: rows i with R_ii < 0 are negated from
+// column i on (diag(R) >= 0), and the eliminated columns are zeroed below the
+// diagonal.  CTA (f, y) takes 32 columns of front f, threads over rows.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) front_finish_kernel(const FrontDesc<T>* descs, const unsigned* masks,
+                                                                int words_per_front) {
+  const FrontDesc<T> d = descs[blockIdx.x];
+  const int c0 = blockIdx.y * 32;
+  if (c0 >= d.n) return;
+  const int c1 = min(d.n, c0 + 32);
+  const int steps = d.c < d.m ? d.c : d.m;
+  const unsigned* mk = masks + (size_t)blockIdx.x * words_per_front;
+  T* X = d.ptr;
+  for (int cc = c0; cc < c1; ++cc) {
+    const int rows = cc < steps ? d.m : steps;  // zeroing below the diagonal only in eliminated columns
+    T* col = X + (int64_t)cc * d.ld;
+    for (int r = threadIdx.x; r < rows; r += kThreads) {
+      if (r > cc) {
+        col[r] = T(0);
+      } else if (r < steps && ((__ldg(&mk[r >> 5]) >> (r & 31)) & 1u)) {
+        col[r] = -col[r];
+      }
+    }
   }
 }
 
@@ -2512,9 +2566,12 @@ cudaError_t launch_front_trailing(const FrontDesc<T>* d, int count, int j0, int 
 }
 
 template <typename T>
-cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, cudaStream_t st) {
+cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, int max_n, unsigned* masks,
+                                cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  front_finish_kernel<T><<<(unsigned)count, kThreads, (size_t)(((max_c + 31) / 32) * 4 + 16), st>>>(d);
+  const int words = (max_c + 31) / 32;
+  front_signs_kernel<T><<<(unsigned)count, kThreads, 0, st>>>(d, masks, words);
+  front_finish_kernel<T><<<dim3((unsigned)count, (unsigned)((max_n + 31) / 32)), kThreads, 0, st>>>(d, masks, words);
   return cudaGetLastError();
 }
 
@@ -2782,8 +2839,13 @@ cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std
           ++*launches;
         }
       }
-      if (e == cudaSuccess) e = launch_front_finish<T>(d[g], cnt, G.param, st);
-      ++*launches;
+      // the sign masks go where the panels' T factors were (no longer needed):
+      // count x 32 x 32 elements hold ceil(max c / 32) words per front
+      int max_n = 0;
+      for (auto& f : host[g]) max_n = std::max(max_n, f.n);
+      if (e == cudaSuccess)
+        e = launch_front_finish<T>(d[g], cnt, G.param, max_n, reinterpret_cast<unsigned*>(Tbuf), st);
+      *launches += 2;
     }
   }
   return e;
@@ -2803,7 +2865,7 @@ cudaError_t launch_front_groups(const std::vector<FrontGroup>& groups, const std
   template cudaError_t launch_front_panel<T>(const FrontDesc<T>*, int, int, int, T*, cudaStream_t, int); \
   template cudaError_t launch_front_trailing<T>(const FrontDesc<T>*, int, int, int, const T*, int,       \
                                                 cudaStream_t);                                           \
-  template cudaError_t launch_front_finish<T>(const FrontDesc<T>*, int, int, cudaStream_t);                   \
+  template cudaError_t launch_front_finish<T>(const FrontDesc<T>*, int, int, int, unsigned*, cudaStream_t);                   \
   template cudaError_t launch_qrcp<T>(const QrcpDesc<T>*, int, double, int, int, int, bool, cudaStream_t, int); \
   template cudaError_t launch_qrcp_grid<T>(const QrcpDesc<T>*, const QrcpGridDesc*, int, int, double, int, int,    \
                                            bool, cudaStream_t);                                                   \

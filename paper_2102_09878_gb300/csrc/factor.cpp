@@ -675,7 +675,12 @@ void Factorizer<T>::front_qr(std::vector<FrontDesc<T>>& fr) {
   for (size_t g = 0; g < groups.size(); ++g) {
     for (int i : groups[g].idx) host[g].push_back(fr[(size_t)i]);
     dev[g] = up_.put(host[g]);
-    if (groups[g].kind == 2) Tbuf = static_cast<T*>(up_.scratch(host[g].size() * 32 * 32 * sizeof(T)));
+    if (groups[g].kind == 2) {  // per front: a 32 x 32 T factor, later the sign mask of diag(R)
+      int maxc = 0;
+      for (auto& f : host[g]) maxc = std::max(maxc, f.c);
+      const size_t per = std::max<size_t>(32 * 32 * sizeof(T), (size_t)((maxc + 31) / 32) * sizeof(unsigned));
+      Tbuf = static_cast<T*>(up_.scratch(host[g].size() * per));
+    }
   }
   // FP32 factor: blocked fronts take the tensor-core trailing updates
   const size_t tc_bytes = front_groups_tc_bytes<T>(groups, host);

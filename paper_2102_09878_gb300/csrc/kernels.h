@@ -111,7 +111,7 @@ template <typename T>
 cudaError_t launch_front_trailing(const FrontDesc<T>* d, int count, int j0, int nb, const T* Tbuf, int max_tiles,
                                   cudaStream_t st);
 template <typename T>
-cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, cudaStream_t st);
+cudaError_t launch_front_finish(const FrontDesc<T>* d, int count, int max_c, int max_n, unsigned* masks, cudaStream_t st);
 // One cluster of cs CTAs per matrix (cs in 1, 2, 4, 8, 16); every matrix of a
 // launch shares cs, nl_max >= ceil(n / cs) and m_max >= m.  smem_slab: the
 // column slabs live in shared memory, else in each descriptor's work buffer
