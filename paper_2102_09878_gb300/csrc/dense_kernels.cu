@@ -607,23 +607,41 @@ __global__ void __launch_bounds__(kThreads, 1) front_panel_cluster_kernel(const 
     if (lane == 0) Gp[l + i * 33] = acc;
   }
   cl.sync();  // (C) partial Gram matrices visible
-  if (rank == 0 && warp == 0) {
-    // G summed over the cluster, then T column by column: T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i]
-    T* Tm = Tbuf + (int64_t)f * nb * nb;
-    for (int i = 0; i < b; ++i) {
+  if (rank == 0) {
+    // G summed over the cluster: one thread per (l, i) pair, its CS remote
+    // loads issued together and added in rank order, in place (no other CTA
+    // reads CTA 0's partials)
+    for (int pq = threadIdx.x; pq < b * b; pq += kThreads) {
+      const int l = pq % b, i = pq / b;
+      if (l >= i) continue;
+      T v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = q < CS ? *cl.map_shared_rank(&Gp[l + i * 33], q) : T(0);
       T g = T(0);
-      if (lane < i)
-        for (int q = 0; q < CS; ++q) g += *cl.map_shared_rank(&Gp[lane + i * 33], q);
-      wsum[lane] = g;  // G[lane, i]
-      __syncwarp();
-      T acc = T(0);
-      if (lane < i)
-        for (int qq = lane; qq < i; ++qq) acc += Tm[lane + qq * nb] * wsum[qq];
-      __syncwarp();
-      if (lane < i) Tm[lane + i * nb] = -taus[i] * acc;
-      if (lane == i) Tm[i + i * nb] = taus[i];
-      if (lane > i && lane < nb) Tm[lane + i * nb] = T(0);
-      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (q < CS) g += v[q];
+      Gp[l + i * 33] = g;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // T column by column, in place over G (column i of G is read into wsum
+      // before column i of T replaces it; later columns need only their own
+      // column of G and the finished columns of T):
+      // T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i]
+      for (int i = 0; i < b; ++i) {
+        wsum[lane] = lane < i ? Gp[lane + i * 33] : T(0);  // G[lane, i]
+        __syncwarp();
+        T acc = T(0);
+        if (lane < i)
+          for (int qq = lane; qq < i; ++qq) acc += Gp[lane + qq * 33] * wsum[qq];
+        __syncwarp();
+        Gp[lane + i * 33] = lane < i ? -taus[i] * acc : (lane == i ? taus[i] : T(0));
+        __syncwarp();
+      }
+      T* Tg = Tbuf + (int64_t)f * nb * nb;
+      for (int i = 0; i < nb; ++i)
+        if (lane < nb) Tg[lane + i * nb] = (i < b && lane < b) ? Gp[lane + i * 33] : T(0);
     }
   }
   // the panel back to global memory (R above, reflectors below the diagonal)
@@ -2326,10 +2344,10 @@ __global__ void __launch_bounds__(kThreads) qrcp_warp_kernel(const QrcpDesc<T>* 
 }
 
 // ------------------------------------------------------ reflector applies
-// A warp applies the k reflectors to kReflVPW vectors at once (lanes over the
-// vector's entries): the vectors' dot products and warp sums are independent,
-// so their latencies overlap, and for row vectors (mode 0) the vectors are
-// neighbours in memory.
+// A warp applies the k reflectors to kReflPerItem / 8 vectors (lanes over the
+// vector's entries).  One vector per warp measured fastest at 1024^2: four per
+// warp overlapped the warp sums but cut the warps in flight by four (2.6 times
+// slower in all).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) refl_kernel(const ReflDesc<T>* descs, const int2* items) {
   constexpr int VPW = kReflPerItem / kWarps;
