@@ -2550,6 +2550,11 @@ cudaError_t launch_front_panel(const FrontDesc<T>* d, int count, int j0, int nb,
   const int per_cap = lim / (nb * (int)sizeof(T)) - 1;
   int cs = 1;
   while (cs < 16 && (rows_max + cs - 1) / cs > per_cap) cs *= 2;
+  // a few fronts: spread their rows over larger clusters (the per-column loops
+  // shorten with the rows per CTA; the two cluster barriers per column do not
+  // grow), while the batch stays within one wave of clusters (about 128 SMs)
+  // and every CTA keeps at least 64 rows
+  while (cs < 16 && (int64_t)count * cs * 2 <= 128 && rows_max / (cs * 2) >= 64) cs *= 2;
   const int per_max = (rows_max + cs - 1) / cs;
   if (rows_max <= 0 || per_max > per_cap) {
     front_panel_kernel<T><<<(unsigned)count, kThreads, 0, st>>>(d, j0, nb, Tbuf);

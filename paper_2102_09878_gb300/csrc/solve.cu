@@ -397,42 +397,45 @@ __global__ void __launch_bounds__(kT) apply_persistent_kernel(const SegDev* segs
 template <typename TW>
 __global__ void __launch_bounds__(kT) form_dense_kernel(const DenseOp<TW>* dops, const int2* items, int64_t nitems,
                                                         double* scratch, int cmax) {
+  // in the arithmetic of the stored factor (FP64, or FP32 for the mixed-precision
+  // factor: the applies use G and G^T alike, so the operator stays consistent)
+  using A = TW;
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * kT + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * kT) >> 5;
-  double* y = scratch + gw * cmax;
+  A* y = reinterpret_cast<A*>(scratch) + gw * cmax;
   for (int64_t t = gw; t < nitems; t += nw) {
     const int2 it = items[t];
     const DenseOp<TW>* op = dops + it.x;
     const int c = op->c, j = it.y;
     if (op->kind == 2) {
-      for (int i = lane; i < c; i += 32) y[i] = i == j ? 1.0 : 0.0;
+      for (int i = lane; i < c; i += 32) y[i] = i == j ? A(1) : A(0);
       __syncwarp();
       for (int q = op->k - 1; q >= 0; --q) {
         const TW* v = op->V + (int64_t)q * c;
-        double d = 0.0;
-        for (int i = q + lane; i < c; i += 32) d += (i == q ? 1.0 : (double)v[i]) * y[i];
-        d = wsum(d) * (double)op->tau[q];
-        for (int i = q + lane; i < c; i += 32) y[i] -= d * (i == q ? 1.0 : (double)v[i]);
+        A d = A(0);
+        for (int i = q + lane; i < c; i += 32) d += (i == q ? A(1) : (A)v[i]) * y[i];
+        d = wsum(d) * (A)op->tau[q];
+        for (int i = q + lane; i < c; i += 32) y[i] -= d * (i == q ? A(1) : (A)v[i]);
         __syncwarp();
       }
     } else {
       const TW* R = op->R;
       int top = c - 1;
       if (j < c) {
-        for (int i = lane; i < c; i += 32) y[i] = i == j ? 1.0 : 0.0;
+        for (int i = lane; i < c; i += 32) y[i] = i == j ? A(1) : A(0);
         top = j;
       } else {
         const TW* b = R + (int64_t)j * c;  // column j - c of R_sn
-        for (int i = lane; i < c; i += 32) y[i] = -(double)b[i];
+        for (int i = lane; i < c; i += 32) y[i] = -(A)b[i];
       }
       __syncwarp();
       for (int i = top; i >= 0; --i) {
-        const double yi = y[i] / (double)R[i + (int64_t)i * c];
+        const A yi = y[i] / (A)R[i + (int64_t)i * c];
         __syncwarp();
         if (lane == 0) y[i] = yi;
         const TW* col = R + (int64_t)i * c;
-        for (int r = lane; r < i; r += 32) y[r] -= yi * (double)col[r];
+        for (int r = lane; r < i; r += 32) y[r] -= yi * (A)col[r];
         __syncwarp();
       }
     }
