@@ -553,16 +553,30 @@ class Factorizer {
   void kill_many(const std::vector<int>& ids) {
     std::vector<std::vector<int>> freed((size_t)ThreadPool::get().workers());
     parallel_for((int64_t)ids.size(), [&](int64_t b, int64_t e, int w) {
+      // groups of one buffer tend to be neighbours: one atomic per run of equal buffers
+      int run_buf = -1, run = 0;
+      auto flush = [&]() {
+        if (run_buf >= 0 && __atomic_sub_fetch(&bufs_[(size_t)run_buf].refs, run, __ATOMIC_ACQ_REL) == 0)
+          freed[(size_t)w].push_back(run_buf);
+        run_buf = -1;
+        run = 0;
+      };
       for (int64_t i = b; i < e; ++i) {
         Group& g = G_[(size_t)ids[(size_t)i]];
-        if (g.buf >= 0 && __atomic_sub_fetch(&bufs_[(size_t)g.buf].refs, 1, __ATOMIC_ACQ_REL) == 0)
-          freed[(size_t)w].push_back(g.buf);
+        if (g.buf >= 0) {
+          if (g.buf != run_buf) {
+            flush();
+            run_buf = g.buf;
+          }
+          ++run;
+        }
         g.buf = -1;
         g.ptr = nullptr;
         g.alive = false;
         g.sup.clear_free();
         g.off.clear_free();
       }
+      flush();
     }, 4096);
     std::vector<int> all;
     for (auto& v : freed) all.insert(all.end(), v.begin(), v.end());
@@ -892,7 +906,21 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
   });
   lap("init: row owners");
   if (empty_row.load() >= 0) throw Error(SPAQR_ERR_INVALID_ARG, "empty row " + std::to_string(empty_row.load()));
-  for (int64_t r = 0; r < M; ++r) sptr[(size_t)r + 1] += sptr[(size_t)r];
+  {  // prefix sums of the support sizes: chunk totals, their prefix, then each chunk
+    const int parts = ThreadPool::get().workers();
+    std::vector<int64_t> base((size_t)parts + 1, 0);
+    parallel_for(parts, [&](int64_t b, int64_t e, int) {
+      for (int64_t p = b; p < e; ++p)
+        for (int64_t r = M * p / parts; r < M * (p + 1) / parts; ++r) base[(size_t)p + 1] += sptr[(size_t)r + 1];
+    }, 1);
+    for (int p = 0; p < parts; ++p) base[(size_t)p + 1] += base[(size_t)p];
+    parallel_for(parts, [&](int64_t b, int64_t e, int) {
+      for (int64_t p = b; p < e; ++p) {
+        int64_t acc = base[(size_t)p];
+        for (int64_t r = M * p / parts; r < M * (p + 1) / parts; ++r) sptr[(size_t)r + 1] = acc += sptr[(size_t)r + 1];
+      }
+    }, 1);
+  }
   sups.resize((size_t)sptr[(size_t)M]);
   parallel_for(M, [&](int64_t b, int64_t e, int) {
     std::vector<int> tmp;
@@ -905,14 +933,20 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
     }
   });
   lap("init: row supports");
-  // counting sort by owner, then (support, row) inside an owner
+  // bucket the rows by owner (in parallel; the order inside a bucket does not
+  // matter: every bucket is then sorted by (support, row))
   std::vector<int64_t> cnt(nc + 1, 0);
-  for (int64_t r = 0; r < M; ++r) cnt[(size_t)owner[(size_t)r] + 1]++;
+  parallel_for(M, [&](int64_t b, int64_t e, int) {
+    for (int64_t r = b; r < e; ++r) __atomic_fetch_add(&cnt[(size_t)owner[(size_t)r] + 1], 1, __ATOMIC_RELAXED);
+  });
   for (size_t c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
   std::vector<int64_t> order((size_t)M);
   {
     std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
-    for (int64_t r = 0; r < M; ++r) order[(size_t)pos[(size_t)owner[(size_t)r]]++] = r;
+    parallel_for(M, [&](int64_t b, int64_t e, int) {
+      for (int64_t r = b; r < e; ++r)
+        order[(size_t)__atomic_fetch_add(&pos[(size_t)owner[(size_t)r]], 1, __ATOMIC_RELAXED)] = r;
+    });
   }
   auto sup_less = [&](int64_t a, int64_t b) {
     const int32_t *pa = &sups[(size_t)sptr[(size_t)a]], *pb = &sups[(size_t)sptr[(size_t)b]];
@@ -959,10 +993,26 @@ void Factorizer<T>::init_stage(const spaqr_csr& A) {
   parallel_for(M, [&](int64_t b, int64_t e, int) {
     for (int64_t t = b; t < e; ++t) starts_here[(size_t)t] = t == 0 || !same(order[(size_t)t], order[(size_t)t - 1]);
   });
+  // the group starts, in order: per-chunk counts, then each chunk writes its own
   std::vector<int64_t> starts;
-  for (int64_t t = 0; t < M; ++t)
-    if (starts_here[(size_t)t]) starts.push_back(t);
-  starts.push_back(M);
+  {
+    const int parts = ThreadPool::get().workers();
+    std::vector<int64_t> pc((size_t)parts + 1, 0);
+    parallel_for(parts, [&](int64_t b, int64_t e, int) {
+      for (int64_t p = b; p < e; ++p)
+        for (int64_t t = M * p / parts; t < M * (p + 1) / parts; ++t) pc[(size_t)p + 1] += starts_here[(size_t)t];
+    }, 1);
+    for (int p = 0; p < parts; ++p) pc[(size_t)p + 1] += pc[(size_t)p];
+    starts.resize((size_t)pc[(size_t)parts] + 1);
+    parallel_for(parts, [&](int64_t b, int64_t e, int) {
+      for (int64_t p = b; p < e; ++p) {
+        int64_t q = pc[(size_t)p];
+        for (int64_t t = M * p / parts; t < M * (p + 1) / parts; ++t)
+          if (starts_here[(size_t)t]) starts[(size_t)q++] = t;
+      }
+    }, 1);
+    starts.back() = M;
+  }
   const size_t ngroups = starts.size() - 1;
   G_.reserve(3 * ngroups + 1024);  // group ids only grow; avoid moving every group on growth
   const int gbase = add_groups(ngroups);
