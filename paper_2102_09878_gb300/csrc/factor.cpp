@@ -752,19 +752,13 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
     dgd[t] = up_.put(gd);
   }
   tm_.begin(st_, 2);
-  // every group is an independent launch: the cooperative CTA-group launches
-  // (the long poles) go first on st_, the shared-memory and warp groups on the
-  // side streams beside them (forked after the uploads above, joined before
-  // anything that follows)
+  // the shared-memory and warp groups are independent launches: they run side by side on st_ and
+  // the side streams (forked after the uploads above, joined before anything that follows); the
+  // cooperative CTA-group launches run alone on st_ afterwards
   std::vector<size_t> plain;
-  bool any_grid = false;
-  for (size_t t = 0; t < groups.size(); ++t) {
-    if (groups[t].grid)
-      any_grid = true;
-    else
-      plain.push_back(t);
-  }
-  const size_t nside = std::min<size_t>(any_grid ? plain.size() : (plain.size() > 0 ? plain.size() - 1 : 0), 3);
+  for (size_t t = 0; t < groups.size(); ++t)
+    if (!groups[t].grid) plain.push_back(t);
+  const size_t nside = std::min<size_t>(plain.size() > 0 ? plain.size() - 1 : 0, 3);
   if (nside) {
     if (!fork_) SPAQR_CUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
     SPAQR_CUDA(cudaEventRecord(fork_, st_));
@@ -776,21 +770,20 @@ void Factorizer<T>::qrcp(std::vector<QrcpDesc<T>>& qs, std::vector<T*>& work_buf
       SPAQR_CUDA(cudaStreamWaitEvent(aux_[a].st, fork_, 0));
     }
   }
-  for (size_t t = 0; t < groups.size(); ++t) {
-    const auto& g = groups[t];
-    if (g.grid)
-      check(launch_qrcp_grid<T>(dg[t], dgd[t], (int)g.idx.size(), gtot[t], eps, g.nl_max, g.m_max, g.slab, st_), "qrcp grid");
-  }
   for (size_t q = 0; q < plain.size(); ++q) {
     const size_t t = plain[q];
     const auto& g = groups[t];
-    // without CTA groups the first plain group takes st_ itself
-    cudaStream_t s = nside == 0 ? st_ : (any_grid ? aux_[q % nside].st : (q == 0 ? st_ : aux_[(q - 1) % nside].st));
+    cudaStream_t s = (q == 0 || nside == 0) ? st_ : aux_[(q - 1) % nside].st;
     check(launch_qrcp<T>(dg[t], (int)g.idx.size(), eps, g.cs, g.nl_max, g.m_max, g.slab, s, g.nb), "qrcp");
   }
   for (size_t a = 0; a < nside; ++a) {
     SPAQR_CUDA(cudaEventRecord(aux_[a].done, aux_[a].st));
     SPAQR_CUDA(cudaStreamWaitEvent(st_, aux_[a].done, 0));
+  }
+  for (size_t t = 0; t < groups.size(); ++t) {
+    const auto& g = groups[t];
+    if (g.grid)
+      check(launch_qrcp_grid<T>(dg[t], dgd[t], (int)g.idx.size(), gtot[t], eps, g.nl_max, g.m_max, g.slab, st_), "qrcp grid");
   }
   tm_.end(st_);
 }

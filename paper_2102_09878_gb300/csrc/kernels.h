@@ -419,20 +419,14 @@ inline bool plan_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, in
       cur->nl_max = std::max(cur->nl_max, nl);
       used += g;
     }
-    // with other groups in the batch the CTA groups leave about a third of the
-    // SMs to them (they run side by side; the groups' step time hardly depends
-    // on the spread once a CTA holds few columns)
-    bool others = false;
-    for (auto& g : out) others = others || !g.grid;
-    const int spread_cap = others ? std::max(17, grid_ctas * 5 / 8) : grid_ctas;
     for (auto& g : out) {
       if (!g.grid) continue;
       int tot = 0;
       for (int c : g.ctas) tot += c;
       bool grew = true;
-      while (tot < spread_cap && grew) {
+      while (tot < grid_ctas && grew) {
         grew = false;
-        for (size_t q = 0; q < g.idx.size() && tot < spread_cap; ++q) {
+        for (size_t q = 0; q < g.idx.size() && tot < grid_ctas; ++q) {
           const int n = ns[(size_t)g.idx[q]];
           if ((n + g.ctas[q] - 1) / g.ctas[q] <= 8) continue;
           ++g.ctas[q];
