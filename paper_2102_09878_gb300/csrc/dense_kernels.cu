@@ -2344,49 +2344,125 @@ __global__ void __launch_bounds__(kThreads) qrcp_warp_kernel(const QrcpDesc<T>* 
 }
 
 // ------------------------------------------------------ reflector applies
-// A warp applies the k reflectors to kReflPerItem / 8 vectors (lanes over the
-// vector's entries).  One vector per warp measured fastest at 1024^2: four per
-// warp overlapped the warp sums but cut the warps in flight by four (2.6 times
-// slower in all).
+// Row vectors (mode 0, rows of a block with leading dimension ld): one thread
+// per row, the reflectors in blocks of kWyB as I - V T V^T (compact WY form;
+// T from the block's Gram matrix, as in the front panels): w = V^T x,
+// w' = T^T w, x <- x - V w', with V staged in shared memory in chunks of rows
+// (the rows' entries are read coalesced across threads; 2 kWyB flops per
+// entry and pass instead of a warp reduction per reflector).
+constexpr int kWyB = 32;
+constexpr int kWyChunk = 64;
+template <typename T>
+__device__ void refl_rows_blocked(const ReflDesc<T>& d, int k, int row0) {
+  __shared__ T Vs[kWyChunk][kWyB + 1];
+  __shared__ T Gs[kWyB][kWyB + 1];  // the block's Gram matrix, then T in place
+  __shared__ T tcol[kWyB];
+  const int len = d.len;
+  const int r = row0 + (int)threadIdx.x;
+  const bool live = r < d.nvec;
+  T* x = d.ptr + (live ? r : 0);  // entry l at x[l * ld]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto stage = [&](int i0, int nb, int l0, int nl) {  // V rows l0.., reflectors i0.. (unit lower)
+    for (int e = threadIdx.x; e < kWyChunk * kWyB; e += kThreads) {
+      const int ll = e % kWyChunk, q = e / kWyChunk;
+      const int l = l0 + ll, i = i0 + q;
+      T v = T(0);
+      if (ll < nl && q < nb) v = l < i ? T(0) : (l == i ? T(1) : d.V[l + (int64_t)i * len]);
+      Vs[ll][q] = v;
+    }
+  };
+  for (int i0 = 0; i0 < k; i0 += kWyB) {
+    const int nb = min(kWyB, k - i0);
+    T w[kWyB];
+#pragma unroll
+    for (int q = 0; q < kWyB; ++q) w[q] = T(0);
+    T g4[4] = {T(0), T(0), T(0), T(0)};  // Gram entries (lane, warp + 8 j)
+    for (int l0 = i0; l0 < len; l0 += kWyChunk) {
+      const int nl = min(kWyChunk, len - l0);
+      __syncthreads();
+      stage(i0, nb, l0, nl);
+      __syncthreads();
+      for (int ll = 0; ll < nl; ++ll) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) g4[j] += Vs[ll][lane] * Vs[ll][warp + 8 * j];
+      }
+      if (live)
+        for (int ll = 0; ll < nl; ++ll) {
+          const T xl = x[(int64_t)(l0 + ll) * d.ld];
+#pragma unroll
+          for (int q = 0; q < kWyB; ++q) w[q] += xl * Vs[ll][q];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Gs[lane][warp + 8 * j] = g4[j];
+    __syncthreads();
+    if (warp == 0) {  // T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i], in place over G
+      for (int i = 0; i < kWyB; ++i) {
+        const T tau_i = i < nb ? d.tau[i0 + i] : T(0);
+        tcol[lane] = lane < i ? Gs[lane][i] : T(0);
+        __syncwarp();
+        T acc = T(0);
+        if (lane < i)
+          for (int qq = lane; qq < i; ++qq) acc += Gs[lane][qq] * tcol[qq];
+        __syncwarp();
+        Gs[lane][i] = lane < i ? -tau_i * acc : (lane == i ? tau_i : T(0));
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    T w2[kWyB];  // T^T w
+#pragma unroll
+    for (int q = 0; q < kWyB; ++q) {
+      T acc = T(0);
+#pragma unroll
+      for (int p = 0; p <= q; ++p) acc += Gs[p][q] * w[p];
+      w2[q] = acc;
+    }
+    for (int l0 = i0; l0 < len; l0 += kWyChunk) {
+      const int nl = min(kWyChunk, len - l0);
+      __syncthreads();
+      stage(i0, nb, l0, nl);
+      __syncthreads();
+      if (live)
+        for (int ll = 0; ll < nl; ++ll) {
+          T xl = x[(int64_t)(l0 + ll) * d.ld];
+#pragma unroll
+          for (int q = 0; q < kWyB; ++q) xl -= Vs[ll][q] * w2[q];
+          x[(int64_t)(l0 + ll) * d.ld] = xl;
+        }
+    }
+  }
+  if (live)
+    for (int l = k; l < len; ++l) x[(int64_t)l * d.ld] = T(0);
+}
+
+// Column vectors (mode 1, contiguous): one warp per vector, lanes over its
+// entries, the reflectors one after the other.  Row vectors take the blocked
+// path above (items of kReflRowsPerItem rows).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) refl_kernel(const ReflDesc<T>* descs, const int2* items) {
-  constexpr int VPW = kReflPerItem / kWarps;
   const int2 it = items[blockIdx.x];  // (descriptor, first vector)
   const ReflDesc<T> d = descs[it.x];
   const int k = *d.k;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int vec0 = it.y + warp * VPW;
-  if (vec0 >= d.nvec) return;
-  const int nv = min(VPW, d.nvec - vec0);
   const int len = d.len;
-  if (k >= len) return;
-  // entry l of vector q
-  const int64_t sl = d.mode == 0 ? d.ld : 1, sq = d.mode == 0 ? 1 : d.ld;
-  T* x = d.ptr + (int64_t)vec0 * sq;
+  if (k >= len) return;  // the same for the whole CTA
+  if (d.mode == 0) {
+    refl_rows_blocked(d, k, it.y);
+    return;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int vec = it.y + warp;
+  if (vec >= d.nvec) return;
+  T* y = d.ptr + (int64_t)vec * d.ld;
   for (int i = 0; i < k; ++i) {
     const T* v = d.V + (int64_t)i * len;
-    T s[VPW];
-#pragma unroll
-    for (int q = 0; q < VPW; ++q) s[q] = T(0);
-    for (int l = i + lane; l < len; l += 32) {
-      const T vl = l == i ? T(1) : v[l];
-#pragma unroll
-      for (int q = 0; q < VPW; ++q)
-        if (q < nv) s[q] += x[(int64_t)l * sl + q * sq] * vl;
-    }
-#pragma unroll
-    for (int q = 0; q < VPW; ++q) s[q] = warp_sum(s[q]) * d.tau[i];
-    for (int l = i + lane; l < len; l += 32) {
-      const T vl = l == i ? T(1) : v[l];
-#pragma unroll
-      for (int q = 0; q < VPW; ++q)
-        if (q < nv) x[(int64_t)l * sl + q * sq] -= s[q] * vl;
-    }
+    T s = T(0);
+    for (int l = i + lane; l < len; l += 32) s += y[l] * (l == i ? T(1) : v[l]);
+    s = warp_sum(s) * d.tau[i];
+    for (int l = i + lane; l < len; l += 32) y[l] -= s * (l == i ? T(1) : v[l]);
   }
-  for (int l = k + lane; l < len; l += 32)
-#pragma unroll
-    for (int q = 0; q < VPW; ++q)
-      if (q < nv) x[(int64_t)l * sl + q * sq] = T(0);
+  for (int l = k + lane; l < len; l += 32) y[l] = T(0);
 }
 
 // ---------------------------------------------------------- X <- X R^{-1}

@@ -1882,7 +1882,11 @@ void Factorizer<T>::step2() {
       }
     if (!rf.empty()) {
       auto* d = up_.put(rf);
-      auto its = items_for(rf.size(), kReflPerItem, [&](size_t i) { return rf[i].nvec; });
+      std::vector<int2> its;
+      for (size_t i = 0; i < rf.size(); ++i) {
+        const int per = rf[i].mode == 0 ? kReflRowsPerItem : kReflPerItem;
+        for (int u = 0; u < rf[i].nvec; u += per) its.push_back(make_int2((int)i, u));
+      }
       int2* di = up_.put(its);
       tm_.begin(st_, 3);
       check(launch_refl<T>(d, di, (int)its.size(), st_), "refl");

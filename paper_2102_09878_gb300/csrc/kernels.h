@@ -540,7 +540,8 @@ inline int front_smem_bytes(int m, int n, int c, int elem) {
 template <typename T> cudaError_t launch_refl(const ReflDesc<T>* d, const int2* items, int nitems, cudaStream_t st);
 template <typename T> cudaError_t launch_trsm(const TrsmDesc<T>* d, const int2* items, int nitems, cudaStream_t st);
 template <typename T> cudaError_t launch_argmax(const ArgmaxDesc<T>* d, const int2* items, int nitems, cudaStream_t st);
-constexpr int kReflPerItem = 8;  // one vector per warp
+constexpr int kReflPerItem = 8;        // column vectors: one per warp
+constexpr int kReflRowsPerItem = 256;  // row vectors: one per thread
 constexpr int kRowsPerItem = 256;
 // Write an identity c x c block at ptr (ld) for each desc (src/transposed unused).
 template <typename T> cudaError_t launch_identity(const CopyDesc<T>* d, int count, cudaStream_t st);
