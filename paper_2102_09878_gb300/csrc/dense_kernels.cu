@@ -2437,9 +2437,9 @@ __device__ void refl_rows_blocked(const ReflDesc<T>& d, int k, int row0) {
     for (int l = k; l < len; ++l) x[(int64_t)l * d.ld] = T(0);
 }
 
-// Column vectors (mode 1, contiguous): one warp per vector, lanes over its
-// entries, the reflectors one after the other.  Row vectors take the blocked
-// path above (items of kReflRowsPerItem rows).
+// Column vectors (mode 1, contiguous), and every vector in FP64: one warp per
+// vector, lanes over its entries, the reflectors one after the other.  FP32
+// row vectors take the blocked path above (items of kReflRowsPerItem rows).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) refl_kernel(const ReflDesc<T>* descs, const int2* items) {
   const int2 it = items[blockIdx.x];  // (descriptor, first vector)
@@ -2447,22 +2447,27 @@ __global__ void __launch_bounds__(kThreads) refl_kernel(const ReflDesc<T>* descs
   const int k = *d.k;
   const int len = d.len;
   if (k >= len) return;  // the same for the whole CTA
-  if (d.mode == 0) {
-    refl_rows_blocked(d, k, it.y);
-    return;
+  if constexpr (sizeof(T) == 4) {
+    if (d.mode == 0) {
+      refl_rows_blocked(d, k, it.y);
+      return;
+    }
   }
+  // one warp per vector (FP64 rows too: the blocked form is bound by the FP64
+  // pipe, the per-reflector form was measured faster there)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int vec = it.y + warp;
   if (vec >= d.nvec) return;
-  T* y = d.ptr + (int64_t)vec * d.ld;
+  const int64_t sl = d.mode == 0 ? d.ld : 1;  // stride between a vector's entries
+  T* y = d.ptr + (d.mode == 0 ? (int64_t)vec : (int64_t)vec * d.ld);
   for (int i = 0; i < k; ++i) {
     const T* v = d.V + (int64_t)i * len;
     T s = T(0);
-    for (int l = i + lane; l < len; l += 32) s += y[l] * (l == i ? T(1) : v[l]);
+    for (int l = i + lane; l < len; l += 32) s += y[l * sl] * (l == i ? T(1) : v[l]);
     s = warp_sum(s) * d.tau[i];
-    for (int l = i + lane; l < len; l += 32) y[l] -= s * (l == i ? T(1) : v[l]);
+    for (int l = i + lane; l < len; l += 32) y[l * sl] -= s * (l == i ? T(1) : v[l]);
   }
-  for (int l = k + lane; l < len; l += 32) y[l] = T(0);
+  for (int l = k + lane; l < len; l += 32) y[l * sl] = T(0);
 }
 
 // ---------------------------------------------------------- X <- X R^{-1}
@@ -2476,6 +2481,26 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(const TrsmDesc<T>* descs
   const int2 it = items[blockIdx.x];  // (descriptor, first row)
   const TrsmDesc<T> d = descs[it.x];
   const int r = it.y + threadIdx.x;
+  if constexpr (sizeof(T) == 8) {
+    // FP64: column by column (the blocked form is bound by the FP64 pipe and
+    // was measured slower), four partial sums per dot product
+    if (r >= d.rows) return;
+    T* x = d.ptr + r;
+    for (int j = 0; j < d.c; ++j) {
+      const T* Rj = d.R + (int64_t)j * d.rld;
+      T s0 = x[(int64_t)j * d.ld], s1 = T(0), s2 = T(0), s3 = T(0);
+      int i = 0;
+      for (; i + 3 < j; i += 4) {
+        s0 -= x[(int64_t)i * d.ld] * Rj[i];
+        s1 -= x[(int64_t)(i + 1) * d.ld] * Rj[i + 1];
+        s2 -= x[(int64_t)(i + 2) * d.ld] * Rj[i + 2];
+        s3 -= x[(int64_t)(i + 3) * d.ld] * Rj[i + 3];
+      }
+      for (; i < j; ++i) s0 -= x[(int64_t)i * d.ld] * Rj[i];
+      x[(int64_t)j * d.ld] = ((s0 + s1) + (s2 + s3)) / Rj[j];
+    }
+    return;
+  }
   const bool live = r < d.rows;
   __shared__ T Rt[kTrsmB][kTrsmB + 1];  // Rt[i][k] = R[i0 + i, j0 + k]
   T* x = d.ptr + (live ? r : 0);

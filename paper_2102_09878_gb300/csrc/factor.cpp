@@ -1884,7 +1884,7 @@ void Factorizer<T>::step2() {
       auto* d = up_.put(rf);
       std::vector<int2> its;
       for (size_t i = 0; i < rf.size(); ++i) {
-        const int per = rf[i].mode == 0 ? kReflRowsPerItem : kReflPerItem;
+        const int per = (rf[i].mode == 0 && sizeof(T) == 4) ? kReflRowsPerItem : kReflPerItem;
         for (int u = 0; u < rf[i].nvec; u += per) its.push_back(make_int2((int)i, u));
       }
       int2* di = up_.put(its);
