@@ -2483,21 +2483,14 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(const TrsmDesc<T>* descs
   const int r = it.y + threadIdx.x;
   if constexpr (sizeof(T) == 8) {
     // FP64: column by column (the blocked form is bound by the FP64 pipe and
-    // was measured slower), four partial sums per dot product
+    // was measured slower)
     if (r >= d.rows) return;
     T* x = d.ptr + r;
     for (int j = 0; j < d.c; ++j) {
       const T* Rj = d.R + (int64_t)j * d.rld;
-      T s0 = x[(int64_t)j * d.ld], s1 = T(0), s2 = T(0), s3 = T(0);
-      int i = 0;
-      for (; i + 3 < j; i += 4) {
-        s0 -= x[(int64_t)i * d.ld] * Rj[i];
-        s1 -= x[(int64_t)(i + 1) * d.ld] * Rj[i + 1];
-        s2 -= x[(int64_t)(i + 2) * d.ld] * Rj[i + 2];
-        s3 -= x[(int64_t)(i + 3) * d.ld] * Rj[i + 3];
-      }
-      for (; i < j; ++i) s0 -= x[(int64_t)i * d.ld] * Rj[i];
-      x[(int64_t)j * d.ld] = ((s0 + s1) + (s2 + s3)) / Rj[j];
+      T s = x[(int64_t)j * d.ld];
+      for (int i = 0; i < j; ++i) s -= x[(int64_t)i * d.ld] * Rj[i];
+      x[(int64_t)j * d.ld] = s / Rj[j];
     }
     return;
   }
