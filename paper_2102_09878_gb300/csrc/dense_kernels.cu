@@ -58,22 +58,37 @@ __global__ void __launch_bounds__(kThreads) copy_kernel(const CopyDesc<T>* descs
       hi = mid - 1;
   }
   const CopyDesc<T> d = descs[lo];
-  const int64_t total = (int64_t)d.rows * d.cols;
-  const int64_t beg = (int64_t)(b - chunk_start[lo]) * kCopyChunk;
+  // flat column-major index e = r + c * rows (a block holds fewer than 2^31
+  // entries); (r, c) of the thread's first entry by one 32-bit division, then
+  // stepped by kThreads rows (a division per step for blocks of fewer rows)
+  const uint32_t rows = (uint32_t)d.rows;
+  const uint32_t total = rows * (uint32_t)d.cols;
+  const uint32_t beg = (uint32_t)(b - chunk_start[lo]) * kCopyChunk;
   if (beg >= total) return;
-  const int64_t end = beg + kCopyChunk < total ? beg + kCopyChunk : total;
-  for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
-    const int r = (int)(e % d.rows);
-    const int c = (int)(e / d.rows);
+  const uint32_t end = beg + kCopyChunk < total ? beg + kCopyChunk : total;
+  uint32_t e = beg + threadIdx.x;
+  uint32_t c = e / rows, r = e - c * rows;
+  for (; e < end; e += kThreads) {
     T v = T(0);
     if (d.src) {
-      const int sr = d.rowidx ? d.rowidx[r] : r;
+      const int sr = d.rowidx ? d.rowidx[r] : (int)r;
       v = d.src[sr + (int64_t)c * d.sld];
     }
     if (d.transpose)
       d.dst[c + (int64_t)r * d.dld] = v;
     else
       d.dst[r + (int64_t)c * d.dld] = v;
+    if (rows >= (uint32_t)kThreads) {
+      r += kThreads;
+      if (r >= rows) {
+        r -= rows;
+        ++c;
+      }
+    } else {
+      const uint32_t n = e + kThreads;
+      c = n / rows;
+      r = n - c * rows;
+    }
   }
 }
 
