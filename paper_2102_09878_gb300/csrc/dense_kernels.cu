@@ -58,6 +58,32 @@ __global__ void __launch_bounds__(kThreads) copy_kernel(const CopyDesc<T>* descs
       hi = mid - 1;
   }
   const CopyDesc<T> d = descs[lo];
+  if (d.transpose) {
+    // tile (32 rows x 64 columns) of the source through shared memory: read
+    // along the source's columns, written along the destination's columns
+    __shared__ T tile[64][33];
+    const int tiles_r = (d.rows + 31) / 32;
+    const int t = b - chunk_start[lo];
+    const int r0 = (t % tiles_r) * 32, c0 = (t / tiles_r) * 64;
+    const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;  // 32 rows x 8 columns per pass
+    for (int cc = lc; cc < 64; cc += kThreads / 32) {
+      const int r = r0 + lr, c = c0 + cc;
+      T v = T(0);
+      if (r < d.rows && c < d.cols && d.src) {
+        const int sr = d.rowidx ? d.rowidx[r] : r;
+        v = d.src[sr + (int64_t)c * d.sld];
+      }
+      tile[cc][lr] = v;
+    }
+    __syncthreads();
+    // destination entry (c, r) at dst[c + r * dld]: lanes over c
+    for (int e = threadIdx.x; e < 64 * 32; e += kThreads) {
+      const int cc = e & 63, rr = e >> 6;
+      const int r = r0 + rr, c = c0 + cc;
+      if (r < d.rows && c < d.cols) d.dst[c + (int64_t)r * d.dld] = tile[cc][rr];
+    }
+    return;
+  }
   // flat column-major index e = r + c * rows (a block holds fewer than 2^31
   // entries); (r, c) of the thread's first entry by one 32-bit division, then
   // stepped by kThreads rows (a division per step for blocks of fewer rows)

@@ -648,6 +648,21 @@ class Factorizer {
     return h_.opt.mode == SPAQR_MODE_SPAQR && k_ <= L_ - h_.opt.skip && k_ >= 2;
   }
   void index_groups(GroupIndex& own, GroupIndex& touch);
+  // step 2's structure (colours, and per interface the groups touching it and
+  // its neighbour clusters) depends only on the groups, not on the step-1
+  // ranks: it is prepared while step 1 runs on the device
+  struct S2Member {
+    std::vector<int> nb, ncols;  // touching groups (by owner, id), neighbour clusters of p1
+    int cn = 0;                  // columns of the neighbour clusters
+  };
+  struct S2Plan {
+    bool ready = false;
+    std::vector<int> ps;
+    int ncol = 0;
+    std::vector<std::vector<int>> members;      // by colour
+    std::vector<std::vector<S2Member>> pre;     // parallel to members
+  } s2_;
+  void prepare_step2();
 };
 
 template <typename T>
@@ -658,7 +673,7 @@ void Factorizer<T>::copies(const std::vector<CopyDesc<T>>& cps) {
   int64_t tot = 0;
   for (size_t i = 0; i < cps.size(); ++i) {
     start[i] = (int)tot;
-    tot += copy_chunks((int64_t)cps[i].rows * cps[i].cols);
+    tot += copy_ctas(cps[i].rows, cps[i].cols, cps[i].transpose);
     if (tot > INT32_MAX / 2) throw Error(SPAQR_ERR_CAPACITY, "block copies larger than one launch covers");
   }
   start[cps.size()] = (int)tot;
@@ -1682,6 +1697,7 @@ void Factorizer<T>::step1() {
   front_qr(fr);
   std::vector<T*> work;
   qrcp(qs, work);
+  prepare_step2();  // while the device runs step 1
   std::vector<int> rank(who.size());
   sync_read(rank.data(), d_rank, who.size());
   for (T* w : work) pool_.release(w);
@@ -1713,19 +1729,18 @@ void Factorizer<T>::step1() {
 
 // ---------------------------------------------------------------- step 2
 template <typename T>
-void Factorizer<T>::step2() {
-  NT nt_f(this, "step2");
-  phase_ = "step2";
-  Lap lap(this);
-  HT ht(ht_[5]);
-  std::vector<int> ps;
+void Factorizer<T>::prepare_step2() {
+  NT nt_f(this, "step2: prepare");
+  S2Plan& P = s2_;
+  P = S2Plan();
+  P.ready = true;
   for (size_t p = 0; p < ccols_.size(); ++p)
-    if (!p1_of_.empty() && p1_of_[p] >= 0) ps.push_back((int)p);
-  if (ps.empty()) return;
+    if (!p1_of_.empty() && p1_of_[p] >= 0) P.ps.push_back((int)p);
+  if (P.ps.empty()) return;
   // greedy colouring of q ~ p  <=>  q in support(p1 of p) or p in support(p1 of q)
   const size_t nc = ccols_.size();
   std::vector<std::vector<int>> adj(nc);
-  for (int p : ps) {
+  for (int p : P.ps) {
     for (int q : G_[(size_t)p1_of_[(size_t)p]].sup)
       if (q != p && p1_of_[(size_t)q] >= 0) {
         adj[(size_t)p].push_back(q);
@@ -1734,13 +1749,9 @@ void Factorizer<T>::step2() {
   }
   std::vector<int> colour(nc, -1);
   int ncol = 0;
-  struct ColourLog {
-    StageLog& l;
-    int& n;
-    ~ColourLog() { l.colours = n; }
-  } colour_log{slog_, ncol};
-  for (int p : ps) {
-    std::vector<char> used((size_t)ncol + 1, 0);
+  std::vector<char> used;
+  for (int p : P.ps) {
+    used.assign((size_t)ncol + 1, 0);
     for (int q : adj[(size_t)p])
       if (colour[(size_t)q] >= 0) used[(size_t)colour[(size_t)q]] = 1;
     int c = 0;
@@ -1748,10 +1759,51 @@ void Factorizer<T>::step2() {
     colour[(size_t)p] = c;
     ncol = std::max(ncol, c + 1);
   }
-  lap("step2: colouring");
+  P.ncol = ncol;
+  P.members.assign((size_t)ncol, {});
+  for (int p : P.ps) P.members[(size_t)colour[(size_t)p]].push_back(p);
   GroupIndex own, touch;
   index_groups(own, touch);
-  lap("step2: index groups");
+  P.pre.resize((size_t)ncol);
+  std::vector<std::pair<int, int>> all;  // (colour, member)
+  for (int col = 0; col < ncol; ++col) {
+    P.pre[(size_t)col].resize(P.members[(size_t)col].size());
+    for (size_t q = 0; q < P.members[(size_t)col].size(); ++q) all.emplace_back(col, (int)q);
+  }
+  parallel_for((int64_t)all.size(), [&](int64_t b, int64_t e, int) {
+    for (int64_t t = b; t < e; ++t) {
+      const int col = all[(size_t)t].first, q = all[(size_t)t].second;
+      const int p = P.members[(size_t)col][(size_t)q];
+      S2Member& x = P.pre[(size_t)col][(size_t)q];
+      for (int g : touch[(size_t)p])
+        if (G_[(size_t)g].alive) x.nb.push_back(g);
+      std::sort(x.nb.begin(), x.nb.end(), [&](int a, int c) {
+        const int oa = G_[(size_t)a].owner, oc = G_[(size_t)c].owner;
+        return oa != oc ? oa < oc : a < c;
+      });
+      const Group& g1 = G_[(size_t)p1_of_[(size_t)p]];
+      for (int c : g1.sup)
+        if (c != p) {
+          x.ncols.push_back(c);
+          x.cn += ccols_[(size_t)c];
+        }
+    }
+  }, 16);
+}
+
+template <typename T>
+void Factorizer<T>::step2() {
+  NT nt_f(this, "step2");
+  phase_ = "step2";
+  Lap lap(this);
+  HT ht(ht_[5]);
+  if (!s2_.ready) prepare_step2();
+  s2_.ready = false;
+  const std::vector<int>& ps = s2_.ps;
+  if (ps.empty()) return;
+  const int ncol = s2_.ncol;
+  slog_.colours = ncol;
+  lap("step2: prepare (not overlapped)");
   // one device rank slot per interface of this phase, read back with a single copy
   int* kdev_all = static_cast<int*>(h_.wpool.alloc(ps.size() * sizeof(int)));
   size_t kdev_next = 0;
@@ -1763,8 +1815,7 @@ void Factorizer<T>::step2() {
   std::vector<P2> recs;
   std::vector<T*> work_all;
   const size_t ops0 = h_.ops.size();  // this phase's ops are appended from here
-  std::vector<std::vector<int>> members((size_t)ncol);
-  for (int p : ps) members[(size_t)colour[(size_t)p]].push_back(p);
+  const auto& members = s2_.members;
   for (int col = 0; col < ncol; ++col) {
     struct MInfo {
       int p, cp, rn, cn;
@@ -1777,29 +1828,22 @@ void Factorizer<T>::step2() {
     parallel_for((int64_t)mem.size(), [&](int64_t q0, int64_t q1, int) {
       for (int64_t qq = q0; qq < q1; ++qq) {
         MInfo& x = mi[(size_t)qq];
+        S2Member& pre = s2_.pre[(size_t)col][(size_t)qq];
         const int p = mem[(size_t)qq];
         x.p = p;
         x.cp = ccols_[(size_t)p];
-        for (int g : touch[(size_t)p])
-          if (G_[(size_t)g].alive) x.nb.push_back(g);
-        std::sort(x.nb.begin(), x.nb.end(), [&](int a, int b) {
-          const int oa = G_[(size_t)a].owner, ob = G_[(size_t)b].owner;
-          return oa != ob ? oa < ob : a < b;
-        });
+        // groups that step 1 emptied (rank 0) are gone
+        x.nb.swap(pre.nb);
+        x.nb.erase(std::remove_if(x.nb.begin(), x.nb.end(), [&](int g) { return !G_[(size_t)g].alive; }), x.nb.end());
         x.rn = 0;
         size_t nc = 0;
         for (int g : x.nb) {
           x.rn += G_[(size_t)g].rows;
           nc += G_[(size_t)g].rows ? 1 : 0;
         }
-        const Group& g1 = G_[(size_t)p1_of_[(size_t)p]];
-        x.cn = 0;
-        for (int c : g1.sup)
-          if (c != p) {
-            x.ncols.push_back(c);
-            x.cn += ccols_[(size_t)c];
-            nc += ccols_[(size_t)c] ? 1 : 0;
-          }
+        x.ncols.swap(pre.ncols);
+        x.cn = pre.cn;
+        for (int c : x.ncols) nc += ccols_[(size_t)c] ? 1 : 0;
         x.cfirst = nc;  // a count here, offsets below
       }
     }, 16);
@@ -1947,7 +1991,6 @@ void Factorizer<T>::step2() {
     }
   h_.ops.resize(w);
   lap("step2: rank bookkeeping");
-  (void)own;
 }
 
 // ---------------------------------------------------------------- merge

@@ -97,6 +97,12 @@ struct ArgmaxDesc {
 template <typename T>
 cudaError_t launch_copy(const CopyDesc<T>* d_desc, const int* chunk_start, int count, int total_chunks, cudaStream_t st);
 inline int copy_chunks(long long elems) { return (int)((elems + 2047) / 2048); }
+// CTAs of one copy descriptor: 2048-entry chunks, or for a transposed copy
+// 32 x 64 tiles (staged in shared memory so that reads and writes coalesce)
+inline int copy_ctas(int rows, int cols, int transpose) {
+  if (transpose) return ((rows + 31) / 32) * ((cols + 63) / 64);
+  return copy_chunks((long long)rows * cols);
+}
 // Small fronts: whole front in shared memory (smem_bytes >= m*n*sizeof(T) for every front).
 template <typename T> cudaError_t launch_front_qr_smem(const FrontDesc<T>* d, int count, int smem_bytes, cudaStream_t st);
 // Tiny fronts (c <= 128, (m|1) * n * sizeof(T) * 8 <= shared memory): one warp per
