@@ -62,6 +62,13 @@ void check_qrcp(const std::vector<int>& ms, const std::vector<int>& ns, int elem
         if (g.slab && elem == 8 && !force) ++big_fp64;
       }
       if (tot > grid_ctas) fail("grid CTAs over the co-resident budget", tot, grid_ctas);
+      // spare CTAs are spread until every member has at most 8 columns per CTA
+      // (one per warp) or the co-resident budget is used up
+      if (g.slab && tot < grid_ctas)
+        for (size_t q = 0; q < g.idx.size(); ++q) {
+          const int n = ns[(size_t)g.idx[q]], G = g.ctas[q];
+          if ((n + G - 1) / G > 8) fail("grid CTAs not spread", n, G);
+        }
       if (qrcp_grid_smem_bytes(g.m_max, g.nl_max, elem, g.slab) > kLimit) fail("grid shared memory");
       // exchange areas: back to back, each access range inside its own area
       std::vector<QrcpGridDesc> gd;

@@ -5,7 +5,8 @@ library's planner header and run on seeded random batches: every matrix or
 front is planned exactly once; each cluster, CTA-group and delayed-update
 QRCP launch fits shared memory; CTA groups stay within one CTA per SM and
 their exchange areas (arrival counters, slots, reflector buffers) are laid out
-back to back with every access range inside its own area; FP64 batches put at
+back to back with every access range inside its own area; spare CTAs of a group
+are spread until each member has at most 8 columns per CTA; FP64 batches put at
 most four matrices into CTA groups; front groups respect their size classes.
 """
 import os
