@@ -1344,23 +1344,6 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ void add_release(int* p, int v) {
   asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-// FP32 CTA groups: a CTA's proposal of step i as one 64-bit key -- the FP32
-// squared norm (low word), the column (24 bits; a group's columns fit shared
-// memory, far below 2^24) and a step tag 1..128 (never 0: the area starts
-// zeroed; buffers alternate, so a stale key differs by 2 mod 128)
-__device__ __forceinline__ unsigned grid_step_tag(int i) { return (unsigned)(i & 0x7F) + 1u; }
-__device__ __forceinline__ unsigned long long grid_key(float v, int j, int i) {
-  const unsigned jj = j == INT_MAX ? 0xFFFFFFu : (unsigned)j;
-  return ((unsigned long long)(jj | (grid_step_tag(i) << 24)) << 32) | (unsigned long long)__float_as_uint(v);
-}
 
 template <typename T, int KG, bool SMEM>
 __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T>* descs, const QrcpGridDesc* gds,
@@ -1386,8 +1369,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
   const int nl = (n + G - 1) / G;
   const int j0 = min(n, rank * nl), j1 = min(n, j0 + nl);
   const int nloc = j1 - j0;
-  const int vstride = (m_max + 3) & ~1;       // shared-memory reflector buffers
-  const int gvs = qrcp_grid_vg_stride(m_max);  // global reflector buffers (FP32: data at the end)
+  const int vstride = (m_max + 3) & ~1;
   int* tags = gd.tags;                        // arrival counters of the two buffers, 128 bytes apart
   GridSlot<T>* slots = reinterpret_cast<GridSlot<T>*>(gd.slots);  // [2][G]
   T* vg = static_cast<T*>(gd.vg);             // [2][G][vstride]
@@ -1406,8 +1388,6 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
   __shared__ int wb_j[kWarps];
   __shared__ T red_h[kWarps], red_l[kWarps];  // partial sums of squares of the CTA's best column
   __shared__ GridSlot<T> wslot[kWarps];  // best slot among each warp's 32 (winner search)
-  __shared__ N wk_v[kWarps];             // FP32 groups: best key among each warp's 32
-  __shared__ int wk_j[kWarps];
   __shared__ T s_part[kWarps * KG];  // partial dot products (few-column apply)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t e = threadIdx.x; e < (int64_t)m * nloc; e += kThreads) {
@@ -1467,7 +1447,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
   for (int i = 0; i < kmax; ++i) {
     const int par = i & 1;
     T* vb = vbuf + par * vstride;
-    T* vmine = vg + ((size_t)par * G + rank) * gvs;
+    T* vmine = vg + ((size_t)par * G + rank) * vstride;
     GridSlot<T>* myslot = slots + (size_t)par * G + rank;
     __syncthreads();  // B1: the warps' proposals of step i
     // (1) the CTA's best column (every thread reduces the warps' proposals),
@@ -1513,25 +1493,16 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
       if (threadIdx.x == 0) {
         vb[0] = T(1);
         vmine[0] = T(1);
-        if constexpr (sizeof(T) == 4) {  // the Householder data travel with the reflector
-          T* f = vmine + gvs - 8;
-          f[0] = hs.beta;
-          f[1] = hs.tau;
-          f[2] = hs.bh;
-          f[3] = hs.bl;
-          f[4] = hs.stop ? T(1) : T(0);
-        } else {
-          GridSlot<T> sl;
-          sl.v = best.v;
-          sl.beta = hs.beta;
-          sl.tau = hs.tau;
-          sl.set_b(hs.bh, hs.bl);
-          sl.j = jloc;
-          sl.stop = hs.stop ? 1 : 0;
-          *myslot = sl;
-        }
+        GridSlot<T> sl;
+        sl.v = best.v;
+        sl.beta = hs.beta;
+        sl.tau = hs.tau;
+        sl.set_b(hs.bh, hs.bl);
+        sl.j = jloc;
+        sl.stop = hs.stop ? 1 : 0;
+        *myslot = sl;
       }
-    } else if (sizeof(T) == 8 && threadIdx.x == 0) {
+    } else if (threadIdx.x == 0) {
       GridSlot<T> sl;
       sl.v = N(-1);
       sl.beta = T(0);
@@ -1541,132 +1512,69 @@ __global__ void __launch_bounds__(kThreads, 1) qrcp_grid_kernel(const QrcpDesc<T
       sl.stop = 1;
       *myslot = sl;
     }
+    // (2) publish: the CTA barrier orders every thread's stores before thread 0's
+    // release increment of the step counter (cumulative at gpu scope); buffer
+    // par counts G arrivals every second step
+    __syncthreads();  // B2
+    if (threadIdx.x == 0) {
+      add_release(tags + 32 * par, 1);
+      // (3) wait for every CTA of the matrix (bounded); the acquire load makes
+      // the step's slots and reflectors visible to the CTA after the barrier
+      const int target = G * (i / 2 + 1) + missing;  // missing > 0 only in failure-path tests
+      const long long t0 = clock64();
+      int spins = 0;
+      while (ld_acquire(tags + 32 * par) < target) {
+        if (((++spins) & 255) == 0 && clock64() - t0 > wait_cycles) {
+          s_late = 1;
+          break;
+        }
+      }
+    }
+    __syncthreads();  // B3
+    if (s_late) {
+      if (threadIdx.x == 0) {
+        atomicExch(tags + kQrcpLateTag, 1);
+        d.rank[0] = -1;
+      }
+      return;
+    }
+    // (4) the winner (lowest column index on ties): warp w loads slots
+    // 32 w .. 32 w + 31 (one per lane, all in one round), keeps its best whole
+    // slot; after a barrier every thread reduces those
+    const int nsw = (G + 31) >> 5;
+    if (warp < nsw) {
+      const int t = (warp << 5) + lane;
+      GridSlot<T> mine;
+      mine.v = N(-1);
+      mine.j = INT_MAX;
+      if (t < G) {
+        const GridSlot<T>* sl = slots + (size_t)par * G + t;
+        mine.v = __ldcg(&sl->v);
+        mine.j = __ldcg(&sl->j);
+        mine.beta = __ldcg(&sl->beta);
+        mine.tau = __ldcg(&sl->tau);
+        mine.stop = __ldcg(&sl->stop);
+        mine.load_b(sl);
+      }
+      N v = mine.v;
+      int j = mine.j;
+      const int who = warp_argmax(v, j);
+      if (lane == who) wslot[warp] = mine;
+    }
+    __syncthreads();  // B3b
     int owner = -1;
     GridSlot<T> win;
     win.v = N(-1);
     win.j = INT_MAX;
-    const int nsw = (G + 31) >> 5;
-    if constexpr (sizeof(T) == 4) {
-      // (2) publish one key per CTA with a release store (after the barrier: every
-      // thread's reflector rows and thread 0's Householder data come first);
-      // (3) warp w polls the keys of CTAs 32 w .. 32 w + 31 with acquire loads
-      // (bounded) -- arrival and proposal in one round -- and keeps the best
-      __syncthreads();  // B2
-      if (threadIdx.x == 0)
-        st_release_u64(reinterpret_cast<unsigned long long*>(slots + (size_t)par * G + rank), grid_key(best.v, jloc, i));
-      if (warp < nsw) {
-        const int t = (warp << 5) + lane;
-        N v = N(-1);
-        int j = INT_MAX;
-        if (t < G) {
-          const unsigned long long* kp = reinterpret_cast<const unsigned long long*>(slots + (size_t)par * G + t);
-          const unsigned tag = grid_step_tag(i);
-          const long long t0 = clock64();
-          int spins = 0;
-          unsigned long long kv = 0;
-          bool ok = true;
-          for (;;) {  // missing > 0 only in failure-path tests: the wait then expires
-            kv = ld_acquire_u64(kp);
-            if (missing == 0 && (unsigned)(kv >> 56) == tag) break;
-            if (((++spins) & 255) == 0 && clock64() - t0 > wait_cycles) {
-              ok = false;
-              break;
-            }
-          }
-          if (!ok) {
-            s_late = 1;
-          } else {
-            v = __uint_as_float((unsigned)kv);
-            const unsigned jj = (unsigned)(kv >> 32) & 0xFFFFFFu;
-            j = jj == 0xFFFFFFu ? INT_MAX : (int)jj;
-          }
-        }
-        warp_argmax(v, j);
-        if (lane == 0) {
-          wk_v[warp] = v;
-          wk_j[warp] = j;
-        }
-      }
-      __syncthreads();  // B3
-      if (s_late) {
-        if (threadIdx.x == 0) {
-          atomicExch(tags + kQrcpLateTag, 1);
-          d.rank[0] = -1;
-        }
-        return;
-      }
-      for (int w = 0; w < nsw; ++w)
-        if (prop_better(wk_v[w], wk_j[w], win.v, win.j)) {
-          win.v = wk_v[w];
-          win.j = wk_j[w];
-        }
-      if (win.j != INT_MAX) owner = win.j / nl;  // CTA t holds columns [t nl, (t + 1) nl)
-      if (owner < 0) break;  // no proposal (non-finite norms): every CTA sees the same
-      const T* fo = vg + ((size_t)par * G + owner) * gvs + gvs - 8;
-      win.beta = __ldcg(fo);
-      win.tau = __ldcg(fo + 1);
-      win.set_b(__ldcg(fo + 2), __ldcg(fo + 3));
-      win.stop = __ldcg(fo + 4) != T(0) ? 1 : 0;
-    } else {
-      // (2) publish: the CTA barrier orders every thread's stores before thread 0's
-      // release increment of the step counter (cumulative at gpu scope); buffer
-      // par counts G arrivals every second step
-      __syncthreads();  // B2
-      if (threadIdx.x == 0) {
-        add_release(tags + 32 * par, 1);
-        // (3) wait for every CTA of the matrix (bounded); the acquire load makes
-        // the step's slots and reflectors visible to the CTA after the barrier
-        const int target = G * (i / 2 + 1) + missing;  // missing > 0 only in failure-path tests
-        const long long t0 = clock64();
-        int spins = 0;
-        while (ld_acquire(tags + 32 * par) < target) {
-          if (((++spins) & 255) == 0 && clock64() - t0 > wait_cycles) {
-            s_late = 1;
-            break;
-          }
-        }
-      }
-      __syncthreads();  // B3
-      if (s_late) {
-        if (threadIdx.x == 0) {
-          atomicExch(tags + kQrcpLateTag, 1);
-          d.rank[0] = -1;
-        }
-        return;
-      }
-      // (4) the winner (lowest column index on ties): warp w loads slots
-      // 32 w .. 32 w + 31 (one per lane, all in one round), keeps its best whole
-      // slot; after a barrier every thread reduces those
-      if (warp < nsw) {
-        const int t = (warp << 5) + lane;
-        GridSlot<T> mine;
-        mine.v = N(-1);
-        mine.j = INT_MAX;
-        if (t < G) {
-          const GridSlot<T>* sl = slots + (size_t)par * G + t;
-          mine.v = __ldcg(&sl->v);
-          mine.j = __ldcg(&sl->j);
-          mine.beta = __ldcg(&sl->beta);
-          mine.tau = __ldcg(&sl->tau);
-          mine.stop = __ldcg(&sl->stop);
-          mine.load_b(sl);
-        }
-        N v = mine.v;
-        int j = mine.j;
-        const int who = warp_argmax(v, j);
-        if (lane == who) wslot[warp] = mine;
-      }
-      __syncthreads();  // B3b
-      for (int w = 0; w < nsw; ++w)
-        if (prop_better(wslot[w].v, wslot[w].j, win.v, win.j)) win = wslot[w];
-      if (win.j != INT_MAX) owner = win.j / nl;  // CTA t holds columns [t nl, (t + 1) nl)
-      if (owner < 0) break;  // no proposal (non-finite norms): every CTA sees the same
-    }
+    for (int w = 0; w < nsw; ++w)
+      if (prop_better(wslot[w].v, wslot[w].j, win.v, win.j)) win = wslot[w];
+    if (win.j != INT_MAX) owner = win.j / nl;  // CTA t holds columns [t nl, (t + 1) nl)
+    if (owner < 0) break;  // no proposal (non-finite norms): every CTA sees the same
     if (i == 0) r11 = win.b_acc();
     if (win.stop) break;  // rank reached: the same decision everywhere
     const int p = win.j;
     if (rank != owner) {
-      const T* vo = vg + ((size_t)par * G + owner) * gvs;
+      const T* vo = vg + ((size_t)par * G + owner) * vstride;
       for (int r = threadIdx.x; r < m - i; r += kThreads) vb[r] = __ldcg(vo + r);
     }
     const T tau = win.tau;

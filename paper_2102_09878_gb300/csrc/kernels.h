@@ -184,7 +184,7 @@ constexpr int kQrcpWarpCap = 24 << 10;  // per-warp region limit for the warp QR
 // holds): matrix f of a launch runs on CTAs [cta0, cta0 + ctas) and exchanges
 // proposals and reflectors through tags / slots / vg (device memory; tags holds
 // the two arrival counters at ints 0 and 32, zeroed before the launch; vg
-// holds 2 x ctas x qrcp_grid_vg_stride(m_max) elements).
+// holds 2 x ctas x ((m_max + 3) & ~1) elements).
 struct QrcpSlot {
   double v, beta, tau;
   int j, stop;
@@ -202,12 +202,9 @@ inline size_t qrcp_grid_tag_bytes(int ctas) {
   return (std::max<size_t>((size_t)2 * ctas, 64) * sizeof(int) + 255) & ~size_t(255);
 }
 inline size_t qrcp_grid_slot_bytes(int ctas) { return ((size_t)2 * ctas * sizeof(QrcpSlot) + 255) & ~size_t(255); }
-// elements per CTA and buffer of the reflector area: the reflector's rows, then
-// (FP32 groups) the step's Householder data in the last 8 entries
-SPAQR_HD inline int qrcp_grid_vg_stride(int m_max) { return ((m_max + 3) & ~1) + 8; }
 inline size_t qrcp_grid_xchg_bytes(int ctas, int m_max, int elem) {
   return qrcp_grid_tag_bytes(ctas) + qrcp_grid_slot_bytes(ctas) +
-         (((size_t)2 * ctas * qrcp_grid_vg_stride(m_max) * elem + 255) & ~size_t(255));
+         (((size_t)2 * ctas * ((m_max + 3) & ~1) * elem + 255) & ~size_t(255));
 }
 // descriptors of one grid-mode group whose exchange areas are laid out back to
 // back from x (qrcp_grid_xchg_bytes each); returns the total CTA count
