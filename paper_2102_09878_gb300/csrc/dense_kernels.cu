@@ -181,7 +181,6 @@ template <>
 struct SqSum<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s = fma(x, x, s); }
-  __device__ __forceinline__ void merge(const SqSum& o) { s += o.s; }
   __device__ __forceinline__ void warp_total(double& hi, double& lo) {
     hi = warp_sum(s);
     lo = 0.0;
@@ -194,11 +193,6 @@ struct SqSum<float> {
     const DF p = df_sqr(x);
     const DF t = df_two_sum(s, p.hi);
     c += t.lo + p.lo;
-    s = t.hi;
-  }
-  __device__ __forceinline__ void merge(const SqSum& o) {
-    const DF t = df_two_sum(s, o.s);
-    c = (c + o.c) + t.lo;
     s = t.hi;
   }
   __device__ __forceinline__ void warp_total(float& hi, float& lo) {
