@@ -379,7 +379,33 @@ __global__ void __launch_bounds__(kThreads) front_qr_smem_kernel(const FrontDesc
         }
       }
     } else if (tau != T(0)) {
-      for (int cc = j + 2 + (warp - 1); cc < n; cc += kWarps - 1) apply_reflector_col(S, m, m, j, tau, cc);
+      // two columns per pass: their dot products and warp sums are independent
+      const int lane = threadIdx.x & 31;
+      const T* v = S + (int64_t)j * m;
+      int cc = j + 2 + (warp - 1);
+      for (; cc + (kWarps - 1) < n; cc += 2 * (kWarps - 1)) {
+        T* c0 = S + (int64_t)cc * m;
+        T* c1 = S + (int64_t)(cc + kWarps - 1) * m;
+        T a0 = T(0), a1 = T(0);
+        for (int i = j + 1 + lane; i < m; i += 32) {
+          const T vi = v[i];
+          a0 += vi * c0[i];
+          a1 += vi * c1[i];
+        }
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        const T w0 = tau * (c0[j] + a0), w1 = tau * (c1[j] + a1);
+        if (lane == 0) {
+          c0[j] -= w0;
+          c1[j] -= w1;
+        }
+        for (int i = j + 1 + lane; i < m; i += 32) {
+          const T vi = v[i];
+          c0[i] -= w0 * vi;
+          c1[i] -= w1 * vi;
+        }
+      }
+      if (cc < n) apply_reflector_col(S, m, m, j, tau, cc);
     }
     __syncthreads();
   }
@@ -432,8 +458,17 @@ __global__ void __launch_bounds__(kThreads) front_qr_warp_kernel(const FrontDesc
       const T tt = h.tau;
       for (int cc = j + 1 + lane; cc < n; cc += 32) {
         T* x = S + cc * ld;
-        T sacc = x[j];
-        for (int r = j + 1; r < m; ++r) sacc += col[r] * x[r];
+        // four independent partial sums (rows j+1.. in steps of four)
+        T s0 = x[j], s1 = T(0), s2 = T(0), s3 = T(0);
+        int r = j + 1;
+        for (; r + 3 < m; r += 4) {
+          s0 += col[r] * x[r];
+          s1 += col[r + 1] * x[r + 1];
+          s2 += col[r + 2] * x[r + 2];
+          s3 += col[r + 3] * x[r + 3];
+        }
+        for (; r < m; ++r) s0 += col[r] * x[r];
+        const T sacc = (s0 + s1) + (s2 + s3);
         const T w = tt * sacc;
         x[j] -= w;
         for (int r = j + 1; r < m; ++r) x[r] -= w * col[r];
