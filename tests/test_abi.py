@@ -51,6 +51,19 @@ def test_compute_entry_points_fail_cleanly_without_gpu(lib):
     assert b"device" in lib.spaqr_last_error()
 
 
+def test_block_cache_is_empty_and_releasable_without_gpu(lib):
+    """Host-only cache bookkeeping: nothing cached before any factorization,
+    and releasing an empty cache is a no-op (the device wait it starts with
+    finds no device here)."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    assert lib.spaqr_cached_bytes() == 0
+    lib.spaqr_release_cached_memory()
+    assert lib.spaqr_cached_bytes() == 0
+
+
 def test_analyze_rejects_bad_grid(lib):
     from paper_2102_09878_gb300 import capi
 
