@@ -381,7 +381,8 @@ int spaqr_dense_qrcp_route(int count, double* const* A, const int* m, const int*
                            double* const* V, double* const* taus, int* rank, int route, void* stream);
 /* spaqr_dense_qrcp_f32: spaqr_dense_qrcp_route in FP32 (the arithmetic of the
  * mixed-precision factorization's pivoted QRs: FP32 data and updates, partial
- * column norms for the pivot order in FP32, R_ii and the eps rank test in FP64),
+ * column norms for the pivot order in FP32, R_ii and the eps rank test to FP64
+ * accuracy in double-float arithmetic),
  * exposed for testing. */
 int spaqr_dense_qrcp_f32(int count, float* const* A, const int* m, const int* n, const int* ld, double eps,
                          float* const* V, float* const* taus, int* rank, int route, void* stream);

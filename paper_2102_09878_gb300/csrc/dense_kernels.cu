@@ -6,10 +6,13 @@
 //    a panel kernel (reflectors + the compact-WY factor T) and a multi-CTA
 //    trailing update C <- C - V (T^T (V^T C)).
 //  * column-pivoted QR (Section 2.5, the rank-revealing QR of Section 4):
-//    one CTA per matrix, pivot by the largest remaining column norm (norms
-//    kept in FP64), stop at |R_ii| < eps |R_11|.
-//  * reflector application, triangular solve X R^{-1}, batched block copies
-//    and the max-norm row assignment (Section 2.2).
+//    a warp, a CTA, a thread-block cluster or a group of CTAs per matrix with
+//    column slabs in shared memory, pivot by the largest remaining column norm
+//    (norms in the data's precision), stop at |R_ii| < eps |R_11| (R_ii and
+//    the test to FP64 accuracy).
+//  * reflector application (compact WY blocks for FP32 row vectors),
+//    triangular solve X R^{-1}, batched block copies and the max-norm row
+//    assignment (Section 2.2).
 #include <cooperative_groups.h>
 
 #include <atomic>

@@ -197,7 +197,8 @@ def test_qrcp_wide_fp64_shallow_panels():
 @pytest.mark.parametrize("route", ["cluster", "grid", "auto"])
 def test_qrcp_f32_matches_oracle(route):
     """The FP32 pivoted QR of the mixed-precision factorization (FP32 data and
-    pivot norms as in single-precision LAPACK, R_ii and the rank test in FP64) against the
+    pivot norms as in single-precision LAPACK, R_ii and the rank test to FP64 accuracy in
+    double-float arithmetic) against the
     FP64 oracle on matrices whose spectrum leaves no doubt about the rank at
     eps = 1e-4 (singular values in [1e-2, 1] above a gap to 1e-7): same rank,
     same pivots, rows and reflectors within FP32 accuracy (5e-4 relative: FP32
